@@ -1,0 +1,1060 @@
+/*
+ * rtw_oracle.c -- plain FP64 CPU oracle of the Ray Theory of Waves far field.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py load it.  It shares no code with the CUDA library.
+ *
+ * Scalar double precision, one ray at a time, compiled with -ffp-contract=off.  OpenMP is
+ * used only to run independent rays side by side (and atomics for the accumulation); no
+ * step is blocked, fused or reordered.  The steps follow the paper (Ren et al.,
+ * arXiv:2403.13856) in its order:
+ *   O1  trace of one ray through the object, every interaction by Eq. (SnellVec),
+ *       Eq. (Fres), the step-by-step Jones update and Eq. (WavefrontEqVec); every internal leg
+ *       by free propagation of Q; amplitude by Eqs. (IntVCRM)/(DivFactVCRM); phase by
+ *       Eqs. (PhasePath)/(PhaseTotal).
+ *   O2  the RTW strategy ("Strategy of Ray Theory of Waves"): the map t -> (direction, A, Phi)
+ *       is interpolated onto the observation directions and all rays are summed (principle iii).
+ *   O3  the same hits, each evaluated exactly by Newton on the trace (the definition the
+ *       interpolation approximates).
+ *   O4  physical-optics "simple integration" over the exit wavefront near an in-plane fold
+ *       ("Diffraction effect correction based on VCRM").
+ */
+#include "rtw_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+static const double PI = 3.14159265358979323846;
+/* rays whose |cos| of incidence falls below this are dropped (grazing, P' singular) */
+static const double GRAZE = 1e-9;
+
+struct or_object {
+    double semi[3];
+    double R[3][3]; /* body -> world, columns are the body axes */
+    double center[3];
+    double W[3][3]; /* (x-c)^T W (x-c) = 1 on the surface */
+    double m;       /* n_object / n_host */
+    double lambda;  /* wavelength in the host medium (um) */
+    double k0;
+    cplx jones[2];
+    double zstart;
+    double S[2][2]; /* projected cross-section: (dx,dy) S (dx,dy)^T <= 1 */
+    double Sinv[2][2];
+    double Lmax, Lmin;
+};
+
+/* ------------------------------------------------------------------------------------- */
+/* small linear algebra                                                                  */
+/* ------------------------------------------------------------------------------------- */
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double norm3(const double* a) { return sqrt(dot3(a, a)); }
+
+static void matvec3(const double M[3][3], const double* v, double* out)
+{
+    for (int i = 0; i < 3; ++i) out[i] = M[i][0] * v[0] + M[i][1] * v[1] + M[i][2] * v[2];
+}
+
+static double det2(const double A[2][2]) { return A[0][0] * A[1][1] - A[0][1] * A[1][0]; }
+
+static int inv2(const double A[2][2], double B[2][2])
+{
+    double d = det2(A);
+    if (d == 0.0) return 0;
+    B[0][0] = A[1][1] / d;
+    B[0][1] = -A[0][1] / d;
+    B[1][0] = -A[1][0] / d;
+    B[1][1] = A[0][0] / d;
+    return 1;
+}
+
+static void mul2(const double A[2][2], const double B[2][2], double C[2][2])
+{
+    double t[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) t[i][j] = A[i][0] * B[0][j] + A[i][1] * B[1][j];
+    memcpy(C, t, sizeof(t));
+}
+
+static void transpose2(const double A[2][2], double B[2][2])
+{
+    double t[2][2] = {{A[0][0], A[1][0]}, {A[0][1], A[1][1]}};
+    memcpy(B, t, sizeof(t));
+}
+
+/* number of negative eigenvalues of a symmetric 2x2 matrix (its symmetric part) */
+static int neg_eigs(const double A[2][2])
+{
+    double off = 0.5 * (A[0][1] + A[1][0]);
+    double det = A[0][0] * A[1][1] - off * off;
+    double tr = A[0][0] + A[1][1];
+    if (det < 0.0) return 1;
+    if (det > 0.0 && tr < 0.0) return 2;
+    if (det == 0.0 && tr < 0.0) return 1;
+    return 0;
+}
+
+/* (-i)^n: the phase factor of n focal lines, each e^{-i pi/2} */
+static cplx minus_i_pow(int n)
+{
+    switch (((n % 4) + 4) % 4) {
+    case 0: return 1.0;
+    case 1: return -I;
+    case 2: return -1.0;
+    default: return I;
+    }
+}
+
+static double wrap_angle(double a)
+{
+    while (a > PI) a -= 2.0 * PI;
+    while (a <= -PI) a += 2.0 * PI;
+    return a;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* object                                                                                */
+/* ------------------------------------------------------------------------------------- */
+
+int or_object_size(void) { return (int)sizeof(or_object); }
+
+int or_make_object(const double* p, or_object* o)
+{
+    memset(o, 0, sizeof(*o));
+    for (int i = 0; i < 3; ++i) {
+        if (!(p[i] > 0.0)) return -1;
+        o->semi[i] = p[i];
+    }
+    double w = p[3], x = p[4], y = p[5], z = p[6];
+    double qn = sqrt(w * w + x * x + y * y + z * z);
+    if (!(qn > 0.0)) return -1;
+    w /= qn; x /= qn; y /= qn; z /= qn;
+    /* rotation matrix of the unit quaternion (w, x, y, z), body -> world */
+    o->R[0][0] = 1 - 2 * (y * y + z * z);
+    o->R[0][1] = 2 * (x * y - w * z);
+    o->R[0][2] = 2 * (x * z + w * y);
+    o->R[1][0] = 2 * (x * y + w * z);
+    o->R[1][1] = 1 - 2 * (x * x + z * z);
+    o->R[1][2] = 2 * (y * z - w * x);
+    o->R[2][0] = 2 * (x * z - w * y);
+    o->R[2][1] = 2 * (y * z + w * x);
+    o->R[2][2] = 1 - 2 * (x * x + y * y);
+    for (int i = 0; i < 3; ++i) o->center[i] = p[7 + i];
+    o->m = p[10];
+    o->lambda = p[11];
+    if (!(o->m > 0.0) || o->m == 1.0 || !(o->lambda > 0.0)) return -1;
+    o->k0 = 2.0 * PI / o->lambda;
+    o->jones[0] = p[12] + I * p[13];
+    o->jones[1] = p[14] + I * p[15];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += o->R[i][k] * o->R[j][k] / (o->semi[k] * o->semi[k]);
+            o->W[i][j] = s;
+        }
+    o->Lmax = fmax(o->semi[0], fmax(o->semi[1], o->semi[2]));
+    o->Lmin = fmin(o->semi[0], fmin(o->semi[1], o->semi[2]));
+    o->zstart = o->center[2] - 2.0 * o->Lmax - 1.0;
+    /* silhouette along z: the Schur complement of W_zz */
+    o->S[0][0] = o->W[0][0] - o->W[0][2] * o->W[0][2] / o->W[2][2];
+    o->S[0][1] = o->W[0][1] - o->W[0][2] * o->W[1][2] / o->W[2][2];
+    o->S[1][0] = o->S[0][1];
+    o->S[1][1] = o->W[1][1] - o->W[1][2] * o->W[1][2] / o->W[2][2];
+    if (!inv2(o->S, o->Sinv)) return -1;
+    return 0;
+}
+
+double or_fan_halfwidth(const or_object* o, double fan_phi)
+{
+    double e0 = cos(fan_phi), e1 = sin(fan_phi);
+    double q = e0 * (o->S[0][0] * e0 + o->S[0][1] * e1) + e1 * (o->S[1][0] * e0 + o->S[1][1] * e1);
+    return 1.0 / sqrt(q);
+}
+
+void or_square_grid(const or_object* o, int64_t n_target, double h_in, double* h, int64_t* nx,
+                    int64_t* ny, double* x0, double* y0)
+{
+    /* spacing so that about n_target grid points fall inside the projected ellipse, whose
+     * area is pi / sqrt(det S) */
+    double hh = h_in > 0.0 ? h_in : sqrt(PI / (sqrt(det2(o->S)) * (double)n_target));
+    double X = sqrt(o->Sinv[0][0]), Y = sqrt(o->Sinv[1][1]);
+    int64_t kx = (int64_t)ceil(X / hh), ky = (int64_t)ceil(Y / hh);
+    *h = hh;
+    *nx = 2 * kx + 2;
+    *ny = 2 * ky + 2;
+    /* x_i = cx + (i + 1/2 - nx/2) h */
+    *x0 = o->center[0];
+    *y0 = o->center[1];
+}
+
+static double grid_coord(double c, int64_t i, int64_t n, double h)
+{
+    return c + ((double)i + 0.5 - (double)(n / 2)) * h;
+}
+
+double or_caustic_cap(const or_object* o)
+{
+    /* GO is off by O(1) within about one Airy width (lambda/L)^(2/3) of a fold, where dA/dOmega
+     * grows like L^2 (L/lambda)^(1/3); rays beyond that cap are treated as caustic */
+    return o->Lmax * o->Lmax * cbrt(o->Lmax / o->lambda);
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* O1: one ray                                                                           */
+/* ------------------------------------------------------------------------------------- */
+
+typedef struct {
+    double k[3];    /* unit propagation direction */
+    double n;       /* refractive index of the medium */
+    double u[2][3]; /* wavefront basis, orthonormal, perpendicular to k */
+    double Q[2][2]; /* wavefront curvature matrix in (u1, u2) */
+    cplx E[2];      /* field components along u1, u2 */
+    double T[2][2]; /* transverse offset of this wave per unit incident offset (x, y) */
+} wave_t;
+
+typedef struct {
+    wave_t refl, trans;
+    int trans_ok;
+    double cos_in, cos_trans; /* |k.n| of the incident and the transmitted wave */
+} split_t;
+
+/* builds one outgoing wave (reflected or transmitted) of an interaction */
+static void outgoing(const or_object* o, const double s[2][3], const double nh[3],
+                     const double C[2][2], const double kvi[3], double ki,
+                     const double PQP[2][2], const double PiinvT[2][2], const wave_t* in,
+                     const double kv[3], double kmag, double n_med, const double ep[3],
+                     cplx c_perp, cplx c_par, cplx Eperp, cplx Epar, wave_t* out)
+{
+    (void)o;
+    for (int c = 0; c < 3; ++c) out->k[c] = kv[c] / kmag;
+    out->n = n_med;
+    /* outgoing wavefront basis: (e_perp, e_perp x k') */
+    for (int c = 0; c < 3; ++c) out->u[0][c] = ep[c];
+    cross3(ep, out->k, out->u[1]);
+    /* P' (Eq. Theta-r): P'_ab = s_a . v_b */
+    double Pp[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) Pp[a][b] = dot3(s[a], out->u[b]);
+    /* right-hand side of the wavefront equation: k_i P_i Q_i P_i^T + C n.(k' - k_i) */
+    double dk[3] = {kv[0] - kvi[0], kv[1] - kvi[1], kv[2] - kvi[2]};
+    double cn = dot3(nh, dk);
+    double M[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) M[a][b] = ki * PQP[a][b] + C[a][b] * cn;
+    /* Q' = P'^{-1} M P'^{-T} / k' */
+    double Ppinv[2][2], PpinvT[2][2], tmp[2][2];
+    inv2(Pp, Ppinv);
+    transpose2(Ppinv, PpinvT);
+    mul2(Ppinv, M, tmp);
+    mul2(tmp, PpinvT, out->Q);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) out->Q[a][b] /= kmag;
+    /* transverse offsets: t_c = P_i^{-T} t_i, t' = P'^T t_c */
+    double PpT[2][2];
+    transpose2(Pp, PpT);
+    mul2(PpT, PiinvT, tmp);
+    mul2(tmp, in->T, out->T);
+    out->E[0] = c_perp * Eperp;
+    out->E[1] = c_par * Epar;
+}
+
+/* one reflection / refraction at surface point r, wave `in` arriving from the medium in->n into
+ * the medium n_other.  Returns 0 for a grazing ray. */
+static int interact(const or_object* o, const double r[3], const wave_t* in, double n_other,
+                    split_t* sp)
+{
+    double x[3] = {r[0] - o->center[0], r[1] - o->center[1], r[2] - o->center[2]};
+    double g[3];
+    matvec3(o->W, x, g);
+    double gn = norm3(g);
+    double nh[3] = {g[0] / gn, g[1] / gn, g[2] / gn}; /* outward normal */
+    double cos_i = dot3(in->k, nh);
+    if (fabs(cos_i) < GRAZE) return 0;
+    /* e_perp normal to the incident plane (Fig. 2) */
+    double ep[3];
+    cross3(in->k, nh, ep);
+    double len = norm3(ep);
+    if (len < 1e-12) {
+        for (int c = 0; c < 3; ++c) ep[c] = in->u[0][c];
+    } else {
+        for (int c = 0; c < 3; ++c) ep[c] /= len;
+    }
+    /* surface basis (s1, s2) = (e_perp, n x e_perp) and the curvature matrix C in it:
+     * second fundamental form of the quadric with respect to the outward normal */
+    double s[2][3];
+    for (int c = 0; c < 3; ++c) s[0][c] = ep[c];
+    cross3(nh, ep, s[1]);
+    double C[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            double Ws[3];
+            matvec3(o->W, s[b], Ws);
+            C[a][b] = dot3(s[a], Ws) / gn;
+        }
+    /* Eq. (SnellVec): the tangential component of the wave vector is kept */
+    double ki = o->k0 * in->n, kt = o->k0 * n_other;
+    double kin = ki * cos_i; /* signed normal component of the incident wave vector */
+    double kvi[3], ktau[3], kvl[3], kvt[3] = {0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+        kvi[c] = ki * in->k[c];
+        ktau[c] = kvi[c] - kin * nh[c];
+        kvl[c] = ktau[c] - kin * nh[c];
+    }
+    double ktau2 = dot3(ktau, ktau);
+    double ktn2 = kt * kt - ktau2;
+    cplx ktn;
+    if (ktn2 > 0.0) {
+        double kr = copysign(sqrt(ktn2), kin);
+        ktn = kr;
+        for (int c = 0; c < 3; ++c) kvt[c] = ktau[c] + kr * nh[c];
+        sp->trans_ok = 1;
+    } else {
+        /* total internal reflection: evanescent normal component, decaying on the far side */
+        ktn = I * copysign(sqrt(-ktn2), kin);
+        sp->trans_ok = 0;
+    }
+    /* Eq. (Fres), with m the index of the far medium relative to the near one */
+    double mr = n_other / in->n;
+    cplx rperp = (kin - ktn) / (kin + ktn);
+    cplx rpar = (mr * mr * kin - ktn) / (mr * mr * kin + ktn);
+    cplx tperp = 2.0 * kin / (kin + ktn);
+    cplx tpar = 2.0 * mr * kin / (mr * mr * kin + ktn);
+    /* incident field projected on (e_perp, e_par_i), e_par_i = e_perp x k_i */
+    double epi[3];
+    cross3(ep, in->k, epi);
+    cplx Eperp = in->E[0] * dot3(in->u[0], ep) + in->E[1] * dot3(in->u[1], ep);
+    cplx Epar = in->E[0] * dot3(in->u[0], epi) + in->E[1] * dot3(in->u[1], epi);
+    /* incident term of Eq. (WavefrontEqVec): P_i Q_i P_i^T with P_i,ab = s_a . u_b */
+    double Pi[2][2], PiT[2][2], tmp[2][2], PQP[2][2], Piinv[2][2], PiinvT[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) Pi[a][b] = dot3(s[a], in->u[b]);
+    transpose2(Pi, PiT);
+    mul2(Pi, in->Q, tmp);
+    mul2(tmp, PiT, PQP);
+    inv2(Pi, Piinv);
+    transpose2(Piinv, PiinvT);
+    outgoing(o, s, nh, C, kvi, ki, PQP, PiinvT, in, kvl, ki, in->n, ep, rperp, rpar, Eperp, Epar,
+             &sp->refl);
+    if (sp->trans_ok)
+        outgoing(o, s, nh, C, kvi, ki, PQP, PiinvT, in, kvt, kt, n_other, ep, tperp, tpar, Eperp,
+                 Epar, &sp->trans);
+    sp->cos_in = fabs(cos_i);
+    sp->cos_trans = sp->trans_ok ? fabs(dot3(sp->trans.k, nh)) : 0.0;
+    return 1;
+}
+
+/* length of the chord from surface point r along the inward direction k */
+static double chord(const or_object* o, const double r[3], const double k[3])
+{
+    double u[3] = {r[0] - o->center[0], r[1] - o->center[1], r[2] - o->center[2]};
+    double Wk[3], Wu[3];
+    matvec3(o->W, k, Wk);
+    matvec3(o->W, u, Wu);
+    double A = dot3(k, Wk), B = dot3(k, Wu), Cq = dot3(u, Wu) - 1.0;
+    double disc = B * B - A * Cq;
+    if (disc < 0.0) disc = 0.0;
+    return (-B + sqrt(disc)) / A;
+}
+
+/* free propagation of the wavefront over distance d: Q(d) = Q (I + d Q)^{-1}; the leg's
+ * Gaussian-curvature ratio kappa_G(q+1)/kappa'_Gq = 1/det(I + d Q) enters D_p (Eq. DivFactVCRM)
+ * and every negative eigenvalue of I + d Q is a focal line crossed */
+static int propagate(wave_t* w, double d, double* dlegs, int* nf)
+{
+    double A[2][2] = {{1.0 + d * w->Q[0][0], d * w->Q[0][1]}, {d * w->Q[1][0], 1.0 + d * w->Q[1][1]}};
+    double detA = det2(A), Ainv[2][2];
+    if (detA == 0.0 || !inv2(A, Ainv)) return 0;
+    mul2(w->Q, Ainv, w->Q);
+    *dlegs /= fabs(detA);
+    *nf += neg_eigs(A);
+    mul2(A, w->T, w->T);
+    return 1;
+}
+
+/* far-field record of an outgoing wave leaving the object at rexit */
+static void far_field(const or_object* o, const wave_t* w, const double rexit[3], double path,
+                      double dlegs, int nf_legs, double cosprod, int nrefl, double* rec)
+{
+    double detQ = det2(w->Q);
+    if (!(fabs(detQ) > 0.0) || !isfinite(detQ)) return;
+    /* last leg to infinity: kappa_GM / kappa'_G(p+1) -> 1/(r^2 det Q'); r^2 is removed */
+    int nf = nf_legs + neg_eigs(w->Q);
+    double D = dlegs / fabs(detQ);
+    cplx ph = minus_i_pow(nf) * sqrt(D);
+    for (int c = 0; c < 3; ++c) {
+        cplx Fc = ph * (w->E[0] * w->u[0][c] + w->E[1] * w->u[1][c]);
+        rec[OR_F + 2 * c] = creal(Fc);
+        rec[OR_F + 2 * c + 1] = cimag(Fc);
+    }
+    /* Eq. (PhasePath) read for the far field: optical path to the exit point minus s.r_exit */
+    rec[OR_PSI] = o->k0 * (path - dot3(w->k, rexit));
+    double J[2][2];
+    mul2(w->Q, w->T, J);
+    double detJ = det2(J);
+    double vx[3];
+    cross3(w->u[0], w->u[1], vx);
+    double hand = dot3(w->k, vx) > 0.0 ? 1.0 : -1.0;
+    rec[OR_VALID] = 1.0;
+    rec[OR_NF] = (double)nf;
+    rec[OR_ORIENT] = (detJ > 0.0 ? 1.0 : -1.0) * hand;
+    rec[OR_NREFL] = (double)nrefl;
+    for (int c = 0; c < 3; ++c) {
+        rec[OR_S + c] = w->k[c];
+        rec[OR_V1 + c] = w->u[0][c];
+        rec[OR_V2 + c] = w->u[1][c];
+        rec[OR_REXIT + c] = rexit[c];
+    }
+    rec[OR_D] = D;
+    rec[OR_DGEO] = 1.0 / fabs(detJ);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            rec[OR_J + 2 * a + b] = J[a][b];
+            rec[OR_Q + 2 * a + b] = w->Q[a][b];
+        }
+    rec[OR_E + 0] = creal(w->E[0]);
+    rec[OR_E + 1] = cimag(w->E[0]);
+    rec[OR_E + 2] = creal(w->E[1]);
+    rec[OR_E + 3] = cimag(w->E[1]);
+    rec[OR_DLEGS] = dlegs;
+    rec[OR_NFLEGS] = (double)nf_legs;
+    rec[OR_PATH] = path;
+    double e2 = creal(w->E[0] * conj(w->E[0]) + w->E[1] * conj(w->E[1]));
+    rec[OR_POWER] = e2 * cosprod;
+    rec[OR_COSPROD] = cosprod;
+    rec[OR_CAUSTIC] = rec[OR_DGEO] > or_caustic_cap(o) ? 1.0 : 0.0;
+}
+
+int or_trace_ray(const or_object* o, double x, double y, int pmax, double* out, double* p_inside)
+{
+    memset(out, 0, sizeof(double) * (size_t)(pmax + 1) * OR_NFIELD);
+    if (p_inside) *p_inside = 0.0;
+    /* incident ray of the plane wave, started below the object */
+    double r0[3] = {x, y, o->zstart};
+    double u[3] = {r0[0] - o->center[0], r0[1] - o->center[1], r0[2] - o->center[2]};
+    double Wu[3];
+    matvec3(o->W, u, Wu);
+    double A = o->W[2][2], B = Wu[2], Cq = dot3(u, Wu) - 1.0;
+    double disc = B * B - A * Cq;
+    if (!(disc > 0.0)) return 0;
+    double t = (-B - sqrt(disc)) / A;
+    double r[3] = {r0[0], r0[1], r0[2] + t};
+    wave_t w;
+    memset(&w, 0, sizeof(w));
+    w.k[2] = 1.0;
+    w.n = 1.0;
+    w.u[0][0] = 1.0;
+    w.u[1][1] = 1.0;
+    w.E[0] = o->jones[0];
+    w.E[1] = o->jones[1];
+    w.T[0][0] = 1.0;
+    w.T[1][1] = 1.0;
+    /* phase of the incident plane wave at the first point, zero at the origin (Phi_i) */
+    double path = r[2];
+    double dlegs = 1.0, cosprod = 1.0;
+    int nf = 0, nrefl = 0;
+    for (int q = 1; q <= pmax + 1; ++q) {
+        double n_other = (q == 1) ? o->m : 1.0;
+        split_t sp;
+        if (!interact(o, r, &w, n_other, &sp)) return 1;
+        if (q == 1) {
+            /* p = 0: external reflection, Eq. (epsilon_VCRM) first line */
+            far_field(o, &sp.refl, r, path, 1.0, 0, 1.0, 1, out);
+            if (!sp.trans_ok) return 1;
+            w = sp.trans;
+            cosprod *= sp.cos_trans / sp.cos_in;
+        } else {
+            /* p = q - 1 leaves by refraction; the reflected wave continues inside */
+            if (sp.trans_ok)
+                far_field(o, &sp.trans, r, path, dlegs, nf, cosprod * sp.cos_trans / sp.cos_in,
+                          nrefl, out + (size_t)(q - 1) * OR_NFIELD);
+            w = sp.refl;
+            nrefl++;
+        }
+        if (q == pmax + 1) break;
+        double d = chord(o, r, w.k);
+        if (!(d > 0.0)) return 1;
+        if (!propagate(&w, d, &dlegs, &nf)) return 1;
+        path += w.n * d;
+        for (int c = 0; c < 3; ++c) r[c] += d * w.k[c];
+    }
+    if (p_inside) {
+        double e2 = creal(w.E[0] * conj(w.E[0]) + w.E[1] * conj(w.E[1]));
+        *p_inside = e2 * w.n * cosprod;
+    }
+    return 1;
+}
+
+void or_trace_rays(const or_object* o, const double* xy, int64_t n, int pmax, double* out,
+                   int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < n; ++i)
+        or_trace_ray(o, xy[2 * i], xy[2 * i + 1], pmax, out + (size_t)i * (pmax + 1) * OR_NFIELD, NULL);
+    (void)nthreads;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* O3: Newton on the exact trace                                                          */
+/* ------------------------------------------------------------------------------------- */
+
+int or_newton(const or_object* o, int p, const double target[3], double* xy, double* rec)
+{
+    double* buf = (double*)malloc(sizeof(double) * (size_t)(p + 1) * OR_NFIELD);
+    int ret = -1;
+    for (int it = 0; it < 30; ++it) {
+        or_trace_ray(o, xy[0], xy[1], p, buf, NULL);
+        const double* r = buf + (size_t)p * OR_NFIELD;
+        if (r[OR_VALID] == 0.0) break;
+        double d[3] = {target[0] - r[OR_S], target[1] - r[OR_S + 1], target[2] - r[OR_S + 2]};
+        if (norm3(d) < 1e-13) {
+            memcpy(rec, r, sizeof(double) * OR_NFIELD);
+            ret = it;
+            break;
+        }
+        double rhs0 = dot3(r + OR_V1, d), rhs1 = dot3(r + OR_V2, d);
+        double J[2][2] = {{r[OR_J], r[OR_J + 1]}, {r[OR_J + 2], r[OR_J + 3]}}, Ji[2][2];
+        if (!inv2(J, Ji)) break;
+        xy[0] += Ji[0][0] * rhs0 + Ji[0][1] * rhs1;
+        xy[1] += Ji[1][0] * rhs0 + Ji[1][1] * rhs1;
+    }
+    free(buf);
+    return ret;
+}
+
+/* Newton in the impact parameter b of a fan: in-plane exit angle alpha(b) = alpha_t */
+static int newton_fan(const or_object* o, int p, double fan_phi, double alpha_t, double* b,
+                      double* rec)
+{
+    double ef[3] = {cos(fan_phi), sin(fan_phi), 0.0};
+    double* buf = (double*)malloc(sizeof(double) * (size_t)(p + 1) * OR_NFIELD);
+    int ret = -1;
+    for (int it = 0; it < 40; ++it) {
+        or_trace_ray(o, o->center[0] + *b * ef[0], o->center[1] + *b * ef[1], p, buf, NULL);
+        const double* r = buf + (size_t)p * OR_NFIELD;
+        if (r[OR_VALID] == 0.0) break;
+        double al = atan2(dot3(r + OR_S, ef), r[OR_S + 2]);
+        double da = wrap_angle(alpha_t - al);
+        if (fabs(da) < 1e-13) {
+            memcpy(rec, r, sizeof(double) * OR_NFIELD);
+            ret = it;
+            break;
+        }
+        /* d s / d b = J (ef_x, ef_y) in the exit basis; d alpha = (d s) . e_alpha */
+        double j0 = r[OR_J] * ef[0] + r[OR_J + 1] * ef[1];
+        double j1 = r[OR_J + 2] * ef[0] + r[OR_J + 3] * ef[1];
+        double ds[3];
+        for (int c = 0; c < 3; ++c) ds[c] = j0 * r[OR_V1 + c] + j1 * r[OR_V2 + c];
+        double ea[3] = {cos(al) * ef[0], cos(al) * ef[1], -sin(al)};
+        double dadb = dot3(ds, ea);
+        if (dadb == 0.0) break;
+        *b += da / dadb;
+    }
+    free(buf);
+    return ret;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* O2 / O3 / O4 on a 1-D fan                                                              */
+/* ------------------------------------------------------------------------------------- */
+
+/* contribution F e^{i Psi} of one record projected on (e_theta, e_phi) */
+static void project_add(const double F[6], double psi, const double eth[3], const double eph[3],
+                        double weight, double* acc)
+{
+    cplx ph = cexp(I * psi);
+    cplx ft = 0.0, fp = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        cplx Fc = (F[2 * c] + I * F[2 * c + 1]) * ph;
+        ft += Fc * eth[c];
+        fp += Fc * eph[c];
+    }
+    acc[0] += weight * creal(ft);
+    acc[1] += weight * cimag(ft);
+    acc[2] += weight * creal(fp);
+    acc[3] += weight * cimag(fp);
+}
+
+/* 1 for |x| <= x0, cos^2 ramp to 0 at x1 */
+static double ramp(double x, double x0, double x1)
+{
+    if (x <= x0) return 1.0;
+    if (x >= x1) return 0.0;
+    double c = cos(0.5 * PI * (x - x0) / (x1 - x0));
+    return c * c;
+}
+
+typedef struct {
+    int p;
+    int64_t jc, jlo, jhi; /* fold ray and window rays [jlo, jhi] */
+    double alpha_c;
+    int ok;
+    double* xap;   /* aperture crossing points, 3 per ray */
+    cplx* U;       /* aperture field, 3 per ray, times taper, dxi and the sagittal factor */
+} po_window;
+
+int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, const double* alpha,
+                 int64_t ndir, int flags, double* out, uint8_t* mask)
+{
+    const int np = pmax + 1;
+    double wdt = or_fan_halfwidth(o, fan_phi);
+    double ef[3] = {cos(fan_phi), sin(fan_phi), 0.0};
+    double* rec = (double*)malloc(sizeof(double) * (size_t)nrays * np * OR_NFIELD);
+    double* al = (double*)malloc(sizeof(double) * (size_t)nrays * np);
+    double* bj = (double*)malloc(sizeof(double) * (size_t)nrays);
+    if (!rec || !al || !bj) return -1;
+    for (int64_t j = 0; j < nrays; ++j) {
+        double b = -wdt + ((double)j + 0.5) * (2.0 * wdt / (double)nrays);
+        bj[j] = b;
+        or_trace_ray(o, o->center[0] + b * ef[0], o->center[1] + b * ef[1], pmax,
+                     rec + (size_t)j * np * OR_NFIELD, NULL);
+        for (int p = 0; p < np; ++p) {
+            const double* r = rec + ((size_t)j * np + p) * OR_NFIELD;
+            al[j * np + p] = atan2(dot3(r + OR_S, ef), r[OR_S + 2]);
+        }
+    }
+    memset(out, 0, sizeof(double) * (size_t)ndir * np * 4);
+    memset(mask, 0, (size_t)ndir);
+    /* target directions and their (e_theta, e_phi) */
+    double* eth = (double*)malloc(sizeof(double) * 3 * (size_t)ndir);
+    double* eph = (double*)malloc(sizeof(double) * 3 * (size_t)ndir);
+    double* dirv = (double*)malloc(sizeof(double) * 3 * (size_t)ndir);
+    double axial = 2.0 * o->lambda / o->Lmin;
+    for (int64_t k = 0; k < ndir; ++k) {
+        double a = alpha[k];
+        double th = fabs(a), ph = a >= 0.0 ? fan_phi : fan_phi + PI;
+        eth[3 * k] = cos(th) * cos(ph);
+        eth[3 * k + 1] = cos(th) * sin(ph);
+        eth[3 * k + 2] = -sin(th);
+        eph[3 * k] = -sin(ph);
+        eph[3 * k + 1] = cos(ph);
+        eph[3 * k + 2] = 0.0;
+        dirv[3 * k] = sin(th) * cos(ph);
+        dirv[3 * k + 1] = sin(th) * sin(ph);
+        dirv[3 * k + 2] = cos(th);
+        if (th < axial || th > PI - axial) mask[k] |= OR_MASK_AXIAL;
+    }
+    /* angular scales of a fold of an object of size L: the Airy width (lambda/L)^(2/3) and the
+     * Fresnel width 1/sqrt(k0 L) of the aperture plane through the object centre.  The PO value
+     * is used alone within 1.5 Airy widths of the fold direction and blended into the ray sum by
+     * 3; the aperture keeps every ray of the fold within 3 Airy + 3 Fresnel widths and tapers
+     * the next 3 Fresnel widths to zero. */
+    const double Aw = pow(o->lambda / o->Lmax, 2.0 / 3.0), Fw = 1.0 / sqrt(o->k0 * o->Lmax);
+    const double po_full = 1.5 * Aw, po_end = 3.0 * Aw;
+    const double ap_full = 3.0 * Aw + 3.0 * Fw, ap_end = 3.0 * Aw + 6.0 * Fw;
+
+    for (int p = 0; p < np; ++p) {
+        /* ---- O4: in-plane folds of this order and their aperture fields ---- */
+        int nwin = 0;
+        po_window win[8];
+        if ((flags & OR_FIELD_PO) && p >= 1) {
+            for (int64_t j = 1; j + 1 < nrays && nwin < 8; ++j) {
+                const double* r0 = rec + ((size_t)(j - 1) * np + p) * OR_NFIELD;
+                const double* r1 = rec + ((size_t)j * np + p) * OR_NFIELD;
+                const double* r2 = rec + ((size_t)(j + 1) * np + p) * OR_NFIELD;
+                if (r0[OR_VALID] == 0.0 || r1[OR_VALID] == 0.0 || r2[OR_VALID] == 0.0) continue;
+                double d0 = wrap_angle(al[j * np + p] - al[(j - 1) * np + p]);
+                double d1 = wrap_angle(al[(j + 1) * np + p] - al[j * np + p]);
+                if (!(d0 * d1 < 0.0)) continue;
+                po_window* wv = &win[nwin];
+                wv->p = p;
+                wv->jc = j;
+                wv->alpha_c = al[j * np + p];
+                /* the window walks along the fan while the rays stay valid, within ap_end of the
+                 * fold direction, on the same side of the +-pi seam and without another fold */
+                int64_t lo = j, hi = j;
+                while (lo - 1 >= 0 && rec[((size_t)(lo - 1) * np + p) * OR_NFIELD + OR_VALID] != 0.0 &&
+                       fabs(wrap_angle(al[(lo - 1) * np + p] - wv->alpha_c)) < ap_end &&
+                       fabs(al[(lo - 1) * np + p] - al[lo * np + p]) < PI &&
+                       (al[(lo - 1) * np + p] - al[lo * np + p]) * d0 < 0.0)
+                    --lo;
+                while (hi + 1 < nrays && rec[((size_t)(hi + 1) * np + p) * OR_NFIELD + OR_VALID] != 0.0 &&
+                       fabs(wrap_angle(al[(hi + 1) * np + p] - wv->alpha_c)) < ap_end &&
+                       fabs(al[(hi + 1) * np + p] - al[hi * np + p]) < PI &&
+                       (al[(hi + 1) * np + p] - al[hi * np + p]) * d1 > 0.0)
+                    ++hi;
+                wv->jlo = lo;
+                wv->jhi = hi;
+                int64_t nw = hi - lo + 1;
+                wv->xap = (double*)malloc(sizeof(double) * 3 * (size_t)nw);
+                wv->U = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)nw);
+                double* xi = (double*)malloc(sizeof(double) * (size_t)nw);
+                /* aperture: the line of the fan plane through the object centre, perpendicular to
+                 * the fold ray (the plane of the virtual exit wavefront) */
+                const double* rc = o->center;
+                const double* sc = r1 + OR_S;
+                double exi[3] = {cos(wv->alpha_c) * ef[0], cos(wv->alpha_c) * ef[1], -sin(wv->alpha_c)};
+                double npl[3];
+                double zz[3] = {0, 0, 1};
+                cross3(ef, zz, npl); /* normal of the plane of the fan (sagittal direction) */
+                wv->ok = nw >= 3;
+                for (int64_t i = lo; i <= hi && wv->ok; ++i) {
+                    const double* ri = rec + ((size_t)i * np + p) * OR_NFIELD;
+                    double dd[3] = {rc[0] - ri[OR_REXIT], rc[1] - ri[OR_REXIT + 1], rc[2] - ri[OR_REXIT + 2]};
+                    double tau = dot3(sc, dd) / dot3(sc, ri + OR_S);
+                    double* xa = wv->xap + 3 * (i - lo);
+                    for (int c = 0; c < 3; ++c) xa[c] = ri[OR_REXIT + c] + tau * ri[OR_S + c];
+                    double rel[3] = {xa[0] - rc[0], xa[1] - rc[1], xa[2] - rc[2]};
+                    xi[i - lo] = dot3(exi, rel);
+                    /* carry the exit wave along its ray to the aperture line (forward for
+                     * tau > 0, backward for tau < 0); each focal line passed on the way adds
+                     * e^{-i pi/2} going forward and e^{+i pi/2} going backward */
+                    double Q[2][2] = {{ri[OR_Q], ri[OR_Q + 1]}, {ri[OR_Q + 2], ri[OR_Q + 3]}};
+                    double Am[2][2] = {{1.0 + tau * Q[0][0], tau * Q[0][1]}, {tau * Q[1][0], 1.0 + tau * Q[1][1]}};
+                    double dA = det2(Am), Ai[2][2], Qa[2][2];
+                    if (dA == 0.0 || !inv2(Am, Ai)) {
+                        wv->ok = 0;
+                        break;
+                    }
+                    int nfl = neg_eigs(Am);
+                    int nf_ap = (int)ri[OR_NFLEGS] + (tau > 0.0 ? nfl : -nfl);
+                    mul2(Q, Ai, Qa);
+                    double c1 = dot3(npl, ri + OR_V1), c2 = dot3(npl, ri + OR_V2);
+                    double Qs = c1 * (Qa[0][0] * c1 + Qa[0][1] * c2) + c2 * (Qa[1][0] * c1 + Qa[1][1] * c2);
+                    if (Qs == 0.0) {
+                        wv->ok = 0;
+                        break;
+                    }
+                    double Rs = 1.0 / Qs;
+                    double Dap = ri[OR_DLEGS] / fabs(dA);
+                    cplx E0 = ri[OR_E] + I * ri[OR_E + 1], E1 = ri[OR_E + 2] + I * ri[OR_E + 3];
+                    cplx amp = sqrt(Dap) * minus_i_pow(nf_ap) *
+                               cexp(I * o->k0 * (ri[OR_PATH] + tau));
+                    /* sagittal Fresnel integral: sqrt(|R_s|) e^{i pi/4 sgn R_s} */
+                    cplx sag = sqrt(fabs(Rs)) * cexp(I * 0.25 * PI * (Rs > 0.0 ? 1.0 : -1.0));
+                    double tap = ramp(fabs(wrap_angle(al[i * np + p] - wv->alpha_c)), ap_full, ap_end);
+                    for (int c = 0; c < 3; ++c)
+                        wv->U[3 * (i - lo) + c] = tap * sag * amp * (E0 * ri[OR_V1 + c] + E1 * ri[OR_V2 + c]);
+                }
+                /* trapezoid weights |d xi| along the ray parameter: where rays cross before the
+                 * line, each branch through a point of the aperture is counted */
+                if (wv->ok) {
+                    for (int64_t i = 0; i < nw; ++i) {
+                        double dxi;
+                        if (i == 0) dxi = 0.5 * (xi[1] - xi[0]);
+                        else if (i == nw - 1) dxi = 0.5 * (xi[nw - 1] - xi[nw - 2]);
+                        else dxi = 0.5 * (xi[i + 1] - xi[i - 1]);
+                        for (int c = 0; c < 3; ++c) wv->U[3 * i + c] *= fabs(dxi);
+                    }
+                }
+                free(xi);
+                ++nwin;
+            }
+        }
+
+        /* ---- O2 (or O3): segment (j, j+1) owns alpha with lambda in [0, 1) ---- */
+        for (int64_t j = 0; j + 1 < nrays; ++j) {
+            const double* ra = rec + ((size_t)j * np + p) * OR_NFIELD;
+            const double* rb = rec + ((size_t)(j + 1) * np + p) * OR_NFIELD;
+            if (ra[OR_VALID] == 0.0 || rb[OR_VALID] == 0.0) continue;
+            int consistent = ra[OR_NF] == rb[OR_NF] && ra[OR_ORIENT] == rb[OR_ORIENT] &&
+                             ra[OR_CAUSTIC] == 0.0 && rb[OR_CAUSTIC] == 0.0;
+            double a0 = al[j * np + p];
+            double da = wrap_angle(al[(j + 1) * np + p] - a0);
+            if (da == 0.0) continue;
+            int wi = -1;
+            for (int w = 0; w < nwin; ++w)
+                if (win[w].ok && j >= win[w].jlo && j + 1 <= win[w].jhi) wi = w;
+            for (int64_t k = 0; k < ndir; ++k) {
+                double lam = wrap_angle(alpha[k] - a0) / da;
+                if (!(lam >= 0.0 && lam < 1.0)) continue;
+                if (!consistent) {
+                    if (wi < 0) mask[k] |= OR_MASK_CAUSTIC;
+                    continue;
+                }
+                double wgo = 1.0;
+                if (wi >= 0) wgo = 1.0 - ramp(fabs(wrap_angle(alpha[k] - win[wi].alpha_c)), po_full, po_end);
+                if (wgo == 0.0) continue;
+                double* acc = out + ((size_t)k * np + p) * 4;
+                if (flags & OR_FIELD_EXACT) {
+                    double b = bj[j] + lam * (bj[j + 1] - bj[j]);
+                    double* r = (double*)malloc(sizeof(double) * OR_NFIELD);
+                    if (newton_fan(o, p, fan_phi, alpha[k], &b, r) >= 0) {
+                        project_add(r + OR_F, r[OR_PSI], eth + 3 * k, eph + 3 * k, wgo, acc);
+                        free(r);
+                        continue;
+                    }
+                    free(r);
+                }
+                double F[6], psi = (1.0 - lam) * ra[OR_PSI] + lam * rb[OR_PSI];
+                for (int c = 0; c < 6; ++c) F[c] = (1.0 - lam) * ra[OR_F + c] + lam * rb[OR_F + c];
+                project_add(F, psi, eth + 3 * k, eph + 3 * k, wgo, acc);
+            }
+        }
+
+        /* ---- O4: the PO integral over the window, blended in around the fold ---- */
+        for (int w = 0; w < nwin; ++w) {
+            po_window* wv = &win[w];
+            if (!wv->ok) continue;
+            cplx pre = sqrt(o->k0 / (2.0 * PI)) * (-I);
+            for (int64_t k = 0; k < ndir; ++k) {
+                double s = ramp(fabs(wrap_angle(alpha[k] - wv->alpha_c)), po_full, po_end);
+                if (s == 0.0) continue;
+                cplx ft = 0.0, fp = 0.0;
+                for (int64_t i = 0; i <= wv->jhi - wv->jlo; ++i) {
+                    cplx e = cexp(-I * o->k0 * dot3(dirv + 3 * k, wv->xap + 3 * i));
+                    for (int c = 0; c < 3; ++c) {
+                        ft += wv->U[3 * i + c] * e * eth[3 * k + c];
+                        fp += wv->U[3 * i + c] * e * eph[3 * k + c];
+                    }
+                }
+                ft *= pre * s;
+                fp *= pre * s;
+                double* acc = out + ((size_t)k * np + p) * 4;
+                acc[0] += creal(ft);
+                acc[1] += cimag(ft);
+                acc[2] += creal(fp);
+                acc[3] += cimag(fp);
+                mask[k] |= OR_MASK_PO;
+            }
+        }
+        for (int w = 0; w < nwin; ++w) {
+            free(win[w].xap);
+            free(win[w].U);
+        }
+    }
+    free(rec);
+    free(al);
+    free(bj);
+    free(eth);
+    free(eph);
+    free(dirv);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* O2 / O3 on a 2-D square ray grid and the (theta, phi) direction grid                    */
+/* ------------------------------------------------------------------------------------- */
+
+typedef struct {
+    double s[3];
+    double F[6];
+    double psi;
+    double x, y; /* impact point */
+    int valid, nf, orient, caustic;
+} crec;
+
+/* edge function (s_lo x s_hi) . x with the endpoints in canonical order (lower ray id first),
+ * returned for the traversal a -> b; both triangles sharing the edge evaluate the same product */
+static double edge_fn(int64_t ia, const double* sa, int64_t ib, const double* sb, const double* x)
+{
+    double c[3];
+    if (ia < ib) {
+        cross3(sa, sb, c);
+        return dot3(c, x);
+    }
+    cross3(sb, sa, c);
+    return -dot3(c, x);
+}
+
+/* half-open inside rule for one edge of a triangle of orientation sigma */
+static int edge_in(double e, int64_t ia, int64_t ib, int sigma)
+{
+    double se = sigma > 0 ? e : -e;
+    if (se > 0.0) return 1;
+    if (se < 0.0) return 0;
+    return (ia < ib) == (sigma > 0);
+}
+
+int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta,
+                      int nphi, const int64_t* window, int flags, double* out, uint8_t* mask,
+                      int nthreads, int64_t* newton_fail)
+{
+    const int np = pmax + 1;
+    double h, xc, yc;
+    int64_t nx, ny;
+    or_square_grid(o, n_target, h_in, &h, &nx, &ny, &xc, &yc);
+    int64_t ix0 = 0, ix1 = nx - 1, iy0 = 0, iy1 = ny - 1; /* cells [ix0, ix1) x [iy0, iy1) */
+    if (window) {
+        ix0 = window[0] < 0 ? 0 : window[0];
+        ix1 = window[1] > nx - 1 ? nx - 1 : window[1];
+        iy0 = window[2] < 0 ? 0 : window[2];
+        iy1 = window[3] > ny - 1 ? ny - 1 : window[3];
+    }
+    if (ix1 <= ix0 || iy1 <= iy0) return 0;
+    int64_t wx = ix1 - ix0 + 1, wy = iy1 - iy0 + 1;
+    crec* cr = (crec*)malloc(sizeof(crec) * (size_t)wx * wy * np);
+    if (!cr) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double* buf = (double*)malloc(sizeof(double) * (size_t)np * OR_NFIELD);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t jy = 0; jy < wy; ++jy)
+            for (int64_t jx = 0; jx < wx; ++jx) {
+                double x = grid_coord(xc, ix0 + jx, nx, h), y = grid_coord(yc, iy0 + jy, ny, h);
+                /* only points strictly inside the projected cross-section are rays */
+                double dx = x - xc, dy = y - yc;
+                double qf = dx * (o->S[0][0] * dx + o->S[0][1] * dy) + dy * (o->S[1][0] * dx + o->S[1][1] * dy);
+                if (qf < 1.0) or_trace_ray(o, x, y, pmax, buf, NULL);
+                else memset(buf, 0, sizeof(double) * (size_t)np * OR_NFIELD);
+                for (int p = 0; p < np; ++p) {
+                    const double* r = buf + (size_t)p * OR_NFIELD;
+                    crec* c = cr + ((size_t)(jy * wx + jx) * np + p);
+                    memcpy(c->s, r + OR_S, sizeof(c->s));
+                    memcpy(c->F, r + OR_F, sizeof(c->F));
+                    c->psi = r[OR_PSI];
+                    c->x = x;
+                    c->y = y;
+                    c->valid = r[OR_VALID] != 0.0;
+                    c->nf = (int)r[OR_NF];
+                    c->orient = (int)r[OR_ORIENT];
+                    c->caustic = r[OR_CAUSTIC] != 0.0;
+                }
+            }
+        free(buf);
+    }
+    const int64_t ndir = (int64_t)ntheta * nphi;
+    memset(out, 0, sizeof(double) * (size_t)ndir * np * 4);
+    memset(mask, 0, (size_t)ndir);
+    const double dth = PI / ntheta, dph = 2.0 * PI / nphi;
+    double axial = 2.0 * o->lambda / o->Lmin;
+    for (int i = 0; i < ntheta; ++i) {
+        double th = (i + 0.5) * dth;
+        if (th < axial || th > PI - axial)
+            for (int j = 0; j < nphi; ++j) mask[(int64_t)i * nphi + j] |= OR_MASK_AXIAL;
+    }
+    int64_t hits = 0, nfail = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : hits, nfail)
+#endif
+    for (int64_t row = 0; row < (int64_t)np * (iy1 - iy0); ++row) {
+        int p = (int)(row / (iy1 - iy0));
+        int64_t cy = iy0 + row % (iy1 - iy0);
+        double* nbuf = (double*)malloc(sizeof(double) * OR_NFIELD);
+        for (int64_t cx = ix0; cx < ix1; ++cx) {
+            /* the cell (cx, cy) is split along its diagonal into two counter-clockwise triangles */
+            int64_t c00 = cy * nx + cx, c10 = c00 + 1, c01 = c00 + nx, c11 = c01 + 1;
+            int64_t tri[2][3] = {{c00, c10, c11}, {c00, c11, c01}};
+            for (int t = 0; t < 2; ++t) {
+                const crec* R[3];
+                int64_t id[3];
+                for (int v = 0; v < 3; ++v) {
+                    id[v] = tri[t][v];
+                    int64_t gx = id[v] % nx, gy = id[v] / nx;
+                    R[v] = cr + ((size_t)((gy - iy0) * wx + (gx - ix0)) * np + p);
+                }
+                if (!R[0]->valid || !R[1]->valid || !R[2]->valid) continue;
+                int consistent = R[0]->nf == R[1]->nf && R[1]->nf == R[2]->nf &&
+                                 R[0]->orient == R[1]->orient && R[1]->orient == R[2]->orient &&
+                                 !R[0]->caustic && !R[1]->caustic && !R[2]->caustic;
+                double c12[3];
+                cross3(R[1]->s, R[2]->s, c12);
+                double vol = dot3(R[0]->s, c12);
+                int sigma = vol > 0.0 ? 1 : (vol < 0.0 ? -1 : 0);
+                if (sigma == 0) continue;
+                if (sigma != R[0]->orient) consistent = 0; /* folded inside the cell */
+                /* candidate directions: the cap around the normalised corner mean */
+                double cm[3] = {R[0]->s[0] + R[1]->s[0] + R[2]->s[0], R[0]->s[1] + R[1]->s[1] + R[2]->s[1],
+                                R[0]->s[2] + R[1]->s[2] + R[2]->s[2]};
+                double cn = norm3(cm);
+                if (!(cn > 0.0)) continue;
+                for (int c = 0; c < 3; ++c) cm[c] /= cn;
+                double mind = 1.0;
+                for (int v = 0; v < 3; ++v) mind = fmin(mind, dot3(cm, R[v]->s));
+                double rho = acos(fmax(-1.0, fmin(1.0, mind))) + 1e-9;
+                double thc = atan2(sqrt(cm[0] * cm[0] + cm[1] * cm[1]), cm[2]);
+                double phc = atan2(cm[1], cm[0]);
+                int it0 = (int)ceil((thc - rho) / dth - 0.5), it1 = (int)floor((thc + rho) / dth - 0.5);
+                if (it0 < 0) it0 = 0;
+                if (it1 > ntheta - 1) it1 = ntheta - 1;
+                int allphi = (thc - rho <= 0.0) || (thc + rho >= PI);
+                double dphi = 0.0;
+                if (!allphi) {
+                    double sr = sin(rho) / sin(thc);
+                    if (sr >= 1.0) allphi = 1;
+                    else dphi = asin(sr);
+                }
+                int64_t jp0 = 0, jcount = nphi;
+                if (!allphi) {
+                    jp0 = (int64_t)ceil((phc - dphi + PI) / dph - 0.5);
+                    int64_t jp1 = (int64_t)floor((phc + dphi + PI) / dph - 0.5);
+                    jcount = jp1 - jp0 + 1;
+                    if (jcount > nphi) {
+                        jp0 = 0;
+                        jcount = nphi;
+                    }
+                }
+                for (int it = it0; it <= it1; ++it) {
+                    double th = (it + 0.5) * dth;
+                    for (int64_t jj = 0; jj < jcount; ++jj) {
+                        int64_t jp = ((jp0 + jj) % nphi + nphi) % nphi;
+                        double ph = -PI + (jp + 0.5) * dph;
+                        double x[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+                        double e01 = edge_fn(id[0], R[0]->s, id[1], R[1]->s, x);
+                        double e12 = edge_fn(id[1], R[1]->s, id[2], R[2]->s, x);
+                        double e20 = edge_fn(id[2], R[2]->s, id[0], R[0]->s, x);
+                        if (!edge_in(e01, id[0], id[1], sigma) || !edge_in(e12, id[1], id[2], sigma) ||
+                            !edge_in(e20, id[2], id[0], sigma))
+                            continue;
+                        int64_t dk = (int64_t)it * nphi + jp;
+                        if (!consistent) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                            mask[dk] |= OR_MASK_CAUSTIC;
+                            continue;
+                        }
+                        /* barycentric weights of the central projection onto the corner plane */
+                        double ssum = e01 + e12 + e20;
+                        double l0 = e12 / ssum, l1 = e20 / ssum, l2 = e01 / ssum;
+                        double F[6], psi;
+                        int done = 0;
+                        if (flags & OR_FIELD_EXACT) {
+                            double xy[2] = {l0 * R[0]->x + l1 * R[1]->x + l2 * R[2]->x,
+                                            l0 * R[0]->y + l1 * R[1]->y + l2 * R[2]->y};
+                            if (or_newton(o, p, x, xy, nbuf) >= 0) {
+                                memcpy(F, nbuf + OR_F, sizeof(F));
+                                psi = nbuf[OR_PSI];
+                                done = 1;
+                            } else {
+                                nfail++;
+                            }
+                        }
+                        if (!done) {
+                            for (int c = 0; c < 6; ++c) F[c] = l0 * R[0]->F[c] + l1 * R[1]->F[c] + l2 * R[2]->F[c];
+                            psi = l0 * R[0]->psi + l1 * R[1]->psi + l2 * R[2]->psi;
+                        }
+                        double eth[3] = {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)};
+                        double eph[3] = {-sin(ph), cos(ph), 0.0};
+                        double acc[4] = {0, 0, 0, 0};
+                        project_add(F, psi, eth, eph, 1.0, acc);
+                        double* dst = out + ((size_t)dk * np + p) * 4;
+                        for (int c = 0; c < 4; ++c) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                            dst[c] += acc[c];
+                        }
+                        hits++;
+                    }
+                }
+            }
+        }
+        free(nbuf);
+    }
+    free(cr);
+    if (newton_fail) *newton_fail = nfail;
+    return hits;
+}

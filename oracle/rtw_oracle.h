@@ -1,0 +1,114 @@
+/*
+ * rtw_oracle.h -- plain FP64 CPU oracle of the Ray Theory of Waves (RTW) far field.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke check of
+ * __graft_entry__ and the CPU-baseline leg of bench.py may load this library.  It shares no
+ * code, header, table or constant with the CUDA library under paper_2403_13856_gb300/.
+ *
+ * Paper: K. F. Ren et al., "Ray Theory of Waves", arXiv:2403.13856.
+ *   principle (i)-(iii)           : a ray carries k, E and the WFC matrix Q (Introduction)
+ *   Eq. (WavefrontEqVec)          : k' P' Q' P'^T = k_i P_i Q_i P_i^T + C n.(k'-k_i)
+ *   Eq. (Theta-r)                 : P_ab = s_a . u_b (Appendix)
+ *   Eq. (SnellVec)                : equal tangential wave-vector components
+ *   Eq. (IntVCRM), (DivFactVCRM)  : A = A0 |eps| sqrt(D_p), D_p = |prod kappa_G ratios|
+ *   Eq. (epsilon_VCRM), (Fres)    : Fresnel factor chain and coefficients from k_in, k_rn
+ *   Eq. (PhasePath), (PhaseTotal) : optical path, Fresnel and focal-line phase
+ *   "Strategy of RTW"             : trace over intermediate variables t, then interpolate
+ *   "Diffraction effect correction": physical-optics integration near caustics
+ *
+ * Conventions (readings of the paper, all listed in the design doc):
+ *   incident plane wave along +z, E_inc = (jones_x, jones_y) e^{i k0 z}, time factor e^{-i w t};
+ *   n outward normal of the object; C > 0 for a convex surface; Q = 1/R with R > 0 diverging;
+ *   every focal line multiplies the field by e^{-i pi/2};
+ *   far field E(r s) = F e^{i Psi} e^{i k0 r} / r with F in micrometres.
+ */
+#ifndef RTW_ORACLE_H
+#define RTW_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Object parameters, flat: a b c qw qx qy qz cx cy cz m lambda jre_x jim_x jre_y jim_y */
+#define OR_NPARAM 16
+
+/* Per-(ray, order) record, flat doubles.  Integers are stored as doubles. */
+enum {
+    OR_VALID = 0,    /* 1 if this order leaves the object along a traced ray            */
+    OR_NF = 1,       /* focal lines crossed, including the last leg to infinity          */
+    OR_ORIENT = 2,   /* sign of the Jacobian of (x, y) -> s (oriented by z and by s)     */
+    OR_NREFL = 3,    /* reflections on the path                                          */
+    OR_S = 4,        /* exit direction s (3)                                             */
+    OR_F = 7,        /* far-field vector amplitude, re/im of x, y, z (6), micrometres    */
+    OR_PSI = 13,     /* far-field phase Psi (rad)                                        */
+    OR_D = 14,       /* divergence factor D_p (um^2), far-field form                     */
+    OR_DGEO = 15,    /* dA/dOmega = 1/|det J| (um^2)                                      */
+    OR_J = 16,       /* J = ds/d(x, y) in the exit basis (v1, v2), row-major (4)          */
+    OR_V1 = 20,      /* exit wavefront basis vector v1 (3)                                */
+    OR_V2 = 23,      /* exit wavefront basis vector v2 (3)                                */
+    OR_REXIT = 26,   /* exit point (3)                                                    */
+    OR_Q = 29,       /* exit WFC matrix in (v1, v2), row-major (4)                         */
+    OR_E = 33,       /* exit Jones components along v1, v2: re, im, re, im (4)            */
+    OR_DLEGS = 37,   /* product of the internal legs' divergence factors                  */
+    OR_NFLEGS = 38,  /* focal lines crossed inside the object                             */
+    OR_PATH = 39,    /* optical path from the plane z = 0 to the exit point (um)          */
+    OR_POWER = 40,   /* power fraction carried by this order                              */
+    OR_COSPROD = 41, /* product of |cos theta'| / |cos theta| over the interactions        */
+    OR_CAUSTIC = 42, /* 1 if D_geo exceeds the caustic cap                                */
+    OR_NFIELD = 48
+};
+
+/* Mask bits of a direction */
+#define OR_MASK_CAUSTIC 1u  /* covered by a cell straddling a fold or flagged near-caustic */
+#define OR_MASK_AXIAL 2u    /* within 2 lambda / min(a,b,c) of the forward or backward axis */
+#define OR_MASK_PO 4u       /* value replaced (fully or partly) by the PO integral          */
+
+/* Field flags */
+#define OR_FIELD_PO 1       /* 1-D fan: physical-optics correction around in-plane folds    */
+#define OR_FIELD_EXACT 2    /* evaluate every hit by Newton on the exact trace (O3)         */
+
+typedef struct or_object or_object;
+
+int or_object_size(void);
+/* Fills *o from the flat parameter array; returns 0, or -1 on invalid parameters. */
+int or_make_object(const double* p, or_object* o);
+
+/* Helpers describing the ray grids of the oracle. */
+double or_fan_halfwidth(const or_object* o, double fan_phi);
+void or_square_grid(const or_object* o, int64_t n_target, double h_in, double* h, int64_t* nx,
+                    int64_t* ny, double* x0, double* y0);
+double or_caustic_cap(const or_object* o);
+
+/* Traces one incident ray at impact point (x, y); out has (pmax+1)*OR_NFIELD doubles.
+ * *p_inside receives the power still travelling inside after the last interaction.
+ * Returns 1 if the ray hits the object, 0 otherwise. */
+int or_trace_ray(const or_object* o, double x, double y, int pmax, double* out, double* p_inside);
+/* Batch form, OpenMP over rays; xy is n x 2. */
+void or_trace_rays(const or_object* o, const double* xy, int64_t n, int pmax, double* out,
+                   int nthreads);
+
+/* 1-D fan (rays of impact parameter b_j = -w + (j+1/2) 2w/nrays in the plane of azimuth
+ * fan_phi).  Target directions are in-plane angles alpha (rad, (-pi, pi]) measured from +z
+ * toward (cos fan_phi, sin fan_phi, 0).  out: ndir x (pmax+1) x 4 doubles, per order
+ * (F_theta re, im, F_phi re, im).  mask: ndir bytes. */
+int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax,
+                 const double* alpha, int64_t ndir, int flags, double* out, uint8_t* mask);
+
+/* 2-D square grid (n_target rays in the projected cross-section, or spacing h_in when
+ * h_in > 0) onto the cell-centred (theta, phi) grid.  window = {ix0, ix1, iy0, iy1} limits the
+ * cells used (NULL = all).  out: ntheta*nphi x (pmax+1) x 4 doubles.  Returns the number of
+ * hits, or a negative value on failure. */
+int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta,
+                      int nphi, const int64_t* window, int flags, double* out, uint8_t* mask,
+                      int nthreads, int64_t* newton_fail);
+
+/* Newton on the exact trace: finds the ray of order p whose exit direction is target, from the
+ * seed impact point xy (2).  Returns iterations used, or -1 if it did not converge. */
+int or_newton(const or_object* o, int p, const double target[3], double* xy, double* rec);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
