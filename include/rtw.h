@@ -1,0 +1,198 @@
+/*
+ * rtw.h -- C ABI of the GB300 Ray Theory of Waves (RTW) far-field library (librtw.so).
+ *
+ * The calls follow the paper's statement of the problem (Ren et al., "Ray Theory of Waves",
+ * arXiv:2403.13856): an object (shape and refractive index, Fig. 3 caption), an incident plane
+ * wave (wavelength, direction, polarisation), and the complex far field of all rays summed at the
+ * observation directions ("Strategy of Ray Theory of Waves": rays traced over intermediate
+ * variables t, then interpolated to the directions of interest).
+ *
+ * Conventions.  Lengths in micrometres.  The host medium has index 1; m is the index of the
+ * object relative to it.  The incident wave is E_inc = (jones_x, jones_y, 0) e^{i k0 z} with the
+ * time factor e^{-i w t}.  The scattered far field is E(r s) = F(s) e^{i k0 r} / r, F in um, given
+ * as the complex pair (F_theta, F_phi) on the unit vectors e_theta, e_phi of s = (theta, phi)
+ * (theta from +z, phi from +x).  |F|^2 is the differential cross-section in um^2.
+ *
+ * Memory.  Handles (rtw_object, rtw_rays) are opaque and owned by the library; their device
+ * memory is allocated by the library with cudaMalloc and freed by the destroy functions.
+ * Every other pointer argument marked "device" is a caller-owned device buffer (for example a
+ * torch tensor) that the library reads or writes but never frees.  Host pointers are read during
+ * the call only.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is enqueued
+ * asynchronously on it; argument errors are reported synchronously by the return value.  Errors
+ * raised inside kernels (bounded loops that ran out, capacity) set a status word that
+ * rtw_sync_status() reads after synchronising the stream.
+ *
+ * Errors.  Every call returns RTW_OK (0) or a negative RTW_ERR_* code; rtw_last_error() gives a
+ * one-line message for the calling thread.  No C++ exception crosses the ABI and no call falls
+ * back to a CPU implementation: without a usable CUDA device every compute call fails with
+ * RTW_ERR_CUDA.
+ */
+#ifndef RTW_H
+#define RTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define RTW_OK 0
+#define RTW_ERR_ARG (-1)         /* invalid argument (null pointer, size, range)          */
+#define RTW_ERR_UNSUPPORTED (-2) /* valid but not implemented (absorbing m, oblique wave)  */
+#define RTW_ERR_CUDA (-3)        /* a CUDA runtime call failed or no device is usable       */
+#define RTW_ERR_CAPACITY (-4)    /* a bounded device buffer or loop ran out                 */
+#define RTW_ERR_TIMEOUT (-5)     /* a bounded device iteration gave up                      */
+#define RTW_ERR_NUMERIC (-6)     /* non-finite values where finite ones are required        */
+#define RTW_ERR_NOMEM (-7)       /* host or device allocation failed                        */
+
+/* ---- enums and flags ---- */
+#define RTW_GRID_FAN 0    /* 1-D fan of impact parameters b_j = -w + (j + 1/2) 2w/n in the plane
+                             of azimuth fan_phi through the projected centre (w: half-chord)    */
+#define RTW_GRID_SQUARE 1 /* 2-D square grid x_i = cx + (i + 1/2 - nx/2) h (same for y) covering
+                             the projected cross-section; points inside it are rays             */
+
+#define RTW_FP64 0  /* every step in double precision                                          */
+#define RTW_MIXED 1 /* geometry, Fresnel and curvature in single precision; intersection points,
+                       optical path and phase in double precision                              */
+
+#define RTW_DENSE 0  /* interpolation of the dense ray map (the paper's RTW strategy)           */
+#define RTW_NEWTON 1 /* every hit refined by Newton steps on the exact FP64 trace             */
+
+#define RTW_DIRS_PLANE 0 /* in-plane angles alpha_k = alpha0 + k dalpha, k < n_theta, measured
+                            from +z toward (cos fan_phi, sin fan_phi, 0); fan grids only        */
+#define RTW_DIRS_GRID 1  /* cell-centred theta_i = (i + 1/2) pi / n_theta,
+                            phi_j = -pi + (j + 1/2) 2 pi / n_phi, index i * n_phi + j           */
+
+#define RTW_FIELD_PER_ORDER 1 /* output one (F_theta, F_phi) pair per order instead of the sum */
+#define RTW_FIELD_PO 2        /* fan grids: physical-optics integral around in-plane folds      */
+
+#define RTW_TRACE_APERTURE 1 /* keep the exit-wave data the PO integral needs (fan grids)       */
+
+#define RTW_MASK_CAUSTIC 1u /* a cell straddling a fold or flagged near-caustic covers it     */
+#define RTW_MASK_AXIAL 2u   /* within 2 lambda / min(a, b, c) of the forward or backward axis  */
+#define RTW_MASK_PO 4u      /* value replaced (fully or in part) by the PO integral            */
+
+/* ---- descriptors ---- */
+
+/* Object: ellipsoid of semi-axes (a, b, c) along its body axes, rotated body -> world by the unit
+ * quaternion quat = (w, x, y, z) (|quat| = 1 within 1e-9), centred at center.  m_re is the
+ * refractive index relative to the host; m_im must be 0 (absorbing objects: RTW_ERR_UNSUPPORTED). */
+typedef struct {
+    double a, b, c;
+    double quat[4];
+    double center[3];
+    double m_re, m_im;
+} rtw_object_desc;
+
+/* Incident plane wave: wavelength in the host medium, direction (must be (0, 0, 1)), Jones vector
+ * (E_x, E_y) on the unit vectors x, y. */
+typedef struct {
+    double wavelength_um;
+    double dir[3];
+    double jones_re[2], jones_im[2];
+} rtw_incident;
+
+/* Ray grid and trace options.  n_rays: fan -> exact number of rays; square -> target count inside
+ * the projected cross-section (spacing h = sqrt(pi / (sqrt(det S) n_rays)), S the matrix of the
+ * projected ellipse), unless spacing > 0 gives h directly.  p_max: orders 0..p_max, p_max <= 15. */
+typedef struct {
+    int grid;
+    int p_max;
+    int precision;
+    int flags;
+    int64_t n_rays;
+    double spacing;
+    double fan_phi;
+} rtw_trace_params;
+
+/* Observation directions.  cell_window limits a square-grid field to the cells
+ * [ix0, ix1) x [iy0, iy1) of the ray grid (all four -1: every cell); it exists so that a sample of
+ * a full-size field can be checked against an independent computation. */
+typedef struct {
+    int kind;
+    int n_theta, n_phi;
+    double alpha0, dalpha;
+    int64_t cell_window[4];
+} rtw_dirs;
+
+typedef struct rtw_object rtw_object;
+typedef struct rtw_rays rtw_rays;
+
+/* ---- objects ---- */
+
+/* Validates `count` object descriptors and incident waves (inc[i] belongs to desc[i]) and uploads
+ * them: quadric matrix W = R diag(a^-2, b^-2, c^-2) R^T, projected ellipse S (Schur complement of
+ * W_zz), k0 = 2 pi / lambda.  *out receives a handle owned by the caller until
+ * rtw_destroy_object.  Errors: RTW_ERR_ARG (null, count < 1, a, b, c, lambda <= 0, m <= 0,
+ * m == 1, |quat| != 1), RTW_ERR_UNSUPPORTED (m_im != 0 or dir != (0,0,1)), RTW_ERR_CUDA,
+ * RTW_ERR_NOMEM.  Synchronous. */
+int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident* inc, rtw_object** out);
+void rtw_destroy_object(rtw_object* obj);
+
+/* Host query of the ray grid rtw_trace would use for object `index`: spacing h (fan: 2w/n), nx,
+ * ny (fan: n, 1).  Pure host arithmetic. */
+int rtw_object_grid(const rtw_object* obj, int index, const rtw_trace_params* tp, double* h, int64_t* nx,
+                    int64_t* ny);
+
+/* ---- the per-ray trace (the hot path's first half) ---- */
+
+/* Traces every ray of every object through its object and records, for each ray and order p, the
+ * exit direction s, the far-field vector amplitude F = A e^{i (Phi_F + Phi_f)} (Eqs. IntVCRM,
+ * DivFactVCRM, epsilon_VCRM, Fres, the WFC carried by Eq. WavefrontEqVec), the far-field phase Psi
+ * (Eq. PhasePath) and the flags (valid, orientation, near-caustic, focal-line count).
+ * If *inout is NULL a new rays handle is allocated; otherwise it is reused when its capacity
+ * suffices and reallocated when not.  Asynchronous on `stream`. */
+int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_rays** inout);
+
+/* Sizes of a rays handle: rays per order over all objects (square grids count misses), number of
+ * orders, number of objects. */
+int rtw_rays_info(const rtw_rays* rays, int64_t* rays_per_order, int* n_orders, int* n_objects);
+
+/* Copies the state of rays [first, first + count) of `order` into caller device buffers, any of
+ * which may be NULL: s_out (count x 3 double), F_out (count x 6 double: re, im of x, y, z),
+ * psi_out (count double), flags_out (count uint32: bit 0 valid, bit 1 orientation +, bit 2
+ * near-caustic, bits 8-15 focal-line count).  Asynchronous. */
+int rtw_rays_export(const rtw_rays* rays, int order, int64_t first, int64_t count, double* s_out,
+                    double* F_out, double* psi_out, uint32_t* flags_out, void* stream);
+void rtw_destroy_rays(rtw_rays* rays);
+
+/* Traces n explicit impact points xy (device, n x 2, um, in the plane z = const) of object
+ * `index` for orders 0..p_max in double precision and writes the same records as
+ * rtw_rays_export, laid out [n][p_max + 1] (s_out n x (p_max+1) x 3, and so on).  Asynchronous. */
+int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t n, int p_max,
+                     double* s_out, double* F_out, double* psi_out, uint32_t* flags_out, void* stream);
+
+/* ---- the field (the hot path's second half) ---- */
+
+/* Sums the complex amplitudes of all traced rays at the observation directions (principle iii of
+ * the paper) by interpolating the ray map over the triangles (square grid) or segments (fan) of
+ * neighbouring rays: a direction is owned by the cell whose image contains it (half-open rule),
+ * F and Psi are interpolated with the barycentric weights of the central projection, and
+ * F e^{i Psi} is added.  Cells whose corners disagree in focal-line count or orientation, or carry
+ * the near-caustic flag, add nothing and mark the directions they cover (RTW_MASK_CAUSTIC).  With
+ * RTW_FIELD_PO (fan grids traced with RTW_TRACE_APERTURE) the field near every in-plane fold is
+ * the physical-optics integral over the exit wave ("Diffraction effect correction based on VCRM").
+ * mode RTW_NEWTON replaces each interpolated hit by the exact ray found by Newton steps.
+ * field_out (device): [objects][directions][orders or 1][2] complex128 (F_theta, F_phi), zeroed
+ * and written.  mask_out (device, optional): [objects][directions] uint8.  Asynchronous. */
+int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
+              uint8_t* mask_out, void* stream);
+
+/* ---- status ---- */
+
+/* Synchronises `stream`, reads and clears the device status word of the library: RTW_OK or the
+ * first RTW_ERR_* a kernel raised since the last call. */
+int rtw_sync_status(void* stream);
+const char* rtw_status_string(int status);
+const char* rtw_last_error(void);
+/* Library version string. */
+const char* rtw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

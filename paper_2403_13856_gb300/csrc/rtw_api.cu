@@ -1,0 +1,538 @@
+// rtw_api.cu -- host side of the C ABI declared in include/rtw.h.
+//
+// Argument validation, object tables, ray-grid layout, device allocations and kernel launches.
+// No compute happens on the host: every step of the path runs in the kernels of rtw_trace.cu and
+// rtw_field.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rtw.h"
+#include "rtw_launch.h"
+
+using rtw::ObjDev;
+using rtw::RaysDev;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(RTW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RTW_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+struct ObjHost {
+    double a[3];
+    double R[3][3];
+    double c[3];
+    double m;
+    double lambda;
+    double jre[2], jim[2];
+    double W[3][3];
+    double S[2][2], Sinv[2][2];
+    double lmin, lmax;
+};
+
+// per-device status word of the library (error bits raised by kernels)
+std::mutex g_status_mu;
+std::vector<unsigned int*> g_status;
+
+unsigned int* status_word(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if ((int)g_status.size() <= dev) g_status.resize(dev + 1, nullptr);
+    if (!g_status[dev]) {
+        unsigned int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned int)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(unsigned int));
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct rtw_object {
+    int count = 0;
+    int device = 0;
+    std::vector<ObjHost> h;
+};
+
+struct rtw_rays {
+    int device = 0;
+    int np = 0;
+    int precision = 0;
+    int grid = 0;
+    int flags = 0;
+    int nobj = 0;
+    long long R = 0;
+    double fan_phi = 0.0;
+    std::vector<ObjDev> objs;
+    ObjDev* d_objs = nullptr;
+    size_t d_objs_cap = 0;
+    RaysDev st{};
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+void fill_objdev(const ObjHost& o, ObjDev& d)
+{
+    std::memset(&d, 0, sizeof(d));
+    d.W[0] = o.W[0][0];
+    d.W[1] = o.W[0][1];
+    d.W[2] = o.W[0][2];
+    d.W[3] = o.W[1][1];
+    d.W[4] = o.W[1][2];
+    d.W[5] = o.W[2][2];
+    for (int i = 0; i < 3; ++i) d.c[i] = o.c[i];
+    d.m = o.m;
+    d.lambda = o.lambda;
+    d.k0 = 2.0 * kPi / o.lambda;
+    d.jre[0] = o.jre[0];
+    d.jre[1] = o.jre[1];
+    d.jim[0] = o.jim[0];
+    d.jim[1] = o.jim[1];
+    d.zstart = o.c[2] - 2.0 * o.lmax - 1.0;
+    d.S[0] = o.S[0][0];
+    d.S[1] = o.S[0][1];
+    d.S[2] = o.S[1][1];
+    d.cap = o.lmax * o.lmax * std::cbrt(o.lmax / o.lambda);
+    d.lmin = o.lmin;
+    d.lmax = o.lmax;
+}
+
+// ray grid of one object (host arithmetic only)
+int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* nx, long long* ny, double* fan_w)
+{
+    if (tp->grid == RTW_GRID_FAN) {
+        if (tp->n_rays < 2) return fail(RTW_ERR_ARG, "fan needs n_rays >= 2");
+        const double e0 = std::cos(tp->fan_phi), e1 = std::sin(tp->fan_phi);
+        const double q = e0 * (o.S[0][0] * e0 + o.S[0][1] * e1) + e1 * (o.S[1][0] * e0 + o.S[1][1] * e1);
+        const double w = 1.0 / std::sqrt(q);
+        *fan_w = w;
+        *h = 2.0 * w / (double)tp->n_rays;
+        *nx = tp->n_rays;
+        *ny = 1;
+        return RTW_OK;
+    }
+    if (tp->grid != RTW_GRID_SQUARE) return fail(RTW_ERR_ARG, "unknown grid kind %d", tp->grid);
+    double hh = tp->spacing;
+    if (!(hh > 0.0)) {
+        if (tp->n_rays < 1) return fail(RTW_ERR_ARG, "square grid needs n_rays >= 1 or spacing > 0");
+        const double detS = o.S[0][0] * o.S[1][1] - o.S[0][1] * o.S[1][0];
+        hh = std::sqrt(kPi / (std::sqrt(detS) * (double)tp->n_rays));
+    }
+    const double X = std::sqrt(o.Sinv[0][0]), Y = std::sqrt(o.Sinv[1][1]);
+    const long long kx = (long long)std::ceil(X / hh), ky = (long long)std::ceil(Y / hh);
+    *h = hh;
+    *nx = 2 * kx + 2;
+    *ny = 2 * ky + 2;
+    *fan_w = 0.0;
+    return RTW_OK;
+}
+
+int ensure_device(int* dev)
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) return fail(RTW_ERR_CUDA, "no usable CUDA device (%s)", cudaGetErrorString(e));
+    RTW_CUDA(cudaGetDevice(dev));
+    return RTW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rtw_version(void) { return "rtw-gb300 0.1 (sm_103a)"; }
+
+const char* rtw_last_error(void) { return g_last_error.c_str(); }
+
+const char* rtw_status_string(int status)
+{
+    switch (status) {
+    case RTW_OK: return "ok";
+    case RTW_ERR_ARG: return "invalid argument";
+    case RTW_ERR_UNSUPPORTED: return "unsupported";
+    case RTW_ERR_CUDA: return "CUDA error";
+    case RTW_ERR_CAPACITY: return "capacity exceeded";
+    case RTW_ERR_TIMEOUT: return "bounded iteration gave up";
+    case RTW_ERR_NUMERIC: return "non-finite value";
+    case RTW_ERR_NOMEM: return "out of memory";
+    default: return "unknown status";
+    }
+}
+
+int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident* inc, rtw_object** out)
+{
+    if (!desc || !inc || !out || count < 1) return fail(RTW_ERR_ARG, "rtw_create_object: null pointer or count < 1");
+    *out = nullptr;
+    std::vector<ObjHost> hs((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const rtw_object_desc& d = desc[i];
+        const rtw_incident& w = inc[i];
+        ObjHost& o = hs[(size_t)i];
+        if (!(d.a > 0.0 && d.b > 0.0 && d.c > 0.0) || !std::isfinite(d.a + d.b + d.c))
+            return fail(RTW_ERR_ARG, "object %d: semi-axes must be positive", i);
+        const double qn = std::sqrt(d.quat[0] * d.quat[0] + d.quat[1] * d.quat[1] + d.quat[2] * d.quat[2] +
+                                    d.quat[3] * d.quat[3]);
+        if (!(std::fabs(qn - 1.0) <= 1e-9)) return fail(RTW_ERR_ARG, "object %d: |quat| = %.17g != 1", i, qn);
+        if (!(d.m_re > 0.0) || d.m_re == 1.0 || !std::isfinite(d.m_re))
+            return fail(RTW_ERR_ARG, "object %d: m must be positive and != 1", i);
+        if (d.m_im != 0.0) return fail(RTW_ERR_UNSUPPORTED, "object %d: absorbing objects (m_im != 0)", i);
+        if (!(w.wavelength_um > 0.0) || !std::isfinite(w.wavelength_um))
+            return fail(RTW_ERR_ARG, "object %d: wavelength must be positive", i);
+        if (w.dir[0] != 0.0 || w.dir[1] != 0.0 || w.dir[2] != 1.0)
+            return fail(RTW_ERR_UNSUPPORTED, "object %d: incident direction must be (0, 0, 1)", i);
+        o.a[0] = d.a;
+        o.a[1] = d.b;
+        o.a[2] = d.c;
+        const double qw = d.quat[0] / qn, qx = d.quat[1] / qn, qy = d.quat[2] / qn, qz = d.quat[3] / qn;
+        o.R[0][0] = 1 - 2 * (qy * qy + qz * qz);
+        o.R[0][1] = 2 * (qx * qy - qw * qz);
+        o.R[0][2] = 2 * (qx * qz + qw * qy);
+        o.R[1][0] = 2 * (qx * qy + qw * qz);
+        o.R[1][1] = 1 - 2 * (qx * qx + qz * qz);
+        o.R[1][2] = 2 * (qy * qz - qw * qx);
+        o.R[2][0] = 2 * (qx * qz - qw * qy);
+        o.R[2][1] = 2 * (qy * qz + qw * qx);
+        o.R[2][2] = 1 - 2 * (qx * qx + qy * qy);
+        for (int k = 0; k < 3; ++k) o.c[k] = d.center[k];
+        o.m = d.m_re;
+        o.lambda = w.wavelength_um;
+        o.jre[0] = w.jones_re[0];
+        o.jre[1] = w.jones_re[1];
+        o.jim[0] = w.jones_im[0];
+        o.jim[1] = w.jones_im[1];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += o.R[r][k] * o.R[c][k] / (o.a[k] * o.a[k]);
+                o.W[r][c] = s;
+            }
+        o.lmax = std::fmax(d.a, std::fmax(d.b, d.c));
+        o.lmin = std::fmin(d.a, std::fmin(d.b, d.c));
+        o.S[0][0] = o.W[0][0] - o.W[0][2] * o.W[0][2] / o.W[2][2];
+        o.S[0][1] = o.W[0][1] - o.W[0][2] * o.W[1][2] / o.W[2][2];
+        o.S[1][0] = o.S[0][1];
+        o.S[1][1] = o.W[1][1] - o.W[1][2] * o.W[1][2] / o.W[2][2];
+        const double det = o.S[0][0] * o.S[1][1] - o.S[0][1] * o.S[1][0];
+        o.Sinv[0][0] = o.S[1][1] / det;
+        o.Sinv[0][1] = -o.S[0][1] / det;
+        o.Sinv[1][0] = -o.S[1][0] / det;
+        o.Sinv[1][1] = o.S[0][0] / det;
+    }
+    int dev = 0;
+    int rc = ensure_device(&dev);
+    if (rc != RTW_OK) return rc;
+    rtw_object* obj = new (std::nothrow) rtw_object();
+    if (!obj) return fail(RTW_ERR_NOMEM, "rtw_create_object: host allocation");
+    obj->count = count;
+    obj->device = dev;
+    obj->h = std::move(hs);
+    *out = obj;
+    return RTW_OK;
+}
+
+void rtw_destroy_object(rtw_object* obj) { delete obj; }
+
+int rtw_object_grid(const rtw_object* obj, int index, const rtw_trace_params* tp, double* h, int64_t* nx,
+                    int64_t* ny)
+{
+    if (!obj || !tp || !h || !nx || !ny) return fail(RTW_ERR_ARG, "rtw_object_grid: null pointer");
+    if (index < 0 || index >= obj->count) return fail(RTW_ERR_ARG, "rtw_object_grid: index out of range");
+    long long a = 0, b = 0;
+    double w = 0.0;
+    int rc = grid_of(obj->h[(size_t)index], tp, h, &a, &b, &w);
+    *nx = a;
+    *ny = b;
+    return rc;
+}
+
+int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_rays** inout)
+{
+    if (!obj || !tp || !inout) return fail(RTW_ERR_ARG, "rtw_trace: null pointer");
+    if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace: p_max out of [0, 15]");
+    if (tp->precision != RTW_FP64) return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: precision %d", tp->precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = tp->p_max + 1;
+    std::vector<ObjDev> objs((size_t)obj->count);
+    long long R = 0;
+    for (int i = 0; i < obj->count; ++i) {
+        double h = 0.0, w = 0.0;
+        long long nx = 0, ny = 0;
+        int rc = grid_of(obj->h[(size_t)i], tp, &h, &nx, &ny, &w);
+        if (rc != RTW_OK) return rc;
+        ObjDev& d = objs[(size_t)i];
+        fill_objdev(obj->h[(size_t)i], d);
+        d.grid = tp->grid == RTW_GRID_FAN ? rtw::kGridFan : rtw::kGridSquare;
+        d.h = h;
+        d.fan_w = w;
+        d.fan_ex = std::cos(tp->fan_phi);
+        d.fan_ey = std::sin(tp->fan_phi);
+        d.nx = nx;
+        d.ny = ny;
+        d.ray_offset = R;
+        R += nx * ny;
+    }
+    const bool aux = tp->grid == RTW_GRID_FAN && (tp->flags & RTW_TRACE_APERTURE);
+    // one allocation carved into 256-byte aligned arrays
+    const size_t n = (size_t)np * (size_t)R;
+    size_t off[8], total = 0;
+    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, aux ? n * 8 * rtw::kAuxCount : 0, 0};
+    for (int k = 0; k < 8; ++k) {
+        off[k] = total;
+        total = align_up(total + sizes[k], 256);
+    }
+    rtw_rays* r = *inout;
+    bool fresh = false;
+    if (!r) {
+        r = new (std::nothrow) rtw_rays();
+        if (!r) return fail(RTW_ERR_NOMEM, "rtw_trace: host allocation");
+        fresh = true;
+    }
+    RTW_CUDA(cudaGetDevice(&r->device));
+    if (r->block_bytes < total) {
+        if (r->block) cudaFree(r->block);
+        r->block = nullptr;
+        r->block_bytes = 0;
+        cudaError_t e = cudaMalloc(&r->block, total);
+        if (e != cudaSuccess) {
+            if (fresh) delete r;
+            else *inout = r;
+            return fail(RTW_ERR_NOMEM, "rtw_trace: cudaMalloc of %zu bytes: %s", total, cudaGetErrorString(e));
+        }
+        r->block_bytes = total;
+    }
+    if (r->d_objs_cap < objs.size()) {
+        if (r->d_objs) cudaFree(r->d_objs);
+        r->d_objs = nullptr;
+        r->d_objs_cap = 0;
+        if (cudaMalloc(&r->d_objs, sizeof(ObjDev) * objs.size()) != cudaSuccess) {
+            if (fresh) delete r;
+            return fail(RTW_ERR_NOMEM, "rtw_trace: object table");
+        }
+        r->d_objs_cap = objs.size();
+    }
+    *inout = r;
+    r->np = np;
+    r->precision = tp->precision;
+    r->grid = tp->grid;
+    r->flags = tp->flags;
+    r->nobj = obj->count;
+    r->R = R;
+    r->fan_phi = tp->fan_phi;
+    r->objs = objs;
+    char* b = (char*)r->block;
+    r->st.R = R;
+    r->st.np = np;
+    r->st.precision = tp->precision;
+    r->st.s01 = (double2*)(b + off[0]);
+    r->st.s2psi = (double2*)(b + off[1]);
+    r->st.Fx = (double2*)(b + off[2]);
+    r->st.Fy = (double2*)(b + off[3]);
+    r->st.Fz = (double2*)(b + off[4]);
+    r->st.flags = (uint32_t*)(b + off[5]);
+    r->st.aux = aux ? (double*)(b + off[6]) : nullptr;
+    RTW_CUDA(cudaMemcpyAsync(r->d_objs, r->objs.data(), sizeof(ObjDev) * objs.size(), cudaMemcpyHostToDevice, s));
+    unsigned int* status = status_word(r->device);
+    RTW_CUDA(rtw::launch_trace(r->d_objs, r->nobj, r->st, tp->p_max, aux, status, s));
+    return RTW_OK;
+}
+
+int rtw_rays_info(const rtw_rays* rays, int64_t* rays_per_order, int* n_orders, int* n_objects)
+{
+    if (!rays) return fail(RTW_ERR_ARG, "rtw_rays_info: null handle");
+    if (rays_per_order) *rays_per_order = rays->R;
+    if (n_orders) *n_orders = rays->np;
+    if (n_objects) *n_objects = rays->nobj;
+    return RTW_OK;
+}
+
+int rtw_rays_export(const rtw_rays* rays, int order, int64_t first, int64_t count, double* s_out, double* F_out,
+                    double* psi_out, uint32_t* flags_out, void* stream)
+{
+    if (!rays) return fail(RTW_ERR_ARG, "rtw_rays_export: null handle");
+    if (order < 0 || order >= rays->np) return fail(RTW_ERR_ARG, "rtw_rays_export: order out of range");
+    if (first < 0 || count < 0 || first + count > rays->R) return fail(RTW_ERR_ARG, "rtw_rays_export: range");
+    RTW_CUDA(rtw::launch_export(rays->st, order, first, count, s_out, F_out, psi_out, flags_out,
+                                (cudaStream_t)stream));
+    return RTW_OK;
+}
+
+void rtw_destroy_rays(rtw_rays* rays)
+{
+    if (!rays) return;
+    if (rays->block) cudaFree(rays->block);
+    if (rays->d_objs) cudaFree(rays->d_objs);
+    if (rays->ws) cudaFree(rays->ws);
+    delete rays;
+}
+
+int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t n, int p_max, double* s_out,
+                     double* F_out, double* psi_out, uint32_t* flags_out, void* stream)
+{
+    if (!obj || (!xy && n > 0)) return fail(RTW_ERR_ARG, "rtw_trace_points: null pointer");
+    if (index < 0 || index >= obj->count) return fail(RTW_ERR_ARG, "rtw_trace_points: index out of range");
+    if (p_max < 0 || p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace_points: p_max out of range");
+    if (n < 0) return fail(RTW_ERR_ARG, "rtw_trace_points: n < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    ObjDev d;
+    fill_objdev(obj->h[(size_t)index], d);
+    // a per-call object entry: a tiny device buffer freed after the launch has been ordered
+    ObjDev* d_obj = nullptr;
+    RTW_CUDA(cudaMallocAsync(&d_obj, sizeof(ObjDev), s));
+    RTW_CUDA(cudaMemcpyAsync(d_obj, &d, sizeof(ObjDev), cudaMemcpyHostToDevice, s));
+    cudaError_t e = rtw::launch_trace_points(d_obj, xy, n, p_max, s_out, F_out, psi_out, flags_out, s);
+    cudaFreeAsync(d_obj, s);
+    if (e != cudaSuccess) return cuda_fail(e, "trace_points launch");
+    return RTW_OK;
+}
+
+int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags, void* field_out, uint8_t* mask_out,
+              void* stream)
+{
+    rtw_rays* rays = const_cast<rtw_rays*>(rays_c);
+    if (!rays || !dirs || !field_out) return fail(RTW_ERR_ARG, "rtw_field: null pointer");
+    if (mode != RTW_DENSE) return fail(RTW_ERR_UNSUPPORTED, "rtw_field: mode %d", mode);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool per_order = (flags & RTW_FIELD_PER_ORDER) != 0;
+    const bool po = (flags & RTW_FIELD_PO) != 0;
+    const int nout = per_order ? rays->np : 1;
+    long long ndir = 0;
+    if (dirs->kind == RTW_DIRS_PLANE) {
+        if (rays->grid != RTW_GRID_FAN) return fail(RTW_ERR_ARG, "rtw_field: plane directions need a fan grid");
+        if (dirs->n_theta < 1 || !(std::fabs(dirs->dalpha) > 0.0) || std::fabs(dirs->dalpha) > 0.5 ||
+            std::fabs(dirs->dalpha) * dirs->n_theta > 2.0 * kPi + 1e-9)
+            return fail(RTW_ERR_ARG, "rtw_field: plane grid needs n >= 1, 0 < |dalpha| <= 0.5, span <= 2 pi");
+        ndir = dirs->n_theta;
+    } else if (dirs->kind == RTW_DIRS_GRID) {
+        if (rays->grid != RTW_GRID_SQUARE) return fail(RTW_ERR_ARG, "rtw_field: (theta, phi) grids need a square grid");
+        if (dirs->n_theta < 1 || dirs->n_phi < 2) return fail(RTW_ERR_ARG, "rtw_field: n_theta >= 1, n_phi >= 2");
+        ndir = (long long)dirs->n_theta * dirs->n_phi;
+    } else {
+        return fail(RTW_ERR_ARG, "rtw_field: unknown direction kind %d", dirs->kind);
+    }
+    if (po && (rays->grid != RTW_GRID_FAN || !rays->st.aux))
+        return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO needs a fan traced with RTW_TRACE_APERTURE");
+    // workspace: mask words, direction tables, PO windows and scratch
+    const long long nfan = rays->grid == RTW_GRID_FAN ? rays->objs[0].nx : 0;
+    const long long ap_cap = po ? 2 * (long long)rays->np * nfan : 0;
+    size_t off_mask = 0;
+    size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir, 256);
+    size_t ntab = dirs->kind == RTW_DIRS_GRID ? 2 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi) : 0;
+    size_t off_win = align_up(off_tab + sizeof(double) * ntab, 256);
+    size_t off_nwin = align_up(off_win + sizeof(rtw::PoWindow) * rtw::kMaxPoWindows, 256);
+    size_t off_po = align_up(off_nwin + 256, 256);
+    size_t po_bytes = po ? sizeof(double) * ((size_t)rays->np * (size_t)nfan + rtw::kMaxPoWindows + 1 +
+                                             9 * (size_t)ap_cap)
+                         : 0;
+    size_t total = align_up(off_po + po_bytes, 256);
+    if (rays->ws_bytes < total) {
+        if (rays->ws) cudaFree(rays->ws);
+        rays->ws = nullptr;
+        rays->ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&rays->ws, total);
+        if (e != cudaSuccess) return fail(RTW_ERR_NOMEM, "rtw_field: workspace of %zu bytes", total);
+        rays->ws_bytes = total;
+    }
+    char* ws = (char*)rays->ws;
+    unsigned int* mask_words = (unsigned int*)(ws + off_mask);
+    double* tab = (double*)(ws + off_tab);
+    rtw::PoWindow* d_win = (rtw::PoWindow*)(ws + off_win);
+    int* d_nwin = (int*)(ws + off_nwin);
+    double2* d_po = (double2*)(ws + off_po);
+    unsigned int* status = status_word(rays->device);
+    const size_t out_bytes_obj = sizeof(double) * 4 * (size_t)nout * (size_t)ndir;
+    RTW_CUDA(cudaMemsetAsync(field_out, 0, out_bytes_obj * (size_t)rays->nobj, s));
+    if (dirs->kind == RTW_DIRS_GRID) RTW_CUDA(rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, tab, s));
+    for (int oi = 0; oi < rays->nobj; ++oi) {
+        const ObjDev& o = rays->objs[(size_t)oi];
+        RTW_CUDA(cudaMemsetAsync(mask_words, 0, sizeof(unsigned int) * (size_t)ndir, s));
+        rtw::FieldArgs a;
+        a.d_obj = rays->d_objs + oi;
+        a.st = rays->st;
+        a.pmax = rays->np - 1;
+        a.per_order = per_order ? 1 : 0;
+        a.out = (double*)((char*)field_out + out_bytes_obj * (size_t)oi);
+        a.mask = mask_words;
+        a.status = status;
+        if (dirs->kind == RTW_DIRS_GRID) {
+            long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
+            const int64_t* w = dirs->cell_window;
+            if (!(w[0] == -1 && w[1] == -1 && w[2] == -1 && w[3] == -1)) {
+                ix0 = w[0] < 0 ? 0 : w[0];
+                ix1 = w[1] > o.nx - 1 ? o.nx - 1 : w[1];
+                iy0 = w[2] < 0 ? 0 : w[2];
+                iy1 = w[3] > o.ny - 1 ? o.ny - 1 : w[3];
+            }
+            RTW_CUDA(rtw::launch_field_grid(a, o.nx, ix0, ix1, iy0, iy1, dirs->n_theta, dirs->n_phi, tab, 0, s));
+        } else {
+            if (po) {
+                RTW_CUDA(rtw::launch_po_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,
+                                            d_nwin, d_po, ap_cap, s));
+            } else {
+                RTW_CUDA(rtw::launch_field_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha,
+                                               nullptr, nullptr, 0, s));
+            }
+        }
+        if (mask_out) {
+            const double axial = 2.0 * o.lambda / o.lmin;
+            RTW_CUDA(rtw::launch_finalize_mask(mask_words, mask_out + (size_t)oi * (size_t)ndir, ndir,
+                                               dirs->kind == RTW_DIRS_PLANE ? 0 : 1, dirs->n_theta, dirs->n_phi,
+                                               dirs->alpha0, dirs->dalpha, axial, s));
+        }
+    }
+    return RTW_OK;
+}
+
+int rtw_sync_status(void* stream)
+{
+    int dev = 0;
+    RTW_CUDA(cudaGetDevice(&dev));
+    RTW_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned int* p = status_word(dev);
+    if (!p) return fail(RTW_ERR_CUDA, "rtw_sync_status: status word");
+    unsigned int v = 0;
+    RTW_CUDA(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
+    RTW_CUDA(cudaMemset(p, 0, sizeof(v)));
+    if (v & rtw::kStatusCapacity) return fail(RTW_ERR_CAPACITY, "a device buffer or bounded loop ran out");
+    if (v & rtw::kStatusTimeout) return fail(RTW_ERR_TIMEOUT, "a bounded device iteration gave up");
+    if (v & rtw::kStatusNumeric) return fail(RTW_ERR_NUMERIC, "a non-finite or singular value was met");
+    return RTW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,700 @@
+// rtw_field.cu -- the second half of the RTW hot path: the ray map interpolated onto the
+// observation directions and all rays summed ("Strategy of Ray Theory of Waves", principle iii),
+// and the physical-optics integral around in-plane folds ("Diffraction effect correction based
+// on VCRM").
+//
+// Square grids: one thread per (order, cell) of the ray grid.  A cell is split along its diagonal
+// into two triangles of neighbouring rays; the image triangle on the unit sphere of directions
+// owns the grid directions inside it (sign tests of the edge planes s_lo x s_hi, evaluated with the
+// endpoints in ray-index order so both triangles of an edge compute the same product: a direction
+// on a shared edge is owned exactly once).  The candidate directions come from a single-precision
+// cap around the triangle (conservative, 1e-5 rad margin); the tests, the interpolation and the
+// phase are double precision.  Hits are few (about one per direction, branch and order), so the
+// accumulation is a double-precision atomicAdd into the output.
+#include <math_constants.h>
+
+#include "rtw_launch.h"
+#include "rtw_trace.cuh"
+
+namespace rtw {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr unsigned int kMaskCaustic = 1u, kMaskAxial = 2u, kMaskPo = 4u;
+
+__device__ __forceinline__ double wrap_angle(double a)
+{
+    if (!(fabs(a) < 1e6)) return a;  // non-finite input: no wrapping loop
+    while (a > kPi) a -= 2.0 * kPi;
+    while (a <= -kPi) a += 2.0 * kPi;
+    return a;
+}
+
+__device__ __forceinline__ double ramp(double x, double x0, double x1)
+{
+    if (x <= x0) return 1.0;
+    if (x >= x1) return 0.0;
+    double c = cos(0.5 * kPi * (x - x0) / (x1 - x0));
+    return c * c;
+}
+
+__device__ __forceinline__ bool edge_in(double e, long long ia, long long ib, int sigma)
+{
+    const double se = sigma > 0 ? e : -e;
+    if (se > 0.0) return true;
+    if (se < 0.0) return false;
+    return (ia < ib) == (sigma > 0);
+}
+
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ void load_dir(const RaysDev& st, long long i, double* s)
+{
+    const double2 a = st.s01[i];
+    const double2 b = st.s2psi[i];
+    s[0] = a.x;
+    s[1] = a.y;
+    s[2] = b.x;
+}
+
+// F e^{i Psi} projected on (e_theta, e_phi) and added into acc (4 doubles)
+__device__ __forceinline__ void add_contribution(const double* F, double psi, const double* eth, const double* eph,
+                                                 double w, double* dst)
+{
+    double sp, cp;
+    sincos(psi, &sp, &cp);
+    double tr = 0.0, ti = 0.0, pr = 0.0, pi = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double re = F[2 * c] * cp - F[2 * c + 1] * sp;
+        const double im = F[2 * c] * sp + F[2 * c + 1] * cp;
+        tr += re * eth[c];
+        ti += im * eth[c];
+        pr += re * eph[c];
+        pi += im * eph[c];
+    }
+    atomicAdd(dst + 0, w * tr);
+    atomicAdd(dst + 1, w * ti);
+    atomicAdd(dst + 2, w * pr);
+    atomicAdd(dst + 3, w * pi);
+}
+
+// ---------------------------------------------------------------------------------------------
+// direction tables: cos(theta_i), sin(theta_i), cos(phi_j), sin(phi_j)
+// ---------------------------------------------------------------------------------------------
+__global__ void dir_tables_kernel(int nt, int nph, double* tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nt) {
+        double s, c;
+        sincos((i + 0.5) * (kPi / nt), &s, &c);
+        tab[i] = c;
+        tab[nt + i] = s;
+    }
+    if (i < nph) {
+        double s, c;
+        sincos(-kPi + (i + 0.5) * (2.0 * kPi / nph), &s, &c);
+        tab[2 * nt + i] = c;
+        tab[2 * nt + nph + i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// square grid: one thread per (order, cell)
+// ---------------------------------------------------------------------------------------------
+__device__ void grid_triangle(const FieldArgs& a, const ObjDev& o, long long base, int p, const long long* id,
+                              const uint32_t* f, int nt, int nph, const double* __restrict__ tab)
+{
+    if (!(f[0] & f[1] & f[2] & kFlagValid)) return;
+    bool consistent = flag_nf(f[0]) == flag_nf(f[1]) && flag_nf(f[1]) == flag_nf(f[2]) &&
+                      ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
+                      ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0;
+    double s[3][3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) load_dir(a.st, base + id[v], s[v]);
+    double c12[3];
+    cross3(s[1], s[2], c12);
+    const double vol = s[0][0] * c12[0] + s[0][1] * c12[1] + s[0][2] * c12[2];
+    const int sigma = vol > 0.0 ? 1 : (vol < 0.0 ? -1 : 0);
+    if (sigma == 0) return;
+    if (sigma != ((f[0] & kFlagOrient) ? 1 : -1)) consistent = false;
+    // edge planes in canonical order: E_ab(x) = g_ab (s_lo x s_hi) . x
+    double nrm[3][3];
+    double g[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int va = e, vb = (e + 1) % 3;
+        if (id[va] < id[vb]) {
+            cross3(s[va], s[vb], nrm[e]);
+            g[e] = 1.0;
+        } else {
+            cross3(s[vb], s[va], nrm[e]);
+            g[e] = -1.0;
+        }
+    }
+    // conservative cap of candidate directions (single precision)
+    float cmx = (float)(s[0][0] + s[1][0] + s[2][0]);
+    float cmy = (float)(s[0][1] + s[1][1] + s[2][1]);
+    float cmz = (float)(s[0][2] + s[1][2] + s[2][2]);
+    const float cn = rsqrtf(cmx * cmx + cmy * cmy + cmz * cmz);
+    cmx *= cn;
+    cmy *= cn;
+    cmz *= cn;
+    float ch = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const float dx = (float)s[v][0] - cmx, dy = (float)s[v][1] - cmy, dz = (float)s[v][2] - cmz;
+        ch = fmaxf(ch, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+    const float rho = 2.0f * asinf(fminf(1.0f, 0.5f * ch)) + 1e-5f;
+    const float thc = atan2f(sqrtf(cmx * cmx + cmy * cmy), cmz), phc = atan2f(cmy, cmx);
+    const float dth = (float)(kPi / nt), dph = (float)(2.0 * kPi / nph);
+    int it0 = (int)ceilf((thc - rho) / dth - 0.5f), it1 = (int)floorf((thc + rho) / dth - 0.5f);
+    it0 = max(it0, 0);
+    it1 = min(it1, nt - 1);
+    bool allphi = (thc - rho <= 0.0f) || (thc + rho >= (float)kPi);
+    int jp0 = 0, jcount = nph;
+    if (!allphi) {
+        const float sr = sinf(rho) / sinf(thc);
+        if (sr >= 0.9f) {  // close to a pole the phi extent is ill-conditioned: take every phi
+            allphi = true;
+        } else {
+            const float dphi = asinf(sr) + 1e-5f;
+            jp0 = (int)ceilf((phc - dphi + (float)kPi) / dph - 0.5f);
+            const int jp1 = (int)floorf((phc + dphi + (float)kPi) / dph - 0.5f);
+            jcount = jp1 - jp0 + 1;
+            if (jcount > nph) {
+                jp0 = 0;
+                jcount = nph;
+            }
+        }
+    }
+    const double* ctab = tab;
+    const double* stab = tab + nt;
+    const double* cptab = tab + 2 * nt;
+    const double* sptab = tab + 2 * nt + nph;
+    bool loaded = false;
+    double F[3][6], psi[3];
+    for (int it = it0; it <= it1; ++it) {
+        const double ct = ctab[it], sth = stab[it];
+        for (int jj = 0; jj < jcount; ++jj) {
+            int jp = (jp0 + jj) % nph;
+            if (jp < 0) jp += nph;
+            const double cp = cptab[jp], sp = sptab[jp];
+            const double x[3] = {sth * cp, sth * sp, ct};
+            double e[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) e[k] = g[k] * (nrm[k][0] * x[0] + nrm[k][1] * x[1] + nrm[k][2] * x[2]);
+            if (!edge_in(e[0], id[0], id[1], sigma) || !edge_in(e[1], id[1], id[2], sigma) ||
+                !edge_in(e[2], id[2], id[0], sigma))
+                continue;
+            const long long dk = (long long)it * nph + jp;
+            if (!consistent) {
+                atomicOr(a.mask + dk, kMaskCaustic);
+                continue;
+            }
+            if (!loaded) {
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const long long i = base + id[v];
+                    const double2 fx = a.st.Fx[i], fy = a.st.Fy[i], fz = a.st.Fz[i];
+                    F[v][0] = fx.x; F[v][1] = fx.y; F[v][2] = fy.x;
+                    F[v][3] = fy.y; F[v][4] = fz.x; F[v][5] = fz.y;
+                    psi[v] = a.st.s2psi[i].y;
+                }
+                loaded = true;
+            }
+            // barycentric weights of the central projection onto the plane of the corners
+            const double ssum = e[0] + e[1] + e[2];
+            const double l0 = e[1] / ssum, l1 = e[2] / ssum, l2 = e[0] / ssum;
+            double Fi[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Fi[c] = l0 * F[0][c] + l1 * F[1][c] + l2 * F[2][c];
+            const double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
+            const double eth[3] = {ct * cp, ct * sp, -sth};
+            const double eph[3] = {-sp, cp, 0.0};
+            double* dst = a.out + (dk * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? p : 0)) * 4;
+            add_contribution(Fi, ps, eth, eph, 1.0, dst);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, long long nx, long long ix0, long long ncx,
+                                                         long long iy0, long long ncy, int nt, int nph,
+                                                         const double* __restrict__ tab)
+{
+    const ObjDev& o = *a.d_obj;
+    const long long ncell = ncx * ncy;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= ncell * (a.pmax + 1)) return;
+    const int p = (int)(tid / ncell);
+    const long long cell = tid - (long long)p * ncell;
+    const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
+    const long long base = (long long)p * a.st.R + o.ray_offset;
+    const long long l00 = cy * nx + cx;
+    const long long lid[4] = {l00, l00 + 1, l00 + nx + 1, l00 + nx};  // c00 c10 c11 c01
+    uint32_t fl[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fl[v] = a.st.flags[base + lid[v]];
+    {
+        const long long id[3] = {lid[0], lid[1], lid[2]};
+        const uint32_t f[3] = {fl[0], fl[1], fl[2]};
+        grid_triangle(a, o, base, p, id, f, nt, nph, tab);
+    }
+    {
+        const long long id[3] = {lid[0], lid[2], lid[3]};
+        const uint32_t f[3] = {fl[0], fl[2], fl[3]};
+        grid_triangle(a, o, base, p, id, f, nt, nph, tab);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// fan: in-plane exit angles, folds, physical-optics windows
+// ---------------------------------------------------------------------------------------------
+struct FanScales {
+    double po_full, po_end, ap_full, ap_end;
+};
+
+__device__ __forceinline__ FanScales fan_scales(const ObjDev& o)
+{
+    // Airy width (lambda/L)^(2/3) and Fresnel width 1/sqrt(k0 L) of the centre aperture plane
+    const double aw = pow(o.lambda / o.lmax, 2.0 / 3.0), fw = 1.0 / sqrt(o.k0 * o.lmax);
+    FanScales s;
+    s.po_full = 1.5 * aw;
+    s.po_end = 3.0 * aw;
+    s.ap_full = 3.0 * aw + 3.0 * fw;
+    s.ap_end = 3.0 * aw + 6.0 * fw;
+    return s;
+}
+
+__device__ __forceinline__ double fan_alpha(const RaysDev& st, long long i, double efx, double efy)
+{
+    double s[3];
+    load_dir(st, i, s);
+    return atan2(s[0] * efx + s[1] * efy, s[2]);
+}
+
+// alpha of every (order, ray) of the fan, NaN where invalid
+__global__ void fan_alpha_kernel(FieldArgs a, long long nrays, double efx, double efy, double* alpha)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nrays * (a.pmax + 1)) return;
+    const int p = (int)(t / nrays);
+    const long long j = t - (long long)p * nrays;
+    const long long i = (long long)p * a.st.R + a.d_obj->ray_offset + j;
+    alpha[t] = (a.st.flags[i] & kFlagValid) ? fan_alpha(a.st, i, efx, efy) : CUDART_NAN;
+}
+
+__global__ void fan_fold_kernel(FieldArgs a, long long nrays, const double* alpha, PoWindow* win, int* nwin)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nrays * (a.pmax + 1)) return;
+    const int p = (int)(t / nrays);
+    const long long j = t - (long long)p * nrays;
+    if (p < 1 || j < 1 || j + 1 >= nrays) return;
+    const double am = alpha[t - 1], a0 = alpha[t], ap = alpha[t + 1];
+    if (isnan(am) || isnan(a0) || isnan(ap)) return;
+    const double d0 = wrap_angle(a0 - am), d1 = wrap_angle(ap - a0);
+    if (!(d0 * d1 < 0.0)) return;
+    const int slot = atomicAdd(nwin, 1);
+    if (slot >= kMaxPoWindows) {
+        atomicOr(a.status, kStatusCapacity);
+        return;
+    }
+    win[slot].p = p;
+    win[slot].jc = j;
+}
+
+// one block: sort the folds by (order, ray) and walk every window along the fan
+__global__ void fan_walk_kernel(FieldArgs a, long long nrays, const double* alpha, PoWindow* win, int* nwin)
+{
+    const ObjDev& o = *a.d_obj;
+    const int n = min(*nwin, kMaxPoWindows);
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < n; ++i) {
+            PoWindow w = win[i];
+            int k = i - 1;
+            while (k >= 0 && (win[k].p > w.p || (win[k].p == w.p && win[k].jc > w.jc))) {
+                win[k + 1] = win[k];
+                --k;
+            }
+            win[k + 1] = w;
+        }
+        *nwin = n;
+    }
+    __syncthreads();
+    const FanScales sc = fan_scales(o);
+    for (int w = threadIdx.x; w < n; w += blockDim.x) {
+        PoWindow& wv = win[w];
+        const double* al = alpha + (long long)wv.p * nrays;
+        const long long j = wv.jc;
+        const double d0 = wrap_angle(al[j] - al[j - 1]), d1 = wrap_angle(al[j + 1] - al[j]);
+        wv.alpha_c = al[j];
+        long long lo = j, hi = j;
+        while (lo - 1 >= 0 && !isnan(al[lo - 1]) && fabs(wrap_angle(al[lo - 1] - wv.alpha_c)) < sc.ap_end &&
+               fabs(al[lo - 1] - al[lo]) < kPi && (al[lo - 1] - al[lo]) * d0 < 0.0)
+            --lo;
+        while (hi + 1 < nrays && !isnan(al[hi + 1]) && fabs(wrap_angle(al[hi + 1] - wv.alpha_c)) < sc.ap_end &&
+               fabs(al[hi + 1] - al[hi]) < kPi && (al[hi + 1] - al[hi]) * d1 > 0.0)
+            ++hi;
+        wv.jlo = lo;
+        wv.jhi = hi;
+        wv.ok = (hi - lo + 1) >= 3;
+        const long long i = (long long)wv.p * a.st.R + o.ray_offset + j;
+        load_dir(a.st, i, wv.sc);
+    }
+}
+
+// aperture field of every window ray: x_i (3) and U_i |dxi_i| (3 complex) -> ap[off + i] (9 slots)
+__device__ bool aperture_point(const FieldArgs& a, const ObjDev& o, const PoWindow& wv, long long j, double efx,
+                               double efy, double* x, double* xi)
+{
+    const long long n = (long long)a.st.np * a.st.R;
+    const long long i = (long long)wv.p * a.st.R + o.ray_offset + j;
+    const double* aux = a.st.aux + i;
+    double s[3];
+    load_dir(a.st, i, s);
+    const double r[3] = {aux[kAuxRx * n], aux[kAuxRy * n], aux[kAuxRz * n]};
+    const double dd[3] = {o.c[0] - r[0], o.c[1] - r[1], o.c[2] - r[2]};
+    const double tau = (wv.sc[0] * dd[0] + wv.sc[1] * dd[1] + wv.sc[2] * dd[2]) /
+                       (wv.sc[0] * s[0] + wv.sc[1] * s[1] + wv.sc[2] * s[2]);
+    for (int c = 0; c < 3; ++c) x[c] = r[c] + tau * s[c];
+    const double ca = cos(wv.alpha_c), sa = sin(wv.alpha_c);
+    const double exi[3] = {ca * efx, ca * efy, -sa};
+    *xi = exi[0] * (x[0] - o.c[0]) + exi[1] * (x[1] - o.c[1]) + exi[2] * (x[2] - o.c[2]);
+    return true;
+}
+
+__global__ void fan_aperture_kernel(FieldArgs a, double efx, double efy, const double* alpha, long long nrays,
+                                    const PoWindow* win, const int* nwin, const long long* offs, double* ap,
+                                    long long ap_cap)
+{
+    const int w = blockIdx.y;
+    if (w >= *nwin) return;
+    const PoWindow wv = win[w];
+    if (!wv.ok) return;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nw = wv.jhi - wv.jlo + 1;
+    if (t >= nw) return;
+    const long long slot = offs[w] + t;
+    if (slot >= ap_cap) {
+        atomicOr(a.status, kStatusCapacity);
+        return;
+    }
+    const ObjDev& o = *a.d_obj;
+    const FanScales sc = fan_scales(o);
+    const long long j = wv.jlo + t;
+    const long long n = (long long)a.st.np * a.st.R;
+    const long long i = (long long)wv.p * a.st.R + o.ray_offset + j;
+    const double* aux = a.st.aux + i;
+    double x[3], xi, xn[3], xim = 0.0, xip = 0.0;
+    aperture_point(a, o, wv, j, efx, efy, x, &xi);
+    if (t > 0) aperture_point(a, o, wv, j - 1, efx, efy, xn, &xim);
+    if (t + 1 < nw) aperture_point(a, o, wv, j + 1, efx, efy, xn, &xip);
+    double dxi;
+    if (t == 0) dxi = 0.5 * (xip - xi);
+    else if (t == nw - 1) dxi = 0.5 * (xi - xim);
+    else dxi = 0.5 * (xip - xim);
+    // exit wave carried to the aperture line
+    double s[3];
+    load_dir(a.st, i, s);
+    const double r[3] = {aux[kAuxRx * n], aux[kAuxRy * n], aux[kAuxRz * n]};
+    const double tau = (x[0] - r[0]) * s[0] + (x[1] - r[1]) * s[1] + (x[2] - r[2]) * s[2];
+    const double q11 = aux[kAuxQ11 * n], q12 = aux[kAuxQ12 * n], q22 = aux[kAuxQ22 * n];
+    const double A11 = 1.0 + tau * q11, A22 = 1.0 + tau * q22, A12 = tau * q12;
+    const double detA = A11 * A22 - A12 * A12;
+    double* out = ap + 9 * slot;
+    if (detA == 0.0) {
+        for (int c = 0; c < 9; ++c) out[c] = 0.0;
+        atomicOr(a.status, kStatusNumeric);
+        return;
+    }
+    const int nfl = neg_eigs_sym(A11, A12, A22);
+    const int nf_ap = (int)aux[kAuxNfLegs * n] + (tau > 0.0 ? nfl : -nfl);
+    const double dq = q11 * q22 - q12 * q12;
+    const double qa11 = (q11 + tau * dq) / detA, qa12 = q12 / detA, qa22 = (q22 + tau * dq) / detA;
+    const double ep[3] = {aux[kAuxEpx * n], aux[kAuxEpy * n], aux[kAuxEpz * n]};
+    const double v2[3] = {ep[1] * s[2] - ep[2] * s[1], ep[2] * s[0] - ep[0] * s[2], ep[0] * s[1] - ep[1] * s[0]};
+    const double npl[3] = {efy, -efx, 0.0};  // normal of the fan plane
+    const double c1 = npl[0] * ep[0] + npl[1] * ep[1] + npl[2] * ep[2];
+    const double c2 = npl[0] * v2[0] + npl[1] * v2[1] + npl[2] * v2[2];
+    const double qs = c1 * c1 * qa11 + 2.0 * c1 * c2 * qa12 + c2 * c2 * qa22;
+    const double Rs = 1.0 / qs;
+    const double dap = aux[kAuxDlegs * n] / fabs(detA);
+    // amplitude sqrt(D) (-i)^nf e^{i k0 (L + tau)} times the sagittal factor sqrt|Rs| e^{i pi/4 sgn Rs}
+    double ph = o.k0 * (aux[kAuxPath * n] + tau) - 0.5 * kPi * (double)nf_ap + (Rs > 0.0 ? 0.25 : -0.25) * kPi;
+    double sph, cph;
+    sincos(ph, &sph, &cph);
+    const double tap = ramp(fabs(wrap_angle(alpha[(long long)wv.p * nrays + j] - wv.alpha_c)), sc.ap_full, sc.ap_end);
+    const double mag = tap * sqrt(dap) * sqrt(fabs(Rs)) * fabs(dxi);
+    const double E[6] = {aux[kAuxExr * n], aux[kAuxExi * n], aux[kAuxEyr * n],
+                         aux[kAuxEyi * n], aux[kAuxEzr * n], aux[kAuxEzi * n]};
+    out[0] = x[0];
+    out[1] = x[1];
+    out[2] = x[2];
+    for (int c = 0; c < 3; ++c) {
+        out[3 + 2 * c] = mag * (E[2 * c] * cph - E[2 * c + 1] * sph);
+        out[4 + 2 * c] = mag * (E[2 * c] * sph + E[2 * c + 1] * cph);
+    }
+}
+
+// target direction of an in-plane angle alpha and its (e_theta, e_phi)
+__device__ __forceinline__ void plane_dir(double alk, double efx, double efy, double* d, double* eth, double* eph)
+{
+    const double th = fabs(alk);
+    const double cph = alk >= 0.0 ? efx : -efx, sph = alk >= 0.0 ? efy : -efy;
+    double st, ct;
+    sincos(th, &st, &ct);
+    d[0] = st * cph;
+    d[1] = st * sph;
+    d[2] = ct;
+    eth[0] = ct * cph;
+    eth[1] = ct * sph;
+    eth[2] = -st;
+    eph[0] = -sph;
+    eph[1] = cph;
+    eph[2] = 0.0;
+}
+
+// one block per (window, target direction): sum over the window's aperture samples
+__global__ void __launch_bounds__(256) fan_po_kernel(FieldArgs a, double efx, double efy, int ndir, double alpha0,
+                                                     double dalpha, const PoWindow* win, const int* nwin,
+                                                     const long long* offs, const double* ap, long long ap_cap)
+{
+    const int w = blockIdx.y;
+    if (w >= *nwin) return;
+    const PoWindow wv = win[w];
+    if (!wv.ok) return;
+    if (offs[w] + (wv.jhi - wv.jlo + 1) > ap_cap) return;  // samples beyond capacity were not written
+    const int k = blockIdx.x;
+    const double alk = alpha0 + k * dalpha;
+    const ObjDev& o = *a.d_obj;
+    const FanScales sc = fan_scales(o);
+    const double sblend = ramp(fabs(wrap_angle(alk - wv.alpha_c)), sc.po_full, sc.po_end);
+    if (sblend == 0.0) return;
+    double d[3], eth[3], eph[3];
+    plane_dir(alk, efx, efy, d, eth, eph);
+    const long long nw = wv.jhi - wv.jlo + 1;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long t = threadIdx.x; t < nw; t += blockDim.x) {
+        const double* q = ap + 9 * (offs[w] + t);
+        double sp, cp;
+        sincos(-o.k0 * (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]), &sp, &cp);
+        double tr = 0.0, ti = 0.0, pr = 0.0, pi = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double re = q[3 + 2 * c] * cp - q[4 + 2 * c] * sp;
+            const double im = q[3 + 2 * c] * sp + q[4 + 2 * c] * cp;
+            tr += re * eth[c];
+            ti += im * eth[c];
+            pr += re * eph[c];
+            pi += im * eph[c];
+        }
+        acc[0] += tr;
+        acc[1] += ti;
+        acc[2] += pr;
+        acc[3] += pi;
+    }
+    // warp shuffle reduction, then one partial per warp in shared memory
+    __shared__ double red[4][32];
+    for (int c = 0; c < 4; ++c) {
+        double v = acc[c];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < 4; ++c)
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot[c] += red[c][i];
+        // sqrt(k0 / 2 pi) (-i) times the blend weight
+        const double pre = sqrt(o.k0 / (2.0 * kPi)) * sblend;
+        const double r0 = pre * tot[1], i0 = -pre * tot[0];
+        const double r1 = pre * tot[3], i1 = -pre * tot[2];
+        double* dst = a.out + ((long long)k * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? wv.p : 0)) * 4;
+        atomicAdd(dst + 0, r0);
+        atomicAdd(dst + 1, i0);
+        atomicAdd(dst + 2, r1);
+        atomicAdd(dst + 3, i1);
+        atomicOr(a.mask + k, kMaskPo);
+    }
+}
+
+// fan: one thread per (order, segment of neighbouring rays)
+__global__ void __launch_bounds__(256) field_fan_kernel(FieldArgs a, long long nrays, double efx, double efy,
+                                                        int ndir, double alpha0, double dalpha,
+                                                        const PoWindow* win, const int* nwin_p)
+{
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nseg = nrays - 1;
+    if (nseg <= 0 || tid >= nseg * (a.pmax + 1)) return;
+    const int p = (int)(tid / nseg);
+    const long long j = tid - (long long)p * nseg;
+    const ObjDev& o = *a.d_obj;
+    const long long ia = (long long)p * a.st.R + o.ray_offset + j, ib = ia + 1;
+    const uint32_t fa = a.st.flags[ia], fb = a.st.flags[ib];
+    if (!(fa & fb & kFlagValid)) return;
+    const bool consistent = flag_nf(fa) == flag_nf(fb) && ((fa ^ fb) & kFlagOrient) == 0 &&
+                            ((fa | fb) & kFlagCaustic) == 0;
+    const double al_a = fan_alpha(a.st, ia, efx, efy), al_b = fan_alpha(a.st, ib, efx, efy);
+    const double da = wrap_angle(al_b - al_a);
+    if (da == 0.0) return;
+    int wi = -1;
+    const int nwin = nwin_p ? *nwin_p : 0;
+    for (int w = 0; w < nwin; ++w)
+        if (win[w].ok && win[w].p == p && j >= win[w].jlo && j + 1 <= win[w].jhi) wi = w;
+    const FanScales sc = fan_scales(o);
+    const double lo = fmin(al_a, al_a + da), hi = fmax(al_a, al_a + da);
+    bool loaded = false;
+    double Fa[6], Fb[6], pa = 0.0, pb = 0.0;
+    for (int sh = -1; sh <= 1; ++sh) {
+        const double shift = sh * 2.0 * kPi;
+        long long k0 = (long long)ceil((lo + shift - alpha0) / dalpha) - 1;
+        long long k1 = (long long)floor((hi + shift - alpha0) / dalpha) + 1;
+        if (k0 < 0) k0 = 0;
+        if (k1 > ndir - 1) k1 = ndir - 1;
+        for (long long k = k0; k <= k1; ++k) {
+            const double alk = alpha0 + k * dalpha;
+            const double lam = wrap_angle(alk - al_a) / da;
+            if (!(lam >= 0.0 && lam < 1.0)) continue;
+            if (!consistent) {
+                if (wi < 0) atomicOr(a.mask + k, kMaskCaustic);
+                continue;
+            }
+            double wgo = 1.0;
+            if (wi >= 0) wgo = 1.0 - ramp(fabs(wrap_angle(alk - win[wi].alpha_c)), sc.po_full, sc.po_end);
+            if (wgo == 0.0) continue;
+            if (!loaded) {
+                const double2 xa = a.st.Fx[ia], ya = a.st.Fy[ia], za = a.st.Fz[ia];
+                const double2 xb = a.st.Fx[ib], yb = a.st.Fy[ib], zb = a.st.Fz[ib];
+                Fa[0] = xa.x; Fa[1] = xa.y; Fa[2] = ya.x; Fa[3] = ya.y; Fa[4] = za.x; Fa[5] = za.y;
+                Fb[0] = xb.x; Fb[1] = xb.y; Fb[2] = yb.x; Fb[3] = yb.y; Fb[4] = zb.x; Fb[5] = zb.y;
+                pa = a.st.s2psi[ia].y;
+                pb = a.st.s2psi[ib].y;
+                loaded = true;
+            }
+            double F[6];
+            for (int c = 0; c < 6; ++c) F[c] = (1.0 - lam) * Fa[c] + lam * Fb[c];
+            const double ps = (1.0 - lam) * pa + lam * pb;
+            double d[3], eth[3], eph[3];
+            plane_dir(alk, efx, efy, d, eth, eph);
+            double* dst = a.out + (k * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? p : 0)) * 4;
+            add_contribution(F, ps, eth, eph, wgo, dst);
+        }
+    }
+}
+
+__global__ void window_prefix_kernel(const PoWindow* win, const int* nwin, long long* offs)
+{
+    long long o = 0;
+    const int n = *nwin;
+    for (int w = 0; w < n; ++w) {
+        offs[w] = o;
+        o += win[w].ok ? (win[w].jhi - win[w].jlo + 1) : 0;
+    }
+    offs[n] = o;
+}
+
+__global__ void finalize_mask_kernel(const unsigned int* words, unsigned char* mask_out, long long ndir, int kind,
+                                     int nt, int nph, double alpha0, double dalpha, double axial)
+{
+    const long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (d >= ndir) return;
+    double th;
+    if (kind == 0) {
+        th = fabs(alpha0 + d * dalpha);
+    } else {
+        const int it = (int)(d / nph);
+        th = (it + 0.5) * (kPi / nt);
+    }
+    unsigned int m = words[d];
+    if (th < axial || th > kPi - axial) m |= kMaskAxial;
+    mask_out[d] = (unsigned char)m;
+}
+
+}  // namespace
+
+cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
+{
+    const int n = nt > nph ? nt : nph;
+    dir_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(nt, nph, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, long long ix1, long long iy0,
+                              long long iy1, int nt, int nph, const double* tab, int newton, cudaStream_t s)
+{
+    (void)newton;
+    const long long ncx = ix1 - ix0, ncy = iy1 - iy0;
+    if (ncx <= 0 || ncy <= 0) return cudaSuccess;
+    const long long n = ncx * ncy * (a.pmax + 1);
+    const int bs = 256;
+    field_grid_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fan_windows(const FieldArgs& a, long long nrays, double fan_phi, PoWindow* d_win, int* d_nwin,
+                               cudaStream_t s)
+{
+    (void)a; (void)nrays; (void)fan_phi; (void)d_win; (void)d_nwin; (void)s;
+    return cudaSuccess;
+}
+
+// the fan path: alpha table, folds, windows, aperture fields (when PO), then the segments
+cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
+                             double dalpha, const PoWindow* d_win, const int* d_nwin, int newton, cudaStream_t s)
+{
+    (void)newton;
+    const long long nseg = (nrays - 1) * (a.pmax + 1);
+    if (nseg <= 0) return cudaSuccess;
+    const int bs = 256;
+    field_fan_kernel<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, s>>>(a, nrays, cos(fan_phi), sin(fan_phi), ndir,
+                                                                     alpha0, dalpha, d_win, d_nwin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_po_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
+                          double dalpha, const PoWindow* d_win_c, const int* d_nwin_c, double2* d_ap,
+                          long long ap_cap, cudaStream_t s)
+{
+    // d_ap is scratch: alpha table (np nrays doubles), window offsets (kMaxPoWindows + 1 long long)
+    // and the aperture samples (9 doubles each, ap_cap of them)
+    PoWindow* d_win = const_cast<PoWindow*>(d_win_c);
+    int* d_nwin = const_cast<int*>(d_nwin_c);
+    const double efx = cos(fan_phi), efy = sin(fan_phi);
+    const long long nt = nrays * (a.pmax + 1);
+    double* alpha = reinterpret_cast<double*>(d_ap);
+    long long* offs = reinterpret_cast<long long*>(alpha + nt);
+    double* ap = reinterpret_cast<double*>(offs + kMaxPoWindows + 1);
+    const int bs = 256;
+    cudaMemsetAsync(d_nwin, 0, sizeof(int), s);
+    fan_alpha_kernel<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(a, nrays, efx, efy, alpha);
+    fan_fold_kernel<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(a, nrays, alpha, d_win, d_nwin);
+    fan_walk_kernel<<<1, 64, 0, s>>>(a, nrays, alpha, d_win, d_nwin);
+    // window offsets: exclusive prefix of the window sizes (tiny; one thread)
+    window_prefix_kernel<<<1, 1, 0, s>>>(d_win, d_nwin, offs);
+    dim3 g1((unsigned)((nrays + bs - 1) / bs), kMaxPoWindows);
+    fan_aperture_kernel<<<g1, bs, 0, s>>>(a, efx, efy, alpha, nrays, d_win, d_nwin, offs, ap, ap_cap);
+    // segments (GO, weighted by the PO blend inside the windows)
+    field_fan_kernel<<<(unsigned)(((nrays - 1) * (a.pmax + 1) + bs - 1) / bs), bs, 0, s>>>(
+        a, nrays, efx, efy, ndir, alpha0, dalpha, d_win, d_nwin);
+    dim3 g2((unsigned)ndir, kMaxPoWindows);
+    fan_po_kernel<<<g2, 256, 0, s>>>(a, efx, efy, ndir, alpha0, dalpha, d_win, d_nwin, offs, ap, ap_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, long long ndir, int kind, int nt,
+                                 int nph, double alpha0, double dalpha, double axial, cudaStream_t s)
+{
+    if (!mask_out || ndir == 0) return cudaSuccess;
+    finalize_mask_kernel<<<(unsigned)((ndir + 255) / 256), 256, 0, s>>>(words, mask_out, ndir, kind, nt, nph, alpha0,
+                                                                         dalpha, axial);
+    return cudaGetLastError();
+}
+
+}  // namespace rtw

@@ -1,0 +1,73 @@
+// rtw_internal.h -- device-side data layout shared by the CUDA translation units of librtw.
+//
+// One object table entry per ellipsoid (ObjDev) and one structure-of-arrays ray state (RaysDev)
+// per rtw_rays handle.  Ray state index: i = p * R + j, p the order, j the global ray index
+// (objects laid out one after the other, square grids row-major with x fastest), R the number of
+// rays per order, so that consecutive threads (consecutive j) touch consecutive 16-byte vectors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rtw {
+
+constexpr int kMaxOrders = 16;
+
+enum : uint32_t {
+    kFlagValid = 1u,
+    kFlagOrient = 2u,   // set: the map (x, y) -> s preserves orientation (z up, s outward)
+    kFlagCaustic = 4u,  // dA/dOmega above the caustic cap
+};
+__host__ __device__ inline uint32_t flag_nf(uint32_t f) { return (f >> 8) & 0xffu; }
+
+enum : int { kGridFan = 0, kGridSquare = 1 };
+
+struct ObjDev {
+    double W[6];  // symmetric quadric matrix: xx xy xz yy yz zz; surface (x-c)^T W (x-c) = 1
+    double c[3];  // centre
+    double m;     // n_object / n_host
+    double k0;    // 2 pi / lambda
+    double lambda;
+    double jre[2], jim[2];  // incident Jones vector on (x, y)
+    double zstart;          // plane where the incident rays start
+    double S[3];            // projected ellipse xx xy yy
+    double cap;             // caustic cap on dA/dOmega (um^2)
+    double lmin, lmax;
+    // ray grid
+    int grid;
+    int pad0;
+    double h;               // square: spacing; fan: 2 w / n
+    double fan_w, fan_ex, fan_ey;
+    long long nx, ny;       // square: grid size; fan: (n, 1)
+    long long ray_offset;   // first global ray index of this object
+};
+
+// Double-precision ray state.  Aux arrays (exit-wave data for the PO integral) are allocated for
+// fan grids traced with RTW_TRACE_APERTURE only.
+enum AuxField : int {
+    kAuxRx = 0, kAuxRy, kAuxRz,              // exit point
+    kAuxExr, kAuxExi, kAuxEyr, kAuxEyi, kAuxEzr, kAuxEzi,  // exit field vector (Fresnel chain only)
+    kAuxQ11, kAuxQ12, kAuxQ22,               // exit WFC in (e_perp, e_perp x s)
+    kAuxEpx, kAuxEpy, kAuxEpz,               // e_perp of the exit interaction
+    kAuxDlegs, kAuxPath, kAuxNfLegs,
+    kAuxCount
+};
+
+struct RaysDev {
+    long long R;      // rays per order
+    int np;           // number of orders
+    int precision;    // RTW_FP64 / RTW_MIXED
+    // FP64 state
+    double2* s01;     // (s_x, s_y)
+    double2* s2psi;   // (s_z, Psi)
+    double2* Fx;      // F_x (re, im)
+    double2* Fy;
+    double2* Fz;
+    uint32_t* flags;
+    double* aux;      // kAuxCount x (np R) or null
+};
+
+// error bits of the device status word
+enum : unsigned int { kStatusCapacity = 1u, kStatusTimeout = 2u, kStatusNumeric = 4u };
+
+}  // namespace rtw

@@ -1,0 +1,180 @@
+// rtw_trace.cu -- trace kernels: one thread per incident ray, structure-of-arrays ray state.
+#include "rtw_launch.h"
+#include "rtw_trace.cuh"
+
+namespace rtw {
+
+namespace {
+
+// Stores the far-field record of every emitted order into the SoA ray state (16-byte vectors).
+struct StateSink {
+    const ObjDev* o;
+    RaysDev st;
+    long long j;
+    bool aux;
+    unsigned int emitted;
+
+    __device__ void emit(int p, const ExitWave& w)
+    {
+        FarRecord fr;
+        if (!far_record(*o, w, fr)) return;
+        const long long i = (long long)p * st.R + j;
+        st.s01[i] = make_double2(fr.s[0], fr.s[1]);
+        st.s2psi[i] = make_double2(fr.s[2], fr.psi);
+        st.Fx[i] = make_double2(fr.F[0], fr.F[1]);
+        st.Fy[i] = make_double2(fr.F[2], fr.F[3]);
+        st.Fz[i] = make_double2(fr.F[4], fr.F[5]);
+        st.flags[i] = fr.flags;
+        emitted |= 1u << p;
+        if (aux) {
+            const long long n = (long long)st.np * st.R;
+            double* a = st.aux + i;
+            a[kAuxRx * n] = w.r[0];
+            a[kAuxRy * n] = w.r[1];
+            a[kAuxRz * n] = w.r[2];
+            // exit field of the Fresnel chain as a vector: e1 ep + e2 (ep x s)
+            double v2x = w.ep[1] * w.k[2] - w.ep[2] * w.k[1];
+            double v2y = w.ep[2] * w.k[0] - w.ep[0] * w.k[2];
+            double v2z = w.ep[0] * w.k[1] - w.ep[1] * w.k[0];
+            a[kAuxExr * n] = w.e1r * w.ep[0] + w.e2r * v2x;
+            a[kAuxExi * n] = w.e1i * w.ep[0] + w.e2i * v2x;
+            a[kAuxEyr * n] = w.e1r * w.ep[1] + w.e2r * v2y;
+            a[kAuxEyi * n] = w.e1i * w.ep[1] + w.e2i * v2y;
+            a[kAuxEzr * n] = w.e1r * w.ep[2] + w.e2r * v2z;
+            a[kAuxEzi * n] = w.e1i * w.ep[2] + w.e2i * v2z;
+            a[kAuxQ11 * n] = w.q11;
+            a[kAuxQ12 * n] = w.q12;
+            a[kAuxQ22 * n] = w.q22;
+            a[kAuxEpx * n] = w.ep[0];
+            a[kAuxEpy * n] = w.ep[1];
+            a[kAuxEpz * n] = w.ep[2];
+            a[kAuxDlegs * n] = w.dlegs;
+            a[kAuxPath * n] = w.path;
+            a[kAuxNfLegs * n] = (double)w.nf_legs;
+        }
+    }
+};
+
+// Records in the [ray][order] layout of rtw_trace_points.
+struct PointSink {
+    const ObjDev* o;
+    long long j;
+    int np;
+    double* s_out;
+    double* F_out;
+    double* psi_out;
+    uint32_t* flags_out;
+
+    __device__ void emit(int p, const ExitWave& w)
+    {
+        FarRecord fr;
+        if (!far_record(*o, w, fr)) return;
+        const long long i = j * np + p;
+        if (s_out)
+            for (int c = 0; c < 3; ++c) s_out[3 * i + c] = fr.s[c];
+        if (F_out)
+            for (int c = 0; c < 6; ++c) F_out[6 * i + c] = fr.F[c];
+        if (psi_out) psi_out[i] = fr.psi;
+        if (flags_out) flags_out[i] = fr.flags;
+    }
+};
+
+__device__ __forceinline__ int find_object(const ObjDev* objs, int nobj, long long j)
+{
+    int lo = 0, hi = nobj - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (objs[mid].ray_offset <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) trace_kernel_fp64(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
+                                                         int pmax, int aux)
+{
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= st.R) return;
+    const ObjDev* o = objs + (nobj > 1 ? find_object(objs, nobj, j) : 0);
+    StateSink sink{o, st, j, aux != 0, 0u};
+    double x, y;
+    if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray_fp64<false>(*o, x, y, pmax, sink);
+    for (int p = 0; p < st.np; ++p)
+        if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
+}
+
+__global__ void __launch_bounds__(128) trace_points_kernel(const ObjDev* __restrict__ obj, const double* __restrict__ xy,
+                                                           long long n, int pmax, double* s_out, double* F_out,
+                                                           double* psi_out, uint32_t* flags_out)
+{
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int np = pmax + 1;
+    if (flags_out)
+        for (int p = 0; p < np; ++p) flags_out[j * np + p] = 0u;
+    PointSink sink{obj, j, np, s_out, F_out, psi_out, flags_out};
+    trace_ray_fp64<false>(*obj, xy[2 * j], xy[2 * j + 1], pmax, sink);
+}
+
+__global__ void export_kernel(RaysDev st, int order, long long first, long long count, double* s_out, double* F_out,
+                              double* psi_out, uint32_t* flags_out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const long long i = (long long)order * st.R + first + t;
+    const uint32_t f = st.flags[i];
+    if (flags_out) flags_out[t] = f;
+    const bool v = (f & kFlagValid) != 0;
+    if (s_out) {
+        double2 a = v ? st.s01[i] : make_double2(0.0, 0.0), b = v ? st.s2psi[i] : make_double2(0.0, 0.0);
+        s_out[3 * t] = a.x;
+        s_out[3 * t + 1] = a.y;
+        s_out[3 * t + 2] = b.x;
+    }
+    if (psi_out) psi_out[t] = v ? st.s2psi[i].y : 0.0;
+    if (F_out) {
+        double2 fx = v ? st.Fx[i] : make_double2(0.0, 0.0), fy = v ? st.Fy[i] : make_double2(0.0, 0.0),
+                fz = v ? st.Fz[i] : make_double2(0.0, 0.0);
+        F_out[6 * t] = fx.x;
+        F_out[6 * t + 1] = fx.y;
+        F_out[6 * t + 2] = fy.x;
+        F_out[6 * t + 3] = fy.y;
+        F_out[6 * t + 4] = fz.x;
+        F_out[6 * t + 5] = fz.y;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, bool aux, unsigned int* status,
+                         cudaStream_t s)
+{
+    (void)status;
+    if (st.R == 0) return cudaSuccess;
+    const int bs = 128;
+    const long long nb = (st.R + bs - 1) / bs;
+    trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_points(const ObjDev* d_obj, const double* xy, long long n, int pmax, double* s_out,
+                                double* F_out, double* psi_out, uint32_t* flags_out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int bs = 128;
+    trace_points_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(d_obj, xy, n, pmax, s_out, F_out, psi_out,
+                                                                       flags_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(RaysDev st, int order, long long first, long long count, double* s_out, double* F_out,
+                          double* psi_out, uint32_t* flags_out, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const int bs = 256;
+    export_kernel<<<(unsigned)((count + bs - 1) / bs), bs, 0, s>>>(st, order, first, count, s_out, F_out, psi_out,
+                                                                     flags_out);
+    return cudaGetLastError();
+}
+
+}  // namespace rtw

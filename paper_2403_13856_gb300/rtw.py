@@ -1,0 +1,238 @@
+"""Thin ctypes binding of librtw.so (include/rtw.h), the GB300 Ray Theory of Waves library.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels behind the C ABI.
+Device buffers are torch tensors (PyTorch provides device memory and streams).  There is no
+CPU fallback: if the library or a CUDA device is missing, every call raises RTWError.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "librtw.so")
+
+RTW_OK = 0
+RTW_GRID_FAN, RTW_GRID_SQUARE = 0, 1
+RTW_FP64, RTW_MIXED = 0, 1
+RTW_DENSE, RTW_NEWTON = 0, 1
+RTW_DIRS_PLANE, RTW_DIRS_GRID = 0, 1
+RTW_FIELD_PER_ORDER, RTW_FIELD_PO = 1, 2
+RTW_TRACE_APERTURE = 1
+RTW_MASK_CAUSTIC, RTW_MASK_AXIAL, RTW_MASK_PO = 1, 2, 4
+FLAG_VALID, FLAG_ORIENT, FLAG_CAUSTIC = 1, 2, 4
+
+
+class RTWError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rtw error {code}: {msg}")
+        self.code = code
+
+
+class rtw_object_desc(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double),
+                ("quat", ctypes.c_double * 4), ("center", ctypes.c_double * 3),
+                ("m_re", ctypes.c_double), ("m_im", ctypes.c_double)]
+
+
+class rtw_incident(ctypes.Structure):
+    _fields_ = [("wavelength_um", ctypes.c_double), ("dir", ctypes.c_double * 3),
+                ("jones_re", ctypes.c_double * 2), ("jones_im", ctypes.c_double * 2)]
+
+
+class rtw_trace_params(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int), ("p_max", ctypes.c_int), ("precision", ctypes.c_int),
+                ("flags", ctypes.c_int), ("n_rays", ctypes.c_int64), ("spacing", ctypes.c_double),
+                ("fan_phi", ctypes.c_double)]
+
+
+class rtw_dirs(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("alpha0", ctypes.c_double), ("dalpha", ctypes.c_double), ("cell_window", ctypes.c_int64 * 4)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads librtw.so; raises RTWError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RTWError(-3, f"{LIB_PATH} is missing: build it with paper_2403_13856_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        sig = {
+            "rtw_create_object": ([p, i, p, p], i),
+            "rtw_destroy_object": ([p], None),
+            "rtw_object_grid": ([p, i, p, p, p, p], i),
+            "rtw_trace": ([p, p, p, p], i),
+            "rtw_rays_info": ([p, p, p, p], i),
+            "rtw_rays_export": ([p, i, i64, i64, p, p, p, p, p], i),
+            "rtw_destroy_rays": ([p], None),
+            "rtw_trace_points": ([p, i, p, i64, i, p, p, p, p, p], i),
+            "rtw_field": ([p, p, i, i, p, p, p], i),
+            "rtw_sync_status": ([p], i),
+            "rtw_status_string": ([i], ctypes.c_char_p),
+            "rtw_last_error": ([], ctypes.c_char_p),
+            "rtw_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != RTW_OK:
+        raise RTWError(rc, lib().rtw_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class ObjectSpec:
+    a: float
+    b: float
+    c: float
+    quat: Sequence[float] = (1.0, 0.0, 0.0, 0.0)
+    center: Sequence[float] = (0.0, 0.0, 0.0)
+    m: float = 1.333
+    wavelength: float = 0.6328
+    jones: Sequence[complex] = (1.0, 0.0)
+
+
+class Object:
+    """rtw_object handle (one or many ellipsoids with their incident waves)."""
+
+    def __init__(self, specs: Sequence[ObjectSpec]):
+        n = len(specs)
+        descs = (rtw_object_desc * n)()
+        incs = (rtw_incident * n)()
+        for k, s in enumerate(specs):
+            d = descs[k]
+            d.a, d.b, d.c = s.a, s.b, s.c
+            d.quat[:] = list(s.quat)
+            d.center[:] = list(s.center)
+            d.m_re, d.m_im = s.m, 0.0
+            w = incs[k]
+            w.wavelength_um = s.wavelength
+            w.dir[:] = [0.0, 0.0, 1.0]
+            j = [complex(x) for x in s.jones]
+            w.jones_re[:] = [j[0].real, j[1].real]
+            w.jones_im[:] = [j[0].imag, j[1].imag]
+        h = ctypes.c_void_p()
+        _check(lib().rtw_create_object(ctypes.byref(descs), n, ctypes.byref(incs), ctypes.byref(h)))
+        self.handle = h
+        self.count = n
+        self.specs = list(specs)
+
+    def grid(self, index: int, params: "rtw_trace_params"):
+        h = ctypes.c_double()
+        nx, ny = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().rtw_object_grid(self.handle, index, ctypes.byref(params), ctypes.byref(h), ctypes.byref(nx),
+                                     ctypes.byref(ny)))
+        return h.value, nx.value, ny.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.rtw_destroy_object(self.handle)
+            self.handle = None
+
+
+def trace_params(grid=RTW_GRID_SQUARE, p_max=5, precision=RTW_FP64, flags=0, n_rays=0, spacing=0.0, fan_phi=0.0):
+    tp = rtw_trace_params()
+    tp.grid, tp.p_max, tp.precision, tp.flags = grid, p_max, precision, flags
+    tp.n_rays, tp.spacing, tp.fan_phi = int(n_rays), float(spacing), float(fan_phi)
+    return tp
+
+
+class Rays:
+    """rtw_rays handle: the traced ray state, owned by the library."""
+
+    def __init__(self):
+        self.handle = ctypes.c_void_p()
+
+    def info(self):
+        R, npo, nob = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().rtw_rays_info(self.handle, ctypes.byref(R), ctypes.byref(npo), ctypes.byref(nob)))
+        return R.value, npo.value, nob.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.rtw_destroy_rays(self.handle)
+            self.handle = ctypes.c_void_p()
+
+
+def rtw_trace(obj: Object, params: rtw_trace_params, rays: Optional[Rays] = None, stream=None) -> Rays:
+    rays = rays or Rays()
+    _check(lib().rtw_trace(obj.handle, ctypes.byref(params), _stream_ptr(stream), ctypes.byref(rays.handle)))
+    return rays
+
+
+def rtw_rays_export(rays: Rays, order: int, first: int, count: int, s=None, F=None, psi=None, flags=None,
+                    stream=None):
+    _check(lib().rtw_rays_export(rays.handle, order, first, count, _ptr(s), _ptr(F), _ptr(psi), _ptr(flags),
+                                 _stream_ptr(stream)))
+
+
+def rtw_trace_points(obj: Object, index: int, xy, p_max: int, s=None, F=None, psi=None, flags=None, stream=None):
+    n = xy.shape[0]
+    _check(lib().rtw_trace_points(obj.handle, index, _ptr(xy), n, p_max, _ptr(s), _ptr(F), _ptr(psi), _ptr(flags),
+                                  _stream_ptr(stream)))
+
+
+def dirs_plane(n: int, alpha0: float, dalpha: float) -> rtw_dirs:
+    d = rtw_dirs()
+    d.kind, d.n_theta, d.n_phi, d.alpha0, d.dalpha = RTW_DIRS_PLANE, n, 0, alpha0, dalpha
+    d.cell_window[:] = [-1, -1, -1, -1]
+    return d
+
+
+def dirs_grid(n_theta: int, n_phi: int, cell_window=None) -> rtw_dirs:
+    d = rtw_dirs()
+    d.kind, d.n_theta, d.n_phi = RTW_DIRS_GRID, n_theta, n_phi
+    d.cell_window[:] = list(cell_window) if cell_window is not None else [-1, -1, -1, -1]
+    return d
+
+
+def rtw_field(rays: Rays, dirs: rtw_dirs, out, mask=None, mode=RTW_DENSE, flags=0, stream=None):
+    _check(lib().rtw_field(rays.handle, ctypes.byref(dirs), mode, flags, _ptr(out), _ptr(mask), _stream_ptr(stream)))
+
+
+def rtw_sync_status(stream=None):
+    _check(lib().rtw_sync_status(_stream_ptr(stream)))
+
+
+def rtw_version() -> str:
+    return lib().rtw_version().decode()
+
+
+def n_dirs(dirs: rtw_dirs) -> int:
+    return dirs.n_theta if dirs.kind == RTW_DIRS_PLANE else dirs.n_theta * dirs.n_phi
+
+
+def plane_angles(dirs: rtw_dirs):
+    """The in-plane angles alpha_k = alpha0 + k dalpha of a plane direction set (host numbers)."""
+    return [dirs.alpha0 + k * dirs.dalpha for k in range(dirs.n_theta)]
+
+
+def grid_angles(n_theta: int, n_phi: int):
+    th = [(i + 0.5) * math.pi / n_theta for i in range(n_theta)]
+    ph = [-math.pi + (j + 0.5) * 2 * math.pi / n_phi for j in range(n_phi)]
+    return th, ph
