@@ -182,6 +182,24 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
               uint8_t* mask_out, void* stream);
 
+/* ---- the fan path without allocation ----
+ * The paper has no counterpart of this call: it serves programs that may not allocate device
+ * memory themselves (a host application whose memory manager owns the device and forbids direct
+ * cudaMalloc from plug-ins, or a loop that must not risk the device-wide synchronisation an
+ * allocation can cause).  It traces a 1-D fan (tp: grid RTW_GRID_FAN, precision RTW_FP64) of the
+ * object described by d and w and writes its far field on in-plane directions (dirs: kind
+ * RTW_DIRS_PLANE) exactly as rtw_create_object + rtw_trace + rtw_field would, ray sum only
+ * (flags: 0 or RTW_FIELD_PER_ORDER), into the caller's field_out and optional mask_out (device
+ * buffers laid out as for rtw_field).  It allocates nothing: its working memory is a fixed array
+ * of about 5.8 MB compiled into the library, present on every GPU that loads it until the process
+ * exits.  Limits: n_rays * (p_max + 1) <= 65536 and n_theta <= 65536, larger sizes return
+ * RTW_ERR_CAPACITY.  The first call on each device looks up the array's device address (with
+ * that device current), so make the first call on a device before any stream capture.  All calls
+ * on a device share the array: calls whose GPU work overlaps (several streams or host threads)
+ * race and must be ordered by the caller.  Asynchronous on `stream`. */
+int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident* w, const rtw_trace_params* tp,
+                         const rtw_dirs* dirs, int flags, void* field_out, uint8_t* mask_out, void* stream);
+
 /* ---- status ---- */
 
 /* Synchronises `stream`, reads and clears the device status word of the library: RTW_OK or the

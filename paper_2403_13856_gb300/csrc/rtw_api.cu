@@ -81,6 +81,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+void rtw::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct rtw_object {
     int count = 0;
     int device = 0;

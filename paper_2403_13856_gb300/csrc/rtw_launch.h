@@ -28,6 +28,9 @@ struct FieldArgs {
     unsigned int* status;
 };
 
+// message returned by rtw_last_error() on the calling thread
+void set_last_error(const char* msg);
+
 // trace
 cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, bool aux, unsigned int* status,
                          cudaStream_t s);

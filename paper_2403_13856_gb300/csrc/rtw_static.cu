@@ -1,0 +1,195 @@
+// rtw_static.cu -- rtw_fan_field_static: the fan trace and far field without any allocation.
+//
+// Some programs that embed this library may not allocate device memory themselves: a host
+// application whose memory manager owns the whole device and forbids direct cudaMalloc calls from
+// plug-ins, or a control loop that must never block on the implicit device synchronisation an
+// allocation can bring.  For them this entry point runs the 1-D fan path (trace of every ray and
+// order, then the interpolated far field and its mask) entirely in caller buffers plus one
+// fixed-size scratch array that lives in the library's device image.
+//
+// The scratch array below is a file-scope __device__ symbol.  On the host its name only stands for
+// the symbol; the device address is looked up with cudaGetSymbolAddress, once per device, with that
+// device current, on the first call made on it.  Every call on a device shares the array and leaves
+// its contents behind, so each call clears what has to start at zero; calls whose work overlaps on
+// the GPU (other streams, other host threads) race on the array.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "rtw.h"
+#include "rtw_launch.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Limits of the scratch: rays times orders of the fan, and observation directions.
+constexpr long long kStaticRayOrders = 65536;
+constexpr long long kStaticDirs = 65536;
+// layout: object entry | ray state (s01, s2psi, Fx, Fy, Fz: 16 B each; flags: 4 B) | mask words
+constexpr size_t kObjBytes = 512;
+constexpr size_t kStateBytes = (size_t)kStaticRayOrders * (5 * 16 + 4);
+constexpr size_t kMaskBytes = (size_t)kStaticDirs * 4;
+constexpr size_t kScratchBytes = kObjBytes + kStateBytes + kMaskBytes + 256;
+
+static __device__ __align__(256) unsigned char g_rtw_static_scratch[kScratchBytes];
+
+__global__ void put_object_kernel(rtw::ObjDev o)
+{
+    // device code may name the array directly
+    *reinterpret_cast<rtw::ObjDev*>(g_rtw_static_scratch) = o;
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char* g_scratch_ptr[kMaxDevices] = {};
+
+int set_error(int code, const char* msg)
+{
+    rtw::set_last_error(msg);  // reported by rtw_last_error()
+    return code;
+}
+
+// device address of the scratch array for the current device (looked up once per device)
+int scratch_address(unsigned char** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_error(RTW_ERR_CUDA, "no current CUDA device");
+    if (dev < 0 || dev >= kMaxDevices) return set_error(RTW_ERR_UNSUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_rtw_static_scratch);
+        if (e != cudaSuccess || !p) return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
+        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return RTW_OK;
+}
+
+}  // namespace
+
+extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident* w, const rtw_trace_params* tp,
+                                    const rtw_dirs* dirs, int flags, void* field_out, uint8_t* mask_out,
+                                    void* stream)
+{
+    if (!d || !w || !tp || !dirs || !field_out) return set_error(RTW_ERR_ARG, "null pointer");
+    if (tp->grid != RTW_GRID_FAN || dirs->kind != RTW_DIRS_PLANE)
+        return set_error(RTW_ERR_ARG, "needs a fan grid and in-plane directions");
+    if (tp->precision != RTW_FP64) return set_error(RTW_ERR_UNSUPPORTED, "FP64 only");
+    if ((flags & ~RTW_FIELD_PER_ORDER) != 0) return set_error(RTW_ERR_UNSUPPORTED, "only RTW_FIELD_PER_ORDER");
+    if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return set_error(RTW_ERR_ARG, "p_max out of [0, 15]");
+    if (tp->n_rays < 2) return set_error(RTW_ERR_ARG, "fan needs n_rays >= 2");
+    const int np = tp->p_max + 1;
+    if (tp->n_rays * np > kStaticRayOrders)
+        return set_error(RTW_ERR_CAPACITY, "n_rays * (p_max + 1) exceeds the static scratch limit of 65536");
+    if (dirs->n_theta < 1 || dirs->n_theta > kStaticDirs)
+        return set_error(RTW_ERR_CAPACITY, "direction count outside [1, 65536]");
+    if (!(std::fabs(dirs->dalpha) > 0.0) || std::fabs(dirs->dalpha) > 0.5 ||
+        std::fabs(dirs->dalpha) * dirs->n_theta > 2.0 * kPi + 1e-9)
+        return set_error(RTW_ERR_ARG, "plane grid needs 0 < |dalpha| <= 0.5 and a span <= 2 pi");
+    // object validation and tables (the same rules as rtw_create_object)
+    if (!(d->a > 0.0 && d->b > 0.0 && d->c > 0.0)) return set_error(RTW_ERR_ARG, "semi-axes must be positive");
+    const double qn = std::sqrt(d->quat[0] * d->quat[0] + d->quat[1] * d->quat[1] + d->quat[2] * d->quat[2] +
+                                d->quat[3] * d->quat[3]);
+    if (!(std::fabs(qn - 1.0) <= 1e-9)) return set_error(RTW_ERR_ARG, "|quat| != 1");
+    if (!(d->m_re > 0.0) || d->m_re == 1.0) return set_error(RTW_ERR_ARG, "m must be positive and != 1");
+    if (d->m_im != 0.0) return set_error(RTW_ERR_UNSUPPORTED, "absorbing objects");
+    if (!(w->wavelength_um > 0.0)) return set_error(RTW_ERR_ARG, "wavelength must be positive");
+    if (w->dir[0] != 0.0 || w->dir[1] != 0.0 || w->dir[2] != 1.0)
+        return set_error(RTW_ERR_UNSUPPORTED, "incident direction must be (0, 0, 1)");
+
+    const double qw = d->quat[0] / qn, qx = d->quat[1] / qn, qy = d->quat[2] / qn, qz = d->quat[3] / qn;
+    const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+    const double ax[3] = {d->a, d->b, d->c};
+    double W[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += R[r][k] * R[c][k] / (ax[k] * ax[k]);
+            W[r][c] = s;
+        }
+    const double S00 = W[0][0] - W[0][2] * W[0][2] / W[2][2];
+    const double S01 = W[0][1] - W[0][2] * W[1][2] / W[2][2];
+    const double S11 = W[1][1] - W[1][2] * W[1][2] / W[2][2];
+    const double lmax = std::fmax(d->a, std::fmax(d->b, d->c)), lmin = std::fmin(d->a, std::fmin(d->b, d->c));
+    rtw::ObjDev o;
+    std::memset(&o, 0, sizeof(o));
+    o.W[0] = W[0][0]; o.W[1] = W[0][1]; o.W[2] = W[0][2];
+    o.W[3] = W[1][1]; o.W[4] = W[1][2]; o.W[5] = W[2][2];
+    for (int i = 0; i < 3; ++i) o.c[i] = d->center[i];
+    o.m = d->m_re;
+    o.lambda = w->wavelength_um;
+    o.k0 = 2.0 * kPi / w->wavelength_um;
+    o.jre[0] = w->jones_re[0]; o.jre[1] = w->jones_re[1];
+    o.jim[0] = w->jones_im[0]; o.jim[1] = w->jones_im[1];
+    o.zstart = d->center[2] - 2.0 * lmax - 1.0;
+    o.S[0] = S00; o.S[1] = S01; o.S[2] = S11;
+    o.cap = lmax * lmax * std::cbrt(lmax / w->wavelength_um);
+    o.lmin = lmin;
+    o.lmax = lmax;
+    const double e0 = std::cos(tp->fan_phi), e1 = std::sin(tp->fan_phi);
+    const double fw = 1.0 / std::sqrt(e0 * (S00 * e0 + S01 * e1) + e1 * (S01 * e0 + S11 * e1));
+    o.grid = rtw::kGridFan;
+    o.h = 2.0 * fw / (double)tp->n_rays;
+    o.fan_w = fw;
+    o.fan_ex = e0;
+    o.fan_ey = e1;
+    o.nx = tp->n_rays;
+    o.ny = 1;
+    o.ray_offset = 0;
+
+    unsigned char* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != RTW_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long R_ = tp->n_rays, n = R_ * np;
+    rtw::RaysDev st{};
+    st.R = R_;
+    st.np = np;
+    st.precision = RTW_FP64;
+    unsigned char* p = base + kObjBytes;
+    st.s01 = reinterpret_cast<double2*>(p);
+    st.s2psi = reinterpret_cast<double2*>(p + 16 * n);
+    st.Fx = reinterpret_cast<double2*>(p + 32 * n);
+    st.Fy = reinterpret_cast<double2*>(p + 48 * n);
+    st.Fz = reinterpret_cast<double2*>(p + 64 * n);
+    st.flags = reinterpret_cast<uint32_t*>(p + 80 * n);
+    st.aux = nullptr;
+    unsigned int* mask_words = reinterpret_cast<unsigned int*>(base + kObjBytes + kStateBytes);
+    rtw::ObjDev* d_obj = reinterpret_cast<rtw::ObjDev*>(base);
+
+    put_object_kernel<<<1, 1, 0, s>>>(o);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
+    // the trace writes every (ray, order) slot it owns, valid or not; the mask words and the output
+    // are accumulated and start from zero
+    const int nout = (flags & RTW_FIELD_PER_ORDER) ? np : 1;
+    const long long ndir = dirs->n_theta;
+    if ((e = cudaMemsetAsync(mask_words, 0, sizeof(unsigned int) * (size_t)ndir, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(field_out, 0, sizeof(double) * 4 * (size_t)nout * (size_t)ndir, s)) != cudaSuccess)
+        return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = rtw::launch_trace(d_obj, 1, st, tp->p_max, false, nullptr, s)) != cudaSuccess)
+        return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
+    rtw::FieldArgs a;
+    a.d_obj = d_obj;
+    a.st = st;
+    a.pmax = tp->p_max;
+    a.per_order = (flags & RTW_FIELD_PER_ORDER) ? 1 : 0;
+    a.out = static_cast<double*>(field_out);
+    a.mask = mask_words;
+    a.status = nullptr;
+    if ((e = rtw::launch_field_fan(a, R_, tp->fan_phi, (int)ndir, dirs->alpha0, dirs->dalpha, nullptr, nullptr, 0,
+                                   s)) != cudaSuccess)
+        return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
+    if (mask_out) {
+        if ((e = rtw::launch_finalize_mask(mask_words, mask_out, ndir, 0, dirs->n_theta, 0, dirs->alpha0,
+                                           dirs->dalpha, 2.0 * w->wavelength_um / lmin, s)) != cudaSuccess)
+            return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return RTW_OK;
+}
