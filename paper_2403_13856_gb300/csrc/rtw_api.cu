@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -314,7 +315,9 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     // one allocation carved into 256-byte aligned arrays
     const size_t n = (size_t)np * (size_t)R;
     size_t off[8], total = 0;
-    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, aux ? n * 8 * rtw::kAuxCount : 0, 0};
+    const bool sf = tp->grid == RTW_GRID_SQUARE;  // single-precision directions for the grid field
+    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, aux ? n * 8 * rtw::kAuxCount : 0,
+                             sf ? n * 32 : 0};
     for (int k = 0; k < 8; ++k) {
         off[k] = total;
         total = align_up(total + sizes[k], 256);
@@ -369,6 +372,8 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     r->st.Fz = (double2*)(b + off[4]);
     r->st.flags = (uint32_t*)(b + off[5]);
     r->st.aux = aux ? (double*)(b + off[6]) : nullptr;
+    r->st.sf = sf ? (float4*)(b + off[7]) : nullptr;
+    r->st.sl = sf ? (float4*)(b + off[7] + n * 16) : nullptr;
     RTW_CUDA(cudaMemcpyAsync(r->d_objs, r->objs.data(), sizeof(ObjDev) * objs.size(), cudaMemcpyHostToDevice, s));
     unsigned int* status = status_word(r->device);
     RTW_CUDA(rtw::launch_trace(r->d_objs, r->nobj, r->st, tp->p_max, aux, status, s));
@@ -455,10 +460,25 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     const long long ap_cap = po ? 2 * (long long)rays->np * nfan : 0;
     size_t off_mask = 0;
     size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir, 256);
-    size_t ntab = dirs->kind == RTW_DIRS_GRID ? 2 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi) : 0;
+    // double tables then their single-precision copies
+    size_t ntab = dirs->kind == RTW_DIRS_GRID ? 3 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi) : 0;
     size_t off_win = align_up(off_tab + sizeof(double) * ntab, 256);
     size_t off_nwin = align_up(off_win + sizeof(rtw::PoWindow) * rtw::kMaxPoWindows, 256);
-    size_t off_po = align_up(off_nwin + 256, 256);
+    // list of large triangles of the square-grid field (1/32 of all triangles, at least 65536)
+    long long ntri = 0;
+    if (dirs->kind == RTW_DIRS_GRID)
+        for (const ObjDev& o : rays->objs) ntri = std::max(ntri, 2 * (o.nx - 1) * (o.ny - 1) * rays->np);
+    const unsigned int big_cap = (unsigned int)std::min<long long>(std::max<long long>(65536, ntri / 32), 1ll << 26);
+    size_t off_big = align_up(off_nwin + 256, 256);
+    size_t off_nbig = align_up(off_big + (dirs->kind == RTW_DIRS_GRID ? 8 * (size_t)big_cap : 0), 256);
+    // (triangle, direction) pairs handed to the double-precision phase: 4 per direction and order
+    const unsigned int hit_cap =
+        dirs->kind == RTW_DIRS_GRID
+            ? (unsigned int)std::min<long long>(4 * ndir * (long long)rays->np + (1 << 20), 0x7fffffffll)
+            : 0;
+    size_t off_hit_tri = align_up(off_nbig + 256, 256);
+    size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
+    size_t off_po = align_up(off_hit_dir + 4 * (size_t)hit_cap + 256, 256);
     size_t po_bytes = po ? sizeof(double) * ((size_t)rays->np * (size_t)nfan + rtw::kMaxPoWindows + 1 +
                                              9 * (size_t)ap_cap)
                          : 0;
@@ -477,6 +497,11 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     rtw::PoWindow* d_win = (rtw::PoWindow*)(ws + off_win);
     int* d_nwin = (int*)(ws + off_nwin);
     double2* d_po = (double2*)(ws + off_po);
+    unsigned long long* d_big = (unsigned long long*)(ws + off_big);
+    unsigned int* d_nbig = (unsigned int*)(ws + off_nbig);
+    unsigned int* d_nhit = d_nbig + 1;
+    unsigned long long* d_hit_tri = (unsigned long long*)(ws + off_hit_tri);
+    unsigned int* d_hit_dir = (unsigned int*)(ws + off_hit_dir);
     unsigned int* status = status_word(rays->device);
     const size_t out_bytes_obj = sizeof(double) * 4 * (size_t)nout * (size_t)ndir;
     RTW_CUDA(cudaMemsetAsync(field_out, 0, out_bytes_obj * (size_t)rays->nobj, s));
@@ -501,7 +526,8 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
                 iy0 = w[2] < 0 ? 0 : w[2];
                 iy1 = w[3] > o.ny - 1 ? o.ny - 1 : w[3];
             }
-            RTW_CUDA(rtw::launch_field_grid(a, o.nx, ix0, ix1, iy0, iy1, dirs->n_theta, dirs->n_phi, tab, 0, s));
+            RTW_CUDA(rtw::launch_field_grid(a, o.nx, ix0, ix1, iy0, iy1, dirs->n_theta, dirs->n_phi, tab, d_big,
+                                            d_nbig, big_cap, d_hit_tri, d_hit_dir, d_nhit, hit_cap, 0, s));
         } else {
             if (po) {
                 RTW_CUDA(rtw::launch_po_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,

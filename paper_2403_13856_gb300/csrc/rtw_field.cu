@@ -85,149 +85,274 @@ __device__ __forceinline__ void add_contribution(const double* F, double psi, co
     atomicAdd(dst + 3, w * pi);
 }
 
+// As add_contribution, with the phase reduced to (-pi, pi] in double precision and its sine and
+// cosine taken in single precision (error below 3e-7 rad, inside the 1e-6 rad bound of the path).
+__device__ __forceinline__ void add_contribution_reduced(const double* F, double psi, const double* eth,
+                                                        const double* eph, double* dst)
+{
+    constexpr double kInv2Pi = 0.15915494309189533577, k2PiHi = 6.28318530717958623200;
+    const double r = fma(-k2PiHi, rint(psi * kInv2Pi), psi);
+    float sf, cf;
+    sincosf((float)r, &sf, &cf);
+    const double sp = sf, cp = cf;
+    double tr = 0.0, ti = 0.0, pr = 0.0, pi = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double re = F[2 * c] * cp - F[2 * c + 1] * sp;
+        const double im = F[2 * c] * sp + F[2 * c + 1] * cp;
+        tr += re * eth[c];
+        ti += im * eth[c];
+        pr += re * eph[c];
+        pi += im * eph[c];
+    }
+    atomicAdd(dst + 0, tr);
+    atomicAdd(dst + 1, ti);
+    atomicAdd(dst + 2, pr);
+    atomicAdd(dst + 3, pi);
+}
+
 // ---------------------------------------------------------------------------------------------
 // direction tables: cos(theta_i), sin(theta_i), cos(phi_j), sin(phi_j)
 // ---------------------------------------------------------------------------------------------
+// double tables (4 x n) followed by single-precision copies (4 x n floats)
 __global__ void dir_tables_kernel(int nt, int nph, double* tab)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float* ftab = reinterpret_cast<float*>(tab + 2 * (nt + nph));
     if (i < nt) {
         double s, c;
         sincos((i + 0.5) * (kPi / nt), &s, &c);
         tab[i] = c;
         tab[nt + i] = s;
+        ftab[i] = (float)c;
+        ftab[nt + i] = (float)s;
     }
     if (i < nph) {
         double s, c;
         sincos(-kPi + (i + 0.5) * (2.0 * kPi / nph), &s, &c);
         tab[2 * nt + i] = c;
         tab[2 * nt + nph + i] = s;
+        ftab[2 * nt + i] = (float)c;
+        ftab[2 * nt + nph + i] = (float)s;
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-// square grid: one thread per (order, cell)
+// square grid.  Phase 1: one thread per (order, cell); a triangle whose candidate cap holds few
+// grid directions is finished in place, a larger one (rim rays near grazing incidence map onto
+// wide image triangles) goes to a list.  Phase 2: one warp per listed triangle, the lanes taking
+// its candidate directions in turn, so that no thread serialises thousands of tests.
 // ---------------------------------------------------------------------------------------------
-__device__ void grid_triangle(const FieldArgs& a, const ObjDev& o, long long base, int p, const long long* id,
-                              const uint32_t* f, int nt, int nph, const double* __restrict__ tab)
+constexpr int kInlineCandidates = 32;
+constexpr unsigned int kHitClose = 0x80000000u;  // hit entry flag: needs the double-precision test
+
+struct TriGeom {
+    long long id[3];  // local ray indices, counter-clockwise in the ray grid
+    uint32_t f[3];
+    float s[3][3];    // single-precision (hi) exit directions
+    float c[3];       // unit vector at the centre of the image triangle (local origin)
+    int it0, it1, jp0, jcount;
+};
+
+// loads the corners and the single-precision candidate cap; returns the number of candidates
+__device__ long long tri_setup(const FieldArgs& a, long long base, TriGeom& g, int nt, int nph)
 {
-    if (!(f[0] & f[1] & f[2] & kFlagValid)) return;
-    bool consistent = flag_nf(f[0]) == flag_nf(f[1]) && flag_nf(f[1]) == flag_nf(f[2]) &&
-                      ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
-                      ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0;
-    double s[3][3];
+    if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) return 0;
 #pragma unroll
-    for (int v = 0; v < 3; ++v) load_dir(a.st, base + id[v], s[v]);
-    double c12[3];
-    cross3(s[1], s[2], c12);
-    const double vol = s[0][0] * c12[0] + s[0][1] * c12[1] + s[0][2] * c12[2];
-    const int sigma = vol > 0.0 ? 1 : (vol < 0.0 ? -1 : 0);
-    if (sigma == 0) return;
-    if (sigma != ((f[0] & kFlagOrient) ? 1 : -1)) consistent = false;
-    // edge planes in canonical order: E_ab(x) = g_ab (s_lo x s_hi) . x
-    double nrm[3][3];
-    double g[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const int va = e, vb = (e + 1) % 3;
-        if (id[va] < id[vb]) {
-            cross3(s[va], s[vb], nrm[e]);
-            g[e] = 1.0;
-        } else {
-            cross3(s[vb], s[va], nrm[e]);
-            g[e] = -1.0;
-        }
+    for (int v = 0; v < 3; ++v) {
+        const float4 q = a.st.sf[base + g.id[v]];
+        g.s[v][0] = q.x;
+        g.s[v][1] = q.y;
+        g.s[v][2] = q.z;
     }
-    // conservative cap of candidate directions (single precision)
-    float cmx = (float)(s[0][0] + s[1][0] + s[2][0]);
-    float cmy = (float)(s[0][1] + s[1][1] + s[2][1]);
-    float cmz = (float)(s[0][2] + s[1][2] + s[2][2]);
+    float cmx = g.s[0][0] + g.s[1][0] + g.s[2][0];
+    float cmy = g.s[0][1] + g.s[1][1] + g.s[2][1];
+    float cmz = g.s[0][2] + g.s[1][2] + g.s[2][2];
     const float cn = rsqrtf(cmx * cmx + cmy * cmy + cmz * cmz);
     cmx *= cn;
     cmy *= cn;
     cmz *= cn;
+    g.c[0] = cmx;
+    g.c[1] = cmy;
+    g.c[2] = cmz;
     float ch = 0.0f;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-        const float dx = (float)s[v][0] - cmx, dy = (float)s[v][1] - cmy, dz = (float)s[v][2] - cmz;
+        const float dx = g.s[v][0] - cmx, dy = g.s[v][1] - cmy, dz = g.s[v][2] - cmz;
         ch = fmaxf(ch, sqrtf(dx * dx + dy * dy + dz * dz));
     }
     const float rho = 2.0f * asinf(fminf(1.0f, 0.5f * ch)) + 1e-5f;
     const float thc = atan2f(sqrtf(cmx * cmx + cmy * cmy), cmz), phc = atan2f(cmy, cmx);
-    const float dth = (float)(kPi / nt), dph = (float)(2.0 * kPi / nph);
-    int it0 = (int)ceilf((thc - rho) / dth - 0.5f), it1 = (int)floorf((thc + rho) / dth - 0.5f);
-    it0 = max(it0, 0);
-    it1 = min(it1, nt - 1);
-    bool allphi = (thc - rho <= 0.0f) || (thc + rho >= (float)kPi);
-    int jp0 = 0, jcount = nph;
+    const float dth = 3.14159265358979f / nt, dph = 6.28318530717959f / nph;
+    g.it0 = max((int)ceilf((thc - rho) / dth - 0.5f), 0);
+    g.it1 = min((int)floorf((thc + rho) / dth - 0.5f), nt - 1);
+    bool allphi = (thc - rho <= 0.0f) || (thc + rho >= 3.14159265358979f);
+    g.jp0 = 0;
+    g.jcount = nph;
     if (!allphi) {
         const float sr = sinf(rho) / sinf(thc);
-        if (sr >= 0.9f) {  // close to a pole the phi extent is ill-conditioned: take every phi
-            allphi = true;
-        } else {
+        if (sr < 0.9f) {  // close to a pole the phi extent is ill-conditioned: take every phi
             const float dphi = asinf(sr) + 1e-5f;
-            jp0 = (int)ceilf((phc - dphi + (float)kPi) / dph - 0.5f);
-            const int jp1 = (int)floorf((phc + dphi + (float)kPi) / dph - 0.5f);
-            jcount = jp1 - jp0 + 1;
-            if (jcount > nph) {
-                jp0 = 0;
-                jcount = nph;
-            }
+            g.jp0 = (int)ceilf((phc - dphi + 3.14159265358979f) / dph - 0.5f);
+            const int jp1 = (int)floorf((phc + dphi + 3.14159265358979f) / dph - 0.5f);
+            g.jcount = min(max(jp1 - g.jp0 + 1, 0), nph);
+            if (jp1 - g.jp0 + 1 > nph) g.jp0 = 0;
         }
     }
-    const double* ctab = tab;
-    const double* stab = tab + nt;
-    const double* cptab = tab + 2 * nt;
-    const double* sptab = tab + 2 * nt + nph;
-    bool loaded = false;
-    double F[3][6], psi[3];
-    for (int it = it0; it <= it1; ++it) {
-        const double ct = ctab[it], sth = stab[it];
-        for (int jj = 0; jj < jcount; ++jj) {
-            int jp = (jp0 + jj) % nph;
-            if (jp < 0) jp += nph;
-            const double cp = cptab[jp], sp = sptab[jp];
-            const double x[3] = {sth * cp, sth * sp, ct};
-            double e[3];
+    if (g.it1 < g.it0 || g.jcount <= 0) return 0;
+    return (long long)(g.it1 - g.it0 + 1) * g.jcount;
+}
+
+__device__ __forceinline__ void cross3f(const float* a, const float* b, float* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Single-precision tests in a local frame.  With c the unit vector at the triangle's centre and
+// d_v = s_v - c (from the hi + lo split of s_v, relative error below 1.2e-7), an edge plane is
+// s_a x s_b = c x (d_b - d_a) + d_a x d_b and its value at a direction x = c + dx is
+// e = (d_a x d_b) . c + (s_a x s_b) . dx.  Every term scales with the triangle, so the rounding of
+// the inputs, of the table direction (3.1e-7) and of the arithmetic stays below
+// 2e-6 (|d_a| + |d_b|); signs beyond that bound are the double-precision signs.  The triangle's
+// orientation c . ((d_1 - d_0) x (d_2 - d_0)) + d_0 . (d_1 x d_2) is decided the same way.  Closer
+// calls go to the double-precision rule.
+struct TriFrame {
+    float n[3][3], k[3], tol[3], sg[3];
+    int sig32;
+    bool ok;  // corners agree in focal lines, orientation and carry no caustic flag, image not folded
+};
+
+__device__ void tri_frame(const FieldArgs& a, long long base, const TriGeom& g, TriFrame& fr)
+{
+    const float* c = g.c;
+    float d[3][3], dn[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) e[k] = g[k] * (nrm[k][0] * x[0] + nrm[k][1] * x[1] + nrm[k][2] * x[2]);
-            if (!edge_in(e[0], id[0], id[1], sigma) || !edge_in(e[1], id[1], id[2], sigma) ||
-                !edge_in(e[2], id[2], id[0], sigma))
-                continue;
-            const long long dk = (long long)it * nph + jp;
-            if (!consistent) {
-                atomicOr(a.mask + dk, kMaskCaustic);
-                continue;
-            }
-            if (!loaded) {
+    for (int v = 0; v < 3; ++v) {
+        const float4 lo = a.st.sl[base + g.id[v]];
+        d[v][0] = (g.s[v][0] - c[0]) + lo.x;
+        d[v][1] = (g.s[v][1] - c[1]) + lo.y;
+        d[v][2] = (g.s[v][2] - c[2]) + lo.z;
+        dn[v] = sqrtf(d[v][0] * d[v][0] + d[v][1] * d[v][1] + d[v][2] * d[v][2]);
+    }
 #pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const long long i = base + id[v];
-                    const double2 fx = a.st.Fx[i], fy = a.st.Fy[i], fz = a.st.Fz[i];
-                    F[v][0] = fx.x; F[v][1] = fx.y; F[v][2] = fy.x;
-                    F[v][3] = fy.y; F[v][4] = fz.x; F[v][5] = fz.y;
-                    psi[v] = a.st.s2psi[i].y;
-                }
-                loaded = true;
-            }
-            // barycentric weights of the central projection onto the plane of the corners
-            const double ssum = e[0] + e[1] + e[2];
-            const double l0 = e[1] / ssum, l1 = e[2] / ssum, l2 = e[0] / ssum;
-            double Fi[6];
+    for (int e = 0; e < 3; ++e) {
+        const int va = e, vb = (e + 1) % 3;
+        const bool fwd = g.id[va] < g.id[vb];
+        const float* dl = fwd ? d[va] : d[vb];
+        const float* dh = fwd ? d[vb] : d[va];
+        fr.sg[e] = fwd ? 1.0f : -1.0f;
+        const float dd[3] = {dh[0] - dl[0], dh[1] - dl[1], dh[2] - dl[2]};
+        float cx[3], dx[3];
+        cross3f(c, dd, cx);
+        cross3f(dl, dh, dx);
+        fr.n[e][0] = cx[0] + dx[0];
+        fr.n[e][1] = cx[1] + dx[1];
+        fr.n[e][2] = cx[2] + dx[2];
+        fr.k[e] = dx[0] * c[0] + dx[1] * c[1] + dx[2] * c[2];
+        fr.tol[e] = 2e-6f * (dn[va] + dn[vb]);
+    }
+    const float u[3] = {d[1][0] - d[0][0], d[1][1] - d[0][1], d[1][2] - d[0][2]};
+    const float w[3] = {d[2][0] - d[0][0], d[2][1] - d[0][1], d[2][2] - d[0][2]};
+    float uw[3], d12[3];
+    cross3f(u, w, uw);
+    cross3f(d[1], d[2], d12);
+    const float vol =
+        c[0] * uw[0] + c[1] * uw[1] + c[2] * uw[2] + d[0][0] * d12[0] + d[0][1] * d12[1] + d[0][2] * d12[2];
+    const float un = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const float wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    const float tv = 2e-6f * (un * wn + dn[0] * dn[1] * dn[2]);
+    fr.sig32 = vol > tv ? 1 : (vol < -tv ? -1 : 0);
+    const uint32_t* f = g.f;
+    fr.ok = flag_nf(f[0]) == flag_nf(f[1]) && flag_nf(f[1]) == flag_nf(f[2]) && ((f[0] ^ f[1]) & kFlagOrient) == 0 &&
+            ((f[1] ^ f[2]) & kFlagOrient) == 0 && ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0 &&
+            fr.sig32 == ((f[0] & kFlagOrient) ? 1 : -1);
+}
+
+// 0: outside; 1: inside (sure); 2: close call
+__device__ __forceinline__ int tri_classify(const TriFrame& fr, float dx0, float dx1, float dx2)
+{
+    int npos = 0, nneg = 0;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) Fi[c] = l0 * F[0][c] + l1 * F[1][c] + l2 * F[2][c];
-            const double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
-            const double eth[3] = {ct * cp, ct * sp, -sth};
-            const double eph[3] = {-sp, cp, 0.0};
-            double* dst = a.out + (dk * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? p : 0)) * 4;
-            add_contribution(Fi, ps, eth, eph, 1.0, dst);
-        }
+    for (int k = 0; k < 3; ++k) {
+        const float ef = fr.sg[k] * (fr.k[k] + fr.n[k][0] * dx0 + fr.n[k][1] * dx1 + fr.n[k][2] * dx2);
+        npos += ef > fr.tol[k];
+        nneg += ef < -fr.tol[k];
+    }
+    if (npos > 0 && nneg > 0) return 0;
+    if ((npos == 3 || nneg == 3) && fr.sig32 != 0) return ((npos == 3 ? 1 : -1) == fr.sig32) ? 1 : 0;
+    return 2;
+}
+
+struct HitArgs {
+    unsigned long long* tri;  // (order-cell index << 1) | triangle
+    unsigned int* dir;        // direction index | kHitClose
+    unsigned int* n;
+    unsigned int cap;
+};
+
+// warp-aggregated append of one (triangle, direction) pair
+__device__ __forceinline__ void push_hit(const HitArgs& h, unsigned int* status, unsigned long long code,
+                                         unsigned int dir)
+{
+    const unsigned int m = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned int b = 0;
+    if (lane == leader) b = atomicAdd(h.n, (unsigned int)__popc(m));
+    b = __shfl_sync(m, b, leader) + __popc(m & ((1u << lane) - 1u));
+    if (b < h.cap) {
+        h.tri[b] = code;
+        h.dir[b] = dir;
+    } else {
+        atomicOr(status, kStatusCapacity);
     }
 }
 
+__device__ __forceinline__ void candidate(const FieldArgs& a, const HitArgs& h, const TriFrame& fr,
+                                          unsigned long long code, int it, int jp, int nph, float dx0, float dx1,
+                                          float dx2)
+{
+    const int cls = tri_classify(fr, dx0, dx1, dx2);
+    if (cls == 0) return;
+    const unsigned int dk = (unsigned int)it * (unsigned int)nph + (unsigned int)jp;
+    if (cls == 2) {
+        push_hit(h, a.status, code, dk | kHitClose);
+    } else if (!fr.ok) {  // singular or folded cell: mark, add nothing
+        if (!(a.mask[dk] & kMaskCaustic)) atomicOr(a.mask + dk, kMaskCaustic);
+    } else {
+        push_hit(h, a.status, code, dk);
+    }
+}
+
+// corners of triangle t (0: c00 c10 c11, 1: c00 c11 c01) of cell (cx, cy)
+__device__ __forceinline__ void cell_triangle(const FieldArgs& a, long long base, long long nx, long long cx,
+                                              long long cy, int t, TriGeom& g)
+{
+    const long long l00 = cy * nx + cx;
+    g.id[0] = l00;
+    g.id[1] = t == 0 ? l00 + 1 : l00 + nx + 1;
+    g.id[2] = t == 0 ? l00 + nx + 1 : l00 + nx;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) g.f[v] = a.st.flags[base + g.id[v]];
+}
+
+struct DirTabF {
+    const float *ct, *st, *cp, *sp;
+};
+
+__device__ __forceinline__ DirTabF dir_tab_f(const double* tab, int nt, int nph)
+{
+    const float* f = reinterpret_cast<const float*>(tab + 2 * (nt + nph));
+    return DirTabF{f, f + nt, f + 2 * nt, f + 2 * nt + nph};
+}
+
+// Phase 1: one thread per (order, cell).  Triangles with few candidates are tested here; larger
+// ones go to the big list (one warp each in phase 2).
 __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, long long nx, long long ix0, long long ncx,
                                                          long long iy0, long long ncy, int nt, int nph,
-                                                         const double* __restrict__ tab)
+                                                         const double* __restrict__ tab, unsigned long long* big,
+                                                         unsigned int* nbig, unsigned int big_cap, HitArgs h)
 {
     const ObjDev& o = *a.d_obj;
     const long long ncell = ncx * ncy;
@@ -237,20 +362,157 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, long long 
     const long long cell = tid - (long long)p * ncell;
     const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
     const long long base = (long long)p * a.st.R + o.ray_offset;
-    const long long l00 = cy * nx + cx;
-    const long long lid[4] = {l00, l00 + 1, l00 + nx + 1, l00 + nx};  // c00 c10 c11 c01
-    uint32_t fl[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) fl[v] = a.st.flags[base + lid[v]];
-    {
-        const long long id[3] = {lid[0], lid[1], lid[2]};
-        const uint32_t f[3] = {fl[0], fl[1], fl[2]};
-        grid_triangle(a, o, base, p, id, f, nt, nph, tab);
+    const DirTabF T = dir_tab_f(tab, nt, nph);
+    for (int t = 0; t < 2; ++t) {
+        TriGeom g;
+        cell_triangle(a, base, nx, cx, cy, t, g);
+        const long long nc = tri_setup(a, base, g, nt, nph);
+        if (nc == 0) continue;
+        const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
+        if (nc > kInlineCandidates) {
+            const unsigned int slot = atomicAdd(nbig, 1u);
+            if (slot < big_cap) {
+                big[slot] = code;
+                continue;
+            }
+        }
+        TriFrame fr;
+        tri_frame(a, base, g, fr);
+        for (int it = g.it0; it <= g.it1; ++it) {
+            const float ct = T.ct[it], sth = T.st[it];
+            for (int jj = 0; jj < g.jcount; ++jj) {
+                int jp = g.jp0 + jj;
+                jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
+                candidate(a, h, fr, code, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
+                          ct - g.c[2]);
+            }
+        }
     }
-    {
-        const long long id[3] = {lid[0], lid[2], lid[3]};
-        const uint32_t f[3] = {fl[0], fl[2], fl[3]};
-        grid_triangle(a, o, base, p, id, f, nt, nph, tab);
+}
+
+// Phase 2: one warp per listed triangle, rows in turn, the lanes taking the columns.
+__global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, long long nx, long long ix0,
+                                                             long long ncx, long long iy0, long long ncy, int nt,
+                                                             int nph, const double* __restrict__ tab,
+                                                             const unsigned long long* big, const unsigned int* nbig,
+                                                             unsigned int big_cap, HitArgs h)
+{
+    const ObjDev& o = *a.d_obj;
+    const long long ncell = ncx * ncy;
+    const unsigned int n = min(*nbig, big_cap);
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const DirTabF T = dir_tab_f(tab, nt, nph);
+    for (long long w = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
+        const unsigned long long code = big[w];
+        const int t = (int)(code & 1ull);
+        const long long tid = (long long)(code >> 1);
+        const int p = (int)(tid / ncell);
+        const long long cell = tid - (long long)p * ncell;
+        const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
+        const long long base = (long long)p * a.st.R + o.ray_offset;
+        TriGeom g;
+        cell_triangle(a, base, nx, cx, cy, t, g);
+        if (tri_setup(a, base, g, nt, nph) == 0) continue;
+        TriFrame fr;
+        tri_frame(a, base, g, fr);
+        for (int it = g.it0; it <= g.it1; ++it) {
+            const float ct = T.ct[it], sth = T.st[it];
+            for (int jj = lane; jj < g.jcount; jj += 32) {
+                int jp = g.jp0 + jj;
+                jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
+                candidate(a, h, fr, code, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
+                          ct - g.c[2]);
+            }
+        }
+    }
+}
+
+// Phase 3: one thread per (triangle, direction) pair: the double-precision rule for close calls,
+// then the barycentric weights of the central projection, F, Psi and F e^{i Psi}.
+__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, long long nx, long long ix0, long long ncx,
+                                                             long long iy0, long long ncy, int nt, int nph,
+                                                             const double* __restrict__ tab, HitArgs h)
+{
+    const ObjDev& o = *a.d_obj;
+    const long long ncell = ncx * ncy;
+    const unsigned int n = min(*h.n, h.cap);
+    const double* ctab = tab;
+    const double* stab = tab + nt;
+    const double* cptab = tab + 2 * nt;
+    const double* sptab = tab + 2 * nt + nph;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long code = h.tri[q];
+        const unsigned int dw = h.dir[q];
+        const bool close = (dw & kHitClose) != 0;
+        const unsigned int dk = dw & ~kHitClose;
+        const int t = (int)(code & 1ull);
+        const long long tid = (long long)(code >> 1);
+        const int p = (int)(tid / ncell);
+        const long long cell = tid - (long long)p * ncell;
+        const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
+        const long long base = (long long)p * a.st.R + o.ray_offset;
+        TriGeom g;
+        cell_triangle(a, base, nx, cx, cy, t, g);
+        double s[3][3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) load_dir(a.st, base + g.id[v], s[v]);
+        double nrm[3][3], sg[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int va = e, vb = (e + 1) % 3;
+            if (g.id[va] < g.id[vb]) {
+                cross3(s[va], s[vb], nrm[e]);
+                sg[e] = 1.0;
+            } else {
+                cross3(s[vb], s[va], nrm[e]);
+                sg[e] = -1.0;
+            }
+        }
+        const int it = (int)(dk / (unsigned int)nph), jp = (int)(dk % (unsigned int)nph);
+        const double ct = ctab[it], sth = stab[it], cp = cptab[jp], sp = sptab[jp];
+        const double x[3] = {sth * cp, sth * sp, ct};
+        double e[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) e[k] = sg[k] * (nrm[k][0] * x[0] + nrm[k][1] * x[1] + nrm[k][2] * x[2]);
+        if (close) {
+            double c12[3];
+            cross3(s[1], s[2], c12);
+            const double vol = s[0][0] * c12[0] + s[0][1] * c12[1] + s[0][2] * c12[2];
+            const int sigma = vol > 0.0 ? 1 : (vol < 0.0 ? -1 : 0);
+            if (sigma == 0) continue;
+            if (!edge_in(e[0], g.id[0], g.id[1], sigma) || !edge_in(e[1], g.id[1], g.id[2], sigma) ||
+                !edge_in(e[2], g.id[2], g.id[0], sigma))
+                continue;
+            const uint32_t* f = g.f;
+            const bool ok = flag_nf(f[0]) == flag_nf(f[1]) && flag_nf(f[1]) == flag_nf(f[2]) &&
+                            ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
+                            ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0 && sigma == ((f[0] & kFlagOrient) ? 1 : -1);
+            if (!ok) {
+                atomicOr(a.mask + dk, kMaskCaustic);
+                continue;
+            }
+        }
+        double F[3][6], psi[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const long long i = base + g.id[v];
+            const double2 fx = a.st.Fx[i], fy = a.st.Fy[i], fz = a.st.Fz[i];
+            F[v][0] = fx.x; F[v][1] = fx.y; F[v][2] = fy.x;
+            F[v][3] = fy.y; F[v][4] = fz.x; F[v][5] = fz.y;
+            psi[v] = a.st.s2psi[i].y;
+        }
+        const double inv = 1.0 / (e[0] + e[1] + e[2]);
+        const double l0 = e[1] * inv, l1 = e[2] * inv, l2 = e[0] * inv;
+        double Fi[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Fi[k] = l0 * F[0][k] + l1 * F[1][k] + l2 * F[2][k];
+        const double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
+        const double eth[3] = {ct * cp, ct * sp, -sth};
+        const double eph[3] = {-sp, cp, 0.0};
+        double* dst = a.out + ((long long)dk * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? p : 0)) * 4;
+        add_contribution_reduced(Fi, ps, eth, eph, dst);
     }
 }
 
@@ -627,14 +889,29 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
 }
 
 cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, long long ix1, long long iy0,
-                              long long iy1, int nt, int nph, const double* tab, int newton, cudaStream_t s)
+                              long long iy1, int nt, int nph, const double* tab, unsigned long long* big,
+                              unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
+                              unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int newton,
+                              cudaStream_t s)
 {
     (void)newton;
     const long long ncx = ix1 - ix0, ncy = iy1 - iy0;
     if (ncx <= 0 || ncy <= 0) return cudaSuccess;
     const long long n = ncx * ncy * (a.pmax + 1);
     const int bs = 256;
-    field_grid_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab);
+    cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nhit, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    HitArgs h{hit_tri, hit_dir, nhit, hit_cap};
+    field_grid_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab, big,
+                                                                     nbig, big_cap, h);
+    // fixed grids walk the lists: 16 blocks per SM
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    field_grid_big_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab, big, nbig,
+                                                              big_cap, h);
+    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab, h);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,8 @@ struct RaysDev {
     double2* Fy;
     double2* Fz;
     uint32_t* flags;
+    float4* sf;       // s split as hi + lo, two floats per component (x, y, z, 0 each), for the
+    float4* sl;       //   field's single-precision candidate tests; null when not kept
     double* aux;      // kAuxCount x (np R) or null
 };
 

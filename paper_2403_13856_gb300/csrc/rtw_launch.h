@@ -42,7 +42,10 @@ cudaError_t launch_export(RaysDev st, int order, long long first, long long coun
 // field
 cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s);
 cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, long long ix1, long long iy0,
-                              long long iy1, int nt, int nph, const double* tab, int newton, cudaStream_t s);
+                              long long iy1, int nt, int nph, const double* tab, unsigned long long* big,
+                              unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
+                              unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int newton,
+                              cudaStream_t s);
 cudaError_t launch_fan_windows(const FieldArgs& a, long long nrays, double fan_phi, PoWindow* d_win,
                                int* d_nwin, cudaStream_t s);
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,

@@ -25,6 +25,11 @@ struct StateSink {
         st.Fy[i] = make_double2(fr.F[2], fr.F[3]);
         st.Fz[i] = make_double2(fr.F[4], fr.F[5]);
         st.flags[i] = fr.flags;
+        if (st.sf) {
+            const float hx = (float)fr.s[0], hy = (float)fr.s[1], hz = (float)fr.s[2];
+            st.sf[i] = make_float4(hx, hy, hz, 0.0f);
+            st.sl[i] = make_float4((float)(fr.s[0] - hx), (float)(fr.s[1] - hy), (float)(fr.s[2] - hz), 0.0f);
+        }
         emitted |= 1u << p;
         if (aux) {
             const long long n = (long long)st.np * st.R;
