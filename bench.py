@@ -29,17 +29,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rays·interfaces/s and far-field directions/s on 1 GB300 at stated error vs FP64"
 UNIT = "rays*interfaces/s"
-# FP64 flops of one interaction of the trace kernel, counted from its source (adds, multiplies,
-# fused multiply-adds as two, divisions and square roots as one each)
-FLOPS_PER_INTERACTION = 380
+# FP64 flops of one interaction of the trace kernel (both outgoing waves and one far-field record),
+# counted from its source: adds, multiplies, divisions and square roots as one, FMA as two
+FLOPS_PER_INTERACTION = 430
 FP64_NOMINAL_GFLOPS = 1250.0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0)
@@ -311,7 +311,7 @@ def main():
                    "l2": "flushed (256 MB write) between timed steps; ray state 2.6 GB > L2"},
         "directions_per_s": dps,
         "ms_trace": 1e3 * tr, "ms_field": 1e3 * statistics.median(t_field),
-        "gpu_launches": 4,
+        "gpu_launches": 6,
         "roofline": {"kernel": "trace_kernel_fp64", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "GFLOP/s FP64", "frac": achieved / peak,
                      "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (nominal 1250)",

@@ -53,7 +53,7 @@ struct StateSink {
             a[kAuxEpx * n] = w.ep[0];
             a[kAuxEpy * n] = w.ep[1];
             a[kAuxEpz * n] = w.ep[2];
-            a[kAuxDlegs * n] = w.dlegs;
+            a[kAuxDlegs * n] = 1.0 / w.pdet;
             a[kAuxPath * n] = w.path;
             a[kAuxNfLegs * n] = (double)w.nf_legs;
         }

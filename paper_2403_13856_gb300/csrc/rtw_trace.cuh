@@ -25,7 +25,8 @@ struct ExitWave {
     double q11, q12, q22;
     double e1r, e1i, e2r, e2i;
     double t11, t12, t21, t22;  // transfer of offsets (x, y) -> basis (only with kJ)
-    double dlegs, cosprod, path;
+    double pdet;   // prod |det(I + d Q)| over the internal legs: D_legs = 1 / pdet
+    double cosprod, path;
     double r[3];   // exit point
     int nf_legs;
     int sT;        // sign of det T
@@ -55,14 +56,15 @@ __device__ __forceinline__ void symv(const double* W, double x, double y, double
     oz = W[2] * x + W[4] * y + W[5] * z;
 }
 
-// Far-field record of an exit wave: F = E' sqrt(D_legs / |det Q'|) (-i)^{N_f}, Psi = k0 (L - s.r).
+// Far-field record of an exit wave: F = E' sqrt(D_legs / |det Q'|) (-i)^{N_f}, Psi = k0 (L - s.r),
+// with sqrt(D) = 1 / sqrt(|det Q'| prod |det(I + d Q)|).
 __device__ __forceinline__ bool far_record(const ObjDev& o, const ExitWave& w, FarRecord& fr)
 {
     double detQ = w.q11 * w.q22 - w.q12 * w.q12;
     if (!(fabs(detQ) > 0.0) || !isfinite(detQ)) return false;
     int nf = w.nf_legs + neg_eigs_sym(w.q11, w.q12, w.q22);
-    double D = w.dlegs / fabs(detQ);
-    double amp = sqrt(D);
+    double amp = rsqrt(fabs(detQ) * w.pdet);
+    double D = amp * amp;
     double pr = 1.0, pi = 0.0;  // (-i)^nf
     switch (nf & 3) {
     case 1: pr = 0.0; pi = -1.0; break;
@@ -88,8 +90,8 @@ __device__ __forceinline__ bool far_record(const ObjDev& o, const ExitWave& w, F
     // orientation of (x, y) -> s: sign(det J) sign(s . (v1 x v2)), det J = det Q' det T,
     // v1 x v2 = ep x (ep x s) = -s
     int orient = (detQ > 0.0 ? 1 : -1) * w.sT * -1;
-    double dgeo = D / w.cosprod;
-    uint32_t f = kFlagValid | (orient > 0 ? kFlagOrient : 0u) | (dgeo > o.cap ? kFlagCaustic : 0u);
+    // caustic when dA/dOmega = D / cosprod exceeds the cap
+    uint32_t f = kFlagValid | (orient > 0 ? kFlagOrient : 0u) | (D > o.cap * w.cosprod ? kFlagCaustic : 0u);
     f |= (uint32_t)(nf > 255 ? 255 : nf) << 8;
     fr.flags = f;
     return true;
@@ -135,15 +137,17 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
     double T11 = 1.0, T12 = 0.0, T21 = 0.0, T22 = -1.0;
     int sT = -1;
     double path = r2;  // phase of the incident plane wave at the first point (zero at the origin)
-    double dlegs = 1.0, cosprod = 1.0;
+    double pdet = 1.0, cosprod = 1.0;
     int nf = 0;
     double n_in = 1.0;
+    // reciprocal wave numbers of the two media, once per ray
+    const double ik_host = 1.0 / o.k0, ik_obj = 1.0 / (o.k0 * o.m);
     for (int q = 1; q <= pmax + 1; ++q) {
         const double n_out = (q == 1) ? o.m : 1.0;
         // outward normal n = W (r - c) / |W (r - c)|
         double gx, gy, gz;
         symv(W, r0 - o.c[0], r1 - o.c[1], r2 - o.c[2], gx, gy, gz);
-        double inv_gn = 1.0 / sqrt(gx * gx + gy * gy + gz * gz);
+        double inv_gn = rsqrt(gx * gx + gy * gy + gz * gz);
         double nx = gx * inv_gn, ny = gy * inv_gn, nz = gz * inv_gn;
         double ci = k0v * nx + k1v * ny + k2v * nz;  // signed cosine of incidence
         if (fabs(ci) < 1e-9) return;                 // grazing: P' singular
@@ -153,7 +157,7 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
         if (el2 < 1e-24) {
             ex = a0; ey = a1; ez = a2;
         } else {
-            double il = 1.0 / sqrt(el2);
+            double il = rsqrt(el2);
             ex *= il; ey *= il; ez *= il;
         }
         // rotation of the incident basis (a, b = a x k) onto (e_perp, e_perp x k)
@@ -191,9 +195,16 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
         bool tok = ktn2 > 0.0;
         double ktn = 0.0;
         double rp_r, rp_i, rq_r, rq_i, tp_r = 0.0, tq_r = 0.0;
+        double inv_ci, inv_ktn = 0.0;
         if (tok) {
             ktn = copysign(sqrt(ktn2), kin);
-            double i1 = 1.0 / (kin + ktn), i2 = 1.0 / (mr2 * kin + ktn);
+            // one reciprocal serves 1/(k_in + k_tn), 1/(m^2 k_in + k_tn), 1/ci and 1/k_tn
+            const double den1 = kin + ktn, den2 = mr2 * kin + ktn;
+            const double aa = den1 * den2, bb = ci * ktn;
+            const double inv = 1.0 / (aa * bb);
+            const double i1 = den2 * bb * inv, i2 = den1 * bb * inv;
+            inv_ci = aa * ktn * inv;
+            inv_ktn = aa * ci * inv;
             rp_r = (kin - ktn) * i1;
             rq_r = (mr2 * kin - ktn) * i2;
             tp_r = 2.0 * kin * i1;
@@ -210,17 +221,17 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
             double d2 = 1.0 / (u * u + kap * kap);
             rq_r = (u * u - kap * kap) * d2;
             rq_i = -2.0 * u * kap * d2;
+            inv_ci = 1.0 / ci;
         }
+        const double inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
         // reflected wave: k_l = tau - k_in n, signed cosine -ci; Eq. (WavefrontEqVec) in the
         // diagonal bases with n.(k_l - k_i) = -2 k_in
         ExitWave wl;
         {
-            double inv_ki = 1.0 / ki;
             wl.k[0] = (tx - kin * nx) * inv_ki;
             wl.k[1] = (ty - kin * ny) * inv_ki;
             wl.k[2] = (tz - kin * nz) * inv_ki;
             double dn = -2.0 * kin;
-            double inv_ci = 1.0 / ci;
             wl.q11 = (ki * Qe11 + C11 * dn) * inv_ki;
             wl.q12 = (-ki * ci * Qe12 + C12 * dn) * inv_ki * inv_ci;
             wl.q22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_ki * inv_ci * inv_ci;
@@ -235,13 +246,12 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
         ExitWave wt;
         double ct = 0.0;
         if (tok) {
-            double inv_kt = 1.0 / kt;
             wt.k[0] = (tx + ktn * nx) * inv_kt;
             wt.k[1] = (ty + ktn * ny) * inv_kt;
             wt.k[2] = (tz + ktn * nz) * inv_kt;
             ct = ktn * inv_kt;  // signed cosine of the transmitted wave
             double dn = ktn - kin;
-            double inv_ct = 1.0 / ct;
+            double inv_ct = kt * inv_ktn;
             wt.q11 = (ki * Qe11 + C11 * dn) * inv_kt;
             wt.q12 = -(-ki * ci * Qe12 + C12 * dn) * inv_kt * inv_ct;
             wt.q22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
@@ -258,7 +268,7 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
         if (q == 1) {
             // order 0: external reflection (Eq. epsilon_VCRM, p = 0)
             wl.ep[0] = ex; wl.ep[1] = ey; wl.ep[2] = ez;
-            wl.dlegs = 1.0;
+            wl.pdet = 1.0;
             wl.cosprod = 1.0;
             wl.path = path;
             wl.r[0] = r0; wl.r[1] = r1; wl.r[2] = r2;
@@ -275,7 +285,7 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
             // order q-1 leaves by refraction; the reflected wave stays inside
             if (tok) {
                 wt.ep[0] = ex; wt.ep[1] = ey; wt.ep[2] = ez;
-                wt.dlegs = dlegs;
+                wt.pdet = pdet;
                 wt.cosprod = cosprod * cos_ratio;
                 wt.path = path;
                 wt.r[0] = r0; wt.r[1] = r1; wt.r[2] = r2;
@@ -313,7 +323,7 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
         q11 = (q11 + d * dq) * idet;
         q12 = q12 * idet;
         q22 = (q22 + d * dq) * idet;
-        dlegs *= fabs(idet);
+        pdet *= fabs(detA);
         nf += neg_eigs_sym(A11, A12, A22);
         if (detA < 0.0) sT = -sT;
         if (kJ) {
