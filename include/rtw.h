@@ -60,7 +60,9 @@ extern "C" {
                        optical path and phase in double precision                              */
 
 #define RTW_DENSE 0  /* interpolation of the dense ray map (the paper's RTW strategy)           */
-#define RTW_NEWTON 1 /* every hit refined by Newton steps on the exact FP64 trace             */
+#define RTW_NEWTON 1 /* hits refined by Newton steps on the exact FP64 trace (fan grids); a
+                        hit whose Newton iteration fails keeps its interpolated value and
+                        raises RTW_ERR_TIMEOUT at rtw_sync_status                               */
 
 #define RTW_DIRS_PLANE 0 /* in-plane angles alpha_k = alpha0 + k dalpha, k < n_theta, measured
                             from +z toward (cos fan_phi, sin fan_phi, 0); fan grids only        */
@@ -69,6 +71,8 @@ extern "C" {
 
 #define RTW_FIELD_PER_ORDER 1 /* output one (F_theta, F_phi) pair per order instead of the sum */
 #define RTW_FIELD_PO 2        /* fan grids: physical-optics integral around in-plane folds      */
+#define RTW_FIELD_NEAR_FOLDS 4 /* with RTW_NEWTON: refine only the hits within 2 deg of an
+                                  in-plane fold of their order (rainbow windows)                 */
 
 #define RTW_TRACE_APERTURE 1 /* keep the exit-wave data the PO integral needs (fan grids)       */
 
@@ -176,7 +180,8 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
  * the near-caustic flag, add nothing and mark the directions they cover (RTW_MASK_CAUSTIC).  With
  * RTW_FIELD_PO (fan grids traced with RTW_TRACE_APERTURE) the field near every in-plane fold is
  * the physical-optics integral over the exit wave ("Diffraction effect correction based on VCRM").
- * mode RTW_NEWTON replaces each interpolated hit by the exact ray found by Newton steps.
+ * mode RTW_NEWTON replaces each interpolated hit (of fan grids) by the exact ray found by Newton steps
+ * on the FP64 trace (all hits, or with RTW_FIELD_NEAR_FOLDS those within 2 deg of a fold).
  * field_out (device): [objects][directions][orders or 1][2] complex128 (F_theta, F_phi), zeroed
  * and written.  mask_out (device, optional): [objects][directions] uint8.  Asynchronous. */
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,

@@ -26,7 +26,7 @@ VALID, NF, ORIENT, NREFL, S, F, PSI, D, DGEO, J = 0, 1, 2, 3, 4, 7, 13, 14, 15, 
 V1, V2, REXIT, Q, E, DLEGS, NFLEGS, PATH, POWER, COSPROD, CAUSTIC = 20, 23, 26, 29, 33, 37, 38, 39, 40, 41, 42
 NFIELD = 48
 MASK_CAUSTIC, MASK_AXIAL, MASK_PO = 1, 2, 4
-FIELD_PO, FIELD_EXACT = 1, 2
+FIELD_PO, FIELD_EXACT, FIELD_EXACT_FOLDS = 1, 2, 4
 
 
 def build(force: bool = False) -> str:

@@ -759,6 +759,23 @@ int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, co
             }
         }
 
+        /* in-plane folds of this order (sign changes of d alpha / d b), for the exact-near-folds
+         * mode: hits within 2 deg of a fold direction are evaluated by Newton */
+        double folds[64];
+        int nfold = 0;
+        if (flags & OR_FIELD_EXACT_FOLDS) {
+            for (int64_t j = 1; j + 1 < nrays && nfold < 64; ++j) {
+                if (rec[((size_t)(j - 1) * np + p) * OR_NFIELD + OR_VALID] == 0.0 ||
+                    rec[((size_t)j * np + p) * OR_NFIELD + OR_VALID] == 0.0 ||
+                    rec[((size_t)(j + 1) * np + p) * OR_NFIELD + OR_VALID] == 0.0)
+                    continue;
+                double d0 = wrap_angle(al[j * np + p] - al[(j - 1) * np + p]);
+                double d1 = wrap_angle(al[(j + 1) * np + p] - al[j * np + p]);
+                if (d0 * d1 < 0.0) folds[nfold++] = al[j * np + p];
+            }
+        }
+        const double fold_window = 2.0 * PI / 180.0;
+
         /* ---- O2 (or O3): segment (j, j+1) owns alpha with lambda in [0, 1) ---- */
         for (int64_t j = 0; j + 1 < nrays; ++j) {
             const double* ra = rec + ((size_t)j * np + p) * OR_NFIELD;
@@ -783,7 +800,10 @@ int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, co
                 if (wi >= 0) wgo = 1.0 - ramp(fabs(wrap_angle(alpha[k] - win[wi].alpha_c)), po_full, po_end);
                 if (wgo == 0.0) continue;
                 double* acc = out + ((size_t)k * np + p) * 4;
-                if (flags & OR_FIELD_EXACT) {
+                int exact = (flags & OR_FIELD_EXACT) != 0;
+                for (int f = 0; f < nfold && !exact; ++f)
+                    if (fabs(wrap_angle(alpha[k] - folds[f])) < fold_window) exact = 1;
+                if (exact) {
                     double b = bj[j] + lam * (bj[j + 1] - bj[j]);
                     double* r = (double*)malloc(sizeof(double) * OR_NFIELD);
                     if (newton_fan(o, p, fan_phi, alpha[k], &b, r) >= 0) {

@@ -68,6 +68,8 @@ enum {
 /* Field flags */
 #define OR_FIELD_PO 1       /* 1-D fan: physical-optics correction around in-plane folds    */
 #define OR_FIELD_EXACT 2    /* evaluate every hit by Newton on the exact trace (O3)         */
+#define OR_FIELD_EXACT_FOLDS 4 /* 1-D fan: O3 only for directions within 2 deg of an in-plane
+                                  fold of the hit's order (rainbow windows), O2 elsewhere    */
 
 typedef struct or_object or_object;
 

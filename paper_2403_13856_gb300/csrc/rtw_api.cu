@@ -289,7 +289,8 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
 {
     if (!obj || !tp || !inout) return fail(RTW_ERR_ARG, "rtw_trace: null pointer");
     if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace: p_max out of [0, 15]");
-    if (tp->precision != RTW_FP64) return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: precision %d", tp->precision);
+    if (tp->precision != RTW_FP64 && tp->precision != RTW_MIXED)
+        return fail(RTW_ERR_ARG, "rtw_trace: precision %d", tp->precision);
     cudaStream_t s = (cudaStream_t)stream;
     const int np = tp->p_max + 1;
     std::vector<ObjDev> objs((size_t)obj->count);
@@ -434,10 +435,15 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
 {
     rtw_rays* rays = const_cast<rtw_rays*>(rays_c);
     if (!rays || !dirs || !field_out) return fail(RTW_ERR_ARG, "rtw_field: null pointer");
-    if (mode != RTW_DENSE) return fail(RTW_ERR_UNSUPPORTED, "rtw_field: mode %d", mode);
+    if (mode != RTW_DENSE && mode != RTW_NEWTON) return fail(RTW_ERR_ARG, "rtw_field: mode %d", mode);
+    if (mode == RTW_NEWTON && rays->grid != RTW_GRID_FAN)
+        return fail(RTW_ERR_UNSUPPORTED, "rtw_field: RTW_NEWTON on square grids");
     cudaStream_t s = (cudaStream_t)stream;
     const bool per_order = (flags & RTW_FIELD_PER_ORDER) != 0;
     const bool po = (flags & RTW_FIELD_PO) != 0;
+    const int newton = mode == RTW_NEWTON ? ((flags & RTW_FIELD_NEAR_FOLDS) ? 2 : 1) : 0;
+    if (po && newton) return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO and RTW_NEWTON exclude each other");
+    const bool folds = po || newton == 2;
     const int nout = per_order ? rays->np : 1;
     long long ndir = 0;
     if (dirs->kind == RTW_DIRS_PLANE) {
@@ -479,9 +485,9 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     size_t off_hit_tri = align_up(off_nbig + 256, 256);
     size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
     size_t off_po = align_up(off_hit_dir + 4 * (size_t)hit_cap + 256, 256);
-    size_t po_bytes = po ? sizeof(double) * ((size_t)rays->np * (size_t)nfan + rtw::kMaxPoWindows + 1 +
-                                             9 * (size_t)ap_cap)
-                         : 0;
+    size_t po_bytes = folds ? sizeof(double) * ((size_t)rays->np * (size_t)nfan + rtw::kMaxPoWindows + 1 +
+                                                9 * (size_t)ap_cap)
+                            : 0;
     size_t total = align_up(off_po + po_bytes, 256);
     if (rays->ws_bytes < total) {
         if (rays->ws) cudaFree(rays->ws);
@@ -529,13 +535,8 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
             RTW_CUDA(rtw::launch_field_grid(a, o.nx, ix0, ix1, iy0, iy1, dirs->n_theta, dirs->n_phi, tab, d_big,
                                             d_nbig, big_cap, d_hit_tri, d_hit_dir, d_nhit, hit_cap, 0, s));
         } else {
-            if (po) {
-                RTW_CUDA(rtw::launch_po_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,
-                                            d_nwin, d_po, ap_cap, s));
-            } else {
-                RTW_CUDA(rtw::launch_field_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha,
-                                               nullptr, nullptr, 0, s));
-            }
+            RTW_CUDA(rtw::launch_field_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,
+                                           d_nwin, d_po, ap_cap, po ? 1 : 0, newton, s));
         }
         if (mask_out) {
             const double axial = 2.0 * o.lambda / o.lmin;

@@ -22,6 +22,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr unsigned int kMaskCaustic = 1u, kMaskAxial = 2u, kMaskPo = 4u;
+constexpr double kFoldNewtonWindow = 2.0 * 3.14159265358979323846 / 180.0;  // 2 deg around a fold
 
 __device__ __forceinline__ double wrap_angle(double a)
 {
@@ -787,10 +788,62 @@ __global__ void __launch_bounds__(256) fan_po_kernel(FieldArgs a, double efx, do
     }
 }
 
+// Newton on the exact double-precision trace (the definition the interpolation approximates):
+// finds the impact parameter b of the fan ray of order p leaving at in-plane angle alpha_t, from
+// the interpolated seed.  The derivative d alpha / d b comes from the transfer matrix carried
+// through the trace: d s = Q' T (e_x, e_y) db in the exit basis (e_perp, e_perp x s).  At most 40
+// steps (quadratic convergence takes 3 to 6), stop at |d alpha| < 1e-13.
+struct CaptureSink {
+    int want;
+    bool got;
+    ExitWave w;
+    __device__ void emit(int p, const ExitWave& ew)
+    {
+        if (p == want) {
+            w = ew;
+            got = true;
+        }
+    }
+};
+
+__device__ bool newton_fan(const ObjDev& o, int p, double efx, double efy, double alpha_t, double b, FarRecord& out)
+{
+    for (int it = 0; it < 40; ++it) {
+        CaptureSink cs;
+        cs.want = p;
+        cs.got = false;
+        trace_ray<double, true>(o, o.c[0] + b * efx, o.c[1] + b * efy, p, cs);
+        if (!cs.got) return false;
+        FarRecord r;
+        if (!far_record(o, cs.w, r)) return false;
+        const double al = atan2(r.s[0] * efx + r.s[1] * efy, r.s[2]);
+        const double da = wrap_angle(alpha_t - al);
+        if (fabs(da) < 1e-13) {
+            out = r;
+            return true;
+        }
+        const ExitWave& w = cs.w;
+        const double J00 = w.q11 * w.t11 + w.q12 * w.t21, J01 = w.q11 * w.t12 + w.q12 * w.t22;
+        const double J10 = w.q12 * w.t11 + w.q22 * w.t21, J11 = w.q12 * w.t12 + w.q22 * w.t22;
+        const double j0 = J00 * efx + J01 * efy, j1 = J10 * efx + J11 * efy;
+        const double v2[3] = {w.ep[1] * w.k[2] - w.ep[2] * w.k[1], w.ep[2] * w.k[0] - w.ep[0] * w.k[2],
+                              w.ep[0] * w.k[1] - w.ep[1] * w.k[0]};
+        double sa, ca;
+        sincos(al, &sa, &ca);
+        const double ea[3] = {ca * efx, ca * efy, -sa};
+        double dadb = 0.0;
+        for (int c = 0; c < 3; ++c) dadb += (j0 * w.ep[c] + j1 * v2[c]) * ea[c];
+        if (dadb == 0.0) return false;
+        b += da / dadb;
+    }
+    return false;
+}
+
 // fan: one thread per (order, segment of neighbouring rays)
 __global__ void __launch_bounds__(256) field_fan_kernel(FieldArgs a, long long nrays, double efx, double efy,
                                                         int ndir, double alpha0, double dalpha,
-                                                        const PoWindow* win, const int* nwin_p)
+                                                        const PoWindow* win, const int* nwin_p, int po,
+                                                        int newton)
 {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nseg = nrays - 1;
@@ -808,8 +861,9 @@ __global__ void __launch_bounds__(256) field_fan_kernel(FieldArgs a, long long n
     if (da == 0.0) return;
     int wi = -1;
     const int nwin = nwin_p ? *nwin_p : 0;
-    for (int w = 0; w < nwin; ++w)
-        if (win[w].ok && win[w].p == p && j >= win[w].jlo && j + 1 <= win[w].jhi) wi = w;
+    if (po)
+        for (int w = 0; w < nwin; ++w)
+            if (win[w].ok && win[w].p == p && j >= win[w].jlo && j + 1 <= win[w].jhi) wi = w;
     const FanScales sc = fan_scales(o);
     const double lo = fmin(al_a, al_a + da), hi = fmax(al_a, al_a + da);
     bool loaded = false;
@@ -842,7 +896,22 @@ __global__ void __launch_bounds__(256) field_fan_kernel(FieldArgs a, long long n
             }
             double F[6];
             for (int c = 0; c < 6; ++c) F[c] = (1.0 - lam) * Fa[c] + lam * Fb[c];
-            const double ps = (1.0 - lam) * pa + lam * pb;
+            double ps = (1.0 - lam) * pa + lam * pb;
+            // Newton on the exact trace: every hit, or the hits within 2 deg of a fold of this order
+            bool exact = newton == 1;
+            if (newton == 2)
+                for (int w = 0; w < nwin && !exact; ++w)
+                    if (win[w].p == p && fabs(wrap_angle(alk - win[w].alpha_c)) < kFoldNewtonWindow) exact = true;
+            if (exact) {
+                const double bj = -o.fan_w + ((double)j + 0.5) * o.h;
+                FarRecord fr;
+                if (newton_fan(o, p, efx, efy, alk, bj + lam * o.h, fr)) {
+                    for (int c = 0; c < 6; ++c) F[c] = fr.F[c];
+                    ps = fr.psi;
+                } else {
+                    atomicOr(a.status, kStatusTimeout);
+                }
+            }
             double d[3], eth[3], eph[3];
             plane_dir(alk, efx, efy, d, eth, eph);
             double* dst = a.out + (k * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? p : 0)) * 4;
@@ -915,53 +984,40 @@ cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, l
     return cudaGetLastError();
 }
 
-cudaError_t launch_fan_windows(const FieldArgs& a, long long nrays, double fan_phi, PoWindow* d_win, int* d_nwin,
-                               cudaStream_t s)
-{
-    (void)a; (void)nrays; (void)fan_phi; (void)d_win; (void)d_nwin; (void)s;
-    return cudaSuccess;
-}
 
-// the fan path: alpha table, folds, windows, aperture fields (when PO), then the segments
+// the fan path: alpha table, folds and windows (when PO or Newton near folds), aperture fields
+// (when PO), the segments, then the PO sums
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
-                             double dalpha, const PoWindow* d_win, const int* d_nwin, int newton, cudaStream_t s)
+                             double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
+                             int newton, cudaStream_t s)
 {
-    (void)newton;
     const long long nseg = (nrays - 1) * (a.pmax + 1);
     if (nseg <= 0) return cudaSuccess;
-    const int bs = 256;
-    field_fan_kernel<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, s>>>(a, nrays, cos(fan_phi), sin(fan_phi), ndir,
-                                                                     alpha0, dalpha, d_win, d_nwin);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_po_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
-                          double dalpha, const PoWindow* d_win_c, const int* d_nwin_c, double2* d_ap,
-                          long long ap_cap, cudaStream_t s)
-{
-    // d_ap is scratch: alpha table (np nrays doubles), window offsets (kMaxPoWindows + 1 long long)
-    // and the aperture samples (9 doubles each, ap_cap of them)
-    PoWindow* d_win = const_cast<PoWindow*>(d_win_c);
-    int* d_nwin = const_cast<int*>(d_nwin_c);
     const double efx = cos(fan_phi), efy = sin(fan_phi);
+    const int bs = 256;
+    const bool folds = po || newton == 2;
     const long long nt = nrays * (a.pmax + 1);
-    double* alpha = reinterpret_cast<double*>(d_ap);
+    double* alpha = reinterpret_cast<double*>(d_scratch);
     long long* offs = reinterpret_cast<long long*>(alpha + nt);
     double* ap = reinterpret_cast<double*>(offs + kMaxPoWindows + 1);
-    const int bs = 256;
-    cudaMemsetAsync(d_nwin, 0, sizeof(int), s);
-    fan_alpha_kernel<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(a, nrays, efx, efy, alpha);
-    fan_fold_kernel<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(a, nrays, alpha, d_win, d_nwin);
-    fan_walk_kernel<<<1, 64, 0, s>>>(a, nrays, alpha, d_win, d_nwin);
-    // window offsets: exclusive prefix of the window sizes (tiny; one thread)
-    window_prefix_kernel<<<1, 1, 0, s>>>(d_win, d_nwin, offs);
-    dim3 g1((unsigned)((nrays + bs - 1) / bs), kMaxPoWindows);
-    fan_aperture_kernel<<<g1, bs, 0, s>>>(a, efx, efy, alpha, nrays, d_win, d_nwin, offs, ap, ap_cap);
-    // segments (GO, weighted by the PO blend inside the windows)
-    field_fan_kernel<<<(unsigned)(((nrays - 1) * (a.pmax + 1) + bs - 1) / bs), bs, 0, s>>>(
-        a, nrays, efx, efy, ndir, alpha0, dalpha, d_win, d_nwin);
-    dim3 g2((unsigned)ndir, kMaxPoWindows);
-    fan_po_kernel<<<g2, 256, 0, s>>>(a, efx, efy, ndir, alpha0, dalpha, d_win, d_nwin, offs, ap, ap_cap);
+    if (folds) {
+        cudaError_t e = cudaMemsetAsync(d_nwin, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        fan_alpha_kernel<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(a, nrays, efx, efy, alpha);
+        fan_fold_kernel<<<(unsigned)((nt + bs - 1) / bs), bs, 0, s>>>(a, nrays, alpha, d_win, d_nwin);
+        fan_walk_kernel<<<1, 64, 0, s>>>(a, nrays, alpha, d_win, d_nwin);
+    }
+    if (po) {
+        window_prefix_kernel<<<1, 1, 0, s>>>(d_win, d_nwin, offs);
+        dim3 g1((unsigned)((nrays + bs - 1) / bs), kMaxPoWindows);
+        fan_aperture_kernel<<<g1, bs, 0, s>>>(a, efx, efy, alpha, nrays, d_win, d_nwin, offs, ap, ap_cap);
+    }
+    field_fan_kernel<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, s>>>(
+        a, nrays, efx, efy, ndir, alpha0, dalpha, folds ? d_win : nullptr, folds ? d_nwin : nullptr, po ? 1 : 0, newton);
+    if (po) {
+        dim3 g2((unsigned)ndir, kMaxPoWindows);
+        fan_po_kernel<<<g2, 256, 0, s>>>(a, efx, efy, ndir, alpha0, dalpha, d_win, d_nwin, offs, ap, ap_cap);
+    }
     return cudaGetLastError();
 }
 

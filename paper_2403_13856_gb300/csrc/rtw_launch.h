@@ -46,12 +46,9 @@ cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, l
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int newton,
                               cudaStream_t s);
-cudaError_t launch_fan_windows(const FieldArgs& a, long long nrays, double fan_phi, PoWindow* d_win,
-                               int* d_nwin, cudaStream_t s);
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
-                             double dalpha, const PoWindow* d_win, const int* d_nwin, int newton, cudaStream_t s);
-cudaError_t launch_po_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0, double dalpha,
-                          const PoWindow* d_win, const int* d_nwin, double2* d_ap, long long ap_cap, cudaStream_t s);
+                             double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
+                             int newton, cudaStream_t s);
 cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, long long ndir, int kind,
                                  int nt, int nph, double alpha0, double dalpha, double axial, cudaStream_t s);
 

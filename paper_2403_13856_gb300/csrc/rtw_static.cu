@@ -185,8 +185,8 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     a.out = static_cast<double*>(field_out);
     a.mask = mask_words;
     a.status = nullptr;
-    if ((e = rtw::launch_field_fan(a, R_, tp->fan_phi, (int)ndir, dirs->alpha0, dirs->dalpha, nullptr, nullptr, 0,
-                                   s)) != cudaSuccess)
+    if ((e = rtw::launch_field_fan(a, R_, tp->fan_phi, (int)ndir, dirs->alpha0, dirs->dalpha, nullptr, nullptr,
+                                   nullptr, 0, 0, 0, s)) != cudaSuccess)
         return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
     if (mask_out) {
         if ((e = rtw::launch_finalize_mask(mask_words, mask_out, ndir, 0, dirs->n_theta, 0, dirs->alpha0,

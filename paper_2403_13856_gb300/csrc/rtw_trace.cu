@@ -95,17 +95,33 @@ __device__ __forceinline__ int find_object(const ObjDev* objs, int nobj, long lo
     return lo;
 }
 
-__global__ void __launch_bounds__(128) trace_kernel_fp64(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
-                                                         int pmax, int aux)
+template <typename T>
+__device__ __forceinline__ void trace_kernel_body(const ObjDev* __restrict__ objs, int nobj, RaysDev st, int pmax,
+                                                  int aux)
 {
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (j >= st.R) return;
     const ObjDev* o = objs + (nobj > 1 ? find_object(objs, nobj, j) : 0);
     StateSink sink{o, st, j, aux != 0, 0u};
     double x, y;
-    if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray_fp64<false>(*o, x, y, pmax, sink);
+    if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray<T, false>(*o, x, y, pmax, sink);
     for (int p = 0; p < st.np; ++p)
         if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
+}
+
+// every step in double precision
+__global__ void __launch_bounds__(128) trace_kernel_fp64(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
+                                                         int pmax, int aux)
+{
+    trace_kernel_body<double>(objs, nobj, st, pmax, aux);
+}
+
+// geometry, Fresnel and curvature in single precision; intersection points (polished by a
+// double-precision Newton step), optical path and phase in double precision
+__global__ void __launch_bounds__(128) trace_kernel_mixed(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
+                                                          int pmax, int aux)
+{
+    trace_kernel_body<float>(objs, nobj, st, pmax, aux);
 }
 
 __global__ void __launch_bounds__(128) trace_points_kernel(const ObjDev* __restrict__ obj, const double* __restrict__ xy,
@@ -158,7 +174,10 @@ cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, b
     if (st.R == 0) return cudaSuccess;
     const int bs = 128;
     const long long nb = (st.R + bs - 1) / bs;
-    trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    if (st.precision == 1)
+        trace_kernel_mixed<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    else
+        trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     return cudaGetLastError();
 }
 

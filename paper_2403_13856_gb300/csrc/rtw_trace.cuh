@@ -114,62 +114,123 @@ __device__ __forceinline__ bool ray_origin(const ObjDev& o, long long local, dou
     return qf < 1.0;
 }
 
-// Traces the incident ray at impact point (x, y) for orders 0..pmax; sink.emit(p, ExitWave) is
-// called for every order that leaves the object.  kJ: also carry the transfer matrix T.
-template <bool kJ, class Sink>
-__device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Sink& sink)
+template <typename T>
+__device__ __forceinline__ void symvT(const T* W, T x, T y, T z, T& ox, T& oy, T& oz)
 {
-    const double* W = o.W;
-    // entry point of the incident ray (plane wave along +z), started below the object
-    double ux = x - o.c[0], uy = y - o.c[1], uz = o.zstart - o.c[2];
-    double wx, wy, wz;
-    symv(W, ux, uy, uz, wx, wy, wz);
-    double A = W[5], B = wz, Cq = ux * wx + uy * wy + uz * wz - 1.0;
-    double disc = B * B - A * Cq;
-    if (!(disc > 0.0)) return;
-    double t = (-B - sqrt(disc)) / A;
-    double r0 = x, r1 = y, r2 = o.zstart + t;
-    // incident wave: k = z, basis (a, b) = (x, -y) so that every basis has a x b = -k
-    double k0v = 0.0, k1v = 0.0, k2v = 1.0;
-    double a0 = 1.0, a1 = 0.0, a2 = 0.0;
-    double q11 = 0.0, q12 = 0.0, q22 = 0.0;
-    double E1r = o.jre[0], E1i = o.jim[0], E2r = -o.jre[1], E2i = -o.jim[1];
-    double T11 = 1.0, T12 = 0.0, T21 = 0.0, T22 = -1.0;
-    int sT = -1;
-    double path = r2;  // phase of the incident plane wave at the first point (zero at the origin)
-    double pdet = 1.0, cosprod = 1.0;
-    int nf = 0;
-    double n_in = 1.0;
-    // reciprocal wave numbers of the two media, once per ray
-    const double ik_host = 1.0 / o.k0, ik_obj = 1.0 / (o.k0 * o.m);
-    for (int q = 1; q <= pmax + 1; ++q) {
-        const double n_out = (q == 1) ? o.m : 1.0;
-        // outward normal n = W (r - c) / |W (r - c)|
+    ox = W[0] * x + W[1] * y + W[2] * z;
+    oy = W[1] * x + W[3] * y + W[4] * z;
+    oz = W[2] * x + W[4] * y + W[5] * z;
+}
+
+// Distance along k from r (double) to the surface: the root t of (r + t k - c)^T W (r + t k - c) = 1
+// given by the quadratic formula in the working precision (sign selects the entry / far root).
+// In single precision the root is then polished by one Newton step evaluated in double precision,
+// so intersection points and optical paths keep double-precision accuracy (the quadric's residual
+// after the step is of the order of the square of the single-precision error).
+template <typename T>
+__device__ __forceinline__ double chord_to_surface(const ObjDev& o, const T* Wt, const double r[3], const T k[3],
+                                                   T sign, bool* ok)
+{
+    const T px = (T)(r[0] - o.c[0]), py = (T)(r[1] - o.c[1]), pz = (T)(r[2] - o.c[2]);
+    T wkx, wky, wkz, wpx, wpy, wpz;
+    symvT(Wt, k[0], k[1], k[2], wkx, wky, wkz);
+    symvT(Wt, px, py, pz, wpx, wpy, wpz);
+    const T Ak = k[0] * wkx + k[1] * wky + k[2] * wkz;
+    const T Bk = k[0] * wpx + k[1] * wpy + k[2] * wpz;
+    const T Ck = px * wpx + py * wpy + pz * wpz - T(1);
+    T dk = Bk * Bk - Ak * Ck;
+    *ok = true;
+    if (sign < T(0)) {
+        if (!(dk > T(0))) {
+            *ok = false;
+            return 0.0;
+        }
+    } else if (dk < T(0)) {
+        dk = T(0);
+    }
+    double d = (double)((-Bk + sign * sqrt(dk)) / Ak);
+    if (sizeof(T) == sizeof(float)) {
+        const double kx = k[0], ky = k[1], kz = k[2];
+        const double ux = r[0] - o.c[0] + d * kx, uy = r[1] - o.c[1] + d * ky, uz = r[2] - o.c[2] + d * kz;
         double gx, gy, gz;
-        symv(W, r0 - o.c[0], r1 - o.c[1], r2 - o.c[2], gx, gy, gz);
-        double inv_gn = rsqrt(gx * gx + gy * gy + gz * gz);
-        double nx = gx * inv_gn, ny = gy * inv_gn, nz = gz * inv_gn;
-        double ci = k0v * nx + k1v * ny + k2v * nz;  // signed cosine of incidence
-        if (fabs(ci) < 1e-9) return;                 // grazing: P' singular
+        symv(o.W, ux, uy, uz, gx, gy, gz);
+        const double f = ux * gx + uy * gy + uz * gz - 1.0;
+        const double fp = 2.0 * (kx * gx + ky * gy + kz * gz);
+        d -= (double)((float)f / (float)fp);
+    }
+    return d;
+}
+
+// A single-precision exit direction is unit only to 6e-8; the far-field phase s.r_exit and the
+// stored direction take it normalised in double precision.
+__device__ __forceinline__ void normalize_exit(ExitWave& w)
+{
+    const double il = rsqrt(w.k[0] * w.k[0] + w.k[1] * w.k[1] + w.k[2] * w.k[2]);
+    w.k[0] *= il;
+    w.k[1] *= il;
+    w.k[2] *= il;
+}
+
+// Traces the incident ray at impact point (x, y) for orders 0..pmax; sink.emit(p, ExitWave) is
+// called for every order that leaves the object.  T is the working precision of directions,
+// bases, curvature, Fresnel and Jones arithmetic; positions and the optical path are double.
+// kJ: also carry the transfer matrix T of transverse offsets.
+template <typename T, bool kJ, class Sink>
+__device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& sink)
+{
+    const T W[6] = {(T)o.W[0], (T)o.W[1], (T)o.W[2], (T)o.W[3], (T)o.W[4], (T)o.W[5]};
+    // entry point of the incident ray (plane wave along +z), started below the object
+    double r[3] = {x, y, o.zstart};
+    T k0v = T(0), k1v = T(0), k2v = T(1);
+    {
+        const T kz[3] = {T(0), T(0), T(1)};
+        bool ok;
+        const double t = chord_to_surface<T>(o, W, r, kz, T(-1), &ok);
+        if (!ok) return;
+        r[2] += t;
+    }
+    // incident wave: k = z, basis (a, b) = (x, -y) so that every basis has a x b = -k
+    T a0 = T(1), a1 = T(0), a2 = T(0);
+    T q11 = T(0), q12 = T(0), q22 = T(0);
+    T E1r = (T)o.jre[0], E1i = (T)o.jim[0], E2r = -(T)o.jre[1], E2i = -(T)o.jim[1];
+    T T11 = T(1), T12 = T(0), T21 = T(0), T22 = T(-1);
+    int sT = -1;
+    double path = r[2];  // phase of the incident plane wave at the first point (zero at the origin)
+    T pdet = T(1), cosprod = T(1);
+    int nf = 0;
+    T n_in = T(1);
+    double n_in_d = 1.0;  // the same index in double precision, for the optical path
+    // reciprocal wave numbers of the two media, once per ray
+    const T k0 = (T)o.k0, mo = (T)o.m;
+    const T ik_host = T(1) / k0, ik_obj = T(1) / (k0 * mo);
+    for (int q = 1; q <= pmax + 1; ++q) {
+        const T n_out = (q == 1) ? mo : T(1);
+        // outward normal n = W (r - c) / |W (r - c)|
+        T gx, gy, gz;
+        symvT(W, (T)(r[0] - o.c[0]), (T)(r[1] - o.c[1]), (T)(r[2] - o.c[2]), gx, gy, gz);
+        const T inv_gn = rsqrt(gx * gx + gy * gy + gz * gz);
+        const T nx = gx * inv_gn, ny = gy * inv_gn, nz = gz * inv_gn;
+        const T ci = k0v * nx + k1v * ny + k2v * nz;  // signed cosine of incidence
+        if (fabs(ci) < T(1e-9)) return;               // grazing: P' singular
         // e_perp = k x n / |k x n| (normal of the incident plane)
-        double ex = k1v * nz - k2v * ny, ey = k2v * nx - k0v * nz, ez = k0v * ny - k1v * nx;
-        double el2 = ex * ex + ey * ey + ez * ez;
-        if (el2 < 1e-24) {
+        T ex = k1v * nz - k2v * ny, ey = k2v * nx - k0v * nz, ez = k0v * ny - k1v * nx;
+        const T el2 = ex * ex + ey * ey + ez * ez;
+        if (el2 < T(1e-24)) {
             ex = a0; ey = a1; ez = a2;
         } else {
-            double il = rsqrt(el2);
+            const T il = rsqrt(el2);
             ex *= il; ey *= il; ez *= il;
         }
         // rotation of the incident basis (a, b = a x k) onto (e_perp, e_perp x k)
-        double b0 = a1 * k2v - a2 * k1v, b1 = a2 * k0v - a0 * k2v, b2 = a0 * k1v - a1 * k0v;
-        double cr = a0 * ex + a1 * ey + a2 * ez, sr = b0 * ex + b1 * ey + b2 * ez;
-        double Ep_r = E1r * cr + E2r * sr, Ep_i = E1i * cr + E2i * sr;
-        double Eq_r = -E1r * sr + E2r * cr, Eq_i = -E1i * sr + E2i * cr;
-        double cc = cr * cr, ss = sr * sr, cs = cr * sr;
-        double Qe11 = cc * q11 + 2.0 * cs * q12 + ss * q22;
-        double Qe12 = -cs * q11 + (cc - ss) * q12 + cs * q22;
-        double Qe22 = ss * q11 - 2.0 * cs * q12 + cc * q22;
-        double Te11 = 0, Te12 = 0, Te21 = 0, Te22 = 0;
+        const T b0 = a1 * k2v - a2 * k1v, b1 = a2 * k0v - a0 * k2v, b2 = a0 * k1v - a1 * k0v;
+        const T cr = a0 * ex + a1 * ey + a2 * ez, sr = b0 * ex + b1 * ey + b2 * ez;
+        const T Ep_r = E1r * cr + E2r * sr, Ep_i = E1i * cr + E2i * sr;
+        const T Eq_r = -E1r * sr + E2r * cr, Eq_i = -E1i * sr + E2i * cr;
+        const T cc = cr * cr, ss = sr * sr, cs = cr * sr;
+        const T Qe11 = cc * q11 + T(2) * cs * q12 + ss * q22;
+        const T Qe12 = -cs * q11 + (cc - ss) * q12 + cs * q22;
+        const T Qe22 = ss * q11 - T(2) * cs * q12 + cc * q22;
+        T Te11 = T(0), Te12 = T(0), Te21 = T(0), Te22 = T(0);
         if (kJ) {
             Te11 = cr * T11 + sr * T21;
             Te12 = cr * T12 + sr * T22;
@@ -177,165 +238,187 @@ __device__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Si
             Te22 = -sr * T12 + cr * T22;
         }
         // surface curvature matrix in (s1, s2) = (e_perp, n x e_perp): C_ab = s_a^T W s_b / |grad|
-        double s2x = ny * ez - nz * ey, s2y = nz * ex - nx * ez, s2z = nx * ey - ny * ex;
-        double wex, wey, wez, wsx, wsy, wsz;
-        symv(W, ex, ey, ez, wex, wey, wez);
-        symv(W, s2x, s2y, s2z, wsx, wsy, wsz);
-        double C11 = (ex * wex + ey * wey + ez * wez) * inv_gn;
-        double C12 = (ex * wsx + ey * wsy + ez * wsz) * inv_gn;
-        double C22 = (s2x * wsx + s2y * wsy + s2z * wsz) * inv_gn;
+        const T s2x = ny * ez - nz * ey, s2y = nz * ex - nx * ez, s2z = nx * ey - ny * ex;
+        T wex, wey, wez, wsx, wsy, wsz;
+        symvT(W, ex, ey, ez, wex, wey, wez);
+        symvT(W, s2x, s2y, s2z, wsx, wsy, wsz);
+        const T C11 = (ex * wex + ey * wey + ez * wez) * inv_gn;
+        const T C12 = (ex * wsx + ey * wsy + ez * wsz) * inv_gn;
+        const T C22 = (s2x * wsx + s2y * wsy + s2z * wsz) * inv_gn;
         // Eq. (SnellVec): common tangential wave vector
-        const double ki = o.k0 * n_in, kt = o.k0 * n_out;
-        const double kin = ki * ci;
-        double tx = ki * k0v - kin * nx, ty = ki * k1v - kin * ny, tz = ki * k2v - kin * nz;
-        double tau2 = tx * tx + ty * ty + tz * tz;
-        double ktn2 = kt * kt - tau2;
-        const double mr = n_out / n_in, mr2 = mr * mr;
+        const T ki = k0 * n_in, kt = k0 * n_out;
+        const T kin = ki * ci;
+        const T tx = ki * k0v - kin * nx, ty = ki * k1v - kin * ny, tz = ki * k2v - kin * nz;
+        const T tau2 = tx * tx + ty * ty + tz * tz;
+        const T ktn2 = kt * kt - tau2;
+        const T mr = n_out / n_in, mr2 = mr * mr;
         // Eq. (Fres)
-        bool tok = ktn2 > 0.0;
-        double ktn = 0.0;
-        double rp_r, rp_i, rq_r, rq_i, tp_r = 0.0, tq_r = 0.0;
-        double inv_ci, inv_ktn = 0.0;
+        const bool tok = ktn2 > T(0);
+        T ktn = T(0);
+        T rp_r, rp_i, rq_r, rq_i, tp_r = T(0), tq_r = T(0);
+        T inv_ci, inv_ktn = T(0);
         if (tok) {
             ktn = copysign(sqrt(ktn2), kin);
             // one reciprocal serves 1/(k_in + k_tn), 1/(m^2 k_in + k_tn), 1/ci and 1/k_tn
-            const double den1 = kin + ktn, den2 = mr2 * kin + ktn;
-            const double aa = den1 * den2, bb = ci * ktn;
-            const double inv = 1.0 / (aa * bb);
-            const double i1 = den2 * bb * inv, i2 = den1 * bb * inv;
+            const T den1 = kin + ktn, den2 = mr2 * kin + ktn;
+            const T aa = den1 * den2, bb = ci * ktn;
+            const T inv = T(1) / (aa * bb);
+            const T i1 = den2 * bb * inv, i2 = den1 * bb * inv;
             inv_ci = aa * ktn * inv;
             inv_ktn = aa * ci * inv;
             rp_r = (kin - ktn) * i1;
             rq_r = (mr2 * kin - ktn) * i2;
-            tp_r = 2.0 * kin * i1;
-            tq_r = 2.0 * mr * kin * i2;
-            rp_i = 0.0;
-            rq_i = 0.0;
+            tp_r = T(2) * kin * i1;
+            tq_r = T(2) * mr * kin * i2;
+            rp_i = T(0);
+            rq_i = T(0);
         } else {
             // total internal reflection: k_tn = i sign(k_in) kappa
-            double kap = copysign(sqrt(-ktn2), kin);
-            double d1 = 1.0 / (kin * kin + kap * kap);
+            const T kap = copysign(sqrt(-ktn2), kin);
+            const T d1 = T(1) / (kin * kin + kap * kap);
             rp_r = (kin * kin - kap * kap) * d1;
-            rp_i = -2.0 * kin * kap * d1;
-            double u = mr2 * kin;
-            double d2 = 1.0 / (u * u + kap * kap);
+            rp_i = T(-2) * kin * kap * d1;
+            const T u = mr2 * kin;
+            const T d2 = T(1) / (u * u + kap * kap);
             rq_r = (u * u - kap * kap) * d2;
-            rq_i = -2.0 * u * kap * d2;
-            inv_ci = 1.0 / ci;
+            rq_i = T(-2) * u * kap * d2;
+            inv_ci = T(1) / ci;
         }
-        const double inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
+        const T inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
         // reflected wave: k_l = tau - k_in n, signed cosine -ci; Eq. (WavefrontEqVec) in the
         // diagonal bases with n.(k_l - k_i) = -2 k_in
-        ExitWave wl;
+        T lk0, lk1, lk2, lq11, lq12, lq22, le1r, le1i, le2r, le2i, lt21 = T(0), lt22 = T(0);
         {
-            wl.k[0] = (tx - kin * nx) * inv_ki;
-            wl.k[1] = (ty - kin * ny) * inv_ki;
-            wl.k[2] = (tz - kin * nz) * inv_ki;
-            double dn = -2.0 * kin;
-            wl.q11 = (ki * Qe11 + C11 * dn) * inv_ki;
-            wl.q12 = (-ki * ci * Qe12 + C12 * dn) * inv_ki * inv_ci;
-            wl.q22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_ki * inv_ci * inv_ci;
-            wl.e1r = rp_r * Ep_r - rp_i * Ep_i;
-            wl.e1i = rp_r * Ep_i + rp_i * Ep_r;
-            wl.e2r = rq_r * Eq_r - rq_i * Eq_i;
-            wl.e2i = rq_r * Eq_i + rq_i * Eq_r;
+            lk0 = (tx - kin * nx) * inv_ki;
+            lk1 = (ty - kin * ny) * inv_ki;
+            lk2 = (tz - kin * nz) * inv_ki;
+            const T dn = T(-2) * kin;
+            lq11 = (ki * Qe11 + C11 * dn) * inv_ki;
+            lq12 = (-ki * ci * Qe12 + C12 * dn) * inv_ki * inv_ci;
+            lq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_ki * inv_ci * inv_ci;
+            le1r = rp_r * Ep_r - rp_i * Ep_i;
+            le1i = rp_r * Ep_i + rp_i * Ep_r;
+            le2r = rq_r * Eq_r - rq_i * Eq_i;
+            le2i = rq_r * Eq_i + rq_i * Eq_r;
             if (kJ) {
-                wl.t11 = Te11; wl.t12 = Te12; wl.t21 = -Te21; wl.t22 = -Te22;
+                lt21 = -Te21;
+                lt22 = -Te22;
             }
         }
-        ExitWave wt;
-        double ct = 0.0;
+        T tk0 = T(0), tk1 = T(0), tk2 = T(0), tq11 = T(0), tq12 = T(0), tq22 = T(0);
+        T te1r = T(0), te1i = T(0), te2r = T(0), te2i = T(0), tt21 = T(0), tt22 = T(0);
+        T ct = T(0);
         if (tok) {
-            wt.k[0] = (tx + ktn * nx) * inv_kt;
-            wt.k[1] = (ty + ktn * ny) * inv_kt;
-            wt.k[2] = (tz + ktn * nz) * inv_kt;
+            tk0 = (tx + ktn * nx) * inv_kt;
+            tk1 = (ty + ktn * ny) * inv_kt;
+            tk2 = (tz + ktn * nz) * inv_kt;
             ct = ktn * inv_kt;  // signed cosine of the transmitted wave
-            double dn = ktn - kin;
-            double inv_ct = kt * inv_ktn;
-            wt.q11 = (ki * Qe11 + C11 * dn) * inv_kt;
-            wt.q12 = -(-ki * ci * Qe12 + C12 * dn) * inv_kt * inv_ct;
-            wt.q22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
-            wt.e1r = tp_r * Ep_r;
-            wt.e1i = tp_r * Ep_i;
-            wt.e2r = tq_r * Eq_r;
-            wt.e2i = tq_r * Eq_i;
+            const T dn = ktn - kin;
+            const T inv_ct = kt * inv_ktn;
+            tq11 = (ki * Qe11 + C11 * dn) * inv_kt;
+            tq12 = -(-ki * ci * Qe12 + C12 * dn) * inv_kt * inv_ct;
+            tq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
+            te1r = tp_r * Ep_r;
+            te1i = tp_r * Ep_i;
+            te2r = tq_r * Eq_r;
+            te2i = tq_r * Eq_i;
             if (kJ) {
-                double f = ct / ci;
-                wt.t11 = Te11; wt.t12 = Te12; wt.t21 = f * Te21; wt.t22 = f * Te22;
+                const T f = ct * inv_ci;
+                tt21 = f * Te21;
+                tt22 = f * Te22;
             }
         }
-        const double cos_ratio = tok ? fabs(ct / ci) : 0.0;
+        const T cos_ratio = tok ? fabs(ct * inv_ci) : T(0);
+        ExitWave w;
         if (q == 1) {
             // order 0: external reflection (Eq. epsilon_VCRM, p = 0)
-            wl.ep[0] = ex; wl.ep[1] = ey; wl.ep[2] = ez;
-            wl.pdet = 1.0;
-            wl.cosprod = 1.0;
-            wl.path = path;
-            wl.r[0] = r0; wl.r[1] = r1; wl.r[2] = r2;
-            wl.nf_legs = 0;
-            wl.sT = -sT;
-            sink.emit(0, wl);
+            w.k[0] = lk0; w.k[1] = lk1; w.k[2] = lk2;
+            w.q11 = lq11; w.q12 = lq12; w.q22 = lq22;
+            w.e1r = le1r; w.e1i = le1i; w.e2r = le2r; w.e2i = le2i;
+            if (kJ) { w.t11 = Te11; w.t12 = Te12; w.t21 = lt21; w.t22 = lt22; }
+            w.ep[0] = ex; w.ep[1] = ey; w.ep[2] = ez;
+            w.pdet = 1.0;
+            w.cosprod = 1.0;
+            w.path = path;
+            w.r[0] = r[0]; w.r[1] = r[1]; w.r[2] = r[2];
+            w.nf_legs = 0;
+            w.sT = -sT;
+            if (sizeof(T) == sizeof(float)) normalize_exit(w);
+            sink.emit(0, w);
             if (!tok) return;
-            k0v = wt.k[0]; k1v = wt.k[1]; k2v = wt.k[2];
-            q11 = wt.q11; q12 = wt.q12; q22 = wt.q22;
-            E1r = wt.e1r; E1i = wt.e1i; E2r = wt.e2r; E2i = wt.e2i;
-            if (kJ) { T11 = wt.t11; T12 = wt.t12; T21 = wt.t21; T22 = wt.t22; }
+            k0v = tk0; k1v = tk1; k2v = tk2;
+            q11 = tq11; q12 = tq12; q22 = tq22;
+            E1r = te1r; E1i = te1i; E2r = te2r; E2i = te2i;
+            if (kJ) { T11 = Te11; T12 = Te12; T21 = tt21; T22 = tt22; }
             cosprod *= cos_ratio;
+            n_in = n_out;  // the transmitted wave continues inside
+            n_in_d = o.m;
         } else {
             // order q-1 leaves by refraction; the reflected wave stays inside
             if (tok) {
-                wt.ep[0] = ex; wt.ep[1] = ey; wt.ep[2] = ez;
-                wt.pdet = pdet;
-                wt.cosprod = cosprod * cos_ratio;
-                wt.path = path;
-                wt.r[0] = r0; wt.r[1] = r1; wt.r[2] = r2;
-                wt.nf_legs = nf;
-                wt.sT = sT;
-                sink.emit(q - 1, wt);
+                w.k[0] = tk0; w.k[1] = tk1; w.k[2] = tk2;
+                w.q11 = tq11; w.q12 = tq12; w.q22 = tq22;
+                w.e1r = te1r; w.e1i = te1i; w.e2r = te2r; w.e2i = te2i;
+                if (kJ) { w.t11 = Te11; w.t12 = Te12; w.t21 = tt21; w.t22 = tt22; }
+                w.ep[0] = ex; w.ep[1] = ey; w.ep[2] = ez;
+                w.pdet = pdet;
+                w.cosprod = cosprod * cos_ratio;
+                w.path = path;
+                w.r[0] = r[0]; w.r[1] = r[1]; w.r[2] = r[2];
+                w.nf_legs = nf;
+                w.sT = sT;
+                if (sizeof(T) == sizeof(float)) normalize_exit(w);
+                sink.emit(q - 1, w);
             }
-            k0v = wl.k[0]; k1v = wl.k[1]; k2v = wl.k[2];
-            q11 = wl.q11; q12 = wl.q12; q22 = wl.q22;
-            E1r = wl.e1r; E1i = wl.e1i; E2r = wl.e2r; E2i = wl.e2i;
-            if (kJ) { T11 = wl.t11; T12 = wl.t12; T21 = wl.t21; T22 = wl.t22; }
+            k0v = lk0; k1v = lk1; k2v = lk2;
+            q11 = lq11; q12 = lq12; q22 = lq22;
+            E1r = le1r; E1i = le1i; E2r = le2r; E2i = le2i;
+            if (kJ) { T11 = Te11; T12 = Te12; T21 = lt21; T22 = lt22; }
             sT = -sT;
         }
         a0 = ex; a1 = ey; a2 = ez;
-        if (q == 1) n_in = n_out;  // the transmitted wave continues inside
         if (q == pmax + 1) break;
         // chord to the next surface point along the inward direction
-        double px = r0 - o.c[0], py = r1 - o.c[1], pz = r2 - o.c[2];
-        double wkx, wky, wkz, wpx, wpy, wpz;
-        symv(W, k0v, k1v, k2v, wkx, wky, wkz);
-        symv(W, px, py, pz, wpx, wpy, wpz);
-        double Ak = k0v * wkx + k1v * wky + k2v * wkz;
-        double Bk = k0v * wpx + k1v * wpy + k2v * wpz;
-        double Ck = px * wpx + py * wpy + pz * wpz - 1.0;
-        double dk = Bk * Bk - Ak * Ck;
-        if (dk < 0.0) dk = 0.0;
-        double d = (-Bk + sqrt(dk)) / Ak;
-        if (!(d > 0.0)) return;
+        bool ok;
+        const T kk[3] = {k0v, k1v, k2v};
+        const double dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok);
+        if (!(dd > 0.0)) return;
+        const T d = (T)dd;
         // free propagation: Q(d) = Q (I + d Q)^{-1} = (Q + d det Q I) / det(I + d Q)
-        double A11 = 1.0 + d * q11, A22 = 1.0 + d * q22, A12 = d * q12;
-        double detA = A11 * A22 - A12 * A12;
-        if (detA == 0.0) return;
-        double idet = 1.0 / detA;
-        double dq = q11 * q22 - q12 * q12;
+        const T A11 = T(1) + d * q11, A22 = T(1) + d * q22, A12 = d * q12;
+        const T detA = A11 * A22 - A12 * A12;
+        if (detA == T(0)) return;
+        const T idet = T(1) / detA;
+        const T dq = q11 * q22 - q12 * q12;
         q11 = (q11 + d * dq) * idet;
         q12 = q12 * idet;
         q22 = (q22 + d * dq) * idet;
         pdet *= fabs(detA);
-        nf += neg_eigs_sym(A11, A12, A22);
-        if (detA < 0.0) sT = -sT;
+        nf += neg_eigs_sym((double)A11, (double)A12, (double)A22);
+        if (detA < T(0)) sT = -sT;
         if (kJ) {
-            double n11 = A11 * T11 + A12 * T21, n12 = A11 * T12 + A12 * T22;
-            double n21 = A12 * T11 + A22 * T21, n22 = A12 * T12 + A22 * T22;
+            const T n11 = A11 * T11 + A12 * T21, n12 = A11 * T12 + A12 * T22;
+            const T n21 = A12 * T11 + A22 * T21, n22 = A12 * T12 + A22 * T22;
             T11 = n11; T12 = n12; T21 = n21; T22 = n22;
         }
-        path += n_in * d;
-        r0 += d * k0v;
-        r1 += d * k1v;
-        r2 += d * k2v;
+        // dd is the parameter along k; in single precision |k| = 1 only to 6e-8, so the optical
+        // path takes the segment's true length dd |k|, evaluated in double precision
+        double seg = dd;
+        if (sizeof(T) == sizeof(float)) {
+            const double kx = k0v, ky = k1v, kz = k2v;
+            seg = dd * sqrt(kx * kx + ky * ky + kz * kz);
+        }
+        path += n_in_d * seg;
+        r[0] += dd * (double)k0v;
+        r[1] += dd * (double)k1v;
+        r[2] += dd * (double)k2v;
     }
+}
+
+template <bool kJ, class Sink>
+__device__ __forceinline__ void trace_ray_fp64(const ObjDev& o, double x, double y, int pmax, Sink& sink)
+{
+    trace_ray<double, kJ>(o, x, y, pmax, sink);
 }
 
 }  // namespace rtw

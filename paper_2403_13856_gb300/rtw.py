@@ -20,7 +20,7 @@ RTW_GRID_FAN, RTW_GRID_SQUARE = 0, 1
 RTW_FP64, RTW_MIXED = 0, 1
 RTW_DENSE, RTW_NEWTON = 0, 1
 RTW_DIRS_PLANE, RTW_DIRS_GRID = 0, 1
-RTW_FIELD_PER_ORDER, RTW_FIELD_PO = 1, 2
+RTW_FIELD_PER_ORDER, RTW_FIELD_PO, RTW_FIELD_NEAR_FOLDS = 1, 2, 4
 RTW_TRACE_APERTURE = 1
 RTW_MASK_CAUSTIC, RTW_MASK_AXIAL, RTW_MASK_PO = 1, 2, 4
 FLAG_VALID, FLAG_ORIENT, FLAG_CAUSTIC = 1, 2, 4
