@@ -187,6 +187,58 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
               uint8_t* mask_out, void* stream);
 
+/* ---- many objects in one launch sequence ---- */
+
+/* Options of rtw_far_field_batch.  n_rays (host, one entry per object, read during the call) is
+ * each object's target ray count inside its projected cross-section, as rtw_trace_params.n_rays
+ * for a square grid.  chunk_ray_orders bounds the ray state held at once, counted in
+ * (ray, order) pairs over the objects of a chunk (0: 2^29, about 62 GB); an object larger than
+ * the bound is a chunk of its own.  trace_variant (0: 2) selects the persistent trace kernel's
+ * block size and register cap, 1..5 = (64 threads), (128), (256), (128, 3 CTAs per SM),
+ * (256, 2 CTAs per SM); trace_ctas_per_sm (0: as many as fit) its resident CTAs per SM;
+ * classify_block (0: 256; 64, 128 or 256) the block size of the grid classification kernel.
+ * use_graph = 1 records the whole launch sequence in a CUDA graph on the first call and replays
+ * it on later calls whose objects, options, directions and output pointers are the same.
+ * timing = 1 records CUDA events around the trace and the field of every chunk (eager runs only,
+ * read with rtw_batch_times). */
+typedef struct {
+    int p_max;
+    int precision;
+    const int64_t* n_rays;
+    int64_t chunk_ray_orders;
+    int trace_variant;
+    int trace_ctas_per_sm;
+    int classify_block;
+    int use_graph;
+    int timing;
+} rtw_batch_params;
+
+typedef struct rtw_batch rtw_batch;
+
+/* The far field of every object of obj (its own wave, square ray grid) on the same (theta, phi)
+ * direction grid: rtw_trace + rtw_field of the square-grid path, object by object, in one
+ * sequence of launches.  Objects are split into chunks of at most chunk_ray_orders ray state;
+ * each chunk is traced by one persistent kernel that takes work items (object, 256 consecutive
+ * rays) from a counter, then its field is accumulated in launch groups of objects.
+ * dirs: kind RTW_DIRS_GRID, cell_window all -1.  flags: 0 or RTW_FIELD_PER_ORDER.
+ * field_out (device): [objects][directions][orders or 1][2] complex128, zeroed and written;
+ * mask_out (device, optional): [objects][directions] uint8.  *inout: NULL on the first call (a
+ * handle owning the ray-state block, the workspace and the graph is created) or a handle from an
+ * earlier call (reused, grown when needed).  Argument errors return before any work; errors of
+ * kernels are read by rtw_sync_status.  Asynchronous on `stream`. */
+int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const rtw_dirs* dirs, int flags,
+                        void* field_out, uint8_t* mask_out, rtw_batch** inout, void* stream);
+
+/* Sizes of the last call: rays over all objects (square grids count misses), chunks, and 1 when
+ * the call replayed a recorded graph. */
+int rtw_batch_info(const rtw_batch* b, int64_t* total_rays, int* n_chunks, int* replayed);
+
+/* Trace and field times (ms, summed over chunks) of the last call made with timing = 1;
+ * synchronises with its events. */
+int rtw_batch_times(const rtw_batch* b, double* trace_ms, double* field_ms);
+
+void rtw_destroy_batch(rtw_batch* b);
+
 /* ---- the fan path without allocation ----
  * The paper has no counterpart of this call: it serves programs that may not allocate device
  * memory themselves (a host application whose memory manager owns the device and forbids direct

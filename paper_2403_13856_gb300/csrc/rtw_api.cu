@@ -16,17 +16,30 @@
 #include <vector>
 
 #include "rtw.h"
+#include "rtw_host.h"
 #include "rtw_launch.h"
 
 using rtw::ObjDev;
 using rtw::RaysDev;
+using rtw::host::align_up;
+using rtw::host::cuda_fail;
+using rtw::host::fail;
+using rtw::host::ObjHost;
+using rtw::host::status_word;
 
 namespace {
-
 constexpr double kPi = 3.14159265358979323846;
 thread_local std::string g_last_error;
+std::mutex g_status_mu;
+std::vector<unsigned int*> g_status;
+}  // namespace
 
-int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+namespace rtw {
+
+void set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace host {
+
 int fail(int code, const char* fmt, ...)
 {
     char buf[512];
@@ -38,32 +51,7 @@ int fail(int code, const char* fmt, ...)
     return code;
 }
 
-int cuda_fail(cudaError_t e, const char* what)
-{
-    return fail(RTW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-#define RTW_CUDA(call)                                         \
-    do {                                                       \
-        cudaError_t e_ = (call);                               \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
-    } while (0)
-
-struct ObjHost {
-    double a[3];
-    double R[3][3];
-    double c[3];
-    double m;
-    double lambda;
-    double jre[2], jim[2];
-    double W[3][3];
-    double S[2][2], Sinv[2][2];
-    double lmin, lmax;
-};
-
-// per-device status word of the library (error bits raised by kernels)
-std::mutex g_status_mu;
-std::vector<unsigned int*> g_status;
+int cuda_fail(cudaError_t e, const char* what) { return fail(RTW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e)); }
 
 unsigned int* status_word(int dev)
 {
@@ -77,39 +65,6 @@ unsigned int* status_word(int dev)
     }
     return g_status[dev];
 }
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-}  // namespace
-
-void rtw::set_last_error(const char* msg) { g_last_error = msg; }
-
-struct rtw_object {
-    int count = 0;
-    int device = 0;
-    std::vector<ObjHost> h;
-};
-
-struct rtw_rays {
-    int device = 0;
-    int np = 0;
-    int precision = 0;
-    int grid = 0;
-    int flags = 0;
-    int nobj = 0;
-    long long R = 0;
-    double fan_phi = 0.0;
-    std::vector<ObjDev> objs;
-    ObjDev* d_objs = nullptr;
-    size_t d_objs_cap = 0;
-    RaysDev st{};
-    void* block = nullptr;
-    size_t block_bytes = 0;
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-};
-
-namespace {
 
 void fill_objdev(const ObjHost& o, ObjDev& d)
 {
@@ -166,6 +121,137 @@ int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* 
     *fan_w = 0.0;
     return RTW_OK;
 }
+
+
+GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs)
+{
+    GridPlan g;
+    const int64_t* win = dirs->cell_window;
+    g.windowed = !(win[0] == -1 && win[1] == -1 && win[2] == -1 && win[3] == -1);
+    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    g.group = (int)std::max<long long>(1, std::min<long long>(nobj, (1ll << 28) / std::max(1ll, 4 * ndir * np)));
+    for (int g0 = 0; g0 < nobj; g0 += g.group) {
+        long long cells = 0;
+        for (int oi = g0; oi < std::min(nobj, g0 + g.group); ++oi) {
+            const ObjDev& o = objs[oi];
+            long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
+            if (g.windowed) {
+                ix0 = win[0] < 0 ? 0 : win[0];
+                ix1 = win[1] > o.nx - 1 ? o.nx - 1 : win[1];
+                iy0 = win[2] < 0 ? 0 : win[2];
+                iy1 = win[3] > o.ny - 1 ? o.ny - 1 : win[3];
+            }
+            cells += std::max(0ll, ix1 - ix0) * std::max(0ll, iy1 - iy0) * np;
+        }
+        g.max_group_cells = std::max(g.max_group_cells, cells);
+    }
+    return g;
+}
+
+size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, GridWs* w)
+{
+    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    // list of large triangles: 1/32 of a group's triangles, at least 65536
+    const unsigned int big_cap =
+        (unsigned int)std::min<long long>(std::max<long long>(65536, 2 * g.max_group_cells / 32), 1ll << 26);
+    const unsigned int hit_cap = (unsigned int)std::min<long long>(4 * ndir * np * g.group + (1 << 20), 1ll << 29);
+    size_t off_mask = 0;
+    size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir * (size_t)g.group, 256);
+    // double tables then their single-precision copies
+    size_t off_cells = align_up(off_tab + sizeof(double) * 3 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi), 256);
+    size_t off_big = align_up(off_cells + sizeof(GridCells) * (size_t)g.group, 256);
+    size_t off_cnt = align_up(off_big + 8 * (size_t)big_cap, 256);
+    size_t off_hit_tri = align_up(off_cnt + 256, 256);
+    size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
+    size_t total = align_up(off_hit_dir + 4 * (size_t)hit_cap, 256);
+    if (base && w) {
+        w->mask_words = (unsigned int*)(base + off_mask);
+        w->tab = (double*)(base + off_tab);
+        w->cells = (GridCells*)(base + off_cells);
+        w->big = (unsigned long long*)(base + off_big);
+        w->nbig = (unsigned int*)(base + off_cnt);
+        w->nhit = w->nbig + 1;
+        w->hit_tri = (unsigned long long*)(base + off_hit_tri);
+        w->hit_dir = (unsigned int*)(base + off_hit_dir);
+        w->big_cap = big_cap;
+        w->hit_cap = hit_cap;
+    }
+    return total;
+}
+
+int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
+                   const rtw_dirs* dirs, bool per_order, double* out, unsigned char* mask_out, const GridWs& w,
+                   int classify_block, unsigned int* status, cudaStream_t s)
+{
+    const int np = st.np;
+    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    const int nout = per_order ? np : 1;
+    const size_t out_obj = 4 * (size_t)nout * (size_t)ndir;  // doubles per object
+    const int64_t* win = dirs->cell_window;
+    for (int g0 = 0; g0 < nobj; g0 += g.group) {
+        const int gn = std::min(g.group, nobj - g0);
+        RTW_CUDA(cudaMemsetAsync(w.mask_words, 0, sizeof(unsigned int) * (size_t)ndir * (size_t)gn, s));
+        FieldArgs a;
+        a.d_obj = d_objs + g0;
+        a.st = st;
+        a.pmax = np - 1;
+        a.per_order = per_order ? 1 : 0;
+        a.out = out + out_obj * (size_t)g0;
+        a.mask = w.mask_words;
+        a.status = status;
+        RTW_CUDA(launch_grid_cells(d_objs + g0, gn, np, g.windowed, win, w.cells, s));
+        GridBatch b;
+        b.cells = w.cells;
+        b.nobj = gn;
+        b.total = 0;
+        for (int oi = g0; oi < g0 + gn; ++oi) {
+            const ObjDev& o = h_objs[oi];
+            long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
+            if (g.windowed) {
+                ix0 = win[0] < 0 ? 0 : win[0];
+                ix1 = win[1] > o.nx - 1 ? o.nx - 1 : win[1];
+                iy0 = win[2] < 0 ? 0 : win[2];
+                iy1 = win[3] > o.ny - 1 ? o.ny - 1 : win[3];
+            }
+            b.total += std::max(0ll, ix1 - ix0) * std::max(0ll, iy1 - iy0) * np;
+        }
+        b.ndir = ndir;
+        b.nout = nout;
+        RTW_CUDA(launch_field_grid(a, b, dirs->n_theta, dirs->n_phi, w.tab, w.big, w.nbig, w.big_cap, w.hit_tri,
+                                   w.hit_dir, w.nhit, w.hit_cap, classify_block, s));
+        if (mask_out)
+            RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir, 1,
+                                          dirs->n_theta, dirs->n_phi, 0.0, 0.0, s));
+    }
+    return RTW_OK;
+}
+
+}  // namespace host
+}  // namespace rtw
+
+struct rtw_rays {
+    int device = 0;
+    int np = 0;
+    int precision = 0;
+    int grid = 0;
+    int flags = 0;
+    int nobj = 0;
+    long long R = 0;
+    double fan_phi = 0.0;
+    std::vector<ObjDev> objs;
+    ObjDev* d_objs = nullptr;
+    size_t d_objs_cap = 0;
+    RaysDev st{};
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace {
+
+using rtw::host::fill_objdev;
+using rtw::host::grid_of;
 
 int ensure_device(int* dev)
 {
@@ -461,30 +547,32 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     }
     if (po && (rays->grid != RTW_GRID_FAN || !rays->st.aux))
         return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO needs a fan traced with RTW_TRACE_APERTURE");
-    // workspace: mask words, direction tables, PO windows and scratch
-    const long long nfan = rays->grid == RTW_GRID_FAN ? rays->objs[0].nx : 0;
+    unsigned int* status = status_word(rays->device);
+    if (dirs->kind == RTW_DIRS_GRID) {
+        const rtw::host::GridPlan g = rtw::host::plan_grid(rays->objs.data(), rays->nobj, rays->np, dirs);
+        const size_t total = rtw::host::grid_ws(g, rays->np, dirs, nullptr, nullptr);
+        if (rays->ws_bytes < total) {
+            if (rays->ws) cudaFree(rays->ws);
+            rays->ws = nullptr;
+            rays->ws_bytes = 0;
+            cudaError_t e = cudaMalloc(&rays->ws, total);
+            if (e != cudaSuccess) return fail(RTW_ERR_NOMEM, "rtw_field: workspace of %zu bytes", total);
+            rays->ws_bytes = total;
+        }
+        rtw::host::GridWs w;
+        rtw::host::grid_ws(g, rays->np, dirs, (char*)rays->ws, &w);
+        RTW_CUDA(cudaMemsetAsync(field_out, 0, sizeof(double) * 4 * (size_t)nout * (size_t)ndir * (size_t)rays->nobj, s));
+        RTW_CUDA(rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, w.tab, s));
+        return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, per_order,
+                                         (double*)field_out, mask_out, w, 0, status, s);
+    }
+    // fan: workspace of mask words, PO windows and scratch
+    const long long nfan = rays->objs[0].nx;
     const long long ap_cap = po ? 2 * (long long)rays->np * nfan : 0;
     size_t off_mask = 0;
-    size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir, 256);
-    // double tables then their single-precision copies
-    size_t ntab = dirs->kind == RTW_DIRS_GRID ? 3 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi) : 0;
-    size_t off_win = align_up(off_tab + sizeof(double) * ntab, 256);
+    size_t off_win = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir, 256);
     size_t off_nwin = align_up(off_win + sizeof(rtw::PoWindow) * rtw::kMaxPoWindows, 256);
-    // list of large triangles of the square-grid field (1/32 of all triangles, at least 65536)
-    long long ntri = 0;
-    if (dirs->kind == RTW_DIRS_GRID)
-        for (const ObjDev& o : rays->objs) ntri = std::max(ntri, 2 * (o.nx - 1) * (o.ny - 1) * rays->np);
-    const unsigned int big_cap = (unsigned int)std::min<long long>(std::max<long long>(65536, ntri / 32), 1ll << 26);
-    size_t off_big = align_up(off_nwin + 256, 256);
-    size_t off_nbig = align_up(off_big + (dirs->kind == RTW_DIRS_GRID ? 8 * (size_t)big_cap : 0), 256);
-    // (triangle, direction) pairs handed to the double-precision phase: 4 per direction and order
-    const unsigned int hit_cap =
-        dirs->kind == RTW_DIRS_GRID
-            ? (unsigned int)std::min<long long>(4 * ndir * (long long)rays->np + (1 << 20), 0x7fffffffll)
-            : 0;
-    size_t off_hit_tri = align_up(off_nbig + 256, 256);
-    size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
-    size_t off_po = align_up(off_hit_dir + 4 * (size_t)hit_cap + 256, 256);
+    size_t off_po = align_up(off_nwin + 256, 256);
     size_t po_bytes = folds ? sizeof(double) * ((size_t)rays->np * (size_t)nfan + rtw::kMaxPoWindows + 1 +
                                                 9 * (size_t)ap_cap)
                             : 0;
@@ -499,21 +587,12 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     }
     char* ws = (char*)rays->ws;
     unsigned int* mask_words = (unsigned int*)(ws + off_mask);
-    double* tab = (double*)(ws + off_tab);
     rtw::PoWindow* d_win = (rtw::PoWindow*)(ws + off_win);
     int* d_nwin = (int*)(ws + off_nwin);
     double2* d_po = (double2*)(ws + off_po);
-    unsigned long long* d_big = (unsigned long long*)(ws + off_big);
-    unsigned int* d_nbig = (unsigned int*)(ws + off_nbig);
-    unsigned int* d_nhit = d_nbig + 1;
-    unsigned long long* d_hit_tri = (unsigned long long*)(ws + off_hit_tri);
-    unsigned int* d_hit_dir = (unsigned int*)(ws + off_hit_dir);
-    unsigned int* status = status_word(rays->device);
     const size_t out_bytes_obj = sizeof(double) * 4 * (size_t)nout * (size_t)ndir;
     RTW_CUDA(cudaMemsetAsync(field_out, 0, out_bytes_obj * (size_t)rays->nobj, s));
-    if (dirs->kind == RTW_DIRS_GRID) RTW_CUDA(rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, tab, s));
     for (int oi = 0; oi < rays->nobj; ++oi) {
-        const ObjDev& o = rays->objs[(size_t)oi];
         RTW_CUDA(cudaMemsetAsync(mask_words, 0, sizeof(unsigned int) * (size_t)ndir, s));
         rtw::FieldArgs a;
         a.d_obj = rays->d_objs + oi;
@@ -523,27 +602,12 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         a.out = (double*)((char*)field_out + out_bytes_obj * (size_t)oi);
         a.mask = mask_words;
         a.status = status;
-        if (dirs->kind == RTW_DIRS_GRID) {
-            long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
-            const int64_t* w = dirs->cell_window;
-            if (!(w[0] == -1 && w[1] == -1 && w[2] == -1 && w[3] == -1)) {
-                ix0 = w[0] < 0 ? 0 : w[0];
-                ix1 = w[1] > o.nx - 1 ? o.nx - 1 : w[1];
-                iy0 = w[2] < 0 ? 0 : w[2];
-                iy1 = w[3] > o.ny - 1 ? o.ny - 1 : w[3];
-            }
-            RTW_CUDA(rtw::launch_field_grid(a, o.nx, ix0, ix1, iy0, iy1, dirs->n_theta, dirs->n_phi, tab, d_big,
-                                            d_nbig, big_cap, d_hit_tri, d_hit_dir, d_nhit, hit_cap, 0, s));
-        } else {
-            RTW_CUDA(rtw::launch_field_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,
-                                           d_nwin, d_po, ap_cap, po ? 1 : 0, newton, s));
-        }
-        if (mask_out) {
-            const double axial = 2.0 * o.lambda / o.lmin;
-            RTW_CUDA(rtw::launch_finalize_mask(mask_words, mask_out + (size_t)oi * (size_t)ndir, ndir,
-                                               dirs->kind == RTW_DIRS_PLANE ? 0 : 1, dirs->n_theta, dirs->n_phi,
-                                               dirs->alpha0, dirs->dalpha, axial, s));
-        }
+        const ObjDev& o = rays->objs[(size_t)oi];
+        RTW_CUDA(rtw::launch_field_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,
+                                       d_nwin, d_po, ap_cap, po ? 1 : 0, newton, s));
+        if (mask_out)
+            RTW_CUDA(rtw::launch_finalize_mask(mask_words, mask_out + (size_t)oi * (size_t)ndir, rays->d_objs + oi, 1,
+                                               ndir, 0, dirs->n_theta, 0, dirs->alpha0, dirs->dalpha, s));
     }
     return RTW_OK;
 }

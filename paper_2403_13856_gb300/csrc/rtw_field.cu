@@ -311,8 +311,8 @@ __device__ __forceinline__ void push_hit(const HitArgs& h, unsigned int* status,
 }
 
 __device__ __forceinline__ void candidate(const FieldArgs& a, const HitArgs& h, const TriFrame& fr,
-                                          unsigned long long code, int it, int jp, int nph, float dx0, float dx1,
-                                          float dx2)
+                                          unsigned long long code, unsigned int* mask, int it, int jp, int nph,
+                                          float dx0, float dx1, float dx2)
 {
     const int cls = tri_classify(fr, dx0, dx1, dx2);
     if (cls == 0) return;
@@ -320,10 +320,35 @@ __device__ __forceinline__ void candidate(const FieldArgs& a, const HitArgs& h, 
     if (cls == 2) {
         push_hit(h, a.status, code, dk | kHitClose);
     } else if (!fr.ok) {  // singular or folded cell: mark, add nothing
-        if (!(a.mask[dk] & kMaskCaustic)) atomicOr(a.mask + dk, kMaskCaustic);
+        if (!(mask[dk] & kMaskCaustic)) atomicOr(mask + dk, kMaskCaustic);
     } else {
         push_hit(h, a.status, code, dk);
     }
+}
+
+// The cells of one launch: objects [obj0, obj0 + nobj) of the table, each with its cell window
+// and the first thread index of its (order, cell) range.
+__device__ __forceinline__ CellRef decode_cell(const FieldArgs& a, const GridBatch& b, long long t)
+{
+    int lo = 0, hi = b.nobj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.cells[mid].first <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const GridCells& gc = b.cells[lo];
+    CellRef r;
+    r.orel = lo;
+    r.o = a.d_obj + lo;
+    const long long ncell = gc.ncx * gc.ncy;
+    const long long local = t - gc.first;
+    r.p = (int)(local / ncell);
+    const long long cell = local - (long long)r.p * ncell;
+    r.cx = gc.ix0 + cell % gc.ncx;
+    r.cy = gc.iy0 + cell / gc.ncx;
+    r.nx = r.o->nx;
+    r.base = (long long)r.p * a.st.R + r.o->ray_offset;
+    return r;
 }
 
 // corners of triangle t (0: c00 c10 c11, 1: c00 c11 c01) of cell (cx, cy)
@@ -348,26 +373,21 @@ __device__ __forceinline__ DirTabF dir_tab_f(const double* tab, int nt, int nph)
     return DirTabF{f, f + nt, f + 2 * nt, f + 2 * nt + nph};
 }
 
-// Phase 1: one thread per (order, cell).  Triangles with few candidates are tested here; larger
-// ones go to the big list (one warp each in phase 2).
-__global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, long long nx, long long ix0, long long ncx,
-                                                         long long iy0, long long ncy, int nt, int nph,
+// Phase 1: one thread per (object, order, cell).  Triangles with few candidates are tested here;
+// larger ones go to the big list (one warp each in phase 2).
+__global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch b, int nt, int nph,
                                                          const double* __restrict__ tab, unsigned long long* big,
                                                          unsigned int* nbig, unsigned int big_cap, HitArgs h)
 {
-    const ObjDev& o = *a.d_obj;
-    const long long ncell = ncx * ncy;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= ncell * (a.pmax + 1)) return;
-    const int p = (int)(tid / ncell);
-    const long long cell = tid - (long long)p * ncell;
-    const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
-    const long long base = (long long)p * a.st.R + o.ray_offset;
+    if (tid >= b.total) return;
+    const CellRef c = decode_cell(a, b, tid);
+    unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
     const DirTabF T = dir_tab_f(tab, nt, nph);
     for (int t = 0; t < 2; ++t) {
         TriGeom g;
-        cell_triangle(a, base, nx, cx, cy, t, g);
-        const long long nc = tri_setup(a, base, g, nt, nph);
+        cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
+        const long long nc = tri_setup(a, c.base, g, nt, nph);
         if (nc == 0) continue;
         const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
         if (nc > kInlineCandidates) {
@@ -378,13 +398,13 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, long long 
             }
         }
         TriFrame fr;
-        tri_frame(a, base, g, fr);
+        tri_frame(a, c.base, g, fr);
         for (int it = g.it0; it <= g.it1; ++it) {
             const float ct = T.ct[it], sth = T.st[it];
             for (int jj = 0; jj < g.jcount; ++jj) {
                 int jp = g.jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidate(a, h, fr, code, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
+                candidate(a, h, fr, code, mask, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
                           ct - g.c[2]);
             }
         }
@@ -392,14 +412,11 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, long long 
 }
 
 // Phase 2: one warp per listed triangle, rows in turn, the lanes taking the columns.
-__global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, long long nx, long long ix0,
-                                                             long long ncx, long long iy0, long long ncy, int nt,
-                                                             int nph, const double* __restrict__ tab,
+__global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBatch b, int nt, int nph,
+                                                             const double* __restrict__ tab,
                                                              const unsigned long long* big, const unsigned int* nbig,
                                                              unsigned int big_cap, HitArgs h)
 {
-    const ObjDev& o = *a.d_obj;
-    const long long ncell = ncx * ncy;
     const unsigned int n = min(*nbig, big_cap);
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -407,22 +424,19 @@ __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, long l
     for (long long w = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
         const unsigned long long code = big[w];
         const int t = (int)(code & 1ull);
-        const long long tid = (long long)(code >> 1);
-        const int p = (int)(tid / ncell);
-        const long long cell = tid - (long long)p * ncell;
-        const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
-        const long long base = (long long)p * a.st.R + o.ray_offset;
+        const CellRef c = decode_cell(a, b, (long long)(code >> 1));
+        unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
         TriGeom g;
-        cell_triangle(a, base, nx, cx, cy, t, g);
-        if (tri_setup(a, base, g, nt, nph) == 0) continue;
+        cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
+        if (tri_setup(a, c.base, g, nt, nph) == 0) continue;
         TriFrame fr;
-        tri_frame(a, base, g, fr);
+        tri_frame(a, c.base, g, fr);
         for (int it = g.it0; it <= g.it1; ++it) {
             const float ct = T.ct[it], sth = T.st[it];
             for (int jj = lane; jj < g.jcount; jj += 32) {
                 int jp = g.jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidate(a, h, fr, code, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
+                candidate(a, h, fr, code, mask, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
                           ct - g.c[2]);
             }
         }
@@ -431,12 +445,9 @@ __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, long l
 
 // Phase 3: one thread per (triangle, direction) pair: the double-precision rule for close calls,
 // then the barycentric weights of the central projection, F, Psi and F e^{i Psi}.
-__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, long long nx, long long ix0, long long ncx,
-                                                             long long iy0, long long ncy, int nt, int nph,
+__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBatch b, int nt, int nph,
                                                              const double* __restrict__ tab, HitArgs h)
 {
-    const ObjDev& o = *a.d_obj;
-    const long long ncell = ncx * ncy;
     const unsigned int n = min(*h.n, h.cap);
     const double* ctab = tab;
     const double* stab = tab + nt;
@@ -449,13 +460,11 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, long l
         const bool close = (dw & kHitClose) != 0;
         const unsigned int dk = dw & ~kHitClose;
         const int t = (int)(code & 1ull);
-        const long long tid = (long long)(code >> 1);
-        const int p = (int)(tid / ncell);
-        const long long cell = tid - (long long)p * ncell;
-        const long long cx = ix0 + cell % ncx, cy = iy0 + cell / ncx;
-        const long long base = (long long)p * a.st.R + o.ray_offset;
+        const CellRef c = decode_cell(a, b, (long long)(code >> 1));
+        const int p = c.p;
+        const long long base = c.base;
         TriGeom g;
-        cell_triangle(a, base, nx, cx, cy, t, g);
+        cell_triangle(a, base, c.nx, c.cx, c.cy, t, g);
         double s[3][3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) load_dir(a.st, base + g.id[v], s[v]);
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, long l
                             ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
                             ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0 && sigma == ((f[0] & kFlagOrient) ? 1 : -1);
             if (!ok) {
-                atomicOr(a.mask + dk, kMaskCaustic);
+                atomicOr(a.mask + (long long)c.orel * b.ndir + dk, kMaskCaustic);
                 continue;
             }
         }
@@ -512,7 +521,7 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, long l
         const double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
         const double eth[3] = {ct * cp, ct * sp, -sth};
         const double eph[3] = {-sp, cp, 0.0};
-        double* dst = a.out + ((long long)dk * (a.per_order ? (a.pmax + 1) : 1) + (a.per_order ? p : 0)) * 4;
+        double* dst = a.out + (((long long)c.orel * b.ndir + dk) * b.nout + (a.per_order ? p : 0)) * 4;
         add_contribution_reduced(Fi, ps, eth, eph, dst);
     }
 }
@@ -931,11 +940,39 @@ __global__ void window_prefix_kernel(const PoWindow* win, const int* nwin, long 
     offs[n] = o;
 }
 
-__global__ void finalize_mask_kernel(const unsigned int* words, unsigned char* mask_out, long long ndir, int kind,
-                                     int nt, int nph, double alpha0, double dalpha, double axial)
+// per-object cell windows and thread offsets of a grid launch (one thread; the group is small)
+__global__ void grid_cells_kernel(const ObjDev* objs, int n, int np, int windowed, long long wx0, long long wx1,
+                                  long long wy0, long long wy1, GridCells* cells)
 {
-    const long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (d >= ndir) return;
+    long long first = 0;
+    for (int i = 0; i < n; ++i) {
+        const ObjDev& o = objs[i];
+        long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
+        if (windowed) {
+            ix0 = wx0 < 0 ? 0 : wx0;
+            ix1 = wx1 > o.nx - 1 ? o.nx - 1 : wx1;
+            iy0 = wy0 < 0 ? 0 : wy0;
+            iy1 = wy1 > o.ny - 1 ? o.ny - 1 : wy1;
+        }
+        GridCells c;
+        c.ix0 = ix0;
+        c.iy0 = iy0;
+        c.ncx = ix1 - ix0 > 0 ? ix1 - ix0 : 0;
+        c.ncy = iy1 - iy0 > 0 ? iy1 - iy0 : 0;
+        c.first = first;
+        first += c.ncx * c.ncy * np;
+        cells[i] = c;
+    }
+}
+
+__global__ void finalize_mask_kernel(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,
+                                     long long ndir, int kind, int nt, int nph, double alpha0, double dalpha)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= ndir * nobj) return;
+    const int oi = (int)(t / ndir);
+    const long long d = t - (long long)oi * ndir;
+    const double axial = 2.0 * objs[oi].lambda / objs[oi].lmin;
     double th;
     if (kind == 0) {
         th = fabs(alpha0 + d * dalpha);
@@ -943,9 +980,9 @@ __global__ void finalize_mask_kernel(const unsigned int* words, unsigned char* m
         const int it = (int)(d / nph);
         th = (it + 0.5) * (kPi / nt);
     }
-    unsigned int m = words[d];
+    unsigned int m = words[t];
     if (th < axial || th > kPi - axial) m |= kMaskAxial;
-    mask_out[d] = (unsigned char)m;
+    mask_out[t] = (unsigned char)m;
 }
 
 }  // namespace
@@ -957,33 +994,27 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, long long ix1, long long iy0,
-                              long long iy1, int nt, int nph, const double* tab, unsigned long long* big,
-                              unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
-                              unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int newton,
-                              cudaStream_t s)
+cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, int nph, const double* tab,
+                              unsigned long long* big, unsigned int* nbig, unsigned int big_cap,
+                              unsigned long long* hit_tri, unsigned int* hit_dir, unsigned int* nhit,
+                              unsigned int hit_cap, int classify_block, cudaStream_t s)
 {
-    (void)newton;
-    const long long ncx = ix1 - ix0, ncy = iy1 - iy0;
-    if (ncx <= 0 || ncy <= 0) return cudaSuccess;
-    const long long n = ncx * ncy * (a.pmax + 1);
+    if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
+    const int cb = classify_block > 0 ? classify_block : bs;
     cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(nhit, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     HitArgs h{hit_tri, hit_dir, nhit, hit_cap};
-    field_grid_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab, big,
-                                                                     nbig, big_cap, h);
+    field_grid_kernel<<<(unsigned)((b.total + cb - 1) / cb), cb, 0, s>>>(a, b, nt, nph, tab, big, nbig, big_cap, h);
     // fixed grids walk the lists: 16 blocks per SM
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    field_grid_big_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab, big, nbig,
-                                                              big_cap, h);
-    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, nx, ix0, ncx, iy0, ncy, nt, nph, tab, h);
+    field_grid_big_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, big, nbig, big_cap, h);
+    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, h);
     return cudaGetLastError();
 }
-
 
 // the fan path: alpha table, folds and windows (when PO or Newton near folds), aperture fields
 // (when PO), the segments, then the PO sums
@@ -1021,12 +1052,21 @@ cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, long long ndir, int kind, int nt,
-                                 int nph, double alpha0, double dalpha, double axial, cudaStream_t s)
+cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
+                              cudaStream_t s)
 {
-    if (!mask_out || ndir == 0) return cudaSuccess;
-    finalize_mask_kernel<<<(unsigned)((ndir + 255) / 256), 256, 0, s>>>(words, mask_out, ndir, kind, nt, nph, alpha0,
-                                                                         dalpha, axial);
+    grid_cells_kernel<<<1, 1, 0, s>>>(objs, n, np, windowed ? 1 : 0, windowed ? win[0] : 0, windowed ? win[1] : 0,
+                                      windowed ? win[2] : 0, windowed ? win[3] : 0, cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,
+                                 long long ndir, int kind, int nt, int nph, double alpha0, double dalpha, cudaStream_t s)
+{
+    if (!mask_out || ndir == 0 || nobj == 0) return cudaSuccess;
+    const long long n = ndir * nobj;
+    finalize_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(words, mask_out, objs, nobj, ndir, kind, nt, nph,
+                                                                      alpha0, dalpha);
     return cudaGetLastError();
 }
 

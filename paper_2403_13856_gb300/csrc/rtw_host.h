@@ -1,0 +1,91 @@
+// rtw_host.h -- host-side helpers shared by the C-ABI translation units of librtw (internal).
+//
+// Object descriptions in double precision, error reporting, the per-device status word, the ray
+// grid of an object, and the square-grid field run in launch groups of objects that both
+// rtw_field and the batched entry point use.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "rtw.h"
+#include "rtw_launch.h"
+
+namespace rtw {
+namespace host {
+
+// One ellipsoid and its incident wave, in double precision: semi-axes, rotation (body to lab),
+// centre, index, wavelength, Jones vector, quadric matrix W = R diag(1/a^2) R^T, the projected
+// ellipse S (x^T S x <= 1 on z = const) and its inverse, smallest and largest semi-axis.
+struct ObjHost {
+    double a[3];
+    double R[3][3];
+    double c[3];
+    double m;
+    double lambda;
+    double jre[2], jim[2];
+    double W[3][3];
+    double S[2][2], Sinv[2][2];
+    double lmin, lmax;
+};
+
+// sets the calling thread's last-error message and returns code
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int cuda_fail(cudaError_t e, const char* what);
+// device word of error bits raised by kernels (allocated once per device)
+unsigned int* status_word(int dev);
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void fill_objdev(const ObjHost& o, ObjDev& d);
+// ray grid of one object: spacing, size, fan half-width (host arithmetic only)
+int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* nx, long long* ny, double* fan_w);
+
+// Launch groups of a square-grid field: objects [k group, (k+1) group) share one launch sequence;
+// the group size is bounded by the hit list (4 (triangle, direction) pairs per direction and order
+// of each object, at most 2^28 pairs).
+struct GridPlan {
+    int group = 1;
+    long long max_group_cells = 0;  // cells x orders of the largest group
+    bool windowed = false;
+};
+GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs);
+
+// Grid-field workspace carved from one device block.
+struct GridWs {
+    unsigned int* mask_words = nullptr;  // group x directions
+    double* tab = nullptr;               // direction tables
+    GridCells* cells = nullptr;          // group entries
+    unsigned long long* big = nullptr;
+    unsigned int* nbig = nullptr;
+    unsigned int* nhit = nullptr;
+    unsigned long long* hit_tri = nullptr;
+    unsigned int* hit_dir = nullptr;
+    unsigned int big_cap = 0, hit_cap = 0;
+};
+// Bytes of the workspace of plan g; carves it from base when base is not null.
+size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, GridWs* w);
+
+// Field of objects [0, nobj) of ray state st on the (theta, phi) grid of dirs.  h_objs and d_objs
+// are the same table on the host and the device.  Adds into out, which the caller cleared:
+// [objects][directions][nout][4] doubles.  mask_out (may be null): [objects][directions] bytes.
+// The direction tables in w must have been filled (launch_dir_tables) on the same stream.
+int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
+                   const rtw_dirs* dirs, bool per_order, double* out, unsigned char* mask_out, const GridWs& w,
+                   int classify_block, unsigned int* status, cudaStream_t s);
+
+}  // namespace host
+}  // namespace rtw
+
+struct rtw_object {
+    int count = 0;
+    int device = 0;
+    std::vector<rtw::host::ObjHost> h;
+};
+
+#define RTW_CUDA(call)                                                    \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return rtw::host::cuda_fail(e_, #call);    \
+    } while (0)

@@ -40,7 +40,12 @@ struct ObjDev {
     double fan_w, fan_ex, fan_ey;
     long long nx, ny;       // square: grid size; fan: (n, 1)
     long long ray_offset;   // first global ray index of this object
+    long long item_first;   // first work item (kRaysPerItem rays) of this object in a batched trace
 };
+static_assert(sizeof(ObjDev) == 256, "object table entries are 256 bytes");
+
+// rays per work item of the persistent batched trace
+constexpr int kRaysPerItem = 256;
 
 // Double-precision ray state.  Aux arrays (exit-wave data for the PO integral) are allocated for
 // fan grids traced with RTW_TRACE_APERTURE only.

@@ -18,8 +18,29 @@ struct PoWindow {
 };
 constexpr int kMaxPoWindows = 64;
 
+// cells of one object in a square-grid field launch
+struct GridCells {
+    long long ix0, iy0, ncx, ncy;  // cell window of the object's ray grid
+    long long first;               // first launch thread of this object (prefix of ncx ncy np)
+};
+
+struct GridBatch {
+    const GridCells* cells;  // device, nobj entries
+    int nobj;
+    long long total;         // threads of the launch
+    long long ndir;          // directions per object
+    int nout;                // (F_theta, F_phi) pairs per direction: orders or 1
+};
+
+struct CellRef {
+    const ObjDev* o;
+    int orel;  // object within the launch
+    int p;
+    long long cx, cy, base, nx;
+};
+
 struct FieldArgs {
-    const ObjDev* d_obj;   // this object's entry of the table
+    const ObjDev* d_obj;   // the launch's first object in the table (grid fields: objects follow)
     RaysDev st;
     int pmax;
     int per_order;
@@ -34,6 +55,11 @@ void set_last_error(const char* msg);
 // trace
 cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, bool aux, unsigned int* status,
                          cudaStream_t s);
+// persistent batched trace over work items; variant 1..kTraceVariants picks the block size and
+// register cap: 1 (64, 1), 2 (128, 1), 3 (256, 1), 4 (128, 3 CTAs/SM), 5 (256, 2 CTAs/SM)
+constexpr int kTraceVariants = 5;
+cudaError_t launch_trace_items(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, unsigned long long* next,
+                               long long nitems, int variant, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_trace_points(const ObjDev* d_obj, const double* xy, long long n, int pmax, double* s_out,
                                 double* F_out, double* psi_out, uint32_t* flags_out, cudaStream_t s);
 cudaError_t launch_export(RaysDev st, int order, long long first, long long count, double* s_out, double* F_out,
@@ -41,15 +67,17 @@ cudaError_t launch_export(RaysDev st, int order, long long first, long long coun
 
 // field
 cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s);
-cudaError_t launch_field_grid(const FieldArgs& a, long long nx, long long ix0, long long ix1, long long iy0,
-                              long long iy1, int nt, int nph, const double* tab, unsigned long long* big,
-                              unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
-                              unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int newton,
-                              cudaStream_t s);
+cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, int nph, const double* tab,
+                              unsigned long long* big, unsigned int* nbig, unsigned int big_cap,
+                              unsigned long long* hit_tri, unsigned int* hit_dir, unsigned int* nhit,
+                              unsigned int hit_cap, int classify_block, cudaStream_t s);
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
                              double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
                              int newton, cudaStream_t s);
-cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, long long ndir, int kind,
-                                 int nt, int nph, double alpha0, double dalpha, double axial, cudaStream_t s);
+cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
+                              cudaStream_t s);
+cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,
+                                 long long ndir, int kind, int nt, int nph, double alpha0, double dalpha,
+                                 cudaStream_t s);
 
 }  // namespace rtw

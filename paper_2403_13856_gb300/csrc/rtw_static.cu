@@ -189,8 +189,8 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
                                    nullptr, 0, 0, 0, s)) != cudaSuccess)
         return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
     if (mask_out) {
-        if ((e = rtw::launch_finalize_mask(mask_words, mask_out, ndir, 0, dirs->n_theta, 0, dirs->alpha0,
-                                           dirs->dalpha, 2.0 * w->wavelength_um / lmin, s)) != cudaSuccess)
+        if ((e = rtw::launch_finalize_mask(mask_words, mask_out, d_obj, 1, ndir, 0, dirs->n_theta, 0, dirs->alpha0,
+                                           dirs->dalpha, s)) != cudaSuccess)
             return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));
     }
     return RTW_OK;

@@ -1,4 +1,6 @@
 // rtw_trace.cu -- trace kernels: one thread per incident ray, structure-of-arrays ray state.
+#include <algorithm>
+
 #include "rtw_launch.h"
 #include "rtw_trace.cuh"
 
@@ -95,6 +97,17 @@ __device__ __forceinline__ int find_object(const ObjDev* objs, int nobj, long lo
     return lo;
 }
 
+// traces global ray j of object o and clears the flags of the orders it does not reach
+template <typename T>
+__device__ __forceinline__ void trace_one(const ObjDev* o, const RaysDev& st, long long j, int pmax, int aux)
+{
+    StateSink sink{o, st, j, aux != 0, 0u};
+    double x, y;
+    if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray<T, false>(*o, x, y, pmax, sink);
+    for (int p = 0; p < st.np; ++p)
+        if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
+}
+
 template <typename T>
 __device__ __forceinline__ void trace_kernel_body(const ObjDev* __restrict__ objs, int nobj, RaysDev st, int pmax,
                                                   int aux)
@@ -102,11 +115,50 @@ __device__ __forceinline__ void trace_kernel_body(const ObjDev* __restrict__ obj
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (j >= st.R) return;
     const ObjDev* o = objs + (nobj > 1 ? find_object(objs, nobj, j) : 0);
-    StateSink sink{o, st, j, aux != 0, 0u};
-    double x, y;
-    if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray<T, false>(*o, x, y, pmax, sink);
-    for (int p = 0; p < st.np; ++p)
-        if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
+    trace_one<T>(o, st, j, pmax, aux);
+}
+
+// object owning work item `it` (largest i with item_first <= it)
+__device__ __forceinline__ int find_item_object(const ObjDev* objs, int nobj, long long it)
+{
+    int lo = 0, hi = nobj - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (objs[mid].item_first <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent batched trace: each CTA takes work items (object, 256 consecutive rays of it) from a
+// counter until none is left.  Items are equal in cost up to misses, so taking them in order is
+// the balanced schedule.  BS threads and MINB CTAs per SM are template parameters (the register
+// cap follows from them); the loop ends after at most nitems / gridDim.x + 1 items per CTA.
+template <typename T, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) trace_items_kernel(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
+                                                               int pmax, unsigned long long* next, long long nitems)
+{
+    __shared__ long long s_item;
+    __shared__ int s_obj;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(next, 1ull);
+            s_item = it;
+            s_obj = it < nitems ? find_item_object(objs, nobj, it) : 0;
+        }
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= nitems) return;
+        const ObjDev* o = objs + s_obj;
+        const long long first = (it - o->item_first) * kRaysPerItem;
+        const long long nr = o->nx * o->ny;
+        for (int r = threadIdx.x; r < kRaysPerItem; r += BS) {
+            const long long local = first + r;
+            if (local >= nr) break;
+            trace_one<T>(o, st, o->ray_offset + local, pmax, 0);
+        }
+    }
 }
 
 // every step in double precision
@@ -179,6 +231,50 @@ cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, b
     else
         trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     return cudaGetLastError();
+}
+
+namespace {
+
+template <typename T, int BS, int MINB>
+cudaError_t launch_items(const ObjDev* d_objs, int nobj, const RaysDev& st, int pmax, unsigned long long* next,
+                         long long nitems, int ctas_per_sm, cudaStream_t s)
+{
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_items_kernel<T, BS, MINB>, BS, 0);
+    if (e != cudaSuccess) return e;
+    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    const long long grid = std::min<long long>((long long)sms * per_sm, nitems);
+    trace_items_kernel<T, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(d_objs, nobj, st, pmax, next, nitems);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_items_variant(int variant, const ObjDev* d_objs, int nobj, const RaysDev& st, int pmax,
+                                 unsigned long long* next, long long nitems, int ctas_per_sm, cudaStream_t s)
+{
+    switch (variant) {
+    case 1: return launch_items<T, 64, 1>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    case 2: return launch_items<T, 128, 1>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    case 3: return launch_items<T, 256, 1>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    case 4: return launch_items<T, 128, 3>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    case 5: return launch_items<T, 256, 2>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_trace_items(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, unsigned long long* next,
+                               long long nitems, int variant, int ctas_per_sm, cudaStream_t s)
+{
+    if (nitems <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (st.precision == 1)
+        return launch_items_variant<float>(variant, d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    return launch_items_variant<double>(variant, d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
 }
 
 cudaError_t launch_trace_points(const ObjDev* d_obj, const double* xy, long long n, int pmax, double* s_out,

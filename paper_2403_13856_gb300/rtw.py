@@ -54,6 +54,15 @@ class rtw_dirs(ctypes.Structure):
                 ("alpha0", ctypes.c_double), ("dalpha", ctypes.c_double), ("cell_window", ctypes.c_int64 * 4)]
 
 
+class rtw_batch_params(ctypes.Structure):
+    _fields_ = [("p_max", ctypes.c_int), ("precision", ctypes.c_int), ("n_rays", ctypes.c_void_p),
+                ("chunk_ray_orders", ctypes.c_int64), ("trace_variant", ctypes.c_int),
+                ("trace_ctas_per_sm", ctypes.c_int), ("classify_block", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+TRACE_VARIANTS = 5
+
 _lib = None
 
 
@@ -75,6 +84,10 @@ def lib():
             "rtw_destroy_rays": ([p], None),
             "rtw_trace_points": ([p, i, p, i64, i, p, p, p, p, p], i),
             "rtw_field": ([p, p, i, i, p, p, p], i),
+            "rtw_far_field_batch": ([p, p, p, i, p, p, p, p], i),
+            "rtw_batch_info": ([p, p, p, p], i),
+            "rtw_batch_times": ([p, p, p], i),
+            "rtw_destroy_batch": ([p], None),
             "rtw_sync_status": ([p], i),
             "rtw_status_string": ([i], ctypes.c_char_p),
             "rtw_last_error": ([], ctypes.c_char_p),
@@ -213,6 +226,49 @@ def dirs_grid(n_theta: int, n_phi: int, cell_window=None) -> rtw_dirs:
 
 def rtw_field(rays: Rays, dirs: rtw_dirs, out, mask=None, mode=RTW_DENSE, flags=0, stream=None):
     _check(lib().rtw_field(rays.handle, ctypes.byref(dirs), mode, flags, _ptr(out), _ptr(mask), _stream_ptr(stream)))
+
+
+class Batch:
+    """rtw_batch handle: ray state, workspace and recorded graph of rtw_far_field_batch."""
+
+    def __init__(self):
+        self.handle = ctypes.c_void_p()
+
+    def info(self):
+        R, nc, rep = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().rtw_batch_info(self.handle, ctypes.byref(R), ctypes.byref(nc), ctypes.byref(rep)))
+        return R.value, nc.value, bool(rep.value)
+
+    def times(self):
+        t, f = ctypes.c_double(), ctypes.c_double()
+        _check(lib().rtw_batch_times(self.handle, ctypes.byref(t), ctypes.byref(f)))
+        return t.value, f.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.rtw_destroy_batch(self.handle)
+            self.handle = ctypes.c_void_p()
+
+
+def batch_params(n_rays, p_max=4, precision=RTW_FP64, chunk_ray_orders=0, trace_variant=0, trace_ctas_per_sm=0,
+                 classify_block=0, use_graph=0, timing=0):
+    """Options of rtw_far_field_batch; n_rays is kept alive on the returned structure."""
+    bp = rtw_batch_params()
+    arr = (ctypes.c_int64 * len(n_rays))(*[int(x) for x in n_rays])
+    bp._n_rays = arr
+    bp.n_rays = ctypes.cast(arr, ctypes.c_void_p)
+    bp.p_max, bp.precision, bp.chunk_ray_orders = p_max, precision, int(chunk_ray_orders)
+    bp.trace_variant, bp.trace_ctas_per_sm, bp.classify_block = trace_variant, trace_ctas_per_sm, classify_block
+    bp.use_graph, bp.timing = int(use_graph), int(timing)
+    return bp
+
+
+def rtw_far_field_batch(obj: Object, params: rtw_batch_params, dirs: rtw_dirs, out, mask=None, flags=0,
+                        batch: Optional[Batch] = None, stream=None) -> Batch:
+    batch = batch or Batch()
+    _check(lib().rtw_far_field_batch(obj.handle, ctypes.byref(params), ctypes.byref(dirs), flags, _ptr(out),
+                                     _ptr(mask), ctypes.byref(batch.handle), _stream_ptr(stream)))
+    return batch
 
 
 def rtw_sync_status(stream=None):

@@ -30,3 +30,59 @@ ELLIPSOID_GRID = dict(n_rays=4_000_000, p_max=5, n_theta=512, n_phi=1024)
 
 # Table 1 of the paper: spheres of radius 50 and 500 um, order p = 2, perpendicular polarisation.
 TABLE1_SPHERES = (50.0, 500.0)
+
+# ------------------------------------------------------------------------------------------------
+# Batched drops: seed-drawn ellipsoids of uneven size, shape, orientation, index and wavelength.
+# Counter-based Philox generator keyed by (master seed, stream), one stream per purpose.
+# ------------------------------------------------------------------------------------------------
+MASTER_SEED = 2403138560
+STREAM_BATCH = 1
+STREAM_TRAIN = 2
+STREAM_EVAL = 3
+
+# 4096 ellipsoids: r0 ~ U[20, 500] um, b, c = r0 U[0.8, 1.2], uniform orientation, m ~ U[1.33, 1.55],
+# lambda ~ U[0.4, 0.8] um, x polarisation, rays clamp(1e6 (r0 / 500)^2, 1e3, 1e6), orders 0..4,
+# 128 x 256 (theta, phi) directions per object.
+BATCH = dict(n_objects=4096, r0=(20.0, 500.0), aspect=(0.8, 1.2), m=(1.33, 1.55), wavelength=(0.4, 0.8),
+             rays_ref=(1e6, 500.0), rays_clamp=(1_000, 1_000_000), p_max=4, n_theta=128, n_phi=256)
+
+
+def philox(stream: int):
+    """numpy Generator on the Philox-4x64 bit generator keyed by (MASTER_SEED, stream)."""
+    import numpy as np
+
+    return np.random.Generator(np.random.Philox(key=np.array([MASTER_SEED, stream], dtype=np.uint64)))
+
+
+def shoemake_quaternions(u):
+    """Uniform random unit quaternions (w, x, y, z) from uniforms u (n x 3) (Shoemake's method)."""
+    import numpy as np
+
+    u1, u2, u3 = u[:, 0], u[:, 1], u[:, 2]
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    q = np.stack([a * np.sin(2 * np.pi * u2), a * np.cos(2 * np.pi * u2), b * np.sin(2 * np.pi * u3),
+                  b * np.cos(2 * np.pi * u3)], axis=1)
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def batch_objects(n_objects=None, stream=STREAM_BATCH, r0=None, rays_ref=None, rays_clamp=None):
+    """Object specs (dicts of a, b, c, quat, m, wavelength) and ray counts of the batched workload.
+    r0, rays_ref = (rays, at radius) and rays_clamp override the size recipe (small test batches)."""
+    import numpy as np
+
+    n = BATCH["n_objects"] if n_objects is None else int(n_objects)
+    lo, hi = BATCH["r0"] if r0 is None else r0
+    nref, rref = BATCH["rays_ref"] if rays_ref is None else rays_ref
+    cmin, cmax = BATCH["rays_clamp"] if rays_clamp is None else rays_clamp
+    g = philox(stream)
+    u = g.random((n, 9))
+    r = lo + (hi - lo) * u[:, 0]
+    b = r * (BATCH["aspect"][0] + (BATCH["aspect"][1] - BATCH["aspect"][0]) * u[:, 1])
+    c = r * (BATCH["aspect"][0] + (BATCH["aspect"][1] - BATCH["aspect"][0]) * u[:, 2])
+    q = shoemake_quaternions(u[:, 3:6])
+    m = BATCH["m"][0] + (BATCH["m"][1] - BATCH["m"][0]) * u[:, 6]
+    lam = BATCH["wavelength"][0] + (BATCH["wavelength"][1] - BATCH["wavelength"][0]) * u[:, 7]
+    rays = np.clip(np.rint(nref * (r / rref) ** 2), cmin, cmax).astype(np.int64)
+    specs = [dict(a=float(r[i]), b=float(b[i]), c=float(c[i]), quat=tuple(float(x) for x in q[i]), m=float(m[i]),
+                  wavelength=float(lam[i])) for i in range(n)]
+    return specs, rays

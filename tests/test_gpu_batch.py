@@ -1,0 +1,162 @@
+"""Batched far field (many ellipsoids, one launch sequence) on the GPU against the FP64 oracle.
+
+Objects come from the batched-drop recipe (uneven size, shape, orientation, index, wavelength);
+small batches use the same distributions at reduced radii so that the oracle computes every object,
+the full-size batch (4096 objects, about 1.4e9 rays) is checked on sampled objects.  Tolerances
+as the single-object grid field: |dF| <= 1e-6 max|F| per object and masks identical (FP64);
+the mixed-precision batch is bounded by the normwise error stated in its test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rtw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_13856_gb300 import build, rtw as R
+
+    build.build()
+    R.lib()
+    return R
+
+
+def make_batch(rtw, specs, jones=(1.0, 0.0)):
+    return rtw.Object([rtw.ObjectSpec(**s, jones=jones) for s in specs])
+
+
+def run_batch(rtw, obj, rays, p_max, nt, nph, flags=0, batch=None, out=None, mask=None, **kw):
+    nout = p_max + 1 if flags & rtw.RTW_FIELD_PER_ORDER else 1
+    n = len(rays)
+    if out is None:
+        out = torch.zeros((n, nt * nph, nout, 2), dtype=torch.complex128, device="cuda")
+        mask = torch.zeros((n, nt * nph), dtype=torch.uint8, device="cuda")
+    bp = rtw.batch_params(rays, p_max=p_max, **kw)
+    batch = rtw.rtw_far_field_batch(obj, bp, rtw.dirs_grid(nt, nph), out, mask, flags=flags, batch=batch)
+    rtw.rtw_sync_status()
+    return out, mask, batch
+
+
+def oracle_field(oracle_mod, spec, jones, p_max, nt, nph, n_rays):
+    o = oracle_mod.Object(spec["a"], spec["b"], spec["c"], quat=spec["quat"], m=spec["m"],
+                          wavelength=spec["wavelength"], jones=jones)
+    ref, rm, hits, _ = o.field_grid(p_max, nt, nph, n_target=int(n_rays))
+    return oracle_mod.complex_field(ref), rm
+
+
+def compare(got, ref, gm, rm, tol=1e-6):
+    assert np.array_equal(gm, rm), f"{(gm != rm).sum()} mask entries differ"
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref).max()
+    assert err <= tol * scale, f"max |dF| {err:.3e} vs scale {scale:.3e}"
+
+
+SMALL = dict(r0=(3.0, 12.0), rays_ref=(2.0e4, 12.0), rays_clamp=(300, 20_000))
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+def test_batch_small_per_order_vs_oracle(rtw, oracle_mod, variant):
+    """12 drops of the batched recipe at radii 3-12 um, orders 0..4 per order, 32 x 64 directions;
+    a chunk bound of 6e4 ray-orders splits them into several chunks; every trace variant."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(12, **SMALL)
+    obj = make_batch(rtw, specs)
+    p_max, nt, nph = 4, 32, 64
+    out, mask, batch = run_batch(rtw, obj, rays, p_max, nt, nph, flags=rtw.RTW_FIELD_PER_ORDER,
+                                 chunk_ray_orders=60_000, trace_variant=variant)
+    total, nchunks, _ = batch.info()
+    assert nchunks >= 3
+    got, gm = out.cpu().numpy(), mask.cpu().numpy()
+    for i, s in enumerate(specs):
+        ref, rm = oracle_field(oracle_mod, s, (1.0, 0.0), p_max, nt, nph, rays[i])
+        compare(got[i], ref, gm[i], rm)
+
+
+def test_batch_graph_replay_and_chunking_agree(rtw):
+    """Graph replay reproduces the eager run; one chunk and many chunks agree (the same sums in
+    another order of atomic additions: relative 1e-12)."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(40, **SMALL)
+    obj = make_batch(rtw, specs, jones=(0.6, 0.8j))
+    p_max, nt, nph = 4, 24, 48
+    eager, em, _ = run_batch(rtw, obj, rays, p_max, nt, nph)
+    out = torch.zeros_like(eager)
+    mask = torch.zeros_like(em)
+    b = None
+    for k in range(3):
+        out.zero_()
+        _, _, b = run_batch(rtw, obj, rays, p_max, nt, nph, batch=b, out=out, mask=mask, use_graph=1,
+                            chunk_ray_orders=100_000)
+        assert b.info()[2] == (k > 0)
+        scale = eager.abs().max().item()
+        assert (out - eager).abs().max().item() <= 1e-12 * scale
+        assert torch.equal(mask, em)
+
+
+def test_batch_mixed_precision_vs_oracle(rtw, oracle_mod):
+    """Mixed precision batch against the FP64 oracle: normwise error per object <= 1e-4 and
+    identical masks."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(8, **SMALL)
+    obj = make_batch(rtw, specs)
+    p_max, nt, nph = 4, 32, 64
+    out, mask, _ = run_batch(rtw, obj, rays, p_max, nt, nph, precision=rtw.RTW_MIXED)
+    got, gm = out.cpu().numpy()[:, :, 0], mask.cpu().numpy()
+    worst = 0.0
+    for i, s in enumerate(specs):
+        ref, rm = oracle_field(oracle_mod, s, (1.0, 0.0), p_max, nt, nph, rays[i])
+        ref = ref.sum(axis=1)
+        assert np.array_equal(gm[i], rm)
+        worst = max(worst, np.linalg.norm(got[i] - ref) / np.linalg.norm(ref))
+    print(f"mixed batch: worst normwise field error {worst:.2e}")
+    assert worst <= 1e-4
+
+
+def test_batch_argument_errors(rtw):
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(2, **SMALL)
+    obj = make_batch(rtw, specs)
+    out = torch.zeros((2, 8 * 16, 1, 2), dtype=torch.complex128, device="cuda")
+    d = rtw.dirs_grid(8, 16)
+    for kw in [dict(trace_variant=9), dict(classify_block=96), dict(p_max=16), dict(chunk_ray_orders=-1)]:
+        args = dict(p_max=4)
+        args.update(kw)
+        with pytest.raises(rtw.RTWError):
+            rtw.rtw_far_field_batch(obj, rtw.batch_params(rays, **args), d, out)
+    with pytest.raises(rtw.RTWError):
+        rtw.rtw_far_field_batch(obj, rtw.batch_params([0, 100]), d, out)
+    with pytest.raises(rtw.RTWError):
+        rtw.rtw_far_field_batch(obj, rtw.batch_params(rays), rtw.dirs_grid(8, 16, [0, 4, 0, 4]), out)
+
+
+def test_batch_full_size_sampled_objects(rtw, oracle_mod):
+    """The full batched workload (4096 drops, r0 20-500 um, about 1.4e9 rays, orders 0..4, 128 x 256
+    directions each) in the launch configuration the benchmark times (FP64, graph); the fields of
+    sampled objects (smallest, median, largest ray count, and two more) against the oracle."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.BATCH
+    specs, rays = W.batch_objects()
+    obj = make_batch(rtw, specs)
+    nt, nph = cfg["n_theta"], cfg["n_phi"]
+    out, mask, batch = run_batch(rtw, obj, rays, cfg["p_max"], nt, nph, use_graph=1)
+    order = np.argsort(rays)
+    picks = [order[0], order[len(order) // 2], order[-1], 7, 1000]
+    got = out[picks].cpu().numpy()[:, :, 0]
+    gm = mask[picks].cpu().numpy()
+    for k, i in enumerate(picks):
+        ref, rm = oracle_field(oracle_mod, specs[i], (1.0, 0.0), cfg["p_max"], nt, nph, rays[i])
+        ref = ref.sum(axis=1)
+        assert np.array_equal(gm[k], rm), f"object {i}: {(gm[k] != rm).sum()} mask entries differ"
+        scale = np.abs(ref).max()
+        err = np.abs(got[k] - ref).max()
+        print(f"object {i} ({rays[i]} rays, a={specs[i]['a']:.1f} um): max |dF| / max |F| = {err / scale:.2e}")
+        assert err <= 1e-6 * scale
