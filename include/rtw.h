@@ -60,9 +60,11 @@ extern "C" {
                        optical path and phase in double precision                              */
 
 #define RTW_DENSE 0  /* interpolation of the dense ray map (the paper's RTW strategy)           */
-#define RTW_NEWTON 1 /* hits refined by Newton steps on the exact FP64 trace (fan grids); a
-                        hit whose Newton iteration fails keeps its interpolated value and
-                        raises RTW_ERR_TIMEOUT at rtw_sync_status                               */
+#define RTW_NEWTON 1 /* hits refined by Newton steps on the exact FP64 trace (Eq. WavefrontEqVec
+                        gives the Jacobian ds/d(x, y) = Q' T), each step halved until the
+                        residual decreases; on square grids the root must lie within 8 h of the
+                        interpolated impact point.  A hit whose iteration does not converge
+                        keeps its interpolated value and is counted (rtw_newton_failures)        */
 
 #define RTW_DIRS_PLANE 0 /* in-plane angles alpha_k = alpha0 + k dalpha, k < n_theta, measured
                             from +z toward (cos fan_phi, sin fan_phi, 0); fan grids only        */
@@ -180,8 +182,9 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
  * the near-caustic flag, add nothing and mark the directions they cover (RTW_MASK_CAUSTIC).  With
  * RTW_FIELD_PO (fan grids traced with RTW_TRACE_APERTURE) the field near every in-plane fold is
  * the physical-optics integral over the exit wave ("Diffraction effect correction based on VCRM").
- * mode RTW_NEWTON replaces each interpolated hit (of fan grids) by the exact ray found by Newton steps
- * on the FP64 trace (all hits, or with RTW_FIELD_NEAR_FOLDS those within 2 deg of a fold).
+ * mode RTW_NEWTON replaces each interpolated hit by the exact ray found by Newton steps on the FP64
+ * trace from the interpolated impact point (all hits, or, on fans with RTW_FIELD_NEAR_FOLDS, those
+ * within 2 deg of a fold).
  * field_out (device): [objects][directions][orders or 1][2] complex128 (F_theta, F_phi), zeroed
  * and written.  mask_out (device, optional): [objects][directions] uint8.  Asynchronous. */
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
@@ -200,7 +203,8 @@ int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, v
  * use_graph = 1 records the whole launch sequence in a CUDA graph on the first call and replays
  * it on later calls whose objects, options, directions and output pointers are the same.
  * timing = 1 records CUDA events around the trace and the field of every chunk (eager runs only,
- * read with rtw_batch_times). */
+ * read with rtw_batch_times).  mode: RTW_DENSE, or RTW_NEWTON (every interpolated hit replaced by
+ * the exact ray, as in rtw_field). */
 typedef struct {
     int p_max;
     int precision;
@@ -211,6 +215,7 @@ typedef struct {
     int classify_block;
     int use_graph;
     int timing;
+    int mode;
 } rtw_batch_params;
 
 typedef struct rtw_batch rtw_batch;
@@ -262,6 +267,9 @@ int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident* w, const 
 /* Synchronises `stream`, reads and clears the device status word of the library: RTW_OK or the
  * first RTW_ERR_* a kernel raised since the last call. */
 int rtw_sync_status(void* stream);
+/* Synchronises `stream`, then reads and clears the device's count of RTW_NEWTON refinements that
+ * did not converge since the last call (their hits kept the interpolated value). */
+int rtw_newton_failures(void* stream, int64_t* count);
 const char* rtw_status_string(int status);
 const char* rtw_last_error(void);
 /* Library version string. */

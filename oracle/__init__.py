@@ -66,7 +66,7 @@ def lib():
         L.or_field_fan.restype = i
         L.or_field_grid.argtypes = [p, i64, d, i, i, i, p, i, p, p, i, p]
         L.or_field_grid.restype = i64
-        L.or_newton.argtypes = [p, i, p, p, p]
+        L.or_newton.argtypes = [p, i, p, p, d, p]
         L.or_newton.restype = i
         _lib = L
     return _lib
@@ -149,11 +149,11 @@ class Object:
             raise RuntimeError("or_field_grid failed")
         return out, mask, int(hits), int(nfail.value)
 
-    def newton(self, p, target, xy):
+    def newton(self, p, target, xy, rmax=0.0):
         target = np.ascontiguousarray(target, dtype=np.float64)
         xy = np.array(xy, dtype=np.float64)
         rec = np.zeros(NFIELD)
-        it = lib().or_newton(self.handle, int(p), _ptr(target), _ptr(xy), _ptr(rec))
+        it = lib().or_newton(self.handle, int(p), _ptr(target), _ptr(xy), float(rmax), _ptr(rec))
         return it, xy, rec
 
 

@@ -515,25 +515,65 @@ void or_trace_rays(const or_object* o, const double* xy, int64_t n, int pmax, do
 /* O3: Newton on the exact trace                                                          */
 /* ------------------------------------------------------------------------------------- */
 
-int or_newton(const or_object* o, int p, const double target[3], double* xy, double* rec)
+/* Residual |target - s_p(x, y)| of the exact trace at xy; the record of order p goes to buf.
+ * Returns 0 when order p does not leave the object from this impact point. */
+static int newton_eval(const or_object* o, int p, const double target[3], const double* xy, double* buf,
+                       double* res)
 {
-    double* buf = (double*)malloc(sizeof(double) * (size_t)(p + 1) * OR_NFIELD);
+    or_trace_ray(o, xy[0], xy[1], p, buf, NULL);
+    const double* r = buf + (size_t)p * OR_NFIELD;
+    if (r[OR_VALID] == 0.0) return 0;
+    double d[3] = {target[0] - r[OR_S], target[1] - r[OR_S + 1], target[2] - r[OR_S + 2]};
+    *res = norm3(d);
+    return 1;
+}
+
+/* Newton steps xy <- xy + J^{-1} [v1.d, v2.d] with d = target - s and J = ds/d(x, y) of the
+ * record, each step shortened by halving (at most 12 times) until the trace of the new point
+ * leaves in order p with a smaller residual.  Converged when |d| < 1e-11 within 30 steps and the
+ * root lies within rmax of the seed (rmax <= 0: anywhere), so that the ray found is the one the
+ * seed stands for and not a neighbouring branch of the same order. */
+int or_newton(const or_object* o, int p, const double target[3], double* xy, double rmax, double* rec)
+{
+    const size_t nb = (size_t)(p + 1) * OR_NFIELD;
+    double* buf = (double*)malloc(sizeof(double) * 2 * nb);
+    double* cur = buf;
+    double* trial = buf + nb;
+    const double x0 = xy[0], y0 = xy[1];
     int ret = -1;
-    for (int it = 0; it < 30; ++it) {
-        or_trace_ray(o, xy[0], xy[1], p, buf, NULL);
-        const double* r = buf + (size_t)p * OR_NFIELD;
-        if (r[OR_VALID] == 0.0) break;
-        double d[3] = {target[0] - r[OR_S], target[1] - r[OR_S + 1], target[2] - r[OR_S + 2]};
-        if (norm3(d) < 1e-13) {
-            memcpy(rec, r, sizeof(double) * OR_NFIELD);
-            ret = it;
-            break;
+    double res;
+    if (newton_eval(o, p, target, xy, cur, &res)) {
+        for (int it = 0; it < 30; ++it) {
+            const double* r = cur + (size_t)p * OR_NFIELD;
+            if (res < 1e-11) {
+                if (rmax <= 0.0 || hypot(xy[0] - x0, xy[1] - y0) <= rmax) {
+                    memcpy(rec, r, sizeof(double) * OR_NFIELD);
+                    ret = it;
+                }
+                break;
+            }
+            double d[3] = {target[0] - r[OR_S], target[1] - r[OR_S + 1], target[2] - r[OR_S + 2]};
+            double rhs0 = dot3(r + OR_V1, d), rhs1 = dot3(r + OR_V2, d);
+            double J[2][2] = {{r[OR_J], r[OR_J + 1]}, {r[OR_J + 2], r[OR_J + 3]}}, Ji[2][2];
+            if (!inv2(J, Ji)) break;
+            const double dx = Ji[0][0] * rhs0 + Ji[0][1] * rhs1, dy = Ji[1][0] * rhs0 + Ji[1][1] * rhs1;
+            double lam = 1.0;
+            int accepted = 0;
+            for (int h = 0; h <= 12; ++h, lam *= 0.5) {
+                double cand[2] = {xy[0] + lam * dx, xy[1] + lam * dy}, rc;
+                if (newton_eval(o, p, target, cand, trial, &rc) && rc < res) {
+                    xy[0] = cand[0];
+                    xy[1] = cand[1];
+                    res = rc;
+                    double* t = cur;
+                    cur = trial;
+                    trial = t;
+                    accepted = 1;
+                    break;
+                }
+            }
+            if (!accepted) break;
         }
-        double rhs0 = dot3(r + OR_V1, d), rhs1 = dot3(r + OR_V2, d);
-        double J[2][2] = {{r[OR_J], r[OR_J + 1]}, {r[OR_J + 2], r[OR_J + 3]}}, Ji[2][2];
-        if (!inv2(J, Ji)) break;
-        xy[0] += Ji[0][0] * rhs0 + Ji[0][1] * rhs1;
-        xy[1] += Ji[1][0] * rhs0 + Ji[1][1] * rhs1;
     }
     free(buf);
     return ret;
@@ -1044,7 +1084,7 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                         if (flags & OR_FIELD_EXACT) {
                             double xy[2] = {l0 * R[0]->x + l1 * R[1]->x + l2 * R[2]->x,
                                             l0 * R[0]->y + l1 * R[1]->y + l2 * R[2]->y};
-                            if (or_newton(o, p, x, xy, nbuf) >= 0) {
+                            if (or_newton(o, p, x, xy, 8.0 * h, nbuf) >= 0) {
                                 memcpy(F, nbuf + OR_F, sizeof(F));
                                 psi = nbuf[OR_PSI];
                                 done = 1;

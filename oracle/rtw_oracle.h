@@ -67,7 +67,8 @@ enum {
 
 /* Field flags */
 #define OR_FIELD_PO 1       /* 1-D fan: physical-optics correction around in-plane folds    */
-#define OR_FIELD_EXACT 2    /* evaluate every hit by Newton on the exact trace (O3)         */
+#define OR_FIELD_EXACT 2    /* evaluate every hit by Newton on the exact trace (O3); square
+                               grids: root within 8 h of the interpolated impact point      */
 #define OR_FIELD_EXACT_FOLDS 4 /* 1-D fan: O3 only for directions within 2 deg of an in-plane
                                   fold of the hit's order (rainbow windows), O2 elsewhere    */
 
@@ -107,8 +108,10 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                       int nthreads, int64_t* newton_fail);
 
 /* Newton on the exact trace: finds the ray of order p whose exit direction is target, from the
- * seed impact point xy (2).  Returns iterations used, or -1 if it did not converge. */
-int or_newton(const or_object* o, int p, const double target[3], double* xy, double* rec);
+ * seed impact point xy (2), with steps halved until the residual decreases; the root must lie
+ * within rmax of the seed (rmax <= 0: no bound).  Returns iterations used, or -1 if it did not
+ * converge. */
+int or_newton(const or_object* o, int p, const double target[3], double* xy, double rmax, double* rec);
 
 #ifdef __cplusplus
 }

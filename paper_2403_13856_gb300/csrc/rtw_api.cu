@@ -25,6 +25,7 @@ using rtw::host::align_up;
 using rtw::host::cuda_fail;
 using rtw::host::fail;
 using rtw::host::ObjHost;
+using rtw::host::newton_counter;
 using rtw::host::status_word;
 
 namespace {
@@ -53,17 +54,24 @@ int fail(int code, const char* fmt, ...)
 
 int cuda_fail(cudaError_t e, const char* what) { return fail(RTW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e)); }
 
+// 16 bytes per device: the status word, then (at byte 8) the Newton failure counter
 unsigned int* status_word(int dev)
 {
     std::lock_guard<std::mutex> lk(g_status_mu);
     if ((int)g_status.size() <= dev) g_status.resize(dev + 1, nullptr);
     if (!g_status[dev]) {
         unsigned int* p = nullptr;
-        if (cudaMalloc(&p, sizeof(unsigned int)) != cudaSuccess) return nullptr;
-        cudaMemset(p, 0, sizeof(unsigned int));
+        if (cudaMalloc(&p, 16) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, 16);
         g_status[dev] = p;
     }
     return g_status[dev];
+}
+
+unsigned long long* newton_counter(int dev)
+{
+    unsigned int* p = status_word(dev);
+    return p ? reinterpret_cast<unsigned long long*>(p + 2) : nullptr;
 }
 
 void fill_objdev(const ObjHost& o, ObjDev& d)
@@ -181,7 +189,8 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
 
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, bool per_order, double* out, unsigned char* mask_out, const GridWs& w,
-                   int classify_block, unsigned int* status, cudaStream_t s)
+                   int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
+                   cudaStream_t s)
 {
     const int np = st.np;
     const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
@@ -199,6 +208,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
         a.out = out + out_obj * (size_t)g0;
         a.mask = w.mask_words;
         a.status = status;
+        a.nfail = nfail;
         RTW_CUDA(launch_grid_cells(d_objs + g0, gn, np, g.windowed, win, w.cells, s));
         GridBatch b;
         b.cells = w.cells;
@@ -218,7 +228,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
         b.ndir = ndir;
         b.nout = nout;
         RTW_CUDA(launch_field_grid(a, b, dirs->n_theta, dirs->n_phi, w.tab, w.big, w.nbig, w.big_cap, w.hit_tri,
-                                   w.hit_dir, w.nhit, w.hit_cap, classify_block, s));
+                                   w.hit_dir, w.nhit, w.hit_cap, classify_block, newton, s));
         if (mask_out)
             RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir, 1,
                                           dirs->n_theta, dirs->n_phi, 0.0, 0.0, s));
@@ -522,8 +532,8 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     rtw_rays* rays = const_cast<rtw_rays*>(rays_c);
     if (!rays || !dirs || !field_out) return fail(RTW_ERR_ARG, "rtw_field: null pointer");
     if (mode != RTW_DENSE && mode != RTW_NEWTON) return fail(RTW_ERR_ARG, "rtw_field: mode %d", mode);
-    if (mode == RTW_NEWTON && rays->grid != RTW_GRID_FAN)
-        return fail(RTW_ERR_UNSUPPORTED, "rtw_field: RTW_NEWTON on square grids");
+    if (mode == RTW_NEWTON && (flags & RTW_FIELD_NEAR_FOLDS) && rays->grid != RTW_GRID_FAN)
+        return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_NEAR_FOLDS needs a fan grid");
     cudaStream_t s = (cudaStream_t)stream;
     const bool per_order = (flags & RTW_FIELD_PER_ORDER) != 0;
     const bool po = (flags & RTW_FIELD_PO) != 0;
@@ -564,7 +574,8 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         RTW_CUDA(cudaMemsetAsync(field_out, 0, sizeof(double) * 4 * (size_t)nout * (size_t)ndir * (size_t)rays->nobj, s));
         RTW_CUDA(rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, w.tab, s));
         return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, per_order,
-                                         (double*)field_out, mask_out, w, 0, status, s);
+                                         (double*)field_out, mask_out, w, 0, newton, status,
+                                         newton_counter(rays->device), s);
     }
     // fan: workspace of mask words, PO windows and scratch
     const long long nfan = rays->objs[0].nx;
@@ -602,6 +613,7 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         a.out = (double*)((char*)field_out + out_bytes_obj * (size_t)oi);
         a.mask = mask_words;
         a.status = status;
+        a.nfail = newton_counter(rays->device);
         const ObjDev& o = rays->objs[(size_t)oi];
         RTW_CUDA(rtw::launch_field_fan(a, o.nx, rays->fan_phi, dirs->n_theta, dirs->alpha0, dirs->dalpha, d_win,
                                        d_nwin, d_po, ap_cap, po ? 1 : 0, newton, s));
@@ -609,6 +621,21 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
             RTW_CUDA(rtw::launch_finalize_mask(mask_words, mask_out + (size_t)oi * (size_t)ndir, rays->d_objs + oi, 1,
                                                ndir, 0, dirs->n_theta, 0, dirs->alpha0, dirs->dalpha, s));
     }
+    return RTW_OK;
+}
+
+int rtw_newton_failures(void* stream, int64_t* count)
+{
+    if (!count) return fail(RTW_ERR_ARG, "rtw_newton_failures: null pointer");
+    int dev = 0;
+    RTW_CUDA(cudaGetDevice(&dev));
+    RTW_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned long long* p = newton_counter(dev);
+    if (!p) return fail(RTW_ERR_CUDA, "rtw_newton_failures: counter");
+    unsigned long long v = 0;
+    RTW_CUDA(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
+    RTW_CUDA(cudaMemset(p, 0, sizeof(v)));
+    *count = (int64_t)v;
     return RTW_OK;
 }
 

@@ -126,7 +126,8 @@ int enqueue(rtw_batch* b, const rtw_batch_params* bp, const rtw_dirs* dirs, bool
         int rc = rtw::host::grid_field_run(b->objs.data() + c.first, b->d_objs + c.first, c.count, st, c.plan, dirs,
                                            per_order, out + 4 * (size_t)nout * (size_t)ndir * (size_t)c.first,
                                            mask_out ? mask_out + (size_t)ndir * (size_t)c.first : nullptr, w,
-                                           bp->classify_block, status, q);
+                                           bp->classify_block, bp->mode == RTW_NEWTON ? 1 : 0, status,
+                                           rtw::host::newton_counter(b->device), q);
         if (rc != RTW_OK) return rc;
         if (timing) RTW_CUDA(cudaEventRecord(b->ev[(size_t)e++], q));
     }
@@ -156,6 +157,8 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: trace_variant %d", bp->trace_variant);
     if (bp->classify_block != 0 && bp->classify_block != 64 && bp->classify_block != 128 && bp->classify_block != 256)
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: classify_block %d", bp->classify_block);
+    if (bp->mode != RTW_DENSE && bp->mode != RTW_NEWTON)
+        return fail(RTW_ERR_ARG, "rtw_far_field_batch: mode %d", bp->mode);
     if (bp->chunk_ray_orders < 0 || bp->trace_ctas_per_sm < 0)
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: negative chunk bound or CTAs per SM");
     cudaStream_t s = (cudaStream_t)stream;
@@ -229,6 +232,7 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
     put(key, bp->trace_variant);
     put(key, bp->trace_ctas_per_sm);
     put(key, bp->classify_block);
+    put(key, bp->mode);
     put(key, dirs->n_theta);
     put(key, dirs->n_phi);
     put(key, flags);

@@ -443,10 +443,89 @@ __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBa
     }
 }
 
+struct CaptureSink {
+    int want;
+    bool got;
+    ExitWave w;
+    __device__ void emit(int p, const ExitWave& ew)
+    {
+        if (p == want) {
+            w = ew;
+            got = true;
+        }
+    }
+};
+
+// Residual |t - s_p(x, y)| of the exact double-precision trace; the exit wave of order p in cs.
+__device__ __forceinline__ bool newton_eval(const ObjDev& o, int p, const double t[3], double x, double y,
+                                            CaptureSink& cs, FarRecord& r, double& res)
+{
+    cs.want = p;
+    cs.got = false;
+    trace_ray<double, true>(o, x, y, p, cs);
+    if (!cs.got || !far_record(o, cs.w, r)) return false;
+    const double d0 = t[0] - r.s[0], d1 = t[1] - r.s[1], d2 = t[2] - r.s[2];
+    res = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    return true;
+}
+
+// Newton steps on the exact double-precision trace in the impact point (x, y) until the exit
+// direction of order p equals the unit target t.  The Jacobian ds/d(x, y) in the exit basis
+// (e_perp, e_perp x s) is the exit wavefront-curvature matrix times the transfer matrix the trace
+// carries (J = Q' T).  A step is halved (at most 12 times) until the new point leaves in order p
+// with a smaller residual.  Converged when |s - t| < 1e-11 within 30 steps and the root lies
+// within rmax of the seed (rmax <= 0: anywhere), so that the ray found is the branch the seed
+// stands for.
+__device__ bool newton_point(const ObjDev& o, int p, const double t[3], double x, double y, double rmax,
+                             FarRecord& out)
+{
+    const double x0 = x, y0 = y;
+    CaptureSink cs;
+    FarRecord r;
+    double res;
+    if (!newton_eval(o, p, t, x, y, cs, r, res)) return false;
+    for (int it = 0; it < 30; ++it) {
+        if (res < 1e-11) {
+            if (rmax > 0.0 && hypot(x - x0, y - y0) > rmax) return false;
+            out = r;
+            return true;
+        }
+        const ExitWave& w = cs.w;
+        const double d[3] = {t[0] - r.s[0], t[1] - r.s[1], t[2] - r.s[2]};
+        const double J00 = w.q11 * w.t11 + w.q12 * w.t21, J01 = w.q11 * w.t12 + w.q12 * w.t22;
+        const double J10 = w.q12 * w.t11 + w.q22 * w.t21, J11 = w.q12 * w.t12 + w.q22 * w.t22;
+        const double v2[3] = {w.ep[1] * w.k[2] - w.ep[2] * w.k[1], w.ep[2] * w.k[0] - w.ep[0] * w.k[2],
+                              w.ep[0] * w.k[1] - w.ep[1] * w.k[0]};
+        const double r0 = w.ep[0] * d[0] + w.ep[1] * d[1] + w.ep[2] * d[2];
+        const double r1 = v2[0] * d[0] + v2[1] * d[1] + v2[2] * d[2];
+        const double det = J00 * J11 - J01 * J10;
+        if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
+        const double dx = (J11 * r0 - J01 * r1) / det, dy = (J00 * r1 - J10 * r0) / det;
+        double lam = 1.0;
+        bool accepted = false;
+        for (int h = 0; h <= 12; ++h, lam *= 0.5) {
+            CaptureSink cc;
+            FarRecord rc;
+            double resc;
+            if (newton_eval(o, p, t, x + lam * dx, y + lam * dy, cc, rc, resc) && resc < res) {
+                x += lam * dx;
+                y += lam * dy;
+                cs = cc;
+                r = rc;
+                res = resc;
+                accepted = true;
+                break;
+            }
+        }
+        if (!accepted) return false;
+    }
+    return false;
+}
+
 // Phase 3: one thread per (triangle, direction) pair: the double-precision rule for close calls,
 // then the barycentric weights of the central projection, F, Psi and F e^{i Psi}.
 __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBatch b, int nt, int nph,
-                                                             const double* __restrict__ tab, HitArgs h)
+                                                             const double* __restrict__ tab, HitArgs h, int newton)
 {
     const unsigned int n = min(*h.n, h.cap);
     const double* ctab = tab;
@@ -518,7 +597,27 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBa
         double Fi[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) Fi[k] = l0 * F[0][k] + l1 * F[1][k] + l2 * F[2][k];
-        const double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
+        double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
+        if (newton) {
+            // exact ray of this branch from the interpolated impact point (the same weights)
+            double xs = 0.0, ys = 0.0;
+            const double lw[3] = {l0, l1, l2};
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                double xv, yv;
+                ray_origin(*c.o, g.id[v], xv, yv);
+                xs += lw[v] * xv;
+                ys += lw[v] * yv;
+            }
+            FarRecord fr;
+            if (newton_point(*c.o, p, x, xs, ys, 8.0 * c.o->h, fr)) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) Fi[k] = fr.F[k];
+                ps = fr.psi;
+            } else if (a.nfail) {
+                atomicAdd(a.nfail, 1ull);
+            }
+        }
         const double eth[3] = {ct * cp, ct * sp, -sth};
         const double eph[3] = {-sp, cp, 0.0};
         double* dst = a.out + (((long long)c.orel * b.ndir + dk) * b.nout + (a.per_order ? p : 0)) * 4;
@@ -802,19 +901,6 @@ __global__ void __launch_bounds__(256) fan_po_kernel(FieldArgs a, double efx, do
 // the interpolated seed.  The derivative d alpha / d b comes from the transfer matrix carried
 // through the trace: d s = Q' T (e_x, e_y) db in the exit basis (e_perp, e_perp x s).  At most 40
 // steps (quadratic convergence takes 3 to 6), stop at |d alpha| < 1e-13.
-struct CaptureSink {
-    int want;
-    bool got;
-    ExitWave w;
-    __device__ void emit(int p, const ExitWave& ew)
-    {
-        if (p == want) {
-            w = ew;
-            got = true;
-        }
-    }
-};
-
 __device__ bool newton_fan(const ObjDev& o, int p, double efx, double efy, double alpha_t, double b, FarRecord& out)
 {
     for (int it = 0; it < 40; ++it) {
@@ -918,7 +1004,7 @@ __global__ void __launch_bounds__(256) field_fan_kernel(FieldArgs a, long long n
                     for (int c = 0; c < 6; ++c) F[c] = fr.F[c];
                     ps = fr.psi;
                 } else {
-                    atomicOr(a.status, kStatusTimeout);
+                    if (a.nfail) atomicAdd(a.nfail, 1ull);
                 }
             }
             double d[3], eth[3], eph[3];
@@ -997,7 +1083,7 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, int nph, const double* tab,
                               unsigned long long* big, unsigned int* nbig, unsigned int big_cap,
                               unsigned long long* hit_tri, unsigned int* hit_dir, unsigned int* nhit,
-                              unsigned int hit_cap, int classify_block, cudaStream_t s)
+                              unsigned int hit_cap, int classify_block, int newton, cudaStream_t s)
 {
     if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
@@ -1012,7 +1098,7 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, in
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     field_grid_big_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, big, nbig, big_cap, h);
-    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, h);
+    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, h, newton);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,8 @@ int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 int cuda_fail(cudaError_t e, const char* what);
 // device word of error bits raised by kernels (allocated once per device)
 unsigned int* status_word(int dev);
+// device counter of Newton refinements that did not converge (next to the status word)
+unsigned long long* newton_counter(int dev);
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void fill_objdev(const ObjHost& o, ObjDev& d);
@@ -71,9 +73,11 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
 // are the same table on the host and the device.  Adds into out, which the caller cleared:
 // [objects][directions][nout][4] doubles.  mask_out (may be null): [objects][directions] bytes.
 // The direction tables in w must have been filled (launch_dir_tables) on the same stream.
+// newton = 1 replaces every interpolated hit by the exact ray found by Newton steps.
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, bool per_order, double* out, unsigned char* mask_out, const GridWs& w,
-                   int classify_block, unsigned int* status, cudaStream_t s);
+                   int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
+                   cudaStream_t s);
 
 }  // namespace host
 }  // namespace rtw

@@ -46,7 +46,8 @@ struct FieldArgs {
     int per_order;
     double* out;           // [directions][nout][4]
     unsigned int* mask;    // [directions] scratch words
-    unsigned int* status;
+    unsigned int* status;  // error bits (may be null where no kernel of the launch can raise one)
+    unsigned long long* nfail;  // Newton refinements that did not converge (may be null without Newton)
 };
 
 // message returned by rtw_last_error() on the calling thread
@@ -70,7 +71,7 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s);
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, int nph, const double* tab,
                               unsigned long long* big, unsigned int* nbig, unsigned int big_cap,
                               unsigned long long* hit_tri, unsigned int* hit_dir, unsigned int* nhit,
-                              unsigned int hit_cap, int classify_block, cudaStream_t s);
+                              unsigned int hit_cap, int classify_block, int newton, cudaStream_t s);
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
                              double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
                              int newton, cudaStream_t s);

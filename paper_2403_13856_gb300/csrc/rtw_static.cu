@@ -184,7 +184,8 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     a.per_order = (flags & RTW_FIELD_PER_ORDER) ? 1 : 0;
     a.out = static_cast<double*>(field_out);
     a.mask = mask_words;
-    a.status = nullptr;
+    a.status = nullptr;  // no kernel of the plain fan path raises an error bit
+    a.nfail = nullptr;
     if ((e = rtw::launch_field_fan(a, R_, tp->fan_phi, (int)ndir, dirs->alpha0, dirs->dalpha, nullptr, nullptr,
                                    nullptr, 0, 0, 0, s)) != cudaSuccess)
         return set_error(RTW_ERR_CUDA, cudaGetErrorString(e));

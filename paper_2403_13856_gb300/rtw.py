@@ -58,7 +58,7 @@ class rtw_batch_params(ctypes.Structure):
     _fields_ = [("p_max", ctypes.c_int), ("precision", ctypes.c_int), ("n_rays", ctypes.c_void_p),
                 ("chunk_ray_orders", ctypes.c_int64), ("trace_variant", ctypes.c_int),
                 ("trace_ctas_per_sm", ctypes.c_int), ("classify_block", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("mode", ctypes.c_int)]
 
 
 TRACE_VARIANTS = 5
@@ -89,6 +89,7 @@ def lib():
             "rtw_batch_times": ([p, p, p], i),
             "rtw_destroy_batch": ([p], None),
             "rtw_sync_status": ([p], i),
+            "rtw_newton_failures": ([p, p], i),
             "rtw_status_string": ([i], ctypes.c_char_p),
             "rtw_last_error": ([], ctypes.c_char_p),
             "rtw_version": ([], ctypes.c_char_p),
@@ -251,7 +252,7 @@ class Batch:
 
 
 def batch_params(n_rays, p_max=4, precision=RTW_FP64, chunk_ray_orders=0, trace_variant=0, trace_ctas_per_sm=0,
-                 classify_block=0, use_graph=0, timing=0):
+                 classify_block=0, use_graph=0, timing=0, mode=RTW_DENSE):
     """Options of rtw_far_field_batch; n_rays is kept alive on the returned structure."""
     bp = rtw_batch_params()
     arr = (ctypes.c_int64 * len(n_rays))(*[int(x) for x in n_rays])
@@ -259,7 +260,7 @@ def batch_params(n_rays, p_max=4, precision=RTW_FP64, chunk_ray_orders=0, trace_
     bp.n_rays = ctypes.cast(arr, ctypes.c_void_p)
     bp.p_max, bp.precision, bp.chunk_ray_orders = p_max, precision, int(chunk_ray_orders)
     bp.trace_variant, bp.trace_ctas_per_sm, bp.classify_block = trace_variant, trace_ctas_per_sm, classify_block
-    bp.use_graph, bp.timing = int(use_graph), int(timing)
+    bp.use_graph, bp.timing, bp.mode = int(use_graph), int(timing), int(mode)
     return bp
 
 
@@ -273,6 +274,12 @@ def rtw_far_field_batch(obj: Object, params: rtw_batch_params, dirs: rtw_dirs, o
 
 def rtw_sync_status(stream=None):
     _check(lib().rtw_sync_status(_stream_ptr(stream)))
+
+
+def rtw_newton_failures(stream=None) -> int:
+    n = ctypes.c_int64()
+    _check(lib().rtw_newton_failures(_stream_ptr(stream), ctypes.byref(n)))
+    return n.value
 
 
 def rtw_version() -> str:

@@ -119,6 +119,27 @@ def test_batch_mixed_precision_vs_oracle(rtw, oracle_mod):
     assert worst <= 1e-4
 
 
+def test_batch_newton_vs_oracle_exact(rtw, oracle_mod):
+    """mode RTW_NEWTON in the batch: 6 drops, every hit refined on the exact trace, against the
+    oracle's exact branch sum per object."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(6, **SMALL)
+    obj = make_batch(rtw, specs)
+    p_max, nt, nph = 4, 32, 64
+    rtw.rtw_newton_failures()
+    out, mask, _ = run_batch(rtw, obj, rays, p_max, nt, nph, flags=rtw.RTW_FIELD_PER_ORDER, mode=rtw.RTW_NEWTON)
+    gfail = rtw.rtw_newton_failures()
+    got, gm = out.cpu().numpy(), mask.cpu().numpy()
+    total_fail = 0
+    for i, s in enumerate(specs):
+        o = oracle_mod.Object(s["a"], s["b"], s["c"], quat=s["quat"], m=s["m"], wavelength=s["wavelength"])
+        ref, rm, _, nfail = o.field_grid(p_max, nt, nph, n_target=int(rays[i]), flags=oracle_mod.FIELD_EXACT)
+        total_fail += nfail
+        compare(got[i], oracle_mod.complex_field(ref), gm[i], rm)
+    assert gfail == total_fail
+
+
 def test_batch_argument_errors(rtw):
     from paper_2403_13856_gb300 import workloads as W
 
@@ -160,3 +181,23 @@ def test_batch_full_size_sampled_objects(rtw, oracle_mod):
         err = np.abs(got[k] - ref).max()
         print(f"object {i} ({rays[i]} rays, a={specs[i]['a']:.1f} um): max |dF| / max |F| = {err / scale:.2e}")
         assert err <= 1e-6 * scale
+
+
+def test_autotuner_on_gpu_picks_valid_options(rtw, tmp_path):
+    """The autotuner times every candidate through the library on a sample and caches the choice;
+    the tuned options reproduce the default run's field."""
+    from paper_2403_13856_gb300 import autotune as A
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(24, **SMALL)
+    p_max, nt, nph = 4, 32, 64
+    path = str(tmp_path / "tune.json")
+    best = A.tune(specs, rays, p_max, rtw.RTW_FP64, nt, nph, cache_path=path, budget_ray_orders=200_000, reps=1)
+    assert best["trace_variant"] in A.TRACE_VARIANTS and best["classify_block"] in A.CLASSIFY_BLOCKS
+    entry = list(A.load(path).values())[0]
+    assert all(v > 0 for v in entry["ms"].values())
+    obj = make_batch(rtw, specs)
+    ref, rm, _ = run_batch(rtw, obj, rays, p_max, nt, nph)
+    got, gm, _ = run_batch(rtw, obj, rays, p_max, nt, nph, **best)
+    assert torch.equal(gm, rm)
+    assert (got - ref).abs().max().item() <= 1e-12 * ref.abs().max().item()

@@ -180,14 +180,14 @@ def test_field_fan_ragged_and_negative_angles(rtw, oracle_mod):
     compare_fields(got, oracle_mod.complex_field(ref), gm, rm)
 
 
-def grid_field(rtw, spec, jones, p_max, nt, nph, n_rays=0, spacing=0.0, window=None):
+def grid_field(rtw, spec, jones, p_max, nt, nph, n_rays=0, spacing=0.0, window=None, mode=0):
     obj = gpu_object(rtw, spec, jones)
     tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=n_rays, spacing=spacing)
     rays = rtw.rtw_trace(obj, tp)
     d = rtw.dirs_grid(nt, nph, window)
     out = torch.zeros((nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
     mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
-    rtw.rtw_field(rays, d, out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_field(rays, d, out, mask, mode=mode, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_sync_status()
     return out.cpu().numpy(), mask.cpu().numpy(), obj, rays
 
@@ -202,6 +202,42 @@ def test_field_grid_ellipsoid_reduced(rtw, oracle_mod):
     ref, rm, hits, _ = o.field_grid(5, 96, 192, n_target=30_000)
     assert hits > 10000
     compare_fields(got, oracle_mod.complex_field(ref), gm, rm)
+
+
+@pytest.mark.parametrize("jones", [(1.0, 0.0), (0.3, 0.7j)])
+def test_field_grid_newton_vs_oracle_exact(rtw, oracle_mod, jones):
+    """RTW_NEWTON on a square grid: every hit of the tilted ellipsoid (about 2e4 rays, orders
+    0..5, 64 x 128 directions) replaced by the exact ray; against the oracle's exact branch sum
+    (O3) on the same hits."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    rtw.rtw_newton_failures()
+    got, gm, _, _ = grid_field(rtw, W.ELLIPSOID, jones, 5, 64, 128, n_rays=20_000, mode=rtw.RTW_NEWTON)
+    gfail = rtw.rtw_newton_failures()
+    o = oracle_object(oracle_mod, W.ELLIPSOID, jones)
+    ref, rm, hits, nfail = o.field_grid(5, 64, 128, n_target=20_000, flags=oracle_mod.FIELD_EXACT)
+    print(f"grid Newton: {hits} hits, {nfail} not converged (oracle), {gfail} (GPU)")
+    assert hits > 5000 and gfail == nfail
+    compare_fields(got, oracle_mod.complex_field(ref), gm, rm)
+
+
+def test_field_grid_newton_removes_interpolation_error(rtw, oracle_mod):
+    """The exact branch sum does not depend on the ray grid: Newton fields from grids of 1e4 and
+    4e4 rays agree far better than the interpolated fields do (sphere, orders 0..2)."""
+    spec = dict(a=8.0, b=8.0, c=8.0, quat=(1.0, 0.0, 0.0, 0.0), m=1.333, wavelength=0.6328)
+    f = {}
+    for n in (10_000, 40_000):
+        for mode in (rtw.RTW_DENSE, rtw.RTW_NEWTON):
+            out, m, _, _ = grid_field(rtw, spec, (1.0, 0.0), 2, 48, 96, n_rays=n, mode=mode)
+            f[n, mode] = (out.sum(axis=1), m)
+    # directions where the two grids see the same branches (all but a few next to masked cells)
+    both = (f[10_000, 0][1] == 0) & (f[40_000, 0][1] == 0)
+    d_dense = np.abs(f[10_000, 0][0] - f[40_000, 0][0])[both].max(axis=-1)
+    d_newton = np.abs(f[10_000, 1][0] - f[40_000, 1][0])[both].max(axis=-1)
+    scale = np.abs(f[40_000, 1][0]).max()
+    q_dense, q_newton = np.quantile(d_dense, 0.9) / scale, np.quantile(d_newton, 0.9) / scale
+    print(f"grid change 1e4 -> 4e4 rays, 90th percentile |dF| / max|F|: dense {q_dense:.2e}, Newton {q_newton:.2e}")
+    assert q_newton < 1e-9 and q_dense > 1e-5
 
 
 def test_field_grid_small_sphere_edge_cases(rtw, oracle_mod):
