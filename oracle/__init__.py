@@ -19,6 +19,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rtw_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c")]
+_HDRS = [os.path.join(_HERE, "rtw_oracle.h"), os.path.join(_HERE, "mlp_oracle.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # record layout (mirrors the enum in rtw_oracle.h)
@@ -31,12 +33,10 @@ FIELD_PO, FIELD_EXACT, FIELD_EXACT_FOLDS = 1, 2, 4
 
 def build(force: bool = False) -> str:
     """Compiles the oracle into ``oracle/liboracle.so`` (plain C, -ffp-contract=off)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "rtw_oracle.h"))
-    ):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS + _HDRS):
         tmp = _LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-fopenmp", "-o", tmp, _SRC, "-lm"]
+               "-fopenmp", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -68,6 +68,19 @@ def lib():
         L.or_field_grid.restype = i64
         L.or_newton.argtypes = [p, i, p, p, d, p]
         L.or_newton.restype = i
+        L.om_gelu.argtypes = [d]
+        L.om_gelu.restype = d
+        L.om_gelu_grad.argtypes = [d]
+        L.om_gelu_grad.restype = d
+        L.om_round_bf16.argtypes = [d]
+        L.om_round_bf16.restype = d
+        L.om_features.argtypes = [p, p, p]
+        L.om_xy_to_uv.argtypes = [p, d, d, p]
+        L.om_uv_to_xy.argtypes = [p, p, p, p]
+        L.om_forward.argtypes = [p, p, i64, i, p]
+        L.om_loss_grad.argtypes = [p, p, p, p, i64, d, i, p]
+        L.om_loss_grad.restype = d
+        L.om_adam.argtypes = [p, p, p, p, i64, i, d, d, d, d]
         _lib = L
     return _lib
 
@@ -160,3 +173,68 @@ class Object:
 def complex_field(out):
     """(..., 4) -> complex (..., 2) = (F_theta, F_phi)."""
     return out[..., 0::2] + 1j * out[..., 1::2]
+
+
+# ------------------------------------------------------------------------------------------------
+# learned inverse-map proposal (mlp_oracle.c)
+# ------------------------------------------------------------------------------------------------
+MLP_IN, MLP_H, MLP_OUT, MLP_HEADS = 16, 128, 16, 4
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + 2 * (MLP_H * MLP_H + MLP_H) + MLP_OUT * MLP_H + MLP_OUT
+
+
+def mlp_features(obj: Object, s):
+    s = np.ascontiguousarray(np.atleast_2d(s), dtype=np.float64)
+    out = np.zeros((s.shape[0], MLP_IN))
+    for i in range(s.shape[0]):
+        lib().om_features(obj.handle, _ptr(s[i]), _ptr(out[i]))
+    return out
+
+
+def xy_to_uv(obj: Object, x, y):
+    uv = np.zeros(2)
+    lib().om_xy_to_uv(obj.handle, float(x), float(y), _ptr(uv))
+    return uv
+
+
+def uv_to_xy(obj: Object, uv):
+    uv = np.ascontiguousarray(uv, dtype=np.float64)
+    x, y = ctypes.c_double(), ctypes.c_double()
+    lib().om_uv_to_xy(obj.handle, _ptr(uv), ctypes.byref(x), ctypes.byref(y))
+    return x.value, y.value
+
+
+def mlp_forward(theta, x, bf16=False):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, MLP_IN)
+    y = np.zeros((x.shape[0], MLP_OUT))
+    lib().om_forward(_ptr(theta), _ptr(x), x.shape[0], int(bf16), _ptr(y))
+    return y
+
+
+def mlp_loss_grad(theta, x, target, valid, beta=0.1, bf16=False):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, MLP_IN)
+    target = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 2)
+    valid = np.ascontiguousarray(valid, dtype=np.uint8)
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().om_loss_grad(_ptr(theta), _ptr(x), _ptr(target), _ptr(valid), x.shape[0], float(beta), int(bf16),
+                              _ptr(g))
+    return loss, g
+
+
+def mlp_adam(theta, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on theta, m, v (float64 arrays)."""
+    lib().om_adam(_ptr(theta), _ptr(m), _ptr(v), _ptr(np.ascontiguousarray(grad, dtype=np.float64)), theta.size,
+                  int(t), float(lr), float(b1), float(b2), float(eps))
+
+
+def gelu(z):
+    return lib().om_gelu(float(z))
+
+
+def gelu_grad(z):
+    return lib().om_gelu_grad(float(z))
+
+
+def round_bf16(v):
+    return lib().om_round_bf16(float(v))

@@ -133,6 +133,23 @@ static double wrap_angle(double a)
 
 int or_object_size(void) { return (int)sizeof(or_object); }
 
+void or_object_frame(const or_object* o, double* R9, double* semi, double* center, double* S4, double* m)
+{
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            if (R9) R9[3 * i + j] = o->R[i][j];
+        if (semi) semi[i] = o->semi[i];
+        if (center) center[i] = o->center[i];
+    }
+    if (S4) {
+        S4[0] = o->S[0][0];
+        S4[1] = o->S[0][1];
+        S4[2] = o->S[1][0];
+        S4[3] = o->S[1][1];
+    }
+    if (m) *m = o->m;
+}
+
 int or_make_object(const double* p, or_object* o)
 {
     memset(o, 0, sizeof(*o));

@@ -83,6 +83,9 @@ double or_fan_halfwidth(const or_object* o, double fan_phi);
 void or_square_grid(const or_object* o, int64_t n_target, double h_in, double* h, int64_t* nx,
                     int64_t* ny, double* x0, double* y0);
 double or_caustic_cap(const or_object* o);
+/* Geometry of the object: rotation body -> lab (row-major 9), semi-axes, centre, projected
+ * ellipse S (row-major 4) and index m; any pointer may be NULL. */
+void or_object_frame(const or_object* o, double* R9, double* semi, double* center, double* S4, double* m);
 
 /* Traces one incident ray at impact point (x, y); out has (pmax+1)*OR_NFIELD doubles.
  * *p_inside receives the power still travelling inside after the last interaction.
