@@ -244,6 +244,53 @@ int rtw_batch_times(const rtw_batch* b, double* trace_ms, double* field_ms);
 
 void rtw_destroy_batch(rtw_batch* b);
 
+/* ---- learned proposal of entry points ----
+ * The paper has no learned component.  This part proposes, for an exit direction s and order p,
+ * where a ray must enter the object to leave along s, so that Newton steps on the exact trace
+ * (Eq. WavefrontEqVec gives their Jacobian) can find the ray without tracing a dense grid.
+ * One network per order: 16 features -> 3 hidden layers of 128 (GELU, tanh form) -> 16 outputs.
+ * Features: s (3), the rotation body -> lab of the object (9, row-major), its semi-axes over the
+ * largest (3), m - 1.  Outputs: 4 candidate entry points uv (outputs 2k, 2k+1) in unit-disk
+ * coordinates of the projected section (d = (x - cx, y - cy), S = L L^T the Cholesky factor of
+ * the projected ellipse, uv = L^T d), 4 logits (outputs 8..11), 4 unused.  Parameters per network
+ * (RTW_MLP_NPARAM floats): W1 (128 x 16), b1, W2 (128 x 128), b2, W3, b3, W4 (16 x 128), b4, each
+ * W row-major (out x in).  Products run on the tensor cores in bfloat16 with FP32 accumulation;
+ * the master parameters and Adam moments are FP32.  Feature rows X are bfloat16 (16 per row),
+ * passed as void*. */
+#define RTW_MLP_NPARAM 37264
+
+typedef struct rtw_mlp rtw_mlp;
+
+/* n_orders networks (orders 0..n_orders-1) with initial parameters init (host, n_orders x
+ * RTW_MLP_NPARAM floats, or NULL for zeros); Adam state zero.  Synchronous. */
+int rtw_mlp_create(int n_orders, const float* init, rtw_mlp** out);
+void rtw_mlp_destroy(rtw_mlp* m);
+/* Host copies of one network's parameters, Adam moments and step (any pointer may be NULL), and
+ * their restoration (checkpoint / resume).  Synchronous. */
+int rtw_mlp_get(const rtw_mlp* m, int order, float* theta, float* adam_m, float* adam_v, int64_t* step);
+int rtw_mlp_set(rtw_mlp* m, int order, const float* theta, const float* adam_m, const float* adam_v, int64_t step);
+
+/* Training samples from the exact FP64 trace: ray i enters object obj_index[i] (device int32) at
+ * unit-disk point uv[i] (device, n x 2 double); for every order p <= p_max, row p n + i of X
+ * (device, bf16, 16 per row) gets the features of its exit direction, T (device, 2 floats per row)
+ * the target uv and valid (device, uint8) whether order p leaves the object (0 for an index
+ * outside [0, count)).  Asynchronous. */
+int rtw_mlp_samples(const rtw_object* obj, const double* uv, const int32_t* obj_index, int64_t n, int p_max,
+                    void* X, float* T, uint8_t* valid, void* stream);
+/* Y (device, rows x 16 float) = network `order` applied to X.  Asynchronous. */
+int rtw_mlp_forward(const rtw_mlp* m, int order, const void* X, int64_t rows, float* Y, void* stream);
+/* Gradient of the mean loss over the valid rows into the network's gradient buffer: for each row
+ * the head nearest the target uv carries the squared distance, and beta times the softmax
+ * cross-entropy of the logits towards that head is added.  loss_out (device double, may be NULL)
+ * receives the loss.  Deterministic (fixed summation order).  Asynchronous. */
+int rtw_mlp_grad(rtw_mlp* m, int order, const void* X, const float* T, const uint8_t* valid, int64_t rows, float beta,
+                 double* loss_out, void* stream);
+/* Copies the gradient buffer (RTW_MLP_NPARAM floats) to grad (host or device).  Asynchronous. */
+int rtw_mlp_grad_get(const rtw_mlp* m, int order, float* grad, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr on the
+ * gradient grad (device, RTW_MLP_NPARAM floats) or, when NULL, the network's own.  Asynchronous. */
+int rtw_mlp_adam(rtw_mlp* m, int order, float lr, const float* grad, void* stream);
+
 /* ---- the fan path without allocation ----
  * The paper has no counterpart of this call: it serves programs that may not allocate device
  * memory themselves (a host application whose memory manager owns the device and forbids direct

@@ -79,6 +79,11 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                    int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s);
 
+// per-object feature table of the learned proposal
+void object_features(const ObjHost& o, ObjFeat& f);
+// bf16 weights of the network of one order
+MlpWeights mlp_weights(const rtw_mlp* m, int order);
+
 }  // namespace host
 }  // namespace rtw
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "rtw_internal.h"
+#include "rtw_mlp.cuh"
 
 namespace rtw {
 
@@ -75,6 +76,20 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, in
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
                              double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
                              int newton, cudaStream_t s);
+// learned proposal (rtw_mlp.cu)
+cudaError_t mlp_prepare_kernels();
+cudaError_t launch_mlp_forward(const MlpWeights& w, const __nv_bfloat16* X, long long rows, float* Y, cudaStream_t s);
+// forward with stored activations, loss, backward and weight gradients of one batch into grad;
+// part holds ceil(rows / 512) x kMlpParams floats
+cudaError_t launch_mlp_grad(const MlpWeights& w, const __nv_bfloat16* X, const float* T, const uint8_t* valid,
+                            long long rows, float beta, const MlpActs& acts, float* part, float* grad, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* grad, int update, float lr, float b1,
+                            float b2, float eps, float c1, float c2, __nv_bfloat16* w1, __nv_bfloat16* w2,
+                            __nv_bfloat16* w3, __nv_bfloat16* w4, __nv_bfloat16* w2t, __nv_bfloat16* w3t,
+                            __nv_bfloat16* w4t, cudaStream_t s);
+cudaError_t launch_mlp_samples(const ObjDev* objs, const ObjFeat* feat, int nobj, const double* uv, const int* oidx,
+                               long long n, int pmax, __nv_bfloat16* X, float* T, uint8_t* valid, cudaStream_t s);
+
 cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
                               cudaStream_t s);
 cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,

@@ -88,6 +88,15 @@ def lib():
             "rtw_batch_info": ([p, p, p, p], i),
             "rtw_batch_times": ([p, p, p], i),
             "rtw_destroy_batch": ([p], None),
+            "rtw_mlp_create": ([i, p, p], i),
+            "rtw_mlp_destroy": ([p], None),
+            "rtw_mlp_get": ([p, i, p, p, p, p], i),
+            "rtw_mlp_set": ([p, i, p, p, p, i64], i),
+            "rtw_mlp_samples": ([p, p, p, i64, i, p, p, p, p], i),
+            "rtw_mlp_forward": ([p, i, p, i64, p, p], i),
+            "rtw_mlp_grad": ([p, i, p, p, p, i64, ctypes.c_float, p, p], i),
+            "rtw_mlp_grad_get": ([p, i, p, p], i),
+            "rtw_mlp_adam": ([p, i, ctypes.c_float, p, p], i),
             "rtw_sync_status": ([p], i),
             "rtw_newton_failures": ([p, p], i),
             "rtw_status_string": ([i], ctypes.c_char_p),
@@ -274,6 +283,68 @@ def rtw_far_field_batch(obj: Object, params: rtw_batch_params, dirs: rtw_dirs, o
 
 def rtw_sync_status(stream=None):
     _check(lib().rtw_sync_status(_stream_ptr(stream)))
+
+
+RTW_MLP_NPARAM = 37264
+
+
+class MLP:
+    """rtw_mlp handle: one network per order (learned entry-point proposal)."""
+
+    def __init__(self, n_orders: int, init=None):
+        import numpy as np
+
+        self.handle = ctypes.c_void_p()
+        self.n_orders = n_orders
+        buf = None
+        if init is not None:
+            buf = np.ascontiguousarray(init, dtype=np.float32).reshape(n_orders, RTW_MLP_NPARAM)
+        _check(lib().rtw_mlp_create(n_orders, None if buf is None else buf.ctypes.data_as(ctypes.c_void_p),
+                                    ctypes.byref(self.handle)))
+
+    def get(self, order: int):
+        import numpy as np
+
+        th, m, v = (np.zeros(RTW_MLP_NPARAM, dtype=np.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        _check(lib().rtw_mlp_get(self.handle, order, th.ctypes.data_as(ctypes.c_void_p),
+                                 m.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
+                                 ctypes.byref(step)))
+        return th, m, v, step.value
+
+    def set(self, order: int, theta, m=None, v=None, step: int = 0):
+        import numpy as np
+
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (theta, m, v)]
+        ptrs = [None if a is None else a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+        _check(lib().rtw_mlp_set(self.handle, order, *ptrs, int(step)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.rtw_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+
+def rtw_mlp_samples(obj: Object, uv, obj_index, p_max, X, T, valid, stream=None):
+    _check(lib().rtw_mlp_samples(obj.handle, _ptr(uv), _ptr(obj_index), uv.shape[0], p_max, _ptr(X), _ptr(T),
+                                 _ptr(valid), _stream_ptr(stream)))
+
+
+def rtw_mlp_forward(mlp: MLP, order, X, Y, stream=None):
+    _check(lib().rtw_mlp_forward(mlp.handle, order, _ptr(X), X.shape[0], _ptr(Y), _stream_ptr(stream)))
+
+
+def rtw_mlp_grad(mlp: MLP, order, X, T, valid, beta=0.1, loss=None, stream=None):
+    _check(lib().rtw_mlp_grad(mlp.handle, order, _ptr(X), _ptr(T), _ptr(valid), X.shape[0], float(beta), _ptr(loss),
+                              _stream_ptr(stream)))
+
+
+def rtw_mlp_grad_get(mlp: MLP, order, grad, stream=None):
+    _check(lib().rtw_mlp_grad_get(mlp.handle, order, _ptr(grad), _stream_ptr(stream)))
+
+
+def rtw_mlp_adam(mlp: MLP, order, lr, grad=None, stream=None):
+    _check(lib().rtw_mlp_adam(mlp.handle, order, float(lr), _ptr(grad), _stream_ptr(stream)))
 
 
 def rtw_newton_failures(stream=None) -> int:

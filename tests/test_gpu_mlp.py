@@ -1,0 +1,192 @@
+"""The learned entry-point proposal on the GPU against the FP64 MLP oracle.
+
+Forward and gradient of the BF16 tensor-core kernels against the oracle run with the same
+bfloat16 rounding of weights, inputs and hidden activations (FP64 arithmetic otherwise): the
+remaining differences are FP32 accumulation and the bfloat16 rounding of the backward signals,
+bounded below.  Adam against the oracle's step on the same gradient; training samples against
+the oracle's trace and features; training determinism (checkpoint / resume bit-exact).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rtw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_13856_gb300 import build, rtw as R
+
+    build.build()
+    R.lib()
+    return R
+
+
+def seeded_params(n_orders, seed, scale=1.0):
+    """He-style initial parameters drawn from a seeded generator (float32)."""
+    import oracle as O
+
+    g = np.random.default_rng(seed)
+    th = np.zeros((n_orders, O.MLP_NPARAM), dtype=np.float32)
+    H, I, OUT = O.MLP_H, O.MLP_IN, O.MLP_OUT
+    for p in range(n_orders):
+        k = 0
+        for nout, nin in ((H, I), (H, H), (H, H), (OUT, H)):
+            th[p, k:k + nout * nin] = g.standard_normal(nout * nin) * scale * np.sqrt(2.0 / nin)
+            k += nout * nin
+            th[p, k:k + nout] = g.standard_normal(nout) * 0.1
+            k += nout
+    return th
+
+
+def bf16_rows(x):
+    t = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16)
+    return t, t.to(torch.float64).numpy()
+
+
+def test_forward_matches_oracle(rtw, oracle_mod):
+    th = seeded_params(2, 11)
+    mlp = rtw.MLP(2, th)
+    g = np.random.default_rng(12)
+    rows = 1000  # 15 full 64-row tiles and a ragged one
+    x = g.uniform(-1, 1, (rows, 16))
+    xb, xr = bf16_rows(x)
+    X = xb.cuda()
+    for order in (0, 1):
+        Y = torch.zeros((rows, 16), dtype=torch.float32, device="cuda")
+        rtw.rtw_mlp_forward(mlp, order, X, Y)
+        torch.cuda.synchronize()
+        ref = oracle_mod.mlp_forward(th[order].astype(np.float64), xr, bf16=True)
+        got = Y.cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref)
+        scale = np.abs(ref).max()
+        print(f"forward order {order}: max |dy| / max |y| = {err.max() / scale:.2e}, "
+              f"median {np.median(err) / scale:.2e}")
+        assert err.max() <= 2e-2 * scale and np.median(err) <= 1e-4 * scale
+
+
+def test_gradient_matches_oracle(rtw, oracle_mod):
+    """Gradient check of the hand-written backward kernels against the oracle's FP64 backprop."""
+    th = seeded_params(1, 21, scale=0.7)
+    mlp = rtw.MLP(1, th)
+    g = np.random.default_rng(22)
+    rows = 777
+    x = g.uniform(-1, 1, (rows, 16))
+    xb, xr = bf16_rows(x)
+    T = g.uniform(-1, 1, (rows, 2)).astype(np.float32)
+    valid = (g.random(rows) < 0.8).astype(np.uint8)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rtw.rtw_mlp_grad(mlp, 0, xb.cuda(), torch.tensor(T).cuda(), torch.tensor(valid).cuda(), beta=0.2, loss=loss)
+    grad = torch.zeros(rtw.RTW_MLP_NPARAM, dtype=torch.float32, device="cuda")
+    rtw.rtw_mlp_grad_get(mlp, 0, grad)
+    torch.cuda.synchronize()
+    ref_loss, ref = oracle_mod.mlp_loss_grad(th[0].astype(np.float64), xr, T.astype(np.float64), valid, beta=0.2,
+                                             bf16=True)
+    got = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - ref_loss) <= 1e-4 * abs(ref_loss)
+    H, I, OUT = 128, 16, 16
+    bounds = [("W1", 0, H * I), ("b1", H * I, H), ("W2", H * I + H, H * H), ("b2", H * I + H + H * H, H),
+              ("W3", H * I + 2 * H + H * H, H * H), ("b3", H * I + 2 * H + 2 * H * H, H),
+              ("W4", H * I + 3 * H + 2 * H * H, OUT * H), ("b4", H * I + 3 * H + 2 * H * H + OUT * H, OUT)]
+    for name, k, n in bounds:
+        r, gt = ref[k:k + n], got[k:k + n]
+        rel = np.linalg.norm(gt - r) / np.linalg.norm(r)
+        print(f"grad {name}: relative error {rel:.2e}")
+        assert rel <= 1e-2, name
+
+
+def test_adam_matches_oracle(rtw, oracle_mod):
+    th = seeded_params(1, 31)
+    mlp = rtw.MLP(1, th)
+    g = np.random.default_rng(32)
+    t_ref = th[0].astype(np.float64)
+    m_ref, v_ref = np.zeros_like(t_ref), np.zeros_like(t_ref)
+    for step in (1, 2, 3):
+        grad = g.standard_normal(rtw.RTW_MLP_NPARAM).astype(np.float32)
+        rtw.rtw_mlp_adam(mlp, 0, 1e-3, torch.tensor(grad).cuda())
+        oracle_mod.mlp_adam(t_ref, m_ref, v_ref, grad.astype(np.float64), step, lr=1e-3)
+    theta, m, v, st = mlp.get(0)
+    assert st == 3
+    assert np.abs(theta - t_ref).max() <= 1e-6 * max(1.0, np.abs(t_ref).max())
+    # FP32 moments: 1 - b2 in single precision differs from 1e-3 by 1.3e-5 relative
+    assert np.allclose(m, m_ref, rtol=1e-5, atol=1e-7) and np.allclose(v, v_ref, rtol=3e-5, atol=1e-9)
+
+
+def test_training_samples_match_oracle_trace(rtw, oracle_mod):
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, _ = W.batch_objects(3, stream=W.STREAM_TRAIN, r0=(5.0, 15.0))
+    obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+    g = np.random.default_rng(41)
+    n, p_max = 300, 3
+    r, a = np.sqrt(g.random(n)), 2 * np.pi * g.random(n)
+    uv = np.stack([r * np.cos(a), r * np.sin(a)], 1)
+    oi = g.integers(0, 3, n).astype(np.int32)
+    X = torch.zeros(((p_max + 1) * n, 16), dtype=torch.bfloat16, device="cuda")
+    T = torch.zeros(((p_max + 1) * n, 2), dtype=torch.float32, device="cuda")
+    valid = torch.zeros((p_max + 1) * n, dtype=torch.uint8, device="cuda")
+    rtw.rtw_mlp_samples(obj, torch.tensor(uv).cuda(), torch.tensor(oi).cuda(), p_max, X, T, valid)
+    torch.cuda.synchronize()
+    Xg = X.to(torch.float64).cpu().numpy().reshape(p_max + 1, n, 16)
+    Tg = T.cpu().numpy().reshape(p_max + 1, n, 2)
+    Vg = valid.cpu().numpy().reshape(p_max + 1, n)
+    objs = [oracle_mod.Object(s["a"], s["b"], s["c"], quat=s["quat"], m=s["m"], wavelength=s["wavelength"])
+            for s in specs]
+    for i in range(n):
+        o = objs[oi[i]]
+        x, y = oracle_mod.uv_to_xy(o, uv[i])
+        rec, _, hit = o.trace_ray(x, y, p_max)
+        for p in range(p_max + 1):
+            ok = bool(rec[p, oracle_mod.VALID])
+            assert bool(Vg[p, i]) == ok
+            assert np.array_equal(Tg[p, i], uv[i].astype(np.float32))
+            if ok:
+                f = oracle_mod.mlp_features(o, rec[p, oracle_mod.S:oracle_mod.S + 3])[0]
+                fb = np.array([oracle_mod.round_bf16(v) for v in f])
+                # features equal after bf16 rounding (a value within 1e-6 of a rounding boundary
+                # may round to the neighbour: one bf16 ulp)
+                assert np.all(np.abs(Xg[p, i] - fb) <= np.abs(fb) * 2 ** -7 + 1e-30)
+
+
+def test_training_is_deterministic_and_resumes_bit_exact(rtw):
+    """Loss decreases over a few hundred steps on traced samples; a checkpoint (parameters, Adam
+    moments, step) restored into a fresh handle continues bit-exactly."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, _ = W.batch_objects(64, stream=W.STREAM_TRAIN)
+    obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+    g = W.philox(W.STREAM_TRAIN)
+    n, p_max = 1 << 16, 0
+    r, a = np.sqrt(g.random(n)), 2 * np.pi * g.random(n)
+    uv = torch.tensor(np.stack([r * np.cos(a), r * np.sin(a)], 1)).cuda()
+    oi = torch.tensor(g.integers(0, len(specs), n).astype(np.int32)).cuda()
+    X = torch.zeros((n, 16), dtype=torch.bfloat16, device="cuda")
+    T = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    valid = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    rtw.rtw_mlp_samples(obj, uv, oi, p_max, X, T, valid)
+    mlp = rtw.MLP(1, seeded_params(1, 51))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bs = 4096
+
+    def run(m, steps, start):
+        out = []
+        for k in range(start, start + steps):
+            sl = slice((k * bs) % n, (k * bs) % n + bs)
+            rtw.rtw_mlp_grad(m, 0, X[sl], T[sl], valid[sl], loss=loss)
+            rtw.rtw_mlp_adam(m, 0, 2e-3)
+            out.append(loss.item())
+        return out
+
+    first = run(mlp, 200, 0)
+    ck = mlp.get(0)
+    a1 = run(mlp, 20, 200)
+    fresh = rtw.MLP(1)
+    fresh.set(0, ck[0], ck[1], ck[2], ck[3])
+    a2 = run(fresh, 20, 200)
+    print(f"training loss: first {np.mean(first[:10]):.4f}, after 200 steps {np.mean(first[-10:]):.4f}")
+    assert np.mean(first[-10:]) < 0.5 * np.mean(first[:10])
+    assert np.array_equal(mlp.get(0)[0], fresh.get(0)[0])
+    assert a1 == a2 or np.allclose(a1, a2, rtol=1e-12)
