@@ -291,6 +291,34 @@ int rtw_mlp_grad_get(const rtw_mlp* m, int order, float* grad, void* stream);
  * gradient grad (device, RTW_MLP_NPARAM floats) or, when NULL, the network's own.  Asynchronous. */
 int rtw_mlp_adam(rtw_mlp* m, int order, float lr, const float* grad, void* stream);
 
+/* Options of rtw_field_learned: orders 0..p_max (networks 0..p_max of the rtw_mlp handle);
+ * heads whose softmax weight is below p_min (0: 0.05) are not tried; at most max_steps Newton
+ * steps per head (0: 5); convergence at |s - target| < tol (0: per object
+ * min(1e-6, 1e-4 / (k0 max(a, b, c))), which keeps the phase error of a converged ray below
+ * 1e-4 rad); rows (object, direction) per launch sequence chunk_rows (0: 2^24). */
+typedef struct {
+    int p_max;
+    float p_min;
+    int max_steps;
+    double tol;
+    int64_t chunk_rows;
+} rtw_learned_params;
+
+/* The far field of every object of obj on the (theta, phi) grid of dirs from learned proposals:
+ * for each direction s and order p, network p (features of s and the object) proposes 4 entry
+ * points (moved onto radius 0.999 of the unit disk when beyond it); each head with softmax
+ * weight >= p_min seeds Newton steps on the exact FP64 trace
+ * (as RTW_NEWTON, at most max_steps steps, no distance bound); a root within 1e-6 max(a, b, c) of
+ * an earlier root of the same direction and order is the same ray and is dropped; every other
+ * root adds its exact F e^{i Psi}, except a near-caustic root, which marks the direction
+ * (RTW_MASK_CAUSTIC) instead.  A branch that no head finds is missing from the sum: roots_out
+ * (device, optional, [objects][directions][orders] uint8) reports the roots found, so that a
+ * caller can fall back to the dense path where it finds none.  field_out and mask_out as
+ * rtw_field (flags: 0 or RTW_FIELD_PER_ORDER).  Working memory is allocated stream-ordered and
+ * freed before the call's work completes.  Asynchronous. */
+int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned_params* lp, const rtw_dirs* dirs,
+                      int flags, void* field_out, uint8_t* mask_out, uint8_t* roots_out, void* stream);
+
 /* ---- the fan path without allocation ----
  * The paper has no counterpart of this call: it serves programs that may not allocate device
  * memory themselves (a host application whose memory manager owns the device and forbids direct

@@ -81,6 +81,8 @@ def lib():
         L.om_loss_grad.argtypes = [p, p, p, p, i64, d, i, p]
         L.om_loss_grad.restype = d
         L.om_adam.argtypes = [p, p, p, p, i64, i, d, d, d, d]
+        L.or_field_learned.argtypes = [p, p, i, i, i, d, i, d, p, p, p]
+        L.or_field_learned.restype = i64
         _lib = L
     return _lib
 
@@ -161,6 +163,17 @@ class Object:
         if hits < 0:
             raise RuntimeError("or_field_grid failed")
         return out, mask, int(hits), int(nfail.value)
+
+    def field_learned(self, theta, pmax, ntheta, nphi, p_min=0.05, max_steps=5, tol=0.0):
+        """theta: (pmax+1) x MLP_NPARAM network parameters; returns out, mask, root counts."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(pmax + 1, -1)
+        ndir = ntheta * nphi
+        out = np.zeros((ndir, pmax + 1, 4))
+        mask = np.zeros(ndir, dtype=np.uint8)
+        roots = np.zeros((ndir, pmax + 1), dtype=np.uint8)
+        lib().or_field_learned(self.handle, _ptr(theta), int(pmax), int(ntheta), int(nphi), float(p_min),
+                               int(max_steps), float(tol), _ptr(out), _ptr(mask), _ptr(roots))
+        return out, mask, roots
 
     def newton(self, p, target, xy, rmax=0.0):
         target = np.ascontiguousarray(target, dtype=np.float64)

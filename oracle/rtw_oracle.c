@@ -547,10 +547,17 @@ static int newton_eval(const or_object* o, int p, const double target[3], const 
 
 /* Newton steps xy <- xy + J^{-1} [v1.d, v2.d] with d = target - s and J = ds/d(x, y) of the
  * record, each step shortened by halving (at most 12 times) until the trace of the new point
- * leaves in order p with a smaller residual.  Converged when |d| < 1e-11 within 30 steps and the
- * root lies within rmax of the seed (rmax <= 0: anywhere), so that the ray found is the one the
- * seed stands for and not a neighbouring branch of the same order. */
+ * leaves in order p with a smaller residual.  Converged when |d| < tol at one of the first
+ * max_checks evaluations (or_newton: 1e-11 within 30) and the root lies within rmax of the seed
+ * (rmax <= 0: anywhere), so that the ray found is the one the seed stands for and not a
+ * neighbouring branch of the same order.  xy ends at the last point reached. */
 int or_newton(const or_object* o, int p, const double target[3], double* xy, double rmax, double* rec)
+{
+    return or_newton_ex(o, p, target, xy, rmax, 30, 1e-11, rec);
+}
+
+int or_newton_ex(const or_object* o, int p, const double target[3], double* xy, double rmax, int max_checks,
+                 double tol, double* rec)
 {
     const size_t nb = (size_t)(p + 1) * OR_NFIELD;
     double* buf = (double*)malloc(sizeof(double) * 2 * nb);
@@ -560,15 +567,16 @@ int or_newton(const or_object* o, int p, const double target[3], double* xy, dou
     int ret = -1;
     double res;
     if (newton_eval(o, p, target, xy, cur, &res)) {
-        for (int it = 0; it < 30; ++it) {
+        for (int it = 0; it < max_checks; ++it) {
             const double* r = cur + (size_t)p * OR_NFIELD;
-            if (res < 1e-11) {
+            if (res < tol) {
                 if (rmax <= 0.0 || hypot(xy[0] - x0, xy[1] - y0) <= rmax) {
                     memcpy(rec, r, sizeof(double) * OR_NFIELD);
                     ret = it;
                 }
                 break;
             }
+            if (it == max_checks - 1) break;
             double d[3] = {target[0] - r[OR_S], target[1] - r[OR_S + 1], target[2] - r[OR_S + 2]};
             double rhs0 = dot3(r + OR_V1, d), rhs1 = dot3(r + OR_V2, d);
             double J[2][2] = {{r[OR_J], r[OR_J + 1]}, {r[OR_J + 2], r[OR_J + 3]}}, Ji[2][2];
@@ -633,8 +641,8 @@ static int newton_fan(const or_object* o, int p, double fan_phi, double alpha_t,
 /* ------------------------------------------------------------------------------------- */
 
 /* contribution F e^{i Psi} of one record projected on (e_theta, e_phi) */
-static void project_add(const double F[6], double psi, const double eth[3], const double eph[3],
-                        double weight, double* acc)
+void or_project_add(const double F[6], double psi, const double eth[3], const double eph[3], double weight,
+                    double* acc)
 {
     cplx ph = cexp(I * psi);
     cplx ft = 0.0, fp = 0.0;
@@ -864,7 +872,7 @@ int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, co
                     double b = bj[j] + lam * (bj[j + 1] - bj[j]);
                     double* r = (double*)malloc(sizeof(double) * OR_NFIELD);
                     if (newton_fan(o, p, fan_phi, alpha[k], &b, r) >= 0) {
-                        project_add(r + OR_F, r[OR_PSI], eth + 3 * k, eph + 3 * k, wgo, acc);
+                        or_project_add(r + OR_F, r[OR_PSI], eth + 3 * k, eph + 3 * k, wgo, acc);
                         free(r);
                         continue;
                     }
@@ -872,7 +880,7 @@ int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, co
                 }
                 double F[6], psi = (1.0 - lam) * ra[OR_PSI] + lam * rb[OR_PSI];
                 for (int c = 0; c < 6; ++c) F[c] = (1.0 - lam) * ra[OR_F + c] + lam * rb[OR_F + c];
-                project_add(F, psi, eth + 3 * k, eph + 3 * k, wgo, acc);
+                or_project_add(F, psi, eth + 3 * k, eph + 3 * k, wgo, acc);
             }
         }
 
@@ -1116,7 +1124,7 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                         double eth[3] = {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)};
                         double eph[3] = {-sin(ph), cos(ph), 0.0};
                         double acc[4] = {0, 0, 0, 0};
-                        project_add(F, psi, eth, eph, 1.0, acc);
+                        or_project_add(F, psi, eth, eph, 1.0, acc);
                         double* dst = out + ((size_t)dk * np + p) * 4;
                         for (int c = 0; c < 4; ++c) {
 #ifdef _OPENMP
@@ -1134,4 +1142,82 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
     free(cr);
     if (newton_fail) *newton_fail = nfail;
     return hits;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Learned proposal: network seeds, Newton on the exact trace, deduplicated roots          */
+/* ------------------------------------------------------------------------------------- */
+
+#include "mlp_oracle.h"
+
+int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int ntheta, int nphi, double p_min,
+                         int max_steps, double tol, double* out, uint8_t* mask, uint8_t* roots)
+{
+    const int np = pmax + 1;
+    const int64_t ndir = (int64_t)ntheta * nphi;
+    const double dth = PI / ntheta, dph = 2.0 * PI / nphi;
+    const double axial = 2.0 * o->lambda / o->Lmin;
+    const double dedup = 1e-6 * o->Lmax;
+    /* tol <= 0: per object, a phase error k0 L |s - t| below 1e-4 rad */
+    if (!(tol > 0.0)) tol = fmin(1e-6, 1e-4 / (o->k0 * o->Lmax));
+    memset(out, 0, sizeof(double) * 4 * (size_t)np * (size_t)ndir);
+    memset(mask, 0, (size_t)ndir);
+    if (roots) memset(roots, 0, (size_t)ndir * (size_t)np);
+    int64_t total = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+#endif
+    for (int64_t dk = 0; dk < ndir; ++dk) {
+        const int it = (int)(dk / nphi), jp = (int)(dk % nphi);
+        const double th = (it + 0.5) * dth, ph = -PI + (jp + 0.5) * dph;
+        const double s[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+        const double eth[3] = {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)};
+        const double eph[3] = {-sin(ph), cos(ph), 0.0};
+        uint8_t mk = (th < axial || th > PI - axial) ? OR_MASK_AXIAL : 0;
+        double x[OM_IN], y[OM_OUT];
+        om_features(o, s, x);
+        double* rec = (double*)malloc(sizeof(double) * (size_t)np * OR_NFIELD);
+        for (int p = 0; p < np; ++p) {
+            om_forward(theta + (size_t)p * OM_NPARAM, x, 1, 1, y);
+            /* softmax weights of the heads */
+            double zmax = y[8], w[OM_HEADS], se = 0.0;
+            for (int k = 1; k < OM_HEADS; ++k) zmax = fmax(zmax, y[8 + k]);
+            for (int k = 0; k < OM_HEADS; ++k) {
+                w[k] = exp(y[8 + k] - zmax);
+                se += w[k];
+            }
+            double found[OM_HEADS][2];
+            int nfound = 0;
+            for (int k = 0; k < OM_HEADS; ++k) {
+                if (w[k] / se < p_min) continue;
+                double xy[2];
+                double uv[2] = {y[2 * k], y[2 * k + 1]};
+                /* an entry point lies inside the section: seeds beyond radius 0.999 move onto it */
+                const double ru = hypot(uv[0], uv[1]);
+                if (ru > 0.999) {
+                    uv[0] *= 0.999 / ru;
+                    uv[1] *= 0.999 / ru;
+                }
+                om_uv_to_xy(o, uv, &xy[0], &xy[1]);
+                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, rec) < 0) continue;
+                int dup = 0;
+                for (int q = 0; q < nfound; ++q)
+                    if (hypot(xy[0] - found[q][0], xy[1] - found[q][1]) <= dedup) dup = 1;
+                if (dup) continue;
+                found[nfound][0] = xy[0];
+                found[nfound][1] = xy[1];
+                nfound++;
+                if (rec[OR_CAUSTIC] != 0.0) {
+                    mk |= OR_MASK_CAUSTIC;
+                    continue;
+                }
+                or_project_add(rec + OR_F, rec[OR_PSI], eth, eph, 1.0, out + ((size_t)dk * np + p) * 4);
+            }
+            if (roots) roots[(size_t)dk * np + p] = (uint8_t)nfound;
+            total += nfound;
+        }
+        free(rec);
+        mask[dk] = mk;
+    }
+    return total;
 }

@@ -90,6 +90,12 @@ cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* grad,
 cudaError_t launch_mlp_samples(const ObjDev* objs, const ObjFeat* feat, int nobj, const double* uv, const int* oidx,
                                long long n, int pmax, __nv_bfloat16* X, float* T, uint8_t* valid, cudaStream_t s);
 
+// learned field (rtw_learned.cu): features of nrows (object, direction) rows, then per order the
+// network's forward pass and the Newton kernel
+cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double* tab, int nt, int nph, long long nrows,
+                           const MlpWeights* nets, int np, __nv_bfloat16* X, float* Y, float p_min, int max_steps,
+                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, cudaStream_t s);
+
 cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
                               cudaStream_t s);
 cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,

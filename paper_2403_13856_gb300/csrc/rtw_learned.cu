@@ -1,0 +1,215 @@
+// rtw_learned.cu -- the far field from learned entry-point proposals: for every (object,
+// direction) row and order p, network p proposes 4 entry points; each confident head seeds Newton
+// steps on the exact FP64 trace; converged roots are deduplicated and summed.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rtw.h"
+#include "rtw_device.cuh"
+#include "rtw_host.h"
+#include "rtw_launch.h"
+
+using rtw::host::align_up;
+using rtw::host::fail;
+
+namespace rtw {
+namespace {
+
+constexpr unsigned int kMaskCausticL = 1u;  // the dense path's RTW_MASK_CAUSTIC bit
+
+// features of row (object o, direction dk): s (3) then the object's 13, in bfloat16
+__global__ void learned_features_kernel(const ObjFeat* __restrict__ feat, const double* __restrict__ tab, int nt,
+                                        int nph, long long nrows, __nv_bfloat16* __restrict__ X)
+{
+    const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (row >= nrows) return;
+    const long long ndir = (long long)nt * nph;
+    const int o = (int)(row / ndir);
+    const long long dk = row - (long long)o * ndir;
+    const int it = (int)(dk / nph), jp = (int)(dk % nph);
+    const double ct = tab[it], st = tab[nt + it], cp = tab[2 * nt + jp], sp = tab[2 * nt + nph + jp];
+    __nv_bfloat16* x = X + row * kMlpIn;
+    x[0] = __float2bfloat16_rn((float)(st * cp));
+    x[1] = __float2bfloat16_rn((float)(st * sp));
+    x[2] = __float2bfloat16_rn((float)ct);
+    const ObjFeat& f = feat[o];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) x[3 + k] = __float2bfloat16_rn(f.f[k]);
+}
+
+// one thread per row: heads of network p -> Newton -> deduplicated roots -> F e^{i Psi}
+__global__ void __launch_bounds__(128) learned_newton_kernel(const ObjDev* __restrict__ objs,
+                                                             const ObjFeat* __restrict__ feat,
+                                                             const double* __restrict__ tab, int nt, int nph,
+                                                             long long nrows, const float* __restrict__ Y, int p,
+                                                             float p_min, int max_steps, double tol, int nout,
+                                                             double* __restrict__ out, unsigned int* __restrict__ mask,
+                                                             uint8_t* __restrict__ roots, int np)
+{
+    const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (row >= nrows) return;
+    const long long ndir = (long long)nt * nph;
+    const int oi = (int)(row / ndir);
+    const long long dk = row - (long long)oi * ndir;
+    const int it = (int)(dk / nph), jp = (int)(dk % nph);
+    const double ct = tab[it], st = tab[nt + it], cp = tab[2 * nt + jp], sp = tab[2 * nt + nph + jp];
+    const double t[3] = {st * cp, st * sp, ct};
+    const double eth[3] = {ct * cp, ct * sp, -st};
+    const double eph[3] = {-sp, cp, 0.0};
+    const ObjDev& o = objs[oi];
+    const ObjFeat& f = feat[oi];
+    const float* y = Y + row * kMlpOut;
+    float zmax = y[8];
+#pragma unroll
+    for (int k = 1; k < kMlpHeads; ++k) zmax = fmaxf(zmax, y[8 + k]);
+    float w[kMlpHeads], se = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMlpHeads; ++k) {
+        w[k] = expf(y[8 + k] - zmax);
+        se += w[k];
+    }
+    const double dedup = 1e-6 * o.lmax;
+    // default tolerance: the phase error k0 L |s - t| of a converged ray stays below 1e-4 rad
+    const double tl = tol > 0.0 ? tol : fmin(1e-6, 1e-4 / (o.k0 * o.lmax));
+    double found[kMlpHeads][2];
+    int nfound = 0;
+    double* dst = out + (row * nout + (nout > 1 ? p : 0)) * 4;
+    for (int k = 0; k < kMlpHeads; ++k) {
+        if (w[k] / se < p_min) continue;
+        double u0 = y[2 * k], u1 = y[2 * k + 1];
+        // an entry point lies inside the section: seeds beyond radius 0.999 move onto it
+        const double ru = sqrt(u0 * u0 + u1 * u1);
+        if (ru > 0.999) {
+            u0 *= 0.999 / ru;
+            u1 *= 0.999 / ru;
+        }
+        const double d1 = u1 / f.l11, d0 = (u0 - f.l10 * d1) / f.l00;
+        FarRecord fr;
+        double root[2];
+        if (!newton_point(o, p, t, o.c[0] + d0, o.c[1] + d1, 0.0, fr, max_steps + 1, tl, root)) continue;
+        bool dup = false;
+        for (int q = 0; q < nfound; ++q)
+            if (hypot(root[0] - found[q][0], root[1] - found[q][1]) <= dedup) dup = true;
+        if (dup) continue;
+        found[nfound][0] = root[0];
+        found[nfound][1] = root[1];
+        ++nfound;
+        if (fr.flags & kFlagCaustic) {
+            atomicOr(mask + row, kMaskCausticL);
+            continue;
+        }
+        add_contribution_reduced(fr.F, fr.psi, eth, eph, dst);
+    }
+    if (roots) roots[row * np + p] = (uint8_t)nfound;
+}
+
+}  // namespace
+
+cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double* tab, int nt, int nph, long long nrows,
+                           const MlpWeights* nets, int np, __nv_bfloat16* X, float* Y, float p_min, int max_steps,
+                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, cudaStream_t s)
+{
+    if (nrows <= 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((nrows + 127) / 128);
+    learned_features_kernel<<<nb, 128, 0, s>>>(feat, tab, nt, nph, nrows, X);
+    cudaError_t e = cudaGetLastError();
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+        e = launch_mlp_forward(nets[p], X, nrows, Y, s);
+        if (e != cudaSuccess) break;
+        learned_newton_kernel<<<nb, 128, 0, s>>>(objs, feat, tab, nt, nph, nrows, Y, p, p_min, max_steps, tol, nout,
+                                                  out, mask, roots, np);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace rtw
+
+extern "C" {
+
+int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned_params* lp, const rtw_dirs* dirs,
+                      int flags, void* field_out, uint8_t* mask_out, uint8_t* roots_out, void* stream)
+{
+    if (!obj || !m || !lp || !dirs || !field_out) return fail(RTW_ERR_ARG, "rtw_field_learned: null pointer");
+    const int np = lp->p_max + 1;
+    if (lp->p_max < 0) return fail(RTW_ERR_ARG, "rtw_field_learned: p_max < 0");
+    for (int p = 0; p < np; ++p) {
+        int64_t step = 0;
+        if (rtw_mlp_get(m, p, nullptr, nullptr, nullptr, &step) != RTW_OK)
+            return fail(RTW_ERR_ARG, "rtw_field_learned: no network for order %d", p);
+    }
+    if (dirs->kind != RTW_DIRS_GRID || dirs->n_theta < 1 || dirs->n_phi < 2)
+        return fail(RTW_ERR_ARG, "rtw_field_learned: a (theta, phi) grid with n_theta >= 1, n_phi >= 2");
+    if (flags & ~RTW_FIELD_PER_ORDER) return fail(RTW_ERR_ARG, "rtw_field_learned: flags 0x%x", flags);
+    if (lp->max_steps < 0 || lp->max_steps > 30 || lp->p_min < 0.0f || lp->p_min > 1.0f || lp->tol < 0.0 ||
+        lp->chunk_rows < 0)
+        return fail(RTW_ERR_ARG, "rtw_field_learned: parameters out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int max_steps = lp->max_steps > 0 ? lp->max_steps : 5;
+    const double tol = lp->tol;  // 0: per object, min(1e-6, 1e-4 / (k0 max(a, b, c)))
+    const float p_min = lp->p_min > 0.0f ? lp->p_min : 0.05f;
+    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    const int nout = (flags & RTW_FIELD_PER_ORDER) ? np : 1;
+    const long long chunk_rows = lp->chunk_rows > 0 ? lp->chunk_rows : (1ll << 24);
+    const int per_chunk = (int)std::max<long long>(1, std::min<long long>(obj->count, chunk_rows / ndir));
+    const long long rows_max = (long long)per_chunk * ndir;
+
+    std::vector<rtw::ObjDev> od((size_t)obj->count);
+    std::vector<rtw::ObjFeat> of((size_t)obj->count);
+    for (int i = 0; i < obj->count; ++i) {
+        rtw::host::fill_objdev(obj->h[(size_t)i], od[(size_t)i]);
+        od[(size_t)i].grid = rtw::kGridSquare;
+        rtw::host::object_features(obj->h[(size_t)i], of[(size_t)i]);
+    }
+    std::vector<rtw::MlpWeights> nets((size_t)np);
+    for (int p = 0; p < np; ++p) nets[(size_t)p] = rtw::host::mlp_weights(m, p);
+
+    // stream-ordered workspace: tables, features, outputs of one network, mask words
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_obj = take(sizeof(rtw::ObjDev) * od.size());
+    const size_t o_feat = take(sizeof(rtw::ObjFeat) * of.size());
+    const size_t o_tab = take(sizeof(double) * 3 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi));
+    const size_t o_x = take(sizeof(__nv_bfloat16) * rtw::kMlpIn * (size_t)rows_max);
+    const size_t o_y = take(sizeof(float) * rtw::kMlpOut * (size_t)rows_max);
+    const size_t o_mask = take(sizeof(unsigned int) * (size_t)rows_max);
+    void* ws = nullptr;
+    RTW_CUDA(cudaMallocAsync(&ws, off, s));
+    char* b = (char*)ws;
+    rtw::ObjDev* d_obj = (rtw::ObjDev*)(b + o_obj);
+    rtw::ObjFeat* d_feat = (rtw::ObjFeat*)(b + o_feat);
+    double* tab = (double*)(b + o_tab);
+    __nv_bfloat16* X = (__nv_bfloat16*)(b + o_x);
+    float* Y = (float*)(b + o_y);
+    unsigned int* words = (unsigned int*)(b + o_mask);
+    int rc = RTW_OK;
+    cudaError_t e = cudaMemcpyAsync(d_obj, od.data(), sizeof(rtw::ObjDev) * od.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_feat, of.data(), sizeof(rtw::ObjFeat) * of.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(field_out, 0, sizeof(double) * 4 * (size_t)nout * ndir * obj->count, s);
+    if (e == cudaSuccess) e = rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, tab, s);
+    for (int c0 = 0; c0 < obj->count && e == cudaSuccess; c0 += per_chunk) {
+        const int cn = std::min(per_chunk, obj->count - c0);
+        const long long rows = (long long)cn * ndir;
+        e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * (size_t)rows, s);
+        if (e != cudaSuccess) break;
+        e = rtw::launch_learned(d_obj + c0, d_feat + c0, tab, dirs->n_theta, dirs->n_phi, rows, nets.data(), np, X, Y,
+                                p_min, max_steps, tol, nout, (double*)field_out + 4 * (size_t)nout * ndir * c0, words,
+                                roots_out ? roots_out + (size_t)np * ndir * c0 : nullptr, s);
+        if (e == cudaSuccess && mask_out)
+            e = rtw::launch_finalize_mask(words, mask_out + (size_t)ndir * c0, d_obj + c0, cn, ndir, 1, dirs->n_theta,
+                                          dirs->n_phi, 0.0, 0.0, s);
+    }
+    if (e != cudaSuccess) rc = rtw::host::cuda_fail(e, "rtw_field_learned");
+    cudaFreeAsync(ws, s);
+    return rc;
+}
+
+}  // extern "C"

@@ -97,6 +97,7 @@ def lib():
             "rtw_mlp_grad": ([p, i, p, p, p, i64, ctypes.c_float, p, p], i),
             "rtw_mlp_grad_get": ([p, i, p, p], i),
             "rtw_mlp_adam": ([p, i, ctypes.c_float, p, p], i),
+            "rtw_field_learned": ([p, p, p, p, i, p, p, p, p], i),
             "rtw_sync_status": ([p], i),
             "rtw_newton_failures": ([p, p], i),
             "rtw_status_string": ([i], ctypes.c_char_p),
@@ -345,6 +346,23 @@ def rtw_mlp_grad_get(mlp: MLP, order, grad, stream=None):
 
 def rtw_mlp_adam(mlp: MLP, order, lr, grad=None, stream=None):
     _check(lib().rtw_mlp_adam(mlp.handle, order, float(lr), _ptr(grad), _stream_ptr(stream)))
+
+
+class rtw_learned_params(ctypes.Structure):
+    _fields_ = [("p_max", ctypes.c_int), ("p_min", ctypes.c_float), ("max_steps", ctypes.c_int),
+                ("tol", ctypes.c_double), ("chunk_rows", ctypes.c_int64)]
+
+
+def learned_params(p_max, p_min=0.0, max_steps=0, tol=0.0, chunk_rows=0):
+    lp = rtw_learned_params()
+    lp.p_max, lp.p_min, lp.max_steps, lp.tol, lp.chunk_rows = p_max, p_min, max_steps, tol, int(chunk_rows)
+    return lp
+
+
+def rtw_field_learned(obj: Object, mlp: MLP, params: rtw_learned_params, dirs: rtw_dirs, out, mask=None, roots=None,
+                      flags=0, stream=None):
+    _check(lib().rtw_field_learned(obj.handle, mlp.handle, ctypes.byref(params), ctypes.byref(dirs), flags, _ptr(out),
+                                   _ptr(mask), _ptr(roots), _stream_ptr(stream)))
 
 
 def rtw_newton_failures(stream=None) -> int:

@@ -1,0 +1,108 @@
+"""The far field from learned entry-point proposals (network -> Newton on the exact trace ->
+deduplicated roots) on the GPU.
+
+Pipeline parity: networks with fixed outputs (hidden layers zero, so every row gets the same four
+seeds and logits, exactly representable) against the oracle's learned field from the same seeds:
+root counts and masks identical, fields within 1e-6 of the largest.  Gain: networks trained on
+traced rays against the same pipeline seeded at the disk centre, both measured against the
+oracle's exact branch sum (O3).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rtw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_13856_gb300 import build, rtw as R
+
+    build.build()
+    R.lib()
+    return R
+
+
+def const_theta(n_orders, seeds, logits):
+    from paper_2403_13856_gb300.rtw import RTW_MLP_NPARAM as P
+
+    th = np.zeros((n_orders, P), dtype=np.float32)
+    th[:, P - 16:P - 8] = np.asarray(seeds, dtype=np.float32).ravel()
+    th[:, P - 8:P - 4] = logits
+    return th
+
+
+def learned_field(rtw, obj, mlp, p_max, nt, nph, n_obj=1):
+    out = torch.zeros((n_obj, nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros((n_obj, nt * nph), dtype=torch.uint8, device="cuda")
+    roots = torch.zeros((n_obj, nt * nph, p_max + 1), dtype=torch.uint8, device="cuda")
+    rtw.rtw_field_learned(obj, mlp, rtw.learned_params(p_max), rtw.dirs_grid(nt, nph), out, mask, roots,
+                          flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    return out.cpu().numpy(), mask.cpu().numpy(), roots.cpu().numpy()
+
+
+SPECS = [dict(a=8.0, b=8.0, c=8.0, quat=(1.0, 0.0, 0.0, 0.0), m=1.333, wavelength=0.6328),
+         dict(a=12.0, b=10.0, c=8.0, quat=(0.9848077530122080, 0.1736481776669303, 0.0, 0.0), m=1.45,
+              wavelength=0.5)]
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_learned_pipeline_matches_oracle(rtw, oracle_mod, k):
+    spec = SPECS[k]
+    p_max, nt, nph = 2, 24, 48
+    seeds = [[0.0, 0.0], [0.5, 0.25], [-0.375, 0.5], [0.125, -0.625]]
+    th = const_theta(p_max + 1, seeds, [0.0, 0.5, -0.25, -4.0])  # head 3 below p_min = 0.05
+    mlp = rtw.MLP(p_max + 1, th)
+    obj = rtw.Object([rtw.ObjectSpec(**spec)])
+    got, gm, gr = learned_field(rtw, obj, mlp, p_max, nt, nph)
+    o = oracle_mod.Object(spec["a"], spec["b"], spec["c"], quat=spec["quat"], m=spec["m"],
+                          wavelength=spec["wavelength"])
+    ref, rm, rr = o.field_learned(th.astype(np.float64), p_max, nt, nph)  # 5 steps, object tolerance
+    ref = oracle_mod.complex_field(ref)
+    print(f"object {k}: roots per order GPU {gr[0].sum(axis=0)}, oracle {rr.sum(axis=0)}")
+    assert np.array_equal(gr[0], rr)
+    assert np.array_equal(gm[0], rm)
+    scale = np.abs(ref).max()
+    assert scale > 0 and np.abs(got[0] - ref).max() <= 1e-6 * scale
+
+
+def test_trained_network_gains_over_fixed_seeds(rtw, oracle_mod):
+    """Networks for orders 0..2 trained on 2^21 traced rays of 4096 drops from the batched recipe
+    (radii 5-15 um) recover a held-out drop's exact branch sum at least twice as well (normwise)
+    as the same Newton pipeline seeded at the disk centre."""
+    from paper_2403_13856_gb300 import learned as Lr
+    from paper_2403_13856_gb300 import workloads as W
+
+    p_max, nt, nph = 2, 32, 64
+    train_specs, _ = W.batch_objects(4096, stream=W.STREAM_TRAIN, r0=(5.0, 15.0))
+    tobj = rtw.Object([rtw.ObjectSpec(**s) for s in train_specs])
+    samples = [Lr.Samples(tobj, 1 << 21, p_max)]
+    mlp = rtw.MLP(p_max + 1, Lr.init_params(p_max + 1))
+    losses = Lr.train(mlp, samples, range(p_max + 1), steps=20000, lr=3e-3, lr_end=3e-5)
+    print("final training losses", losses)
+    spec = W.batch_objects(1, stream=W.STREAM_EVAL, r0=(5.0, 15.0))[0][0]
+    obj = rtw.Object([rtw.ObjectSpec(**spec)])
+    got, gm, gr = learned_field(rtw, obj, mlp, p_max, nt, nph)
+    base = rtw.MLP(p_max + 1, const_theta(p_max + 1, [[0.0, 0.0]] * 4, [0.0, 0.0, 0.0, 0.0]))
+    b0, bm, br = learned_field(rtw, obj, base, p_max, nt, nph)
+    o = oracle_mod.Object(spec["a"], spec["b"], spec["c"], quat=spec["quat"], m=spec["m"],
+                          wavelength=spec["wavelength"])
+    ref, rm, hits, _ = o.field_grid(p_max, nt, nph, n_target=40_000, flags=oracle_mod.FIELD_EXACT)
+    ref = oracle_mod.complex_field(ref)
+    # the dense grid's outermost cells end inside the rim, so the exact branch sum seeded from them
+    # lacks the grazing reflections leaving within about 15 deg of forward: compare beyond 20 deg
+    th_deg = np.repeat((np.arange(nt) + 0.5) * 180.0 / nt, nph)
+    sel = (rm == 0) & (gm[0] == 0) & (bm[0] == 0) & (th_deg > 20.0)
+    e_t = np.linalg.norm((got[0] - ref)[sel]) / np.linalg.norm(ref[sel])
+    e_b = np.linalg.norm((b0[0] - ref)[sel]) / np.linalg.norm(ref[sel])
+    per_p = [np.linalg.norm((got[0][:, p] - ref[:, p])[sel]) / np.linalg.norm(ref[:, p][sel]) for p in range(3)]
+    ok = [np.mean((np.abs(got[0][:, p] - ref[:, p]).max(axis=-1) <= 1e-3 * np.abs(ref[:, p]).max())[sel])
+          for p in range(3)]
+    print(f"normwise error vs exact branch sum: trained {e_t:.2e} (per order {np.round(per_p, 4)}), "
+          f"fixed seeds {e_b:.2e}; roots trained {gr[0].sum(axis=0)}, fixed {br[0].sum(axis=0)}; "
+          f"directions within 1e-3 per order {np.round(ok, 3)}")
+    assert e_t < 0.5 * e_b
