@@ -273,15 +273,17 @@ int rtw_mlp_set(rtw_mlp* m, int order, const float* theta, const float* adam_m, 
 /* Training samples from the exact FP64 trace: ray i enters object obj_index[i] (device int32) at
  * unit-disk point uv[i] (device, n x 2 double); for every order p <= p_max, row p n + i of X
  * (device, bf16, 16 per row) gets the features of its exit direction, T (device, 2 floats per row)
- * the target uv and valid (device, uint8) whether order p leaves the object (0 for an index
- * outside [0, count)).  Asynchronous. */
+ * the target uv and valid (device, uint8) the row's label: 0 when order p does not leave the
+ * object (or the index is outside [0, count)), else 1 + (N_f mod 4) with N_f the ray's focal-line
+ * count, the head that learns its branch (the branches of one direction and order differ in N_f).
+ * Asynchronous. */
 int rtw_mlp_samples(const rtw_object* obj, const double* uv, const int32_t* obj_index, int64_t n, int p_max,
                     void* X, float* T, uint8_t* valid, void* stream);
 /* Y (device, rows x 16 float) = network `order` applied to X.  Asynchronous. */
 int rtw_mlp_forward(const rtw_mlp* m, int order, const void* X, int64_t rows, float* Y, void* stream);
-/* Gradient of the mean loss over the valid rows into the network's gradient buffer: for each row
- * the head nearest the target uv carries the squared distance, and beta times the softmax
- * cross-entropy of the logits towards that head is added.  loss_out (device double, may be NULL)
+/* Gradient of the mean loss over the labelled rows (valid != 0) into the network's gradient
+ * buffer: for each row head valid - 1 carries the squared distance to the target uv, and beta
+ * times the softmax cross-entropy of the logits towards that head is added.  loss_out (device double, may be NULL)
  * receives the loss.  Deterministic (fixed summation order).  Asynchronous. */
 int rtw_mlp_grad(rtw_mlp* m, int order, const void* X, const float* T, const uint8_t* valid, int64_t rows, float beta,
                  double* loss_out, void* stream);

@@ -225,6 +225,7 @@ def mlp_forward(theta, x, bf16=False):
 
 
 def mlp_loss_grad(theta, x, target, valid, beta=0.1, bf16=False):
+    """valid: per-row label, 0 = ignored, 1..4 = head label - 1 carries the target."""
     theta = np.ascontiguousarray(theta, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, MLP_IN)
     target = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 2)

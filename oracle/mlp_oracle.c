@@ -141,31 +141,24 @@ static void dense_back(const double* W, const double* a, const double* dz, int n
         }
 }
 
-double om_loss_grad(const double* theta, const double* x, const double* target, const uint8_t* valid, int64_t n,
+double om_loss_grad(const double* theta, const double* x, const double* target, const uint8_t* label, int64_t n,
                     double beta, int bf16, double* grad)
 {
     memset(grad, 0, sizeof(double) * OM_NPARAM);
     int64_t nv = 0;
-    for (int64_t i = 0; i < n; ++i) nv += valid[i] != 0;
+    for (int64_t i = 0; i < n; ++i) nv += label[i] != 0;
     if (nv == 0) return 0.0;
     const double inv = 1.0 / (double)nv;
     om_row* r = (om_row*)malloc(sizeof(om_row));
     double loss = 0.0;
     for (int64_t i = 0; i < n; ++i) {
-        if (!valid[i]) continue;
+        if (!label[i]) continue;
         forward_row(theta, x + i * OM_IN, bf16, r);
         const double* t = target + 2 * i;
-        /* the head nearest the target carries the regression term */
-        int j = 0;
-        double best = 0.0;
-        for (int k = 0; k < OM_HEADS; ++k) {
-            const double e0 = r->y[2 * k] - t[0], e1 = r->y[2 * k + 1] - t[1];
-            const double d = e0 * e0 + e1 * e1;
-            if (k == 0 || d < best) {
-                best = d;
-                j = k;
-            }
-        }
+        /* the head of the ray's branch carries the regression term */
+        const int j = (label[i] - 1) % OM_HEADS;
+        const double e0 = r->y[2 * j] - t[0], e1 = r->y[2 * j + 1] - t[1];
+        const double best = e0 * e0 + e1 * e1;
         /* softmax cross-entropy of the logits against head j */
         double zmax = r->y[8];
         for (int k = 1; k < OM_HEADS; ++k) zmax = fmax(zmax, r->y[8 + k]);

@@ -19,8 +19,11 @@
  *                    g(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));
  *   outputs y (16):  y[2k], y[2k+1] the uv of head k (k < 4), y[8 + k] the logit of head k,
  *                    y[12..15] unused;
- *   loss of a row:   j = argmin_k |uv_k - uv*|^2 (first on ties), loss = |uv_j - uv*|^2 +
- *                    beta CE(softmax(y[8..11]), j); mean over the valid rows;
+ *   labels:          a row's label is 0 (no ray: ignored) or 1 + (N_f mod 4), N_f the focal
+ *                    lines of its ray: the branches of one direction and order differ in N_f
+ *                    (their orientation follows its parity), so head N_f mod 4 learns one branch;
+ *   loss of a row:   j = label - 1, loss = |uv_j - uv*|^2 + beta CE(softmax(y[8..11]), j);
+ *                    mean over the labelled rows;
  *   Adam:            m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
  *                    w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
  * bf16 = 1 rounds the weights, the inputs and every hidden activation to bfloat16 (round to
@@ -64,8 +67,9 @@ void om_uv_to_xy(const or_object* o, const double uv[2], double* x, double* y);
 
 /* y (n x 16) of rows x (n x 16) */
 void om_forward(const double* theta, const double* x, int64_t n, int bf16, double* y);
-/* mean loss over the valid rows and its gradient (OM_NPARAM doubles, overwritten) */
-double om_loss_grad(const double* theta, const double* x, const double* target, const uint8_t* valid, int64_t n,
+/* mean loss over the labelled rows (label 1..4: head label - 1 carries the target; 0: ignored)
+ * and its gradient (OM_NPARAM doubles, overwritten) */
+double om_loss_grad(const double* theta, const double* x, const double* target, const uint8_t* label, int64_t n,
                     double beta, int bf16, double* grad);
 /* one Adam step t (1-based) on n parameters */
 void om_adam(double* theta, double* m, double* v, const double* grad, int64_t n, int t, double lr, double b1,

@@ -192,8 +192,9 @@ __global__ void mlp_count_kernel(const uint8_t* __restrict__ valid, long long ro
     if (threadIdx.x == 0 && n) atomicAdd(scal + 1, (double)n);
 }
 
-// loss of each row and dL/dy: the head nearest the target carries the squared distance, the
-// logits a softmax cross-entropy towards that head; mean over the valid rows
+// loss of each row and dL/dy: the row's label names the head of its branch (label - 1, from
+// the ray's focal-line count); that head carries the squared distance, the logits a softmax
+// cross-entropy towards it; mean over the labelled rows
 __global__ void mlp_loss_kernel(const float* __restrict__ Y, const float* __restrict__ T,
                                 const uint8_t* __restrict__ valid, long long rows, float beta, MlpActs acts)
 {
@@ -207,17 +208,9 @@ __global__ void mlp_loss_kernel(const float* __restrict__ Y, const float* __rest
         const float inv = nv > 0.0 ? (float)(1.0 / nv) : 0.0f;
         const float* y = Y + i * kMlpOut;
         const float t0 = T[2 * i], t1 = T[2 * i + 1];
-        int j = 0;
-        float best = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kMlpHeads; ++k) {
-            const float e0 = y[2 * k] - t0, e1 = y[2 * k + 1] - t1;
-            const float d = e0 * e0 + e1 * e1;
-            if (k == 0 || d < best) {
-                best = d;
-                j = k;
-            }
-        }
+        const int j = (valid[i] - 1) & (kMlpHeads - 1);
+        const float e0 = y[2 * j] - t0, e1 = y[2 * j + 1] - t1;
+        const float best = e0 * e0 + e1 * e1;
         float zmax = y[8];
 #pragma unroll
         for (int k = 1; k < kMlpHeads; ++k) zmax = fmaxf(zmax, y[8 + k]);
@@ -425,10 +418,11 @@ __global__ void mlp_adam_kernel(float* __restrict__ theta, float* __restrict__ m
     }
 }
 
-// exit directions of orders 0..pmax of one ray
+// exit directions and focal-line counts of orders 0..pmax of one ray
 struct DirSink {
     const ObjDev* o;
     double s[kMaxOrders][3];
+    uint8_t nf[kMaxOrders];
     unsigned int got;
     __device__ void emit(int p, const ExitWave& w)
     {
@@ -437,6 +431,7 @@ struct DirSink {
             s[p][0] = r.s[0];
             s[p][1] = r.s[1];
             s[p][2] = r.s[2];
+            nf[p] = (uint8_t)flag_nf(r.flags);
             got |= 1u << p;
         }
     }
@@ -464,7 +459,7 @@ __global__ void mlp_samples_kernel(const ObjDev* __restrict__ objs, const ObjFea
     for (int p = 0; p <= pmax; ++p) {
         const long long r = (long long)p * n + i;
         const bool ok = (sink.got >> p) & 1u;
-        valid[r] = ok ? 1 : 0;
+        valid[r] = ok ? (uint8_t)(1 + (sink.nf[p] & 3)) : 0;  // label: head N_f mod 4
         T[2 * r] = (float)u0;
         T[2 * r + 1] = (float)u1;
         __nv_bfloat16* x = X + r * kMlpIn;

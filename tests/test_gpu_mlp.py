@@ -77,7 +77,7 @@ def test_gradient_matches_oracle(rtw, oracle_mod):
     x = g.uniform(-1, 1, (rows, 16))
     xb, xr = bf16_rows(x)
     T = g.uniform(-1, 1, (rows, 2)).astype(np.float32)
-    valid = (g.random(rows) < 0.8).astype(np.uint8)
+    valid = np.where(g.random(rows) < 0.8, g.integers(1, 5, rows), 0).astype(np.uint8)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     rtw.rtw_mlp_grad(mlp, 0, xb.cuda(), torch.tensor(T).cuda(), torch.tensor(valid).cuda(), beta=0.2, loss=loss)
     grad = torch.zeros(rtw.RTW_MLP_NPARAM, dtype=torch.float32, device="cuda")
@@ -141,7 +141,7 @@ def test_training_samples_match_oracle_trace(rtw, oracle_mod):
         rec, _, hit = o.trace_ray(x, y, p_max)
         for p in range(p_max + 1):
             ok = bool(rec[p, oracle_mod.VALID])
-            assert bool(Vg[p, i]) == ok
+            assert Vg[p, i] == ((1 + int(rec[p, oracle_mod.NF]) % 4) if ok else 0)
             assert np.array_equal(Tg[p, i], uv[i].astype(np.float32))
             if ok:
                 f = oracle_mod.mlp_features(o, rec[p, oracle_mod.S:oracle_mod.S + 3])[0]

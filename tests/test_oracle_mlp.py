@@ -95,7 +95,7 @@ def test_forward_hidden_permutation_invariance():
 
 def test_loss_closed_form_small_case():
     """Constant network (last layer zero): heads at fixed points, known logits; the loss is the
-    squared distance to the nearest head plus beta times the cross-entropy of that head."""
+    squared distance of the labelled head plus beta times that head's cross-entropy."""
     off = offsets()
     th = rand_theta(7)
     th[off["w4"]:off["b4"]] = 0.0
@@ -105,13 +105,14 @@ def test_loss_closed_form_small_case():
     b4[8:12] = [0.1, -0.3, 0.7, 0.0]
     th[off["b4"]:] = b4
     x = np.zeros((3, O.MLP_IN))
-    target = np.array([[0.45, 0.52], [-0.4, 0.25], [2.0, 2.0]])
-    valid = np.array([1, 1, 0], dtype=np.uint8)
-    loss, _ = O.mlp_loss_grad(th, x, target, valid, beta=0.25)
+    target = np.array([[0.45, 0.52], [-0.4, 0.25], [2.0, 2.0], [0.0, 0.0]])
+    label = np.array([2, 3, 0, 4], dtype=np.uint8)  # heads 1, 2, none, 3
+    loss, _ = O.mlp_loss_grad(th, x[[0, 1, 2, 2]], target, label, beta=0.25)
     lse = math.log(sum(math.exp(v) for v in b4[8:12]))
     l0 = (0.05 ** 2 + 0.02 ** 2) + 0.25 * (lse - (-0.3))
     l1 = (0.1 ** 2 + 0.05 ** 2) + 0.25 * (lse - 0.7)
-    assert abs(loss - (l0 + l1) / 2) < 1e-14
+    l3 = (0.9 ** 2 + 0.9 ** 2) + 0.25 * (lse - 0.0)
+    assert abs(loss - (l0 + l1 + l3) / 3) < 1e-14
 
 
 def test_backward_matches_finite_differences():
@@ -119,7 +120,7 @@ def test_backward_matches_finite_differences():
     g = np.random.default_rng(9)
     x = g.standard_normal((6, O.MLP_IN))
     target = g.uniform(-1, 1, (6, 2))
-    valid = np.array([1, 1, 0, 1, 1, 1], dtype=np.uint8)
+    valid = np.array([1, 2, 0, 3, 4, 1], dtype=np.uint8)
     loss, grad = O.mlp_loss_grad(th, x, target, valid, beta=0.3)
     idx = np.concatenate([g.choice(O.MLP_NPARAM, 60, replace=False), [0, O.MLP_NPARAM - 5, O.MLP_NPARAM - 9]])
     def cd(i, eps):
@@ -130,8 +131,9 @@ def test_backward_matches_finite_differences():
                 O.mlp_loss_grad(tm, x, target, valid, beta=0.3)[0]) / (2 * eps)
 
     for i in idx:
-        fd = (4 * cd(i, 5e-5) - cd(i, 1e-4)) / 3  # Richardson: O(eps^4)
-        assert abs(fd - grad[i]) <= 1e-8 * max(1.0, abs(grad[i])), (i, fd, grad[i])
+        fd = (4 * cd(i, 2.5e-4) - cd(i, 5e-4)) / 3  # Richardson: O(eps^4)
+        # roundoff of the differences: 1e-16 loss / eps
+        assert abs(fd - grad[i]) <= 1e-8 * max(1.0, abs(grad[i])) + 1e-12 * loss, (i, fd, grad[i])
 
 
 def test_adam_first_steps_closed_form():
