@@ -43,13 +43,17 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0)
-    ap.add_argument("--workload", default="ellipsoid", choices=["ellipsoid", "batch"],
-                    help="ellipsoid: the single tilted drop (default); batch: 4096 seed-drawn drops")
+    ap.add_argument("--workload", default="ellipsoid", choices=["ellipsoid", "batch", "learned"],
+                    help="ellipsoid: the single tilted drop (default); batch: 4096 seed-drawn drops; "
+                         "learned: learned proposals vs dense tracing on 1024 drops")
+    ap.add_argument("--retrain", action="store_true", help="learned workload: train even if a checkpoint exists")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="batch workload only")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: default launch options")
     args = ap.parse_args()
     if args.workload == "batch" and args.steps == 50:
         args.steps = 5  # a batch step takes seconds
+    if args.workload == "learned" and args.steps == 50:
+        args.steps, args.warmup = 1, 1  # a learned step takes tens of seconds
     return args
 
 
@@ -246,6 +250,8 @@ def main():
     rtw.lib()
     if args.workload == "batch":
         return bench_batch(args, rank, world, local, dist)
+    if args.workload == "learned":
+        return bench_learned(args, rank, world, local, dist)
     return bench_ellipsoid(args, rank, world, local, dist)
 
 
@@ -523,6 +529,122 @@ def bench_batch(args, rank, world, local, dist):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def field_errors(torch, got, ref, gmask, rmask):
+    """Per-direction errors of a summed field against a reference on the directions unmasked in
+    both whose reference intensity exceeds 1e-3 of its object's largest: fraction within 1e-3
+    relative intensity and 1e-3 rad phase (dominant component), normwise error."""
+    g = got[:, :, 0, :]
+    r = ref[:, :, 0, :]
+    ir = (r.abs() ** 2).sum(-1)
+    ig = (g.abs() ** 2).sum(-1)
+    sel = (gmask == 0) & (rmask == 0) & (ir > 1e-3 * ir.amax(dim=1, keepdim=True))
+    k = r.abs().argmax(-1, keepdim=True)
+    ph = torch.angle(torch.gather(g, -1, k) / torch.gather(r, -1, k))[..., 0].abs()
+    rel = (ig - ir).abs() / ir.clamp_min(1e-300)
+    ok = sel & (rel <= 1e-3) & (ph <= 1e-3)
+    nsel = int(sel.sum().item())
+    d = (g - r)[sel]
+    return {"directions": nsel, "within_1e-3": int(ok.sum().item()) / max(nsel, 1),
+            "normwise": float((d.abs() ** 2).sum().sqrt() / (r[sel].abs() ** 2).sum().sqrt())}
+
+
+def bench_learned(args, rank, world, local, dist):
+    """Learned proposals + Newton on the exact trace against dense tracing on 1024 drops."""
+    import torch
+
+    from paper_2403_13856_gb300 import autotune
+    from paper_2403_13856_gb300 import learned as Lr
+    from paper_2403_13856_gb300 import rtw
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.LEARNED
+    p_max, nt, nph = cfg["p_max"], cfg["n_theta"], cfg["n_phi"]
+    np_ = p_max + 1
+    stream = torch.cuda.current_stream()
+    # networks: trained once on traced rays, kept as a checkpoint
+    ck = os.path.join(ROOT, "paper_2403_13856_gb300", "_cache", "learned_p%d" % p_max)
+    t_train = None
+    if os.path.exists(ck + ".json") and not args.retrain:
+        mlp = Lr.load(ck)
+    else:
+        t0 = time.perf_counter()
+        tspecs, _ = W.batch_objects(cfg["train_objects"], stream=W.STREAM_TRAIN)
+        tobj = rtw.Object([rtw.ObjectSpec(**s) for s in tspecs])
+        samples = [Lr.Samples(tobj, cfg["train_rays"], p_max)]
+        mlp = rtw.MLP(np_, Lr.init_params(np_))
+        losses = Lr.train(mlp, samples, range(np_), steps=cfg["train_steps"], batch=cfg["batch"], lr=3e-3,
+                          lr_end=3e-5)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        Lr.save(mlp, ck, {"losses": losses, "train_s": t_train})
+        del samples, tobj
+    specs, rays = W.batch_objects(cfg["n_objects"], stream=W.STREAM_EVAL)
+    n = len(specs)
+    obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+    dirs = rtw.dirs_grid(nt, nph)
+    ndir = nt * nph
+    shape = (n, ndir, 1, 2)
+    out_l = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    mask_l = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
+    roots = torch.empty((n, ndir, np_), dtype=torch.uint8, device="cuda")
+    lp = rtw.learned_params(p_max)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    with ClockSampler(local) as clk:
+        t_learned = timed(lambda: rtw.rtw_field_learned(obj, mlp, lp, dirs, out_l, mask_l, roots, stream=stream),
+                          args.steps, args.warmup)
+    rtw.rtw_sync_status(stream)
+    # dense tracing on the same drops (autotuned batched launch, graph replay)
+    opts = autotune.tune(specs, rays, p_max, rtw.RTW_FP64, nt, nph)
+    out_d = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    mask_d = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, prec, mode in (("dense_fp64", rtw.RTW_FP64, rtw.RTW_DENSE), ("dense_mixed", rtw.RTW_MIXED, rtw.RTW_DENSE),
+                             ("exact", rtw.RTW_FP64, rtw.RTW_NEWTON)):
+        o_ = out_d if name != "exact" else torch.empty(shape, dtype=torch.complex128, device="cuda")
+        m_ = mask_d if name != "exact" else torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
+        bp = rtw.batch_params(rays, p_max=p_max, precision=prec, use_graph=1, mode=mode, **opts)
+        b = rtw.Batch()
+        t = timed(lambda: rtw.rtw_far_field_batch(obj, bp, dirs, o_, m_, batch=b, stream=stream), 1, 1)
+        rtw.rtw_sync_status(stream)
+        res[name] = (t, o_, m_)
+    ref, rmask = res["exact"][1], res["exact"][2]
+    e_learned = field_errors(torch, out_l, ref, mask_l, rmask)
+    e_dense = field_errors(torch, res["dense_fp64"][1], ref, res["dense_fp64"][2], rmask)
+    t_dense = res["dense_fp64"][0]
+    rows = n * ndir
+    found = roots.to(torch.int64).sum(dim=(0, 1)).tolist()
+    line = {
+        "metric": METRIC, "value": rows / t_learned, "unit": "directions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_learned, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
+        "config": {"workload": "1024 drops of the batched recipe (stream 3), 256x512 (theta,phi) directions, "
+                               "p=0..4; networks trained on 2e7 traced rays of 16384 drops (stream 2)",
+                   "learned_params": {"p_min": 0.05, "max_steps": 5, "tol": "min(1e-6, 1e-4/(k0 L))"},
+                   "l2": "inputs larger than L2"},
+        "learned": {"s_per_field": t_learned, "roots_per_order": found, "errors_vs_exact": e_learned},
+        "dense_fp64": {"s_per_field": t_dense, "errors_vs_exact": e_dense},
+        "dense_mixed": {"s_per_field": res["dense_mixed"][0]},
+        "exact_reference": {"s_per_field": res["exact"][0],
+                            "what": "dense FP64 trace with every hit refined by Newton on the exact trace"},
+        "speedup_learned_vs_dense_fp64": t_dense / t_learned,
+        "train_s": t_train,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

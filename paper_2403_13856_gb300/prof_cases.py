@@ -1,0 +1,94 @@
+"""Small, fixed launches of the library's kernels for profilers (ncu) and quick timings.
+
+    python -m paper_2403_13856_gb300.prof_cases mlp_forward [--rows N]
+    python -m paper_2403_13856_gb300.prof_cases batch [--objects N]
+    python -m paper_2403_13856_gb300.prof_cases learned [--objects N]
+    python -m paper_2403_13856_gb300.prof_cases ellipsoid [--rays N]
+
+Each case builds its inputs (seeded), runs the launch sequence `--reps` times (default 3) after
+one warm-up and prints the CUDA-event time of the last repetition.  Sizes default to cases that
+hold a few GB at most, with inputs larger than L2 where the kernel streams memory.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def _timed(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    t = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+    return t
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid"])
+    ap.add_argument("--rows", type=int, default=1 << 22)
+    ap.add_argument("--objects", type=int, default=64)
+    ap.add_argument("--rays", type=int, default=1_000_000)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    import torch
+
+    from . import build, learned, rtw
+    from . import workloads as W
+
+    build.build()
+    rtw.lib()
+    if a.case == "mlp_forward":
+        mlp = rtw.MLP(1, learned.init_params(1))
+        g = np.random.default_rng(1)
+        X = torch.tensor(g.uniform(-1, 1, (a.rows, 16)), dtype=torch.float32).to(torch.bfloat16).cuda()
+        Y = torch.empty((a.rows, 16), dtype=torch.float32, device="cuda")
+        ms = _timed(torch, lambda: rtw.rtw_mlp_forward(mlp, 0, X, Y), a.reps)
+        flops = 2.0 * a.rows * (16 * 128 + 2 * 128 * 128 + 128 * 16)
+        print(f"mlp_forward rows={a.rows}: {ms:.3f} ms, {flops / ms / 1e9:.1f} TFLOP/s")
+    elif a.case == "batch":
+        specs, rays = W.batch_objects(a.objects)
+        obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+        cfg = W.BATCH
+        out = torch.empty((a.objects, cfg["n_theta"] * cfg["n_phi"], 1, 2), dtype=torch.complex128, device="cuda")
+        bp = rtw.batch_params(rays, p_max=cfg["p_max"])
+        b = rtw.Batch()
+        ms = _timed(torch, lambda: rtw.rtw_far_field_batch(obj, bp, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]), out,
+                                                           batch=b), a.reps)
+        print(f"batch objects={a.objects} rays={int(np.sum(rays))}: {ms:.3f} ms")
+    elif a.case == "learned":
+        cfg = W.LEARNED
+        specs, _ = W.batch_objects(a.objects, stream=W.STREAM_EVAL)
+        obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+        mlp = rtw.MLP(cfg["p_max"] + 1, learned.init_params(cfg["p_max"] + 1))
+        nd = cfg["n_theta"] * cfg["n_phi"]
+        out = torch.empty((a.objects, nd, 1, 2), dtype=torch.complex128, device="cuda")
+        lp = rtw.learned_params(cfg["p_max"])
+        ms = _timed(torch, lambda: rtw.rtw_field_learned(obj, mlp, lp, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]),
+                                                         out), a.reps)
+        print(f"learned objects={a.objects}: {ms:.3f} ms")
+    else:
+        spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
+        obj = rtw.Object([rtw.ObjectSpec(**spec)])
+        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=a.rays)
+        rays = rtw.rtw_trace(obj, tp)
+        out = torch.empty((cfg["n_theta"] * cfg["n_phi"], 1, 2), dtype=torch.complex128, device="cuda")
+
+        def step():
+            rtw.rtw_trace(obj, tp, rays)
+            rtw.rtw_field(rays, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]), out)
+
+        ms = _timed(torch, step, a.reps)
+        print(f"ellipsoid rays={a.rays}: {ms:.3f} ms")
+    rtw.rtw_sync_status()
+
+
+if __name__ == "__main__":
+    main()
