@@ -70,6 +70,8 @@ extern "C" {
                             from +z toward (cos fan_phi, sin fan_phi, 0); fan grids only        */
 #define RTW_DIRS_GRID 1  /* cell-centred theta_i = (i + 1/2) pi / n_theta,
                             phi_j = -pi + (j + 1/2) 2 pi / n_phi, index i * n_phi + j           */
+#define RTW_DIRS_LIST 2  /* n_list directions (theta, phi) read from list (device, n_list x 2
+                            doubles, theta from +z, phi from +x); square grids only            */
 
 #define RTW_FIELD_PER_ORDER 1 /* output one (F_theta, F_phi) pair per order instead of the sum */
 #define RTW_FIELD_PO 2        /* fan grids: physical-optics integral around in-plane folds      */
@@ -115,14 +117,19 @@ typedef struct {
     double fan_phi;
 } rtw_trace_params;
 
-/* Observation directions.  cell_window limits a square-grid field to the cells
- * [ix0, ix1) x [iy0, iy1) of the ray grid (all four -1: every cell); it exists so that a sample of
- * a full-size field can be checked against an independent computation. */
+/* Observation directions (the paper's "directions of interest"): kind RTW_DIRS_PLANE (n_theta,
+ * alpha0, dalpha), RTW_DIRS_GRID (n_theta, n_phi) or RTW_DIRS_LIST (list, n_list; n_list <
+ * 2^31; the list is binned on the device for each call and read during the call only).
+ * cell_window limits a square-grid field to the cells [ix0, ix1) x [iy0, iy1) of the ray grid
+ * (all four -1: every cell); it exists so that a sample of a full-size field can be checked
+ * against an independent computation. */
 typedef struct {
     int kind;
     int n_theta, n_phi;
     double alpha0, dalpha;
     int64_t cell_window[4];
+    const double* list;
+    int64_t n_list;
 } rtw_dirs;
 
 typedef struct rtw_object rtw_object;

@@ -66,6 +66,8 @@ def lib():
         L.or_field_fan.restype = i
         L.or_field_grid.argtypes = [p, i64, d, i, i, i, p, i, p, p, i, p]
         L.or_field_grid.restype = i64
+        L.or_field_dirs.argtypes = [p, i64, d, i, p, i64, i, p, p, i, p]
+        L.or_field_dirs.restype = i64
         L.or_newton.argtypes = [p, i, p, p, d, p]
         L.or_newton.restype = i
         L.om_gelu.argtypes = [d]
@@ -174,6 +176,18 @@ class Object:
         lib().or_field_learned(self.handle, _ptr(theta), int(pmax), int(ntheta), int(nphi), float(p_min),
                                int(max_steps), float(tol), _ptr(out), _ptr(mask), _ptr(roots))
         return out, mask, roots
+
+    def field_dirs(self, pmax, dirs, n_target=0, h=0.0, flags=0, threads=0):
+        """The square-grid field on a list of directions dirs (n x 2: theta, phi)."""
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
+        out = np.zeros((dirs.shape[0], pmax + 1, 4))
+        mask = np.zeros(dirs.shape[0], dtype=np.uint8)
+        nfail = ctypes.c_int64(0)
+        hits = lib().or_field_dirs(self.handle, int(n_target), float(h), int(pmax), _ptr(dirs), dirs.shape[0],
+                                   int(flags), _ptr(out), _ptr(mask), int(threads), ctypes.byref(nfail))
+        if hits < 0:
+            raise RuntimeError("or_field_dirs failed")
+        return out, mask, int(hits), int(nfail.value)
 
     def newton(self, p, target, xy, rmax=0.0):
         target = np.ascontiguousarray(target, dtype=np.float64)

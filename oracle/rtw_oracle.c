@@ -958,9 +958,12 @@ static int edge_in(double e, int64_t ia, int64_t ib, int sigma)
     return (ia < ib) == (sigma > 0);
 }
 
-int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta,
-                      int nphi, const int64_t* window, int flags, double* out, uint8_t* mask,
-                      int nthreads, int64_t* newton_fail)
+/* The square-grid field on either the cell-centred (theta, phi) grid (list == NULL) or the
+ * directions of a list (n_list x (theta, phi)); one loop body tests a direction against a cell
+ * triangle for both. */
+static int64_t field_square(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
+                            const double* list, int64_t n_list, const int64_t* window, int flags, double* out,
+                            uint8_t* mask, int nthreads, int64_t* newton_fail)
 {
     const int np = pmax + 1;
     double h, xc, yc;
@@ -1010,15 +1013,33 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
             }
         free(buf);
     }
-    const int64_t ndir = (int64_t)ntheta * nphi;
+    const int64_t ndir = list ? n_list : (int64_t)ntheta * nphi;
     memset(out, 0, sizeof(double) * (size_t)ndir * np * 4);
     memset(mask, 0, (size_t)ndir);
-    const double dth = PI / ntheta, dph = 2.0 * PI / nphi;
+    const double dth = list ? 1.0 : PI / ntheta, dph = list ? 1.0 : 2.0 * PI / nphi;
     double axial = 2.0 * o->lambda / o->Lmin;
-    for (int i = 0; i < ntheta; ++i) {
-        double th = (i + 0.5) * dth;
-        if (th < axial || th > PI - axial)
-            for (int j = 0; j < nphi; ++j) mask[(int64_t)i * nphi + j] |= OR_MASK_AXIAL;
+    /* unit vector, e_theta, e_phi of every direction */
+    double* dv = (double*)malloc(sizeof(double) * 9 * (size_t)(ndir > 0 ? ndir : 1));
+    for (int64_t dk = 0; dk < ndir; ++dk) {
+        double th, ph;
+        if (list) {
+            th = list[2 * dk];
+            ph = list[2 * dk + 1];
+        } else {
+            th = (dk / nphi + 0.5) * dth;
+            ph = -PI + (dk % nphi + 0.5) * dph;
+        }
+        double* d = dv + 9 * dk;
+        d[0] = sin(th) * cos(ph);
+        d[1] = sin(th) * sin(ph);
+        d[2] = cos(th);
+        d[3] = cos(th) * cos(ph);
+        d[4] = cos(th) * sin(ph);
+        d[5] = -sin(th);
+        d[6] = -sin(ph);
+        d[7] = cos(ph);
+        d[8] = 0.0;
+        if (th < axial || th > PI - axial) mask[dk] |= OR_MASK_AXIAL;
     }
     int64_t hits = 0, nfail = 0;
 #ifdef _OPENMP
@@ -1058,42 +1079,62 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                 for (int c = 0; c < 3; ++c) cm[c] /= cn;
                 double mind = 1.0;
                 for (int v = 0; v < 3; ++v) mind = fmin(mind, dot3(cm, R[v]->s));
+                /* corners more than 90 deg from their mean do not lie in one hemisphere: the edge
+                   planes then bound no proper spherical triangle, and the cell is skipped */
+                if (!(mind > 0.0)) continue;
                 double rho = acos(fmax(-1.0, fmin(1.0, mind))) + 1e-9;
                 double thc = atan2(sqrt(cm[0] * cm[0] + cm[1] * cm[1]), cm[2]);
                 double phc = atan2(cm[1], cm[0]);
-                int it0 = (int)ceil((thc - rho) / dth - 0.5), it1 = (int)floor((thc + rho) / dth - 0.5);
-                if (it0 < 0) it0 = 0;
-                if (it1 > ntheta - 1) it1 = ntheta - 1;
-                int allphi = (thc - rho <= 0.0) || (thc + rho >= PI);
-                double dphi = 0.0;
-                if (!allphi) {
-                    double sr = sin(rho) / sin(thc);
-                    if (sr >= 1.0) allphi = 1;
-                    else dphi = asin(sr);
-                }
-                int64_t jp0 = 0, jcount = nphi;
-                if (!allphi) {
-                    jp0 = (int64_t)ceil((phc - dphi + PI) / dph - 0.5);
-                    int64_t jp1 = (int64_t)floor((phc + dphi + PI) / dph - 0.5);
-                    jcount = jp1 - jp0 + 1;
-                    if (jcount > nphi) {
-                        jp0 = 0;
-                        jcount = nphi;
+                /* candidate directions: the list (all within the cap), or the grid rows and
+                   columns whose centres fall in the cap */
+                int64_t ncand = 0, jp0 = 0, jcount = 0;
+                int it0 = 0, it1 = -1;
+                if (list) {
+                    ncand = ndir;
+                } else {
+                    it0 = (int)ceil((thc - rho) / dth - 0.5);
+                    it1 = (int)floor((thc + rho) / dth - 0.5);
+                    if (it0 < 0) it0 = 0;
+                    if (it1 > ntheta - 1) it1 = ntheta - 1;
+                    int allphi = (thc - rho <= 0.0) || (thc + rho >= PI);
+                    double dphi = 0.0;
+                    if (!allphi) {
+                        double sr = sin(rho) / sin(thc);
+                        if (sr >= 1.0) allphi = 1;
+                        else dphi = asin(sr);
                     }
+                    jp0 = 0;
+                    jcount = nphi;
+                    if (!allphi) {
+                        jp0 = (int64_t)ceil((phc - dphi + PI) / dph - 0.5);
+                        int64_t jp1 = (int64_t)floor((phc + dphi + PI) / dph - 0.5);
+                        jcount = jp1 - jp0 + 1;
+                        if (jcount > nphi) {
+                            jp0 = 0;
+                            jcount = nphi;
+                        }
+                    }
+                    ncand = it1 >= it0 && jcount > 0 ? (int64_t)(it1 - it0 + 1) * jcount : 0;
                 }
-                for (int it = it0; it <= it1; ++it) {
-                    double th = (it + 0.5) * dth;
-                    for (int64_t jj = 0; jj < jcount; ++jj) {
-                        int64_t jp = ((jp0 + jj) % nphi + nphi) % nphi;
-                        double ph = -PI + (jp + 0.5) * dph;
-                        double x[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+                const double cosr = cos(rho);
+                for (int64_t q = 0; q < ncand; ++q) {
+                    int64_t dk;
+                    if (list) {
+                        dk = q;
+                        if (dot3(cm, dv + 9 * dk) < cosr - 1e-12) continue;
+                    } else {
+                        int it = it0 + (int)(q / jcount);
+                        int64_t jp = ((jp0 + q % jcount) % nphi + nphi) % nphi;
+                        dk = (int64_t)it * nphi + jp;
+                    }
+                    {
+                        const double* x = dv + 9 * dk;
                         double e01 = edge_fn(id[0], R[0]->s, id[1], R[1]->s, x);
                         double e12 = edge_fn(id[1], R[1]->s, id[2], R[2]->s, x);
                         double e20 = edge_fn(id[2], R[2]->s, id[0], R[0]->s, x);
                         if (!edge_in(e01, id[0], id[1], sigma) || !edge_in(e12, id[1], id[2], sigma) ||
                             !edge_in(e20, id[2], id[0], sigma))
                             continue;
-                        int64_t dk = (int64_t)it * nphi + jp;
                         if (!consistent) {
 #ifdef _OPENMP
 #pragma omp atomic
@@ -1121,8 +1162,8 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                             for (int c = 0; c < 6; ++c) F[c] = l0 * R[0]->F[c] + l1 * R[1]->F[c] + l2 * R[2]->F[c];
                             psi = l0 * R[0]->psi + l1 * R[1]->psi + l2 * R[2]->psi;
                         }
-                        double eth[3] = {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)};
-                        double eph[3] = {-sin(ph), cos(ph), 0.0};
+                        const double* eth = x + 3;
+                        const double* eph = x + 6;
                         double acc[4] = {0, 0, 0, 0};
                         or_project_add(F, psi, eth, eph, 1.0, acc);
                         double* dst = out + ((size_t)dk * np + p) * 4;
@@ -1140,8 +1181,24 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
         free(nbuf);
     }
     free(cr);
+    free(dv);
     if (newton_fail) *newton_fail = nfail;
     return hits;
+}
+
+int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
+                      const int64_t* window, int flags, double* out, uint8_t* mask, int nthreads,
+                      int64_t* newton_fail)
+{
+    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, window, flags, out, mask, nthreads,
+                        newton_fail);
+}
+
+int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pmax, const double* dirs,
+                      int64_t ndir, int flags, double* out, uint8_t* mask, int nthreads, int64_t* newton_fail)
+{
+    return field_square(o, n_target, h_in, pmax, 0, 0, dirs, ndir, NULL, flags, out, mask, nthreads,
+                        newton_fail);
 }
 
 /* ------------------------------------------------------------------------------------- */

@@ -110,6 +110,12 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                       int nphi, const int64_t* window, int flags, double* out, uint8_t* mask,
                       int nthreads, int64_t* newton_fail);
 
+/* The same field on an arbitrary list of directions: dirs is ndir x (theta, phi) (theta from +z,
+ * phi from +x); out: ndir x (pmax+1) x 4, mask: ndir.  Every direction is tested against every
+ * cell triangle whose cap contains it. */
+int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pmax, const double* dirs,
+                      int64_t ndir, int flags, double* out, uint8_t* mask, int nthreads, int64_t* newton_fail);
+
 /* Newton on the exact trace: finds the ray of order p whose exit direction is target, from the
  * seed impact point xy (2), with steps halved until the residual decreases; the root must lie
  * within rmax of the seed (rmax <= 0: no bound).  Returns iterations used, or -1 if it did not

@@ -131,12 +131,47 @@ int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* 
 }
 
 
+long long dir_count(const rtw_dirs* dirs)
+{
+    return dirs->kind == RTW_DIRS_LIST ? (long long)dirs->n_list : (long long)dirs->n_theta * dirs->n_phi;
+}
+
+// a list is binned on about one bin per direction: nt x 2 nt bins, nt up to 1024
+void dir_grid(const rtw_dirs* dirs, int* nt, int* nph)
+{
+    if (dirs->kind == RTW_DIRS_LIST) {
+        const long long want = (long long)std::ceil(std::sqrt(0.5 * (double)dirs->n_list));
+        const int b = (int)std::min<long long>(1024, std::max<long long>(1, want));
+        *nt = b;
+        *nph = 2 * b;
+    } else {
+        *nt = dirs->n_theta;
+        *nph = dirs->n_phi;
+    }
+}
+
+int check_grid_dirs(const rtw_dirs* dirs, bool window_allowed, const char* who)
+{
+    if (dirs->kind == RTW_DIRS_GRID) {
+        if (dirs->n_theta < 1 || dirs->n_phi < 2) return fail(RTW_ERR_ARG, "%s: n_theta >= 1, n_phi >= 2", who);
+    } else if (dirs->kind == RTW_DIRS_LIST) {
+        if (!dirs->list || dirs->n_list < 1 || dirs->n_list >= (1ll << 31))
+            return fail(RTW_ERR_ARG, "%s: a direction list needs a device pointer and 1 <= n_list < 2^31", who);
+    } else {
+        return fail(RTW_ERR_ARG, "%s: a (theta, phi) grid or list of directions is required", who);
+    }
+    const int64_t* win = dirs->cell_window;
+    const bool windowed = !(win[0] == -1 && win[1] == -1 && win[2] == -1 && win[3] == -1);
+    if (windowed && !window_allowed) return fail(RTW_ERR_ARG, "%s: cell windows are not taken", who);
+    return RTW_OK;
+}
+
 GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs)
 {
     GridPlan g;
     const int64_t* win = dirs->cell_window;
     g.windowed = !(win[0] == -1 && win[1] == -1 && win[2] == -1 && win[3] == -1);
-    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    const long long ndir = dir_count(dirs);
     g.group = (int)std::max<long long>(1, std::min<long long>(nobj, (1ll << 28) / std::max(1ll, 4 * ndir * np)));
     for (int g0 = 0; g0 < nobj; g0 += g.group) {
         long long cells = 0;
@@ -158,7 +193,11 @@ GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs)
 
 size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, GridWs* w)
 {
-    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    const long long ndir = dir_count(dirs);
+    int nt = 0, nph = 0;
+    dir_grid(dirs, &nt, &nph);
+    const bool list = dirs->kind == RTW_DIRS_LIST;
+    const size_t nl = list ? (size_t)ndir : 0, nb = list ? (size_t)nt * (size_t)nph + 1 : 0;
     // list of large triangles: 1/32 of a group's triangles, at least 65536
     const unsigned int big_cap =
         (unsigned int)std::min<long long>(std::max<long long>(65536, 2 * g.max_group_cells / 32), 1ll << 26);
@@ -166,8 +205,15 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     size_t off_mask = 0;
     size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir * (size_t)g.group, 256);
     // double tables then their single-precision copies
-    size_t off_cells = align_up(off_tab + sizeof(double) * 3 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi), 256);
-    size_t off_big = align_up(off_cells + sizeof(GridCells) * (size_t)g.group, 256);
+    size_t off_cells = align_up(off_tab + sizeof(double) * 3 * ((size_t)nt + (size_t)nph), 256);
+    size_t off_ldir = align_up(off_cells + sizeof(GridCells) * (size_t)g.group, 256);
+    size_t off_ldirf = align_up(off_ldir + sizeof(double) * 4 * nl, 256);
+    size_t off_binid = align_up(off_ldirf + sizeof(float4) * nl, 256);
+    size_t off_count = align_up(off_binid + sizeof(int) * nl, 256);
+    size_t off_first = align_up(off_count + sizeof(int) * nb, 256);
+    size_t off_cursor = align_up(off_first + sizeof(int) * nb, 256);
+    size_t off_bindir = align_up(off_cursor + sizeof(int) * nb, 256);
+    size_t off_big = align_up(off_bindir + sizeof(int) * nl, 256);
     size_t off_cnt = align_up(off_big + 8 * (size_t)big_cap, 256);
     size_t off_hit_tri = align_up(off_cnt + 256, 256);
     size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
@@ -176,6 +222,13 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
         w->mask_words = (unsigned int*)(base + off_mask);
         w->tab = (double*)(base + off_tab);
         w->cells = (GridCells*)(base + off_cells);
+        w->ldir = list ? (double*)(base + off_ldir) : nullptr;
+        w->ldir_f = list ? (float4*)(base + off_ldirf) : nullptr;
+        w->binid = list ? (int*)(base + off_binid) : nullptr;
+        w->count = list ? (int*)(base + off_count) : nullptr;
+        w->first = list ? (int*)(base + off_first) : nullptr;
+        w->cursor = list ? (int*)(base + off_cursor) : nullptr;
+        w->bin_dir = list ? (int*)(base + off_bindir) : nullptr;
         w->big = (unsigned long long*)(base + off_big);
         w->nbig = (unsigned int*)(base + off_cnt);
         w->nhit = w->nbig + 1;
@@ -187,13 +240,36 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     return total;
 }
 
+int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t s)
+{
+    std::memset(d, 0, sizeof(*d));
+    dir_grid(dirs, &d->nt, &d->nph);
+    d->tab = w.tab;
+    d->ndir = dir_count(dirs);
+    RTW_CUDA(launch_dir_tables(d->nt, d->nph, w.tab, s));
+    if (dirs->kind == RTW_DIRS_LIST) {
+        d->list = 1;
+        d->bin_first = w.first;
+        d->bin_dir = w.bin_dir;
+        d->ldir = w.ldir;
+        d->ldir_f = w.ldir_f;
+        d->lsrc = dirs->list;
+        // a bin spans pi / nt in theta and at most as much in arc along phi: its points lie within
+        // sqrt(2) / 2 pi / nt of its centre
+        d->pad = (float)(0.75 * kPi / d->nt + 1e-6);
+        RTW_CUDA(launch_bin_dirs(dirs->list, d->ndir, d->nt, d->nph, w.ldir, w.ldir_f, w.binid, w.count, w.first,
+                                 w.cursor, w.bin_dir, s));
+    }
+    return RTW_OK;
+}
+
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
-                   const rtw_dirs* dirs, bool per_order, double* out, unsigned char* mask_out, const GridWs& w,
-                   int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
+                   const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
+                   const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s)
 {
     const int np = st.np;
-    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    const long long ndir = d.ndir;
     const int nout = per_order ? np : 1;
     const size_t out_obj = 4 * (size_t)nout * (size_t)ndir;  // doubles per object
     const int64_t* win = dirs->cell_window;
@@ -227,11 +303,11 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
         }
         b.ndir = ndir;
         b.nout = nout;
-        RTW_CUDA(launch_field_grid(a, b, dirs->n_theta, dirs->n_phi, w.tab, w.big, w.nbig, w.big_cap, w.hit_tri,
-                                   w.hit_dir, w.nhit, w.hit_cap, classify_block, newton, s));
+        RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
+                                   classify_block, newton, s));
         if (mask_out)
-            RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir, 1,
-                                          dirs->n_theta, dirs->n_phi, 0.0, 0.0, s));
+            RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir,
+                                          d.list ? 2 : 1, d.nt, d.nph, 0.0, 0.0, s, d.lsrc));
     }
     return RTW_OK;
 }
@@ -548,17 +624,19 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
             std::fabs(dirs->dalpha) * dirs->n_theta > 2.0 * kPi + 1e-9)
             return fail(RTW_ERR_ARG, "rtw_field: plane grid needs n >= 1, 0 < |dalpha| <= 0.5, span <= 2 pi");
         ndir = dirs->n_theta;
-    } else if (dirs->kind == RTW_DIRS_GRID) {
-        if (rays->grid != RTW_GRID_SQUARE) return fail(RTW_ERR_ARG, "rtw_field: (theta, phi) grids need a square grid");
-        if (dirs->n_theta < 1 || dirs->n_phi < 2) return fail(RTW_ERR_ARG, "rtw_field: n_theta >= 1, n_phi >= 2");
-        ndir = (long long)dirs->n_theta * dirs->n_phi;
+    } else if (dirs->kind == RTW_DIRS_GRID || dirs->kind == RTW_DIRS_LIST) {
+        if (rays->grid != RTW_GRID_SQUARE)
+            return fail(RTW_ERR_ARG, "rtw_field: (theta, phi) grids and lists need a square grid");
+        int rc = rtw::host::check_grid_dirs(dirs, true, "rtw_field");
+        if (rc != RTW_OK) return rc;
+        ndir = rtw::host::dir_count(dirs);
     } else {
         return fail(RTW_ERR_ARG, "rtw_field: unknown direction kind %d", dirs->kind);
     }
     if (po && (rays->grid != RTW_GRID_FAN || !rays->st.aux))
         return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO needs a fan traced with RTW_TRACE_APERTURE");
     unsigned int* status = status_word(rays->device);
-    if (dirs->kind == RTW_DIRS_GRID) {
+    if (dirs->kind != RTW_DIRS_PLANE) {
         const rtw::host::GridPlan g = rtw::host::plan_grid(rays->objs.data(), rays->nobj, rays->np, dirs);
         const size_t total = rtw::host::grid_ws(g, rays->np, dirs, nullptr, nullptr);
         if (rays->ws_bytes < total) {
@@ -572,9 +650,11 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         rtw::host::GridWs w;
         rtw::host::grid_ws(g, rays->np, dirs, (char*)rays->ws, &w);
         RTW_CUDA(cudaMemsetAsync(field_out, 0, sizeof(double) * 4 * (size_t)nout * (size_t)ndir * (size_t)rays->nobj, s));
-        RTW_CUDA(rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, w.tab, s));
-        return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, per_order,
-                                         (double*)field_out, mask_out, w, 0, newton, status,
+        rtw::DirSet d;
+        int rc = rtw::host::dirs_prepare(dirs, w, &d, s);
+        if (rc != RTW_OK) return rc;
+        return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, d,
+                                         per_order, (double*)field_out, mask_out, w, 0, newton, status,
                                          newton_counter(rays->device), s);
     }
     // fan: workspace of mask words, PO windows and scratch

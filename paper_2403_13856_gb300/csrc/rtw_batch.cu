@@ -102,7 +102,7 @@ int enqueue(rtw_batch* b, const rtw_batch_params* bp, const rtw_dirs* dirs, bool
             uint8_t* mask_out, bool timing, cudaStream_t q)
 {
     const int np = bp->p_max + 1;
-    const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
+    const long long ndir = rtw::host::dir_count(dirs);
     const int nout = per_order ? np : 1;
     unsigned int* status = rtw::host::status_word(b->device);
     if (!status) return fail(RTW_ERR_CUDA, "rtw_far_field_batch: status word");
@@ -112,7 +112,9 @@ int enqueue(rtw_batch* b, const rtw_batch_params* bp, const rtw_dirs* dirs, bool
     rtw::host::GridWs w;
     rtw::host::grid_ws(b->ws_plan, np, dirs, ws + 256, &w);
     RTW_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 4 * (size_t)nout * (size_t)ndir * b->objs.size(), q));
-    RTW_CUDA(rtw::launch_dir_tables(dirs->n_theta, dirs->n_phi, w.tab, q));
+    rtw::DirSet d;
+    int rcd = rtw::host::dirs_prepare(dirs, w, &d, q);
+    if (rcd != RTW_OK) return rcd;
     const int variant = bp->trace_variant > 0 ? bp->trace_variant : 2;
     int e = 0;
     for (const Chunk& c : b->chunks) {
@@ -124,7 +126,7 @@ int enqueue(rtw_batch* b, const rtw_batch_params* bp, const rtw_dirs* dirs, bool
                                          bp->trace_ctas_per_sm, q));
         if (timing) RTW_CUDA(cudaEventRecord(b->ev[(size_t)e++], q));
         int rc = rtw::host::grid_field_run(b->objs.data() + c.first, b->d_objs + c.first, c.count, st, c.plan, dirs,
-                                           per_order, out + 4 * (size_t)nout * (size_t)ndir * (size_t)c.first,
+                                           d, per_order, out + 4 * (size_t)nout * (size_t)ndir * (size_t)c.first,
                                            mask_out ? mask_out + (size_t)ndir * (size_t)c.first : nullptr, w,
                                            bp->classify_block, bp->mode == RTW_NEWTON ? 1 : 0, status,
                                            rtw::host::newton_counter(b->device), q);
@@ -149,10 +151,10 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
     if (bp->precision != RTW_FP64 && bp->precision != RTW_MIXED)
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: precision %d", bp->precision);
     if (flags & ~RTW_FIELD_PER_ORDER) return fail(RTW_ERR_ARG, "rtw_far_field_batch: flags 0x%x", flags);
-    if (dirs->kind != RTW_DIRS_GRID || dirs->n_theta < 1 || dirs->n_phi < 2)
-        return fail(RTW_ERR_ARG, "rtw_far_field_batch: a (theta, phi) grid with n_theta >= 1, n_phi >= 2");
-    for (int k = 0; k < 4; ++k)
-        if (dirs->cell_window[k] != -1) return fail(RTW_ERR_ARG, "rtw_far_field_batch: cell windows are not taken");
+    {
+        int rcd = rtw::host::check_grid_dirs(dirs, false, "rtw_far_field_batch");
+        if (rcd != RTW_OK) return rcd;
+    }
     if (bp->trace_variant < 0 || bp->trace_variant > rtw::kTraceVariants)
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: trace_variant %d", bp->trace_variant);
     if (bp->classify_block != 0 && bp->classify_block != 64 && bp->classify_block != 128 && bp->classify_block != 256)
@@ -233,8 +235,11 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
     put(key, bp->trace_ctas_per_sm);
     put(key, bp->classify_block);
     put(key, bp->mode);
+    put(key, dirs->kind);
     put(key, dirs->n_theta);
     put(key, dirs->n_phi);
+    put(key, dirs->list);
+    put(key, dirs->n_list);
     put(key, flags);
     put(key, field_out);
     put(key, mask_out);

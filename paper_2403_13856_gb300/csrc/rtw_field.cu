@@ -132,8 +132,9 @@ struct TriGeom {
 };
 
 // loads the corners and the single-precision candidate cap; returns the number of candidates
-__device__ long long tri_setup(const FieldArgs& a, long long base, TriGeom& g, int nt, int nph)
+__device__ long long tri_setup(const FieldArgs& a, long long base, TriGeom& g, const DirSet& d)
 {
+    const int nt = d.nt, nph = d.nph;
     if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) return 0;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -158,7 +159,11 @@ __device__ long long tri_setup(const FieldArgs& a, long long base, TriGeom& g, i
         const float dx = g.s[v][0] - cmx, dy = g.s[v][1] - cmy, dz = g.s[v][2] - cmz;
         ch = fmaxf(ch, sqrtf(dx * dx + dy * dy + dz * dz));
     }
-    const float rho = 2.0f * asinf(fminf(1.0f, 0.5f * ch)) + 1e-5f;
+    // corners more than 90 deg (chord sqrt 2) from their mean do not lie in one hemisphere: the
+    // edge planes bound no proper spherical triangle, and the cell is skipped
+    if (!(ch < 1.41421356f)) return 0;
+    // a list's bins are candidates when their centre lies within the cap widened by a bin radius
+    const float rho = 2.0f * asinf(fminf(1.0f, 0.5f * ch)) + 1e-5f + d.pad;
     const float thc = atan2f(sqrtf(cmx * cmx + cmy * cmy), cmz), phc = atan2f(cmy, cmx);
     const float dth = 3.14159265358979f / nt, dph = 6.28318530717959f / nph;
     g.it0 = max((int)ceilf((thc - rho) / dth - 0.5f), 0);
@@ -287,12 +292,11 @@ __device__ __forceinline__ void push_hit(const HitArgs& h, unsigned int* status,
 }
 
 __device__ __forceinline__ void candidate(const FieldArgs& a, const HitArgs& h, const TriFrame& fr,
-                                          unsigned long long code, unsigned int* mask, int it, int jp, int nph,
-                                          float dx0, float dx1, float dx2)
+                                          unsigned long long code, unsigned int* mask, unsigned int dk, float dx0,
+                                          float dx1, float dx2)
 {
     const int cls = tri_classify(fr, dx0, dx1, dx2);
     if (cls == 0) return;
-    const unsigned int dk = (unsigned int)it * (unsigned int)nph + (unsigned int)jp;
     if (cls == 2) {
         push_hit(h, a.status, code, dk | kHitClose);
     } else if (!fr.ok) {  // singular or folded cell: mark, add nothing
@@ -351,19 +355,38 @@ __device__ __forceinline__ DirTabF dir_tab_f(const double* tab, int nt, int nph)
 
 // Phase 1: one thread per (object, order, cell).  Triangles with few candidates are tested here;
 // larger ones go to the big list (one warp each in phase 2).
-__global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch b, int nt, int nph,
-                                                         const double* __restrict__ tab, unsigned long long* big,
+// every candidate direction of one (bin) grid point (it, jp): the point itself, or a bin's list
+__device__ __forceinline__ void candidates_at(const FieldArgs& a, const HitArgs& h, const DirSet& d,
+                                              const DirTabF& T, const TriFrame& fr, const TriGeom& g,
+                                              unsigned long long code, unsigned int* mask, int it, int jp)
+{
+    if (!d.list) {
+        const float sth = T.st[it];
+        candidate(a, h, fr, code, mask, (unsigned int)it * (unsigned int)d.nph + (unsigned int)jp,
+                  sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1], T.ct[it] - g.c[2]);
+        return;
+    }
+    const int bn = it * d.nph + jp;
+    for (int m = d.bin_first[bn]; m < d.bin_first[bn + 1]; ++m) {
+        const unsigned int dk = (unsigned int)d.bin_dir[m];
+        const float4 x = d.ldir_f[dk];
+        candidate(a, h, fr, code, mask, dk, x.x - g.c[0], x.y - g.c[1], x.z - g.c[2]);
+    }
+}
+
+__global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch b, DirSet d, unsigned long long* big,
                                                          unsigned int* nbig, unsigned int big_cap, HitArgs h)
 {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= b.total) return;
     const CellRef c = decode_cell(a, b, tid);
     unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
-    const DirTabF T = dir_tab_f(tab, nt, nph);
+    const int nph = d.nph;
+    const DirTabF T = dir_tab_f(d.tab, d.nt, nph);
     for (int t = 0; t < 2; ++t) {
         TriGeom g;
         cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
-        const long long nc = tri_setup(a, c.base, g, nt, nph);
+        const long long nc = tri_setup(a, c.base, g, d);
         if (nc == 0) continue;
         const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
         if (nc > kInlineCandidates) {
@@ -376,27 +399,25 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
         TriFrame fr;
         tri_frame(a, c.base, g, fr);
         for (int it = g.it0; it <= g.it1; ++it) {
-            const float ct = T.ct[it], sth = T.st[it];
             for (int jj = 0; jj < g.jcount; ++jj) {
                 int jp = g.jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidate(a, h, fr, code, mask, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
-                          ct - g.c[2]);
+                candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
             }
         }
     }
 }
 
 // Phase 2: one warp per listed triangle, rows in turn, the lanes taking the columns.
-__global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBatch b, int nt, int nph,
-                                                             const double* __restrict__ tab,
+__global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBatch b, DirSet d,
                                                              const unsigned long long* big, const unsigned int* nbig,
                                                              unsigned int big_cap, HitArgs h)
 {
     const unsigned int n = min(*nbig, big_cap);
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    const DirTabF T = dir_tab_f(tab, nt, nph);
+    const int nph = d.nph;
+    const DirTabF T = dir_tab_f(d.tab, d.nt, nph);
     for (long long w = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
         const unsigned long long code = big[w];
         const int t = (int)(code & 1ull);
@@ -404,16 +425,14 @@ __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBa
         unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
         TriGeom g;
         cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
-        if (tri_setup(a, c.base, g, nt, nph) == 0) continue;
+        if (tri_setup(a, c.base, g, d) == 0) continue;
         TriFrame fr;
         tri_frame(a, c.base, g, fr);
         for (int it = g.it0; it <= g.it1; ++it) {
-            const float ct = T.ct[it], sth = T.st[it];
             for (int jj = lane; jj < g.jcount; jj += 32) {
                 int jp = g.jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidate(a, h, fr, code, mask, it, jp, nph, sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1],
-                          ct - g.c[2]);
+                candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
             }
         }
     }
@@ -421,14 +440,15 @@ __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBa
 
 // Phase 3: one thread per (triangle, direction) pair: the double-precision rule for close calls,
 // then the barycentric weights of the central projection, F, Psi and F e^{i Psi}.
-__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBatch b, int nt, int nph,
-                                                             const double* __restrict__ tab, HitArgs h, int newton)
+__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h,
+                                                             int newton)
 {
     const unsigned int n = min(*h.n, h.cap);
-    const double* ctab = tab;
-    const double* stab = tab + nt;
-    const double* cptab = tab + 2 * nt;
-    const double* sptab = tab + 2 * nt + nph;
+    const int nt = d.nt, nph = d.nph;
+    const double* ctab = d.tab;
+    const double* stab = d.tab + nt;
+    const double* cptab = d.tab + 2 * nt;
+    const double* sptab = d.tab + 2 * nt + nph;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
         const unsigned long long code = h.tri[q];
@@ -456,8 +476,20 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBa
                 sg[e] = -1.0;
             }
         }
-        const int it = (int)(dk / (unsigned int)nph), jp = (int)(dk % (unsigned int)nph);
-        const double ct = ctab[it], sth = stab[it], cp = cptab[jp], sp = sptab[jp];
+        double ct, sth, cp, sp;
+        if (d.list) {
+            const double* q = d.ldir + 4 * (long long)dk;
+            ct = q[0];
+            sth = q[1];
+            cp = q[2];
+            sp = q[3];
+        } else {
+            const int it = (int)(dk / (unsigned int)nph), jp = (int)(dk % (unsigned int)nph);
+            ct = ctab[it];
+            sth = stab[it];
+            cp = cptab[jp];
+            sp = sptab[jp];
+        }
         const double x[3] = {sth * cp, sth * sp, ct};
         double e[3];
 #pragma unroll
@@ -949,7 +981,8 @@ __global__ void grid_cells_kernel(const ObjDev* objs, int n, int np, int windowe
 }
 
 __global__ void finalize_mask_kernel(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,
-                                     long long ndir, int kind, int nt, int nph, double alpha0, double dalpha)
+                                     long long ndir, int kind, int nt, int nph, double alpha0, double dalpha,
+                                     const double* list)
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= ndir * nobj) return;
@@ -959,16 +992,91 @@ __global__ void finalize_mask_kernel(const unsigned int* words, unsigned char* m
     double th;
     if (kind == 0) {
         th = fabs(alpha0 + d * dalpha);
-    } else {
+    } else if (kind == 1) {
         const int it = (int)(d / nph);
         th = (it + 0.5) * (kPi / nt);
+    } else {
+        th = acos(fmin(1.0, fmax(-1.0, cos(list[2 * d]))));  // polar angle of the listed direction
     }
     unsigned int m = words[t];
     if (th < axial || th > kPi - axial) m |= kMaskAxial;
     mask_out[t] = (unsigned char)m;
 }
 
+// unit vector (double cos/sin pairs and single-precision xyz) and bin of every listed direction
+__global__ void list_prep_kernel(const double* __restrict__ list, long long n, int nt, int nph, double* ldir,
+                                 float4* ldir_f, int* binid, int* count)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double th = list[2 * i], ph = list[2 * i + 1];
+    double st, ct, sp, cp;
+    sincos(th, &st, &ct);
+    sincos(ph, &sp, &cp);
+    ldir[4 * i] = ct;
+    ldir[4 * i + 1] = st;
+    ldir[4 * i + 2] = cp;
+    ldir[4 * i + 3] = sp;
+    const double x = st * cp, y = st * sp;
+    ldir_f[i] = make_float4((float)x, (float)y, (float)ct, 0.0f);
+    // bin of the direction itself (theta in [0, pi], phi in [-pi, pi))
+    const double tq = atan2(sqrt(x * x + y * y), ct), pq = atan2(y, x);
+    int it = (int)floor(tq * nt / kPi), jp = (int)floor((pq + kPi) * nph / (2.0 * kPi));
+    it = it < 0 ? 0 : (it >= nt ? nt - 1 : it);
+    jp = jp < 0 ? 0 : (jp >= nph ? nph - 1 : jp);
+    const int b = it * nph + jp;
+    binid[i] = b;
+    atomicAdd(count + b, 1);
+}
+
+// exclusive prefix of count[0, n) into first[0, n] (one block; n up to a few million)
+__global__ void __launch_bounds__(1024) list_scan_kernel(const int* __restrict__ count, int n, int* __restrict__ first)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x, per = (n + 1023) / 1024;
+    const int lo = min(t * per, n), hi = min(lo + per, n);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += count[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int i = lo; i < hi; ++i) {
+        first[i] = run;
+        run += count[i];
+    }
+    if (t == 1023) first[n] = part[1023];
+}
+
+__global__ void list_fill_kernel(const int* __restrict__ binid, long long n, const int* __restrict__ first,
+                                 int* cursor, int* __restrict__ bin_dir)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = binid[i];
+    bin_dir[first[b] + atomicAdd(cursor + b, 1)] = (int)i;
+}
+
 }  // namespace
+
+cudaError_t launch_bin_dirs(const double* list, long long n, int nt, int nph, double* ldir, float4* ldir_f,
+                            int* binid, int* count, int* first, int* cursor, int* bin_dir, cudaStream_t s)
+{
+    const int nb = nt * nph;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(nb + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)(nb + 1), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    list_prep_kernel<<<g, 256, 0, s>>>(list, n, nt, nph, ldir, ldir_f, binid, count);
+    list_scan_kernel<<<1, 1024, 0, s>>>(count, nb, first);
+    list_fill_kernel<<<g, 256, 0, s>>>(binid, n, first, cursor, bin_dir);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
 {
@@ -977,10 +1085,10 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, int nph, const double* tab,
-                              unsigned long long* big, unsigned int* nbig, unsigned int big_cap,
-                              unsigned long long* hit_tri, unsigned int* hit_dir, unsigned int* nhit,
-                              unsigned int hit_cap, int classify_block, int newton, cudaStream_t s)
+cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
+                              unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
+                              unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
+                              int newton, cudaStream_t s)
 {
     if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
@@ -989,13 +1097,13 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, in
     if (e == cudaSuccess) e = cudaMemsetAsync(nhit, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     HitArgs h{hit_tri, hit_dir, nhit, hit_cap};
-    field_grid_kernel<<<(unsigned)((b.total + cb - 1) / cb), cb, 0, s>>>(a, b, nt, nph, tab, big, nbig, big_cap, h);
+    field_grid_kernel<<<(unsigned)((b.total + cb - 1) / cb), cb, 0, s>>>(a, b, d, big, nbig, big_cap, h);
     // fixed grids walk the lists: 16 blocks per SM
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    field_grid_big_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, big, nbig, big_cap, h);
-    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, nt, nph, tab, h, newton);
+    field_grid_big_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, big, nbig, big_cap, h);
+    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h, newton);
     return cudaGetLastError();
 }
 
@@ -1044,12 +1152,13 @@ cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, 
 }
 
 cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,
-                                 long long ndir, int kind, int nt, int nph, double alpha0, double dalpha, cudaStream_t s)
+                                 long long ndir, int kind, int nt, int nph, double alpha0, double dalpha, cudaStream_t s,
+                                 const double* list)
 {
     if (!mask_out || ndir == 0 || nobj == 0) return cudaSuccess;
     const long long n = ndir * nobj;
     finalize_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(words, mask_out, objs, nobj, ndir, kind, nt, nph,
-                                                                      alpha0, dalpha);
+                                                                      alpha0, dalpha, list);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,12 @@ void fill_objdev(const ObjHost& o, ObjDev& d);
 // ray grid of one object: spacing, size, fan half-width (host arithmetic only)
 int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* nx, long long* ny, double* fan_w);
 
+// number of directions of a (theta, phi) grid or list; the (bin) grid the kernels walk
+long long dir_count(const rtw_dirs* dirs);
+void dir_grid(const rtw_dirs* dirs, int* nt, int* nph);
+// validates a (theta, phi) grid or list for a square-grid field (window allowed or not)
+int check_grid_dirs(const rtw_dirs* dirs, bool window_allowed, const char* who);
+
 // Launch groups of a square-grid field: objects [k group, (k+1) group) share one launch sequence;
 // the group size is bounded by the hit list (4 (triangle, direction) pairs per direction and order
 // of each object, at most 2^28 pairs).
@@ -57,8 +63,16 @@ GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs);
 // Grid-field workspace carved from one device block.
 struct GridWs {
     unsigned int* mask_words = nullptr;  // group x directions
-    double* tab = nullptr;               // direction tables
+    double* tab = nullptr;               // tables of the direction (or bin) grid
     GridCells* cells = nullptr;          // group entries
+    // direction lists: per-direction unit vectors and bins, bin offsets and lists
+    double* ldir = nullptr;
+    float4* ldir_f = nullptr;
+    int* binid = nullptr;
+    int* count = nullptr;
+    int* first = nullptr;
+    int* cursor = nullptr;
+    int* bin_dir = nullptr;
     unsigned long long* big = nullptr;
     unsigned int* nbig = nullptr;
     unsigned int* nhit = nullptr;
@@ -69,14 +83,17 @@ struct GridWs {
 // Bytes of the workspace of plan g; carves it from base when base is not null.
 size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, GridWs* w);
 
-// Field of objects [0, nobj) of ray state st on the (theta, phi) grid of dirs.  h_objs and d_objs
+// Fills the direction tables (and bins a list) in w; d describes the directions to the kernels.
+int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t s);
+
+// Field of objects [0, nobj) of ray state st on the (theta, phi) grid or list of dirs (d from
+// dirs_prepare on the same stream).  h_objs and d_objs
 // are the same table on the host and the device.  Adds into out, which the caller cleared:
 // [objects][directions][nout][4] doubles.  mask_out (may be null): [objects][directions] bytes.
-// The direction tables in w must have been filled (launch_dir_tables) on the same stream.
 // newton = 1 replaces every interpolated hit by the exact ray found by Newton steps.
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
-                   const rtw_dirs* dirs, bool per_order, double* out, unsigned char* mask_out, const GridWs& w,
-                   int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
+                   const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
+                   const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s);
 
 // per-object feature table of the learned proposal

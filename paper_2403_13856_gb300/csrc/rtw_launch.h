@@ -33,6 +33,21 @@ struct GridBatch {
     int nout;                // (F_theta, F_phi) pairs per direction: orders or 1
 };
 
+// Directions of a square-grid field: the cell-centred (theta, phi) grid, or a list binned on a
+// (theta, phi) grid of bins (then nt x nph are the bins and each bin lists its directions).
+struct DirSet {
+    int nt, nph;             // direction grid, or bin grid of a list
+    const double* tab;       // cos theta, sin theta, cos phi, sin phi of the (bin) grid, then float copies
+    int list;                // 1: the directions come from a list
+    long long ndir;          // grid: nt nph; list: its length
+    const int* bin_first;    // list: first entry of every bin (nt nph + 1)
+    const int* bin_dir;      // list: direction indices, bin after bin
+    const double* ldir;      // list: cos theta, sin theta, cos phi, sin phi per direction
+    const float4* ldir_f;    // list: unit vector (x, y, z, 0) in single precision
+    const double* lsrc;      // list: the caller's (theta, phi) pairs
+    float pad;               // list: angular radius of a bin (widens the candidate cap)
+};
+
 struct CellRef {
     const ObjDev* o;
     int orel;  // object within the launch
@@ -69,10 +84,14 @@ cudaError_t launch_export(RaysDev st, int order, long long first, long long coun
 
 // field
 cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s);
-cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, int nt, int nph, const double* tab,
-                              unsigned long long* big, unsigned int* nbig, unsigned int big_cap,
-                              unsigned long long* hit_tri, unsigned int* hit_dir, unsigned int* nhit,
-                              unsigned int hit_cap, int classify_block, int newton, cudaStream_t s);
+cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
+                              unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
+                              unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
+                              int newton, cudaStream_t s);
+// bins a direction list: unit vectors, bin of every direction, bin offsets and bin lists;
+// count and cursor hold nt nph + 1 ints each
+cudaError_t launch_bin_dirs(const double* list, long long n, int nt, int nph, double* ldir, float4* ldir_f,
+                            int* binid, int* count, int* first, int* cursor, int* bin_dir, cudaStream_t s);
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
                              double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
                              int newton, cudaStream_t s);
@@ -98,8 +117,9 @@ cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double
 
 cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
                               cudaStream_t s);
+// kind 0: plane angles alpha0 + k dalpha; 1: (theta, phi) grid nt x nph; 2: list of (theta, phi) pairs
 cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_out, const ObjDev* objs, int nobj,
                                  long long ndir, int kind, int nt, int nph, double alpha0, double dalpha,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const double* list = nullptr);
 
 }  // namespace rtw

@@ -19,7 +19,7 @@ RTW_OK = 0
 RTW_GRID_FAN, RTW_GRID_SQUARE = 0, 1
 RTW_FP64, RTW_MIXED = 0, 1
 RTW_DENSE, RTW_NEWTON = 0, 1
-RTW_DIRS_PLANE, RTW_DIRS_GRID = 0, 1
+RTW_DIRS_PLANE, RTW_DIRS_GRID, RTW_DIRS_LIST = 0, 1, 2
 RTW_FIELD_PER_ORDER, RTW_FIELD_PO, RTW_FIELD_NEAR_FOLDS = 1, 2, 4
 RTW_TRACE_APERTURE = 1
 RTW_MASK_CAUSTIC, RTW_MASK_AXIAL, RTW_MASK_PO = 1, 2, 4
@@ -51,7 +51,8 @@ class rtw_trace_params(ctypes.Structure):
 
 class rtw_dirs(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
-                ("alpha0", ctypes.c_double), ("dalpha", ctypes.c_double), ("cell_window", ctypes.c_int64 * 4)]
+                ("alpha0", ctypes.c_double), ("dalpha", ctypes.c_double), ("cell_window", ctypes.c_int64 * 4),
+                ("list", ctypes.c_void_p), ("n_list", ctypes.c_int64)]
 
 
 class rtw_batch_params(ctypes.Structure):
@@ -235,6 +236,18 @@ def dirs_grid(n_theta: int, n_phi: int, cell_window=None) -> rtw_dirs:
     return d
 
 
+def dirs_list(theta_phi) -> rtw_dirs:
+    """Directions from a device tensor of (theta, phi) pairs (float64, n x 2), kept alive on the
+    returned structure."""
+    d = rtw_dirs()
+    d.kind, d.n_theta, d.n_phi, d.alpha0, d.dalpha = RTW_DIRS_LIST, 0, 0, 0.0, 0.0
+    d.cell_window[:] = [-1, -1, -1, -1]
+    d._keep = theta_phi
+    d.list = theta_phi.data_ptr()
+    d.n_list = theta_phi.shape[0]
+    return d
+
+
 def rtw_field(rays: Rays, dirs: rtw_dirs, out, mask=None, mode=RTW_DENSE, flags=0, stream=None):
     _check(lib().rtw_field(rays.handle, ctypes.byref(dirs), mode, flags, _ptr(out), _ptr(mask), _stream_ptr(stream)))
 
@@ -376,6 +389,8 @@ def rtw_version() -> str:
 
 
 def n_dirs(dirs: rtw_dirs) -> int:
+    if dirs.kind == RTW_DIRS_LIST:
+        return dirs.n_list
     return dirs.n_theta if dirs.kind == RTW_DIRS_PLANE else dirs.n_theta * dirs.n_phi
 
 

@@ -140,6 +140,29 @@ def test_batch_newton_vs_oracle_exact(rtw, oracle_mod):
     assert gfail == total_fail
 
 
+def test_batch_direction_list_vs_oracle(rtw, oracle_mod):
+    """The batch on a list of 1500 directions (poles, seam, duplicate included), 5 drops."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(5, **SMALL)
+    obj = make_batch(rtw, specs)
+    g = np.random.default_rng(8)
+    dirs = np.concatenate([np.stack([np.arccos(g.uniform(-1, 1, 1494)), g.uniform(-np.pi, np.pi, 1494)], 1),
+                           [[0.0, 0.0], [np.pi, 1.0], [1.0, -np.pi], [1.0, np.pi], [2.0, 0.5], [2.0, 0.5]]])
+    n = len(dirs)
+    out = torch.zeros((5, n, 5, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros((5, n), dtype=torch.uint8, device="cuda")
+    bp = rtw.batch_params(rays, p_max=4, chunk_ray_orders=80_000)
+    rtw.rtw_far_field_batch(obj, bp, rtw.dirs_list(torch.tensor(dirs).cuda()), out, mask,
+                            flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    got, gm = out.cpu().numpy(), mask.cpu().numpy()
+    for i, s in enumerate(specs):
+        o = oracle_mod.Object(s["a"], s["b"], s["c"], quat=s["quat"], m=s["m"], wavelength=s["wavelength"])
+        ref, rm, _, _ = o.field_dirs(4, dirs, n_target=int(rays[i]))
+        compare(got[i], oracle_mod.complex_field(ref), gm[i], rm)
+
+
 def test_batch_argument_errors(rtw):
     from paper_2403_13856_gb300 import workloads as W
 

@@ -240,6 +240,68 @@ def test_field_grid_newton_removes_interpolation_error(rtw, oracle_mod):
     assert q_newton < 1e-9 and q_dense > 1e-5
 
 
+def direction_list(n, seed):
+    """n directions uniform on the sphere plus the poles, the phi seam and a duplicate."""
+    g = np.random.default_rng(seed)
+    z = g.uniform(-1, 1, n)
+    th = np.arccos(z)
+    ph = g.uniform(-np.pi, np.pi, n)
+    extra = np.array([[0.0, 0.0], [np.pi, 1.0], [1.0, -np.pi], [1.0, np.pi], [2.0, 0.5], [2.0, 0.5]])
+    return np.concatenate([np.stack([th, ph], 1), extra])
+
+
+@pytest.mark.parametrize("mode", ["dense", "newton"])
+def test_field_direction_list_vs_oracle(rtw, oracle_mod, mode):
+    """Arbitrary directions of interest: 3000 directions on the sphere (poles, seam, duplicate)
+    for the tilted ellipsoid at about 3e4 rays, orders 0..5, per order."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    jones = (1.0, 0.0)
+    dirs = direction_list(3000, 5)
+    obj = gpu_object(rtw, W.ELLIPSOID, jones)
+    tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=5, n_rays=30_000)
+    rays = rtw.rtw_trace(obj, tp)
+    d = rtw.dirs_list(torch.tensor(dirs).cuda())
+    out = torch.zeros((len(dirs), 6, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(len(dirs), dtype=torch.uint8, device="cuda")
+    m = rtw.RTW_NEWTON if mode == "newton" else rtw.RTW_DENSE
+    rtw.rtw_newton_failures()
+    rtw.rtw_field(rays, d, out, mask, mode=m, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    gfail = rtw.rtw_newton_failures()
+    o = oracle_object(oracle_mod, W.ELLIPSOID, jones)
+    ref, rm, hits, nfail = o.field_dirs(5, dirs, n_target=30_000,
+                                        flags=oracle_mod.FIELD_EXACT if mode == "newton" else 0)
+    assert hits > 1000 and gfail == nfail
+    compare_fields(out.cpu().numpy(), oracle_mod.complex_field(ref), mask.cpu().numpy(), rm)
+
+
+def test_field_direction_list_equals_grid(rtw):
+    """The grid's own directions given as a shuffled list (and a single direction) reproduce the
+    grid field."""
+    spec = dict(a=6.0, b=5.0, c=4.0, quat=(0.9659258262890683, 0.2588190451025207, 0.0, 0.0), m=1.333,
+                wavelength=0.6328)
+    nt, nph = 24, 48
+    got, gm, obj, rays = grid_field(rtw, spec, (0.0, 1.0), 2, nt, nph, n_rays=20_000)
+    th = (np.arange(nt) + 0.5) * np.pi / nt
+    ph = -np.pi + (np.arange(nph) + 0.5) * 2 * np.pi / nph
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    dirs = np.stack([T.ravel(), P.ravel()], 1)
+    perm = np.random.default_rng(4).permutation(len(dirs))
+    out = torch.zeros((len(dirs), 3, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(len(dirs), dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_list(torch.tensor(dirs[perm]).cuda()), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    scale = np.abs(got).max()
+    assert np.abs(out.cpu().numpy() - got[perm]).max() <= 1e-12 * scale
+    assert np.array_equal(mask.cpu().numpy(), gm[perm])
+    k = int(np.argmax(np.abs(got).sum(axis=(1, 2))))
+    one = torch.zeros((1, 3, 2), dtype=torch.complex128, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_list(torch.tensor(dirs[k:k + 1]).cuda()), one, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    assert np.abs(one.cpu().numpy()[0] - got[k]).max() <= 1e-12 * scale
+
+
 def test_field_grid_small_sphere_edge_cases(rtw, oracle_mod):
     """A sphere on a coarse grid (many directions per triangle, poles of the direction grid inside
     triangles) and a ragged direction grid."""

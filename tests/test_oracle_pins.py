@@ -512,3 +512,22 @@ def test_grid_matches_fan_in_symmetry_plane(oracle_mod):
     ok = (mask.reshape(nt, nph)[:, j] == 0) & (m1 == 0) & (th > 0.2) & (th < 1.2)
     assert ok.sum() > 20
     assert np.allclose(F[ok, j, :], F1[ok], rtol=1e-7, atol=1e-7 * np.abs(F1[ok]).max())
+
+
+def test_direction_list_matches_grid(oracle_mod):
+    """The field on a list of directions equals the grid field on the same directions (the grid's
+    own directions in shuffled order), including the masks."""
+    o = oracle_mod.Object(6.0, 5.0, 4.0, quat=(0.9659258262890683, 0.2588190451025207, 0.0, 0.0), m=1.333,
+                          wavelength=0.6328)
+    nt, nph = 24, 48
+    ref, rm, hits, _ = o.field_grid(2, nt, nph, n_target=20_000)
+    th = (np.arange(nt) + 0.5) * np.pi / nt
+    ph = -np.pi + (np.arange(nph) + 0.5) * 2 * np.pi / nph
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    dirs = np.stack([T.ravel(), P.ravel()], 1)
+    perm = np.random.default_rng(3).permutation(dirs.shape[0])
+    out, m, h2, _ = o.field_dirs(2, dirs[perm], n_target=20_000)
+    assert h2 == hits
+    assert np.array_equal(m, rm[perm])
+    # the same contributions, added in another thread order
+    assert np.abs(out - ref[perm]).max() <= 1e-13 * np.abs(ref).max()
