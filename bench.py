@@ -113,6 +113,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(dist, x: float) -> float:
+    """The largest x over the ranks of the process group (the slowest rank's time); the tensor
+    lives where the backend wants it (CUDA for NCCL, host memory for gloo)."""
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank: float, steps: int, world: int, slowest_s: float) -> float:
+    """Weak scaling: every rank runs its own copy of the workload, so the job processed world x
+    units per step; the rate divides by the slowest rank's time."""
+    return world * units_per_rank * steps / slowest_s
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -309,11 +326,9 @@ def bench_ellipsoid(args, rank, world, local, dist):
     t_field = [e[1].elapsed_time(e[2]) / 1e3 for e in evs]
     total = sum(t_step)
     if dist:
-        tt = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = tt.item()
-    value = world * units * args.steps / total
-    dps = world * ndir * args.steps / total
+        total = max_over_ranks(dist, total)
+    value = whole_job_rate(units, args.steps, world, total)
+    dps = whole_job_rate(ndir, args.steps, world, total)
 
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
@@ -464,11 +479,9 @@ def bench_batch(args, rank, world, local, dist):
     t_step = [e[0].elapsed_time(e[1]) / 1e3 for e in evs]
     total = sum(t_step)
     if dist:
-        tt = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = tt.item()
-    value = world * units * args.steps / total
-    dps = world * n * ndir * args.steps / total
+        total = max_over_ranks(dist, total)
+    value = whole_job_rate(units, args.steps, world, total)
+    dps = whole_job_rate(n * ndir, args.steps, world, total)
 
     # trace and field split: one eager run with the library's own events (same options)
     bpt = rtw.batch_params(rays, p_max=p_max, precision=precision, timing=1, **opts)
