@@ -33,6 +33,10 @@ UNIT = "rays*interfaces/s"
 # counted from its source: adds, multiplies, divisions and square roots as one, FMA as two
 FLOPS_PER_INTERACTION = 430
 FP64_NOMINAL_GFLOPS = 1250.0
+# DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload: ncu measured
+# 1.90 MB + 572.9 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
+# 4x at 4e6
+TRACE_TRAFFIC_BYTES = 4 * (1_901_056 + 572_906_496)
 
 
 def parse():
@@ -375,7 +379,9 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "roofline": {"kernel": "trace_kernel_fp64", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "GFLOP/s FP64", "frac": achieved / peak,
                      "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (nominal 1250)",
-                     "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": None},
+                     "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": TRACE_TRAFFIC_BYTES,
+                     "traffic_note": "DRAM bytes per launch from ncu at 1e6 rays, scaled by hits (4x); "
+                                     "profiles/trace_kernel_fp64_ellipsoid_1e6rays.md"},
         "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
