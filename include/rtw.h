@@ -316,8 +316,8 @@ typedef struct {
 /* The far field of every object of obj on the (theta, phi) grid of dirs from learned proposals:
  * for each direction s and order p, network p (features of s and the object) proposes 4 entry
  * points (moved onto radius 0.999 of the unit disk when beyond it); each head with softmax
- * weight >= p_min seeds Newton steps on the exact FP64 trace
- * (as RTW_NEWTON, at most max_steps steps, no distance bound); a root within 1e-6 max(a, b, c) of
+ * weight >= p_min seeds Newton steps on the exact FP64 trace (as RTW_NEWTON, at most max_steps
+ * steps of at most 3 halvings each, no distance bound); a root within 1e-6 max(a, b, c) of
  * an earlier root of the same direction and order is the same ray and is dropped; every other
  * root adds its exact F e^{i Psi}, except a near-caustic root, which marks the direction
  * (RTW_MASK_CAUSTIC) instead.  A branch that no head finds is missing from the sum: roots_out

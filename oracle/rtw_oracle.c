@@ -546,18 +546,18 @@ static int newton_eval(const or_object* o, int p, const double target[3], const 
 }
 
 /* Newton steps xy <- xy + J^{-1} [v1.d, v2.d] with d = target - s and J = ds/d(x, y) of the
- * record, each step shortened by halving (at most 12 times) until the trace of the new point
+ * record, each step shortened by halving (at most max_halvings times; or_newton: 12) until the trace of the new point
  * leaves in order p with a smaller residual.  Converged when |d| < tol at one of the first
  * max_checks evaluations (or_newton: 1e-11 within 30) and the root lies within rmax of the seed
  * (rmax <= 0: anywhere), so that the ray found is the one the seed stands for and not a
  * neighbouring branch of the same order.  xy ends at the last point reached. */
 int or_newton(const or_object* o, int p, const double target[3], double* xy, double rmax, double* rec)
 {
-    return or_newton_ex(o, p, target, xy, rmax, 30, 1e-11, rec);
+    return or_newton_ex(o, p, target, xy, rmax, 30, 1e-11, 12, rec);
 }
 
 int or_newton_ex(const or_object* o, int p, const double target[3], double* xy, double rmax, int max_checks,
-                 double tol, double* rec)
+                 double tol, int max_halvings, double* rec)
 {
     const size_t nb = (size_t)(p + 1) * OR_NFIELD;
     double* buf = (double*)malloc(sizeof(double) * 2 * nb);
@@ -584,7 +584,7 @@ int or_newton_ex(const or_object* o, int p, const double target[3], double* xy, 
             const double dx = Ji[0][0] * rhs0 + Ji[0][1] * rhs1, dy = Ji[1][0] * rhs0 + Ji[1][1] * rhs1;
             double lam = 1.0;
             int accepted = 0;
-            for (int h = 0; h <= 12; ++h, lam *= 0.5) {
+            for (int h = 0; h <= max_halvings; ++h, lam *= 0.5) {
                 double cand[2] = {xy[0] + lam * dx, xy[1] + lam * dy}, rc;
                 if (newton_eval(o, p, target, cand, trial, &rc) && rc < res) {
                     xy[0] = cand[0];
@@ -1256,7 +1256,7 @@ int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int 
                     uv[1] *= 0.999 / ru;
                 }
                 om_uv_to_xy(o, uv, &xy[0], &xy[1]);
-                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, rec) < 0) continue;
+                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, 3, rec) < 0) continue;
                 int dup = 0;
                 for (int q = 0; q < nfound; ++q)
                     if (hypot(xy[0] - found[q][0], xy[1] - found[q][1]) <= dedup) dup = 1;

@@ -121,9 +121,10 @@ int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pma
  * within rmax of the seed (rmax <= 0: no bound).  Returns iterations used, or -1 if it did not
  * converge. */
 int or_newton(const or_object* o, int p, const double target[3], double* xy, double rmax, double* rec);
-/* The same with at most max_checks evaluations of the residual and convergence at |s - t| < tol. */
+/* The same with at most max_checks evaluations of the residual, convergence at |s - t| < tol and
+ * at most max_halvings halvings of a step. */
 int or_newton_ex(const or_object* o, int p, const double target[3], double* xy, double rmax, int max_checks,
-                 double tol, double* rec);
+                 double tol, int max_halvings, double* rec);
 /* acc (4) += weight * (F e^{i psi}) . (e_theta, e_phi) as (re, im, re, im) */
 void or_project_add(const double F[6], double psi, const double eth[3], const double eph[3], double weight,
                     double* acc);
@@ -132,8 +133,8 @@ void or_project_add(const double F[6], double psi, const double eth[3], const do
  * p the network of order p (mlp_oracle.h; theta: (pmax+1) x OM_NPARAM doubles, evaluated with
  * bfloat16 rounding as the tensor cores do) proposes 4 entry points (moved onto radius 0.999 of
  * the unit disk when beyond it); each head whose softmax weight is at least p_min seeds
- * or_newton_ex (at most max_steps steps, no distance bound, |s - t| < tol, or for tol <= 0
- * min(1e-6, 1e-4 / (k0 max(a, b, c)))); a root within 1e-6 max(a, b, c) of an earlier root of
+ * or_newton_ex (at most max_steps steps, at most 3 halvings of a step, no distance bound,
+ * |s - t| < tol, or for tol <= 0 min(1e-6, 1e-4 / (k0 max(a, b, c)))); a root within 1e-6 max(a, b, c) of an earlier root of
  * the same direction and order is the same ray and is dropped; every other root adds
  * F e^{i Psi}, except a near-caustic one, which marks the direction instead.
  * out: ndir x (pmax+1) x 4; mask: ndir (axial as or_field_grid); roots (may be NULL):

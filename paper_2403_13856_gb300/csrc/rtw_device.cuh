@@ -62,14 +62,14 @@ __device__ __forceinline__ bool newton_eval(const ObjDev& o, int p, const double
 // Newton steps on the exact double-precision trace in the impact point (x, y) until the exit
 // direction of order p equals the unit target t.  The Jacobian ds/d(x, y) in the exit basis
 // (e_perp, e_perp x s) is the exit wavefront-curvature matrix times the transfer matrix the trace
-// carries (J = Q' T).  A step is halved (at most 12 times) until the new point leaves in order p
+// carries (J = Q' T).  A step is halved (at most max_halvings times) until the new point leaves in order p
 // with a smaller residual.  Converged when |s - t| < tol at one of the first max_checks
 // evaluations (so at most max_checks - 1 steps) and the root lies within rmax of the seed
 // (rmax <= 0: anywhere), so that the ray found is the branch the seed stands for; the root
 // impact point goes to root (when given).
 __device__ __forceinline__ bool newton_point(const ObjDev& o, int p, const double t[3], double x, double y,
                                              double rmax, FarRecord& out, int max_checks = 30, double tol = 1e-11,
-                                             double* root = nullptr)
+                                             double* root = nullptr, int max_halvings = 12)
 {
     const double x0 = x, y0 = y;
     CaptureSink cs;
@@ -100,7 +100,7 @@ __device__ __forceinline__ bool newton_point(const ObjDev& o, int p, const doubl
         const double dx = (J11 * r0 - J01 * r1) / det, dy = (J00 * r1 - J10 * r0) / det;
         double lam = 1.0;
         bool accepted = false;
-        for (int h = 0; h <= 12; ++h, lam *= 0.5) {
+        for (int h = 0; h <= max_halvings; ++h, lam *= 0.5) {
             CaptureSink cc;
             FarRecord rc;
             double resc;

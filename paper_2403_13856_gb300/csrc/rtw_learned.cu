@@ -19,6 +19,9 @@ namespace rtw {
 namespace {
 
 constexpr unsigned int kMaskCausticL = 1u;  // the dense path's RTW_MASK_CAUSTIC bit
+// a proposal is a seed that should already be close: a step is halved at most 3 times before the
+// head is given up (a far seed would otherwise cost up to 13 traces per step)
+constexpr int kLearnedHalvings = 3;
 
 // features of row (object o, direction dk): s (3) then the object's 13, in bfloat16
 __global__ void learned_features_kernel(const ObjFeat* __restrict__ feat, const double* __restrict__ tab, int nt,
@@ -89,7 +92,8 @@ __global__ void __launch_bounds__(128) learned_newton_kernel(const ObjDev* __res
         const double d1 = u1 / f.l11, d0 = (u0 - f.l10 * d1) / f.l00;
         FarRecord fr;
         double root[2];
-        if (!newton_point(o, p, t, o.c[0] + d0, o.c[1] + d1, 0.0, fr, max_steps + 1, tl, root)) continue;
+        if (!newton_point(o, p, t, o.c[0] + d0, o.c[1] + d1, 0.0, fr, max_steps + 1, tl, root, kLearnedHalvings))
+            continue;
         bool dup = false;
         for (int q = 0; q < nfound; ++q)
             if (hypot(root[0] - found[q][0], root[1] - found[q][1]) <= dedup) dup = true;
