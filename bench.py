@@ -663,7 +663,27 @@ def bench_learned(args, rank, world, local, dist):
         "train_s": t_train,
         "clocks": clk.summary(),
     }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_learned(specs[0], p_max, nt, nph)
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_learned(spec, p_max, nt, nph):
+    """The oracle's learned-field pipeline on one evaluation drop (every direction and order),
+    OpenMP over the host's cores.  Its networks are fixed outputs (all heads at the disk centre):
+    the trained weights are outputs of the GPU and stay off the oracle."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    th = np.zeros((p_max + 1, oracle.MLP_NPARAM))
+    o = oracle.Object(spec["a"], spec["b"], spec["c"], quat=spec["quat"], m=spec["m"], wavelength=spec["wavelength"])
+    t0 = time.perf_counter()
+    o.field_learned(th, p_max, nt, nph)
+    dt = time.perf_counter() - t0
+    return {"value": nt * nph / dt, "unit": "directions/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"1 drop, {nt}x{nph} directions, orders 0..{p_max}, seeds at the disk centre, {dt:.1f} s"}
 
 
 if __name__ == "__main__":
