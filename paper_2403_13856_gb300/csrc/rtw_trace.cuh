@@ -127,14 +127,22 @@ __device__ __forceinline__ void symvT(const T* W, T x, T y, T z, T& ox, T& oy, T
 // In single precision the root is then polished by one Newton step evaluated in double precision,
 // so intersection points and optical paths keep double-precision accuracy (the quadric's residual
 // after the step is of the order of the square of the single-precision error).
+// wp, when given, is W (r - c) already formed in the working precision at this r (the normal's
+// gradient), which the quadratic reuses.
 template <typename T>
 __device__ __forceinline__ double chord_to_surface(const ObjDev& o, const T* Wt, const double r[3], const T k[3],
-                                                   T sign, bool* ok)
+                                                   T sign, bool* ok, const T* wp = nullptr)
 {
     const T px = (T)(r[0] - o.c[0]), py = (T)(r[1] - o.c[1]), pz = (T)(r[2] - o.c[2]);
     T wkx, wky, wkz, wpx, wpy, wpz;
     symvT(Wt, k[0], k[1], k[2], wkx, wky, wkz);
-    symvT(Wt, px, py, pz, wpx, wpy, wpz);
+    if (wp) {
+        wpx = wp[0];
+        wpy = wp[1];
+        wpz = wp[2];
+    } else {
+        symvT(Wt, px, py, pz, wpx, wpy, wpz);
+    }
     const T Ak = k[0] * wkx + k[1] * wky + k[2] * wkz;
     const T Bk = k[0] * wpx + k[1] * wpy + k[2] * wpz;
     const T Ck = px * wpx + py * wpy + pz * wpz - T(1);
@@ -287,8 +295,10 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         const T inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
         // reflected wave: k_l = tau - k_in n, signed cosine -ci; Eq. (WavefrontEqVec) in the
         // diagonal bases with n.(k_l - k_i) = -2 k_in
-        T lk0, lk1, lk2, lq11, lq12, lq22, le1r, le1i, le2r, le2i, lt21 = T(0), lt22 = T(0);
-        {
+        T lk0 = T(0), lk1 = T(0), lk2 = T(0), lq11 = T(0), lq12 = T(0), lq22 = T(0);
+        T le1r = T(0), le1i = T(0), le2r = T(0), le2i = T(0), lt21 = T(0), lt22 = T(0);
+        // the wave reflected inside at the last interaction is never used
+        if (q == 1 || q <= pmax) {
             lk0 = (tx - kin * nx) * inv_ki;
             lk1 = (ty - kin * ny) * inv_ki;
             lk2 = (tz - kin * nz) * inv_ki;
@@ -381,7 +391,8 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         // chord to the next surface point along the inward direction
         bool ok;
         const T kk[3] = {k0v, k1v, k2v};
-        const double dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok);
+        const T wg[3] = {gx, gy, gz};
+        const double dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok, wg);
         if (!(dd > 0.0)) return;
         const T d = (T)dd;
         // free propagation: Q(d) = Q (I + d Q)^{-1} = (Q + d det Q I) / det(I + d Q)

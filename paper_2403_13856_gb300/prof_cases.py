@@ -37,6 +37,7 @@ def main():
     ap.add_argument("--objects", type=int, default=64)
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--mixed", action="store_true", help="ellipsoid / batch: mixed-precision trace")
     a = ap.parse_args()
     import torch
 
@@ -58,7 +59,7 @@ def main():
         obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
         cfg = W.BATCH
         out = torch.empty((a.objects, cfg["n_theta"] * cfg["n_phi"], 1, 2), dtype=torch.complex128, device="cuda")
-        bp = rtw.batch_params(rays, p_max=cfg["p_max"])
+        bp = rtw.batch_params(rays, p_max=cfg["p_max"], precision=rtw.RTW_MIXED if a.mixed else rtw.RTW_FP64)
         b = rtw.Batch()
         ms = _timed(torch, lambda: rtw.rtw_far_field_batch(obj, bp, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]), out,
                                                            batch=b), a.reps)
@@ -77,7 +78,8 @@ def main():
     else:
         spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
         obj = rtw.Object([rtw.ObjectSpec(**spec)])
-        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=a.rays)
+        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=a.rays,
+                              precision=rtw.RTW_MIXED if a.mixed else rtw.RTW_FP64)
         rays = rtw.rtw_trace(obj, tp)
         out = torch.empty((cfg["n_theta"] * cfg["n_phi"], 1, 2), dtype=torch.complex128, device="cuda")
 
@@ -86,7 +88,8 @@ def main():
             rtw.rtw_field(rays, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]), out)
 
         ms = _timed(torch, step, a.reps)
-        print(f"ellipsoid rays={a.rays}: {ms:.3f} ms")
+        mt = _timed(torch, lambda: rtw.rtw_trace(obj, tp, rays), a.reps)
+        print(f"ellipsoid rays={a.rays} {'mixed' if a.mixed else 'fp64'}: trace + field {ms:.3f} ms, trace {mt:.3f} ms")
     rtw.rtw_sync_status()
 
 
