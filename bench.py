@@ -51,7 +51,7 @@ def parse():
                     help="ellipsoid: the single tilted drop (default); batch: 4096 seed-drawn drops; "
                          "learned: learned proposals vs dense tracing on 1024 drops")
     ap.add_argument("--retrain", action="store_true", help="learned workload: train even if a checkpoint exists")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"], help="batch workload only")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "dfloat"], help="batch workload only")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: default launch options")
     args = ap.parse_args()
     if args.workload == "batch" and args.steps == 50:
@@ -334,6 +334,31 @@ def bench_ellipsoid(args, rank, world, local, dist):
     value = whole_job_rate(units, args.steps, world, total)
     dps = whole_job_rate(ndir, args.steps, world, total)
 
+    # the other precisions of the trace on the same step (secondary numbers; the line's value is
+    # FP64): mixed (1e-4 amplitude, 1e-5 rad phase per ray) and double-float (within the FP64
+    # path's 1e-6 bounds)
+    forms = {}
+    for name, prec in (("mixed", rtw.RTW_MIXED), ("double_float", rtw.RTW_DFLOAT)):
+        tpf = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=cfg["n_rays"], precision=prec)
+        rf = rtw.rtw_trace(obj, tpf, stream=stream)
+        for _ in range(3):
+            rtw.rtw_trace(obj, tpf, rf, stream=stream)
+            rtw.rtw_field(rf, dirs, out, mask)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+        for e in ev:
+            flush.zero_()
+            e[0].record(stream)
+            rtw.rtw_trace(obj, tpf, rf, stream=stream)
+            e[1].record(stream)
+            rtw.rtw_field(rf, dirs, out, mask)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
+        ts = statistics.median([e[0].elapsed_time(e[2]) for e in ev])
+        forms[name] = {"value": units / (ts / 1e3), "ms_per_step": ts, "ms_trace": tt}
+        del rf
+    rtw.rtw_sync_status(stream)
+
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
     host_mask = torch.empty(ndir, dtype=torch.uint8, pin_memory=True)
@@ -385,6 +410,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        "precision_forms": forms,
     }
     if cpu:
         line["cpu_baseline"] = cpu
@@ -450,7 +476,7 @@ def bench_batch(args, rank, world, local, dist):
 
     cfg = W.BATCH
     p_max, nt, nph = cfg["p_max"], cfg["n_theta"], cfg["n_phi"]
-    precision = rtw.RTW_MIXED if args.precision == "mixed" else rtw.RTW_FP64
+    precision = {"mixed": rtw.RTW_MIXED, "dfloat": rtw.RTW_DFLOAT}.get(args.precision, rtw.RTW_FP64)
     specs, rays = W.batch_objects()
     n = len(specs)
     ndir = nt * nph
@@ -524,7 +550,7 @@ def bench_batch(args, rank, world, local, dist):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == rtw.RTW_FP64 else "f32+f64", "data": "synthetic",
+        "dtype": {rtw.RTW_FP64: "f64", rtw.RTW_MIXED: "f32+f64"}.get(precision, "f32x2+f64"), "data": "synthetic",
         "config": {"workload": "4096 drops: r0 U[20,500] um, b,c = r0 U[0.8,1.2], uniform orientation, "
                                "m U[1.33,1.55], lambda U[0.4,0.8] um, x-pol, rays clamp(1e6 (r0/500)^2, 1e3, 1e6), "
                                f"p=0..4, 128x256 (theta,phi) directions each, {args.precision}",

@@ -58,6 +58,9 @@ extern "C" {
 #define RTW_FP64 0  /* every step in double precision                                          */
 #define RTW_MIXED 1 /* geometry, Fresnel and curvature in single precision; intersection points,
                        optical path and phase in double precision                              */
+#define RTW_DFLOAT 2 /* every step of the trace in double-float (pairs of single-precision
+                        numbers, about 48 significant bits; single-precision exponent range);
+                        intersection points and optical path in double precision           */
 
 #define RTW_DENSE 0  /* interpolation of the dense ray map (the paper's RTW strategy)           */
 #define RTW_NEWTON 1 /* hits refined by Newton steps on the exact FP64 trace (Eq. WavefrontEqVec

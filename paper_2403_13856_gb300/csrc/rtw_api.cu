@@ -461,7 +461,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
 {
     if (!obj || !tp || !inout) return fail(RTW_ERR_ARG, "rtw_trace: null pointer");
     if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace: p_max out of [0, 15]");
-    if (tp->precision != RTW_FP64 && tp->precision != RTW_MIXED)
+    if (tp->precision != RTW_FP64 && tp->precision != RTW_MIXED && tp->precision != RTW_DFLOAT)
         return fail(RTW_ERR_ARG, "rtw_trace: precision %d", tp->precision);
     cudaStream_t s = (cudaStream_t)stream;
     const int np = tp->p_max + 1;

@@ -148,7 +148,7 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: null pointer");
     if (bp->p_max < 0 || bp->p_max >= rtw::kMaxOrders)
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: p_max out of [0, 15]");
-    if (bp->precision != RTW_FP64 && bp->precision != RTW_MIXED)
+    if (bp->precision != RTW_FP64 && bp->precision != RTW_MIXED && bp->precision != RTW_DFLOAT)
         return fail(RTW_ERR_ARG, "rtw_far_field_batch: precision %d", bp->precision);
     if (flags & ~RTW_FIELD_PER_ORDER) return fail(RTW_ERR_ARG, "rtw_far_field_batch: flags 0x%x", flags);
     {

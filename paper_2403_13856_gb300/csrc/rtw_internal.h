@@ -61,7 +61,7 @@ enum AuxField : int {
 struct RaysDev {
     long long R;      // rays per order
     int np;           // number of orders
-    int precision;    // RTW_FP64 / RTW_MIXED
+    int precision;    // RTW_FP64 / RTW_MIXED / RTW_DFLOAT
     // FP64 state
     double2* s01;     // (s_x, s_y)
     double2* s2psi;   // (s_z, Psi)

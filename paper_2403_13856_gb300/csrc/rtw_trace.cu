@@ -176,6 +176,14 @@ __global__ void __launch_bounds__(128) trace_kernel_mixed(const ObjDev* __restri
     trace_kernel_body<float>(objs, nobj, st, pmax, aux);
 }
 
+// every step in double-float (pairs of single-precision numbers); positions and the optical path
+// in double precision
+__global__ void __launch_bounds__(128) trace_kernel_df(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
+                                                       int pmax, int aux)
+{
+    trace_kernel_body<df>(objs, nobj, st, pmax, aux);
+}
+
 __global__ void __launch_bounds__(128) trace_points_kernel(const ObjDev* __restrict__ obj, const double* __restrict__ xy,
                                                            long long n, int pmax, double* s_out, double* F_out,
                                                            double* psi_out, uint32_t* flags_out)
@@ -228,6 +236,8 @@ cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, b
     const long long nb = (st.R + bs - 1) / bs;
     if (st.precision == 1)
         trace_kernel_mixed<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    else if (st.precision == 2)
+        trace_kernel_df<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     else
         trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     return cudaGetLastError();
@@ -274,6 +284,11 @@ cudaError_t launch_trace_items(const ObjDev* d_objs, int nobj, RaysDev st, int p
     if (e != cudaSuccess) return e;
     if (st.precision == 1)
         return launch_items_variant<float>(variant, d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    if (st.precision == 2) {
+        // double-float: the 128-thread instances only (register use as FP64)
+        return variant == 4 ? launch_items<df, 128, 3>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s)
+                            : launch_items<df, 128, 1>(d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
+    }
     return launch_items_variant<double>(variant, d_objs, nobj, st, pmax, next, nitems, ctas_per_sm, s);
 }
 

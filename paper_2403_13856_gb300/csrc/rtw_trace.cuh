@@ -15,6 +15,7 @@
 //     transverse offsets (orientation of the map t -> s).
 #pragma once
 
+#include "rtw_df.cuh"
 #include "rtw_internal.h"
 
 namespace rtw {

@@ -38,6 +38,7 @@ def main():
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--mixed", action="store_true", help="ellipsoid / batch: mixed-precision trace")
+    ap.add_argument("--dfloat", action="store_true", help="ellipsoid / batch: double-float trace")
     a = ap.parse_args()
     import torch
 
@@ -46,6 +47,8 @@ def main():
 
     build.build()
     rtw.lib()
+    prec = rtw.RTW_MIXED if a.mixed else (rtw.RTW_DFLOAT if a.dfloat else rtw.RTW_FP64)
+    pname = {rtw.RTW_MIXED: "mixed", rtw.RTW_DFLOAT: "dfloat"}.get(prec, "fp64")
     if a.case == "mlp_forward":
         mlp = rtw.MLP(1, learned.init_params(1))
         g = np.random.default_rng(1)
@@ -59,11 +62,11 @@ def main():
         obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
         cfg = W.BATCH
         out = torch.empty((a.objects, cfg["n_theta"] * cfg["n_phi"], 1, 2), dtype=torch.complex128, device="cuda")
-        bp = rtw.batch_params(rays, p_max=cfg["p_max"], precision=rtw.RTW_MIXED if a.mixed else rtw.RTW_FP64)
+        bp = rtw.batch_params(rays, p_max=cfg["p_max"], precision=prec)
         b = rtw.Batch()
         ms = _timed(torch, lambda: rtw.rtw_far_field_batch(obj, bp, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]), out,
                                                            batch=b), a.reps)
-        print(f"batch objects={a.objects} rays={int(np.sum(rays))}: {ms:.3f} ms")
+        print(f"batch objects={a.objects} rays={int(np.sum(rays))} {pname}: {ms:.3f} ms")
     elif a.case == "learned":
         cfg = W.LEARNED
         specs, _ = W.batch_objects(a.objects, stream=W.STREAM_EVAL)
@@ -79,7 +82,7 @@ def main():
         spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
         obj = rtw.Object([rtw.ObjectSpec(**spec)])
         tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=a.rays,
-                              precision=rtw.RTW_MIXED if a.mixed else rtw.RTW_FP64)
+                              precision=prec)
         rays = rtw.rtw_trace(obj, tp)
         out = torch.empty((cfg["n_theta"] * cfg["n_phi"], 1, 2), dtype=torch.complex128, device="cuda")
 
@@ -89,7 +92,7 @@ def main():
 
         ms = _timed(torch, step, a.reps)
         mt = _timed(torch, lambda: rtw.rtw_trace(obj, tp, rays), a.reps)
-        print(f"ellipsoid rays={a.rays} {'mixed' if a.mixed else 'fp64'}: trace + field {ms:.3f} ms, trace {mt:.3f} ms")
+        print(f"ellipsoid rays={a.rays} {pname}: trace + field {ms:.3f} ms, trace {mt:.3f} ms")
     rtw.rtw_sync_status()
 
 

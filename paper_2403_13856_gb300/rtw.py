@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "librtw.so")
 
 RTW_OK = 0
 RTW_GRID_FAN, RTW_GRID_SQUARE = 0, 1
-RTW_FP64, RTW_MIXED = 0, 1
+RTW_FP64, RTW_MIXED, RTW_DFLOAT = 0, 1, 2
 RTW_DENSE, RTW_NEWTON = 0, 1
 RTW_DIRS_PLANE, RTW_DIRS_GRID, RTW_DIRS_LIST = 0, 1, 2
 RTW_FIELD_PER_ORDER, RTW_FIELD_PO, RTW_FIELD_NEAR_FOLDS = 1, 2, 4
