@@ -95,9 +95,13 @@ cudaError_t launch_bin_dirs(const double* list, long long n, int nt, int nph, do
 cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi, int ndir, double alpha0,
                              double dalpha, PoWindow* d_win, int* d_nwin, double2* d_scratch, long long ap_cap, int po,
                              int newton, cudaStream_t s);
-// learned proposal (rtw_mlp.cu)
+// learned proposal (rtw_mlp.cu; the inference forward pass is rtw_mlp_tc.cu)
 cudaError_t mlp_prepare_kernels();
-cudaError_t launch_mlp_forward(const MlpWeights& w, const __nv_bfloat16* X, long long rows, float* Y, cudaStream_t s);
+cudaError_t mlp_prepare_tc_kernel();
+// X (rows x 16 bf16) and Y (rows x 16 f32) 16-byte aligned; a bounded wait that gives up sets the
+// timeout bit of *status
+cudaError_t launch_mlp_forward(const MlpWeights& w, const __nv_bfloat16* X, long long rows, float* Y,
+                               unsigned int* status, cudaStream_t s);
 // forward with stored activations, loss, backward and weight gradients of one batch into grad;
 // part holds ceil(rows / 512) x kMlpParams floats
 cudaError_t launch_mlp_grad(const MlpWeights& w, const __nv_bfloat16* X, const float* T, const uint8_t* valid,
@@ -113,7 +117,8 @@ cudaError_t launch_mlp_samples(const ObjDev* objs, const ObjFeat* feat, int nobj
 // network's forward pass and the Newton kernel
 cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double* tab, int nt, int nph, long long nrows,
                            const MlpWeights* nets, int np, __nv_bfloat16* X, float* Y, float p_min, int max_steps,
-                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, cudaStream_t s);
+                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, unsigned int* status,
+                           cudaStream_t s);
 
 cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
                               cudaStream_t s);

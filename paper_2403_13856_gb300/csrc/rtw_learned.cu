@@ -114,14 +114,15 @@ __global__ void __launch_bounds__(128) learned_newton_kernel(const ObjDev* __res
 
 cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double* tab, int nt, int nph, long long nrows,
                            const MlpWeights* nets, int np, __nv_bfloat16* X, float* Y, float p_min, int max_steps,
-                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, cudaStream_t s)
+                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, unsigned int* status,
+                           cudaStream_t s)
 {
     if (nrows <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nrows + 127) / 128);
     learned_features_kernel<<<nb, 128, 0, s>>>(feat, tab, nt, nph, nrows, X);
     cudaError_t e = cudaGetLastError();
     for (int p = 0; p < np && e == cudaSuccess; ++p) {
-        e = launch_mlp_forward(nets[p], X, nrows, Y, s);
+        e = launch_mlp_forward(nets[p], X, nrows, Y, status, s);
         if (e != cudaSuccess) break;
         learned_newton_kernel<<<nb, 128, 0, s>>>(objs, feat, tab, nt, nph, nrows, Y, p, p_min, max_steps, tol, nout,
                                                   out, mask, roots, np);
@@ -152,6 +153,10 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
         lp->chunk_rows < 0)
         return fail(RTW_ERR_ARG, "rtw_field_learned: parameters out of range");
     cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    RTW_CUDA(cudaGetDevice(&dev));
+    unsigned int* status = rtw::host::status_word(dev);
+    if (!status) return fail(RTW_ERR_CUDA, "rtw_field_learned: status word");
     const int max_steps = lp->max_steps > 0 ? lp->max_steps : 5;
     const double tol = lp->tol;  // 0: per object, min(1e-6, 1e-4 / (k0 max(a, b, c)))
     const float p_min = lp->p_min > 0.0f ? lp->p_min : 0.05f;
@@ -206,7 +211,7 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
         if (e != cudaSuccess) break;
         e = rtw::launch_learned(d_obj + c0, d_feat + c0, tab, dirs->n_theta, dirs->n_phi, rows, nets.data(), np, X, Y,
                                 p_min, max_steps, tol, nout, (double*)field_out + 4 * (size_t)nout * ndir * c0, words,
-                                roots_out ? roots_out + (size_t)np * ndir * c0 : nullptr, s);
+                                roots_out ? roots_out + (size_t)np * ndir * c0 : nullptr, status, s);
         if (e == cudaSuccess && mask_out)
             e = rtw::launch_finalize_mask(words, mask_out + (size_t)ndir * c0, d_obj + c0, cn, ndir, 1, dirs->n_theta,
                                           dirs->n_phi, 0.0, 0.0, s);

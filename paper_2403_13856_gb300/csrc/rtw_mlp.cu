@@ -480,11 +480,10 @@ __global__ void mlp_samples_kernel(const ObjDev* __restrict__ objs, const ObjFea
 
 cudaError_t mlp_prepare_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mlp_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    if (e == cudaSuccess) e = mlp_prepare_tc_kernel();
     return e;
 }
 
@@ -495,14 +494,6 @@ static int grid_for(long long rows)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (rows + 63) / 64;
     return (int)std::min<long long>(tiles, (long long)sms * 2);
-}
-
-cudaError_t launch_mlp_forward(const MlpWeights& w, const __nv_bfloat16* X, long long rows, float* Y, cudaStream_t s)
-{
-    if (rows <= 0) return cudaSuccess;
-    MlpActs none{};
-    mlp_fwd_kernel<false><<<grid_for(rows), 128, kFwdSmem, s>>>(w, X, rows, Y, none);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_grad(const MlpWeights& w, const __nv_bfloat16* X, const float* T, const uint8_t* valid,

@@ -260,7 +260,10 @@ int rtw_mlp_forward(const rtw_mlp* m, int order, const void* X, int64_t rows, fl
     int rc = check_order(m, order);
     if (rc != RTW_OK) return rc;
     if (rows < 0 || (rows > 0 && (!X || !Y))) return fail(RTW_ERR_ARG, "rtw_mlp_forward: arguments");
-    RTW_CUDA(rtw::launch_mlp_forward(weights_of(m->nets[(size_t)order]), (const __nv_bfloat16*)X, rows, Y,
+    if (((uintptr_t)X | (uintptr_t)Y) & 15u) return fail(RTW_ERR_ARG, "rtw_mlp_forward: X and Y must be 16-byte aligned");
+    unsigned int* status = rtw::host::status_word(m->device);
+    if (!status) return fail(RTW_ERR_CUDA, "rtw_mlp_forward: status word");
+    RTW_CUDA(rtw::launch_mlp_forward(weights_of(m->nets[(size_t)order]), (const __nv_bfloat16*)X, rows, Y, status,
                                      (cudaStream_t)stream));
     return RTW_OK;
 }

@@ -68,6 +68,45 @@ def test_forward_matches_oracle(rtw, oracle_mod):
         assert err.max() <= 2e-2 * scale and np.median(err) <= 1e-4 * scale
 
 
+def test_forward_many_tiles_matches_oracle(rtw, oracle_mod):
+    """Every CTA runs several 128-row tiles in each of its two warpgroups, with a ragged last tile:
+    sampled rows (the tail included) against the oracle, and every row against a second call on
+    the same rows placed 24 rows later in the tile grid."""
+    th = seeded_params(1, 13)
+    mlp = rtw.MLP(1, th)
+    g = np.random.default_rng(14)
+    rows = 152 * 2 * 128 * 3 + 77
+    x = g.uniform(-1, 1, (rows, 16))
+    xb, xr = bf16_rows(x)
+    X = xb.cuda()
+    Y = torch.zeros((rows, 16), dtype=torch.float32, device="cuda")
+    rtw.rtw_mlp_forward(mlp, 0, X, Y)
+    X2 = torch.zeros((rows + 24, 16), dtype=torch.bfloat16, device="cuda")
+    X2[24:] = X
+    Y2 = torch.zeros((rows + 24, 16), dtype=torch.float32, device="cuda")
+    rtw.rtw_mlp_forward(mlp, 0, X2, Y2)
+    rtw.rtw_sync_status()
+    got = Y.cpu().numpy().astype(np.float64)
+    assert torch.equal(Y, Y2[24:]), "a row's output depends on its place in the tile grid"
+    sample = np.concatenate([g.choice(rows - 200, 1800, replace=False), np.arange(rows - 200, rows)])
+    ref = oracle_mod.mlp_forward(th[0].astype(np.float64), xr[sample], bf16=True)
+    err = np.abs(got[sample] - ref)
+    scale = np.abs(ref).max()
+    print(f"forward {rows} rows: max |dy| / max |y| = {err.max() / scale:.2e}, median {np.median(err) / scale:.2e}")
+    assert err.max() <= 2e-2 * scale and np.median(err) <= 1e-4 * scale
+
+
+def test_forward_rejects_misaligned_rows(rtw):
+    """The forward pass reads rows as 16-byte vectors: an input or output 8 bytes off is refused."""
+    mlp = rtw.MLP(1, seeded_params(1, 15))
+    X = torch.zeros((65, 16), dtype=torch.bfloat16, device="cuda")
+    Y = torch.zeros((65, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(rtw.RTWError):
+        rtw.rtw_mlp_forward(mlp, 0, X.view(-1)[4:4 + 64 * 16].view(64, 16), Y[:64])
+    with pytest.raises(rtw.RTWError):
+        rtw.rtw_mlp_forward(mlp, 0, X[:64], Y.view(-1)[2:2 + 64 * 16].view(64, 16))
+
+
 def test_gradient_matches_oracle(rtw, oracle_mod):
     """Gradient check of the hand-written backward kernels against the oracle's FP64 backprop."""
     th = seeded_params(1, 21, scale=0.7)
