@@ -289,7 +289,9 @@ int rtw_mlp_set(rtw_mlp* m, int order, const float* theta, const float* adam_m, 
  * Asynchronous. */
 int rtw_mlp_samples(const rtw_object* obj, const double* uv, const int32_t* obj_index, int64_t n, int p_max,
                     void* X, float* T, uint8_t* valid, void* stream);
-/* Y (device, rows x 16 float) = network `order` applied to X.  Asynchronous. */
+/* Y (device, rows x 16 float) = network `order` applied to X (device, rows x 16 bf16), on the
+ * tensor cores.  X and Y must start on 16-byte boundaries (RTW_ERR_ARG otherwise).  Asynchronous; a
+ * bounded wait inside the kernel that gives up is reported as RTW_ERR_TIMEOUT by rtw_sync_status. */
 int rtw_mlp_forward(const rtw_mlp* m, int order, const void* X, int64_t rows, float* Y, void* stream);
 /* Gradient of the mean loss over the labelled rows (valid != 0) into the network's gradient
  * buffer: for each row head valid - 1 carries the squared distance to the target uv, and beta
