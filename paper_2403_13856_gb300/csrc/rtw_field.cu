@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
     }
 }
 
-// Phase 2: one warp per listed triangle, rows in turn, the lanes taking the columns.
+// Phase 2: one warp per listed triangle; the lanes take its candidate grid points (row-major over
+// the candidate rows and columns) 32 apart, so that a narrow triangle spanning many rows keeps
+// every lane busy.
 __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBatch b, DirSet d,
                                                              const unsigned long long* big, const unsigned int* nbig,
                                                              unsigned int big_cap, HitArgs h)
@@ -428,11 +430,18 @@ __global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBa
         if (tri_setup(a, c.base, g, d) == 0) continue;
         TriFrame fr;
         tri_frame(a, c.base, g, fr);
-        for (int it = g.it0; it <= g.it1; ++it) {
-            for (int jj = lane; jj < g.jcount; jj += 32) {
-                int jp = g.jp0 + jj;
-                jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
+        // candidate q = (it - it0) jcount + jj; each lane steps q by 32 = step_r rows + step_c columns
+        const int jc = g.jcount, step_r = 32 / jc, step_c = 32 % jc;
+        int it = g.it0 + lane / jc, jj = lane % jc;
+        while (it <= g.it1) {
+            int jp = g.jp0 + jj;
+            jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
+            candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
+            it += step_r;
+            jj += step_c;
+            if (jj >= jc) {
+                jj -= jc;
+                ++it;
             }
         }
     }
