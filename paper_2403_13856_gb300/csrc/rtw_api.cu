@@ -198,9 +198,10 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     dir_grid(dirs, &nt, &nph);
     const bool list = dirs->kind == RTW_DIRS_LIST;
     const size_t nl = list ? (size_t)ndir : 0, nb = list ? (size_t)nt * (size_t)nph + 1 : 0;
-    // list of large triangles: 1/32 of a group's triangles, at least 65536
+    // list of large triangles: room for every triangle of a group (coarse ray grids make most of them
+    // large), up to 2^29 entries; a triangle beyond the list is classified by its own thread
     const unsigned int big_cap =
-        (unsigned int)std::min<long long>(std::max<long long>(65536, 2 * g.max_group_cells / 32), 1ll << 26);
+        (unsigned int)std::min<long long>(std::max<long long>(65536, 2 * g.max_group_cells), 1ll << 29);
     const unsigned int hit_cap = (unsigned int)std::min<long long>(4 * ndir * np * g.group + (1 << 20), 1ll << 29);
     size_t off_mask = 0;
     size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir * (size_t)g.group, 256);
