@@ -120,29 +120,24 @@ __global__ void dir_tables_kernel(int nt, int nph, double* tab)
 // wide image triangles) goes to a list.  Phase 2: one warp per listed triangle, the lanes taking
 // its candidate directions in turn, so that no thread serialises thousands of tests.
 // ---------------------------------------------------------------------------------------------
-constexpr int kInlineCandidates = 64;  // measured best of 32..512 on the ellipsoid workload
+constexpr int kInlineCandidates = 16;  // measured best of 2..64 on the ellipsoid workload (1e6, 4e6 rays)
 constexpr unsigned int kHitClose = 0x80000000u;  // hit entry flag: needs the double-precision test
 
 struct TriGeom {
     long long id[3];  // local ray indices, counter-clockwise in the ray grid
     uint32_t f[3];
     float s[3][3];    // single-precision (hi) exit directions
+    float l[3][3];    //   and their lo parts
     float c[3];       // unit vector at the centre of the image triangle (local origin)
     int it0, it1, jp0, jcount;
 };
 
-// loads the corners and the single-precision candidate cap; returns the number of candidates
-__device__ long long tri_setup(const FieldArgs& a, long long base, TriGeom& g, const DirSet& d)
+// the single-precision candidate cap of a triangle whose corners are loaded; returns the number of
+// candidates
+__device__ __forceinline__ long long tri_setup(TriGeom& g, const DirSet& d)
 {
     const int nt = d.nt, nph = d.nph;
     if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) return 0;
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-        const float4 q = a.st.sf[base + g.id[v]];
-        g.s[v][0] = q.x;
-        g.s[v][1] = q.y;
-        g.s[v][2] = q.z;
-    }
     float cmx = g.s[0][0] + g.s[1][0] + g.s[2][0];
     float cmy = g.s[0][1] + g.s[1][1] + g.s[2][1];
     float cmz = g.s[0][2] + g.s[1][2] + g.s[2][2];
@@ -206,16 +201,15 @@ struct TriFrame {
     bool ok;  // corners agree in focal lines, orientation and carry no caustic flag, image not folded
 };
 
-__device__ void tri_frame(const FieldArgs& a, long long base, const TriGeom& g, TriFrame& fr)
+__device__ __forceinline__ void tri_frame(const TriGeom& g, TriFrame& fr)
 {
     const float* c = g.c;
     float d[3][3], dn[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-        const float4 lo = a.st.sl[base + g.id[v]];
-        d[v][0] = (g.s[v][0] - c[0]) + lo.x;
-        d[v][1] = (g.s[v][1] - c[1]) + lo.y;
-        d[v][2] = (g.s[v][2] - c[2]) + lo.z;
+        d[v][0] = (g.s[v][0] - c[0]) + g.l[v][0];
+        d[v][1] = (g.s[v][1] - c[1]) + g.l[v][1];
+        d[v][2] = (g.s[v][2] - c[2]) + g.l[v][2];
         dn[v] = sqrtf(d[v][0] * d[v][0] + d[v][1] * d[v][1] + d[v][2] * d[v][2]);
     }
 #pragma unroll
@@ -343,6 +337,23 @@ __device__ __forceinline__ void cell_triangle(const FieldArgs& a, long long base
     for (int v = 0; v < 3; ++v) g.f[v] = a.st.flags[base + g.id[v]];
 }
 
+// corners of triangle t with their single-precision directions (hi and lo parts)
+__device__ __forceinline__ void load_triangle(const FieldArgs& a, long long base, long long nx, long long cx,
+                                              long long cy, int t, TriGeom& g)
+{
+    cell_triangle(a, base, nx, cx, cy, t, g);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const float4 hi = a.st.sf[base + g.id[v]], lo = a.st.sl[base + g.id[v]];
+        g.s[v][0] = hi.x;
+        g.s[v][1] = hi.y;
+        g.s[v][2] = hi.z;
+        g.l[v][0] = lo.x;
+        g.l[v][1] = lo.y;
+        g.l[v][2] = lo.z;
+    }
+}
+
 struct DirTabF {
     const float *ct, *st, *cp, *sp;
 };
@@ -386,7 +397,15 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
     for (int t = 0; t < 2; ++t) {
         TriGeom g;
         cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
-        const long long nc = tri_setup(a, c.base, g, d);
+        if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) continue;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float4 hi = a.st.sf[c.base + g.id[v]];
+            g.s[v][0] = hi.x;
+            g.s[v][1] = hi.y;
+            g.s[v][2] = hi.z;
+        }
+        const long long nc = tri_setup(g, d);
         if (nc == 0) continue;
         const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
         if (nc > kInlineCandidates) {
@@ -396,8 +415,15 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
                 continue;
             }
         }
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float4 lo = a.st.sl[c.base + g.id[v]];
+            g.l[v][0] = lo.x;
+            g.l[v][1] = lo.y;
+            g.l[v][2] = lo.z;
+        }
         TriFrame fr;
-        tri_frame(a, c.base, g, fr);
+        tri_frame(g, fr);
         for (int it = g.it0; it <= g.it1; ++it) {
             for (int jj = 0; jj < g.jcount; ++jj) {
                 int jp = g.jp0 + jj;
@@ -408,42 +434,84 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
     }
 }
 
-// Phase 2: one warp per listed triangle; the lanes take its candidate grid points (row-major over
-// the candidate rows and columns) 32 apart, so that a narrow triangle spanning many rows keeps
-// every lane busy.
-__global__ void __launch_bounds__(256) field_grid_big_kernel(FieldArgs a, GridBatch b, DirSet d,
-                                                             const unsigned long long* big, const unsigned int* nbig,
-                                                             unsigned int big_cap, HitArgs h)
+// Phase 2: the listed triangles in batches of 32 per warp.  First every lane sets up one triangle
+// of the batch (cell, corners, candidate cap, edge frame) into shared memory; then the warp takes
+// the batch's triangles in turn, the lanes walking a triangle's candidate grid points (row-major
+// over the candidate rows and columns) 32 apart, so that narrow triangles spanning many rows keep
+// every lane busy and no lane repeats another's set-up.
+struct BigRec {
+    TriFrame fr;
+    float c[3];
+    int it0, it1, jp0, jcount;
+    unsigned long long code;
+    int orel, valid;
+};
+constexpr int kBigWarps = 8;  // warps per block of the large-triangle kernel
+
+__global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArgs a, GridBatch b, DirSet d,
+                                                                      const unsigned long long* big,
+                                                                      const unsigned int* nbig, unsigned int big_cap,
+                                                                      HitArgs h)
 {
+    __shared__ BigRec rec[kBigWarps][32];
     const unsigned int n = min(*nbig, big_cap);
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long warps = (long long)gridDim.x * kBigWarps;
     const int nph = d.nph;
     const DirTabF T = dir_tab_f(d.tab, d.nt, nph);
-    for (long long w = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
-        const unsigned long long code = big[w];
-        const int t = (int)(code & 1ull);
-        const CellRef c = decode_cell(a, b, (long long)(code >> 1));
-        unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
-        TriGeom g;
-        cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
-        if (tri_setup(a, c.base, g, d) == 0) continue;
-        TriFrame fr;
-        tri_frame(a, c.base, g, fr);
-        // candidate q = (it - it0) jcount + jj; each lane steps q by 32 = step_r rows + step_c columns
-        const int jc = g.jcount, step_r = 32 / jc, step_c = 32 % jc;
-        int it = g.it0 + lane / jc, jj = lane % jc;
-        while (it <= g.it1) {
-            int jp = g.jp0 + jj;
-            jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-            candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
-            it += step_r;
-            jj += step_c;
-            if (jj >= jc) {
-                jj -= jc;
-                ++it;
+    // lane l of warp w takes list entries w + warps (32 i + l): consecutive entries (neighbouring,
+    // alike triangles) are spread over all warps
+    const long long w = blockIdx.x * (long long)kBigWarps + wib;
+    for (long long i0 = 0; w + warps * i0 < n; i0 += 32) {
+        BigRec& mine = rec[wib][lane];
+        mine.valid = 0;
+        const long long e = w + warps * (i0 + lane);
+        if (e < n) {
+            const unsigned long long code = big[e];
+            const CellRef c = decode_cell(a, b, (long long)(code >> 1));
+            TriGeom g;
+            load_triangle(a, c.base, c.nx, c.cx, c.cy, (int)(code & 1ull), g);
+            if (tri_setup(g, d) != 0) {
+                tri_frame(g, mine.fr);
+                mine.c[0] = g.c[0];
+                mine.c[1] = g.c[1];
+                mine.c[2] = g.c[2];
+                mine.it0 = g.it0;
+                mine.it1 = g.it1;
+                mine.jp0 = g.jp0;
+                mine.jcount = g.jcount;
+                mine.code = code;
+                mine.orel = c.orel;
+                mine.valid = 1;
             }
         }
+        __syncwarp();
+        for (int k = 0; k < 32; ++k) {
+            const BigRec& r = rec[wib][k];
+            if (!r.valid) continue;
+            const TriFrame fr = r.fr;
+            TriGeom g;
+            g.c[0] = r.c[0];
+            g.c[1] = r.c[1];
+            g.c[2] = r.c[2];
+            const unsigned long long code = r.code;
+            unsigned int* mask = a.mask + (long long)r.orel * b.ndir;
+            // candidate q = (it - it0) jcount + jj; each lane steps q by 32 = step_r rows + step_c columns
+            const int jc = r.jcount, it1 = r.it1, jp0 = r.jp0, step_r = 32 / jc, step_c = 32 % jc;
+            int it = r.it0 + lane / jc, jj = lane % jc;
+            while (it <= it1) {
+                int jp = jp0 + jj;
+                jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
+                candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
+                it += step_r;
+                jj += step_c;
+                if (jj >= jc) {
+                    jj -= jc;
+                    ++it;
+                }
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -1111,7 +1179,7 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirS
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    field_grid_big_kernel<<<(unsigned)(32 * sms), bs, 0, s>>>(a, b, d, big, nbig, big_cap, h);
+    field_grid_big_kernel<<<(unsigned)(32 * sms), 32 * kBigWarps, 0, s>>>(a, b, d, big, nbig, big_cap, h);
     field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h, newton);
     return cudaGetLastError();
 }
