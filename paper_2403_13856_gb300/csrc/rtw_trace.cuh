@@ -129,14 +129,19 @@ __device__ __forceinline__ void symvT(const T* W, T x, T y, T z, T& ox, T& oy, T
 // so intersection points and optical paths keep double-precision accuracy (the quadric's residual
 // after the step is of the order of the square of the single-precision error).
 // wp, when given, is W (r - c) already formed in the working precision at this r (the normal's
-// gradient), which the quadratic reuses.
+// gradient), which the quadratic reuses; wk_out, when given, receives W k.
 template <typename T>
 __device__ __forceinline__ double chord_to_surface(const ObjDev& o, const T* Wt, const double r[3], const T k[3],
-                                                   T sign, bool* ok, const T* wp = nullptr)
+                                                   T sign, bool* ok, const T* wp = nullptr, T* wk_out = nullptr)
 {
     const T px = (T)(r[0] - o.c[0]), py = (T)(r[1] - o.c[1]), pz = (T)(r[2] - o.c[2]);
     T wkx, wky, wkz, wpx, wpy, wpz;
     symvT(Wt, k[0], k[1], k[2], wkx, wky, wkz);
+    if (wk_out) {
+        wk_out[0] = wkx;
+        wk_out[1] = wky;
+        wk_out[2] = wkz;
+    }
     if (wp) {
         wpx = wp[0];
         wpy = wp[1];
@@ -211,12 +216,22 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
     double n_in_d = 1.0;  // the same index in double precision, for the optical path
     // reciprocal wave numbers of the two media, once per ray
     const T k0 = (T)o.k0, mo = (T)o.m;
-    const T ik_host = T(1) / k0, ik_obj = T(1) / (k0 * mo);
+    const T ik_host = T(1) / k0, ik_obj = T(1) / (k0 * mo), inv_mo = T(1) / mo;
+    // in double precision the gradient at the next surface point is carried forward:
+    // W (r + d k - c) = W (r - c) + d W k, with W k from the chord
+    constexpr bool kCarryGrad = sizeof(T) == sizeof(double);
+    T gnext[3] = {T(0), T(0), T(0)};
     for (int q = 1; q <= pmax + 1; ++q) {
         const T n_out = (q == 1) ? mo : T(1);
         // outward normal n = W (r - c) / |W (r - c)|
         T gx, gy, gz;
-        symvT(W, (T)(r[0] - o.c[0]), (T)(r[1] - o.c[1]), (T)(r[2] - o.c[2]), gx, gy, gz);
+        if (kCarryGrad && q > 1) {
+            gx = gnext[0];
+            gy = gnext[1];
+            gz = gnext[2];
+        } else {
+            symvT(W, (T)(r[0] - o.c[0]), (T)(r[1] - o.c[1]), (T)(r[2] - o.c[2]), gx, gy, gz);
+        }
         const T inv_gn = rsqrt(gx * gx + gy * gy + gz * gz);
         const T nx = gx * inv_gn, ny = gy * inv_gn, nz = gz * inv_gn;
         const T ci = k0v * nx + k1v * ny + k2v * nz;  // signed cosine of incidence
@@ -260,7 +275,7 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         const T tx = ki * k0v - kin * nx, ty = ki * k1v - kin * ny, tz = ki * k2v - kin * nz;
         const T tau2 = tx * tx + ty * ty + tz * tz;
         const T ktn2 = kt * kt - tau2;
-        const T mr = n_out / n_in, mr2 = mr * mr;
+        const T mr = (q == 1) ? mo : inv_mo, mr2 = mr * mr;  // n_out / n_in
         // Eq. (Fres)
         const bool tok = ktn2 > T(0);
         T ktn = T(0);
@@ -393,9 +408,15 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         bool ok;
         const T kk[3] = {k0v, k1v, k2v};
         const T wg[3] = {gx, gy, gz};
-        const double dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok, wg);
+        T wk[3];
+        const double dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok, wg, wk);
         if (!(dd > 0.0)) return;
         const T d = (T)dd;
+        if (kCarryGrad) {
+            gnext[0] = gx + d * wk[0];
+            gnext[1] = gy + d * wk[1];
+            gnext[2] = gz + d * wk[2];
+        }
         // free propagation: Q(d) = Q (I + d Q)^{-1} = (Q + d det Q I) / det(I + d Q)
         const T A11 = T(1) + d * q11, A22 = T(1) + d * q22, A12 = d * q12;
         const T detA = A11 * A22 - A12 * A12;
