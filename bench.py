@@ -34,9 +34,9 @@ UNIT = "rays*interfaces/s"
 FLOPS_PER_INTERACTION = 430
 FP64_NOMINAL_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload: ncu measured
-# 1.90 MB + 572.9 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
+# 2.53 MB + 573.7 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
 # 4x at 4e6
-TRACE_TRAFFIC_BYTES = 4 * (1_901_056 + 572_906_496)
+TRACE_TRAFFIC_BYTES = 4 * (2_534_656 + 573_732_352)
 
 
 def parse():
