@@ -316,10 +316,19 @@ __device__ __forceinline__ CellRef decode_cell(const FieldArgs& a, const GridBat
     r.o = a.d_obj + lo;
     const long long ncell = gc.ncx * gc.ncy;
     const long long local = t - gc.first;
-    r.p = (int)(local / ncell);
-    const long long cell = local - (long long)r.p * ncell;
-    r.cx = gc.ix0 + cell % gc.ncx;
-    r.cy = gc.iy0 + cell / gc.ncx;
+    if (local <= 0xffffffffll && ncell <= 0xffffffffll) {
+        // 32-bit division where the indices fit (every grid here): far cheaper than 64-bit
+        const unsigned int l32 = (unsigned int)local, n32 = (unsigned int)ncell, x32 = (unsigned int)gc.ncx;
+        const unsigned int p32 = l32 / n32, c32 = l32 - p32 * n32, y32 = c32 / x32;
+        r.p = (int)p32;
+        r.cx = gc.ix0 + (long long)(c32 - y32 * x32);
+        r.cy = gc.iy0 + (long long)y32;
+    } else {
+        r.p = (int)(local / ncell);
+        const long long cell = local - (long long)r.p * ncell;
+        r.cx = gc.ix0 + cell % gc.ncx;
+        r.cy = gc.iy0 + cell / gc.ncx;
+    }
     r.nx = r.o->nx;
     r.base = (long long)r.p * a.st.R + r.o->ray_offset;
     return r;
