@@ -68,6 +68,10 @@ def lib():
         L.or_field_grid.restype = i64
         L.or_field_dirs.argtypes = [p, i64, d, i, p, i64, i, p, p, i, p]
         L.or_field_dirs.restype = i64
+        L.or_near_record.argtypes = [p, p, d, p]
+        L.or_near_record.restype = i
+        L.or_field_sphere.argtypes = [p, i64, d, i, i, i, d, p, p, i]
+        L.or_field_sphere.restype = i64
         L.or_newton.argtypes = [p, i, p, p, d, p]
         L.or_newton.restype = i
         L.om_gelu.argtypes = [d]
@@ -177,6 +181,24 @@ class Object:
                                int(max_steps), float(tol), _ptr(out), _ptr(mask), _ptr(roots))
         return out, mask, roots
 
+    def near_record(self, rec, R):
+        """One order's record (NFIELD doubles) at the ray's crossing with the sphere |M| = R."""
+        rec = np.ascontiguousarray(rec, dtype=np.float64)
+        out = np.zeros(NFIELD)
+        ok = lib().or_near_record(self.handle, _ptr(rec), float(R), _ptr(out))
+        return out, bool(ok)
+
+    def field_sphere(self, pmax, ntheta, nphi, R, n_target=0, h=0.0, threads=0):
+        """The field on the sphere of radius R at the cell-centred (theta, phi) grid points:
+        out is ndir x (pmax+1) x 6 (E_r, E_theta, E_phi as re, im), dimensionless."""
+        out = np.zeros((ntheta * nphi, pmax + 1, 6))
+        mask = np.zeros(ntheta * nphi, dtype=np.uint8)
+        hits = lib().or_field_sphere(self.handle, int(n_target), float(h), int(pmax), int(ntheta), int(nphi),
+                                     float(R), _ptr(out), _ptr(mask), int(threads))
+        if hits < 0:
+            raise ValueError("or_field_sphere: R must enclose the object")
+        return out, mask, int(hits)
+
     def field_dirs(self, pmax, dirs, n_target=0, h=0.0, flags=0, threads=0):
         """The square-grid field on a list of directions dirs (n x 2: theta, phi)."""
         dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
@@ -198,7 +220,7 @@ class Object:
 
 
 def complex_field(out):
-    """(..., 4) -> complex (..., 2) = (F_theta, F_phi)."""
+    """(..., 2k) -> complex (..., k): (F_theta, F_phi), or (E_r, E_theta, E_phi) on a sphere."""
     return out[..., 0::2] + 1j * out[..., 1::2]
 
 

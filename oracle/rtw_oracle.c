@@ -456,6 +456,54 @@ static void far_field(const or_object* o, const wave_t* w, const double rexit[3]
     rec[OR_CAUSTIC] = rec[OR_DGEO] > or_caustic_cap(o) ? 1.0 : 0.0;
 }
 
+/* Record of the same ray at the point M where it crosses the sphere |M| = R (Eqs. IntVCRM,
+ * DivFactVCRM and PhasePath at a finite point): the last leg of length t from the exit point ends
+ * the product of Gaussian-curvature ratios with kappa_GM / kappa'_G(p+1) = 1 / det(I + t Q'), its
+ * negative eigenvalues are focal lines crossed, and the optical path runs to M.  The record's
+ * direction is the unit vector of M, its amplitude the field at M for a unit incident wave
+ * (dimensionless), its phase k0 (path + t).  The orientation is that of (x, y) -> M on the sphere
+ * (the far-field one times sign det(I + t Q') sign det Q'), the caustic measure
+ * t^2 / |det(I + t Q') det T|, the far-field dA/dOmega in the limit t -> infinity. */
+int or_near_record(const or_object* o, const double* far, double R, double* rec)
+{
+    memcpy(rec, far, sizeof(double) * OR_NFIELD);
+    if (far[OR_VALID] == 0.0) return 0;
+    const double* r = far + OR_REXIT;
+    const double* sv = far + OR_S;
+    double sr = dot3(sv, r), rr = dot3(r, r), disc = sr * sr - rr + R * R;
+    if (!(R * R > rr) || disc < 0.0) {
+        rec[OR_VALID] = 0.0;
+        return 0;
+    }
+    double t = -sr + sqrt(disc);
+    double Q[2][2] = {{far[OR_Q + 0], far[OR_Q + 1]}, {far[OR_Q + 2], far[OR_Q + 3]}};
+    double A[2][2] = {{1.0 + t * Q[0][0], t * Q[0][1]}, {t * Q[1][0], 1.0 + t * Q[1][1]}};
+    double detA = det2(A), detQ = det2(Q);
+    double J[2][2] = {{far[OR_J + 0], far[OR_J + 1]}, {far[OR_J + 2], far[OR_J + 3]}};
+    double detJ = det2(J);
+    if (!(fabs(detA) > 0.0) || !(fabs(detQ) > 0.0) || !(fabs(detJ) > 0.0)) {
+        rec[OR_VALID] = 0.0;
+        return 0;
+    }
+    int nf = (int)far[OR_NFLEGS] + neg_eigs(A);
+    double D = far[OR_DLEGS] / fabs(detA);
+    cplx E0 = far[OR_E + 0] + I * far[OR_E + 1], E1 = far[OR_E + 2] + I * far[OR_E + 3];
+    cplx ph = minus_i_pow(nf) * sqrt(D);
+    for (int c = 0; c < 3; ++c) {
+        cplx Fc = ph * (E0 * far[OR_V1 + c] + E1 * far[OR_V2 + c]);
+        rec[OR_F + 2 * c] = creal(Fc);
+        rec[OR_F + 2 * c + 1] = cimag(Fc);
+        rec[OR_S + c] = (r[c] + t * sv[c]) / R;
+    }
+    rec[OR_PSI] = o->k0 * (far[OR_PATH] + t);
+    rec[OR_NF] = (double)nf;
+    rec[OR_ORIENT] = far[OR_ORIENT] * (detA > 0.0 ? 1.0 : -1.0) * (detQ > 0.0 ? 1.0 : -1.0);
+    rec[OR_D] = D;
+    rec[OR_DGEO] = t * t * fabs(detQ) / (fabs(detA) * fabs(detJ));
+    rec[OR_CAUSTIC] = rec[OR_DGEO] > or_caustic_cap(o) ? 1.0 : 0.0;
+    return 1;
+}
+
 int or_trace_ray(const or_object* o, double x, double y, int pmax, double* out, double* p_inside)
 {
     memset(out, 0, sizeof(double) * (size_t)(pmax + 1) * OR_NFIELD);
@@ -655,6 +703,27 @@ void or_project_add(const double F[6], double psi, const double eth[3], const do
     acc[1] += weight * cimag(ft);
     acc[2] += weight * creal(fp);
     acc[3] += weight * cimag(fp);
+}
+
+/* as or_project_add, onto (e_r, e_theta, e_phi): the field at a finite point M has a radial part
+ * because the ray through M need not be radial (acc: 6 doubles) */
+static void project_add3(const double F[6], double psi, const double* er, const double* eth, const double* eph,
+                         double* acc)
+{
+    cplx ph = cexp(I * psi);
+    cplx fr = 0.0, ft = 0.0, fp = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        cplx Fc = (F[2 * c] + I * F[2 * c + 1]) * ph;
+        fr += Fc * er[c];
+        ft += Fc * eth[c];
+        fp += Fc * eph[c];
+    }
+    acc[0] += creal(fr);
+    acc[1] += cimag(fr);
+    acc[2] += creal(ft);
+    acc[3] += cimag(ft);
+    acc[4] += creal(fp);
+    acc[5] += cimag(fp);
 }
 
 /* 1 for |x| <= x0, cos^2 ramp to 0 at x1 */
@@ -963,7 +1032,7 @@ static int edge_in(double e, int64_t ia, int64_t ib, int sigma)
  * triangle for both. */
 static int64_t field_square(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
                             const double* list, int64_t n_list, const int64_t* window, int flags, double* out,
-                            uint8_t* mask, int nthreads, int64_t* newton_fail)
+                            uint8_t* mask, int nthreads, int64_t* newton_fail, double near_R)
 {
     const int np = pmax + 1;
     double h, xc, yc;
@@ -986,6 +1055,7 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
 #endif
     {
         double* buf = (double*)malloc(sizeof(double) * (size_t)np * OR_NFIELD);
+        double near[OR_NFIELD];
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -999,6 +1069,10 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
                 else memset(buf, 0, sizeof(double) * (size_t)np * OR_NFIELD);
                 for (int p = 0; p < np; ++p) {
                     const double* r = buf + (size_t)p * OR_NFIELD;
+                    if (near_R > 0.0) {
+                        or_near_record(o, r, near_R, near);
+                        r = near;
+                    }
                     crec* c = cr + ((size_t)(jy * wx + jx) * np + p);
                     memcpy(c->s, r + OR_S, sizeof(c->s));
                     memcpy(c->F, r + OR_F, sizeof(c->F));
@@ -1014,7 +1088,8 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
         free(buf);
     }
     const int64_t ndir = list ? n_list : (int64_t)ntheta * nphi;
-    memset(out, 0, sizeof(double) * (size_t)ndir * np * 4);
+    const int nout = near_R > 0.0 ? 6 : 4; /* (E_r,) E_theta, E_phi: re, im */
+    memset(out, 0, sizeof(double) * (size_t)ndir * np * nout);
     memset(mask, 0, (size_t)ndir);
     const double dth = list ? 1.0 : PI / ntheta, dph = list ? 1.0 : 2.0 * PI / nphi;
     double axial = 2.0 * o->lambda / o->Lmin;
@@ -1164,10 +1239,11 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
                         }
                         const double* eth = x + 3;
                         const double* eph = x + 6;
-                        double acc[4] = {0, 0, 0, 0};
-                        or_project_add(F, psi, eth, eph, 1.0, acc);
-                        double* dst = out + ((size_t)dk * np + p) * 4;
-                        for (int c = 0; c < 4; ++c) {
+                        double acc[6] = {0, 0, 0, 0, 0, 0};
+                        if (nout == 6) project_add3(F, psi, x, eth, eph, acc);
+                        else or_project_add(F, psi, eth, eph, 1.0, acc);
+                        double* dst = out + ((size_t)dk * np + p) * nout;
+                        for (int c = 0; c < nout; ++c) {
 #ifdef _OPENMP
 #pragma omp atomic
 #endif
@@ -1191,14 +1267,22 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                       int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, window, flags, out, mask, nthreads,
-                        newton_fail);
+                        newton_fail, 0.0);
+}
+
+int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi, double R,
+                        double* out, uint8_t* mask, int nthreads)
+{
+    double rc = sqrt(dot3(o->center, o->center));
+    if (!(R > rc + o->Lmax)) return -1;
+    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, R);
 }
 
 int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pmax, const double* dirs,
                       int64_t ndir, int flags, double* out, uint8_t* mask, int nthreads, int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, 0, 0, dirs, ndir, NULL, flags, out, mask, nthreads,
-                        newton_fail);
+                        newton_fail, 0.0);
 }
 
 /* ------------------------------------------------------------------------------------- */

@@ -116,6 +116,20 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
 int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pmax, const double* dirs,
                       int64_t ndir, int flags, double* out, uint8_t* mask, int nthreads, int64_t* newton_fail);
 
+/* Record of a traced ray (far, one order's record) at the point where it crosses the sphere
+ * |M| = R (R beyond the object): the final leg of length t adds kappa_GM / kappa'_G(p+1) =
+ * 1/det(I + t Q') to D_p and its focal lines to N_f, the phase is k0 (path + t), the direction is
+ * M / R and the amplitude is the field at M for a unit incident wave.  Returns 1 if valid. */
+int or_near_record(const or_object* o, const double* far, double R, double* rec);
+
+/* The field on the sphere |M| = R (R beyond the object's bounding sphere) at the points R u of
+ * the cell-centred (theta, phi) grid: the dense-ray interpolation (O2) of the near records.
+ * out: ntheta*nphi x (pmax+1) x 6 (E_r re, im, E_theta re, im, E_phi re, im; dimensionless: the
+ * ray through M need not be radial), mask as or_field_grid.  Returns the number of hits, or -1 if
+ * R does not enclose the object. */
+int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi, double R,
+                        double* out, uint8_t* mask, int nthreads);
+
 /* Newton on the exact trace: finds the ray of order p whose exit direction is target, from the
  * seed impact point xy (2), with steps halved until the residual decreases; the root must lie
  * within rmax of the seed (rmax <= 0: no bound).  Returns iterations used, or -1 if it did not

@@ -531,3 +531,128 @@ def test_direction_list_matches_grid(oracle_mod):
     assert np.array_equal(m, rm[perm])
     # the same contributions, added in another thread order
     assert np.abs(out - ref[perm]).max() <= 1e-13 * np.abs(ref).max()
+
+
+# --------------------------------------------------------------------------------------------
+# Fields at finite points M (Eqs. IntVCRM, DivFactVCRM with kappa_GM, PhasePath to r_M)
+# --------------------------------------------------------------------------------------------
+
+def sphere_crossing(r, s, R):
+    """t > 0 with |r + t s| = R, from the quadratic in t."""
+    sr, rr = float(np.dot(s, r)), float(np.dot(r, r))
+    return -sr + math.sqrt(sr * sr - rr + R * R)
+
+
+@pytest.mark.parametrize("deg", [5.0, 30.0, 60.0, 85.0])
+@pytest.mark.parametrize("R", [20.0, 50.0, 400.0])
+def test_near_field_convex_mirror(oracle_mod, deg, R):
+    """p = 0 on a sphere of radius a, seen at the point M where the reflected ray meets the sphere
+    |M| = R: a convex mirror's reflected wave diverges from the focal lines a cos(i)/2 and
+    a/(2 cos i) behind the surface (Coddington's equations for a plane wave), so
+    |E(M)|^2 = |r_perp|^2 / ((1 + 2t/(a cos i)) (1 + 2t cos(i)/a)); the phase is k (z_1 + t) with
+    z_1 = -a cos i the incidence point, M lies on the mirror-reflected ray, no focal line is met."""
+    a = 10.0
+    o = sphere(oracle_mod, a=a)
+    i = math.radians(deg)
+    rec, _ = rec_at(oracle_mod, o, a * math.sin(i), pmax=0)
+    near, ok = o.near_record(rec[0], R)
+    assert ok
+    r1 = np.array([a * math.sin(i), 0.0, -a * math.cos(i)])
+    n = r1 / a
+    s = np.array([0.0, 0.0, 1.0]) - 2 * n[2] * n  # law of reflection for k = z
+    t = sphere_crossing(r1, s, R)
+    rs, _ = fresnel_closed(i, M_WATER)
+    I_closed = rs * rs / ((1 + 2 * t / (a * math.cos(i))) * (1 + 2 * t * math.cos(i) / a))
+    F = near[oracle_mod.F:oracle_mod.F + 6]
+    assert F[0::2] @ F[0::2] + F[1::2] @ F[1::2] == pytest.approx(I_closed, rel=1e-12)
+    assert near[oracle_mod.PSI] == pytest.approx(o.k0 * (-a * math.cos(i) + t), rel=1e-14)
+    assert np.allclose(near[oracle_mod.S:oracle_mod.S + 3], (r1 + t * s) / R, atol=1e-14)
+    assert near[oracle_mod.NF] == 0 and near[oracle_mod.ORIENT] == rec[0, oracle_mod.ORIENT]
+
+
+def test_near_field_tends_to_far_field(oracle_mod):
+    """Far from the object, R E(R u) e^{-ikR} tends to the far-field amplitude F(s), M/R to s,
+    and the phase of E(M) to k R + Psi plus k (R + s.r - t), the end-point term; checked on every
+    order 0..3 of rays of the tilted ellipsoid at R = 1e8 um.  The amplitude's deviation is
+    bounded by (|tr Q'^-1| + |r_exit|) / R (the wavefront's radii and the exit point against R),
+    the direction's by |r_exit| / R, the phase's by the rounding of k R = 1e9 rad."""
+    o = tilted_ellipsoid(oracle_mod)
+    R = 1e8
+    for b in (-70.0, -20.0, 5.0, 45.0, 90.0):
+        rec, _, hit = o.trace_ray(b, 0.3 * b, 3)
+        assert hit
+        for p in range(4):
+            if rec[p, oracle_mod.VALID] == 0.0:
+                continue
+            near, ok = o.near_record(rec[p], R)
+            assert ok
+            s = rec[p, oracle_mod.S:oracle_mod.S + 3]
+            r = rec[p, oracle_mod.REXIT:oracle_mod.REXIT + 3]
+            Q = rec[p, oracle_mod.Q:oracle_mod.Q + 4].reshape(2, 2)
+            Ff = rec[p, oracle_mod.F:oracle_mod.F + 6]
+            Fn = near[oracle_mod.F:oracle_mod.F + 6] * R
+            bound = (abs(np.trace(np.linalg.inv(Q))) + np.linalg.norm(r)) / R
+            assert np.abs(Fn - Ff).max() <= bound * np.abs(Ff).max()
+            assert np.abs(near[oracle_mod.S:oracle_mod.S + 3] - s).max() <= np.linalg.norm(r) / R
+            sr, rr = float(s @ r), float(r @ r)
+            geo = (sr * sr - rr) / (math.sqrt(sr * sr - rr + R * R) + R)
+            expect = rec[p, oracle_mod.PSI] + o.k0 * R + o.k0 * geo
+            assert near[oracle_mod.PSI] == pytest.approx(expect, abs=1e-6)
+            assert near[oracle_mod.NF] == rec[p, oracle_mod.NF]
+
+
+def mirror_closed(a, m, R, theta):
+    """Convex-mirror reflection (p = 0) seen on the sphere |M| = R at polar angle theta: the
+    incidence angle i whose reflected ray reaches that M (bisection on the law of reflection),
+    the last leg t and |r_perp|, |r_par| (Born & Wolf)."""
+    def geo(i):
+        r1 = np.array([a * math.sin(i), 0.0, -a * math.cos(i)])
+        s = np.array([0.0, 0.0, 1.0]) - 2 * (r1[2] / a) * (r1 / a)
+        t = sphere_crossing(r1, s, R)
+        M = r1 + t * s
+        return math.atan2(M[0], M[2]), t
+    lo, hi = 1e-9, math.pi / 2 - 1e-9
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (geo(lo)[0] - theta) * (geo(mid)[0] - theta) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    i = 0.5 * (lo + hi)
+    t = geo(i)[1]
+    r_ = math.asin(math.sin(i) / m)
+    ci, cr = math.cos(i), math.cos(r_)
+    return i, t, (ci - m * cr) / (ci + m * cr), (m * ci - cr) / (m * ci + cr)
+
+
+def test_near_field_sphere_grid_matches_mirror(oracle_mod):
+    """The dense-ray field on the sphere |M| = 40 um around a reflecting sphere of radius 10 um
+    (p = 0, x-polarised light) against the convex-mirror closed form: the plane of incidence at
+    azimuth phi carries r_par cos(phi) and r_perp sin(phi), so
+    |E|^2 = (r_par^2 cos^2 phi + r_perp^2 sin^2 phi) / ((1 + 2t/(a cos i)) (1 + 2t cos(i)/a)),
+    counted over all three components (the ray through M is not radial).  The error falls like
+    the square of the ray spacing."""
+    a, R = 10.0, 40.0
+    o = sphere(oracle_mod, a=a, jones=(1.0, 0.0))
+    nt, nph = 24, 48
+    th = (np.arange(nt) + 0.5) * math.pi / nt
+    ph = -math.pi + (np.arange(nph) + 0.5) * 2 * math.pi / nph
+    closed = {it: mirror_closed(a, M_WATER, R, th[it]) for it in range(6, nt - 2)}
+    errs = []
+    for n_target in (4_000, 16_000, 64_000):
+        out, mask, hits = o.field_sphere(0, nt, nph, R, n_target=n_target)
+        assert hits > 0
+        E = oracle_mod.complex_field(out)[:, 0]
+        I_grid = (np.abs(E) ** 2).sum(axis=-1)
+        e = 0.0
+        for it, (i, t, rs, rp) in closed.items():
+            for jp in range(nph):
+                k = it * nph + jp
+                if mask[k]:
+                    continue
+                c2 = math.cos(ph[jp]) ** 2
+                Ic = (rp * rp * c2 + rs * rs * (1 - c2)) / ((1 + 2 * t / (a * math.cos(i))) * (1 + 2 * t * math.cos(i) / a))
+                e = max(e, abs(I_grid[k] / Ic - 1))
+        errs.append(e)
+    print("near-field sphere: max relative intensity error per ray density", errs)
+    assert errs[1] < 0.4 * errs[0] and errs[2] < 0.4 * errs[1] and errs[2] < 3e-3
