@@ -359,6 +359,31 @@ def bench_ellipsoid(args, rank, world, local, dist):
         del rf
     rtw.rtw_sync_status(stream)
 
+    # the field at finite points: the same rays recorded where they cross the sphere |M| = 1000 um
+    # (about 8 semi-axes), the same 512 x 1024 grid of points on it, three components per point
+    near_r = 1000.0
+    tpn = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=cfg["n_rays"], observe_radius=near_r)
+    rn = rtw.rtw_trace(obj, tpn, stream=stream)
+    outn = torch.zeros((ndir, 1, 3), dtype=torch.complex128, device="cuda")
+    for _ in range(3):
+        rtw.rtw_trace(obj, tpn, rn, stream=stream)
+        rtw.rtw_field(rn, dirs, outn, mask)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        rtw.rtw_trace(obj, tpn, rn, stream=stream)
+        e[1].record(stream)
+        rtw.rtw_field(rn, dirs, outn, mask)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    rtw.rtw_sync_status(stream)
+    tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
+    ts = statistics.median([e[0].elapsed_time(e[2]) for e in ev])
+    near = {"radius_um": near_r, "value": units / (ts / 1e3), "unit": UNIT, "ms_per_step": ts, "ms_trace": tt,
+            "ms_field": ts - tt, "points_per_s": ndir / (ts / 1e3), "kernel": "trace_kernel_fp64_near"}
+    del rn, outn
+
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
     host_mask = torch.empty(ndir, dtype=torch.uint8, pin_memory=True)
@@ -411,6 +436,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "precision_forms": forms,
+        "near_field": near,
     }
     if cpu:
         line["cpu_baseline"] = cpu

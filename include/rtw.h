@@ -109,7 +109,13 @@ typedef struct {
 
 /* Ray grid and trace options.  n_rays: fan -> exact number of rays; square -> target count inside
  * the projected cross-section (spacing h = sqrt(pi / (sqrt(det S) n_rays)), S the matrix of the
- * projected ellipse), unless spacing > 0 gives h directly.  p_max: orders 0..p_max, p_max <= 15. */
+ * projected ellipse), unless spacing > 0 gives h directly.  p_max: orders 0..p_max, p_max <= 15.
+ * observe_radius: 0 for the far field; R > 0 (square grids and RTW_FP64 only, R beyond |center| +
+ * max semi-axis of every object, else RTW_ERR_ARG / RTW_ERR_UNSUPPORTED) records every ray where it
+ * crosses the sphere |M| = R about the origin instead: the field at a finite point M (Eqs.
+ * IntVCRM, DivFactVCRM with the Gaussian curvature kappa_GM at M, and PhasePath to r_M), whose
+ * last leg of length t contributes 1 / det(I + t Q') to the divergence factor, its focal lines to
+ * N_f and k t to the phase. */
 typedef struct {
     int grid;
     int p_max;
@@ -118,6 +124,7 @@ typedef struct {
     int64_t n_rays;
     double spacing;
     double fan_phi;
+    double observe_radius;
 } rtw_trace_params;
 
 /* Observation directions (the paper's "directions of interest"): kind RTW_DIRS_PLANE (n_theta,
@@ -196,7 +203,10 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
  * trace from the interpolated impact point (all hits, or, on fans with RTW_FIELD_NEAR_FOLDS, those
  * within 2 deg of a fold).
  * field_out (device): [objects][directions][orders or 1][2] complex128 (F_theta, F_phi), zeroed
- * and written.  mask_out (device, optional): [objects][directions] uint8.  Asynchronous. */
+ * and written.  For rays traced with observe_radius R > 0 the directions u name the points M = R u
+ * and field_out is [objects][directions][orders or 1][3] complex128 (E_r, E_theta, E_phi), the field
+ * at M for a unit incident wave (the ray through M need not be radial); mode RTW_DENSE only, no PO.
+ * mask_out (device, optional): [objects][directions] uint8.  Asynchronous. */
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
               uint8_t* mask_out, void* stream);
 

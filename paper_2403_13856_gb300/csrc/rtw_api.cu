@@ -272,7 +272,8 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
     const int np = st.np;
     const long long ndir = d.ndir;
     const int nout = per_order ? np : 1;
-    const size_t out_obj = 4 * (size_t)nout * (size_t)ndir;  // doubles per object
+    const size_t ncomp = st.near_r > 0.0 ? 6 : 4;  // (E_r,) theta, phi components, re and im
+    const size_t out_obj = ncomp * (size_t)nout * (size_t)ndir;  // doubles per object
     const int64_t* win = dirs->cell_window;
     for (int g0 = 0; g0 < nobj; g0 += g.group) {
         const int gn = std::min(g.group, nobj - g0);
@@ -464,6 +465,22 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace: p_max out of [0, 15]");
     if (tp->precision != RTW_FP64 && tp->precision != RTW_MIXED && tp->precision != RTW_DFLOAT)
         return fail(RTW_ERR_ARG, "rtw_trace: precision %d", tp->precision);
+    if (!(tp->observe_radius >= 0.0) || !std::isfinite(tp->observe_radius))
+        return fail(RTW_ERR_ARG, "rtw_trace: observe_radius must be finite and >= 0");
+    if (tp->observe_radius > 0.0) {
+        if (tp->grid != RTW_GRID_SQUARE) return fail(RTW_ERR_ARG, "rtw_trace: observe_radius needs a square grid");
+        if (tp->precision != RTW_FP64)
+            return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: observe_radius is traced in double precision only");
+        if (tp->flags & RTW_TRACE_APERTURE)
+            return fail(RTW_ERR_ARG, "rtw_trace: observe_radius excludes RTW_TRACE_APERTURE");
+        for (int i = 0; i < obj->count; ++i) {
+            const rtw::host::ObjHost& h = obj->h[(size_t)i];
+            const double rc = std::sqrt(h.c[0] * h.c[0] + h.c[1] * h.c[1] + h.c[2] * h.c[2]);
+            if (!(tp->observe_radius > rc + h.lmax))
+                return fail(RTW_ERR_ARG, "rtw_trace: observe_radius %g does not enclose object %d (|c| + a_max = %g)",
+                            tp->observe_radius, i, rc + h.lmax);
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const int np = tp->p_max + 1;
     std::vector<ObjDev> objs((size_t)obj->count);
@@ -539,6 +556,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     r->st.R = R;
     r->st.np = np;
     r->st.precision = tp->precision;
+    r->st.near_r = tp->observe_radius;
     r->st.s01 = (double2*)(b + off[0]);
     r->st.s2psi = (double2*)(b + off[1]);
     r->st.Fx = (double2*)(b + off[2]);
@@ -616,6 +634,8 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     const bool po = (flags & RTW_FIELD_PO) != 0;
     const int newton = mode == RTW_NEWTON ? ((flags & RTW_FIELD_NEAR_FOLDS) ? 2 : 1) : 0;
     if (po && newton) return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO and RTW_NEWTON exclude each other");
+    if (rays->st.near_r > 0.0 && (newton || po))
+        return fail(RTW_ERR_ARG, "rtw_field: rays traced to a finite radius take the dense mode without PO");
     const bool folds = po || newton == 2;
     const int nout = per_order ? rays->np : 1;
     long long ndir = 0;
@@ -650,7 +670,9 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         }
         rtw::host::GridWs w;
         rtw::host::grid_ws(g, rays->np, dirs, (char*)rays->ws, &w);
-        RTW_CUDA(cudaMemsetAsync(field_out, 0, sizeof(double) * 4 * (size_t)nout * (size_t)ndir * (size_t)rays->nobj, s));
+        const size_t ncomp = rays->st.near_r > 0.0 ? 6 : 4;
+        RTW_CUDA(cudaMemsetAsync(field_out, 0,
+                                 sizeof(double) * ncomp * (size_t)nout * (size_t)ndir * (size_t)rays->nobj, s));
         rtw::DirSet d;
         int rc = rtw::host::dirs_prepare(dirs, w, &d, s);
         if (rc != RTW_OK) return rc;

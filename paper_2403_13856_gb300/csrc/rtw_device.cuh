@@ -33,6 +33,36 @@ __device__ __forceinline__ void add_contribution_reduced(const double* F, double
     atomicAdd(dst + 3, pi);
 }
 
+// As add_contribution_reduced onto (e_r, e_theta, e_phi): at a finite point the ray need not be
+// radial, so the field has a radial part (6 doubles at dst)
+__device__ __forceinline__ void add_contribution_reduced3(const double* F, double psi, const double* er,
+                                                         const double* eth, const double* eph, double* dst)
+{
+    constexpr double kInv2Pi = 0.15915494309189533577, k2PiHi = 6.28318530717958623200;
+    const double r = fma(-k2PiHi, rint(psi * kInv2Pi), psi);
+    float sf, cf;
+    sincosf((float)r, &sf, &cf);
+    const double sp = sf, cp = cf;
+    double rr = 0.0, ri = 0.0, tr = 0.0, ti = 0.0, pr = 0.0, pi = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double re = F[2 * c] * cp - F[2 * c + 1] * sp;
+        const double im = F[2 * c] * sp + F[2 * c + 1] * cp;
+        rr += re * er[c];
+        ri += im * er[c];
+        tr += re * eth[c];
+        ti += im * eth[c];
+        pr += re * eph[c];
+        pi += im * eph[c];
+    }
+    atomicAdd(dst + 0, rr);
+    atomicAdd(dst + 1, ri);
+    atomicAdd(dst + 2, tr);
+    atomicAdd(dst + 3, ti);
+    atomicAdd(dst + 4, pr);
+    atomicAdd(dst + 5, pi);
+}
+
 struct CaptureSink {
     int want;
     bool got;

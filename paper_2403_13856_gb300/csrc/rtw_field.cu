@@ -635,8 +635,13 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBa
         }
         const double eth[3] = {ct * cp, ct * sp, -sth};
         const double eph[3] = {-sp, cp, 0.0};
-        double* dst = a.out + (((long long)c.orel * b.ndir + dk) * b.nout + (a.per_order ? p : 0)) * 4;
-        add_contribution_reduced(Fi, ps, eth, eph, dst);
+        if (a.st.near_r > 0.0) {
+            double* dst = a.out + (((long long)c.orel * b.ndir + dk) * b.nout + (a.per_order ? p : 0)) * 6;
+            add_contribution_reduced3(Fi, ps, x, eth, eph, dst);
+        } else {
+            double* dst = a.out + (((long long)c.orel * b.ndir + dk) * b.nout + (a.per_order ? p : 0)) * 4;
+            add_contribution_reduced(Fi, ps, eth, eph, dst);
+        }
     }
 }
 

@@ -62,6 +62,7 @@ struct RaysDev {
     long long R;      // rays per order
     int np;           // number of orders
     int precision;    // RTW_FP64 / RTW_MIXED / RTW_DFLOAT
+    double near_r;    // > 0: records at the points where the rays cross the sphere |M| = near_r
     // FP64 state
     double2* s01;     // (s_x, s_y)
     double2* s2psi;   // (s_z, Psi)

@@ -79,6 +79,7 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     if (tp->grid != RTW_GRID_FAN || dirs->kind != RTW_DIRS_PLANE)
         return set_error(RTW_ERR_ARG, "needs a fan grid and in-plane directions");
     if (tp->precision != RTW_FP64) return set_error(RTW_ERR_UNSUPPORTED, "FP64 only");
+    if (tp->observe_radius != 0.0) return set_error(RTW_ERR_ARG, "far field only (observe_radius 0)");
     if ((flags & ~RTW_FIELD_PER_ORDER) != 0) return set_error(RTW_ERR_UNSUPPORTED, "only RTW_FIELD_PER_ORDER");
     if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return set_error(RTW_ERR_ARG, "p_max out of [0, 15]");
     if (tp->n_rays < 2) return set_error(RTW_ERR_ARG, "fan needs n_rays >= 2");

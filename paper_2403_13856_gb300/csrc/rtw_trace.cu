@@ -8,7 +8,9 @@ namespace rtw {
 
 namespace {
 
-// Stores the far-field record of every emitted order into the SoA ray state (16-byte vectors).
+// Stores the far-field record (kNear: the record at the sphere |M| = st.near_r) of every emitted
+// order into the SoA ray state (16-byte vectors).
+template <bool kNear>
 struct StateSink {
     const ObjDev* o;
     RaysDev st;
@@ -19,7 +21,11 @@ struct StateSink {
     __device__ void emit(int p, const ExitWave& w)
     {
         FarRecord fr;
-        if (!far_record(*o, w, fr)) return;
+        if constexpr (kNear) {
+            if (!near_record(*o, w, st.near_r, fr)) return;
+        } else {
+            if (!far_record(*o, w, fr)) return;
+        }
         const long long i = (long long)p * st.R + j;
         st.s01[i] = make_double2(fr.s[0], fr.s[1]);
         st.s2psi[i] = make_double2(fr.s[2], fr.psi);
@@ -98,24 +104,24 @@ __device__ __forceinline__ int find_object(const ObjDev* objs, int nobj, long lo
 }
 
 // traces global ray j of object o and clears the flags of the orders it does not reach
-template <typename T>
+template <typename T, bool kNear = false>
 __device__ __forceinline__ void trace_one(const ObjDev* o, const RaysDev& st, long long j, int pmax, int aux)
 {
-    StateSink sink{o, st, j, aux != 0, 0u};
+    StateSink<kNear> sink{o, st, j, aux != 0, 0u};
     double x, y;
     if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray<T, false>(*o, x, y, pmax, sink);
     for (int p = 0; p < st.np; ++p)
         if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
 }
 
-template <typename T>
+template <typename T, bool kNear = false>
 __device__ __forceinline__ void trace_kernel_body(const ObjDev* __restrict__ objs, int nobj, RaysDev st, int pmax,
                                                   int aux)
 {
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (j >= st.R) return;
     const ObjDev* o = objs + (nobj > 1 ? find_object(objs, nobj, j) : 0);
-    trace_one<T>(o, st, j, pmax, aux);
+    trace_one<T, kNear>(o, st, j, pmax, aux);
 }
 
 // object owning work item `it` (largest i with item_first <= it)
@@ -166,6 +172,13 @@ __global__ void __launch_bounds__(128) trace_kernel_fp64(const ObjDev* __restric
                                                          int pmax, int aux)
 {
     trace_kernel_body<double>(objs, nobj, st, pmax, aux);
+}
+
+// the same, recording every ray where it crosses the sphere |M| = st.near_r
+__global__ void __launch_bounds__(128) trace_kernel_fp64_near(const ObjDev* __restrict__ objs, int nobj,
+                                                              RaysDev st, int pmax, int aux)
+{
+    trace_kernel_body<double, true>(objs, nobj, st, pmax, aux);
 }
 
 // geometry, Fresnel and curvature in single precision; intersection points (polished by a
@@ -234,7 +247,9 @@ cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, b
     if (st.R == 0) return cudaSuccess;
     const int bs = 128;
     const long long nb = (st.R + bs - 1) / bs;
-    if (st.precision == 1)
+    if (st.near_r > 0.0)
+        trace_kernel_fp64_near<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    else if (st.precision == 1)
         trace_kernel_mixed<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     else if (st.precision == 2)
         trace_kernel_df<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);

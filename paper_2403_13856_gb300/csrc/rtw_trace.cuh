@@ -98,6 +98,56 @@ __device__ __forceinline__ bool far_record(const ObjDev& o, const ExitWave& w, F
     return true;
 }
 
+// Record of an exit wave at the point M where it crosses the sphere |M| = R (R beyond the exit
+// point), following the divergence chain and the optical path to M (Eqs. DivFactVCRM with
+// kappa_GM, PhasePath): the last leg of length t ends the chain with 1 / det(I + t Q') and adds
+// its focal lines; F = E' sqrt(D_legs / |det(I + t Q')|) (-i)^{N_f} is the field at M for a unit
+// incident wave, Psi = k0 (L + t), s = M / R.  Orientation of (x, y) -> M: sign det(I + t Q')
+// sign det T (times the far-field convention's -1); caustic when t^2 D / cosprod exceeds the cap
+// (dA/dOmega in the limit t -> infinity).
+__device__ __forceinline__ bool near_record(const ObjDev& o, const ExitWave& w, double R, FarRecord& fr)
+{
+    const double sr = w.k[0] * w.r[0] + w.k[1] * w.r[1] + w.k[2] * w.r[2];
+    const double rr = w.r[0] * w.r[0] + w.r[1] * w.r[1] + w.r[2] * w.r[2];
+    const double disc = sr * sr - rr + R * R;
+    if (!(R * R > rr) || !(disc >= 0.0)) return false;
+    const double t = sqrt(disc) - sr;
+    const double a11 = 1.0 + t * w.q11, a12 = t * w.q12, a22 = 1.0 + t * w.q22;
+    const double detA = a11 * a22 - a12 * a12;
+    if (!(fabs(detA) > 0.0) || !isfinite(detA)) return false;
+    const int nf = w.nf_legs + neg_eigs_sym(a11, a12, a22);
+    const double amp = rsqrt(fabs(detA) * w.pdet);
+    const double D = amp * amp;
+    double pr = 1.0, pi = 0.0;  // (-i)^nf
+    switch (nf & 3) {
+    case 1: pr = 0.0; pi = -1.0; break;
+    case 2: pr = -1.0; pi = 0.0; break;
+    case 3: pr = 0.0; pi = 1.0; break;
+    default: break;
+    }
+    const double a1r = amp * (w.e1r * pr - w.e1i * pi), a1i = amp * (w.e1r * pi + w.e1i * pr);
+    const double a2r = amp * (w.e2r * pr - w.e2i * pi), a2i = amp * (w.e2r * pi + w.e2i * pr);
+    const double v2x = w.ep[1] * w.k[2] - w.ep[2] * w.k[1];
+    const double v2y = w.ep[2] * w.k[0] - w.ep[0] * w.k[2];
+    const double v2z = w.ep[0] * w.k[1] - w.ep[1] * w.k[0];
+    const double iR = 1.0 / R;
+    fr.s[0] = (w.r[0] + t * w.k[0]) * iR;
+    fr.s[1] = (w.r[1] + t * w.k[1]) * iR;
+    fr.s[2] = (w.r[2] + t * w.k[2]) * iR;
+    fr.F[0] = a1r * w.ep[0] + a2r * v2x;
+    fr.F[1] = a1i * w.ep[0] + a2i * v2x;
+    fr.F[2] = a1r * w.ep[1] + a2r * v2y;
+    fr.F[3] = a1i * w.ep[1] + a2i * v2y;
+    fr.F[4] = a1r * w.ep[2] + a2r * v2z;
+    fr.F[5] = a1i * w.ep[2] + a2i * v2z;
+    fr.psi = o.k0 * (w.path + t);
+    const int orient = (detA > 0.0 ? 1 : -1) * w.sT * -1;
+    uint32_t f = kFlagValid | (orient > 0 ? kFlagOrient : 0u) | (t * t * D > o.cap * w.cosprod ? kFlagCaustic : 0u);
+    f |= (uint32_t)(nf > 255 ? 255 : nf) << 8;
+    fr.flags = f;
+    return true;
+}
+
 // Impact point of grid ray `local` of object o; false if it lies outside the projected section.
 __device__ __forceinline__ bool ray_origin(const ObjDev& o, long long local, double& x, double& y)
 {

@@ -46,7 +46,7 @@ class rtw_incident(ctypes.Structure):
 class rtw_trace_params(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int), ("p_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("flags", ctypes.c_int), ("n_rays", ctypes.c_int64), ("spacing", ctypes.c_double),
-                ("fan_phi", ctypes.c_double)]
+                ("fan_phi", ctypes.c_double), ("observe_radius", ctypes.c_double)]
 
 
 class rtw_dirs(ctypes.Structure):
@@ -180,10 +180,12 @@ class Object:
             self.handle = None
 
 
-def trace_params(grid=RTW_GRID_SQUARE, p_max=5, precision=RTW_FP64, flags=0, n_rays=0, spacing=0.0, fan_phi=0.0):
+def trace_params(grid=RTW_GRID_SQUARE, p_max=5, precision=RTW_FP64, flags=0, n_rays=0, spacing=0.0, fan_phi=0.0,
+                 observe_radius=0.0):
     tp = rtw_trace_params()
     tp.grid, tp.p_max, tp.precision, tp.flags = grid, p_max, precision, flags
     tp.n_rays, tp.spacing, tp.fan_phi = int(n_rays), float(spacing), float(fan_phi)
+    tp.observe_radius = float(observe_radius)
     return tp
 
 
