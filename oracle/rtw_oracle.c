@@ -48,6 +48,9 @@ struct or_object {
     double S[2][2]; /* projected cross-section: (dx,dy) S (dx,dy)^T <= 1 */
     double Sinv[2][2];
     double Lmax, Lmin;
+    double gc[2];   /* centre of the ray grid (plane wave: the object's centre x, y) */
+    int src;        /* 0: plane wave along +z; 1: point source */
+    double src_pos[3], e1[3], e2[3];
 };
 
 /* ------------------------------------------------------------------------------------- */
@@ -192,6 +195,54 @@ int or_make_object(const double* p, or_object* o)
     o->S[0][1] = o->W[0][1] - o->W[0][2] * o->W[1][2] / o->W[2][2];
     o->S[1][0] = o->S[0][1];
     o->S[1][1] = o->W[1][1] - o->W[1][2] * o->W[1][2] / o->W[2][2];
+    o->gc[0] = o->center[0];
+    o->gc[1] = o->center[1];
+    o->src = p[16] != 0.0;
+    if (o->src) {
+        /* point source s: rays s + t v through X = c + x e1 + y e2 meet the surface where
+         * (v.W g)^2 - (v.W v)(g.W g - 1) > 0 (g = c - s), i.e. v^T K v > 0 with
+         * K = W g g^T W - (g^T W g - 1) W; over X this is an ellipse of the plane:
+         * (w - w0)^T S (w - w0) < 1 with w = (x, y) */
+        double g[3], Wg[3];
+        for (int i = 0; i < 3; ++i) {
+            o->src_pos[i] = p[17 + i];
+            g[i] = o->center[i] - o->src_pos[i];
+        }
+        matvec3(o->W, g, Wg);
+        double gWg = dot3(g, Wg);
+        if (!(gWg > 1.0)) return -1; /* the source must lie outside the object */
+        double d = sqrt(dot3(g, g)), a[3] = {g[0] / d, g[1] / d, g[2] / d};
+        double ref[3] = {1.0, 0.0, 0.0};
+        if (fabs(a[0]) > 0.9) {
+            ref[0] = 0.0;
+            ref[1] = 1.0;
+        }
+        double ra = dot3(ref, a);
+        for (int i = 0; i < 3; ++i) o->e1[i] = ref[i] - ra * a[i];
+        double n1 = sqrt(dot3(o->e1, o->e1));
+        for (int i = 0; i < 3; ++i) o->e1[i] /= n1;
+        cross3(a, o->e1, o->e2);
+        double K[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) K[i][j] = Wg[i] * Wg[j] - (gWg - 1.0) * o->W[i][j];
+        const double* E[2] = {o->e1, o->e2};
+        double M2[2][2], b2[2], Kg[3], KE[3];
+        matvec3(K, g, Kg);
+        for (int a2 = 0; a2 < 2; ++a2) {
+            b2[a2] = dot3(E[a2], Kg);
+            matvec3(K, E[a2], KE);
+            for (int b3 = 0; b3 < 2; ++b3) M2[b3][a2] = dot3(E[b3], KE);
+        }
+        double Mi[2][2];
+        if (!inv2(M2, Mi)) return -1;
+        double w0[2] = {-(Mi[0][0] * b2[0] + Mi[0][1] * b2[1]), -(Mi[1][0] * b2[0] + Mi[1][1] * b2[1])};
+        double f0 = dot3(g, Kg) + b2[0] * w0[0] + b2[1] * w0[1];
+        if (!(f0 > 0.0)) return -1;
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) o->S[i][j] = -M2[i][j] / f0;
+        o->gc[0] = w0[0];
+        o->gc[1] = w0[1];
+    }
     if (!inv2(o->S, o->Sinv)) return -1;
     return 0;
 }
@@ -215,8 +266,8 @@ void or_square_grid(const or_object* o, int64_t n_target, double h_in, double* h
     *nx = 2 * kx + 2;
     *ny = 2 * ky + 2;
     /* x_i = cx + (i + 1/2 - nx/2) h */
-    *x0 = o->center[0];
-    *y0 = o->center[1];
+    *x0 = o->gc[0];
+    *y0 = o->gc[1];
 }
 
 static double grid_coord(double c, int64_t i, int64_t n, double h)
@@ -508,28 +559,81 @@ int or_trace_ray(const or_object* o, double x, double y, int pmax, double* out, 
 {
     memset(out, 0, sizeof(double) * (size_t)(pmax + 1) * OR_NFIELD);
     if (p_inside) *p_inside = 0.0;
-    /* incident ray of the plane wave, started below the object */
-    double r0[3] = {x, y, o->zstart};
-    double u[3] = {r0[0] - o->center[0], r0[1] - o->center[1], r0[2] - o->center[2]};
-    double Wu[3];
-    matvec3(o->W, u, Wu);
-    double A = o->W[2][2], B = Wu[2], Cq = dot3(u, Wu) - 1.0;
-    double disc = B * B - A * Cq;
-    if (!(disc > 0.0)) return 0;
-    double t = (-B - sqrt(disc)) / A;
-    double r[3] = {r0[0], r0[1], r0[2] + t};
     wave_t w;
     memset(&w, 0, sizeof(w));
-    w.k[2] = 1.0;
-    w.n = 1.0;
-    w.u[0][0] = 1.0;
-    w.u[1][1] = 1.0;
-    w.E[0] = o->jones[0];
-    w.E[1] = o->jones[1];
-    w.T[0][0] = 1.0;
-    w.T[1][1] = 1.0;
-    /* phase of the incident plane wave at the first point, zero at the origin (Phi_i) */
-    double path = r[2];
+    double r[3], path;
+    if (!o->src) {
+        /* incident ray of the plane wave, started below the object */
+        double r0[3] = {x, y, o->zstart};
+        double u[3] = {r0[0] - o->center[0], r0[1] - o->center[1], r0[2] - o->center[2]};
+        double Wu[3];
+        matvec3(o->W, u, Wu);
+        double A = o->W[2][2], B = Wu[2], Cq = dot3(u, Wu) - 1.0;
+        double disc = B * B - A * Cq;
+        if (!(disc > 0.0)) return 0;
+        double t = (-B - sqrt(disc)) / A;
+        r[0] = r0[0];
+        r[1] = r0[1];
+        r[2] = r0[2] + t;
+        w.k[2] = 1.0;
+        w.n = 1.0;
+        w.u[0][0] = 1.0;
+        w.u[1][1] = 1.0;
+        w.E[0] = o->jones[0];
+        w.E[1] = o->jones[1];
+        w.T[0][0] = 1.0;
+        w.T[1][1] = 1.0;
+        /* phase of the incident plane wave at the first point, zero at the origin (Phi_i) */
+        path = r[2];
+    } else {
+        /* point source: the ray toward X = c + x e1 + y e2 reaches the surface at distance rho
+         * with the spherical wave's curvature I / rho (diverging), amplitude 1 / rho (A_0 of
+         * Eq. IntVCRM) and phase k rho (Phi_i of Eq. PhaseTotal) */
+        double v[3], g[3];
+        for (int i = 0; i < 3; ++i) {
+            v[i] = o->center[i] + x * o->e1[i] + y * o->e2[i] - o->src_pos[i];
+            g[i] = o->src_pos[i] - o->center[i];
+        }
+        double dP = sqrt(dot3(v, v));
+        for (int i = 0; i < 3; ++i) w.k[i] = v[i] / dP;
+        /* the quadratic is solved from the ray's point of closest approach to the centre, so that a
+         * distant source does not cancel the discriminant: rho = t0 + u */
+        double t0 = -dot3(w.k, g), f[3], Wk[3], Wf[3];
+        for (int i = 0; i < 3; ++i) f[i] = g[i] + t0 * w.k[i]; /* foot point minus centre */
+        matvec3(o->W, w.k, Wk);
+        matvec3(o->W, f, Wf);
+        double A = dot3(w.k, Wk), B = dot3(w.k, Wf), Cq = dot3(f, Wf) - 1.0;
+        double disc = B * B - A * Cq;
+        if (!(disc > 0.0)) return 0;
+        double rho = t0 + (-B - sqrt(disc)) / A;
+        if (!(rho > 0.0)) return 0;
+        for (int i = 0; i < 3; ++i) r[i] = o->center[i] + f[i] + (rho - t0) * w.k[i];
+        w.n = 1.0;
+        /* basis u1 = e1 made perpendicular to k, u2 = k x u1 */
+        double ek = dot3(o->e1, w.k);
+        for (int i = 0; i < 3; ++i) w.u[0][i] = o->e1[i] - ek * w.k[i];
+        double nu = sqrt(dot3(w.u[0], w.u[0]));
+        for (int i = 0; i < 3; ++i) w.u[0][i] /= nu;
+        cross3(w.k, w.u[0], w.u[1]);
+        w.Q[0][0] = w.Q[1][1] = 1.0 / rho;
+        cplx pv[3], pk = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            pv[i] = o->jones[0] * o->e1[i] + o->jones[1] * o->e2[i];
+            pk += pv[i] * w.k[i];
+        }
+        for (int i = 0; i < 3; ++i) pv[i] -= pk * w.k[i];
+        for (int a = 0; a < 2; ++a) {
+            cplx e = 0.0;
+            for (int i = 0; i < 3; ++i) e += pv[i] * w.u[a][i];
+            w.E[a] = e / rho;
+        }
+        /* transverse offset at the surface per unit (x, y): (rho / |X - s|) times the plane's
+         * axes projected on the basis */
+        const double* ax[2] = {o->e1, o->e2};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) w.T[a][b] = rho / dP * dot3(w.u[a], ax[b]);
+        path = rho;
+    }
     double dlegs = 1.0, cosprod = 1.0;
     int nf = 0, nrefl = 0;
     for (int q = 1; q <= pmax + 1; ++q) {
@@ -748,6 +852,7 @@ int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, co
                  int64_t ndir, int flags, double* out, uint8_t* mask)
 {
     const int np = pmax + 1;
+    if (o->src) return -1; /* fans: plane wave only */
     double wdt = or_fan_halfwidth(o, fan_phi);
     double ef[3] = {cos(fan_phi), sin(fan_phi), 0.0};
     double* rec = (double*)malloc(sizeof(double) * (size_t)nrays * np * OR_NFIELD);

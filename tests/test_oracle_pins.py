@@ -656,3 +656,141 @@ def test_near_field_sphere_grid_matches_mirror(oracle_mod):
         errs.append(e)
     print("near-field sphere: max relative intensity error per ray density", errs)
     assert errs[1] < 0.4 * errs[0] and errs[2] < 0.4 * errs[1] and errs[2] < 3e-3
+
+
+# --------------------------------------------------------------------------------------------
+# Incident waves that are not plane: a point source (Eq. PhaseTotal's Phi_i, Q_i of
+# Eq. WavefrontEqVec at the first point, A_0 of Eq. IntVCRM)
+# --------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("zs", [30.0, 100.0, 1000.0])
+@pytest.mark.parametrize("x", [0.5, 3.0, 6.0, 9.0])
+def test_point_source_convex_mirror(oracle_mod, zs, x):
+    """A point source on the axis at distance zs below a sphere of radius a: a ray leaving it
+    toward the point (x, 0) of the plane through the centre meets the sphere at r_1, at distance
+    rho, with incidence angle i.  A convex mirror images a source at distance rho into virtual
+    focal lines of curvature 1/rho + 2/(a cos i) and 1/rho + 2 cos(i)/a (Coddington's equations),
+    so the reflected far field of the spherical wave e^{ik rho}/rho is
+    |F|^2 = |r_perp|^2 / (rho^2 (1/rho + 2/(a cos i)) (1/rho + 2 cos(i)/a)) with phase
+    k (rho - s.r_1), s the mirror-reflected direction (y-polarised source: perpendicular to the
+    plane of incidence)."""
+    a = 10.0
+    o = oracle_mod.Object(a, a, a, m=M_WATER, wavelength=LAM, jones=(0.0, 1.0), source=(0.0, 0.0, -zs))
+    rec, _, hit = o.trace_ray(x, 0.0, 0)
+    assert hit
+    S = np.array([0.0, 0.0, -zs])
+    k = np.array([x, 0.0, zs]) / math.hypot(x, zs)
+    # entry point: |S + rho k| = a, smaller root
+    b = float(k @ S)
+    rho = -b - math.sqrt(b * b - (S @ S - a * a))
+    r1 = S + rho * k
+    n = r1 / a
+    ci = -float(k @ n)
+    s = k - 2 * float(k @ n) * n
+    i = math.acos(ci)
+    rs, _ = fresnel_closed(i, M_WATER)
+    I_closed = rs * rs / (rho * rho * (1 / rho + 2 / (a * ci)) * (1 / rho + 2 * ci / a))
+    F = rec[0, oracle_mod.F:oracle_mod.F + 6]
+    assert F[0::2] @ F[0::2] + F[1::2] @ F[1::2] == pytest.approx(I_closed, rel=1e-12)
+    # r_1 = S + rho k cancels to about 1e-16 zs in this closed form
+    assert np.allclose(rec[0, oracle_mod.S:oracle_mod.S + 3], s, atol=1e-14 * zs)
+    assert rec[0, oracle_mod.PSI] == pytest.approx(o.k0 * (rho - s @ r1), abs=1e-12 * o.k0 * zs)
+    assert rec[0, oracle_mod.NF] == 0
+
+
+def test_point_source_tends_to_plane_wave(oracle_mod):
+    """A source far below the tilted ellipsoid, at distance Z = 1e9 um: every order 0..3 of the
+    ray through (x, y) approaches the plane wave's ray at (x, y): Z F -> F (within 1e-5, a hundred
+    times L / Z), s -> s, and the phase exceeds the plane wave's by k (Z + (x^2 + y^2) /
+    (2 Z)) up to the first-order change k r_exit . ds of the far-field phase with the direction and
+    the rounding of k Z = 1e10 rad."""
+    Z = 1e9
+    plane = tilted_ellipsoid(oracle_mod, jones=(1.0, 0.3j))
+    h = math.radians(20.0) / 2
+    point = oracle_mod.Object(120.0, 100.0, 80.0, quat=(math.cos(h), math.sin(h), 0, 0), m=M_WATER, wavelength=LAM,
+                              jones=(1.0, 0.3j), source=(0.0, 0.0, -Z))
+    for x, y in ((-70.0, 10.0), (-20.0, -30.0), (5.0, 2.0), (45.0, 60.0), (90.0, -5.0)):
+        rp, _, hp = plane.trace_ray(x, y, 3)
+        rq, _, hq = point.trace_ray(x, y, 3)
+        assert hp and hq
+        for p in range(4):
+            assert rq[p, oracle_mod.VALID] == rp[p, oracle_mod.VALID]
+            if rp[p, oracle_mod.VALID] == 0.0:
+                continue
+            # corrections of order L / Z = 1e-7, magnified where F varies quickly with s: 1e-5
+            Fp = rp[p, oracle_mod.F:oracle_mod.F + 6]
+            assert np.abs(Z * rq[p, oracle_mod.F:oracle_mod.F + 6] - Fp).max() <= 1e-5 * np.abs(Fp).max()
+            ds = np.linalg.norm(rq[p, oracle_mod.S:oracle_mod.S + 3] - rp[p, oracle_mod.S:oracle_mod.S + 3])
+            assert ds < 1e-6
+            # the far-field phase varies with the direction as dPsi/ds = -k r_exit: the direction's
+            # O(L/Z) shift moves it by at most k |r_exit| |ds| (first order)
+            d = rq[p, oracle_mod.PSI] - rp[p, oracle_mod.PSI] - plane.k0 * (Z + (x * x + y * y) / (2 * Z))
+            rx = np.linalg.norm(rp[p, oracle_mod.REXIT:oracle_mod.REXIT + 3])
+            assert abs(d) <= 1.5 * plane.k0 * rx * ds + 5e-6
+            assert rq[p, oracle_mod.NF] == rp[p, oracle_mod.NF]
+            assert rq[p, oracle_mod.ORIENT] == rp[p, oracle_mod.ORIENT]
+
+
+def point_mirror_closed(a, m, zs, theta):
+    """Reflection (p = 0) of the spherical wave from a source at distance zs below a sphere of
+    radius a, reaching the far-field polar angle theta: the ray through (x, 0) of the centre plane
+    found by bisection on x, its rho, incidence angle i and tilt alpha from the axis, and the two
+    reflected curvatures 1/rho + 2/(a cos i), 1/rho + 2 cos(i)/a."""
+    S = np.array([0.0, 0.0, -zs])
+    def geo(x):
+        k = np.array([x, 0.0, zs]) / math.hypot(x, zs)
+        b = float(k @ S)
+        rho = -b - math.sqrt(b * b - (S @ S - a * a))
+        r1 = S + rho * k
+        n = r1 / a
+        s = k - 2 * float(k @ n) * n
+        return math.atan2(s[0], s[2]), rho, -float(k @ n), k
+    xmax = a * zs / math.sqrt(zs * zs - a * a) * (1 - 1e-9)  # the tangent ray
+    lo, hi = 1e-9, xmax
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (geo(lo)[0] - theta) * (geo(mid)[0] - theta) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    _, rho, ci, k = geo(0.5 * (lo + hi))
+    r_ = math.asin(math.sqrt(1 - ci * ci) / m)
+    cr = math.cos(r_)
+    rs, rp = (ci - m * cr) / (ci + m * cr), (m * ci - cr) / (m * ci + cr)
+    return rho, ci, float(k[2]), rs, rp
+
+
+def test_point_source_grid_matches_mirror(oracle_mod):
+    """The dense-ray far field of a sphere (radius 10 um, p = 0) lit by an x-polarised point
+    source 40 um below its centre, against the mirror closed form: the source's field at the
+    first point carries r_par with weight cos^2(phi) cos^2(alpha) and r_perp with sin^2(phi)
+    (p = x made perpendicular to the ray of tilt alpha), so
+    |F|^2 = (r_par^2 cos^2 phi cos^2 alpha + r_perp^2 sin^2 phi) /
+            (rho^2 (1/rho + 2/(a cos i)) (1/rho + 2 cos(i)/a));
+    the error falls with the ray spacing."""
+    a, zs = 10.0, 40.0
+    o = oracle_mod.Object(a, a, a, m=M_WATER, wavelength=LAM, jones=(1.0, 0.0), source=(0.0, 0.0, -zs))
+    nt, nph = 24, 48
+    th = (np.arange(nt) + 0.5) * math.pi / nt
+    ph = -math.pi + (np.arange(nph) + 0.5) * 2 * math.pi / nph
+    # away from the edge of the reflected cone (grazing rays end near theta = 14.5 deg), which the
+    # outermost cells of a coarse grid need not reach
+    closed = {it: point_mirror_closed(a, M_WATER, zs, th[it]) for it in range(6, nt - 2)}
+    errs = []
+    for n_target in (4_000, 16_000, 64_000):
+        out, mask, hits, _ = o.field_grid(0, nt, nph, n_target=n_target)
+        assert hits > 0
+        I_grid = (np.abs(oracle_mod.complex_field(out)[:, 0]) ** 2).sum(axis=-1)
+        e = 0.0
+        for it, (rho, ci, ca, rs, rp) in closed.items():
+            for jp in range(nph):
+                k = it * nph + jp
+                if mask[k]:
+                    continue
+                c2 = math.cos(ph[jp]) ** 2
+                Ic = (rp * rp * c2 * ca * ca + rs * rs * (1 - c2)) / (
+                    rho * rho * (1 / rho + 2 / (a * ci)) * (1 / rho + 2 * ci / a))
+                e = max(e, abs(I_grid[k] / Ic - 1))
+        errs.append(e)
+    print("point source, sphere p = 0: max relative intensity error per ray density", errs)
+    assert errs[1] < 0.4 * errs[0] and errs[2] < 0.4 * errs[1] and errs[2] < 5e-3
