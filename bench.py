@@ -384,6 +384,32 @@ def bench_ellipsoid(args, rank, world, local, dist):
             "ms_field": ts - tt, "points_per_s": ndir / (ts / 1e3), "kernel": "trace_kernel_fp64_near"}
     del rn, outn
 
+    # an incident wave that is not plane: a point source 1000 um below the centre, rays through the
+    # same number of grid points of the plane through the centre, the same far-field grid
+    objs = rtw.Object([rtw.ObjectSpec(**spec, jones=(1.0, 0.0), source=(0.0, 0.0, -1000.0))])
+    rs = rtw.rtw_trace(objs, tp, stream=stream)
+    fls = torch.zeros(rs.info()[0], dtype=torch.int32, device="cuda")
+    rtw.rtw_rays_export(rs, 0, 0, rs.info()[0], flags=fls)
+    units_s = int(((fls & 1) != 0).sum().item()) * (p_max + 1)
+    for _ in range(3):
+        rtw.rtw_trace(objs, tp, rs, stream=stream)
+        rtw.rtw_field(rs, dirs, out, mask)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        rtw.rtw_trace(objs, tp, rs, stream=stream)
+        e[1].record(stream)
+        rtw.rtw_field(rs, dirs, out, mask)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    rtw.rtw_sync_status(stream)
+    tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
+    ts = statistics.median([e[0].elapsed_time(e[2]) for e in ev])
+    point = {"source_um": [0.0, 0.0, -1000.0], "value": units_s / (ts / 1e3), "unit": UNIT, "ms_per_step": ts,
+             "ms_trace": tt, "ms_field": ts - tt}
+    del rs, objs
+
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
     host_mask = torch.empty(ndir, dtype=torch.uint8, pin_memory=True)
@@ -398,7 +424,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         host_mask.copy_(mask, non_blocking=True)
         torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
-    h2d = 256  # the object table entry uploaded by rtw_trace (sizeof(ObjDev) rounded)
+    h2d = 352  # the object table entry uploaded by rtw_trace (sizeof(ObjDev))
     d2h = host_out.numel() * 16 + host_mask.numel()
 
     if rank != 0:
@@ -437,6 +463,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "precision_forms": forms,
         "near_field": near,
+        "point_source": point,
     }
     if cpu:
         line["cpu_baseline"] = cpu
@@ -562,7 +589,7 @@ def bench_batch(args, rank, world, local, dist):
         host_mask.copy_(mask, non_blocking=True)
         torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
-    h2d = 256 * n  # the object table (256-byte entries)
+    h2d = 352 * n  # the object table (352-byte entries)
     d2h = host_out.numel() * 16 + host_mask.numel()
     if rank != 0:
         if dist:

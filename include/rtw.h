@@ -99,12 +99,23 @@ typedef struct {
     double m_re, m_im;
 } rtw_object_desc;
 
-/* Incident plane wave: wavelength in the host medium, direction (must be (0, 0, 1)), Jones vector
- * (E_x, E_y) on the unit vectors x, y. */
+/* Incident wave.  kind RTW_INCIDENT_PLANE: plane wave with direction dir (must be (0, 0, 1)) and
+ * Jones vector (E_x, E_y) on the unit vectors x, y.  kind RTW_INCIDENT_POINT (an incident wave that
+ * is not plane: Phi_i of Eq. PhaseTotal, Q_i of Eq. WavefrontEqVec, A_0 of Eq. IntVCRM): a point
+ * source at `source` (um), outside the object (else RTW_ERR_ARG), field e^{ik rho} p_perp / rho at
+ * distance rho with p = jones_x e1 + jones_y e2 made perpendicular to the ray; e1, e2 span the plane
+ * through the object's centre perpendicular to a = (center - source) / |center - source| (e1 = x,
+ * or y when a is within 26 deg of x, made perpendicular to a; e2 = a x e1).  Rays leave the source
+ * through the square grid of that plane (a ray's (x, y) are its coordinates there, from the
+ * centre); square grids and RTW_FP64 only; the far field F is then dimensionless.
+ * wavelength_um: in the host medium. */
+enum { RTW_INCIDENT_PLANE = 0, RTW_INCIDENT_POINT = 1 };
 typedef struct {
     double wavelength_um;
     double dir[3];
     double jones_re[2], jones_im[2];
+    int kind;
+    double source[3];
 } rtw_incident;
 
 /* Ray grid and trace options.  n_rays: fan -> exact number of rays; square -> target count inside

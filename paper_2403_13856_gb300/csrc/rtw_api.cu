@@ -98,6 +98,14 @@ void fill_objdev(const ObjHost& o, ObjDev& d)
     d.cap = o.lmax * o.lmax * std::cbrt(o.lmax / o.lambda);
     d.lmin = o.lmin;
     d.lmax = o.lmax;
+    d.gc[0] = o.gc[0];
+    d.gc[1] = o.gc[1];
+    d.src_mode = o.src;
+    for (int i = 0; i < 3; ++i) {
+        d.src[i] = o.src_pos[i];
+        d.e1[i] = o.e1[i];
+        d.e2[i] = o.e2[i];
+    }
 }
 
 // ray grid of one object (host arithmetic only)
@@ -392,8 +400,12 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
         if (d.m_im != 0.0) return fail(RTW_ERR_UNSUPPORTED, "object %d: absorbing objects (m_im != 0)", i);
         if (!(w.wavelength_um > 0.0) || !std::isfinite(w.wavelength_um))
             return fail(RTW_ERR_ARG, "object %d: wavelength must be positive", i);
-        if (w.dir[0] != 0.0 || w.dir[1] != 0.0 || w.dir[2] != 1.0)
+        if (w.kind != RTW_INCIDENT_PLANE && w.kind != RTW_INCIDENT_POINT)
+            return fail(RTW_ERR_ARG, "object %d: incident kind %d", i, w.kind);
+        if (w.kind == RTW_INCIDENT_PLANE && (w.dir[0] != 0.0 || w.dir[1] != 0.0 || w.dir[2] != 1.0))
             return fail(RTW_ERR_UNSUPPORTED, "object %d: incident direction must be (0, 0, 1)", i);
+        if (w.kind == RTW_INCIDENT_POINT && !std::isfinite(w.source[0] + w.source[1] + w.source[2]))
+            return fail(RTW_ERR_ARG, "object %d: source position must be finite", i);
         o.a[0] = d.a;
         o.a[1] = d.b;
         o.a[2] = d.c;
@@ -426,6 +438,59 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
         o.S[0][1] = o.W[0][1] - o.W[0][2] * o.W[1][2] / o.W[2][2];
         o.S[1][0] = o.S[0][1];
         o.S[1][1] = o.W[1][1] - o.W[1][2] * o.W[1][2] / o.W[2][2];
+        o.gc[0] = o.c[0];
+        o.gc[1] = o.c[1];
+        o.src = w.kind == RTW_INCIDENT_POINT;
+        if (o.src) {
+            // rays from the source s through X = c + x e1 + y e2 (v = X - s = g + x e1 + y e2, g = c - s)
+            // hit where (v.W g)^2 - (v.W v)(g.W g - 1) > 0: v^T K v > 0 with K = W g g^T W - (g.W g - 1) W,
+            // an ellipse (w - w0)^T S (w - w0) < 1 of the plane
+            double g[3], Wg[3];
+            for (int k = 0; k < 3; ++k) {
+                o.src_pos[k] = w.source[k];
+                g[k] = o.c[k] - w.source[k];
+            }
+            for (int r = 0; r < 3; ++r) Wg[r] = o.W[r][0] * g[0] + o.W[r][1] * g[1] + o.W[r][2] * g[2];
+            const double gWg = g[0] * Wg[0] + g[1] * Wg[1] + g[2] * Wg[2];
+            if (!(gWg > 1.0)) return fail(RTW_ERR_ARG, "object %d: the source lies inside the object", i);
+            const double gd = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            const double ax[3] = {g[0] / gd, g[1] / gd, g[2] / gd};
+            const double ref[3] = {std::fabs(ax[0]) > 0.9 ? 0.0 : 1.0, std::fabs(ax[0]) > 0.9 ? 1.0 : 0.0, 0.0};
+            const double ra = ref[0] * ax[0] + ref[1] * ax[1] + ref[2] * ax[2];
+            double n1 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                o.e1[k] = ref[k] - ra * ax[k];
+                n1 += o.e1[k] * o.e1[k];
+            }
+            n1 = std::sqrt(n1);
+            for (int k = 0; k < 3; ++k) o.e1[k] /= n1;
+            o.e2[0] = ax[1] * o.e1[2] - ax[2] * o.e1[1];
+            o.e2[1] = ax[2] * o.e1[0] - ax[0] * o.e1[2];
+            o.e2[2] = ax[0] * o.e1[1] - ax[1] * o.e1[0];
+            double K[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) K[r][c] = Wg[r] * Wg[c] - (gWg - 1.0) * o.W[r][c];
+            auto Kv = [&](const double* v, double* out3) {
+                for (int r = 0; r < 3; ++r) out3[r] = K[r][0] * v[0] + K[r][1] * v[1] + K[r][2] * v[2];
+            };
+            auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+            double Kg[3], K1[3], K2[3];
+            Kv(g, Kg);
+            Kv(o.e1, K1);
+            Kv(o.e2, K2);
+            const double M00 = dot(o.e1, K1), M01 = dot(o.e1, K2), M11 = dot(o.e2, K2);
+            const double b0 = dot(o.e1, Kg), b1 = dot(o.e2, Kg);
+            const double dM = M00 * M11 - M01 * M01;
+            if (!(dM > 0.0)) return fail(RTW_ERR_ARG, "object %d: degenerate view from the source", i);
+            const double w0x = -(M11 * b0 - M01 * b1) / dM, w0y = -(M00 * b1 - M01 * b0) / dM;
+            const double f0 = dot(g, Kg) + b0 * w0x + b1 * w0y;
+            if (!(f0 > 0.0)) return fail(RTW_ERR_ARG, "object %d: degenerate view from the source", i);
+            o.S[0][0] = -M00 / f0;
+            o.S[0][1] = o.S[1][0] = -M01 / f0;
+            o.S[1][1] = -M11 / f0;
+            o.gc[0] = w0x;
+            o.gc[1] = w0y;
+        }
         const double det = o.S[0][0] * o.S[1][1] - o.S[0][1] * o.S[1][0];
         o.Sinv[0][0] = o.S[1][1] / det;
         o.Sinv[0][1] = -o.S[0][1] / det;
@@ -465,6 +530,9 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace: p_max out of [0, 15]");
     if (tp->precision != RTW_FP64 && tp->precision != RTW_MIXED && tp->precision != RTW_DFLOAT)
         return fail(RTW_ERR_ARG, "rtw_trace: precision %d", tp->precision);
+    for (int i = 0; i < obj->count; ++i)
+        if (obj->h[(size_t)i].src && (tp->grid != RTW_GRID_SQUARE || tp->precision != RTW_FP64))
+            return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: a point source takes a square grid in double precision");
     if (!(tp->observe_radius >= 0.0) || !std::isfinite(tp->observe_radius))
         return fail(RTW_ERR_ARG, "rtw_trace: observe_radius must be finite and >= 0");
     if (tp->observe_radius > 0.0) {

@@ -181,6 +181,7 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
         tp.n_rays = bp->n_rays[i];
         double h = 0.0, fw = 0.0;
         long long nx = 0, ny = 0;
+        if (obj->h[(size_t)i].src) return fail(RTW_ERR_UNSUPPORTED, "rtw_far_field_batch: plane waves only");
         int rc = rtw::host::grid_of(obj->h[(size_t)i], &tp, &h, &nx, &ny, &fw);
         if (rc != RTW_OK) return rc;
         ObjDev& d = objs[(size_t)i];

@@ -27,8 +27,11 @@ struct ObjHost {
     double lambda;
     double jre[2], jim[2];
     double W[3][3];
-    double S[2][2], Sinv[2][2];
+    double S[2][2], Sinv[2][2];  // rays that hit: (w - gc)^T S (w - gc) < 1 on the grid's plane
     double lmin, lmax;
+    double gc[2];                 // centre of the ray grid (plane wave: c_x, c_y)
+    int src;                      // 1: point source
+    double src_pos[3], e1[3], e2[3];
 };
 
 // sets the calling thread's last-error message and returns code

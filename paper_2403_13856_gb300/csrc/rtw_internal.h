@@ -41,8 +41,13 @@ struct ObjDev {
     long long nx, ny;       // square: grid size; fan: (n, 1)
     long long ray_offset;   // first global ray index of this object
     long long item_first;   // first work item (kRaysPerItem rays) of this object in a batched trace
+    double gc[2];           // centre of the square ray grid (plane wave: c_x, c_y)
+    double src[3];          // point source (src_mode 1): rays leave it through c + x e1 + y e2
+    double e1[3], e2[3];
+    int src_mode;
+    int pad1;
 };
-static_assert(sizeof(ObjDev) == 256, "object table entries are 256 bytes");
+static_assert(sizeof(ObjDev) == 352, "object table entries are 352 bytes");
 
 // rays per work item of the persistent batched trace
 constexpr int kRaysPerItem = 256;

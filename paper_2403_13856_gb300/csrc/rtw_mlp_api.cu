@@ -238,6 +238,7 @@ int rtw_mlp_samples(const rtw_object* obj, const double* uv, const int32_t* obj_
     std::vector<rtw::ObjDev> od((size_t)obj->count);
     std::vector<rtw::ObjFeat> of((size_t)obj->count);
     for (int i = 0; i < obj->count; ++i) {
+        if (obj->h[(size_t)i].src) return fail(RTW_ERR_UNSUPPORTED, "rtw_mlp_samples: plane waves only");
         rtw::host::fill_objdev(obj->h[(size_t)i], od[(size_t)i]);
         od[(size_t)i].grid = rtw::kGridSquare;
         rtw::host::object_features(obj->h[(size_t)i], of[(size_t)i]);

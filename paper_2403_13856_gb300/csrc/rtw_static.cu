@@ -99,6 +99,7 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     if (!(d->m_re > 0.0) || d->m_re == 1.0) return set_error(RTW_ERR_ARG, "m must be positive and != 1");
     if (d->m_im != 0.0) return set_error(RTW_ERR_UNSUPPORTED, "absorbing objects");
     if (!(w->wavelength_um > 0.0)) return set_error(RTW_ERR_ARG, "wavelength must be positive");
+    if (w->kind != RTW_INCIDENT_PLANE) return set_error(RTW_ERR_UNSUPPORTED, "plane waves only");
     if (w->dir[0] != 0.0 || w->dir[1] != 0.0 || w->dir[2] != 1.0)
         return set_error(RTW_ERR_UNSUPPORTED, "incident direction must be (0, 0, 1)");
 

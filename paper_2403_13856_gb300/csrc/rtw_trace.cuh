@@ -15,6 +15,8 @@
 //     transverse offsets (orientation of the map t -> s).
 #pragma once
 
+#include <type_traits>
+
 #include "rtw_df.cuh"
 #include "rtw_internal.h"
 
@@ -158,9 +160,9 @@ __device__ __forceinline__ bool ray_origin(const ObjDev& o, long long local, dou
         return true;
     }
     long long ix = local % o.nx, iy = local / o.nx;
-    x = o.c[0] + ((double)ix + 0.5 - (double)(o.nx / 2)) * o.h;
-    y = o.c[1] + ((double)iy + 0.5 - (double)(o.ny / 2)) * o.h;
-    double dx = x - o.c[0], dy = y - o.c[1];
+    x = o.gc[0] + ((double)ix + 0.5 - (double)(o.nx / 2)) * o.h;
+    y = o.gc[1] + ((double)iy + 0.5 - (double)(o.ny / 2)) * o.h;
+    double dx = x - o.gc[0], dy = y - o.gc[1];
     double qf = dx * (o.S[0] * dx + o.S[1] * dy) + dy * (o.S[1] * dx + o.S[2] * dy);
     return qf < 1.0;
 }
@@ -246,21 +248,84 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
     // entry point of the incident ray (plane wave along +z), started below the object
     double r[3] = {x, y, o.zstart};
     T k0v = T(0), k1v = T(0), k2v = T(1);
-    {
-        const T kz[3] = {T(0), T(0), T(1)};
-        bool ok;
-        const double t = chord_to_surface<T>(o, W, r, kz, T(-1), &ok);
-        if (!ok) return;
-        r[2] += t;
-    }
     // incident wave: k = z, basis (a, b) = (x, -y) so that every basis has a x b = -k
     T a0 = T(1), a1 = T(0), a2 = T(0);
     T q11 = T(0), q12 = T(0), q22 = T(0);
     T E1r = (T)o.jre[0], E1i = (T)o.jim[0], E2r = -(T)o.jre[1], E2i = -(T)o.jim[1];
     T T11 = T(1), T12 = T(0), T21 = T(0), T22 = T(-1);
     int sT = -1;
-    double path = r[2];  // phase of the incident plane wave at the first point (zero at the origin)
     T pdet = T(1), cosprod = T(1);
+    double path;
+    if (!o.src_mode) {
+        const T kz[3] = {T(0), T(0), T(1)};
+        bool ok;
+        const double t = chord_to_surface<T>(o, W, r, kz, T(-1), &ok);
+        if (!ok) return;
+        r[2] += t;
+        path = r[2];  // phase of the incident plane wave at the first point (zero at the origin)
+    } else if constexpr (std::is_same<T, double>::value) {
+        // point source s: the ray toward X = c + x e1 + y e2 meets the surface at distance rho with
+        // the spherical wave's curvature I / rho, amplitude 1 / rho and phase k rho; the entry root
+        // is solved from the ray's point of closest approach to the centre (no cancellation for a
+        // distant source)
+        double v[3], g[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            v[i] = o.c[i] + x * o.e1[i] + y * o.e2[i] - o.src[i];
+            g[i] = o.src[i] - o.c[i];
+        }
+        const double dP = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), iP = 1.0 / dP;
+        const double k[3] = {v[0] * iP, v[1] * iP, v[2] * iP};
+        const double t0 = -(k[0] * g[0] + k[1] * g[1] + k[2] * g[2]);
+        const double f[3] = {g[0] + t0 * k[0], g[1] + t0 * k[1], g[2] + t0 * k[2]};
+        double wkx, wky, wkz, wfx, wfy, wfz;
+        symv(o.W, k[0], k[1], k[2], wkx, wky, wkz);
+        symv(o.W, f[0], f[1], f[2], wfx, wfy, wfz);
+        const double A = k[0] * wkx + k[1] * wky + k[2] * wkz, B = k[0] * wfx + k[1] * wfy + k[2] * wfz;
+        const double Cq = f[0] * wfx + f[1] * wfy + f[2] * wfz - 1.0;
+        const double disc = B * B - A * Cq;
+        if (!(disc > 0.0)) return;
+        const double u = (-B - sqrt(disc)) / A, rho = t0 + u;
+        if (!(rho > 0.0)) return;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) r[i] = o.c[i] + f[i] + u * k[i];
+        k0v = k[0];
+        k1v = k[1];
+        k2v = k[2];
+        // basis a = e1 made perpendicular to k, b = a x k
+        const double ek = o.e1[0] * k[0] + o.e1[1] * k[1] + o.e1[2] * k[2];
+        double ax = o.e1[0] - ek * k[0], ay = o.e1[1] - ek * k[1], az = o.e1[2] - ek * k[2];
+        const double ia = rsqrt(ax * ax + ay * ay + az * az);
+        ax *= ia;
+        ay *= ia;
+        az *= ia;
+        const double bx = ay * k[2] - az * k[1], by = az * k[0] - ax * k[2], bz = ax * k[1] - ay * k[0];
+        a0 = ax;
+        a1 = ay;
+        a2 = az;
+        const double irho = 1.0 / rho;
+        q11 = irho;
+        q22 = irho;
+        // E = (p . a, p . b) / rho with p = jones_x e1 + jones_y e2 (its part along k drops out)
+        const double a_e1 = ax * o.e1[0] + ay * o.e1[1] + az * o.e1[2], a_e2 = ax * o.e2[0] + ay * o.e2[1] + az * o.e2[2];
+        const double b_e1 = bx * o.e1[0] + by * o.e1[1] + bz * o.e1[2], b_e2 = bx * o.e2[0] + by * o.e2[1] + bz * o.e2[2];
+        E1r = (o.jre[0] * a_e1 + o.jre[1] * a_e2) * irho;
+        E1i = (o.jim[0] * a_e1 + o.jim[1] * a_e2) * irho;
+        E2r = (o.jre[0] * b_e1 + o.jre[1] * b_e2) * irho;
+        E2i = (o.jim[0] * b_e1 + o.jim[1] * b_e2) * irho;
+        // transverse offset at the surface per unit (x, y) of the grid's plane
+        const double sc = rho * iP;
+        T11 = sc * a_e1;
+        T12 = sc * a_e2;
+        T21 = sc * b_e1;
+        T22 = sc * b_e2;
+        const double dT = T11 * T22 - T12 * T21;
+        sT = dT > 0.0 ? 1 : -1;
+        cosprod = fabs(dT);  // dA/dOmega of the caustic test counts grid area: |det T| of the start
+        path = rho;
+    } else {
+        return;  // point sources are traced in double precision (the entry points reject others)
+    }
     int nf = 0;
     T n_in = T(1);
     double n_in_d = 1.0;  // the same index in double precision, for the optical path

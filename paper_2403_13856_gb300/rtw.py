@@ -40,7 +40,8 @@ class rtw_object_desc(ctypes.Structure):
 
 class rtw_incident(ctypes.Structure):
     _fields_ = [("wavelength_um", ctypes.c_double), ("dir", ctypes.c_double * 3),
-                ("jones_re", ctypes.c_double * 2), ("jones_im", ctypes.c_double * 2)]
+                ("jones_re", ctypes.c_double * 2), ("jones_im", ctypes.c_double * 2), ("kind", ctypes.c_int),
+                ("source", ctypes.c_double * 3)]
 
 
 class rtw_trace_params(ctypes.Structure):
@@ -140,6 +141,7 @@ class ObjectSpec:
     m: float = 1.333
     wavelength: float = 0.6328
     jones: Sequence[complex] = (1.0, 0.0)
+    source: Optional[Sequence[float]] = None  # point source position (um), else a plane wave along +z
 
 
 class Object:
@@ -161,6 +163,8 @@ class Object:
             j = [complex(x) for x in s.jones]
             w.jones_re[:] = [j[0].real, j[1].real]
             w.jones_im[:] = [j[0].imag, j[1].imag]
+            w.kind = 0 if s.source is None else 1
+            w.source[:] = [0.0, 0.0, 0.0] if s.source is None else [float(v) for v in s.source]
         h = ctypes.c_void_p()
         _check(lib().rtw_create_object(ctypes.byref(descs), n, ctypes.byref(incs), ctypes.byref(h)))
         self.handle = h
