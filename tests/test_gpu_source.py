@@ -101,3 +101,24 @@ def test_point_source_arguments(rtw, oracle_mod):
     out = torch.zeros((1, 8 * 16, 1, 2), dtype=torch.complex128, device="cuda")
     with pytest.raises(rtw.RTWError):  # the batched path takes plane waves
         rtw.rtw_far_field_batch(g, rtw.batch_params(np.array([1000]), p_max=1), rtw.dirs_grid(8, 16), out)
+
+
+def test_point_source_on_a_sphere_of_points(rtw, oracle_mod):
+    """Both extensions together: a point source lighting the drop, the field taken on the sphere
+    |M| = 500 um (three components per point), against the oracle's sphere field."""
+    g, o = objects(rtw, oracle_mod, (0.0, 1.0), (0.0, 0.0, -600.0))
+    p_max, nt, nph, R = 3, 32, 64, 500.0
+    tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=20_000, observe_radius=R)
+    rays = rtw.rtw_trace(g, tp)
+    out = torch.zeros((nt * nph, p_max + 1, 3), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_grid(nt, nph), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    ref, rm, hits = o.field_sphere(p_max, nt, nph, R, n_target=20_000)
+    ref = oracle_mod.complex_field(ref)
+    assert hits > 2000
+    assert np.array_equal(mask.cpu().numpy(), rm)
+    scale = np.abs(ref).max()
+    err = np.abs(out.cpu().numpy() - ref).max()
+    print(f"point source, sphere of points: max |dE| / max |E| = {err / scale:.2e}")
+    assert scale > 0 and err <= 1e-6 * scale
