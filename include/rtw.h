@@ -126,7 +126,8 @@ typedef struct {
  * crosses the sphere |M| = R about the origin instead: the field at a finite point M (Eqs.
  * IntVCRM, DivFactVCRM with the Gaussian curvature kappa_GM at M, and PhasePath to r_M), whose
  * last leg of length t contributes 1 / det(I + t Q') to the divergence factor, its focal lines to
- * N_f and k t to the phase. */
+ * N_f and k t to the phase; the records' directions (rtw_rays_export) are then the unit vectors
+ * M / R of the crossing points and their fields the fields at M. */
 typedef struct {
     int grid;
     int p_max;

@@ -122,3 +122,25 @@ def test_point_source_on_a_sphere_of_points(rtw, oracle_mod):
     err = np.abs(out.cpu().numpy() - ref).max()
     print(f"point source, sphere of points: max |dE| / max |E| = {err / scale:.2e}")
     assert scale > 0 and err <= 1e-6 * scale
+
+
+def test_point_source_newton_vs_oracle_exact(rtw, oracle_mod):
+    """RTW_NEWTON with a point source: every hit (about 1.5e4 rays, orders 0..3, 48 x 96
+    directions) replaced by the exact ray found by Newton steps in the grid plane's coordinates;
+    against the oracle's exact branch sum on the same hits, the same failures."""
+    g, o = objects(rtw, oracle_mod, (1.0, 0.0))
+    p_max, nt, nph = 3, 48, 96
+    rtw.rtw_newton_failures()
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=15_000))
+    out = torch.zeros((nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_grid(nt, nph), out, mask, mode=rtw.RTW_NEWTON, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    gfail = rtw.rtw_newton_failures()
+    ref, rm, hits, nfail = o.field_grid(p_max, nt, nph, n_target=15_000, flags=oracle_mod.FIELD_EXACT)
+    ref = oracle_mod.complex_field(ref)
+    print(f"point source Newton: {hits} hits, {nfail} not converged (oracle), {gfail} (GPU)")
+    assert hits > 3000 and gfail == nfail
+    assert np.array_equal(mask.cpu().numpy(), rm)
+    scale = np.abs(ref).max()
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-6 * scale
