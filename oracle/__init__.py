@@ -101,13 +101,14 @@ class Object:
     """One ellipsoid in a plane wave along +z (host medium index 1)."""
 
     def __init__(self, a, b, c, quat=(1.0, 0.0, 0.0, 0.0), center=(0.0, 0.0, 0.0), m=1.333,
-                 wavelength=0.6328, jones=(1.0, 0.0), source=None):
-        """source: None for a plane wave along +z, else the point source's position (um)."""
+                 wavelength=0.6328, jones=(1.0, 0.0), source=None, shape_e=1.0):
+        """source: None for a plane wave along +z, else the point source's position (um).
+        shape_e: superellipsoid exponent e >= 1 (surface sum |u_i|^(2e) = 1), 1 for the ellipsoid."""
         L = lib()
         j = [complex(x) for x in jones]
         src = (0.0, 0.0, 0.0, 0.0) if source is None else (1.0, *source)
         self.params = np.array([a, b, c, *quat, *center, m, wavelength,
-                                j[0].real, j[0].imag, j[1].real, j[1].imag, *src], dtype=np.float64)
+                                j[0].real, j[0].imag, j[1].real, j[1].imag, *src, shape_e], dtype=np.float64)
         self._buf = ctypes.create_string_buffer(L.or_object_size())
         if L.or_make_object(_ptr(self.params), self._buf) != 0:
             raise ValueError("invalid object parameters")

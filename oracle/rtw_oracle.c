@@ -51,6 +51,8 @@ struct or_object {
     double gc[2];   /* centre of the ray grid (plane wave: the object's centre x, y) */
     int src;        /* 0: plane wave along +z; 1: point source */
     double src_pos[3], e1[3], e2[3];
+    double shape_e; /* superellipsoid exponent e >= 1: sum_i |u_i|^(2e) = 1; e = 1 is the ellipsoid */
+    double Rbound;  /* radius about the centre that contains the object */
 };
 
 /* ------------------------------------------------------------------------------------- */
@@ -187,17 +189,27 @@ int or_make_object(const double* p, or_object* o)
             for (int k = 0; k < 3; ++k) s += o->R[i][k] * o->R[j][k] / (o->semi[k] * o->semi[k]);
             o->W[i][j] = s;
         }
+    o->shape_e = p[20];
+    if (!(o->shape_e >= 1.0) || !isfinite(o->shape_e)) return -1;
     o->Lmax = fmax(o->semi[0], fmax(o->semi[1], o->semi[2]));
     o->Lmin = fmin(o->semi[0], fmin(o->semi[1], o->semi[2]));
     o->zstart = o->center[2] - 2.0 * o->Lmax - 1.0;
-    /* silhouette along z: the Schur complement of W_zz */
-    o->S[0][0] = o->W[0][0] - o->W[0][2] * o->W[0][2] / o->W[2][2];
-    o->S[0][1] = o->W[0][1] - o->W[0][2] * o->W[1][2] / o->W[2][2];
+    /* a superellipsoid lies inside the ellipsoid of semi-axes a_i 3^((1 - 1/e) / 2): by the power-mean
+     * inequality sum u_i^2 / 3 <= (sum |u_i|^(2e) / 3)^(1/e) <= 3^(-1/e) */
+    const double grow = sqrt(pow(3.0, 1.0 - 1.0 / o->shape_e));
+    o->Rbound = o->Lmax * grow;
+    double Wb[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Wb[i][j] = o->W[i][j] / (grow * grow);
+    /* silhouette along z (of the bounding ellipsoid for e > 1): the Schur complement of W_zz */
+    o->S[0][0] = Wb[0][0] - Wb[0][2] * Wb[0][2] / Wb[2][2];
+    o->S[0][1] = Wb[0][1] - Wb[0][2] * Wb[1][2] / Wb[2][2];
     o->S[1][0] = o->S[0][1];
-    o->S[1][1] = o->W[1][1] - o->W[1][2] * o->W[1][2] / o->W[2][2];
+    o->S[1][1] = Wb[1][1] - Wb[1][2] * Wb[1][2] / Wb[2][2];
     o->gc[0] = o->center[0];
     o->gc[1] = o->center[1];
     o->src = p[16] != 0.0;
+    if (o->src && o->shape_e != 1.0) return -1; /* point sources: ellipsoids only */
     if (o->src) {
         /* point source s: rays s + t v through X = c + x e1 + y e2 meet the surface where
          * (v.W g)^2 - (v.W v)(g.W g - 1) > 0 (g = c - s), i.e. v^T K v > 0 with
@@ -341,14 +353,144 @@ static void outgoing(const or_object* o, const double s[2][3], const double nh[3
     out->E[1] = c_par * Epar;
 }
 
+/* ------------------------------------------------------------------------------------- */
+/* the surface: ellipsoid (e = 1) or superellipsoid F(x) = sum_i |u_i|^(2e) = 1,            */
+/* u = diag(1/a) R^T (x - c); F is convex for e >= 1, so a line meets the surface twice      */
+/* at most and the Introduction's principle (iii) (one curvature matrix per point) holds     */
+/* wherever F is twice differentiable, which e >= 1 ensures                                  */
+/* ------------------------------------------------------------------------------------- */
+
+/* body coordinates u of point x and the body-frame rate kappa of direction k (u(t) = u + t kappa) */
+static void body_line(const or_object* o, const double x[3], const double k[3], double u[3], double kap[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        double su = 0.0, sk = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            su += o->R[j][i] * (x[j] - o->center[j]);
+            sk += o->R[j][i] * k[j];
+        }
+        u[i] = su / o->semi[i];
+        kap[i] = sk / o->semi[i];
+    }
+}
+
+/* phi(t) = F(x + t k) - 1 and its derivative along the line */
+static double line_phi(const or_object* o, const double u[3], const double kap[3], double t, double* dphi)
+{
+    const double e = o->shape_e;
+    double f = -1.0, df = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double v = u[i] + t * kap[i], av = fabs(v);
+        f += pow(av, 2.0 * e);
+        df += 2.0 * e * copysign(pow(av, 2.0 * e - 1.0), v) * kap[i];
+    }
+    if (dphi) *dphi = df;
+    return f;
+}
+
+/* g = grad F / 2 and H = (Hessian of F) / 2 at surface point x; for e = 1 these are W (x - c) and W.
+ * The surface's second fundamental form for the outward normal g / |g| is s^T H s / |g|. */
+static void shape_gH(const or_object* o, const double x[3], double g[3], double H[3][3])
+{
+    double d[3] = {x[0] - o->center[0], x[1] - o->center[1], x[2] - o->center[2]};
+    if (o->shape_e == 1.0) {
+        matvec3(o->W, d, g);
+        memcpy(H, o->W, sizeof(o->W));
+        return;
+    }
+    const double e = o->shape_e;
+    double gb[3], hb[3];
+    for (int i = 0; i < 3; ++i) {
+        double ui = (o->R[0][i] * d[0] + o->R[1][i] * d[1] + o->R[2][i] * d[2]) / o->semi[i];
+        double au = fabs(ui);
+        /* d/dx_b of |u_i|^(2e) / 2 = e |u_i|^(2e-1) sgn(u_i) / a_i, second derivative
+         * e (2e - 1) |u_i|^(2e-2) / a_i^2, both along body axis i */
+        gb[i] = e * copysign(pow(au, 2.0 * e - 1.0), ui) / o->semi[i];
+        hb[i] = e * (2.0 * e - 1.0) * pow(au, 2.0 * e - 2.0) / (o->semi[i] * o->semi[i]);
+    }
+    for (int i = 0; i < 3; ++i) {
+        g[i] = o->R[i][0] * gb[0] + o->R[i][1] * gb[1] + o->R[i][2] * gb[2];
+        for (int j = 0; j < 3; ++j)
+            H[i][j] = o->R[i][0] * o->R[j][0] * hb[0] + o->R[i][1] * o->R[j][1] * hb[1] + o->R[i][2] * o->R[j][2] * hb[2];
+    }
+}
+
+/* parameter t at which the line u + t kappa leaves the body box |u_i| <= 1 (u inside it) */
+static double box_exit(const double u[3], const double kap[3])
+{
+    double t = INFINITY;
+    for (int i = 0; i < 3; ++i)
+        if (kap[i] != 0.0) t = fmin(t, (copysign(1.0, kap[i]) - u[i]) / kap[i]);
+    return t;
+}
+
+/* superellipsoid chord from surface point r along the inward direction k: the positive root of the
+ * convex phi with phi(0) = 0.  The box exit lies at or beyond it (phi >= 0 there, F >= 1 on the box
+ * faces), and Newton from the right of a root of a convex increasing function decreases
+ * monotonically to it. */
+static double chord_super(const or_object* o, const double r[3], const double k[3])
+{
+    double u[3], kap[3];
+    body_line(o, r, k, u, kap);
+    double t = box_exit(u, kap);
+    if (!(t > 0.0) || !isfinite(t)) return 0.0;
+    const double t0 = t;
+    for (int it = 0; it < 400; ++it) {
+        double df, f = line_phi(o, u, kap, t, &df);
+        if (!(f > 0.0) || !(df > 0.0)) break;
+        double step = f / df;
+        t -= step;
+        if (step <= 1e-16 * t0) break;
+    }
+    return t;
+}
+
+/* entry of a line into the superellipsoid: the smaller root of phi.  The line crosses the body box on
+ * [t_in, t_out]; bisection on the increasing phi' there finds the minimum of phi (no hit unless
+ * it is negative); Newton from t_in (phi >= 0, decreasing) increases monotonically to the root. */
+static int entry_super(const or_object* o, const double r0[3], const double k[3], double* t_hit)
+{
+    double u[3], kap[3];
+    body_line(o, r0, k, u, kap);
+    double tin = -INFINITY, tout = INFINITY;
+    for (int i = 0; i < 3; ++i) {
+        if (kap[i] == 0.0) {
+            if (!(fabs(u[i]) < 1.0)) return 0;
+            continue;
+        }
+        double ta = (-1.0 - u[i]) / kap[i], tb = (1.0 - u[i]) / kap[i];
+        tin = fmax(tin, fmin(ta, tb));
+        tout = fmin(tout, fmax(ta, tb));
+    }
+    if (!(tin < tout)) return 0;
+    double a = tin, b = tout;
+    for (int it = 0; it < 200 && b - a > 1e-16 * (fabs(a) + fabs(b)); ++it) {
+        double mid = 0.5 * (a + b), dm;
+        line_phi(o, u, kap, mid, &dm);
+        if (dm > 0.0) b = mid;
+        else a = mid;
+    }
+    double tm = 0.5 * (a + b);
+    if (!(line_phi(o, u, kap, tm, NULL) < 0.0)) return 0;
+    double t = tin;
+    for (int it = 0; it < 400; ++it) {
+        double df, f = line_phi(o, u, kap, t, &df);
+        if (!(f > 0.0) || !(df < 0.0)) break;
+        double step = -f / df;
+        t += step;
+        if (step <= 1e-16 * fabs(tm)) break;
+    }
+    *t_hit = t;
+    return 1;
+}
+
 /* one reflection / refraction at surface point r, wave `in` arriving from the medium in->n into
  * the medium n_other.  Returns 0 for a grazing ray. */
 static int interact(const or_object* o, const double r[3], const wave_t* in, double n_other,
                     split_t* sp)
 {
-    double x[3] = {r[0] - o->center[0], r[1] - o->center[1], r[2] - o->center[2]};
-    double g[3];
-    matvec3(o->W, x, g);
+    double g[3], H[3][3];
+    shape_gH(o, r, g, H);
     double gn = norm3(g);
     double nh[3] = {g[0] / gn, g[1] / gn, g[2] / gn}; /* outward normal */
     double cos_i = dot3(in->k, nh);
@@ -363,7 +505,7 @@ static int interact(const or_object* o, const double r[3], const wave_t* in, dou
         for (int c = 0; c < 3; ++c) ep[c] /= len;
     }
     /* surface basis (s1, s2) = (e_perp, n x e_perp) and the curvature matrix C in it:
-     * second fundamental form of the quadric with respect to the outward normal */
+     * second fundamental form of the surface with respect to the outward normal */
     double s[2][3];
     for (int c = 0; c < 3; ++c) s[0][c] = ep[c];
     cross3(nh, ep, s[1]);
@@ -371,7 +513,7 @@ static int interact(const or_object* o, const double r[3], const wave_t* in, dou
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
             double Ws[3];
-            matvec3(o->W, s[b], Ws);
+            matvec3(H, s[b], Ws);
             C[a][b] = dot3(s[a], Ws) / gn;
         }
     /* Eq. (SnellVec): the tangential component of the wave vector is kept */
@@ -429,6 +571,7 @@ static int interact(const or_object* o, const double r[3], const wave_t* in, dou
 /* length of the chord from surface point r along the inward direction k */
 static double chord(const or_object* o, const double r[3], const double k[3])
 {
+    if (o->shape_e != 1.0) return chord_super(o, r, k);
     double u[3] = {r[0] - o->center[0], r[1] - o->center[1], r[2] - o->center[2]};
     double Wk[3], Wu[3];
     matvec3(o->W, k, Wk);
@@ -565,13 +708,19 @@ int or_trace_ray(const or_object* o, double x, double y, int pmax, double* out, 
     if (!o->src) {
         /* incident ray of the plane wave, started below the object */
         double r0[3] = {x, y, o->zstart};
-        double u[3] = {r0[0] - o->center[0], r0[1] - o->center[1], r0[2] - o->center[2]};
-        double Wu[3];
-        matvec3(o->W, u, Wu);
-        double A = o->W[2][2], B = Wu[2], Cq = dot3(u, Wu) - 1.0;
-        double disc = B * B - A * Cq;
-        if (!(disc > 0.0)) return 0;
-        double t = (-B - sqrt(disc)) / A;
+        double t;
+        if (o->shape_e != 1.0) {
+            const double kz[3] = {0.0, 0.0, 1.0};
+            if (!entry_super(o, r0, kz, &t)) return 0;
+        } else {
+            double u[3] = {r0[0] - o->center[0], r0[1] - o->center[1], r0[2] - o->center[2]};
+            double Wu[3];
+            matvec3(o->W, u, Wu);
+            double A = o->W[2][2], B = Wu[2], Cq = dot3(u, Wu) - 1.0;
+            double disc = B * B - A * Cq;
+            if (!(disc > 0.0)) return 0;
+            t = (-B - sqrt(disc)) / A;
+        }
         r[0] = r0[0];
         r[1] = r0[1];
         r[2] = r0[2] + t;
@@ -852,7 +1001,7 @@ int or_field_fan(const or_object* o, int64_t nrays, double fan_phi, int pmax, co
                  int64_t ndir, int flags, double* out, uint8_t* mask)
 {
     const int np = pmax + 1;
-    if (o->src) return -1; /* fans: plane wave only */
+    if (o->src || o->shape_e != 1.0) return -1; /* fans: plane wave on an ellipsoid only */
     double wdt = or_fan_halfwidth(o, fan_phi);
     double ef[3] = {cos(fan_phi), sin(fan_phi), 0.0};
     double* rec = (double*)malloc(sizeof(double) * (size_t)nrays * np * OR_NFIELD);
@@ -1379,7 +1528,7 @@ int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int p
                         double* out, uint8_t* mask, int nthreads)
 {
     double rc = sqrt(dot3(o->center, o->center));
-    if (!(R > rc + o->Lmax)) return -1;
+    if (!(R > rc + o->Rbound)) return -1;
     return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, R);
 }
 
