@@ -359,27 +359,36 @@ def bench_ellipsoid(args, rank, world, local, dist):
         del rf
     rtw.rtw_sync_status(stream)
 
+    def timed_trace_field(o, tpx, rx, outx, reps=10):
+        """median ms of (trace, trace + field) over reps steps after 3 warm-up steps, L2 flushed"""
+        for _ in range(3):
+            rtw.rtw_trace(o, tpx, rx, stream=stream)
+            rtw.rtw_field(rx, dirs, outx, mask)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+        for e in ev:
+            flush.zero_()
+            e[0].record(stream)
+            rtw.rtw_trace(o, tpx, rx, stream=stream)
+            e[1].record(stream)
+            rtw.rtw_field(rx, dirs, outx, mask)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        rtw.rtw_sync_status(stream)
+        return (statistics.median([e[0].elapsed_time(e[1]) for e in ev]),
+                statistics.median([e[0].elapsed_time(e[2]) for e in ev]))
+
+    def hit_units(rx):
+        flx = torch.zeros(rx.info()[0], dtype=torch.int32, device="cuda")
+        rtw.rtw_rays_export(rx, 0, 0, rx.info()[0], flags=flx)
+        return int(((flx & 1) != 0).sum().item()) * (p_max + 1)
+
     # the field at finite points: the same rays recorded where they cross the sphere |M| = 1000 um
     # (about 8 semi-axes), the same 512 x 1024 grid of points on it, three components per point
     near_r = 1000.0
     tpn = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=cfg["n_rays"], observe_radius=near_r)
     rn = rtw.rtw_trace(obj, tpn, stream=stream)
     outn = torch.zeros((ndir, 1, 3), dtype=torch.complex128, device="cuda")
-    for _ in range(3):
-        rtw.rtw_trace(obj, tpn, rn, stream=stream)
-        rtw.rtw_field(rn, dirs, outn, mask)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
-    for e in ev:
-        flush.zero_()
-        e[0].record(stream)
-        rtw.rtw_trace(obj, tpn, rn, stream=stream)
-        e[1].record(stream)
-        rtw.rtw_field(rn, dirs, outn, mask)
-        e[2].record(stream)
-    torch.cuda.synchronize()
-    rtw.rtw_sync_status(stream)
-    tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
-    ts = statistics.median([e[0].elapsed_time(e[2]) for e in ev])
+    tt, ts = timed_trace_field(obj, tpn, rn, outn)
     near = {"radius_um": near_r, "value": units / (ts / 1e3), "unit": UNIT, "ms_per_step": ts, "ms_trace": tt,
             "ms_field": ts - tt, "points_per_s": ndir / (ts / 1e3), "kernel": "trace_kernel_fp64_near"}
     del rn, outn
@@ -388,27 +397,22 @@ def bench_ellipsoid(args, rank, world, local, dist):
     # same number of grid points of the plane through the centre, the same far-field grid
     objs = rtw.Object([rtw.ObjectSpec(**spec, jones=(1.0, 0.0), source=(0.0, 0.0, -1000.0))])
     rs = rtw.rtw_trace(objs, tp, stream=stream)
-    fls = torch.zeros(rs.info()[0], dtype=torch.int32, device="cuda")
-    rtw.rtw_rays_export(rs, 0, 0, rs.info()[0], flags=fls)
-    units_s = int(((fls & 1) != 0).sum().item()) * (p_max + 1)
-    for _ in range(3):
-        rtw.rtw_trace(objs, tp, rs, stream=stream)
-        rtw.rtw_field(rs, dirs, out, mask)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
-    for e in ev:
-        flush.zero_()
-        e[0].record(stream)
-        rtw.rtw_trace(objs, tp, rs, stream=stream)
-        e[1].record(stream)
-        rtw.rtw_field(rs, dirs, out, mask)
-        e[2].record(stream)
-    torch.cuda.synchronize()
-    rtw.rtw_sync_status(stream)
-    tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
-    ts = statistics.median([e[0].elapsed_time(e[2]) for e in ev])
+    units_s = hit_units(rs)
+    tt, ts = timed_trace_field(objs, tp, rs, out)
     point = {"source_um": [0.0, 0.0, -1000.0], "value": units_s / (ts / 1e3), "unit": UNIT, "ms_per_step": ts,
              "ms_trace": tt, "ms_field": ts - tt}
     del rs, objs
+
+    # another smooth convex body: the superellipsoid |u|^4 + |v|^4 + |w|^4 = 1 on the same semi-axes,
+    # turned about all three axes, 4e6 rays over the bounding ellipsoid's silhouette, the same grid
+    obje = rtw.Object([rtw.ObjectSpec(**W.SUPERELLIPSOID, jones=(1.0, 0.0))])
+    re_ = rtw.rtw_trace(obje, tp, stream=stream)
+    units_e = hit_units(re_)
+    tt, ts = timed_trace_field(obje, tp, re_, out)
+    superellipsoid = {"shape_e": W.SUPERELLIPSOID["shape_e"], "value": units_e / (ts / 1e3), "unit": UNIT,
+                      "ms_per_step": ts, "ms_trace": tt, "ms_field": ts - tt, "rays_hit": units_e // (p_max + 1),
+                      "kernel": "trace_kernel_fp64_super"}
+    del re_, obje
 
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
@@ -424,7 +428,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         host_mask.copy_(mask, non_blocking=True)
         torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
-    h2d = 352  # the object table entry uploaded by rtw_trace (sizeof(ObjDev))
+    h2d = 464  # the object table entry uploaded by rtw_trace (sizeof(ObjDev))
     d2h = host_out.numel() * 16 + host_mask.numel()
 
     if rank != 0:
@@ -464,6 +468,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "precision_forms": forms,
         "near_field": near,
         "point_source": point,
+        "superellipsoid": superellipsoid,
     }
     if cpu:
         line["cpu_baseline"] = cpu
@@ -589,7 +594,7 @@ def bench_batch(args, rank, world, local, dist):
         host_mask.copy_(mask, non_blocking=True)
         torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
-    h2d = 352 * n  # the object table (352-byte entries)
+    h2d = 464 * n  # the object table (464-byte entries)
     d2h = host_out.numel() * 16 + host_mask.numel()
     if rank != 0:
         if dist:

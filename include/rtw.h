@@ -91,12 +91,21 @@ extern "C" {
 
 /* Object: ellipsoid of semi-axes (a, b, c) along its body axes, rotated body -> world by the unit
  * quaternion quat = (w, x, y, z) (|quat| = 1 within 1e-9), centred at center.  m_re is the
- * refractive index relative to the host; m_im must be 0 (absorbing objects: RTW_ERR_UNSUPPORTED). */
+ * refractive index relative to the host; m_im must be 0 (absorbing objects: RTW_ERR_UNSUPPORTED).
+ * shape_e: 0 or 1 for the ellipsoid; e > 1 for the superellipsoid |u|^(2e) + |v|^(2e) + |w|^(2e) = 1
+ * with (u, v, w) the body coordinates divided by (a, b, c), a smooth convex body between the
+ * ellipsoid and the box (the Introduction's principle (iii): the wavefront equation needs of the
+ * surface only its normal and curvature matrix at each point, here from the gradient and Hessian
+ * of that function).  A superellipsoid takes a plane wave, rtw_trace with a square grid, RTW_FP64
+ * and observe_radius 0, and rtw_field in RTW_DENSE mode without RTW_FIELD_PO; its ray grid covers
+ * the silhouette of the bounding ellipsoid of semi-axes (a, b, c) 3^((1 - 1/e) / 2), so n_rays
+ * counts the rays inside that silhouette.  Other entry points answer RTW_ERR_UNSUPPORTED. */
 typedef struct {
     double a, b, c;
     double quat[4];
     double center[3];
     double m_re, m_im;
+    double shape_e;
 } rtw_object_desc;
 
 /* Incident wave.  kind RTW_INCIDENT_PLANE: plane wave with direction dir (must be (0, 0, 1)) and
@@ -163,7 +172,8 @@ typedef struct rtw_rays rtw_rays;
  * them: quadric matrix W = R diag(a^-2, b^-2, c^-2) R^T, projected ellipse S (Schur complement of
  * W_zz), k0 = 2 pi / lambda.  *out receives a handle owned by the caller until
  * rtw_destroy_object.  Errors: RTW_ERR_ARG (null, count < 1, a, b, c, lambda <= 0, m <= 0,
- * m == 1, |quat| != 1), RTW_ERR_UNSUPPORTED (m_im != 0 or dir != (0,0,1)), RTW_ERR_CUDA,
+ * m == 1, |quat| != 1, shape_e neither 0 nor >= 1), RTW_ERR_UNSUPPORTED (m_im != 0, dir != (0,0,1),
+ * a superellipsoid with a point source), RTW_ERR_CUDA,
  * RTW_ERR_NOMEM.  Synchronous. */
 int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident* inc, rtw_object** out);
 void rtw_destroy_object(rtw_object* obj);
@@ -218,7 +228,11 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
  * and written.  For rays traced with observe_radius R > 0 the directions u name the points M = R u
  * and field_out is [objects][directions][orders or 1][3] complex128 (E_r, E_theta, E_phi), the field
  * at M for a unit incident wave (the ray through M need not be radial); mode RTW_DENSE only, no PO.
- * mask_out (device, optional): [objects][directions] uint8.  Asynchronous. */
+ * mask_out (device, optional): [objects][directions] uint8.  Asynchronous, except with superellipsoids
+ * among the objects: their ray branches per direction multiply with the order (rounded edges fan
+ * the rays out again at every internal reflection), so the field is summed in slices of ray-grid
+ * rows sized to the hit list, each classified first and its pair count read back (the stream is
+ * synchronised once per slice); RTW_ERR_CAPACITY when a single row does not fit. */
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
               uint8_t* mask_out, void* stream);
 

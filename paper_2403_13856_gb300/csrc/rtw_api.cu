@@ -105,7 +105,13 @@ void fill_objdev(const ObjHost& o, ObjDev& d)
         d.src[i] = o.src_pos[i];
         d.e1[i] = o.e1[i];
         d.e2[i] = o.e2[i];
+        d.inv_a[i] = 1.0 / o.a[i];
+        for (int j = 0; j < 3; ++j) d.Rb[3 * i + j] = o.R[i][j];
     }
+    d.shape_e = o.shape_e;
+    d.bound2 = std::pow(3.0, 1.0 - 1.0 / o.shape_e);
+    const double n2 = 2.0 * o.shape_e;
+    d.shape_n = (n2 == std::floor(n2) && n2 >= 3.0 && n2 <= 32.0) ? (int)n2 : 0;
 }
 
 // ray grid of one object (host arithmetic only)
@@ -181,6 +187,7 @@ GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs)
     g.windowed = !(win[0] == -1 && win[1] == -1 && win[2] == -1 && win[3] == -1);
     const long long ndir = dir_count(dirs);
     g.group = (int)std::max<long long>(1, std::min<long long>(nobj, (1ll << 28) / std::max(1ll, 4 * ndir * np)));
+    for (int oi = 0; oi < nobj; ++oi) g.super_shapes = g.super_shapes || objs[oi].shape_e != 1.0;
     for (int g0 = 0; g0 < nobj; g0 += g.group) {
         long long cells = 0;
         for (int oi = g0; oi < std::min(nobj, g0 + g.group); ++oi) {
@@ -210,7 +217,11 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     // large), up to 2^29 entries; a triangle beyond the list is classified by its own thread
     const unsigned int big_cap =
         (unsigned int)std::min<long long>(std::max<long long>(65536, 2 * g.max_group_cells), 1ll << 29);
-    const unsigned int hit_cap = (unsigned int)std::min<long long>(4 * ndir * np * g.group + (1 << 20), 1ll << 29);
+    // hit list: 4 pairs per direction and order (ellipsoids: one to a few branches each); 32 with
+    // superellipsoids, whose runs are sliced to fit
+    const long long per_dir = g.super_shapes ? 32 : 4;
+    const unsigned int hit_cap =
+        (unsigned int)std::min<long long>(per_dir * ndir * np * g.group + (1 << 20), 1ll << 29);
     size_t off_mask = 0;
     size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir * (size_t)g.group, 256);
     // double tables then their single-precision copies
@@ -275,7 +286,7 @@ int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t 
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
-                   cudaStream_t s)
+                   cudaStream_t s, long long* slice_rows)
 {
     const int np = st.np;
     const long long ndir = d.ndir;
@@ -295,26 +306,82 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
         a.mask = w.mask_words;
         a.status = status;
         a.nfail = nfail;
-        RTW_CUDA(launch_grid_cells(d_objs + g0, gn, np, g.windowed, win, w.cells, s));
-        GridBatch b;
-        b.cells = w.cells;
-        b.nobj = gn;
-        b.total = 0;
-        for (int oi = g0; oi < g0 + gn; ++oi) {
-            const ObjDev& o = h_objs[oi];
-            long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
-            if (g.windowed) {
-                ix0 = win[0] < 0 ? 0 : win[0];
-                ix1 = win[1] > o.nx - 1 ? o.nx - 1 : win[1];
-                iy0 = win[2] < 0 ? 0 : win[2];
-                iy1 = win[3] > o.ny - 1 ? o.ny - 1 : win[3];
+        // cells [ix0, ix1) x [iy0, iy1) of every object of the group, window wv (when windowed)
+        auto batch = [&](bool windowed, const int64_t* wv, GridBatch& b) -> int {
+            RTW_CUDA(launch_grid_cells(d_objs + g0, gn, np, windowed, wv, w.cells, s));
+            b.cells = w.cells;
+            b.nobj = gn;
+            b.total = 0;
+            for (int oi = g0; oi < g0 + gn; ++oi) {
+                const ObjDev& o = h_objs[oi];
+                long long ix0 = 0, ix1 = o.nx - 1, iy0 = 0, iy1 = o.ny - 1;
+                if (windowed) {
+                    ix0 = wv[0] < 0 ? 0 : wv[0];
+                    ix1 = wv[1] > o.nx - 1 ? o.nx - 1 : wv[1];
+                    iy0 = wv[2] < 0 ? 0 : wv[2];
+                    iy1 = wv[3] > o.ny - 1 ? o.ny - 1 : wv[3];
+                }
+                b.total += std::max(0ll, ix1 - ix0) * std::max(0ll, iy1 - iy0) * np;
             }
-            b.total += std::max(0ll, ix1 - ix0) * std::max(0ll, iy1 - iy0) * np;
+            b.ndir = ndir;
+            b.nout = nout;
+            return RTW_OK;
+        };
+        if (!g.super_shapes) {
+            GridBatch b;
+            int rc = batch(g.windowed, win, b);
+            if (rc != RTW_OK) return rc;
+            RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
+                                       classify_block, newton, s));
+        } else {
+            long long rows = 0, cols = 0;
+            for (int oi = g0; oi < g0 + gn; ++oi) {
+                rows = std::max(rows, h_objs[oi].ny - 1);
+                cols = std::max(cols, h_objs[oi].nx - 1);
+            }
+            const long long x0 = g.windowed ? win[0] : 0, x1 = g.windowed ? win[1] : cols;
+            const long long y0 = g.windowed ? std::max<long long>(0, win[2]) : 0;
+            const long long y1 = g.windowed ? std::min<long long>(rows, win[3]) : rows;
+            std::vector<std::pair<long long, long long>> todo;
+            const long long hint = slice_rows ? *slice_rows : 0;
+            if (y1 > y0) {
+                if (hint > 0 && hint < y1 - y0) {
+                    // slices of the hinted height, taken from the stack in increasing row order
+                    for (long long a0 = y0 + (y1 - y0 - 1) / hint * hint; a0 >= y0; a0 -= hint)
+                        todo.emplace_back(a0, std::min(y1, a0 + hint));
+                } else {
+                    todo.emplace_back(y0, y1);
+                }
+            }
+            long long fitted = 0;
+            while (!todo.empty()) {
+                const auto sl = todo.back();
+                todo.pop_back();
+                const int64_t wv[4] = {x0, x1, sl.first, sl.second};
+                GridBatch b;
+                int rc = batch(true, wv, b);
+                if (rc != RTW_OK) return rc;
+                RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
+                                           classify_block, newton, s, kFieldClassify));
+                unsigned int want = 0;
+                RTW_CUDA(cudaMemcpyAsync(&want, w.nhit, sizeof(want), cudaMemcpyDeviceToHost, s));
+                RTW_CUDA(cudaStreamSynchronize(s));
+                if (b.total > 0 && want > w.hit_cap) {
+                    if (sl.second - sl.first <= 1)
+                        return fail(RTW_ERR_CAPACITY, "rtw_field: one row of the ray grid wants %u (triangle, "
+                                    "direction) pairs, more than the %u of the hit list", want, w.hit_cap);
+                    const long long mid = sl.first + (sl.second - sl.first) / 2;
+                    todo.emplace_back(mid, sl.second);
+                    todo.emplace_back(sl.first, mid);
+                    continue;
+                }
+                RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
+                                           classify_block, newton, s, kFieldSum));
+                const long long hgt = sl.second - sl.first;
+                fitted = fitted == 0 ? hgt : std::min(fitted, hgt);
+            }
+            if (slice_rows && fitted > 0) *slice_rows = fitted;
         }
-        b.ndir = ndir;
-        b.nout = nout;
-        RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
-                                   classify_block, newton, s));
         if (mask_out)
             RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir,
                                           d.list ? 2 : 1, d.nt, d.nph, 0.0, 0.0, s, d.lsrc));
@@ -338,6 +405,9 @@ struct rtw_rays {
     ObjDev* d_objs = nullptr;
     size_t d_objs_cap = 0;
     RaysDev st{};
+    // superellipsoid fields: slice height that fitted the hit list, for directions x orders slice_key
+    long long slice_rows = 0;
+    long long slice_key = -1;
     void* block = nullptr;
     size_t block_bytes = 0;
     void* ws = nullptr;
@@ -406,6 +476,13 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
             return fail(RTW_ERR_UNSUPPORTED, "object %d: incident direction must be (0, 0, 1)", i);
         if (w.kind == RTW_INCIDENT_POINT && !std::isfinite(w.source[0] + w.source[1] + w.source[2]))
             return fail(RTW_ERR_ARG, "object %d: source position must be finite", i);
+        const double se = d.shape_e == 0.0 ? 1.0 : d.shape_e;
+        if (!(se >= 1.0) || !std::isfinite(se))
+            return fail(RTW_ERR_ARG, "object %d: shape exponent %g (0 or 1: ellipsoid, > 1: superellipsoid)", i,
+                        d.shape_e);
+        if (se != 1.0 && w.kind != RTW_INCIDENT_PLANE)
+            return fail(RTW_ERR_UNSUPPORTED, "object %d: a superellipsoid takes a plane wave", i);
+        o.shape_e = se;
         o.a[0] = d.a;
         o.a[1] = d.b;
         o.a[2] = d.c;
@@ -438,6 +515,13 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
         o.S[0][1] = o.W[0][1] - o.W[0][2] * o.W[1][2] / o.W[2][2];
         o.S[1][0] = o.S[0][1];
         o.S[1][1] = o.W[1][1] - o.W[1][2] * o.W[1][2] / o.W[2][2];
+        if (se != 1.0) {
+            // the superellipsoid lies inside the ellipsoid of semi-axes a_i 3^((1 - 1/e) / 2) (power-mean
+            // inequality); its silhouette bounds the ray grid
+            const double g2 = std::pow(3.0, 1.0 - 1.0 / se);
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) o.S[r][c] /= g2;
+        }
         o.gc[0] = o.c[0];
         o.gc[1] = o.c[1];
         o.src = w.kind == RTW_INCIDENT_POINT;
@@ -530,9 +614,17 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     if (tp->p_max < 0 || tp->p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace: p_max out of [0, 15]");
     if (tp->precision != RTW_FP64 && tp->precision != RTW_MIXED && tp->precision != RTW_DFLOAT)
         return fail(RTW_ERR_ARG, "rtw_trace: precision %d", tp->precision);
-    for (int i = 0; i < obj->count; ++i)
+    bool super_shapes = false;
+    for (int i = 0; i < obj->count; ++i) {
         if (obj->h[(size_t)i].src && (tp->grid != RTW_GRID_SQUARE || tp->precision != RTW_FP64))
             return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: a point source takes a square grid in double precision");
+        if (obj->h[(size_t)i].shape_e != 1.0) {
+            if (tp->grid != RTW_GRID_SQUARE || tp->precision != RTW_FP64 || tp->observe_radius != 0.0)
+                return fail(RTW_ERR_UNSUPPORTED,
+                            "rtw_trace: a superellipsoid takes a square grid, double precision and the far field");
+            super_shapes = true;
+        }
+    }
     if (!(tp->observe_radius >= 0.0) || !std::isfinite(tp->observe_radius))
         return fail(RTW_ERR_ARG, "rtw_trace: observe_radius must be finite and >= 0");
     if (tp->observe_radius > 0.0) {
@@ -612,6 +704,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
         r->d_objs_cap = objs.size();
     }
     *inout = r;
+    if (r->R != R || r->np != np || r->grid != tp->grid) r->slice_rows = 0;  // another ray grid
     r->np = np;
     r->precision = tp->precision;
     r->grid = tp->grid;
@@ -636,7 +729,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     r->st.sl = sf ? (float4*)(b + off[7] + n * 16) : nullptr;
     RTW_CUDA(cudaMemcpyAsync(r->d_objs, r->objs.data(), sizeof(ObjDev) * objs.size(), cudaMemcpyHostToDevice, s));
     unsigned int* status = status_word(r->device);
-    RTW_CUDA(rtw::launch_trace(r->d_objs, r->nobj, r->st, tp->p_max, aux, status, s));
+    RTW_CUDA(rtw::launch_trace(r->d_objs, r->nobj, r->st, tp->p_max, aux, status, s, super_shapes));
     return RTW_OK;
 }
 
@@ -676,6 +769,7 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
     if (index < 0 || index >= obj->count) return fail(RTW_ERR_ARG, "rtw_trace_points: index out of range");
     if (p_max < 0 || p_max >= rtw::kMaxOrders) return fail(RTW_ERR_ARG, "rtw_trace_points: p_max out of range");
     if (n < 0) return fail(RTW_ERR_ARG, "rtw_trace_points: n < 0");
+    if (obj->h[(size_t)index].shape_e != 1.0) return fail(RTW_ERR_UNSUPPORTED, "rtw_trace_points: ellipsoids only");
     cudaStream_t s = (cudaStream_t)stream;
     ObjDev d;
     fill_objdev(obj->h[(size_t)index], d);
@@ -704,6 +798,10 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
     if (po && newton) return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO and RTW_NEWTON exclude each other");
     if (rays->st.near_r > 0.0 && (newton || po))
         return fail(RTW_ERR_ARG, "rtw_field: rays traced to a finite radius take the dense mode without PO");
+    if (newton || po)
+        for (int i = 0; i < rays->nobj; ++i)
+            if (rays->objs[(size_t)i].shape_e != 1.0)
+                return fail(RTW_ERR_UNSUPPORTED, "rtw_field: a superellipsoid takes the dense mode without PO");
     const bool folds = po || newton == 2;
     const int nout = per_order ? rays->np : 1;
     long long ndir = 0;
@@ -744,9 +842,16 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         rtw::DirSet d;
         int rc = rtw::host::dirs_prepare(dirs, w, &d, s);
         if (rc != RTW_OK) return rc;
+        // the slice height found for these directions and this window is kept for the next call
+        const int64_t* cw = dirs->cell_window;
+        const long long key = (ndir * 64 + rays->np) ^ (cw[0] * 7919 + cw[1] * 104729 + cw[2] * 1299709 + cw[3] * 15485863);
+        if (rays->slice_key != key) {
+            rays->slice_key = key;
+            rays->slice_rows = 0;
+        }
         return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, d,
                                          per_order, (double*)field_out, mask_out, w, 0, newton, status,
-                                         newton_counter(rays->device), s);
+                                         newton_counter(rays->device), s, &rays->slice_rows);
     }
     // fan: workspace of mask words, PO windows and scratch
     const long long nfan = rays->objs[0].nx;

@@ -182,6 +182,8 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
         double h = 0.0, fw = 0.0;
         long long nx = 0, ny = 0;
         if (obj->h[(size_t)i].src) return fail(RTW_ERR_UNSUPPORTED, "rtw_far_field_batch: plane waves only");
+        if (obj->h[(size_t)i].shape_e != 1.0)
+            return fail(RTW_ERR_UNSUPPORTED, "rtw_far_field_batch: ellipsoids only (superellipsoids: rtw_trace)");
         int rc = rtw::host::grid_of(obj->h[(size_t)i], &tp, &h, &nx, &ny, &fw);
         if (rc != RTW_OK) return rc;
         ObjDev& d = objs[(size_t)i];

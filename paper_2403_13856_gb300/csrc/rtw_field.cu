@@ -1179,22 +1179,24 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
-                              int newton, cudaStream_t s)
+                              int newton, cudaStream_t s, int stage)
 {
     if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
     const int cb = classify_block > 0 ? classify_block : bs;
-    cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(nhit, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
     HitArgs h{hit_tri, hit_dir, nhit, hit_cap};
-    field_grid_kernel<<<(unsigned)((b.total + cb - 1) / cb), cb, 0, s>>>(a, b, d, big, nbig, big_cap, h);
     // fixed grids walk the lists: 32 blocks per SM for the large triangles, 16 for the hits
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    field_grid_big_kernel<<<(unsigned)(32 * sms), 32 * kBigWarps, 0, s>>>(a, b, d, big, nbig, big_cap, h);
-    field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h, newton);
+    if (stage != 2) {
+        cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(nhit, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        field_grid_kernel<<<(unsigned)((b.total + cb - 1) / cb), cb, 0, s>>>(a, b, d, big, nbig, big_cap, h);
+        field_grid_big_kernel<<<(unsigned)(32 * sms), 32 * kBigWarps, 0, s>>>(a, b, d, big, nbig, big_cap, h);
+    }
+    if (stage != 1) field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h, newton);
     return cudaGetLastError();
 }
 

@@ -16,9 +16,10 @@
 namespace rtw {
 namespace host {
 
-// One ellipsoid and its incident wave, in double precision: semi-axes, rotation (body to lab),
-// centre, index, wavelength, Jones vector, quadric matrix W = R diag(1/a^2) R^T, the projected
-// ellipse S (x^T S x <= 1 on z = const) and its inverse, smallest and largest semi-axis.
+// One ellipsoid (or superellipsoid) and its incident wave, in double precision: semi-axes,
+// rotation (body to lab), centre, index, wavelength, Jones vector, quadric matrix
+// W = R diag(1/a^2) R^T, the projected ellipse S (x^T S x <= 1 on z = const; of the bounding
+// ellipsoid for a superellipsoid) and its inverse, smallest and largest semi-axis.
 struct ObjHost {
     double a[3];
     double R[3][3];
@@ -32,6 +33,7 @@ struct ObjHost {
     double gc[2];                 // centre of the ray grid (plane wave: c_x, c_y)
     int src;                      // 1: point source
     double src_pos[3], e1[3], e2[3];
+    double shape_e;               // superellipsoid exponent (1: the ellipsoid)
 };
 
 // sets the calling thread's last-error message and returns code
@@ -60,6 +62,7 @@ struct GridPlan {
     int group = 1;
     long long max_group_cells = 0;  // cells x orders of the largest group
     bool windowed = false;
+    bool super_shapes = false;      // the objects include superellipsoids: sliced runs (grid_field_run)
 };
 GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs);
 
@@ -94,10 +97,16 @@ int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t 
 // are the same table on the host and the device.  Adds into out, which the caller cleared:
 // [objects][directions][nout][4] doubles.  mask_out (may be null): [objects][directions] bytes.
 // newton = 1 replaces every interpolated hit by the exact ray found by Newton steps.
+// With superellipsoids (g.super_shapes) the number of ray branches per direction grows quickly with
+// the order, so each group is run in slices of ray-grid rows: a slice is classified, the count of
+// (triangle, direction) pairs it wants is read back (the stream is synchronised), and a slice that
+// does not fit the hit list is halved before any of its hits is summed.  slice_rows (optional, in
+// and out): the slice height to start from (0: the whole grid); receives the smallest height that
+// fitted, so that the next run on the same directions starts from slices that fit.
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
-                   cudaStream_t s);
+                   cudaStream_t s, long long* slice_rows = nullptr);
 
 // per-object feature table of the learned proposal
 void object_features(const ObjHost& o, ObjFeat& f);

@@ -45,9 +45,15 @@ struct ObjDev {
     double src[3];          // point source (src_mode 1): rays leave it through c + x e1 + y e2
     double e1[3], e2[3];
     int src_mode;
-    int pad1;
+    int shape_n;            // 2 shape_e when that is an integer in [3, 32] (powers by products), else 0
+    // superellipsoid sum_i |u_i|^(2e) = 1, u_i = inv_a[i] (Rb^T (x - c))_i, for shape_e > 1 (1: the
+    // quadric W above); the body lies inside the ellipsoid sum_i u_i^2 = bound2 = 3^(1 - 1/e)
+    double Rb[9];           // body -> world rotation, row-major (columns are the body axes)
+    double inv_a[3];
+    double shape_e;
+    double bound2;
 };
-static_assert(sizeof(ObjDev) == 352, "object table entries are 352 bytes");
+static_assert(sizeof(ObjDev) == 464, "object table entries are 464 bytes");
 
 // rays per work item of the persistent batched trace
 constexpr int kRaysPerItem = 256;

@@ -69,9 +69,9 @@ struct FieldArgs {
 // message returned by rtw_last_error() on the calling thread
 void set_last_error(const char* msg);
 
-// trace
+// trace; super_shapes: the object set holds superellipsoids (double precision, far field)
 cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, bool aux, unsigned int* status,
-                         cudaStream_t s);
+                         cudaStream_t s, bool super_shapes = false);
 // persistent batched trace over work items; variant 1..kTraceVariants picks the block size and
 // register cap: 1 (64, 1), 2 (128, 1), 3 (256, 1), 4 (128, 3 CTAs/SM), 5 (256, 2 CTAs/SM)
 constexpr int kTraceVariants = 5;
@@ -87,7 +87,11 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s);
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
-                              int newton, cudaStream_t s);
+                              int newton, cudaStream_t s, int stage = 0);
+// stage of launch_field_grid: 0 classifies the triangles and sums their hits; 1 only classifies
+// (*nhit then holds the number of pairs the batch wants, which may exceed hit_cap); 2 sums the hits
+// of a stage-1 run that fitted
+enum { kFieldAll = 0, kFieldClassify = 1, kFieldSum = 2 };
 // bins a direction list: unit vectors, bin of every direction, bin offsets and bin lists;
 // count and cursor hold nt nph + 1 ints each
 cudaError_t launch_bin_dirs(const double* list, long long n, int nt, int nph, double* ldir, float4* ldir_f,

@@ -170,6 +170,7 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
     std::vector<rtw::ObjFeat> of((size_t)obj->count);
     for (int i = 0; i < obj->count; ++i) {
         if (obj->h[(size_t)i].src) return fail(RTW_ERR_UNSUPPORTED, "rtw_field_learned: plane waves only");
+        if (obj->h[(size_t)i].shape_e != 1.0) return fail(RTW_ERR_UNSUPPORTED, "rtw_field_learned: ellipsoids only");
         rtw::host::fill_objdev(obj->h[(size_t)i], od[(size_t)i]);
         od[(size_t)i].grid = rtw::kGridSquare;
         rtw::host::object_features(obj->h[(size_t)i], of[(size_t)i]);

@@ -239,6 +239,7 @@ int rtw_mlp_samples(const rtw_object* obj, const double* uv, const int32_t* obj_
     std::vector<rtw::ObjFeat> of((size_t)obj->count);
     for (int i = 0; i < obj->count; ++i) {
         if (obj->h[(size_t)i].src) return fail(RTW_ERR_UNSUPPORTED, "rtw_mlp_samples: plane waves only");
+        if (obj->h[(size_t)i].shape_e != 1.0) return fail(RTW_ERR_UNSUPPORTED, "rtw_mlp_samples: ellipsoids only");
         rtw::host::fill_objdev(obj->h[(size_t)i], od[(size_t)i]);
         od[(size_t)i].grid = rtw::kGridSquare;
         rtw::host::object_features(obj->h[(size_t)i], of[(size_t)i]);

@@ -100,6 +100,7 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     if (d->m_im != 0.0) return set_error(RTW_ERR_UNSUPPORTED, "absorbing objects");
     if (!(w->wavelength_um > 0.0)) return set_error(RTW_ERR_ARG, "wavelength must be positive");
     if (w->kind != RTW_INCIDENT_PLANE) return set_error(RTW_ERR_UNSUPPORTED, "plane waves only");
+    if (d->shape_e != 0.0 && d->shape_e != 1.0) return set_error(RTW_ERR_UNSUPPORTED, "ellipsoids only");
     if (w->dir[0] != 0.0 || w->dir[1] != 0.0 || w->dir[2] != 1.0)
         return set_error(RTW_ERR_UNSUPPORTED, "incident direction must be (0, 0, 1)");
 

@@ -104,24 +104,32 @@ __device__ __forceinline__ int find_object(const ObjDev* objs, int nobj, long lo
 }
 
 // traces global ray j of object o and clears the flags of the orders it does not reach
-template <typename T, bool kNear = false>
+// kSuper: the object set holds superellipsoids; each object takes the path of its own shape.
+template <typename T, bool kNear = false, bool kSuper = false>
 __device__ __forceinline__ void trace_one(const ObjDev* o, const RaysDev& st, long long j, int pmax, int aux)
 {
     StateSink<kNear> sink{o, st, j, aux != 0, 0u};
     double x, y;
-    if (ray_origin(*o, j - o->ray_offset, x, y)) trace_ray<T, false>(*o, x, y, pmax, sink);
+    if (ray_origin(*o, j - o->ray_offset, x, y)) {
+        if constexpr (kSuper) {
+            if (o->shape_e != 1.0) trace_ray<double, false, StateSink<kNear>, true>(*o, x, y, pmax, sink);
+            else trace_ray<double, false>(*o, x, y, pmax, sink);
+        } else {
+            trace_ray<T, false>(*o, x, y, pmax, sink);
+        }
+    }
     for (int p = 0; p < st.np; ++p)
         if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
 }
 
-template <typename T, bool kNear = false>
+template <typename T, bool kNear = false, bool kSuper = false>
 __device__ __forceinline__ void trace_kernel_body(const ObjDev* __restrict__ objs, int nobj, RaysDev st, int pmax,
                                                   int aux)
 {
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (j >= st.R) return;
     const ObjDev* o = objs + (nobj > 1 ? find_object(objs, nobj, j) : 0);
-    trace_one<T, kNear>(o, st, j, pmax, aux);
+    trace_one<T, kNear, kSuper>(o, st, j, pmax, aux);
 }
 
 // object owning work item `it` (largest i with item_first <= it)
@@ -179,6 +187,13 @@ __global__ void __launch_bounds__(128) trace_kernel_fp64_near(const ObjDev* __re
                                                               RaysDev st, int pmax, int aux)
 {
     trace_kernel_body<double, true>(objs, nobj, st, pmax, aux);
+}
+
+// object sets with superellipsoids (every step in double precision)
+__global__ void __launch_bounds__(128) trace_kernel_fp64_super(const ObjDev* __restrict__ objs, int nobj,
+                                                               RaysDev st, int pmax, int aux)
+{
+    trace_kernel_body<double, false, true>(objs, nobj, st, pmax, aux);
 }
 
 // geometry, Fresnel and curvature in single precision; intersection points (polished by a
@@ -241,13 +256,15 @@ __global__ void export_kernel(RaysDev st, int order, long long first, long long 
 }  // namespace
 
 cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, bool aux, unsigned int* status,
-                         cudaStream_t s)
+                         cudaStream_t s, bool super_shapes)
 {
     (void)status;
     if (st.R == 0) return cudaSuccess;
     const int bs = 128;
     const long long nb = (st.R + bs - 1) / bs;
-    if (st.near_r > 0.0)
+    if (super_shapes)
+        trace_kernel_fp64_super<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    else if (st.near_r > 0.0)
         trace_kernel_fp64_near<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     else if (st.precision == 1)
         trace_kernel_mixed<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);

@@ -227,6 +227,145 @@ __device__ __forceinline__ double chord_to_surface(const ObjDev& o, const T* Wt,
     return d;
 }
 
+// ---- superellipsoid F(x) = sum_i |u_i|^(2e) = 1 (e > 1), u = diag(1/a) Rb^T (x - c) ----
+// F is convex, so a line meets the surface at most twice, and phi(t) = F(r + t k) - 1 is convex
+// along every line: Newton from a point beyond a root on the side where phi >= 0 moves
+// monotonically to that root.  The brackets are the body box |u_i| <= 1 and the bounding
+// ellipsoid sum u_i^2 = bound2, both of which contain the body (phi >= 0 on them).
+
+// body coordinates of r and body rates of the direction k
+__device__ __forceinline__ void super_line(const ObjDev& o, const double r[3], const double k[3], double u[3],
+                                           double kap[3])
+{
+    const double dx = r[0] - o.c[0], dy = r[1] - o.c[1], dz = r[2] - o.c[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        u[i] = (o.Rb[i] * dx + o.Rb[3 + i] * dy + o.Rb[6 + i] * dz) * o.inv_a[i];
+        kap[i] = (o.Rb[i] * k[0] + o.Rb[3 + i] * k[1] + o.Rb[6 + i] * k[2]) * o.inv_a[i];
+    }
+}
+
+// |v|^(2e-2) for v >= 0 (0 at v = 0 for e > 1): n - 2 products when 2e is an integer n, else pow
+__device__ __forceinline__ double super_pow(const ObjDev& o, double av)
+{
+    const int n = o.shape_n;
+    if (n > 0) {
+        double r = 1.0;
+        for (int i = 2; i < n; ++i) r *= av;
+        return r;
+    }
+    return pow(av, 2.0 * o.shape_e - 2.0);
+}
+
+// phi(t) and phi'(t) = 2e sum |v_i|^(2e-2) v_i kappa_i, v = u + t kappa
+__device__ __forceinline__ double super_phi(const ObjDev& o, const double u[3], const double kap[3], double t,
+                                            double& dphi)
+{
+    const double e2 = 2.0 * o.shape_e;
+    double f = -1.0, df = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double v = fma(t, kap[i], u[i]), av = fabs(v);
+        const double pw = super_pow(o, av);
+        f = fma(pw * av, av, f);
+        df = fma(pw * v, kap[i], df);
+    }
+    dphi = e2 * df;
+    return f;
+}
+
+// parameters where the line u + t kappa crosses the bounding ellipsoid sum u_i^2 = bound2
+__device__ __forceinline__ bool super_bound(const ObjDev& o, const double u[3], const double kap[3], double& t_in,
+                                            double& t_out)
+{
+    const double A = kap[0] * kap[0] + kap[1] * kap[1] + kap[2] * kap[2];
+    const double B = u[0] * kap[0] + u[1] * kap[1] + u[2] * kap[2];
+    const double C = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] - o.bound2;
+    const double disc = B * B - A * C;
+    if (!(disc > 0.0)) return false;
+    const double sq = sqrt(disc);
+    t_in = (-B - sq) / A;
+    t_out = (-B + sq) / A;
+    return true;
+}
+
+// entry of the ray r0 + t k into the body: Newton from the entry of the bracket (box and bounding
+// ellipsoid), where phi >= 0 and decreasing.  A point past the minimum of phi (phi' >= 0) with
+// phi still positive, or past the bracket, means the line misses: a root would lie before it.
+__device__ __forceinline__ bool super_entry(const ObjDev& o, const double r0[3], const double k[3], double& t_hit)
+{
+    double u[3], kap[3];
+    super_line(o, r0, k, u, kap);
+    double tin, tout;
+    if (!super_bound(o, u, kap, tin, tout)) return false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (kap[i] == 0.0) {
+            if (!(fabs(u[i]) < 1.0)) return false;
+        } else {
+            const double ta = (-1.0 - u[i]) / kap[i], tb = (1.0 - u[i]) / kap[i];
+            tin = fmax(tin, fmin(ta, tb));
+            tout = fmin(tout, fmax(ta, tb));
+        }
+    }
+    if (!(tin < tout)) return false;
+    double t = tin;
+    for (int it = 0; it < 96; ++it) {
+        double df;
+        const double f = super_phi(o, u, kap, t, df);
+        if (!(f > 0.0)) break;
+        if (!(df < 0.0)) return false;
+        const double step = -f / df;
+        t += step;
+        if (t > tout) return false;
+        if (step <= 4e-16 * fabs(t)) break;
+    }
+    t_hit = t;
+    return true;
+}
+
+// chord from surface point r along the inward direction k: Newton from the nearer exit of the
+// bracket, where phi >= 0 and increasing, down to the positive root
+__device__ __forceinline__ double super_chord(const ObjDev& o, const double r[3], const double k[3])
+{
+    double u[3], kap[3];
+    super_line(o, r, k, u, kap);
+    double tin, t;
+    if (!super_bound(o, u, kap, tin, t)) return 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        if (kap[i] != 0.0) t = fmin(t, (copysign(1.0, kap[i]) - u[i]) / kap[i]);
+    if (!(t > 0.0)) return 0.0;
+    for (int it = 0; it < 96; ++it) {
+        double df;
+        const double f = super_phi(o, u, kap, t, df);
+        if (!(f > 0.0) || !(df > 0.0)) break;
+        const double step = f / df;
+        t -= step;
+        if (step <= 4e-16 * t) break;
+    }
+    return t;
+}
+
+// g = grad F / 2 at surface point r (world frame) and the body-diagonal half Hessian
+// hb_i = e (2e - 1) |u_i|^(2e-2) / a_i^2: the curvature form is sigma_a^T diag(hb) sigma_b / |g|
+// with sigma = Rb^T s (body components of the surface vectors)
+__device__ __forceinline__ void super_grad(const ObjDev& o, const double r[3], double g[3], double hb[3])
+{
+    const double dx = r[0] - o.c[0], dy = r[1] - o.c[1], dz = r[2] - o.c[2];
+    const double e = o.shape_e;
+    double gb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double ui = (o.Rb[i] * dx + o.Rb[3 + i] * dy + o.Rb[6 + i] * dz) * o.inv_a[i];
+        const double pw = super_pow(o, fabs(ui));
+        gb[i] = e * pw * ui * o.inv_a[i];
+        hb[i] = e * (2.0 * e - 1.0) * pw * o.inv_a[i] * o.inv_a[i];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g[j] = o.Rb[3 * j] * gb[0] + o.Rb[3 * j + 1] * gb[1] + o.Rb[3 * j + 2] * gb[2];
+}
+
 // A single-precision exit direction is unit only to 6e-8; the far-field phase s.r_exit and the
 // stored direction take it normalised in double precision.
 __device__ __forceinline__ void normalize_exit(ExitWave& w)
@@ -240,10 +379,12 @@ __device__ __forceinline__ void normalize_exit(ExitWave& w)
 // Traces the incident ray at impact point (x, y) for orders 0..pmax; sink.emit(p, ExitWave) is
 // called for every order that leaves the object.  T is the working precision of directions,
 // bases, curvature, Fresnel and Jones arithmetic; positions and the optical path are double.
-// kJ: also carry the transfer matrix T of transverse offsets.
-template <typename T, bool kJ, class Sink>
+// kJ: also carry the transfer matrix T of transverse offsets.  kSuper: the object is a
+// superellipsoid (double precision only): entry, chords, normal and curvature come from F above.
+template <typename T, bool kJ, class Sink, bool kSuper = false>
 __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& sink)
 {
+    static_assert(!kSuper || std::is_same<T, double>::value, "superellipsoids are traced in double precision");
     const T W[6] = {(T)o.W[0], (T)o.W[1], (T)o.W[2], (T)o.W[3], (T)o.W[4], (T)o.W[5]};
     // entry point of the incident ray (plane wave along +z), started below the object
     double r[3] = {x, y, o.zstart};
@@ -256,7 +397,13 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
     int sT = -1;
     T pdet = T(1), cosprod = T(1);
     double path;
-    if (!o.src_mode) {
+    if constexpr (kSuper) {
+        const double kz[3] = {0.0, 0.0, 1.0};
+        double t;
+        if (!super_entry(o, r, kz, t)) return;
+        r[2] += t;
+        path = r[2];
+    } else if (!o.src_mode) {
         const T kz[3] = {T(0), T(0), T(1)};
         bool ok;
         const double t = chord_to_surface<T>(o, W, r, kz, T(-1), &ok);
@@ -334,13 +481,20 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
     const T ik_host = T(1) / k0, ik_obj = T(1) / (k0 * mo), inv_mo = T(1) / mo;
     // in double precision the gradient at the next surface point is carried forward:
     // W (r + d k - c) = W (r - c) + d W k, with W k from the chord
-    constexpr bool kCarryGrad = sizeof(T) == sizeof(double);
+    constexpr bool kCarryGrad = sizeof(T) == sizeof(double) && !kSuper;
     T gnext[3] = {T(0), T(0), T(0)};
     for (int q = 1; q <= pmax + 1; ++q) {
         const T n_out = (q == 1) ? mo : T(1);
         // outward normal n = W (r - c) / |W (r - c)|
         T gx, gy, gz;
-        if (kCarryGrad && q > 1) {
+        T hb[3] = {T(0), T(0), T(0)};
+        if constexpr (kSuper) {
+            double gs[3];
+            super_grad(o, r, gs, hb);
+            gx = gs[0];
+            gy = gs[1];
+            gz = gs[2];
+        } else if (kCarryGrad && q > 1) {
             gx = gnext[0];
             gy = gnext[1];
             gz = gnext[2];
@@ -378,12 +532,29 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         }
         // surface curvature matrix in (s1, s2) = (e_perp, n x e_perp): C_ab = s_a^T W s_b / |grad|
         const T s2x = ny * ez - nz * ey, s2y = nz * ex - nx * ez, s2z = nx * ey - ny * ex;
-        T wex, wey, wez, wsx, wsy, wsz;
-        symvT(W, ex, ey, ez, wex, wey, wez);
-        symvT(W, s2x, s2y, s2z, wsx, wsy, wsz);
-        const T C11 = (ex * wex + ey * wey + ez * wez) * inv_gn;
-        const T C12 = (ex * wsx + ey * wsy + ez * wsz) * inv_gn;
-        const T C22 = (s2x * wsx + s2y * wsy + s2z * wsz) * inv_gn;
+        T C11, C12, C22;
+        if constexpr (kSuper) {
+            // C_ab = sigma_a^T diag(hb) sigma_b / |g|, sigma = Rb^T s
+            C11 = C12 = C22 = T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T p1 = o.Rb[i] * ex + o.Rb[3 + i] * ey + o.Rb[6 + i] * ez;
+                const T p2 = o.Rb[i] * s2x + o.Rb[3 + i] * s2y + o.Rb[6 + i] * s2z;
+                C11 += hb[i] * p1 * p1;
+                C12 += hb[i] * p1 * p2;
+                C22 += hb[i] * p2 * p2;
+            }
+            C11 *= inv_gn;
+            C12 *= inv_gn;
+            C22 *= inv_gn;
+        } else {
+            T wex, wey, wez, wsx, wsy, wsz;
+            symvT(W, ex, ey, ez, wex, wey, wez);
+            symvT(W, s2x, s2y, s2z, wsx, wsy, wsz);
+            C11 = (ex * wex + ey * wey + ez * wez) * inv_gn;
+            C12 = (ex * wsx + ey * wsy + ez * wsz) * inv_gn;
+            C22 = (s2x * wsx + s2y * wsy + s2z * wsz) * inv_gn;
+        }
         // Eq. (SnellVec): common tangential wave vector
         const T ki = k0 * n_in, kt = k0 * n_out;
         const T kin = ki * ci;
@@ -520,11 +691,16 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         a0 = ex; a1 = ey; a2 = ez;
         if (q == pmax + 1) break;
         // chord to the next surface point along the inward direction
-        bool ok;
         const T kk[3] = {k0v, k1v, k2v};
-        const T wg[3] = {gx, gy, gz};
         T wk[3];
-        const double dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok, wg, wk);
+        double dd;
+        if constexpr (kSuper) {
+            dd = super_chord(o, r, kk);
+        } else {
+            bool ok;
+            const T wg[3] = {gx, gy, gz};
+            dd = chord_to_surface<T>(o, W, r, kk, T(1), &ok, wg, wk);
+        }
         if (!(dd > 0.0)) return;
         const T d = (T)dd;
         if (kCarryGrad) {

@@ -35,7 +35,7 @@ class RTWError(RuntimeError):
 class rtw_object_desc(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double),
                 ("quat", ctypes.c_double * 4), ("center", ctypes.c_double * 3),
-                ("m_re", ctypes.c_double), ("m_im", ctypes.c_double)]
+                ("m_re", ctypes.c_double), ("m_im", ctypes.c_double), ("shape_e", ctypes.c_double)]
 
 
 class rtw_incident(ctypes.Structure):
@@ -142,6 +142,7 @@ class ObjectSpec:
     wavelength: float = 0.6328
     jones: Sequence[complex] = (1.0, 0.0)
     source: Optional[Sequence[float]] = None  # point source position (um), else a plane wave along +z
+    shape_e: float = 1.0  # superellipsoid exponent e >= 1 (sum |u_i|^(2e) = 1); 1: the ellipsoid
 
 
 class Object:
@@ -157,6 +158,7 @@ class Object:
             d.quat[:] = list(s.quat)
             d.center[:] = list(s.center)
             d.m_re, d.m_im = s.m, 0.0
+            d.shape_e = s.shape_e
             w = incs[k]
             w.wavelength_um = s.wavelength
             w.dir[:] = [0.0, 0.0, 1.0]

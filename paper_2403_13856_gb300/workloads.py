@@ -28,6 +28,18 @@ SPHERE10_FAN = dict(n_rays=10_000, p_max=3, n_dirs=1801, alpha0=0.0, dalpha=math
 ELLIPSOID = dict(a=120.0, b=100.0, c=80.0, quat=quat_about_x(20.0), m=WATER, wavelength=HE_NE)
 ELLIPSOID_GRID = dict(n_rays=4_000_000, p_max=5, n_theta=512, n_phi=1024)
 
+
+def unit_quat(w: float, x: float, y: float, z: float):
+    n = math.sqrt(w * w + x * x + y * y + z * z)
+    return (w / n, x / n, y / n, z / n)
+
+
+# Superellipsoid |u|^4 + |v|^4 + |w|^4 = 1 (e = 2) on the drop's semi-axes (120, 100, 80) um,
+# turned about all three axes; the same grid sizes as the ellipsoid (the ray count is taken
+# inside the silhouette of the bounding ellipsoid, 3^(1/4) times the semi-axes).
+SUPERELLIPSOID = dict(a=120.0, b=100.0, c=80.0, quat=unit_quat(0.9, 0.25, -0.3, 0.15), m=WATER,
+                      wavelength=HE_NE, shape_e=2.0)
+
 # Table 1 of the paper: spheres of radius 50 and 500 um, order p = 2, perpendicular polarisation.
 TABLE1_SPHERES = (50.0, 500.0)
 
