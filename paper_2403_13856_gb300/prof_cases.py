@@ -4,6 +4,7 @@
     python -m paper_2403_13856_gb300.prof_cases batch [--objects N]
     python -m paper_2403_13856_gb300.prof_cases learned [--objects N]
     python -m paper_2403_13856_gb300.prof_cases ellipsoid [--rays N]
+    python -m paper_2403_13856_gb300.prof_cases superellipsoid [--rays N] [--shape-e E]
 
 Each case builds its inputs (seeded), runs the launch sequence `--reps` times (default 3) after
 one warm-up and prints the CUDA-event time of the last repetition.  Sizes default to cases that
@@ -32,11 +33,12 @@ def _timed(torch, fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid"])
+    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid", "superellipsoid"])
     ap.add_argument("--rows", type=int, default=1 << 22)
     ap.add_argument("--objects", type=int, default=64)
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--shape-e", type=float, default=2.0, help="superellipsoid exponent e")
     ap.add_argument("--mixed", action="store_true", help="ellipsoid / batch: mixed-precision trace")
     ap.add_argument("--dfloat", action="store_true", help="ellipsoid / batch: double-float trace")
     a = ap.parse_args()
@@ -80,6 +82,8 @@ def main():
         print(f"learned objects={a.objects}: {ms:.3f} ms")
     else:
         spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
+        if a.case == "superellipsoid":
+            spec = dict(W.SUPERELLIPSOID, shape_e=a.shape_e)
         obj = rtw.Object([rtw.ObjectSpec(**spec)])
         tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=a.rays,
                               precision=prec)
@@ -92,7 +96,7 @@ def main():
 
         ms = _timed(torch, step, a.reps)
         mt = _timed(torch, lambda: rtw.rtw_trace(obj, tp, rays), a.reps)
-        print(f"ellipsoid rays={a.rays} {pname}: trace + field {ms:.3f} ms, trace {mt:.3f} ms")
+        print(f"{a.case} rays={a.rays} {pname}: trace + field {ms:.3f} ms, trace {mt:.3f} ms")
     rtw.rtw_sync_status()
 
 
