@@ -181,3 +181,77 @@ def test_super_arguments(rtw, oracle_mod):
     outb = torch.zeros((1, 8 * 16, 1, 2), dtype=torch.complex128, device="cuda")
     with pytest.raises(rtw.RTWError):  # the batched path takes ellipsoids
         rtw.rtw_far_field_batch(g, rtw.batch_params(np.array([1000]), p_max=1), rtw.dirs_grid(8, 16), outb)
+
+
+def test_super_full_size_windows(rtw, oracle_mod):
+    """The full-size superellipsoid workload (4e6 grid rays, 512 x 1024 directions, orders 0..5):
+    field of sampled 40 x 40-cell windows of the ray grid against the oracle on the same windows."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.ELLIPSOID_GRID
+    sp = dict(W.SUPERELLIPSOID, jones=(1.0, 0.0))
+    g = rtw.Object([rtw.ObjectSpec(**sp)])
+    tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=cfg["n_rays"])
+    rays = rtw.rtw_trace(g, tp)
+    h, nx, ny = g.grid(0, tp)
+    o = oracle_mod.Object(**sp)
+    nt, nph = cfg["n_theta"], cfg["n_phi"]
+    out = torch.zeros((nt * nph, cfg["p_max"] + 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
+    for fx, fy in [(0.5, 0.5), (0.3, 0.62), (0.75, 0.3)]:
+        ix0, iy0 = int(fx * nx), int(fy * ny)
+        win = [ix0, ix0 + 40, iy0, iy0 + 40]
+        rtw.rtw_field(rays, rtw.dirs_grid(nt, nph, win), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+        rtw.rtw_sync_status()
+        ref, rm, hits, _ = o.field_grid(cfg["p_max"], nt, nph, n_target=cfg["n_rays"], window=win)
+        ref = oracle_mod.complex_field(ref)
+        assert hits > 0
+        assert np.array_equal(mask.cpu().numpy(), rm)
+        scale = np.abs(ref).max()
+        err = np.abs(out.cpu().numpy() - ref).max()
+        print(f"window {win}: {hits} hits, max |dF| / max |F| = {err / scale:.2e}")
+        assert scale > 0 and err <= 1e-6 * scale
+
+
+def test_super_full_size_sampled_rays(rtw, oracle_mod):
+    """Full-size superellipsoid trace: 2000 sampled rays of the 4e6-ray grid, orders 0..5, against
+    the oracle's rays at the same grid points."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.ELLIPSOID_GRID
+    sp = dict(W.SUPERELLIPSOID, jones=(1.0, 0.0))
+    p_max = cfg["p_max"]
+    g = rtw.Object([rtw.ObjectSpec(**sp)])
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=cfg["n_rays"]))
+    R, npo, _ = rays.info()
+    o = oracle_mod.Object(**sp)
+    h, nx, ny, xc, yc = o.square_grid(n_target=cfg["n_rays"])
+    assert R == nx * ny
+    idx = np.sort(np.random.default_rng(8).choice(R, size=2000, replace=False))
+    x = xc + (idx % nx + 0.5 - nx // 2) * h
+    y = yc + (idx // nx + 0.5 - ny // 2) * h
+    ref = o.trace_rays(np.stack([x, y], 1), p_max)
+    checked = 0
+    for p in range(npo):
+        s = torch.zeros((R, 3), dtype=torch.float64, device="cuda")
+        F = torch.zeros((R, 6), dtype=torch.float64, device="cuda")
+        psi = torch.zeros(R, dtype=torch.float64, device="cuda")
+        fl = torch.zeros(R, dtype=torch.int32, device="cuda")
+        rtw.rtw_rays_export(rays, p, 0, R, s, F, psi, fl)
+        ii = torch.tensor(idx, device="cuda")
+        s, F, psi = s[ii].cpu().numpy(), F[ii].cpu().numpy(), psi[ii].cpu().numpy()
+        fl = fl[ii].cpu().numpy().view(np.uint32)
+        for k in range(len(idx)):
+            r = ref[k, p]
+            assert bool(fl[k] & 1) == (r[oracle_mod.VALID] != 0.0), (p, k)
+            if not fl[k] & 1:
+                continue
+            assert np.abs(s[k] - r[oracle_mod.S:oracle_mod.S + 3]).max() < 1e-11
+            Fr = r[oracle_mod.F:oracle_mod.F + 6]
+            assert np.abs(F[k] - Fr).max() <= 1e-9 * np.abs(Fr).max() + 1e-15
+            assert abs(psi[k] - r[oracle_mod.PSI]) < 1e-7
+            assert ((fl[k] >> 8) & 0xFF) == int(r[oracle_mod.NF])
+            assert bool(fl[k] & 2) == (r[oracle_mod.ORIENT] > 0)
+            assert bool(fl[k] & 4) == (r[oracle_mod.CAUSTIC] != 0.0)
+            checked += 1
+    assert checked > 4000
