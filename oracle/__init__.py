@@ -72,6 +72,8 @@ def lib():
         L.or_near_record.restype = i
         L.or_field_sphere.argtypes = [p, i64, d, i, i, i, d, p, p, i]
         L.or_field_sphere.restype = i64
+        L.or_field_po2d.argtypes = [p, i64, d, i, p, d, d, d, d, p, i64, p]
+        L.or_field_po2d.restype = i64
         L.or_newton.argtypes = [p, i, p, p, d, p]
         L.or_newton.restype = i
         L.om_gelu.argtypes = [d]
@@ -160,6 +162,21 @@ class Object:
         if rc != 0:
             raise RuntimeError("or_field_fan failed")
         return out, mask
+
+    def field_po2d(self, p, window, dirs, aperture_dir, cone, n_target=0, h=0.0):
+        """2-D physical-optics field of order p over the rays of a vertex window of the square grid:
+        aperture plane through the centre with normal aperture_dir = (theta, phi), rays weighted by
+        the angle of their exit direction to that normal (1 up to cone[0], 0 from cone[1]);
+        dirs: (n, 2) (theta, phi).  Returns (n, 2) complex (F_theta, F_phi) and the rays summed."""
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
+        win = np.ascontiguousarray(window, dtype=np.int64)
+        out = np.zeros((dirs.shape[0], 4))
+        used = lib().or_field_po2d(self.handle, int(n_target), float(h), int(p), _ptr(win), float(aperture_dir[0]),
+                                   float(aperture_dir[1]), float(cone[0]), float(cone[1]), _ptr(dirs),
+                                   dirs.shape[0], _ptr(out))
+        if used < 0:
+            raise ValueError("invalid aperture window or cone")
+        return complex_field(out), int(used)
 
     def field_grid(self, pmax, ntheta, nphi, n_target=0, h=0.0, window=None, flags=0, threads=0):
         out = np.zeros((ntheta * nphi, pmax + 1, 4))

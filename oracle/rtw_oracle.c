@@ -1540,6 +1540,139 @@ int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pma
 }
 
 /* ------------------------------------------------------------------------------------- */
+/* 2-D physical optics over an aperture of rays ("Diffraction effect correction based on   */
+/* VCRM": near singularities the ray sum is replaced by a diffraction integral of the      */
+/* complex amplitudes the rays carry)                                                       */
+/* ------------------------------------------------------------------------------------- */
+
+int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, const int64_t* window,
+                      double ap_theta, double ap_phi, double cone_full, double cone_end, const double* dirs,
+                      int64_t ndir, double* out)
+{
+    double h, xc, yc;
+    int64_t nx, ny;
+    or_square_grid(o, n_target, h_in, &h, &nx, &ny, &xc, &yc);
+    const int64_t ix0 = window[0], ix1 = window[1], iy0 = window[2], iy1 = window[3];
+    if (ix0 < 0 || iy0 < 0 || ix1 >= nx || iy1 >= ny || ix1 - ix0 < 2 || iy1 - iy0 < 2 || p < 0) return -1;
+    if (!(cone_full >= 0.0 && cone_end > cone_full && cone_end <= 0.5 * PI)) return -1;
+    const int64_t wx = ix1 - ix0 + 1, wy = iy1 - iy0 + 1, n = wx * wy;
+    /* aperture: the plane through the object centre with normal a */
+    const double a[3] = {sin(ap_theta) * cos(ap_phi), sin(ap_theta) * sin(ap_phi), cos(ap_theta)};
+    double* xa = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    cplx* U = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)n);
+    uint8_t* ok = (uint8_t*)malloc((size_t)n);
+    double* buf = (double*)malloc(sizeof(double) * (size_t)(p + 1) * OR_NFIELD);
+    if (!xa || !U || !ok || !buf) {
+        free(xa); free(U); free(ok); free(buf);
+        return -1;
+    }
+    /* each ray's exit wave carried along its ray to the plane: the point x, and the field
+     * U = E' sqrt(D_legs / |det(I + tau Q')|) (-i)^{N_f} e^{i k0 (L + tau)} (Eqs. IntVCRM,
+     * DivFactVCRM, PhasePath), focal lines counted forward (tau > 0) or undone backward */
+    double* wgt = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!wgt) {
+        free(xa); free(U); free(ok); free(buf);
+        return -1;
+    }
+    free(buf);
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+    double* rb = (double*)malloc(sizeof(double) * (size_t)(p + 1) * OR_NFIELD);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+    for (int64_t jy = 0; jy < wy; ++jy)
+        for (int64_t jx = 0; jx < wx; ++jx) {
+            const int64_t q = jy * wx + jx;
+            ok[q] = 0;
+            wgt[q] = 0.0;
+            double x = grid_coord(xc, ix0 + jx, nx, h), y = grid_coord(yc, iy0 + jy, ny, h);
+            if (!or_trace_ray(o, x, y, p, rb, NULL)) continue;
+            const double* r = rb + (size_t)p * OR_NFIELD;
+            if (r[OR_VALID] == 0.0) continue;
+            const double* sj = r + OR_S;
+            double dd[3] = {o->center[0] - r[OR_REXIT], o->center[1] - r[OR_REXIT + 1], o->center[2] - r[OR_REXIT + 2]};
+            double sa = dot3(a, sj);
+            if (!(fabs(sa) > 1e-6)) continue;
+            double tau = dot3(a, dd) / sa;
+            for (int c = 0; c < 3; ++c) xa[3 * q + c] = r[OR_REXIT + c] + tau * sj[c];
+            double Am[2][2] = {{1.0 + tau * r[OR_Q], tau * r[OR_Q + 1]}, {tau * r[OR_Q + 2], 1.0 + tau * r[OR_Q + 3]}};
+            double dA = det2(Am);
+            if (dA == 0.0) continue;
+            int nfl = neg_eigs(Am);
+            int nf_ap = (int)r[OR_NFLEGS] + (tau > 0.0 ? nfl : -nfl);
+            cplx amp = sqrt(r[OR_DLEGS] / fabs(dA)) * minus_i_pow(nf_ap) * cexp(I * o->k0 * (r[OR_PATH] + tau));
+            cplx E0 = r[OR_E] + I * r[OR_E + 1], E1 = r[OR_E + 2] + I * r[OR_E + 3];
+            for (int c = 0; c < 3; ++c) U[3 * q + c] = amp * (E0 * r[OR_V1 + c] + E1 * r[OR_V2 + c]);
+            /* the aperture keeps the rays whose exit directions lie within cone_full of the axis and
+             * tapers them to zero at cone_end (the role of the 1-D window's angular taper) */
+            double ca = dot3(a, sj);
+            wgt[q] = ramp(acos(ca > 1.0 ? 1.0 : (ca < -1.0 ? -1.0 : ca)), cone_full, cone_end);
+            ok[q] = 1;
+        }
+    free(rb);
+    }
+    /* area of the plane per grid cell at each ray, from central differences of the aperture
+     * points over the grid (one-sided at the window edge and next to rays that do not leave),
+     * times the angular taper: each branch through a point of the plane is counted */
+    int64_t used = 0;
+    for (int64_t jy = 0; jy < wy; ++jy)
+        for (int64_t jx = 0; jx < wx; ++jx) {
+            const int64_t q = jy * wx + jx;
+            if (!ok[q]) continue;
+            const int64_t qxm = jx > 0 && ok[q - 1] ? q - 1 : q, qxp = jx + 1 < wx && ok[q + 1] ? q + 1 : q;
+            const int64_t qym = jy > 0 && ok[q - wx] ? q - wx : q, qyp = jy + 1 < wy && ok[q + wx] ? q + wx : q;
+            double w = wgt[q];
+            if (qxm == qxp || qym == qyp || w == 0.0) {
+                ok[q] = 0;
+                continue;
+            }
+            double ex[3], ey[3], cr[3];
+            for (int c = 0; c < 3; ++c) {
+                ex[c] = (xa[3 * qxp + c] - xa[3 * qxm + c]) / (double)(qxp - qxm);
+                ey[c] = (xa[3 * qyp + c] - xa[3 * qym + c]) / (double)((qyp - qym) / wx);
+            }
+            cross3(ex, ey, cr);
+            double area = fabs(dot3(cr, a));
+            for (int c = 0; c < 3; ++c) U[3 * q + c] *= w * area;
+            ++used;
+        }
+    /* Kirchhoff far field of the plane aperture: F(s) = k0 / (2 pi i) sum U dA e^{-i k0 s.x} */
+    const cplx pre = -I * o->k0 / (2.0 * PI);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t k = 0; k < ndir; ++k) {
+        double th = dirs[2 * k], ph = dirs[2 * k + 1];
+        double sv[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+        double et[3] = {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)};
+        double ep[3] = {-sin(ph), cos(ph), 0.0};
+        cplx ft = 0.0, fp = 0.0;
+        for (int64_t q = 0; q < n; ++q) {
+            if (!ok[q]) continue;
+            cplx e = cexp(-I * o->k0 * dot3(sv, xa + 3 * q));
+            for (int c = 0; c < 3; ++c) {
+                ft += U[3 * q + c] * e * et[c];
+                fp += U[3 * q + c] * e * ep[c];
+            }
+        }
+        ft *= pre;
+        fp *= pre;
+        out[4 * k] = creal(ft);
+        out[4 * k + 1] = cimag(ft);
+        out[4 * k + 2] = creal(fp);
+        out[4 * k + 3] = cimag(fp);
+    }
+    free(xa);
+    free(U);
+    free(ok);
+    free(wgt);
+    return used;
+}
+
+/* ------------------------------------------------------------------------------------- */
 /* Learned proposal: network seeds, Newton on the exact trace, deduplicated roots          */
 /* ------------------------------------------------------------------------------------- */
 

@@ -140,6 +140,20 @@ int or_near_record(const or_object* o, const double* far, double R, double* rec)
 int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi, double R,
                         double* out, uint8_t* mask, int nthreads);
 
+/* 2-D physical-optics field of order p over an aperture of rays ("Diffraction effect correction
+ * based on VCRM"; Kirchhoff's integral over a plane): the rays of the grid vertices
+ * [ix0, ix1] x [iy0, iy1] (window) of the square grid carry their exit waves to the plane through the
+ * object centre with normal a = (ap_theta, ap_phi), where each has the field
+ * U = E' sqrt(D_legs / |det(I + tau Q')|) (-i)^{N_f} e^{i k0 (L + tau)} and the area dA of the plane
+ * per grid cell (central differences of the crossing points); a ray whose exit direction makes the
+ * angle g with a has the weight ramp(g): 1 up to cone_full, cos^2 down to 0 at cone_end (the
+ * window should hold every ray within cone_end; its own edges are not tapered).
+ * F(s) = k0 / (2 pi i) sum w U dA e^{-i k0 s.x}, projected on e_theta, e_phi.  dirs: ndir x
+ * (theta, phi); out: ndir x 4.  Returns the number of rays in the sum, or -1 for invalid arguments. */
+int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, const int64_t* window,
+                      double ap_theta, double ap_phi, double cone_full, double cone_end, const double* dirs,
+                      int64_t ndir, double* out);
+
 /* Newton on the exact trace: finds the ray of order p whose exit direction is target, from the
  * seed impact point xy (2), with steps halved until the residual decreases; the root must lie
  * within rmax of the seed (rmax <= 0: no bound).  Returns iterations used, or -1 if it did not
