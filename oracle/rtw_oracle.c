@@ -1626,7 +1626,7 @@ int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, 
             const int64_t qym = jy > 0 && ok[q - wx] ? q - wx : q, qyp = jy + 1 < wy && ok[q + wx] ? q + wx : q;
             double w = wgt[q];
             if (qxm == qxp || qym == qyp || w == 0.0) {
-                ok[q] = 0;
+                wgt[q] = 0.0; /* out of the sum; it stays a neighbour of the others */
                 continue;
             }
             double ex[3], ey[3], cr[3];
@@ -1639,6 +1639,8 @@ int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, 
             for (int c = 0; c < 3; ++c) U[3 * q + c] *= w * area;
             ++used;
         }
+    for (int64_t q = 0; q < n; ++q)
+        if (wgt[q] == 0.0) ok[q] = 0;
     /* Kirchhoff far field of the plane aperture: F(s) = k0 / (2 pi i) sum U dA e^{-i k0 s.x} */
     const cplx pre = -I * o->k0 / (2.0 * PI);
 #ifdef _OPENMP
