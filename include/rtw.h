@@ -81,7 +81,8 @@ extern "C" {
 #define RTW_FIELD_NEAR_FOLDS 4 /* with RTW_NEWTON: refine only the hits within 2 deg of an
                                   in-plane fold of their order (rainbow windows)                 */
 
-#define RTW_TRACE_APERTURE 1 /* keep the exit-wave data the PO integral needs (fan grids)       */
+#define RTW_TRACE_APERTURE 1 /* keep the exit-wave data the PO integrals need (fans; square grids
+                                in RTW_FP64 for rtw_field_po2d): 144 B more per (ray, order)      */
 
 #define RTW_MASK_CAUSTIC 1u /* a cell straddling a fold or flagged near-caustic covers it     */
 #define RTW_MASK_AXIAL 2u   /* within 2 lambda / min(a, b, c) of the forward or backward axis  */
@@ -235,6 +236,33 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
  * synchronised once per slice); RTW_ERR_CAPACITY when a single row does not fit. */
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
               uint8_t* mask_out, void* stream);
+
+/* 2-D physical optics of one order over an aperture of rays ("Diffraction effect correction based
+ * on VCRM": near a singularity the field is a diffraction integral of the complex amplitudes the rays
+ * carry; this is Kirchhoff's integral over a plane, both directions numerical, where RTW_FIELD_PO
+ * integrates one direction of a fan and takes the other by stationary phase).  The rays of the grid
+ * vertices [window[0], window[1]] x [window[2], window[3]] carry their exit waves to the plane through
+ * the object's centre with normal a = (axis_theta, axis_phi): crossing point x = r + tau s, field
+ * U = E' sqrt(D_legs / |det(I + tau Q')|) (-i)^{N_f} e^{i k0 (L + tau)} (focal lines of the last
+ * stretch counted forward for tau > 0, undone for tau < 0); dA = the plane's area per grid cell from
+ * central differences of the neighbours' crossing points; each ray weighted by the angle g of its
+ * exit direction to a: 1 for g <= cone_full, cos^2 to 0 at cone_end (the window should hold every ray
+ * within cone_end; its own edges are not tapered).  F(s) = k0 / (2 pi i) sum w U dA e^{-i k0 s.x},
+ * the far field of that order (same convention as rtw_field), near the directions of the rays kept.
+ * rays: one object, square grid, RTW_FP64, traced with RTW_TRACE_APERTURE, far field.  dirs (device,
+ * read during the call): n_dirs (theta, phi) pairs, 1 <= n_dirs < 2^31.  field_out (device):
+ * [n_dirs][2] complex128 (F_theta, F_phi), overwritten.  Errors: RTW_ERR_ARG (null, rays not so traced,
+ * order outside [0, p_max], a window beyond the grid or under 3 x 3 vertices or over 2^31 rays,
+ * not 0 <= cone_full < cone_end <= pi/2), RTW_ERR_CUDA.  Asynchronous; a scratch block of 152 B per
+ * window ray and 48 B per direction is allocated and freed in stream order. */
+typedef struct {
+    int order;
+    int64_t window[4];
+    double axis_theta, axis_phi;
+    double cone_full, cone_end;
+} rtw_po2d_params;
+int rtw_field_po2d(const rtw_rays* rays, const rtw_po2d_params* pp, const double* dirs, int64_t n_dirs,
+                   void* field_out, void* stream);
 
 /* ---- many objects in one launch sequence ---- */
 

@@ -662,7 +662,10 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
         d.ray_offset = R;
         R += nx * ny;
     }
-    const bool aux = tp->grid == RTW_GRID_FAN && (tp->flags & RTW_TRACE_APERTURE);
+    // aperture data: fans (the 1-D PO of rtw_field) and square grids in double precision (rtw_field_po2d)
+    if ((tp->flags & RTW_TRACE_APERTURE) && tp->grid == RTW_GRID_SQUARE && tp->precision != RTW_FP64)
+        return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: RTW_TRACE_APERTURE on a square grid needs RTW_FP64");
+    const bool aux = (tp->flags & RTW_TRACE_APERTURE) != 0;
     // one allocation carved into 256-byte aligned arrays
     const size_t n = (size_t)np * (size_t)R;
     size_t off[8], total = 0;
@@ -780,6 +783,40 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
     cudaError_t e = rtw::launch_trace_points(d_obj, xy, n, p_max, s_out, F_out, psi_out, flags_out, s);
     cudaFreeAsync(d_obj, s);
     if (e != cudaSuccess) return cuda_fail(e, "trace_points launch");
+    return RTW_OK;
+}
+
+int rtw_field_po2d(const rtw_rays* rays, const rtw_po2d_params* pp, const double* dirs, int64_t n_dirs,
+                   void* field_out, void* stream)
+{
+    if (!rays || !pp || !dirs || !field_out) return fail(RTW_ERR_ARG, "rtw_field_po2d: null pointer");
+    if (rays->grid != RTW_GRID_SQUARE || rays->nobj != 1 || !rays->st.aux || rays->st.near_r != 0.0)
+        return fail(RTW_ERR_ARG, "rtw_field_po2d: one object on a square grid traced with RTW_TRACE_APERTURE "
+                                 "(far field) is required");
+    if (pp->order < 0 || pp->order >= rays->np) return fail(RTW_ERR_ARG, "rtw_field_po2d: order out of range");
+    const ObjDev& o = rays->objs[0];
+    const int64_t* w = pp->window;
+    if (w[0] < 0 || w[2] < 0 || w[1] >= o.nx || w[3] >= o.ny || w[1] - w[0] < 2 || w[3] - w[2] < 2)
+        return fail(RTW_ERR_ARG, "rtw_field_po2d: window must hold at least 3 x 3 vertices of the %lld x %lld grid",
+                    o.nx, o.ny);
+    if ((w[1] - w[0] + 1) * (w[3] - w[2] + 1) >= (1ll << 31))
+        return fail(RTW_ERR_ARG, "rtw_field_po2d: more than 2^31 rays in the window");
+    if (!(pp->cone_full >= 0.0 && pp->cone_end > pp->cone_full && pp->cone_end <= 0.5 * kPi))
+        return fail(RTW_ERR_ARG, "rtw_field_po2d: 0 <= cone_full < cone_end <= pi/2");
+    if (!std::isfinite(pp->axis_theta + pp->axis_phi)) return fail(RTW_ERR_ARG, "rtw_field_po2d: axis");
+    if (n_dirs < 1 || n_dirs >= (1ll << 31)) return fail(RTW_ERR_ARG, "rtw_field_po2d: 1 <= n_dirs < 2^31");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long win[4] = {w[0], w[1], w[2], w[3]};
+    const long long nwin = (win[1] - win[0] + 1) * (win[3] - win[2] + 1);
+    const double axis[3] = {std::sin(pp->axis_theta) * std::cos(pp->axis_phi),
+                            std::sin(pp->axis_theta) * std::sin(pp->axis_phi), std::cos(pp->axis_theta)};
+    // a per-call scratch block, freed once the launches have been ordered
+    void* scratch = nullptr;
+    RTW_CUDA(cudaMallocAsync(&scratch, rtw::po2d_scratch_bytes(nwin, n_dirs), s));
+    cudaError_t e = rtw::launch_po2d(rays->st, pp->order, o.nx, win, o.c, axis, o.k0, pp->cone_full, pp->cone_end,
+                                     dirs, n_dirs, (double2*)field_out, scratch, s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "po2d launch");
     return RTW_OK;
 }
 

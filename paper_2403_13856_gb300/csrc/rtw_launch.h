@@ -88,6 +88,15 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirS
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
                               int newton, cudaStream_t s, int stage = 0);
+// 2-D physical optics over a window of grid vertices [win0, win1] x [win2, win3] of one square-grid
+// object (nx vertices per row; rays traced with the aperture data): plane through c with normal axis,
+// rays weighted by the angle of their exit direction to it (1 up to cone_full, 0 from cone_end);
+// dirs: ndir (theta, phi) pairs on the device; out: ndir x (F_theta, F_phi).  scratch holds
+// po2d_scratch_bytes(window vertices, ndir) bytes.
+size_t po2d_scratch_bytes(long long nwin, long long ndir);
+cudaError_t launch_po2d(const RaysDev& st, int order, long long nx, const long long win[4], const double c[3],
+                        const double axis[3], double k0, double cone_full, double cone_end, const double* dirs,
+                        long long ndir, double2* out, void* scratch, cudaStream_t s);
 // stage of launch_field_grid: 0 classifies the triangles and sums their hits; 1 only classifies
 // (*nhit then holds the number of pairs the batch wants, which may exceed hit_cap); 2 sums the hits
 // of a stage-1 run that fitted

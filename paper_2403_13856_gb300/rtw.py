@@ -86,6 +86,7 @@ def lib():
             "rtw_destroy_rays": ([p], None),
             "rtw_trace_points": ([p, i, p, i64, i, p, p, p, p, p], i),
             "rtw_field": ([p, p, i, i, p, p, p], i),
+            "rtw_field_po2d": ([p, p, p, i64, p, p], i),
             "rtw_far_field_batch": ([p, p, p, i, p, p, p, p], i),
             "rtw_batch_info": ([p, p, p, p], i),
             "rtw_batch_times": ([p, p, p], i),
@@ -254,6 +255,26 @@ def dirs_list(theta_phi) -> rtw_dirs:
     d.list = theta_phi.data_ptr()
     d.n_list = theta_phi.shape[0]
     return d
+
+
+class rtw_po2d_params(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("window", ctypes.c_int64 * 4), ("axis_theta", ctypes.c_double),
+                ("axis_phi", ctypes.c_double), ("cone_full", ctypes.c_double), ("cone_end", ctypes.c_double)]
+
+
+def po2d_params(order, window, axis, cone) -> rtw_po2d_params:
+    pp = rtw_po2d_params()
+    pp.order = int(order)
+    pp.window[:] = [int(v) for v in window]
+    pp.axis_theta, pp.axis_phi = float(axis[0]), float(axis[1])
+    pp.cone_full, pp.cone_end = float(cone[0]), float(cone[1])
+    return pp
+
+
+def rtw_field_po2d(rays: Rays, pp: rtw_po2d_params, dirs, out, stream=None):
+    """dirs: (n, 2) float64 (theta, phi) on the device; out: (n, 2) complex128 on the device."""
+    _check(lib().rtw_field_po2d(rays.handle, ctypes.byref(pp), _ptr(dirs), dirs.shape[0], _ptr(out),
+                                _stream_ptr(stream)))
 
 
 def rtw_field(rays: Rays, dirs: rtw_dirs, out, mask=None, mode=RTW_DENSE, flags=0, stream=None):
