@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -414,6 +415,43 @@ def bench_ellipsoid(args, rank, world, local, dist):
                       "kernel": "trace_kernel_fp64_super"}
     del re_, obje
 
+    # 2-D physical optics at the rainbow of a 500 um sphere (order 2, perpendicular polarisation):
+    # 4002 x 4002 grid rays traced with the aperture data, the left half as the window, rays tapered
+    # like the 1-D window (3 Airy + 3 Fresnel widths, to zero at + 6), 64 x 64 directions around the bow
+    a_s = 500.0
+    sph = rtw.Object([rtw.ObjectSpec(a=a_s, b=a_s, c=a_s, quat=(1.0, 0.0, 0.0, 0.0), m=W.WATER, wavelength=W.HE_NE,
+                                     jones=(0.0, 1.0))])
+    tpa = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=2, spacing=0.25, flags=rtw.RTW_TRACE_APERTURE)
+    ra = rtw.rtw_trace(sph, tpa, stream=stream)
+    _, nxa, nya = sph.grid(0, tpa)
+    k0s = 2.0 * math.pi / W.HE_NE
+    aw, fw, thc = (W.HE_NE / a_s) ** (2.0 / 3.0), 1.0 / math.sqrt(k0s * a_s), math.radians(137.922)
+    tg, pg = torch.meshgrid(thc + torch.linspace(-0.4 * aw, 1.5 * aw, 64, dtype=torch.float64),
+                            torch.linspace(-math.radians(2.0), math.radians(2.0), 64, dtype=torch.float64), indexing="ij")
+    dirs_po = torch.stack([tg.reshape(-1), pg.reshape(-1)], 1).cuda()
+    out_po = torch.zeros((dirs_po.shape[0], 2), dtype=torch.complex128, device="cuda")
+    pp = rtw.po2d_params(2, [0, nxa // 2, 0, nya - 1], (thc, 0.0), (3 * aw + 3 * fw, 3 * aw + 6 * fw))
+    used_po = rtw.rtw_field_po2d(ra, pp, dirs_po, out_po, count=True, stream=stream)
+    for _ in range(3):
+        rtw.rtw_trace(sph, tpa, ra, stream=stream)
+        rtw.rtw_field_po2d(ra, pp, dirs_po, out_po, stream=stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(5)]
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        rtw.rtw_trace(sph, tpa, ra, stream=stream)
+        e[1].record(stream)
+        rtw.rtw_field_po2d(ra, pp, dirs_po, out_po, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    rtw.rtw_sync_status(stream)
+    tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
+    tpo = statistics.median([e[1].elapsed_time(e[2]) for e in ev])
+    po2d = {"sphere_um": a_s, "grid_rays": nxa * nya, "rays_in_sum": used_po, "directions": int(dirs_po.shape[0]),
+            "ms_trace_aperture": tt, "ms_po2d": tpo, "terms_per_s": used_po * dirs_po.shape[0] / (tpo / 1e3),
+            "kernel": "po2d_sum_kernel (FP64: one sincos per ray-direction term)"}
+    del ra, sph, out_po, dirs_po
+
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
     host_mask = torch.empty(ndir, dtype=torch.uint8, pin_memory=True)
@@ -469,6 +507,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "near_field": near,
         "point_source": point,
         "superellipsoid": superellipsoid,
+        "po2d_rainbow": po2d,
     }
     if cpu:
         line["cpu_baseline"] = cpu

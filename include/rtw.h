@@ -254,7 +254,8 @@ int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, v
  * [n_dirs][2] complex128 (F_theta, F_phi), overwritten.  Errors: RTW_ERR_ARG (null, rays not so traced,
  * order outside [0, p_max], a window beyond the grid or under 3 x 3 vertices or over 2^31 rays,
  * not 0 <= cone_full < cone_end <= pi/2), RTW_ERR_CUDA.  Asynchronous; a scratch block of 152 B per
- * window ray and 48 B per direction is allocated and freed in stream order. */
+ * window ray and 48 B per direction is allocated and freed in stream order.  n_used (host, optional):
+ * receives the number of rays in the sum (the call then synchronises the stream to read it). */
 typedef struct {
     int order;
     int64_t window[4];
@@ -262,7 +263,7 @@ typedef struct {
     double cone_full, cone_end;
 } rtw_po2d_params;
 int rtw_field_po2d(const rtw_rays* rays, const rtw_po2d_params* pp, const double* dirs, int64_t n_dirs,
-                   void* field_out, void* stream);
+                   void* field_out, int64_t* n_used, void* stream);
 
 /* ---- many objects in one launch sequence ---- */
 

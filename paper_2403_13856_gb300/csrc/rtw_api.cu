@@ -787,7 +787,7 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
 }
 
 int rtw_field_po2d(const rtw_rays* rays, const rtw_po2d_params* pp, const double* dirs, int64_t n_dirs,
-                   void* field_out, void* stream)
+                   void* field_out, int64_t* n_used, void* stream)
 {
     if (!rays || !pp || !dirs || !field_out) return fail(RTW_ERR_ARG, "rtw_field_po2d: null pointer");
     if (rays->grid != RTW_GRID_SQUARE || rays->nobj != 1 || !rays->st.aux || rays->st.near_r != 0.0)
@@ -813,10 +813,18 @@ int rtw_field_po2d(const rtw_rays* rays, const rtw_po2d_params* pp, const double
     // a per-call scratch block, freed once the launches have been ordered
     void* scratch = nullptr;
     RTW_CUDA(cudaMallocAsync(&scratch, rtw::po2d_scratch_bytes(nwin, n_dirs), s));
+    const size_t bytes = rtw::po2d_scratch_bytes(nwin, n_dirs);
     cudaError_t e = rtw::launch_po2d(rays->st, pp->order, o.nx, win, o.c, axis, o.k0, pp->cone_full, pp->cone_end,
                                      dirs, n_dirs, (double2*)field_out, scratch, s);
+    unsigned int used = 0;
+    if (e == cudaSuccess && n_used) {
+        // the count sits in the last 256 bytes of the scratch block
+        e = cudaMemcpyAsync(&used, (char*)scratch + bytes - 256, sizeof(used), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "po2d launch");
+    if (n_used) *n_used = (int64_t)used;
     return RTW_OK;
 }
 

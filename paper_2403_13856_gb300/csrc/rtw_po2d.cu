@@ -233,7 +233,8 @@ cudaError_t launch_po2d(const RaysDev& st, int order, long long nx, const long l
     double* cw = cxp + 3 * nwin;
     double* acc = cw + 6 * nwin;
     unsigned char* ok = (unsigned char*)(acc + 6 * ndir);
-    unsigned int* count = (unsigned int*)(ok + (nwin + 255) / 256 * 256);
+    // the count occupies the last 256 bytes of the block (the host reads it there)
+    unsigned int* count = (unsigned int*)((char*)scratch + po2d_scratch_bytes(nwin, ndir) - 256);
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 6 * (size_t)ndir, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;

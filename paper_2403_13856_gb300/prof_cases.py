@@ -5,6 +5,7 @@
     python -m paper_2403_13856_gb300.prof_cases learned [--objects N]
     python -m paper_2403_13856_gb300.prof_cases ellipsoid [--rays N]
     python -m paper_2403_13856_gb300.prof_cases superellipsoid [--rays N] [--shape-e E]
+    python -m paper_2403_13856_gb300.prof_cases po2d [--sphere A] [--spacing H]
 
 Each case builds its inputs (seeded), runs the launch sequence `--reps` times (default 3) after
 one warm-up and prints the CUDA-event time of the last repetition.  Sizes default to cases that
@@ -33,12 +34,14 @@ def _timed(torch, fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid", "superellipsoid"])
+    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid", "superellipsoid", "po2d"])
     ap.add_argument("--rows", type=int, default=1 << 22)
     ap.add_argument("--objects", type=int, default=64)
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--shape-e", type=float, default=2.0, help="superellipsoid exponent e")
+    ap.add_argument("--sphere", type=float, default=200.0, help="po2d: sphere radius (um)")
+    ap.add_argument("--spacing", type=float, default=0.25, help="po2d: ray grid spacing (um)")
     ap.add_argument("--mixed", action="store_true", help="ellipsoid / batch: mixed-precision trace")
     ap.add_argument("--dfloat", action="store_true", help="ellipsoid / batch: double-float trace")
     a = ap.parse_args()
@@ -80,6 +83,26 @@ def main():
         ms = _timed(torch, lambda: rtw.rtw_field_learned(obj, mlp, lp, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]),
                                                          out), a.reps)
         print(f"learned objects={a.objects}: {ms:.3f} ms")
+    elif a.case == "po2d":
+        import math
+
+        sa = a.sphere
+        obj = rtw.Object([rtw.ObjectSpec(a=sa, b=sa, c=sa, quat=(1.0, 0.0, 0.0, 0.0), m=W.WATER, wavelength=W.HE_NE,
+                                         jones=(0.0, 1.0))])
+        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=2, spacing=a.spacing, flags=rtw.RTW_TRACE_APERTURE)
+        rays = rtw.rtw_trace(obj, tp)
+        _, nx, ny = obj.grid(0, tp)
+        aw, fw = (W.HE_NE / sa) ** (2.0 / 3.0), 1.0 / math.sqrt(2.0 * math.pi / W.HE_NE * sa)
+        thc = math.radians(137.922)
+        tg, pg = torch.meshgrid(thc + torch.linspace(-0.4 * aw, 1.5 * aw, 64, dtype=torch.float64),
+                                torch.linspace(-0.035, 0.035, 64, dtype=torch.float64), indexing="ij")
+        dirs = torch.stack([tg.reshape(-1), pg.reshape(-1)], 1).cuda()
+        out = torch.empty((dirs.shape[0], 2), dtype=torch.complex128, device="cuda")
+        pp = rtw.po2d_params(2, [0, nx // 2, 0, ny - 1], (thc, 0.0), (3 * aw + 3 * fw, 3 * aw + 6 * fw))
+        used = rtw.rtw_field_po2d(rays, pp, dirs, out, count=True)
+        ms = _timed(torch, lambda: rtw.rtw_field_po2d(rays, pp, dirs, out), a.reps)
+        print(f"po2d sphere={sa} grid={nx}x{ny} rays={used} dirs={dirs.shape[0]}: {ms:.3f} ms, "
+              f"{used * dirs.shape[0] / ms / 1e6:.3f} Gterms/s")
     else:
         spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
         if a.case == "superellipsoid":

@@ -86,7 +86,7 @@ def lib():
             "rtw_destroy_rays": ([p], None),
             "rtw_trace_points": ([p, i, p, i64, i, p, p, p, p, p], i),
             "rtw_field": ([p, p, i, i, p, p, p], i),
-            "rtw_field_po2d": ([p, p, p, i64, p, p], i),
+            "rtw_field_po2d": ([p, p, p, i64, p, p, p], i),
             "rtw_far_field_batch": ([p, p, p, i, p, p, p, p], i),
             "rtw_batch_info": ([p, p, p, p], i),
             "rtw_batch_times": ([p, p, p], i),
@@ -271,10 +271,13 @@ def po2d_params(order, window, axis, cone) -> rtw_po2d_params:
     return pp
 
 
-def rtw_field_po2d(rays: Rays, pp: rtw_po2d_params, dirs, out, stream=None):
-    """dirs: (n, 2) float64 (theta, phi) on the device; out: (n, 2) complex128 on the device."""
+def rtw_field_po2d(rays: Rays, pp: rtw_po2d_params, dirs, out, count=False, stream=None):
+    """dirs: (n, 2) float64 (theta, phi) on the device; out: (n, 2) complex128 on the device.
+    count=True returns the number of rays in the sum (the call then synchronises the stream)."""
+    n = ctypes.c_int64(-1)
     _check(lib().rtw_field_po2d(rays.handle, ctypes.byref(pp), _ptr(dirs), dirs.shape[0], _ptr(out),
-                                _stream_ptr(stream)))
+                                ctypes.byref(n) if count else None, _stream_ptr(stream)))
+    return n.value if count else None
 
 
 def rtw_field(rays: Rays, dirs: rtw_dirs, out, mask=None, mode=RTW_DENSE, flags=0, stream=None):

@@ -32,9 +32,9 @@ def po2d_gpu(rtw, spec, jones, h, p_max, order, window, axis, cone, dirs):
     rays = rtw.rtw_trace(g, tp)
     d = torch.tensor(dirs, dtype=torch.float64, device="cuda")
     out = torch.zeros((len(dirs), 2), dtype=torch.complex128, device="cuda")
-    rtw.rtw_field_po2d(rays, rtw.po2d_params(order, window, axis, cone), d, out)
+    used = rtw.rtw_field_po2d(rays, rtw.po2d_params(order, window, axis, cone), d, out, count=True)
     rtw.rtw_sync_status()
-    return out.cpu().numpy(), g, rays, tp
+    return out.cpu().numpy(), used, g, tp
 
 
 @pytest.mark.parametrize("a,h", [(50.0, 0.1), (500.0, 0.25)])
@@ -48,10 +48,10 @@ def test_po2d_rainbow_matches_oracle(rtw, oracle_mod, a, h):
     _, nx, ny, _, _ = o.square_grid(h=h)
     win = [0, nx // 2, 0, ny - 1]
     cone = (3 * Aw + 3 * Fw, 3 * Aw + 6 * Fw)
-    got, g, rays, tp = po2d_gpu(rtw, spec, (0.0, 1.0), h, 2, 2, win, (thc, 0.0), cone, dirs)
+    got, gused, g, tp = po2d_gpu(rtw, spec, (0.0, 1.0), h, 2, 2, win, (thc, 0.0), cone, dirs)
     assert g.grid(0, tp)[1:] == (nx, ny)
     ref, used = o.field_po2d(2, win, dirs, (thc, 0.0), cone, h=h)
-    assert used > 100_000
+    assert used > 100_000 and gused == used
     scale = np.abs(ref).max()
     err = np.abs(got - ref).max()
     print(f"a = {a}: {used} rays, max |dF| / max |F| = {err / scale:.2e}")
@@ -73,8 +73,9 @@ def test_po2d_ellipsoid_matches_oracle(rtw, oracle_mod):
     th0, ph0 = math.acos(s0[2]), math.atan2(s0[1], s0[0])
     dirs = np.array([[th0 + dt, ph0 + dp] for dt in np.linspace(-0.02, 0.02, 5) for dp in np.linspace(-0.02, 0.02, 5)])
     win = [0, nx - 1, 0, ny - 1]
-    got, _, _, _ = po2d_gpu(rtw, spec, (0.6, 0.8j), h, 1, 1, win, (th0, ph0), (0.2, 0.35), dirs)
+    got, gused, _, _ = po2d_gpu(rtw, spec, (0.6, 0.8j), h, 1, 1, win, (th0, ph0), (0.2, 0.35), dirs)
     ref, used = o.field_po2d(1, win, dirs, (th0, ph0), (0.2, 0.35), h=h)
+    assert gused == used
     scale = np.abs(ref).max()
     err = np.abs(got - ref).max()
     print(f"ellipsoid order 1: {used} rays, max |dF| / max |F| = {err / scale:.2e}")
