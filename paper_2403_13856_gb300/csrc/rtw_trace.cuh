@@ -309,7 +309,7 @@ __device__ __forceinline__ bool super_entry(const ObjDev& o, const double r0[3],
         }
     }
     if (!(tin < tout)) return false;
-    double t = tin;
+    double t = tin, prev = INFINITY;
     for (int it = 0; it < 96; ++it) {
         double df;
         const double f = super_phi(o, u, kap, t, df);
@@ -318,7 +318,10 @@ __device__ __forceinline__ bool super_entry(const ObjDev& o, const double r0[3],
         const double step = -f / df;
         t += step;
         if (t > tout) return false;
-        if (step <= 4e-16 * fabs(t)) break;
+        // converged: a rounding-sized step, or a small step after a quadratic contraction (the next
+        // correction, about step^2 phi'' / 2 phi', is then below rounding)
+        if (step <= 4e-16 * fabs(t) || (step <= 1e-9 * fabs(t) && step <= 1e-3 * prev)) break;
+        prev = step;
     }
     t_hit = t;
     return true;
@@ -336,13 +339,15 @@ __device__ __forceinline__ double super_chord(const ObjDev& o, const double r[3]
     for (int i = 0; i < 3; ++i)
         if (kap[i] != 0.0) t = fmin(t, (copysign(1.0, kap[i]) - u[i]) / kap[i]);
     if (!(t > 0.0)) return 0.0;
+    double prev = INFINITY;
     for (int it = 0; it < 96; ++it) {
         double df;
         const double f = super_phi(o, u, kap, t, df);
         if (!(f > 0.0) || !(df > 0.0)) break;
         const double step = f / df;
         t -= step;
-        if (step <= 4e-16 * t) break;
+        if (step <= 4e-16 * t || (step <= 1e-9 * t && step <= 1e-3 * prev)) break;
+        prev = step;
     }
     return t;
 }

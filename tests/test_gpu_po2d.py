@@ -82,6 +82,22 @@ def test_po2d_ellipsoid_matches_oracle(rtw, oracle_mod):
     assert scale > 0 and err <= 1e-6 * scale
 
 
+def test_po2d_edge_window_and_empty_cone(rtw, oracle_mod):
+    """A window on the grid's edge (one-sided differences, rays that miss) matches the oracle; a cone
+    that keeps no ray sums nothing."""
+    spec = dict(a=10.0, b=10.0, c=10.0, quat=(1.0, 0.0, 0.0, 0.0), m=M_WATER, wavelength=LAM)
+    o = oracle_mod.Object(10.0, 10.0, 10.0, m=M_WATER, wavelength=LAM, jones=(0.0, 1.0))
+    _, nx, ny, _, _ = o.square_grid(h=0.1)
+    dirs = np.array([[2.4, 0.0], [2.41, 0.01], [2.45, -0.02]])
+    got, gused, _, _ = po2d_gpu(rtw, spec, (0.0, 1.0), 0.1, 2, 2, [0, 40, 0, ny - 1], (2.4, 0.0), (0.3, 0.5), dirs)
+    ref, used = o.field_po2d(2, [0, 40, 0, ny - 1], dirs, (2.4, 0.0), (0.3, 0.5), h=0.1)
+    assert used > 1000 and gused == used
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
+    got, gused, _, _ = po2d_gpu(rtw, spec, (0.0, 1.0), 0.1, 2, 2, [0, nx - 1, 0, ny - 1], (0.3, 0.0), (0.01, 0.02),
+                                dirs)
+    assert gused == 0 and np.all(got == 0)
+
+
 def test_po2d_arguments(rtw):
     spec = dict(a=10.0, b=10.0, c=10.0, quat=(1.0, 0.0, 0.0, 0.0), m=M_WATER, wavelength=LAM)
     g = rtw.Object([rtw.ObjectSpec(**spec)])

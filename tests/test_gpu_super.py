@@ -71,10 +71,11 @@ def test_super_records_match_oracle(rtw, oracle_mod):
     assert checked > 1000
 
 
-@pytest.mark.parametrize("e", [1.5, 1.7, 2.0, 4.0])
+@pytest.mark.parametrize("e", [1.5, 1.7, 2.0, 4.0, 8.0])
 def test_super_field_matches_oracle(rtw, oracle_mod, e):
     """About 3e4 rays, orders 0..4, 48 x 96 far-field directions: masks equal, every component
-    within 1e-6 of the largest.  2e = 3, 4, 8 take powers by products, 2e = 3.4 the pow function."""
+    within 1e-6 of the largest.  2e = 3, 4, 8, 16 take powers by products, 2e = 3.4 the pow
+    function; e = 8 is nearly a box, whose flat faces leave most directions masked as caustic."""
     sp = spec(e)
     p_max, nt, nph = 4, 48, 96
     g = rtw.Object([rtw.ObjectSpec(**sp, jones=(1.0, 0.0))])
@@ -88,10 +89,15 @@ def test_super_field_matches_oracle(rtw, oracle_mod, e):
     ref, rm, hits, _ = o.field_grid(p_max, nt, nph, n_target=30_000)
     ref = oracle_mod.complex_field(ref)
     assert hits > 5000
-    assert np.array_equal(gm, rm), f"{(gm != rm).sum()} mask entries differ"
+    # Near the rim of a nearly flat face one principal curvature is ~1e-16 of the other, so the sign
+    # of det Q' (a ray's orientation, hence whether a cell folds) is set by rounding, which differs
+    # between the two sides: for e = 8 a few directions may be masked on one side only; values are
+    # compared where the masks agree.  Smooth bodies (e <= 4) must agree everywhere.
+    differ = gm != rm
+    assert differ.sum() <= (0 if e <= 4 else 0.002 * differ.size), f"{differ.sum()} mask entries differ"
     scale = np.abs(ref).max()
-    err = np.abs(got - ref).max()
-    print(f"e = {e}: max |dF| / max |F| = {err / scale:.2e}")
+    err = np.abs(got - ref)[~differ].max()
+    print(f"e = {e}: max |dF| / max |F| = {err / scale:.2e}, {differ.sum()} masks differ")
     assert scale > 0 and err <= 1e-6 * scale
 
 
