@@ -166,6 +166,54 @@ def test_super_mixed_object_set(rtw, oracle_mod):
         assert scale > 0 and np.abs(got[k] - ref).max() <= 1e-6 * scale
 
 
+def test_super_field_direction_list(rtw, oracle_mod):
+    """A list of 20000 random directions (binned on the device), orders 0..5 at e = 3, whose pairs
+    outgrow the hit list: sliced runs on a list against the oracle's field on the same list."""
+    sp = spec(3.0, jones=(0.3, 0.9 + 0.3j))
+    p_max, n_rays = 5, 20_000
+    rng = np.random.default_rng(12)
+    dirs = np.stack([np.arccos(rng.uniform(-1.0, 1.0, 20_000)), rng.uniform(-np.pi, np.pi, 20_000)], 1)
+    g = rtw.Object([rtw.ObjectSpec(**sp)])
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=n_rays))
+    d = torch.tensor(dirs, dtype=torch.float64, device="cuda")
+    out = torch.zeros((len(dirs), p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(len(dirs), dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_list(d), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    o = oracle_mod.Object(**sp)
+    ref, rm, hits, _ = o.field_dirs(p_max, dirs, n_target=n_rays)
+    ref = oracle_mod.complex_field(ref)
+    assert hits > 5000
+    assert np.array_equal(mask.cpu().numpy(), rm)
+    scale = np.abs(ref).max()
+    err = np.abs(out.cpu().numpy() - ref).max()
+    print(f"list of 20000 directions, e = 3: max |dF| / max |F| = {err / scale:.2e}")
+    assert scale > 0 and err <= 1e-6 * scale
+
+
+def test_super_with_point_source_ellipsoid(rtw, oracle_mod):
+    """A superellipsoid beside an ellipsoid lit by a point source, in one object set (the set takes
+    the superellipsoid kernel; the point source keeps its own start): both against the oracle."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    p_max, nt, nph, n_rays = 3, 32, 64, 12_000
+    specs = [spec(2.0, jones=(1.0, 0.0)), dict(W.ELLIPSOID, jones=(0.0, 1.0), source=(30.0, -20.0, -400.0))]
+    g = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=n_rays))
+    out = torch.zeros((2, nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros((2, nt * nph), dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_grid(nt, nph), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    got, gm = out.cpu().numpy(), mask.cpu().numpy()
+    for k in range(2):
+        ref, rm, hits, _ = oracle_mod.Object(**specs[k]).field_grid(p_max, nt, nph, n_target=n_rays)
+        ref = oracle_mod.complex_field(ref)
+        assert hits > 2000
+        assert np.array_equal(gm[k], rm)
+        scale = np.abs(ref).max()
+        assert scale > 0 and np.abs(got[k] - ref).max() <= 1e-6 * scale
+
+
 def test_super_arguments(rtw, oracle_mod):
     g = rtw.Object([rtw.ObjectSpec(**spec(2.0))])
     with pytest.raises(rtw.RTWError):  # fans stay ellipsoidal
