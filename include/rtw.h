@@ -97,8 +97,9 @@ extern "C" {
  * with (u, v, w) the body coordinates divided by (a, b, c), a smooth convex body between the
  * ellipsoid and the box (the Introduction's principle (iii): the wavefront equation needs of the
  * surface only its normal and curvature matrix at each point, here from the gradient and Hessian
- * of that function).  A superellipsoid takes a plane wave, rtw_trace with a square grid, RTW_FP64
- * and observe_radius 0, and rtw_field in RTW_DENSE mode without RTW_FIELD_PO; its ray grid covers
+ * of that function).  A superellipsoid takes a plane wave, rtw_trace with a square grid and RTW_FP64
+ * (far field or observe_radius beyond |center| + max(a, b, c) 3^((1 - 1/e) / 2)), and rtw_field in
+ * RTW_DENSE mode without RTW_FIELD_PO; its ray grid covers
  * the silhouette of the bounding ellipsoid of semi-axes (a, b, c) 3^((1 - 1/e) / 2), so n_rays
  * counts the rays inside that silhouette.  Other entry points answer RTW_ERR_UNSUPPORTED. */
 typedef struct {
@@ -132,7 +133,8 @@ typedef struct {
  * the projected cross-section (spacing h = sqrt(pi / (sqrt(det S) n_rays)), S the matrix of the
  * projected ellipse), unless spacing > 0 gives h directly.  p_max: orders 0..p_max, p_max <= 15.
  * observe_radius: 0 for the far field; R > 0 (square grids and RTW_FP64 only, R beyond |center| +
- * max semi-axis of every object, else RTW_ERR_ARG / RTW_ERR_UNSUPPORTED) records every ray where it
+ * max semi-axis of every object (of its bounding ellipsoid for a superellipsoid), else RTW_ERR_ARG /
+ * RTW_ERR_UNSUPPORTED) records every ray where it
  * crosses the sphere |M| = R about the origin instead: the field at a finite point M (Eqs.
  * IntVCRM, DivFactVCRM with the Gaussian curvature kappa_GM at M, and PhasePath to r_M), whose
  * last leg of length t contributes 1 / det(I + t Q') to the divergence factor, its focal lines to

@@ -619,9 +619,8 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
         if (obj->h[(size_t)i].src && (tp->grid != RTW_GRID_SQUARE || tp->precision != RTW_FP64))
             return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: a point source takes a square grid in double precision");
         if (obj->h[(size_t)i].shape_e != 1.0) {
-            if (tp->grid != RTW_GRID_SQUARE || tp->precision != RTW_FP64 || tp->observe_radius != 0.0)
-                return fail(RTW_ERR_UNSUPPORTED,
-                            "rtw_trace: a superellipsoid takes a square grid, double precision and the far field");
+            if (tp->grid != RTW_GRID_SQUARE || tp->precision != RTW_FP64)
+                return fail(RTW_ERR_UNSUPPORTED, "rtw_trace: a superellipsoid takes a square grid in double precision");
             super_shapes = true;
         }
     }
@@ -636,9 +635,12 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
         for (int i = 0; i < obj->count; ++i) {
             const rtw::host::ObjHost& h = obj->h[(size_t)i];
             const double rc = std::sqrt(h.c[0] * h.c[0] + h.c[1] * h.c[1] + h.c[2] * h.c[2]);
-            if (!(tp->observe_radius > rc + h.lmax))
-                return fail(RTW_ERR_ARG, "rtw_trace: observe_radius %g does not enclose object %d (|c| + a_max = %g)",
-                            tp->observe_radius, i, rc + h.lmax);
+            // radius about the centre that holds the body: the largest semi-axis, times 3^((1 - 1/e) / 2)
+            // for a superellipsoid (its bounding ellipsoid)
+            const double rb = h.lmax * std::sqrt(std::pow(3.0, 1.0 - 1.0 / h.shape_e));
+            if (!(tp->observe_radius > rc + rb))
+                return fail(RTW_ERR_ARG, "rtw_trace: observe_radius %g does not enclose object %d (|c| + %g)",
+                            tp->observe_radius, i, rb);
         }
     }
     cudaStream_t s = (cudaStream_t)stream;

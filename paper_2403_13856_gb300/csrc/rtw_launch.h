@@ -69,7 +69,7 @@ struct FieldArgs {
 // message returned by rtw_last_error() on the calling thread
 void set_last_error(const char* msg);
 
-// trace; super_shapes: the object set holds superellipsoids (double precision, far field)
+// trace; super_shapes: the object set holds superellipsoids (double precision)
 cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, bool aux, unsigned int* status,
                          cudaStream_t s, bool super_shapes = false);
 // persistent batched trace over work items; variant 1..kTraceVariants picks the block size and

@@ -196,6 +196,13 @@ __global__ void __launch_bounds__(128) trace_kernel_fp64_super(const ObjDev* __r
     trace_kernel_body<double, false, true>(objs, nobj, st, pmax, aux);
 }
 
+// the same, recording every ray where it crosses the sphere |M| = st.near_r
+__global__ void __launch_bounds__(128) trace_kernel_fp64_super_near(const ObjDev* __restrict__ objs, int nobj,
+                                                                    RaysDev st, int pmax, int aux)
+{
+    trace_kernel_body<double, true, true>(objs, nobj, st, pmax, aux);
+}
+
 // geometry, Fresnel and curvature in single precision; intersection points (polished by a
 // double-precision Newton step), optical path and phase in double precision
 __global__ void __launch_bounds__(128) trace_kernel_mixed(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
@@ -262,7 +269,9 @@ cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, b
     if (st.R == 0) return cudaSuccess;
     const int bs = 128;
     const long long nb = (st.R + bs - 1) / bs;
-    if (super_shapes)
+    if (super_shapes && st.near_r > 0.0)
+        trace_kernel_fp64_super_near<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    else if (super_shapes)
         trace_kernel_fp64_super<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     else if (st.near_r > 0.0)
         trace_kernel_fp64_near<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);

@@ -214,14 +214,35 @@ def test_super_with_point_source_ellipsoid(rtw, oracle_mod):
         assert scale > 0 and np.abs(got[k] - ref).max() <= 1e-6 * scale
 
 
+def test_super_field_on_a_sphere_of_points(rtw, oracle_mod):
+    """The superellipsoid's field at the points of the sphere |M| = 600 um (three components per
+    point; the superellipsoid kernel with records at the crossing points) against the oracle."""
+    sp = spec(2.0, jones=(0.6, 0.8j))
+    p_max, nt, nph, R, n_rays = 3, 32, 64, 600.0, 20_000
+    g = rtw.Object([rtw.ObjectSpec(**sp)])
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=n_rays, observe_radius=R))
+    out = torch.zeros((nt * nph, p_max + 1, 3), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_grid(nt, nph), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    ref, rm, hits = oracle_mod.Object(**sp).field_sphere(p_max, nt, nph, R, n_target=n_rays)
+    ref = oracle_mod.complex_field(ref)
+    assert hits > 2000
+    assert np.array_equal(mask.cpu().numpy(), rm)
+    scale = np.abs(ref).max()
+    err = np.abs(out.cpu().numpy() - ref).max()
+    print(f"superellipsoid, sphere of points: max |dE| / max |E| = {err / scale:.2e}")
+    assert scale > 0 and err <= 1e-6 * scale
+
+
 def test_super_arguments(rtw, oracle_mod):
     g = rtw.Object([rtw.ObjectSpec(**spec(2.0))])
     with pytest.raises(rtw.RTWError):  # fans stay ellipsoidal
         rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_FAN, n_rays=1000))
     with pytest.raises(rtw.RTWError):  # double precision only
         rtw.rtw_trace(g, rtw.trace_params(n_rays=1000, precision=rtw.RTW_MIXED))
-    with pytest.raises(rtw.RTWError):  # far field only
-        rtw.rtw_trace(g, rtw.trace_params(n_rays=1000, observe_radius=1000.0))
+    with pytest.raises(rtw.RTWError):  # 150 um encloses the semi-axes but not the bounding ellipsoid (158 um)
+        rtw.rtw_trace(g, rtw.trace_params(n_rays=1000, observe_radius=150.0))
     with pytest.raises(rtw.RTWError):  # not convex
         rtw.Object([rtw.ObjectSpec(**spec(0.7))])
     with pytest.raises(rtw.RTWError):  # plane waves only
