@@ -209,7 +209,6 @@ int or_make_object(const double* p, or_object* o)
     o->gc[0] = o->center[0];
     o->gc[1] = o->center[1];
     o->src = p[16] != 0.0;
-    if (o->src && o->shape_e != 1.0) return -1; /* point sources: ellipsoids only */
     if (o->src) {
         /* point source s: rays s + t v through X = c + x e1 + y e2 meet the surface where
          * (v.W g)^2 - (v.W v)(g.W g - 1) > 0 (g = c - s), i.e. v^T K v > 0 with
@@ -220,9 +219,10 @@ int or_make_object(const double* p, or_object* o)
             o->src_pos[i] = p[17 + i];
             g[i] = o->center[i] - o->src_pos[i];
         }
-        matvec3(o->W, g, Wg);
+        /* for a superellipsoid the same construction on its bounding ellipsoid (Wb = W for e = 1) */
+        matvec3(Wb, g, Wg);
         double gWg = dot3(g, Wg);
-        if (!(gWg > 1.0)) return -1; /* the source must lie outside the object */
+        if (!(gWg > 1.0)) return -1; /* the source must lie outside the object (its bounding ellipsoid) */
         double d = sqrt(dot3(g, g)), a[3] = {g[0] / d, g[1] / d, g[2] / d};
         double ref[3] = {1.0, 0.0, 0.0};
         if (fabs(a[0]) > 0.9) {
@@ -236,7 +236,7 @@ int or_make_object(const double* p, or_object* o)
         cross3(a, o->e1, o->e2);
         double K[3][3];
         for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) K[i][j] = Wg[i] * Wg[j] - (gWg - 1.0) * o->W[i][j];
+            for (int j = 0; j < 3; ++j) K[i][j] = Wg[i] * Wg[j] - (gWg - 1.0) * Wb[i][j];
         const double* E[2] = {o->e1, o->e2};
         double M2[2][2], b2[2], Kg[3], KE[3];
         matvec3(K, g, Kg);
@@ -745,18 +745,25 @@ int or_trace_ray(const or_object* o, double x, double y, int pmax, double* out, 
         }
         double dP = sqrt(dot3(v, v));
         for (int i = 0; i < 3; ++i) w.k[i] = v[i] / dP;
-        /* the quadratic is solved from the ray's point of closest approach to the centre, so that a
-         * distant source does not cancel the discriminant: rho = t0 + u */
-        double t0 = -dot3(w.k, g), f[3], Wk[3], Wf[3];
-        for (int i = 0; i < 3; ++i) f[i] = g[i] + t0 * w.k[i]; /* foot point minus centre */
-        matvec3(o->W, w.k, Wk);
-        matvec3(o->W, f, Wf);
-        double A = dot3(w.k, Wk), B = dot3(w.k, Wf), Cq = dot3(f, Wf) - 1.0;
-        double disc = B * B - A * Cq;
-        if (!(disc > 0.0)) return 0;
-        double rho = t0 + (-B - sqrt(disc)) / A;
-        if (!(rho > 0.0)) return 0;
-        for (int i = 0; i < 3; ++i) r[i] = o->center[i] + f[i] + (rho - t0) * w.k[i];
+        double rho;
+        if (o->shape_e != 1.0) {
+            /* superellipsoid: the smaller root of the line function from the source */
+            if (!entry_super(o, o->src_pos, w.k, &rho)) return 0;
+            for (int i = 0; i < 3; ++i) r[i] = o->src_pos[i] + rho * w.k[i];
+        } else {
+            /* the quadratic is solved from the ray's point of closest approach to the centre, so that
+             * a distant source does not cancel the discriminant: rho = t0 + u */
+            double t0 = -dot3(w.k, g), f[3], Wk[3], Wf[3];
+            for (int i = 0; i < 3; ++i) f[i] = g[i] + t0 * w.k[i]; /* foot point minus centre */
+            matvec3(o->W, w.k, Wk);
+            matvec3(o->W, f, Wf);
+            double A = dot3(w.k, Wk), B = dot3(w.k, Wf), Cq = dot3(f, Wf) - 1.0;
+            double disc = B * B - A * Cq;
+            if (!(disc > 0.0)) return 0;
+            rho = t0 + (-B - sqrt(disc)) / A;
+            if (!(rho > 0.0)) return 0;
+            for (int i = 0; i < 3; ++i) r[i] = o->center[i] + f[i] + (rho - t0) * w.k[i];
+        }
         w.n = 1.0;
         /* basis u1 = e1 made perpendicular to k, u2 = k x u1 */
         double ek = dot3(o->e1, w.k);

@@ -34,8 +34,9 @@ extern "C" {
 /* Object parameters, flat: a b c qw qx qy qz cx cy cz m lambda jre_x jim_x jre_y jim_y kind sx sy sz e.
  * e >= 1 is the superellipsoid exponent: the surface is sum_i |u_i|^(2e) = 1 with u the body coordinates
  * divided by the semi-axes (a, b, c); e = 1 is the ellipsoid.  For e > 1 the square ray grid covers
- * the silhouette of the bounding ellipsoid of semi-axes (a, b, c) 3^((1 - 1/e) / 2), fans are refused
- * and so are point sources.
+ * the silhouette of the bounding ellipsoid of semi-axes (a, b, c) 3^((1 - 1/e) / 2) (with a point source:
+ * the ellipse of the source's plane whose rays meet that ellipsoid, the source outside it), and fans
+ * are refused.
  * kind 0: plane wave along +z, Jones vector on (x, y).  kind 1: point source at (sx, sy, sz) outside
  * the object, field e^{ik rho} / rho p_perp at distance rho, p = jx e1 + jy e2 projected
  * perpendicular to the ray; rays leave the source through the plane through the centre

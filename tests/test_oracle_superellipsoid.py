@@ -260,12 +260,98 @@ def test_super_quarter_turn_field(oracle_mod):
     assert one.sum() < 0.06 * both.sum(), (one.sum(), both.sum())
 
 
+def source_frame(c, src):
+    """The grid plane's axes of a point source as the oracle's header defines them: a = (c - s)/|c - s|,
+    e1 = x (y when a is within 26 deg of x) made perpendicular to a, e2 = a x e1."""
+    a = np.asarray(c, float) - np.asarray(src, float)
+    a /= np.linalg.norm(a)
+    ref = np.array([0.0, 1.0, 0.0]) if abs(a[0]) > 0.9 else np.array([1.0, 0.0, 0.0])
+    e1 = ref - (ref @ a) * a
+    e1 /= np.linalg.norm(e1)
+    return e1, np.cross(a, e1)
+
+
+@pytest.mark.parametrize("e", [1.5, 3.0])
+def test_super_point_source_geometry_bruteforce(oracle_mod, e):
+    """A point source lighting a tilted superellipsoid: rays from the source through points of the
+    grid plane, orders 0..3, exit directions, exit points and optical paths (from the source) against
+    the brute-force tracer."""
+    semi, center, src = (12.0, 10.0, 8.0), (0.7, -0.4, 0.3), (15.0, -10.0, -60.0)
+    o = oracle_mod.Object(*semi, quat=QUAT, center=center, m=M_WATER, wavelength=LAM, shape_e=e, source=src)
+    body = Body(semi, QUAT, center, e)
+    e1, e2 = source_frame(center, src)
+    rng = np.random.default_rng(17)
+    checked = 0
+    for _ in range(70):
+        x, y = rng.uniform(-16, 16, 2)
+        rec, _, hit = o.trace_ray(x, y, 3)
+        v = np.asarray(center) + x * e1 + y * e2 - np.asarray(src)
+        k = v / np.linalg.norm(v)
+        t = body.root(np.asarray(src, float), k, True)
+        assert hit == (t is not None)
+        if t is None:
+            continue
+        r1 = np.asarray(src, float) + t * k
+        n1 = body.normal(r1)
+        ref = [(reflect(k, n1), r1.copy(), t)]
+        kk = refract(k, n1, 1.0, M_WATER)
+        r, path = r1, t
+        for p in range(1, 4):
+            d = body.root(r, kk, False)
+            if d is None:
+                break
+            r = r + d * kk
+            path += M_WATER * d
+            n = body.normal(r)
+            kt = refract(kk, n, M_WATER, 1.0)
+            ref.append(None if kt is None else (kt, r.copy(), path))
+            kk = reflect(kk, n)
+        for p, rp in enumerate(ref):
+            if rp is None:
+                assert rec[p, oracle_mod.VALID] == 0
+                continue
+            assert rec[p, oracle_mod.VALID] == 1
+            assert np.allclose(rec[p, oracle_mod.S:oracle_mod.S + 3], rp[0], rtol=0, atol=1e-8)
+            assert np.allclose(rec[p, oracle_mod.REXIT:oracle_mod.REXIT + 3], rp[1], rtol=0, atol=1e-7)
+            assert rec[p, oracle_mod.PATH] == pytest.approx(rp[2], abs=1e-7)
+            checked += 1
+    assert checked > 60
+
+
+def test_super_point_source_e1_limit(oracle_mod):
+    """e = 1 + 1e-12 with a point source reproduces the ellipsoid's closed-form entry from the
+    source (and its lit ellipse on the grid plane)."""
+    kw = dict(quat=QUAT, m=M_WATER, wavelength=LAM, jones=(0.3, 0.9 + 0.3j), source=(20.0, -5.0, -80.0))
+    oq = oracle_mod.Object(12.0, 10.0, 8.0, **kw)
+    os_ = oracle_mod.Object(12.0, 10.0, 8.0, shape_e=1.0 + 1e-12, **kw)
+    assert np.allclose(oq.square_grid(n_target=5000), os_.square_grid(n_target=5000), rtol=1e-9, atol=1e-9)
+    rng = np.random.default_rng(4)
+    n = 0
+    for _ in range(60):
+        x, y = rng.uniform(-12, 12, 2)
+        ra, _, ha = oq.trace_ray(x, y, 4)
+        rb, _, hb = os_.trace_ray(x, y, 4)
+        assert ha == hb
+        if not ha:
+            continue
+        for p in range(5):
+            if ra[p, oracle_mod.VALID] == 0:
+                continue
+            for f, w in [(oracle_mod.S, 3), (oracle_mod.REXIT, 3), (oracle_mod.F, 6)]:
+                a, b = ra[p, f:f + w], rb[p, f:f + w]
+                assert np.allclose(a, b, rtol=0, atol=1e-8 * max(1.0, np.abs(a).max())), (p, f)
+            assert ra[p, oracle_mod.PSI] == pytest.approx(rb[p, oracle_mod.PSI], abs=1e-7)
+            n += 1
+    assert n > 100
+
+
 def test_super_refusals(oracle_mod):
-    """e < 1 (not convex) is refused, and so are point sources and fans on a superellipsoid."""
+    """e < 1 (not convex) is refused, and so are a source inside the bounding ellipsoid and fans on a
+    superellipsoid."""
     with pytest.raises(ValueError):
         oracle_mod.Object(10.0, 9.0, 8.0, shape_e=0.8)
-    with pytest.raises(ValueError):
-        oracle_mod.Object(10.0, 9.0, 8.0, shape_e=2.0, source=(0.0, 0.0, -100.0))
+    with pytest.raises(ValueError):  # outside the body (c = 8) but inside its bounding ellipsoid (8 x 3^(1/4))
+        oracle_mod.Object(10.0, 9.0, 8.0, shape_e=2.0, source=(0.0, 0.0, -10.2))
     o = oracle_mod.Object(10.0, 9.0, 8.0, shape_e=2.0)
     with pytest.raises(RuntimeError):
         o.field_fan(100, np.linspace(0.1, 3.0, 8), 1)
