@@ -97,11 +97,11 @@ extern "C" {
  * with (u, v, w) the body coordinates divided by (a, b, c), a smooth convex body between the
  * ellipsoid and the box (the Introduction's principle (iii): the wavefront equation needs of the
  * surface only its normal and curvature matrix at each point, here from the gradient and Hessian
- * of that function).  A superellipsoid takes a plane wave, rtw_trace with a square grid and RTW_FP64
- * (far field or observe_radius beyond |center| + max(a, b, c) 3^((1 - 1/e) / 2)), and rtw_field in
- * RTW_DENSE mode without RTW_FIELD_PO; its ray grid covers
- * the silhouette of the bounding ellipsoid of semi-axes (a, b, c) 3^((1 - 1/e) / 2), so n_rays
- * counts the rays inside that silhouette.  Other entry points answer RTW_ERR_UNSUPPORTED. */
+ * of that function).  A superellipsoid takes rtw_trace with a square grid and RTW_FP64 (far field
+ * or observe_radius beyond |center| + max(a, b, c) 3^((1 - 1/e) / 2)), a plane wave or a point source
+ * outside its bounding ellipsoid of semi-axes (a, b, c) 3^((1 - 1/e) / 2), and rtw_field in
+ * RTW_DENSE mode without RTW_FIELD_PO; its ray grid covers the rays that meet that bounding
+ * ellipsoid, so n_rays counts those.  Other entry points answer RTW_ERR_UNSUPPORTED. */
 typedef struct {
     double a, b, c;
     double quat[4];
@@ -175,8 +175,8 @@ typedef struct rtw_rays rtw_rays;
  * them: quadric matrix W = R diag(a^-2, b^-2, c^-2) R^T, projected ellipse S (Schur complement of
  * W_zz), k0 = 2 pi / lambda.  *out receives a handle owned by the caller until
  * rtw_destroy_object.  Errors: RTW_ERR_ARG (null, count < 1, a, b, c, lambda <= 0, m <= 0,
- * m == 1, |quat| != 1, shape_e neither 0 nor >= 1), RTW_ERR_UNSUPPORTED (m_im != 0, dir != (0,0,1),
- * a superellipsoid with a point source), RTW_ERR_CUDA,
+ * m == 1, |quat| != 1, shape_e neither 0 nor >= 1, a source inside the object or the bounding
+ * ellipsoid of a superellipsoid), RTW_ERR_UNSUPPORTED (m_im != 0, dir != (0,0,1)), RTW_ERR_CUDA,
  * RTW_ERR_NOMEM.  Synchronous. */
 int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident* inc, rtw_object** out);
 void rtw_destroy_object(rtw_object* obj);

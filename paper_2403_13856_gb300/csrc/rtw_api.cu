@@ -480,8 +480,6 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
         if (!(se >= 1.0) || !std::isfinite(se))
             return fail(RTW_ERR_ARG, "object %d: shape exponent %g (0 or 1: ellipsoid, > 1: superellipsoid)", i,
                         d.shape_e);
-        if (se != 1.0 && w.kind != RTW_INCIDENT_PLANE)
-            return fail(RTW_ERR_UNSUPPORTED, "object %d: a superellipsoid takes a plane wave", i);
         o.shape_e = se;
         o.a[0] = d.a;
         o.a[1] = d.b;
@@ -515,13 +513,15 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
         o.S[0][1] = o.W[0][1] - o.W[0][2] * o.W[1][2] / o.W[2][2];
         o.S[1][0] = o.S[0][1];
         o.S[1][1] = o.W[1][1] - o.W[1][2] * o.W[1][2] / o.W[2][2];
-        if (se != 1.0) {
-            // the superellipsoid lies inside the ellipsoid of semi-axes a_i 3^((1 - 1/e) / 2) (power-mean
-            // inequality); its silhouette bounds the ray grid
-            const double g2 = std::pow(3.0, 1.0 - 1.0 / se);
+        // a superellipsoid lies inside the ellipsoid of semi-axes a_i 3^((1 - 1/e) / 2) (power-mean
+        // inequality), Wb = W / g2; the rays that meet it bound the ray grid (Wb = W for e = 1)
+        const double g2 = se != 1.0 ? std::pow(3.0, 1.0 - 1.0 / se) : 1.0;
+        double Wb[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) Wb[r][c] = o.W[r][c] / g2;
+        if (se != 1.0)
             for (int r = 0; r < 2; ++r)
                 for (int c = 0; c < 2; ++c) o.S[r][c] /= g2;
-        }
         o.gc[0] = o.c[0];
         o.gc[1] = o.c[1];
         o.src = w.kind == RTW_INCIDENT_POINT;
@@ -534,9 +534,10 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
                 o.src_pos[k] = w.source[k];
                 g[k] = o.c[k] - w.source[k];
             }
-            for (int r = 0; r < 3; ++r) Wg[r] = o.W[r][0] * g[0] + o.W[r][1] * g[1] + o.W[r][2] * g[2];
+            for (int r = 0; r < 3; ++r) Wg[r] = Wb[r][0] * g[0] + Wb[r][1] * g[1] + Wb[r][2] * g[2];
             const double gWg = g[0] * Wg[0] + g[1] * Wg[1] + g[2] * Wg[2];
-            if (!(gWg > 1.0)) return fail(RTW_ERR_ARG, "object %d: the source lies inside the object", i);
+            if (!(gWg > 1.0))
+                return fail(RTW_ERR_ARG, "object %d: the source lies inside the object (its bounding ellipsoid)", i);
             const double gd = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             const double ax[3] = {g[0] / gd, g[1] / gd, g[2] / gd};
             const double ref[3] = {std::fabs(ax[0]) > 0.9 ? 0.0 : 1.0, std::fabs(ax[0]) > 0.9 ? 1.0 : 0.0, 0.0};
@@ -553,7 +554,7 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
             o.e2[2] = ax[0] * o.e1[1] - ax[1] * o.e1[0];
             double K[3][3];
             for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c) K[r][c] = Wg[r] * Wg[c] - (gWg - 1.0) * o.W[r][c];
+                for (int c = 0; c < 3; ++c) K[r][c] = Wg[r] * Wg[c] - (gWg - 1.0) * Wb[r][c];
             auto Kv = [&](const double* v, double* out3) {
                 for (int r = 0; r < 3; ++r) out3[r] = K[r][0] * v[0] + K[r][1] * v[1] + K[r][2] * v[2];
             };

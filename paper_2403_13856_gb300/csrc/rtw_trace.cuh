@@ -402,18 +402,19 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
     int sT = -1;
     T pdet = T(1), cosprod = T(1);
     double path;
-    if constexpr (kSuper) {
-        const double kz[3] = {0.0, 0.0, 1.0};
-        double t;
-        if (!super_entry(o, r, kz, t)) return;
-        r[2] += t;
-        path = r[2];
-    } else if (!o.src_mode) {
-        const T kz[3] = {T(0), T(0), T(1)};
-        bool ok;
-        const double t = chord_to_surface<T>(o, W, r, kz, T(-1), &ok);
-        if (!ok) return;
-        r[2] += t;
+    if (!o.src_mode) {
+        if constexpr (kSuper) {
+            const double kz[3] = {0.0, 0.0, 1.0};
+            double t;
+            if (!super_entry(o, r, kz, t)) return;
+            r[2] += t;
+        } else {
+            const T kz[3] = {T(0), T(0), T(1)};
+            bool ok;
+            const double t = chord_to_surface<T>(o, W, r, kz, T(-1), &ok);
+            if (!ok) return;
+            r[2] += t;
+        }
         path = r[2];  // phase of the incident plane wave at the first point (zero at the origin)
     } else if constexpr (std::is_same<T, double>::value) {
         // point source s: the ray toward X = c + x e1 + y e2 meets the surface at distance rho with
@@ -428,19 +429,28 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         }
         const double dP = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), iP = 1.0 / dP;
         const double k[3] = {v[0] * iP, v[1] * iP, v[2] * iP};
-        const double t0 = -(k[0] * g[0] + k[1] * g[1] + k[2] * g[2]);
-        const double f[3] = {g[0] + t0 * k[0], g[1] + t0 * k[1], g[2] + t0 * k[2]};
-        double wkx, wky, wkz, wfx, wfy, wfz;
-        symv(o.W, k[0], k[1], k[2], wkx, wky, wkz);
-        symv(o.W, f[0], f[1], f[2], wfx, wfy, wfz);
-        const double A = k[0] * wkx + k[1] * wky + k[2] * wkz, B = k[0] * wfx + k[1] * wfy + k[2] * wfz;
-        const double Cq = f[0] * wfx + f[1] * wfy + f[2] * wfz - 1.0;
-        const double disc = B * B - A * Cq;
-        if (!(disc > 0.0)) return;
-        const double u = (-B - sqrt(disc)) / A, rho = t0 + u;
-        if (!(rho > 0.0)) return;
+        double rho;
+        if constexpr (kSuper) {
+            // superellipsoid: the smaller root of the line function from the source
+            if (!super_entry(o, o.src, k, rho)) return;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) r[i] = o.c[i] + f[i] + u * k[i];
+            for (int i = 0; i < 3; ++i) r[i] = o.src[i] + rho * k[i];
+        } else {
+            const double t0 = -(k[0] * g[0] + k[1] * g[1] + k[2] * g[2]);
+            const double f[3] = {g[0] + t0 * k[0], g[1] + t0 * k[1], g[2] + t0 * k[2]};
+            double wkx, wky, wkz, wfx, wfy, wfz;
+            symv(o.W, k[0], k[1], k[2], wkx, wky, wkz);
+            symv(o.W, f[0], f[1], f[2], wfx, wfy, wfz);
+            const double A = k[0] * wkx + k[1] * wky + k[2] * wkz, B = k[0] * wfx + k[1] * wfy + k[2] * wfz;
+            const double Cq = f[0] * wfx + f[1] * wfy + f[2] * wfz - 1.0;
+            const double disc = B * B - A * Cq;
+            if (!(disc > 0.0)) return;
+            const double u = (-B - sqrt(disc)) / A;
+            rho = t0 + u;
+            if (!(rho > 0.0)) return;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) r[i] = o.c[i] + f[i] + u * k[i];
+        }
         k0v = k[0];
         k1v = k[1];
         k2v = k[2];
@@ -655,7 +665,7 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
             if (kJ) { w.t11 = Te11; w.t12 = Te12; w.t21 = lt21; w.t22 = lt22; }
             w.ep[0] = ex; w.ep[1] = ey; w.ep[2] = ez;
             w.pdet = 1.0;
-            w.cosprod = 1.0;
+            w.cosprod = cosprod;  // 1 for a plane wave; |det T| of the start for a point source
             w.path = path;
             w.r[0] = r[0]; w.r[1] = r[1]; w.r[2] = r[2];
             w.nf_legs = 0;

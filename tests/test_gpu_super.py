@@ -30,10 +30,12 @@ def spec(e, **kw):
     return d
 
 
-def test_super_records_match_oracle(rtw, oracle_mod):
+@pytest.mark.parametrize("source", [None, (30.0, -20.0, -400.0)])
+def test_super_records_match_oracle(rtw, oracle_mod, source):
     """Every third ray of a square grid of about 2e3 rays, orders 0..3: direction, field, phase and
-    flags against the oracle's ray at the same grid point."""
-    sp = spec(2.0)
+    flags (near-caustic included: the flat faces bring order 0 of a point source near the cap)
+    against the oracle's ray at the same grid point."""
+    sp = spec(2.0) if source is None else spec(2.0, source=source)
     p_max = 3
     g = rtw.Object([rtw.ObjectSpec(**sp, jones=(0.6, 0.8j))])
     o = oracle_mod.Object(**sp, jones=(0.6, 0.8j))
@@ -235,6 +237,28 @@ def test_super_field_on_a_sphere_of_points(rtw, oracle_mod):
     assert scale > 0 and err <= 1e-6 * scale
 
 
+@pytest.mark.parametrize("source", [(30.0, -20.0, -400.0), (0.0, 0.0, -3000.0)])
+def test_super_point_source_field(rtw, oracle_mod, source):
+    """A point source lighting the superellipsoid (e = 2), about 2e4 rays through the source's grid
+    plane, orders 0..4, 48 x 96 directions, against the oracle."""
+    sp = spec(2.0, jones=(1.0, 0.0), source=source)
+    p_max, nt, nph, n_rays = 4, 48, 96, 20_000
+    g = rtw.Object([rtw.ObjectSpec(**sp)])
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=n_rays))
+    out = torch.zeros((nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_grid(nt, nph), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    ref, rm, hits, _ = oracle_mod.Object(**sp).field_grid(p_max, nt, nph, n_target=n_rays)
+    ref = oracle_mod.complex_field(ref)
+    assert hits > 3000
+    assert np.array_equal(mask.cpu().numpy(), rm)
+    scale = np.abs(ref).max()
+    err = np.abs(out.cpu().numpy() - ref).max()
+    print(f"superellipsoid, source {source}: max |dF| / max |F| = {err / scale:.2e}")
+    assert scale > 0 and err <= 1e-6 * scale
+
+
 def test_super_arguments(rtw, oracle_mod):
     g = rtw.Object([rtw.ObjectSpec(**spec(2.0))])
     with pytest.raises(rtw.RTWError):  # fans stay ellipsoidal
@@ -245,8 +269,8 @@ def test_super_arguments(rtw, oracle_mod):
         rtw.rtw_trace(g, rtw.trace_params(n_rays=1000, observe_radius=150.0))
     with pytest.raises(rtw.RTWError):  # not convex
         rtw.Object([rtw.ObjectSpec(**spec(0.7))])
-    with pytest.raises(rtw.RTWError):  # plane waves only
-        rtw.Object([rtw.ObjectSpec(**spec(2.0, source=(0.0, 0.0, -1000.0)))])
+    with pytest.raises(rtw.RTWError):  # a source outside the body but inside its bounding ellipsoid
+        rtw.Object([rtw.ObjectSpec(**spec(2.0, source=(0.0, 0.0, -100.0)))])
     with pytest.raises(rtw.RTWError):
         rtw.rtw_trace_points(g, 0, torch.zeros((4, 2), dtype=torch.float64, device="cuda"), 1)
     rays = rtw.rtw_trace(g, rtw.trace_params(n_rays=1000, p_max=1))
