@@ -283,10 +283,26 @@ __device__ __forceinline__ bool super_bound(const ObjDev& o, const double u[3], 
     const double C = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] - o.bound2;
     const double disc = B * B - A * C;
     if (!(disc > 0.0)) return false;
-    const double sq = sqrt(disc);
-    t_in = (-B - sq) / A;
-    t_out = (-B + sq) / A;
+    const double sq = sqrt(disc), iA = 1.0 / A;
+    t_in = (-B - sq) * iA;
+    t_out = (-B + sq) * iA;
     return true;
+}
+
+// reciprocals of the three body rates, from one division when none is zero (a bracket needs no
+// more than their rounding)
+__device__ __forceinline__ void super_inv_rates(const double kap[3], double inv[3])
+{
+    const double p01 = kap[0] * kap[1], pall = p01 * kap[2];
+    if (pall != 0.0) {
+        const double r = 1.0 / pall;
+        inv[0] = r * kap[1] * kap[2];
+        inv[1] = r * kap[0] * kap[2];
+        inv[2] = r * p01;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) inv[i] = kap[i] != 0.0 ? 1.0 / kap[i] : 0.0;
+    }
 }
 
 // entry of the ray r0 + t k into the body: Newton from the entry of the bracket (box and bounding
@@ -298,12 +314,14 @@ __device__ __forceinline__ bool super_entry(const ObjDev& o, const double r0[3],
     super_line(o, r0, k, u, kap);
     double tin, tout;
     if (!super_bound(o, u, kap, tin, tout)) return false;
+    double inv[3];
+    super_inv_rates(kap, inv);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         if (kap[i] == 0.0) {
             if (!(fabs(u[i]) < 1.0)) return false;
         } else {
-            const double ta = (-1.0 - u[i]) / kap[i], tb = (1.0 - u[i]) / kap[i];
+            const double ta = (-1.0 - u[i]) * inv[i], tb = (1.0 - u[i]) * inv[i];
             tin = fmax(tin, fmin(ta, tb));
             tout = fmin(tout, fmax(ta, tb));
         }
@@ -335,9 +353,11 @@ __device__ __forceinline__ double super_chord(const ObjDev& o, const double r[3]
     super_line(o, r, k, u, kap);
     double tin, t;
     if (!super_bound(o, u, kap, tin, t)) return 0.0;
+    double inv[3];
+    super_inv_rates(kap, inv);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        if (kap[i] != 0.0) t = fmin(t, (copysign(1.0, kap[i]) - u[i]) / kap[i]);
+        if (kap[i] != 0.0) t = fmin(t, (copysign(1.0, kap[i]) - u[i]) * inv[i]);
     if (!(t > 0.0)) return 0.0;
     double prev = INFINITY;
     for (int it = 0; it < 96; ++it) {
