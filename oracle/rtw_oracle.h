@@ -16,7 +16,7 @@
  *   "Strategy of RTW"             : trace over intermediate variables t, then interpolate
  *   "Diffraction effect correction": physical-optics integration near caustics
  *
- * Conventions (readings of the paper, all listed in the design doc):
+ * Conventions (readings of the paper):
  *   incident plane wave along +z, E_inc = (jones_x, jones_y) e^{i k0 z}, time factor e^{-i w t};
  *   n outward normal of the object; C > 0 for a convex surface; Q = 1/R with R > 0 diverging;
  *   every focal line multiplies the field by e^{-i pi/2};

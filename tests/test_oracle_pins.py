@@ -210,8 +210,10 @@ def test_sphere_closed_forms(oracle_mod, m, deg):
     assert rec[0, oracle_mod.PSI] == pytest.approx(-2 * o.k0 * a * math.cos(i), abs=1e-11)
 
 
-def test_survey_worked_values(oracle_mod):
-    """a = 10 um, m = 1.333, i = 45 deg (the worked example of the closed forms)."""
+def test_sphere_worked_values(oracle_mod):
+    """a = 10 um, m = 1.333, i = 45 deg: the sphere's closed forms of the test above (deviation,
+    divergence factor a^2 sin i cos i / (sin theta |d theta / d i|), optical path), evaluated by hand
+    to six figures, as a fixed cross-check of the oracle's orders 1..3."""
     a = 10.0
     o = sphere(oracle_mod, a=a)
     rec, _ = rec_at(oracle_mod, o, a * math.sin(math.radians(45.0)), pmax=3)
