@@ -163,7 +163,7 @@ def fp64_peak_gflops(torch):
     return 2.0 * n ** 3 / best / 1e9
 
 
-def cpu_baseline(rows: int):
+def cpu_baseline(rows: int, single_thread_rows: int = 0):
     """The FP64 oracle on a band of `rows` rows of cells of the same ray grid (all columns, all
     orders, same direction grid; rows <= 0: every row, the whole workload), OpenMP over the host's
     cores."""
@@ -193,9 +193,24 @@ def cpu_baseline(rows: int):
     rec = o.trace_rays(np.stack([X.ravel(), Y.ravel()], 1), 0, threads=cores)
     nhit = int((rec[:, 0, oracle.VALID] != 0).sum())
     units = nhit * (cfg["p_max"] + 1)
-    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    line = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{rows + 1} of {ny} grid rows ({nhit} rays), all {cfg['p_max'] + 1} orders, "
                       f"{cfg['n_theta']}x{cfg['n_phi']} directions, trace + field, {dt:.1f} s"}
+    if single_thread_rows > 0:
+        # the same oracle on one thread, on a central band of rows (bounded to a few seconds)
+        r1 = min(single_thread_rows, ny - 1)
+        j0 = ny // 2 - r1 // 2
+        t1 = time.perf_counter()
+        o.field_grid(cfg["p_max"], cfg["n_theta"], cfg["n_phi"], n_target=cfg["n_rays"], window=[0, nx - 1, j0, j0 + r1],
+                     threads=1)
+        d1 = time.perf_counter() - t1
+        ys1 = yc + (np.arange(j0, j0 + r1 + 1) + 0.5 - ny // 2) * h
+        X1, Y1 = np.meshgrid(xs, ys1)
+        rec1 = o.trace_rays(np.stack([X1.ravel(), Y1.ravel()], 1), 0, threads=cores)
+        n1 = int((rec1[:, 0, oracle.VALID] != 0).sum())
+        line["single_thread"] = {"value": n1 * (cfg["p_max"] + 1) / d1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{r1 + 1} central grid rows ({n1} rays), {d1:.1f} s"}
+    return line
 
 
 def reference_arm(args, rank, world):
@@ -485,7 +500,8 @@ def bench_ellipsoid(args, rank, world, local, dist):
     clocks = clk.summary()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(args.cpu_sample_rows)  # default: the whole workload (about 1 s on 16 cores)
+        # default: the whole workload on every core (about 1 s on 16 cores), and one thread on 150 rows
+        cpu = cpu_baseline(args.cpu_sample_rows, single_thread_rows=150)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
