@@ -232,10 +232,11 @@ int rtw_trace_points(const rtw_object* obj, int index, const double* xy, int64_t
  * and field_out is [objects][directions][orders or 1][3] complex128 (E_r, E_theta, E_phi), the field
  * at M for a unit incident wave (the ray through M need not be radial); mode RTW_DENSE only, no PO.
  * mask_out (device, optional): [objects][directions] uint8.  Asynchronous, except with superellipsoids
- * among the objects: their ray branches per direction multiply with the order (rounded edges fan
- * the rays out again at every internal reflection), so the field is summed in slices of ray-grid
- * rows sized to the hit list, each classified first and its pair count read back (the stream is
- * synchronised once per slice); RTW_ERR_CAPACITY when a single row does not fit. */
+ * among the objects (their ray branches per direction multiply with the order: rounded edges fan
+ * the rays out again at every internal reflection) or direction grids of more than about 2^27 / (p_max
+ * + 1) directions: the field is then summed in slices of ray-grid rows sized to the hit list, each
+ * classified first and its pair count read back (the stream is synchronised once per slice);
+ * RTW_ERR_CAPACITY when a single row does not fit. */
 int rtw_field(const rtw_rays* rays, const rtw_dirs* dirs, int mode, int flags, void* field_out,
               uint8_t* mask_out, void* stream);
 

@@ -188,6 +188,9 @@ GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs)
     const long long ndir = dir_count(dirs);
     g.group = (int)std::max<long long>(1, std::min<long long>(nobj, (1ll << 28) / std::max(1ll, 4 * ndir * np)));
     for (int oi = 0; oi < nobj; ++oi) g.super_shapes = g.super_shapes || objs[oi].shape_e != 1.0;
+    // sliced runs: superellipsoids (hundreds of branches per direction), or direction grids so fine
+    // that four pairs per direction and order no longer fit the largest hit list
+    g.sliced = g.super_shapes || 4 * ndir * np * (long long)g.group + (1 << 20) > (1ll << 29);
     for (int g0 = 0; g0 < nobj; g0 += g.group) {
         long long cells = 0;
         for (int oi = g0; oi < std::min(nobj, g0 + g.group); ++oi) {
@@ -327,7 +330,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
             b.nout = nout;
             return RTW_OK;
         };
-        if (!g.super_shapes) {
+        if (!g.sliced) {
             GridBatch b;
             int rc = batch(g.windowed, win, b);
             if (rc != RTW_OK) return rc;
@@ -367,12 +370,15 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                 RTW_CUDA(cudaMemcpyAsync(&want, w.nhit, sizeof(want), cudaMemcpyDeviceToHost, s));
                 RTW_CUDA(cudaStreamSynchronize(s));
                 if (b.total > 0 && want > w.hit_cap) {
-                    if (sl.second - sl.first <= 1)
+                    const long long h = sl.second - sl.first;
+                    if (h <= 1)
                         return fail(RTW_ERR_CAPACITY, "rtw_field: one row of the ray grid wants %u (triangle, "
                                     "direction) pairs, more than the %u of the hit list", want, w.hit_cap);
-                    const long long mid = sl.first + (sl.second - sl.first) / 2;
-                    todo.emplace_back(mid, sl.second);
-                    todo.emplace_back(sl.first, mid);
+                    // the count is exact: split into enough equal slices for three quarters of the list
+                    // each (uneven rows split again), taken in increasing row order
+                    const long long k = std::min(h, std::max(2ll, (long long)(want / (0.75 * w.hit_cap)) + 1));
+                    for (long long q = k - 1; q >= 0; --q)
+                        todo.emplace_back(sl.first + h * q / k, sl.first + h * (q + 1) / k);
                     continue;
                 }
                 RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,

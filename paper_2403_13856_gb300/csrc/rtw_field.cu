@@ -266,6 +266,7 @@ struct HitArgs {
     unsigned int* dir;        // direction index | kHitClose
     unsigned int* n;
     unsigned int cap;
+    int raise;                // 1: an overflow is an error; 0: the host reads *n and splits the run
 };
 
 // warp-aggregated append of one (triangle, direction) pair
@@ -280,7 +281,7 @@ __device__ __forceinline__ void push_hit(const HitArgs& h, unsigned int* status,
     if (b < h.cap) {
         h.tri[b] = code;
         h.dir[b] = dir;
-    } else {
+    } else if (h.raise) {
         atomicOr(status, kStatusCapacity);
     }
 }
@@ -1184,7 +1185,7 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirS
     if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
     const int cb = classify_block > 0 ? classify_block : bs;
-    HitArgs h{hit_tri, hit_dir, nhit, hit_cap};
+    HitArgs h{hit_tri, hit_dir, nhit, hit_cap, stage == kFieldClassify ? 0 : 1};
     // fixed grids walk the lists: 32 blocks per SM for the large triangles, 16 for the hits
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);

@@ -62,7 +62,8 @@ struct GridPlan {
     int group = 1;
     long long max_group_cells = 0;  // cells x orders of the largest group
     bool windowed = false;
-    bool super_shapes = false;      // the objects include superellipsoids: sliced runs (grid_field_run)
+    bool super_shapes = false;      // the objects include superellipsoids
+    bool sliced = false;            // run in row slices sized to the hit list (grid_field_run)
 };
 GridPlan plan_grid(const ObjDev* objs, int nobj, int np, const rtw_dirs* dirs);
 
@@ -97,8 +98,8 @@ int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t 
 // are the same table on the host and the device.  Adds into out, which the caller cleared:
 // [objects][directions][nout][4] doubles.  mask_out (may be null): [objects][directions] bytes.
 // newton = 1 replaces every interpolated hit by the exact ray found by Newton steps.
-// With superellipsoids (g.super_shapes) the number of ray branches per direction grows quickly with
-// the order, so each group is run in slices of ray-grid rows: a slice is classified, the count of
+// With superellipsoids (the number of ray branches per direction grows quickly with the order) or
+// direction grids too fine for the hit list (g.sliced), each group is run in slices of ray-grid rows: a slice is classified, the count of
 // (triangle, direction) pairs it wants is read back (the stream is synchronised), and a slice that
 // does not fit the hit list is halved before any of its hits is summed.  slice_rows (optional, in
 // and out): the slice height to start from (0: the whole grid); receives the smallest height that

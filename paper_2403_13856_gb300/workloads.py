@@ -29,6 +29,15 @@ ELLIPSOID = dict(a=120.0, b=100.0, c=80.0, quat=quat_about_x(20.0), m=WATER, wav
 ELLIPSOID_GRID = dict(n_rays=4_000_000, p_max=5, n_theta=512, n_phi=1024)
 
 
+# Oblate spheroid a = b = 100, c = 90 um lit along its x axis (the spheroid of the paper's Fig. 3
+# setting): the incident wave travels along +z, so the body is turned by -90 deg about y, which
+# carries its x axis onto z.
+SPHEROID_SIDE = dict(a=100.0, b=100.0, c=90.0, quat=(math.cos(math.radians(-45.0)), 0.0, math.sin(math.radians(-45.0)), 0.0),
+                     m=WATER, wavelength=HE_NE)
+# its 3-D pattern at 0.01 deg over the whole sphere of directions: 4e6 rays, orders 0..5
+SPHEROID_PATTERN = dict(n_rays=4_000_000, p_max=5, n_theta=18_000, n_phi=36_000)
+
+
 def unit_quat(w: float, x: float, y: float, z: float):
     n = math.sqrt(w * w + x * x + y * y + z * z)
     return (w / n, x / n, y / n, z / n)
