@@ -470,6 +470,36 @@ def bench_ellipsoid(args, rank, world, local, dist):
             "kernel": "po2d_sum_kernel (FP64: one sincos per ray-direction term)"}
     del ra, sph, out_po, dirs_po
 
+    # the paper's Fig. 3 setting: the oblate spheroid a = b = 100, c = 90 um lit along its x axis, its
+    # whole 3-D pattern at 0.01 deg (18000 x 36000 directions), 4e6 rays, orders 0..5 (the paper's
+    # own timing of this pattern, 9.4 min on a desktop CPU with an unstated ray count, is context)
+    cf = W.SPHEROID_PATTERN
+    sph3 = rtw.Object([rtw.ObjectSpec(**W.SPHEROID_SIDE, jones=(0.0, 1.0))])
+    tp3 = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cf["p_max"], n_rays=cf["n_rays"])
+    r3 = rtw.rtw_trace(sph3, tp3, stream=stream)
+    nd3 = cf["n_theta"] * cf["n_phi"]
+    out3 = torch.zeros((nd3, 1, 2), dtype=torch.complex128, device="cuda")
+    mask3 = torch.zeros(nd3, dtype=torch.uint8, device="cuda")
+    dirs3 = rtw.dirs_grid(cf["n_theta"], cf["n_phi"])
+    rtw.rtw_trace(sph3, tp3, r3, stream=stream)
+    rtw.rtw_field(r3, dirs3, out3, mask3, stream=stream)  # warm-up (also finds the slice height)
+    ev3 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(2)]
+    for e in ev3:
+        e[0].record(stream)
+        rtw.rtw_trace(sph3, tp3, r3, stream=stream)
+        e[1].record(stream)
+        rtw.rtw_field(r3, dirs3, out3, mask3, stream=stream)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    rtw.rtw_sync_status(stream)
+    t3 = statistics.median([e[0].elapsed_time(e[2]) for e in ev3])
+    fig3 = {"workload": "oblate spheroid a=b=100, c=90 um, m=1.333, incidence along its x axis, 4e6 rays, "
+                        "p=0..5, 18000x36000 (theta,phi) = 0.01 deg over the whole sphere, FP64",
+            "s_per_pattern": t3 / 1e3, "ms_trace": statistics.median([e[0].elapsed_time(e[1]) for e in ev3]),
+            "directions_per_s": nd3 / (t3 / 1e3), "masked_fraction": float((mask3 != 0).float().mean().item()),
+            "paper_context": "9.4 min for this pattern on an Intel i9-13900KS (CPU, ray count not stated)"}
+    del r3, out3, mask3, sph3
+
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
     host_mask = torch.empty(ndir, dtype=torch.uint8, pin_memory=True)
@@ -527,6 +557,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "point_source": point,
         "superellipsoid": superellipsoid,
         "po2d_rainbow": po2d,
+        "paper_fig3_pattern": fig3,
     }
     if cpu:
         line["cpu_baseline"] = cpu

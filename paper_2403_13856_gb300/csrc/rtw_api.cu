@@ -289,7 +289,7 @@ int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t 
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
-                   cudaStream_t s, long long* slice_rows)
+                   cudaStream_t s, std::vector<std::pair<long long, long long>>* slices)
 {
     const int np = st.np;
     const long long ndir = d.ndir;
@@ -345,18 +345,15 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
             const long long x0 = g.windowed ? win[0] : 0, x1 = g.windowed ? win[1] : cols;
             const long long y0 = g.windowed ? std::max<long long>(0, win[2]) : 0;
             const long long y1 = g.windowed ? std::min<long long>(rows, win[3]) : rows;
-            std::vector<std::pair<long long, long long>> todo;
-            const long long hint = slice_rows ? *slice_rows : 0;
+            std::vector<std::pair<long long, long long>> todo, fitted;
             if (y1 > y0) {
-                if (hint > 0 && hint < y1 - y0) {
-                    // slices of the hinted height, taken from the stack in increasing row order
-                    for (long long a0 = y0 + (y1 - y0 - 1) / hint * hint; a0 >= y0; a0 -= hint)
-                        todo.emplace_back(a0, std::min(y1, a0 + hint));
+                if (slices && !slices->empty() && slices->front().first == y0 && slices->back().second == y1) {
+                    // the slices that fitted last time, taken from the stack in increasing row order
+                    todo.assign(slices->rbegin(), slices->rend());
                 } else {
                     todo.emplace_back(y0, y1);
                 }
             }
-            long long fitted = 0;
             while (!todo.empty()) {
                 const auto sl = todo.back();
                 todo.pop_back();
@@ -383,10 +380,12 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                 }
                 RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
                                            classify_block, newton, s, kFieldSum));
-                const long long hgt = sl.second - sl.first;
-                fitted = fitted == 0 ? hgt : std::min(fitted, hgt);
+                fitted.push_back(sl);
             }
-            if (slice_rows && fitted > 0) *slice_rows = fitted;
+            if (slices) {
+                std::sort(fitted.begin(), fitted.end());
+                *slices = fitted;
+            }
         }
         if (mask_out)
             RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir,
@@ -411,8 +410,8 @@ struct rtw_rays {
     ObjDev* d_objs = nullptr;
     size_t d_objs_cap = 0;
     RaysDev st{};
-    // superellipsoid fields: slice height that fitted the hit list, for directions x orders slice_key
-    long long slice_rows = 0;
+    // sliced field runs: the row slices that fitted the hit list, for the directions of slice_key
+    std::vector<std::pair<long long, long long>> slices;
     long long slice_key = -1;
     void* block = nullptr;
     size_t block_bytes = 0;
@@ -716,7 +715,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
         r->d_objs_cap = objs.size();
     }
     *inout = r;
-    if (r->R != R || r->np != np || r->grid != tp->grid) r->slice_rows = 0;  // another ray grid
+    if (r->R != R || r->np != np || r->grid != tp->grid) r->slices.clear();  // another ray grid
     r->np = np;
     r->precision = tp->precision;
     r->grid = tp->grid;
@@ -896,16 +895,16 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         rtw::DirSet d;
         int rc = rtw::host::dirs_prepare(dirs, w, &d, s);
         if (rc != RTW_OK) return rc;
-        // the slice height found for these directions and this window is kept for the next call
+        // the slices found for these directions and this window are kept for the next call
         const int64_t* cw = dirs->cell_window;
         const long long key = (ndir * 64 + rays->np) ^ (cw[0] * 7919 + cw[1] * 104729 + cw[2] * 1299709 + cw[3] * 15485863);
         if (rays->slice_key != key) {
             rays->slice_key = key;
-            rays->slice_rows = 0;
+            rays->slices.clear();
         }
         return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, d,
                                          per_order, (double*)field_out, mask_out, w, 0, newton, status,
-                                         newton_counter(rays->device), s, &rays->slice_rows);
+                                         newton_counter(rays->device), s, &rays->slices);
     }
     // fan: workspace of mask words, PO windows and scratch
     const long long nfan = rays->objs[0].nx;

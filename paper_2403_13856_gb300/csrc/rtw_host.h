@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <utility>
 #include <vector>
 
 #include "rtw.h"
@@ -101,13 +102,14 @@ int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t 
 // With superellipsoids (the number of ray branches per direction grows quickly with the order) or
 // direction grids too fine for the hit list (g.sliced), each group is run in slices of ray-grid rows: a slice is classified, the count of
 // (triangle, direction) pairs it wants is read back (the stream is synchronised), and a slice that
-// does not fit the hit list is halved before any of its hits is summed.  slice_rows (optional, in
-// and out): the slice height to start from (0: the whole grid); receives the smallest height that
-// fitted, so that the next run on the same directions starts from slices that fit.
+// does not fit the hit list is split by its count before any of its hits is summed.  slices
+// (optional, in and out): row slices to start from when they cover the run's rows (else the whole
+// grid); receives the slices that fitted, so that the next run on the same rays and directions
+// takes them directly.
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
-                   cudaStream_t s, long long* slice_rows = nullptr);
+                   cudaStream_t s, std::vector<std::pair<long long, long long>>* slices = nullptr);
 
 // per-object feature table of the learned proposal
 void object_features(const ObjHost& o, ObjFeat& f);

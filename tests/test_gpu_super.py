@@ -118,7 +118,7 @@ def test_super_field_sliced(rtw, oracle_mod, window):
     mask = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
     rtw.rtw_field(rays, rtw.dirs_grid(nt, nph, cell_window=window), out, mask, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_sync_status()
-    # a second call starts from the slice height that fitted; the sum is the same up to the order
+    # a second call starts from the slices that fitted; the sum is the same up to the order
     # of the atomic additions
     out2 = torch.zeros_like(out)
     rtw.rtw_field(rays, rtw.dirs_grid(nt, nph, cell_window=window), out2, mask, flags=rtw.RTW_FIELD_PER_ORDER)
