@@ -470,6 +470,36 @@ def bench_ellipsoid(args, rank, world, local, dist):
             "kernel": "po2d_sum_kernel (FP64: one sincos per ray-direction term)"}
     del ra, sph, out_po, dirs_po
 
+    # the 10 um sphere (W1): a fan of 1e4 rays, orders 0..3, 1801 in-plane angles, s and p polarisation;
+    # too small to fill the GPU (launch and latency bound), timed over 50 steps of both polarisations
+    c1 = W.SPHERE10_FAN
+    fans = [rtw.Object([rtw.ObjectSpec(**W.SPHERE10, jones=jv)]) for jv in ((0.0, 1.0), (1.0, 0.0))]
+    tpf = rtw.trace_params(grid=rtw.RTW_GRID_FAN, p_max=c1["p_max"], n_rays=c1["n_rays"])
+    dpl = rtw.dirs_plane(c1["n_dirs"], c1["alpha0"], c1["dalpha"])
+    rf1 = [rtw.rtw_trace(f, tpf, stream=stream) for f in fans]
+    outf = torch.zeros((c1["n_dirs"], 1, 2), dtype=torch.complex128, device="cuda")
+    for _ in range(5):
+        for f, r in zip(fans, rf1):
+            rtw.rtw_trace(f, tpf, r, stream=stream)
+            rtw.rtw_field(r, dpl, outf, stream=stream)
+    e1a, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e1a.record(stream)
+    for _ in range(50):
+        for f, r in zip(fans, rf1):
+            rtw.rtw_trace(f, tpf, r, stream=stream)
+            rtw.rtw_field(r, dpl, outf, stream=stream)
+    e1b.record(stream)
+    torch.cuda.synchronize()
+    rtw.rtw_sync_status(stream)
+    us1 = 1e3 * e1a.elapsed_time(e1b) / 100  # per polarisation
+    flf = torch.zeros(c1["n_rays"], dtype=torch.int32, device="cuda")
+    rtw.rtw_rays_export(rf1[0], 0, 0, c1["n_rays"], flags=flf)
+    units1 = int(((flf & 1) != 0).sum().item()) * (c1["p_max"] + 1)
+    sphere_fan = {"workload": "sphere a=10 um, m=1.333, fan of 1e4 rays, p=0..3, 1801 angles, s and p, FP64",
+                  "us_per_step": us1, "value": units1 / (us1 / 1e6), "unit": UNIT,
+                  "directions_per_s": c1["n_dirs"] / (us1 / 1e6)}
+    del rf1, fans
+
     # the paper's Fig. 3 setting: the oblate spheroid a = b = 100, c = 90 um lit along its x axis, its
     # whole 3-D pattern at 0.01 deg (18000 x 36000 directions), 4e6 rays, orders 0..5 (the paper's
     # own timing of this pattern, 9.4 min on a desktop CPU with an unstated ray count, is context)
@@ -558,6 +588,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "superellipsoid": superellipsoid,
         "po2d_rainbow": po2d,
         "paper_fig3_pattern": fig3,
+        "sphere_fan": sphere_fan,
     }
     if cpu:
         line["cpu_baseline"] = cpu
