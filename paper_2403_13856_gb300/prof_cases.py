@@ -6,6 +6,7 @@
     python -m paper_2403_13856_gb300.prof_cases ellipsoid [--rays N]
     python -m paper_2403_13856_gb300.prof_cases superellipsoid [--rays N] [--shape-e E]
     python -m paper_2403_13856_gb300.prof_cases po2d [--sphere A] [--spacing H]
+    python -m paper_2403_13856_gb300.prof_cases pattern [--rays N] [--res DEG]
 
 Each case builds its inputs (seeded), runs the launch sequence `--reps` times (default 3) after
 one warm-up and prints the CUDA-event time of the last repetition.  Sizes default to cases that
@@ -34,7 +35,8 @@ def _timed(torch, fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid", "superellipsoid", "po2d"])
+    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid", "superellipsoid", "po2d",
+                                     "pattern"])
     ap.add_argument("--rows", type=int, default=1 << 22)
     ap.add_argument("--objects", type=int, default=64)
     ap.add_argument("--rays", type=int, default=1_000_000)
@@ -42,6 +44,7 @@ def main():
     ap.add_argument("--shape-e", type=float, default=2.0, help="superellipsoid exponent e")
     ap.add_argument("--sphere", type=float, default=200.0, help="po2d: sphere radius (um)")
     ap.add_argument("--spacing", type=float, default=0.25, help="po2d: ray grid spacing (um)")
+    ap.add_argument("--res", type=float, default=0.05, help="pattern: angular resolution (deg)")
     ap.add_argument("--mixed", action="store_true", help="ellipsoid / batch: mixed-precision trace")
     ap.add_argument("--dfloat", action="store_true", help="ellipsoid / batch: double-float trace")
     a = ap.parse_args()
@@ -83,6 +86,17 @@ def main():
         ms = _timed(torch, lambda: rtw.rtw_field_learned(obj, mlp, lp, rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"]),
                                                          out), a.reps)
         print(f"learned objects={a.objects}: {ms:.3f} ms")
+    elif a.case == "pattern":
+        # the side-lit spheroid's whole pattern at --res degrees (0.01 with 4e6 rays is the benchmark;
+        # 0.05 with 1.6e5 rays keeps the same directions per triangle)
+        obj = rtw.Object([rtw.ObjectSpec(**W.SPHEROID_SIDE, jones=(0.0, 1.0))])
+        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=5, n_rays=a.rays)
+        rays = rtw.rtw_trace(obj, tp)
+        nt = int(round(180.0 / a.res))
+        out = torch.empty((nt * 2 * nt, 1, 2), dtype=torch.complex128, device="cuda")
+        dirs = rtw.dirs_grid(nt, 2 * nt)
+        ms = _timed(torch, lambda: rtw.rtw_field(rays, dirs, out), a.reps)
+        print(f"pattern rays={a.rays} res={a.res} deg ({nt}x{2 * nt}): field {ms:.3f} ms")
     elif a.case == "po2d":
         import math
 
