@@ -526,9 +526,11 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
 }
 
 // Phase 3: one thread per (triangle, direction) pair: the double-precision rule for close calls,
-// then the barycentric weights of the central projection, F, Psi and F e^{i Psi}.
-__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h,
-                                                             int newton)
+// then the barycentric weights of the central projection, F, Psi and F e^{i Psi}.  kNewton: replace
+// the interpolated hit by the exact ray found by Newton steps (a separate instantiation, so that the
+// dense mode does not carry the exact trace's registers).
+template <bool kNewton>
+__global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h)
 {
     const unsigned int n = min(*h.n, h.cap);
     const int nt = d.nt, nph = d.nph;
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBa
 #pragma unroll
         for (int k = 0; k < 6; ++k) Fi[k] = l0 * F[0][k] + l1 * F[1][k] + l2 * F[2][k];
         double ps = l0 * psi[0] + l1 * psi[1] + l2 * psi[2];
-        if (newton) {
+        if constexpr (kNewton) {
             // exact ray of this branch from the interpolated impact point (the same weights)
             double xs = 0.0, ys = 0.0;
             const double lw[3] = {l0, l1, l2};
@@ -1197,7 +1199,10 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirS
         field_grid_kernel<<<(unsigned)((b.total + cb - 1) / cb), cb, 0, s>>>(a, b, d, big, nbig, big_cap, h);
         field_grid_big_kernel<<<(unsigned)(32 * sms), 32 * kBigWarps, 0, s>>>(a, b, d, big, nbig, big_cap, h);
     }
-    if (stage != 1) field_grid_hit_kernel<<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h, newton);
+    if (stage != 1) {
+        if (newton) field_grid_hit_kernel<true><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
+        else field_grid_hit_kernel<false><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
+    }
     return cudaGetLastError();
 }
 
