@@ -35,9 +35,9 @@ UNIT = "rays*interfaces/s"
 FLOPS_PER_INTERACTION = 430
 FP64_NOMINAL_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload: ncu measured
-# 2.53 MB + 573.7 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
+# 1.56 MB + 578.0 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
 # 4x at 4e6
-TRACE_TRAFFIC_BYTES = 4 * (2_534_656 + 573_732_352)
+TRACE_TRAFFIC_BYTES = 4 * (1_564_160 + 577_976_576)
 
 
 def parse():

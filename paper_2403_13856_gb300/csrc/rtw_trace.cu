@@ -175,11 +175,20 @@ __global__ void __launch_bounds__(BS, MINB) trace_items_kernel(const ObjDev* __r
     }
 }
 
-// every step in double precision
+// every step in double precision (no aperture data: the writes of trace_kernel_fp64_aux compile away)
 __global__ void __launch_bounds__(128) trace_kernel_fp64(const ObjDev* __restrict__ objs, int nobj, RaysDev st,
                                                          int pmax, int aux)
 {
-    trace_kernel_body<double>(objs, nobj, st, pmax, aux);
+    (void)aux;
+    trace_kernel_body<double>(objs, nobj, st, pmax, 0);
+}
+
+// the same, keeping the exit-wave data of the physical-optics integrals (RTW_TRACE_APERTURE)
+__global__ void __launch_bounds__(128) trace_kernel_fp64_aux(const ObjDev* __restrict__ objs, int nobj,
+                                                             RaysDev st, int pmax, int aux)
+{
+    (void)aux;
+    trace_kernel_body<double>(objs, nobj, st, pmax, 1);
 }
 
 // the same, recording every ray where it crosses the sphere |M| = st.near_r
@@ -279,8 +288,10 @@ cudaError_t launch_trace(const ObjDev* d_objs, int nobj, RaysDev st, int pmax, b
         trace_kernel_mixed<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
     else if (st.precision == 2)
         trace_kernel_df<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+    else if (aux)
+        trace_kernel_fp64_aux<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, 1);
     else
-        trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, aux ? 1 : 0);
+        trace_kernel_fp64<<<(unsigned)nb, bs, 0, s>>>(d_objs, nobj, st, pmax, 0);
     return cudaGetLastError();
 }
 
