@@ -377,20 +377,22 @@ int rtw_mlp_adam(rtw_mlp* m, int order, float lr, const float* grad, void* strea
  * heads whose softmax weight is below p_min (0: 0.05) are not tried; at most max_steps Newton
  * steps per head (0: 5); convergence at |s - target| < tol (0: per object
  * min(1e-6, 1e-4 / (k0 max(a, b, c))), which keeps the phase error of a converged ray below
- * 1e-4 rad); rows (object, direction) per launch sequence chunk_rows (0: 2^24). */
+ * 1e-4 rad); rows (object, direction) per launch sequence chunk_rows (0: 2^24); a step is halved
+ * at most max_halvings times (0: 3, range 1..30) before its head is given up. */
 typedef struct {
     int p_max;
     float p_min;
     int max_steps;
     double tol;
     int64_t chunk_rows;
+    int max_halvings;
 } rtw_learned_params;
 
 /* The far field of every object of obj on the (theta, phi) grid of dirs from learned proposals:
  * for each direction s and order p, network p (features of s and the object) proposes 4 entry
  * points (moved onto radius 0.999 of the unit disk when beyond it); each head with softmax
  * weight >= p_min seeds Newton steps on the exact FP64 trace (as RTW_NEWTON, at most max_steps
- * steps of at most 3 halvings each, no distance bound); a root within 1e-6 max(a, b, c) of
+ * steps of at most max_halvings halvings each, no distance bound); a root within 1e-6 max(a, b, c) of
  * an earlier root of the same direction and order is the same ray and is dropped; every other
  * root adds its exact F e^{i Psi}, except a near-caustic root, which marks the direction
  * (RTW_MASK_CAUSTIC) instead.  A branch that no head finds is missing from the sum: roots_out

@@ -66,6 +66,8 @@ def lib():
         L.or_field_fan.restype = i
         L.or_field_grid.argtypes = [p, i64, d, i, i, i, p, i, p, p, i, p]
         L.or_field_grid.restype = i64
+        L.or_field_grid_counts.argtypes = [p, i64, d, i, i, i, i, p, p, p, i, p]
+        L.or_field_grid_counts.restype = i64
         L.or_field_dirs.argtypes = [p, i64, d, i, p, i64, i, p, p, i, p]
         L.or_field_dirs.restype = i64
         L.or_near_record.argtypes = [p, p, d, p]
@@ -89,8 +91,10 @@ def lib():
         L.om_loss_grad.argtypes = [p, p, p, p, i64, d, i, p]
         L.om_loss_grad.restype = d
         L.om_adam.argtypes = [p, p, p, p, i64, i, d, d, d, d]
-        L.or_field_learned.argtypes = [p, p, i, i, i, d, i, d, p, p, p]
+        L.or_field_learned.argtypes = [p, p, i, i, i, d, i, d, i, p, p, p]
         L.or_field_learned.restype = i64
+        L.or_field_learned_dirs.argtypes = [p, p, i, p, i64, d, i, d, i, p, p, p]
+        L.or_field_learned_dirs.restype = i64
         _lib = L
     return _lib
 
@@ -190,15 +194,42 @@ class Object:
             raise RuntimeError("or_field_grid failed")
         return out, mask, int(hits), int(nfail.value)
 
-    def field_learned(self, theta, pmax, ntheta, nphi, p_min=0.05, max_steps=5, tol=0.0):
-        """theta: (pmax+1) x MLP_NPARAM network parameters; returns out, mask, root counts."""
+    def field_grid_counts(self, pmax, ntheta, nphi, n_target=0, h=0.0, flags=0, threads=0):
+        """or_field_grid over every cell, with the number of hits per (direction, order): with
+        FIELD_EXACT, the exact branches found (bit 0x80: a hit whose Newton step failed)."""
+        out = np.zeros((ntheta * nphi, pmax + 1, 4))
+        mask = np.zeros(ntheta * nphi, dtype=np.uint8)
+        counts = np.zeros((ntheta * nphi, pmax + 1), dtype=np.uint8)
+        nfail = ctypes.c_int64(0)
+        hits = lib().or_field_grid_counts(self.handle, int(n_target), float(h), int(pmax), int(ntheta), int(nphi),
+                                          int(flags), _ptr(out), _ptr(mask), _ptr(counts), int(threads),
+                                          ctypes.byref(nfail))
+        if hits < 0:
+            raise RuntimeError("or_field_grid_counts failed")
+        return out, mask, counts, int(nfail.value)
+
+    def field_learned(self, theta, pmax, ntheta, nphi, p_min=0.05, max_steps=5, tol=0.0, max_halvings=3):
+        """theta: (pmax+1) x MLP_NPARAM network parameters; each head's Newton steps are halved at
+        most max_halvings times; returns out, mask, root counts."""
         theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(pmax + 1, -1)
         ndir = ntheta * nphi
         out = np.zeros((ndir, pmax + 1, 4))
         mask = np.zeros(ndir, dtype=np.uint8)
         roots = np.zeros((ndir, pmax + 1), dtype=np.uint8)
         lib().or_field_learned(self.handle, _ptr(theta), int(pmax), int(ntheta), int(nphi), float(p_min),
-                               int(max_steps), float(tol), _ptr(out), _ptr(mask), _ptr(roots))
+                               int(max_steps), float(tol), int(max_halvings), _ptr(out), _ptr(mask), _ptr(roots))
+        return out, mask, roots
+
+    def field_learned_dirs(self, theta, pmax, dirs, p_min=0.05, max_steps=5, tol=0.0, max_halvings=3):
+        """The learned field on a list of directions dirs (n x 2: theta, phi)."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(pmax + 1, -1)
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
+        ndir = dirs.shape[0]
+        out = np.zeros((ndir, pmax + 1, 4))
+        mask = np.zeros(ndir, dtype=np.uint8)
+        roots = np.zeros((ndir, pmax + 1), dtype=np.uint8)
+        lib().or_field_learned_dirs(self.handle, _ptr(theta), int(pmax), _ptr(dirs), ndir, float(p_min),
+                                    int(max_steps), float(tol), int(max_halvings), _ptr(out), _ptr(mask), _ptr(roots))
         return out, mask, roots
 
     def near_record(self, rec, R):

@@ -1293,7 +1293,7 @@ static int edge_in(double e, int64_t ia, int64_t ib, int sigma)
  * triangle for both. */
 static int64_t field_square(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
                             const double* list, int64_t n_list, const int64_t* window, int flags, double* out,
-                            uint8_t* mask, int nthreads, int64_t* newton_fail, double near_R)
+                            uint8_t* mask, int nthreads, int64_t* newton_fail, double near_R, uint8_t* counts)
 {
     const int np = pmax + 1;
     double h, xc, yc;
@@ -1352,6 +1352,7 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
     const int nout = near_R > 0.0 ? 6 : 4; /* (E_r,) E_theta, E_phi: re, im */
     memset(out, 0, sizeof(double) * (size_t)ndir * np * nout);
     memset(mask, 0, (size_t)ndir);
+    if (counts) memset(counts, 0, (size_t)ndir * np);
     const double dth = list ? 1.0 : PI / ntheta, dph = list ? 1.0 : 2.0 * PI / nphi;
     double axial = 2.0 * o->lambda / o->Lmin;
     /* unit vector, e_theta, e_phi of every direction */
@@ -1492,6 +1493,12 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
                                 done = 1;
                             } else {
                                 nfail++;
+                                if (counts) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                                    counts[(size_t)dk * np + p] |= 0x80;
+                                }
                             }
                         }
                         if (!done) {
@@ -1509,6 +1516,12 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
 #pragma omp atomic
 #endif
                             dst[c] += acc[c];
+                        }
+                        if (counts) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                            counts[(size_t)dk * np + p] += 1;
                         }
                         hits++;
                     }
@@ -1528,7 +1541,14 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                       int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, window, flags, out, mask, nthreads,
-                        newton_fail, 0.0);
+                        newton_fail, 0.0, NULL);
+}
+
+int64_t or_field_grid_counts(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
+                             int flags, double* out, uint8_t* mask, uint8_t* counts, int nthreads, int64_t* newton_fail)
+{
+    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, flags, out, mask, nthreads,
+                        newton_fail, 0.0, counts);
 }
 
 int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi, double R,
@@ -1536,14 +1556,14 @@ int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int p
 {
     double rc = sqrt(dot3(o->center, o->center));
     if (!(R > rc + o->Rbound)) return -1;
-    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, R);
+    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, R, NULL);
 }
 
 int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pmax, const double* dirs,
                       int64_t ndir, int flags, double* out, uint8_t* mask, int nthreads, int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, 0, 0, dirs, ndir, NULL, flags, out, mask, nthreads,
-                        newton_fail, 0.0);
+                        newton_fail, 0.0, NULL);
 }
 
 /* ------------------------------------------------------------------------------------- */
@@ -1687,12 +1707,15 @@ int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, 
 
 #include "mlp_oracle.h"
 
-int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int ntheta, int nphi, double p_min,
-                         int max_steps, double tol, double* out, uint8_t* mask, uint8_t* roots)
+/* the learned field on the cell-centred (theta, phi) grid (list == NULL) or on the directions of a
+ * list (n_list x (theta, phi)) */
+static int64_t field_learned(const or_object* o, const double* theta, int pmax, int ntheta, int nphi,
+                             const double* list, int64_t n_list, double p_min, int max_steps, double tol,
+                             int max_halvings, double* out, uint8_t* mask, uint8_t* roots)
 {
     const int np = pmax + 1;
-    const int64_t ndir = (int64_t)ntheta * nphi;
-    const double dth = PI / ntheta, dph = 2.0 * PI / nphi;
+    const int64_t ndir = list ? n_list : (int64_t)ntheta * nphi;
+    const double dth = list ? 1.0 : PI / ntheta, dph = list ? 1.0 : 2.0 * PI / nphi;
     const double axial = 2.0 * o->lambda / o->Lmin;
     const double dedup = 1e-6 * o->Lmax;
     /* tol <= 0: per object, a phase error k0 L |s - t| below 1e-4 rad */
@@ -1705,8 +1728,14 @@ int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int 
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
 #endif
     for (int64_t dk = 0; dk < ndir; ++dk) {
-        const int it = (int)(dk / nphi), jp = (int)(dk % nphi);
-        const double th = (it + 0.5) * dth, ph = -PI + (jp + 0.5) * dph;
+        double th, ph;
+        if (list) {
+            th = list[2 * dk];
+            ph = list[2 * dk + 1];
+        } else {
+            th = ((int)(dk / nphi) + 0.5) * dth;
+            ph = -PI + ((int)(dk % nphi) + 0.5) * dph;
+        }
         const double s[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
         const double eth[3] = {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)};
         const double eph[3] = {-sin(ph), cos(ph), 0.0};
@@ -1736,7 +1765,7 @@ int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int 
                     uv[1] *= 0.999 / ru;
                 }
                 om_uv_to_xy(o, uv, &xy[0], &xy[1]);
-                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, 3, rec) < 0) continue;
+                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, max_halvings, rec) < 0) continue;
                 int dup = 0;
                 for (int q = 0; q < nfound; ++q)
                     if (hypot(xy[0] - found[q][0], xy[1] - found[q][1]) <= dedup) dup = 1;
@@ -1757,4 +1786,18 @@ int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int 
         mask[dk] = mk;
     }
     return total;
+}
+
+int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int ntheta, int nphi, double p_min,
+                         int max_steps, double tol, int max_halvings, double* out, uint8_t* mask, uint8_t* roots)
+{
+    return field_learned(o, theta, pmax, ntheta, nphi, NULL, 0, p_min, max_steps, tol, max_halvings, out, mask,
+                         roots);
+}
+
+int64_t or_field_learned_dirs(const or_object* o, const double* theta, int pmax, const double* dirs, int64_t ndir,
+                              double p_min, int max_steps, double tol, int max_halvings, double* out, uint8_t* mask,
+                              uint8_t* roots)
+{
+    return field_learned(o, theta, pmax, 0, 0, dirs, ndir, p_min, max_steps, tol, max_halvings, out, mask, roots);
 }

@@ -121,6 +121,12 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                       int nphi, const int64_t* window, int flags, double* out, uint8_t* mask,
                       int nthreads, int64_t* newton_fail);
 
+/* or_field_grid over every cell, with counts (ndir x (pmax+1) bytes): the number of hits that added
+ * to each (direction, order) -- with OR_FIELD_EXACT the number of exact branches found, bit 0x80 set
+ * where a hit's Newton refinement did not converge (that hit kept its interpolated value). */
+int64_t or_field_grid_counts(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
+                             int flags, double* out, uint8_t* mask, uint8_t* counts, int nthreads, int64_t* newton_fail);
+
 /* The same field on an arbitrary list of directions: dirs is ndir x (theta, phi) (theta from +z,
  * phi from +x); out: ndir x (pmax+1) x 4, mask: ndir.  Every direction is tested against every
  * cell triangle whose cap contains it. */
@@ -172,14 +178,19 @@ void or_project_add(const double F[6], double psi, const double eth[3], const do
  * p the network of order p (mlp_oracle.h; theta: (pmax+1) x OM_NPARAM doubles, evaluated with
  * bfloat16 rounding as the tensor cores do) proposes 4 entry points (moved onto radius 0.999 of
  * the unit disk when beyond it); each head whose softmax weight is at least p_min seeds
- * or_newton_ex (at most max_steps steps, at most 3 halvings of a step, no distance bound,
+ * or_newton_ex (at most max_steps steps, at most max_halvings halvings of a step, no distance bound,
  * |s - t| < tol, or for tol <= 0 min(1e-6, 1e-4 / (k0 max(a, b, c)))); a root within 1e-6 max(a, b, c) of an earlier root of
  * the same direction and order is the same ray and is dropped; every other root adds
  * F e^{i Psi}, except a near-caustic one, which marks the direction instead.
  * out: ndir x (pmax+1) x 4; mask: ndir (axial as or_field_grid); roots (may be NULL):
  * ndir x (pmax+1) counts.  Returns the number of roots. */
 int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int ntheta, int nphi, double p_min,
-                         int max_steps, double tol, double* out, uint8_t* mask, uint8_t* roots);
+                         int max_steps, double tol, int max_halvings, double* out, uint8_t* mask, uint8_t* roots);
+/* The same on a list of directions: dirs is ndir x (theta, phi); out: ndir x (pmax+1) x 4, mask: ndir,
+ * roots (may be NULL): ndir x (pmax+1). */
+int64_t or_field_learned_dirs(const or_object* o, const double* theta, int pmax, const double* dirs, int64_t ndir,
+                              double p_min, int max_steps, double tol, int max_halvings, double* out, uint8_t* mask,
+                              uint8_t* roots);
 
 #ifdef __cplusplus
 }

@@ -19,9 +19,6 @@ namespace rtw {
 namespace {
 
 constexpr unsigned int kMaskCausticL = 1u;  // the dense path's RTW_MASK_CAUSTIC bit
-// a proposal is a seed that should already be close: a step is halved at most 3 times before the
-// head is given up (a far seed would otherwise cost up to 13 traces per step)
-constexpr int kLearnedHalvings = 3;
 
 // features of row (object o, direction dk): s (3) then the object's 13, in bfloat16
 __global__ void learned_features_kernel(const ObjFeat* __restrict__ feat, const double* __restrict__ tab, int nt,
@@ -48,8 +45,9 @@ __global__ void __launch_bounds__(128) learned_newton_kernel(const ObjDev* __res
                                                              const ObjFeat* __restrict__ feat,
                                                              const double* __restrict__ tab, int nt, int nph,
                                                              long long nrows, const float* __restrict__ Y, int p,
-                                                             float p_min, int max_steps, double tol, int nout,
-                                                             double* __restrict__ out, unsigned int* __restrict__ mask,
+                                                             float p_min, int max_steps, double tol, int max_halvings,
+                                                             int nout, double* __restrict__ out,
+                                                             unsigned int* __restrict__ mask,
                                                              uint8_t* __restrict__ roots, int np)
 {
     const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -92,7 +90,7 @@ __global__ void __launch_bounds__(128) learned_newton_kernel(const ObjDev* __res
         const double d1 = u1 / f.l11, d0 = (u0 - f.l10 * d1) / f.l00;
         FarRecord fr;
         double root[2];
-        if (!newton_point(o, p, t, o.c[0] + d0, o.c[1] + d1, 0.0, fr, max_steps + 1, tl, root, kLearnedHalvings))
+        if (!newton_point(o, p, t, o.c[0] + d0, o.c[1] + d1, 0.0, fr, max_steps + 1, tl, root, max_halvings))
             continue;
         bool dup = false;
         for (int q = 0; q < nfound; ++q)
@@ -114,8 +112,8 @@ __global__ void __launch_bounds__(128) learned_newton_kernel(const ObjDev* __res
 
 cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double* tab, int nt, int nph, long long nrows,
                            const MlpWeights* nets, int np, __nv_bfloat16* X, float* Y, float p_min, int max_steps,
-                           double tol, int nout, double* out, unsigned int* mask, uint8_t* roots, unsigned int* status,
-                           cudaStream_t s)
+                           double tol, int max_halvings, int nout, double* out, unsigned int* mask, uint8_t* roots,
+                           unsigned int* status, cudaStream_t s)
 {
     if (nrows <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nrows + 127) / 128);
@@ -124,8 +122,8 @@ cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double
     for (int p = 0; p < np && e == cudaSuccess; ++p) {
         e = launch_mlp_forward(nets[p], X, nrows, Y, status, s);
         if (e != cudaSuccess) break;
-        learned_newton_kernel<<<nb, 128, 0, s>>>(objs, feat, tab, nt, nph, nrows, Y, p, p_min, max_steps, tol, nout,
-                                                  out, mask, roots, np);
+        learned_newton_kernel<<<nb, 128, 0, s>>>(objs, feat, tab, nt, nph, nrows, Y, p, p_min, max_steps, tol,
+                                                  max_halvings, nout, out, mask, roots, np);
         e = cudaGetLastError();
     }
     return e;
@@ -150,7 +148,7 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
         return fail(RTW_ERR_ARG, "rtw_field_learned: a (theta, phi) grid with n_theta >= 1, n_phi >= 2");
     if (flags & ~RTW_FIELD_PER_ORDER) return fail(RTW_ERR_ARG, "rtw_field_learned: flags 0x%x", flags);
     if (lp->max_steps < 0 || lp->max_steps > 30 || lp->p_min < 0.0f || lp->p_min > 1.0f || lp->tol < 0.0 ||
-        lp->chunk_rows < 0)
+        lp->chunk_rows < 0 || lp->max_halvings < 0 || lp->max_halvings > 30)
         return fail(RTW_ERR_ARG, "rtw_field_learned: parameters out of range");
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
@@ -158,6 +156,7 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
     unsigned int* status = rtw::host::status_word(dev);
     if (!status) return fail(RTW_ERR_CUDA, "rtw_field_learned: status word");
     const int max_steps = lp->max_steps > 0 ? lp->max_steps : 5;
+    const int max_halvings = lp->max_halvings > 0 ? lp->max_halvings : 3;
     const double tol = lp->tol;  // 0: per object, min(1e-6, 1e-4 / (k0 max(a, b, c)))
     const float p_min = lp->p_min > 0.0f ? lp->p_min : 0.05f;
     const long long ndir = (long long)dirs->n_theta * dirs->n_phi;
@@ -212,7 +211,7 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
         e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * (size_t)rows, s);
         if (e != cudaSuccess) break;
         e = rtw::launch_learned(d_obj + c0, d_feat + c0, tab, dirs->n_theta, dirs->n_phi, rows, nets.data(), np, X, Y,
-                                p_min, max_steps, tol, nout, (double*)field_out + 4 * (size_t)nout * ndir * c0, words,
+                                p_min, max_steps, tol, max_halvings, nout, (double*)field_out + 4 * (size_t)nout * ndir * c0, words,
                                 roots_out ? roots_out + (size_t)np * ndir * c0 : nullptr, status, s);
         if (e == cudaSuccess && mask_out)
             e = rtw::launch_finalize_mask(words, mask_out + (size_t)ndir * c0, d_obj + c0, cn, ndir, 1, dirs->n_theta,

@@ -395,12 +395,13 @@ def rtw_mlp_adam(mlp: MLP, order, lr, grad=None, stream=None):
 
 class rtw_learned_params(ctypes.Structure):
     _fields_ = [("p_max", ctypes.c_int), ("p_min", ctypes.c_float), ("max_steps", ctypes.c_int),
-                ("tol", ctypes.c_double), ("chunk_rows", ctypes.c_int64)]
+                ("tol", ctypes.c_double), ("chunk_rows", ctypes.c_int64), ("max_halvings", ctypes.c_int)]
 
 
-def learned_params(p_max, p_min=0.0, max_steps=0, tol=0.0, chunk_rows=0):
+def learned_params(p_max, p_min=0.0, max_steps=0, tol=0.0, chunk_rows=0, max_halvings=0):
     lp = rtw_learned_params()
     lp.p_max, lp.p_min, lp.max_steps, lp.tol, lp.chunk_rows = p_max, p_min, max_steps, tol, int(chunk_rows)
+    lp.max_halvings = int(max_halvings)
     return lp
 
 

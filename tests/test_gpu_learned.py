@@ -39,8 +39,8 @@ def learned_field(rtw, obj, mlp, p_max, nt, nph, n_obj=1):
     out = torch.zeros((n_obj, nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
     mask = torch.zeros((n_obj, nt * nph), dtype=torch.uint8, device="cuda")
     roots = torch.zeros((n_obj, nt * nph, p_max + 1), dtype=torch.uint8, device="cuda")
-    rtw.rtw_field_learned(obj, mlp, rtw.learned_params(p_max), rtw.dirs_grid(nt, nph), out, mask, roots,
-                          flags=rtw.RTW_FIELD_PER_ORDER)
+    lp = rtw.learned_params(p_max, max_halvings=3)
+    rtw.rtw_field_learned(obj, mlp, lp, rtw.dirs_grid(nt, nph), out, mask, roots, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_sync_status()
     return out.cpu().numpy(), mask.cpu().numpy(), roots.cpu().numpy()
 
@@ -61,7 +61,7 @@ def test_learned_pipeline_matches_oracle(rtw, oracle_mod, k):
     got, gm, gr = learned_field(rtw, obj, mlp, p_max, nt, nph)
     o = oracle_mod.Object(spec["a"], spec["b"], spec["c"], quat=spec["quat"], m=spec["m"],
                           wavelength=spec["wavelength"])
-    ref, rm, rr = o.field_learned(th.astype(np.float64), p_max, nt, nph)  # 5 steps, object tolerance
+    ref, rm, rr = o.field_learned(th.astype(np.float64), p_max, nt, nph, max_halvings=3)  # 5 steps, object tolerance
     ref = oracle_mod.complex_field(ref)
     print(f"object {k}: roots per order GPU {gr[0].sum(axis=0)}, oracle {rr.sum(axis=0)}")
     assert np.array_equal(gr[0], rr)
