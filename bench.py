@@ -32,12 +32,26 @@ METRIC = "rays·interfaces/s and far-field directions/s on 1 GB300 at stated err
 UNIT = "rays*interfaces/s"
 # FP64 flops of one interaction of the trace kernel (both outgoing waves and one far-field record),
 # counted from its source: adds, multiplies, divisions and square roots as one, FMA as two
-FLOPS_PER_INTERACTION = 430
+KERNEL_FLOPS_PER_INTERACTION = 430
+
+
+def _oracle_flops():
+    """The algorithmic flops of one interaction: the operations the oracle's trace executes per
+    interaction on the benchmark ellipsoid, counted by its counting build and stored by the test
+    suite's script (tests/golden/oracle_flops_per_interaction.json)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_flops_per_interaction.json")) as f:
+            return float(json.load(f)["flops_per_interaction"]), "oracle operation count (counting build, stored)"
+    except (OSError, KeyError, ValueError):
+        return float(KERNEL_FLOPS_PER_INTERACTION), "hand count of the kernel source (stored oracle count missing)"
 FP64_NOMINAL_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload: ncu measured
 # 1.56 MB + 578.0 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
 # 4x at 4e6
 TRACE_TRAFFIC_BYTES = 4 * (1_564_160 + 577_976_576)
+TRACE_TRAFFIC_NOTE = ("DRAM bytes per launch from ncu at 1e6 rays, scaled by hits (4x); "
+                      "profiles/trace_kernel_fp64_ellipsoid_1e6rays.md")
+FLOPS_PER_INTERACTION, FLOPS_SOURCE = _oracle_flops()
 
 
 def parse():
@@ -161,6 +175,32 @@ def fp64_peak_gflops(torch):
         best = min(best, e0.elapsed_time(e1) / 1e3)
     del a, b
     return 2.0 * n ** 3 / best / 1e9
+
+
+def pipe_peaks(torch, rtw, local):
+    """Throughput of the FP64 (DFMA) and FP32 (FFMA, packed FFMA2) pipes of this GPU, measured with
+    the library's dependency-free FMA chain kernels (rtw_pipe_peak), best of 5 launches of about
+    50 ms each timed with CUDA events; the SM clock is sampled while they run."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    with ClockSampler(local) as clk:
+        for name, kind, iters in (("fp64", rtw.RTW_PEAK_FP64, 1600), ("fp32", rtw.RTW_PEAK_FP32, 100_000),
+                                  ("fp32x2", rtw.RTW_PEAK_FP32X2, 50_000)):
+            rtw.rtw_pipe_peak(kind, max(1, iters // 20), 4, sink, stream)
+            best = 1e30
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                flops = rtw.rtw_pipe_peak(kind, iters, 4, sink, stream)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            res[name] = flops / best / 1e9
+    c = clk.summary()
+    return {"fp64_gflops": res["fp64"], "fp32_gflops": max(res["fp32"], res["fp32x2"]),
+            "fp32_scalar_gflops": res["fp32"], "fp32x2_gflops": res["fp32x2"], "sm_mhz": c.get("sm_mhz"),
+            "how": "rtw_pipe_peak: 8 independent FMA chains per thread, 4 blocks of 256 per SM, best of 5"}
 
 
 def cpu_baseline(rows: int, single_thread_rows: int = 0):
@@ -553,11 +593,18 @@ def bench_ellipsoid(args, rank, world, local, dist):
         return
 
     peaks = measured_peaks()
-    fp64_meas = fp64_peak_gflops(torch)
+    pipes = pipe_peaks(torch, rtw, local)
+    fp64_dgemm = fp64_peak_gflops(torch)
     tr = statistics.median(t_trace)
+    tf = statistics.median(t_field)
     achieved = FLOPS_PER_INTERACTION * units / tr / 1e9
-    peak = fp64_meas
+    peak = pipes["fp64_gflops"]
     clocks = clk.summary()
+    # the field's algorithmic bytes: the ray state it reads (direction, F, Psi, flags per (ray,
+    # order) that hit: 68 B) and the complex128 grid it writes
+    field_bytes = units * 68 + ndir * 32
+    hbm = peaks.get("hbm_gbs")
+    mixed_tr = forms["mixed"]["ms_trace"] / 1e3
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         # default: the whole workload on every core (about 1 s on 16 cores), and one thread on 150 rows
@@ -575,10 +622,22 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "gpu_launches": 6,
         "roofline": {"kernel": "trace_kernel_fp64", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "GFLOP/s FP64", "frac": achieved / peak,
-                     "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (nominal 1250)",
-                     "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": TRACE_TRAFFIC_BYTES,
-                     "traffic_note": "DRAM bytes per launch from ncu at 1e6 rays, scaled by hits (4x); "
-                                     "profiles/trace_kernel_fp64_ellipsoid_1e6rays.md"},
+                     "peak_source": f"measured: DFMA chains (rtw_pipe_peak) at {pipes['sm_mhz']} MHz; "
+                                    f"cuBLAS DGEMM 4096^3 {fp64_dgemm:.0f}; nominal {FP64_NOMINAL_GFLOPS:.0f}",
+                     "flops_per_interaction": FLOPS_PER_INTERACTION, "flops_source": FLOPS_SOURCE,
+                     "frac_kernel_count": KERNEL_FLOPS_PER_INTERACTION * units / tr / 1e9 / peak,
+                     "traffic": TRACE_TRAFFIC_BYTES, "traffic_note": TRACE_TRAFFIC_NOTE},
+        "roofline_field": {"kernels": "field_grid_kernel, field_grid_big_kernel, field_grid_hit_kernel",
+                           "bound": "hbm", "achieved": field_bytes / tf / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": (field_bytes / tf / 1e9 / hbm) if hbm else None, "bytes": field_bytes,
+                           "bytes_note": "ray state read (68 B per hit ray and order) + complex128 grid written"},
+        "roofline_mixed": {"kernel": "trace_kernel_mixed", "bound": "alu",
+                           "achieved": FLOPS_PER_INTERACTION * units / mixed_tr / 1e9,
+                           "peak": pipes["fp32_gflops"], "unit": "GFLOP/s FP32",
+                           "frac": FLOPS_PER_INTERACTION * units / mixed_tr / 1e9 / pipes["fp32_gflops"],
+                           "note": "the same algorithmic flops as the FP64 trace over the mixed trace's time, "
+                                   "against the FP32 pipe (the larger of FFMA and packed FFMA2)"},
+        "pipe_peaks": pipes,
         "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
@@ -720,8 +779,9 @@ def bench_batch(args, rank, world, local, dist):
         if dist:
             dist.destroy_process_group()
         return
-    fp64_meas = fp64_peak_gflops(torch)
+    pipes = pipe_peaks(torch, rtw, local)
     achieved = FLOPS_PER_INTERACTION * units / (t_trace / 1e3) / 1e9
+    pk = pipes["fp64_gflops"] if precision == rtw.RTW_FP64 else pipes["fp32_gflops"]
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_batch()
@@ -738,15 +798,18 @@ def bench_batch(args, rank, world, local, dist):
         "directions_per_s": dps,
         "ms_trace": t_trace, "ms_field": t_field,
         "gpu_launches": 2 + nchunks * 7,
-        "roofline": {"kernel": "trace_items_kernel", "bound": "alu", "achieved": achieved, "peak": fp64_meas,
-                     "unit": "GFLOP/s FP64", "frac": achieved / fp64_meas,
-                     "peak_source": "measured: cuBLAS DGEMM 4096^3 on this GPU (nominal 1250)",
-                     "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": None},
+        "roofline": {"kernel": "trace_items_kernel", "bound": "alu", "achieved": achieved, "peak": pk,
+                     "unit": "GFLOP/s " + ("FP64" if precision == rtw.RTW_FP64 else "FP32"),
+                     "frac": achieved / pk,
+                     "peak_source": f"measured: FMA chains (rtw_pipe_peak) at {pipes['sm_mhz']} MHz",
+                     "flops_per_interaction": FLOPS_PER_INTERACTION, "flops_source": FLOPS_SOURCE,
+                     "traffic": None},
+        "pipe_peaks": pipes,
         "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
     }
     if precision != rtw.RTW_FP64:
-        line["roofline"]["note"] = "mixed: FP32 geometry; the FP64 figure is the FP64-equivalent rate"
+        line["roofline"]["note"] = "mixed: the algorithmic flops of the FP64 trace against the FP32 pipe"
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -421,6 +421,20 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
 int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident* w, const rtw_trace_params* tp,
                          const rtw_dirs* dirs, int flags, void* field_out, uint8_t* mask_out, void* stream);
 
+/* ---- measurement ----
+ * The paper has no counterpart of this call: it runs a throughput kernel of one floating-point
+ * pipe, the denominator of the trace kernels' rooflines.  kind: RTW_PEAK_FP64 (DFMA),
+ * RTW_PEAK_FP32 (FFMA) or RTW_PEAK_FP32X2 (packed fma.rn.f32x2); one launch of SMs x blocks_per_sm
+ * (1..32) blocks of 256 threads, each thread running 8 independent fused multiply-add chains of
+ * 16 iters (1..2^30) steps, no memory traffic.  *flops (host) receives the floating-point
+ * operations of the launch (2 per FMA and lane).  sink: device buffer of one double, written only
+ * if the chains reach a value they cannot reach (it keeps the compiler from removing them).
+ * Asynchronous on `stream`: time it with events on that stream. */
+#define RTW_PEAK_FP64 0
+#define RTW_PEAK_FP32 1
+#define RTW_PEAK_FP32X2 2
+int rtw_pipe_peak(int kind, int64_t iters, int blocks_per_sm, void* sink, double* flops, void* stream);
+
 /* ---- status ---- */
 
 /* Synchronises `stream`, reads and clears the device status word of the library: RTW_OK or the

@@ -21,15 +21,16 @@
  */
 #include "rtw_oracle.h"
 
-#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
-
+#ifndef OR_OPCOUNT
+#include <complex.h>
 typedef double complex cplx;
+#endif /* else: the counting build (opcount.h) provides cplx */
 
 static const double PI = 3.14159265358979323846;
 /* rays whose |cos| of incidence falls below this are dropped (grazing, P' singular) */

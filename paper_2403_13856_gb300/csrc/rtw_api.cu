@@ -144,6 +144,153 @@ int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* 
     return RTW_OK;
 }
 
+// Validates one object description and its incident wave and fills the host description (no
+// device work, no allocation beyond the error message); i numbers the object in messages.
+int make_object_host(const rtw_object_desc& d, const rtw_incident& w, int i, ObjHost& o)
+{
+    if (!(d.a > 0.0 && d.b > 0.0 && d.c > 0.0) || !std::isfinite(d.a + d.b + d.c))
+        return fail(RTW_ERR_ARG, "object %d: semi-axes must be positive", i);
+    const double qn = std::sqrt(d.quat[0] * d.quat[0] + d.quat[1] * d.quat[1] + d.quat[2] * d.quat[2] +
+                                d.quat[3] * d.quat[3]);
+    if (!(std::fabs(qn - 1.0) <= 1e-9)) return fail(RTW_ERR_ARG, "object %d: |quat| = %.17g != 1", i, qn);
+    if (!(d.m_re > 0.0) || d.m_re == 1.0 || !std::isfinite(d.m_re))
+        return fail(RTW_ERR_ARG, "object %d: m must be positive and != 1", i);
+    if (d.m_im != 0.0) return fail(RTW_ERR_UNSUPPORTED, "object %d: absorbing objects (m_im != 0)", i);
+    if (!(w.wavelength_um > 0.0) || !std::isfinite(w.wavelength_um))
+        return fail(RTW_ERR_ARG, "object %d: wavelength must be positive", i);
+    if (w.kind != RTW_INCIDENT_PLANE && w.kind != RTW_INCIDENT_POINT)
+        return fail(RTW_ERR_ARG, "object %d: incident kind %d", i, w.kind);
+    if (w.kind == RTW_INCIDENT_PLANE && (w.dir[0] != 0.0 || w.dir[1] != 0.0 || w.dir[2] != 1.0))
+        return fail(RTW_ERR_UNSUPPORTED, "object %d: incident direction must be (0, 0, 1)", i);
+    if (w.kind == RTW_INCIDENT_POINT && !std::isfinite(w.source[0] + w.source[1] + w.source[2]))
+        return fail(RTW_ERR_ARG, "object %d: source position must be finite", i);
+    const double se = d.shape_e == 0.0 ? 1.0 : d.shape_e;
+    if (!(se >= 1.0) || !std::isfinite(se))
+        return fail(RTW_ERR_ARG, "object %d: shape exponent %g (0 or 1: ellipsoid, > 1: superellipsoid)", i,
+                    d.shape_e);
+    o.shape_e = se;
+    o.a[0] = d.a;
+    o.a[1] = d.b;
+    o.a[2] = d.c;
+    const double qw = d.quat[0] / qn, qx = d.quat[1] / qn, qy = d.quat[2] / qn, qz = d.quat[3] / qn;
+    o.R[0][0] = 1 - 2 * (qy * qy + qz * qz);
+    o.R[0][1] = 2 * (qx * qy - qw * qz);
+    o.R[0][2] = 2 * (qx * qz + qw * qy);
+    o.R[1][0] = 2 * (qx * qy + qw * qz);
+    o.R[1][1] = 1 - 2 * (qx * qx + qz * qz);
+    o.R[1][2] = 2 * (qy * qz - qw * qx);
+    o.R[2][0] = 2 * (qx * qz - qw * qy);
+    o.R[2][1] = 2 * (qy * qz + qw * qx);
+    o.R[2][2] = 1 - 2 * (qx * qx + qy * qy);
+    for (int k = 0; k < 3; ++k) o.c[k] = d.center[k];
+    o.m = d.m_re;
+    o.lambda = w.wavelength_um;
+    o.jre[0] = w.jones_re[0];
+    o.jre[1] = w.jones_re[1];
+    o.jim[0] = w.jones_im[0];
+    o.jim[1] = w.jones_im[1];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += o.R[r][k] * o.R[c][k] / (o.a[k] * o.a[k]);
+            o.W[r][c] = s;
+        }
+    o.lmax = std::fmax(d.a, std::fmax(d.b, d.c));
+    o.lmin = std::fmin(d.a, std::fmin(d.b, d.c));
+    o.S[0][0] = o.W[0][0] - o.W[0][2] * o.W[0][2] / o.W[2][2];
+    o.S[0][1] = o.W[0][1] - o.W[0][2] * o.W[1][2] / o.W[2][2];
+    o.S[1][0] = o.S[0][1];
+    o.S[1][1] = o.W[1][1] - o.W[1][2] * o.W[1][2] / o.W[2][2];
+    // a superellipsoid lies inside the ellipsoid of semi-axes a_i 3^((1 - 1/e) / 2) (power-mean
+    // inequality), Wb = W / g2; the rays that meet it bound the ray grid (Wb = W for e = 1)
+    const double g2 = se != 1.0 ? std::pow(3.0, 1.0 - 1.0 / se) : 1.0;
+    double Wb[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Wb[r][c] = o.W[r][c] / g2;
+    if (se != 1.0)
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) o.S[r][c] /= g2;
+    o.gc[0] = o.c[0];
+    o.gc[1] = o.c[1];
+    o.src = w.kind == RTW_INCIDENT_POINT;
+    if (o.src) {
+        // rays from the source s through X = c + x e1 + y e2 (v = X - s = g + x e1 + y e2, g = c - s)
+        // hit where (v.W g)^2 - (v.W v)(g.W g - 1) > 0: v^T K v > 0 with K = W g g^T W - (g.W g - 1) W,
+        // an ellipse (w - w0)^T S (w - w0) < 1 of the plane
+        double g[3], Wg[3];
+        for (int k = 0; k < 3; ++k) {
+            o.src_pos[k] = w.source[k];
+            g[k] = o.c[k] - w.source[k];
+        }
+        for (int r = 0; r < 3; ++r) Wg[r] = Wb[r][0] * g[0] + Wb[r][1] * g[1] + Wb[r][2] * g[2];
+        const double gWg = g[0] * Wg[0] + g[1] * Wg[1] + g[2] * Wg[2];
+        if (!(gWg > 1.0))
+            return fail(RTW_ERR_ARG, "object %d: the source lies inside the object (its bounding ellipsoid)", i);
+        const double gd = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const double ax[3] = {g[0] / gd, g[1] / gd, g[2] / gd};
+        const double ref[3] = {std::fabs(ax[0]) > 0.9 ? 0.0 : 1.0, std::fabs(ax[0]) > 0.9 ? 1.0 : 0.0, 0.0};
+        const double ra = ref[0] * ax[0] + ref[1] * ax[1] + ref[2] * ax[2];
+        double n1 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            o.e1[k] = ref[k] - ra * ax[k];
+            n1 += o.e1[k] * o.e1[k];
+        }
+        n1 = std::sqrt(n1);
+        for (int k = 0; k < 3; ++k) o.e1[k] /= n1;
+        o.e2[0] = ax[1] * o.e1[2] - ax[2] * o.e1[1];
+        o.e2[1] = ax[2] * o.e1[0] - ax[0] * o.e1[2];
+        o.e2[2] = ax[0] * o.e1[1] - ax[1] * o.e1[0];
+        double K[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) K[r][c] = Wg[r] * Wg[c] - (gWg - 1.0) * Wb[r][c];
+        auto Kv = [&](const double* v, double* out3) {
+            for (int r = 0; r < 3; ++r) out3[r] = K[r][0] * v[0] + K[r][1] * v[1] + K[r][2] * v[2];
+        };
+        auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+        double Kg[3], K1[3], K2[3];
+        Kv(g, Kg);
+        Kv(o.e1, K1);
+        Kv(o.e2, K2);
+        const double M00 = dot(o.e1, K1), M01 = dot(o.e1, K2), M11 = dot(o.e2, K2);
+        const double b0 = dot(o.e1, Kg), b1 = dot(o.e2, Kg);
+        const double dM = M00 * M11 - M01 * M01;
+        if (!(dM > 0.0)) return fail(RTW_ERR_ARG, "object %d: degenerate view from the source", i);
+        const double w0x = -(M11 * b0 - M01 * b1) / dM, w0y = -(M00 * b1 - M01 * b0) / dM;
+        const double f0 = dot(g, Kg) + b0 * w0x + b1 * w0y;
+        if (!(f0 > 0.0)) return fail(RTW_ERR_ARG, "object %d: degenerate view from the source", i);
+        o.S[0][0] = -M00 / f0;
+        o.S[0][1] = o.S[1][0] = -M01 / f0;
+        o.S[1][1] = -M11 / f0;
+        o.gc[0] = w0x;
+        o.gc[1] = w0y;
+    }
+    const double det = o.S[0][0] * o.S[1][1] - o.S[0][1] * o.S[1][0];
+    o.Sinv[0][0] = o.S[1][1] / det;
+    o.Sinv[0][1] = -o.S[0][1] / det;
+    o.Sinv[1][0] = -o.S[1][0] / det;
+    o.Sinv[1][1] = o.S[0][0] / det;
+    return RTW_OK;
+}
+
+// The device table entry of object o for the ray grid of tp: the object's tables and its grid
+// (spacing, size, fan half-width and axis), its rays starting at ray_offset.
+int object_device_entry(const ObjHost& o, const rtw_trace_params* tp, long long ray_offset, ObjDev& d)
+{
+    double h = 0.0, w = 0.0;
+    long long nx = 0, ny = 0;
+    int rc = grid_of(o, tp, &h, &nx, &ny, &w);
+    if (rc != RTW_OK) return rc;
+    fill_objdev(o, d);
+    d.grid = tp->grid == RTW_GRID_FAN ? rtw::kGridFan : rtw::kGridSquare;
+    d.h = h;
+    d.fan_w = w;
+    d.fan_ex = std::cos(tp->fan_phi);
+    d.fan_ey = std::sin(tp->fan_phi);
+    d.nx = nx;
+    d.ny = ny;
+    d.ray_offset = ray_offset;
+    return RTW_OK;
+}
 
 long long dir_count(const rtw_dirs* dirs)
 {
@@ -228,7 +375,7 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     size_t off_mask = 0;
     size_t off_tab = align_up(off_mask + sizeof(unsigned int) * (size_t)ndir * (size_t)g.group, 256);
     // double tables then their single-precision copies
-    size_t off_cells = align_up(off_tab + sizeof(double) * 3 * ((size_t)nt + (size_t)nph), 256);
+    size_t off_cells = align_up(off_tab + sizeof(double) * 4 * ((size_t)nt + (size_t)nph), 256);
     size_t off_ldir = align_up(off_cells + sizeof(GridCells) * (size_t)g.group, 256);
     size_t off_ldirf = align_up(off_ldir + sizeof(double) * 4 * nl, 256);
     size_t off_binid = align_up(off_ldirf + sizeof(float4) * nl, 256);
@@ -240,7 +387,11 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     size_t off_cnt = align_up(off_big + 8 * (size_t)big_cap, 256);
     size_t off_hit_tri = align_up(off_cnt + 256, 256);
     size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
-    size_t total = align_up(off_hit_dir + 4 * (size_t)hit_cap, 256);
+    // the sort of the hits by output tile: at most np slots per object
+    const long long ntiles = field_tiles(g.group, np, list, nt, nph, ndir);
+    size_t off_tile = align_up(off_hit_dir + 4 * (size_t)hit_cap, 256);
+    size_t off_perm = align_up(off_tile + 4 * (size_t)tile_words(ntiles), 256);
+    size_t total = align_up(off_perm + 4 * (size_t)hit_cap, 256);
     if (base && w) {
         w->mask_words = (unsigned int*)(base + off_mask);
         w->tab = (double*)(base + off_tab);
@@ -259,6 +410,8 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
         w->hit_dir = (unsigned int*)(base + off_hit_dir);
         w->big_cap = big_cap;
         w->hit_cap = hit_cap;
+        w->tile_ws = (unsigned int*)(base + off_tile);
+        w->perm = (unsigned int*)(base + off_perm);
     }
     return total;
 }
@@ -291,6 +444,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s, std::vector<std::pair<long long, long long>>* slices)
 {
+    const bool tiled = !newton && st.fmax && w.tile_ws && w.perm;
     const int np = st.np;
     const long long ndir = d.ndir;
     const int nout = per_order ? np : 1;
@@ -330,12 +484,13 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
             b.nout = nout;
             return RTW_OK;
         };
+        const unsigned int* fmax = tiled ? st.fmax + g0 : nullptr;
         if (!g.sliced) {
             GridBatch b;
             int rc = batch(g.windowed, win, b);
             if (rc != RTW_OK) return rc;
             RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
-                                       classify_block, newton, s));
+                                       classify_block, newton, s, kFieldAll, fmax, w.tile_ws, w.perm));
         } else {
             long long rows = 0, cols = 0;
             for (int oi = g0; oi < g0 + gn; ++oi) {
@@ -379,7 +534,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                     continue;
                 }
                 RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
-                                           classify_block, newton, s, kFieldSum));
+                                           classify_block, newton, s, kFieldSum, fmax, w.tile_ws, w.perm));
                 fitted.push_back(sl);
             }
             if (slices) {
@@ -387,6 +542,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                 *slices = fitted;
             }
         }
+        if (tiled) RTW_CUDA(launch_field_convert(a.out, (long long)out_obj, gn, fmax, s));
         if (mask_out)
             RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir,
                                           d.list ? 2 : 1, d.nt, d.nph, 0.0, 0.0, s, d.lsrc));
@@ -462,130 +618,8 @@ int rtw_create_object(const rtw_object_desc* desc, int count, const rtw_incident
     *out = nullptr;
     std::vector<ObjHost> hs((size_t)count);
     for (int i = 0; i < count; ++i) {
-        const rtw_object_desc& d = desc[i];
-        const rtw_incident& w = inc[i];
-        ObjHost& o = hs[(size_t)i];
-        if (!(d.a > 0.0 && d.b > 0.0 && d.c > 0.0) || !std::isfinite(d.a + d.b + d.c))
-            return fail(RTW_ERR_ARG, "object %d: semi-axes must be positive", i);
-        const double qn = std::sqrt(d.quat[0] * d.quat[0] + d.quat[1] * d.quat[1] + d.quat[2] * d.quat[2] +
-                                    d.quat[3] * d.quat[3]);
-        if (!(std::fabs(qn - 1.0) <= 1e-9)) return fail(RTW_ERR_ARG, "object %d: |quat| = %.17g != 1", i, qn);
-        if (!(d.m_re > 0.0) || d.m_re == 1.0 || !std::isfinite(d.m_re))
-            return fail(RTW_ERR_ARG, "object %d: m must be positive and != 1", i);
-        if (d.m_im != 0.0) return fail(RTW_ERR_UNSUPPORTED, "object %d: absorbing objects (m_im != 0)", i);
-        if (!(w.wavelength_um > 0.0) || !std::isfinite(w.wavelength_um))
-            return fail(RTW_ERR_ARG, "object %d: wavelength must be positive", i);
-        if (w.kind != RTW_INCIDENT_PLANE && w.kind != RTW_INCIDENT_POINT)
-            return fail(RTW_ERR_ARG, "object %d: incident kind %d", i, w.kind);
-        if (w.kind == RTW_INCIDENT_PLANE && (w.dir[0] != 0.0 || w.dir[1] != 0.0 || w.dir[2] != 1.0))
-            return fail(RTW_ERR_UNSUPPORTED, "object %d: incident direction must be (0, 0, 1)", i);
-        if (w.kind == RTW_INCIDENT_POINT && !std::isfinite(w.source[0] + w.source[1] + w.source[2]))
-            return fail(RTW_ERR_ARG, "object %d: source position must be finite", i);
-        const double se = d.shape_e == 0.0 ? 1.0 : d.shape_e;
-        if (!(se >= 1.0) || !std::isfinite(se))
-            return fail(RTW_ERR_ARG, "object %d: shape exponent %g (0 or 1: ellipsoid, > 1: superellipsoid)", i,
-                        d.shape_e);
-        o.shape_e = se;
-        o.a[0] = d.a;
-        o.a[1] = d.b;
-        o.a[2] = d.c;
-        const double qw = d.quat[0] / qn, qx = d.quat[1] / qn, qy = d.quat[2] / qn, qz = d.quat[3] / qn;
-        o.R[0][0] = 1 - 2 * (qy * qy + qz * qz);
-        o.R[0][1] = 2 * (qx * qy - qw * qz);
-        o.R[0][2] = 2 * (qx * qz + qw * qy);
-        o.R[1][0] = 2 * (qx * qy + qw * qz);
-        o.R[1][1] = 1 - 2 * (qx * qx + qz * qz);
-        o.R[1][2] = 2 * (qy * qz - qw * qx);
-        o.R[2][0] = 2 * (qx * qz - qw * qy);
-        o.R[2][1] = 2 * (qy * qz + qw * qx);
-        o.R[2][2] = 1 - 2 * (qx * qx + qy * qy);
-        for (int k = 0; k < 3; ++k) o.c[k] = d.center[k];
-        o.m = d.m_re;
-        o.lambda = w.wavelength_um;
-        o.jre[0] = w.jones_re[0];
-        o.jre[1] = w.jones_re[1];
-        o.jim[0] = w.jones_im[0];
-        o.jim[1] = w.jones_im[1];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                double s = 0.0;
-                for (int k = 0; k < 3; ++k) s += o.R[r][k] * o.R[c][k] / (o.a[k] * o.a[k]);
-                o.W[r][c] = s;
-            }
-        o.lmax = std::fmax(d.a, std::fmax(d.b, d.c));
-        o.lmin = std::fmin(d.a, std::fmin(d.b, d.c));
-        o.S[0][0] = o.W[0][0] - o.W[0][2] * o.W[0][2] / o.W[2][2];
-        o.S[0][1] = o.W[0][1] - o.W[0][2] * o.W[1][2] / o.W[2][2];
-        o.S[1][0] = o.S[0][1];
-        o.S[1][1] = o.W[1][1] - o.W[1][2] * o.W[1][2] / o.W[2][2];
-        // a superellipsoid lies inside the ellipsoid of semi-axes a_i 3^((1 - 1/e) / 2) (power-mean
-        // inequality), Wb = W / g2; the rays that meet it bound the ray grid (Wb = W for e = 1)
-        const double g2 = se != 1.0 ? std::pow(3.0, 1.0 - 1.0 / se) : 1.0;
-        double Wb[3][3];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) Wb[r][c] = o.W[r][c] / g2;
-        if (se != 1.0)
-            for (int r = 0; r < 2; ++r)
-                for (int c = 0; c < 2; ++c) o.S[r][c] /= g2;
-        o.gc[0] = o.c[0];
-        o.gc[1] = o.c[1];
-        o.src = w.kind == RTW_INCIDENT_POINT;
-        if (o.src) {
-            // rays from the source s through X = c + x e1 + y e2 (v = X - s = g + x e1 + y e2, g = c - s)
-            // hit where (v.W g)^2 - (v.W v)(g.W g - 1) > 0: v^T K v > 0 with K = W g g^T W - (g.W g - 1) W,
-            // an ellipse (w - w0)^T S (w - w0) < 1 of the plane
-            double g[3], Wg[3];
-            for (int k = 0; k < 3; ++k) {
-                o.src_pos[k] = w.source[k];
-                g[k] = o.c[k] - w.source[k];
-            }
-            for (int r = 0; r < 3; ++r) Wg[r] = Wb[r][0] * g[0] + Wb[r][1] * g[1] + Wb[r][2] * g[2];
-            const double gWg = g[0] * Wg[0] + g[1] * Wg[1] + g[2] * Wg[2];
-            if (!(gWg > 1.0))
-                return fail(RTW_ERR_ARG, "object %d: the source lies inside the object (its bounding ellipsoid)", i);
-            const double gd = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            const double ax[3] = {g[0] / gd, g[1] / gd, g[2] / gd};
-            const double ref[3] = {std::fabs(ax[0]) > 0.9 ? 0.0 : 1.0, std::fabs(ax[0]) > 0.9 ? 1.0 : 0.0, 0.0};
-            const double ra = ref[0] * ax[0] + ref[1] * ax[1] + ref[2] * ax[2];
-            double n1 = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                o.e1[k] = ref[k] - ra * ax[k];
-                n1 += o.e1[k] * o.e1[k];
-            }
-            n1 = std::sqrt(n1);
-            for (int k = 0; k < 3; ++k) o.e1[k] /= n1;
-            o.e2[0] = ax[1] * o.e1[2] - ax[2] * o.e1[1];
-            o.e2[1] = ax[2] * o.e1[0] - ax[0] * o.e1[2];
-            o.e2[2] = ax[0] * o.e1[1] - ax[1] * o.e1[0];
-            double K[3][3];
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c) K[r][c] = Wg[r] * Wg[c] - (gWg - 1.0) * Wb[r][c];
-            auto Kv = [&](const double* v, double* out3) {
-                for (int r = 0; r < 3; ++r) out3[r] = K[r][0] * v[0] + K[r][1] * v[1] + K[r][2] * v[2];
-            };
-            auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
-            double Kg[3], K1[3], K2[3];
-            Kv(g, Kg);
-            Kv(o.e1, K1);
-            Kv(o.e2, K2);
-            const double M00 = dot(o.e1, K1), M01 = dot(o.e1, K2), M11 = dot(o.e2, K2);
-            const double b0 = dot(o.e1, Kg), b1 = dot(o.e2, Kg);
-            const double dM = M00 * M11 - M01 * M01;
-            if (!(dM > 0.0)) return fail(RTW_ERR_ARG, "object %d: degenerate view from the source", i);
-            const double w0x = -(M11 * b0 - M01 * b1) / dM, w0y = -(M00 * b1 - M01 * b0) / dM;
-            const double f0 = dot(g, Kg) + b0 * w0x + b1 * w0y;
-            if (!(f0 > 0.0)) return fail(RTW_ERR_ARG, "object %d: degenerate view from the source", i);
-            o.S[0][0] = -M00 / f0;
-            o.S[0][1] = o.S[1][0] = -M01 / f0;
-            o.S[1][1] = -M11 / f0;
-            o.gc[0] = w0x;
-            o.gc[1] = w0y;
-        }
-        const double det = o.S[0][0] * o.S[1][1] - o.S[0][1] * o.S[1][0];
-        o.Sinv[0][0] = o.S[1][1] / det;
-        o.Sinv[0][1] = -o.S[0][1] / det;
-        o.Sinv[1][0] = -o.S[1][0] / det;
-        o.Sinv[1][1] = o.S[0][0] / det;
+        const int rc = rtw::host::make_object_host(desc[i], inc[i], i, hs[(size_t)i]);
+        if (rc != RTW_OK) return rc;
     }
     int dev = 0;
     int rc = ensure_device(&dev);
@@ -654,21 +688,10 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     std::vector<ObjDev> objs((size_t)obj->count);
     long long R = 0;
     for (int i = 0; i < obj->count; ++i) {
-        double h = 0.0, w = 0.0;
-        long long nx = 0, ny = 0;
-        int rc = grid_of(obj->h[(size_t)i], tp, &h, &nx, &ny, &w);
-        if (rc != RTW_OK) return rc;
         ObjDev& d = objs[(size_t)i];
-        fill_objdev(obj->h[(size_t)i], d);
-        d.grid = tp->grid == RTW_GRID_FAN ? rtw::kGridFan : rtw::kGridSquare;
-        d.h = h;
-        d.fan_w = w;
-        d.fan_ex = std::cos(tp->fan_phi);
-        d.fan_ey = std::sin(tp->fan_phi);
-        d.nx = nx;
-        d.ny = ny;
-        d.ray_offset = R;
-        R += nx * ny;
+        int rc = rtw::host::object_device_entry(obj->h[(size_t)i], tp, R, d);
+        if (rc != RTW_OK) return rc;
+        R += d.nx * d.ny;
     }
     // aperture data: fans (the 1-D PO of rtw_field) and square grids in double precision (rtw_field_po2d)
     if ((tp->flags & RTW_TRACE_APERTURE) && tp->grid == RTW_GRID_SQUARE && tp->precision != RTW_FP64)
@@ -676,11 +699,11 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     const bool aux = (tp->flags & RTW_TRACE_APERTURE) != 0;
     // one allocation carved into 256-byte aligned arrays
     const size_t n = (size_t)np * (size_t)R;
-    size_t off[8], total = 0;
+    size_t off[9], total = 0;
     const bool sf = tp->grid == RTW_GRID_SQUARE;  // single-precision directions for the grid field
-    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, aux ? n * 8 * rtw::kAuxCount : 0,
-                             sf ? n * 32 : 0};
-    for (int k = 0; k < 8; ++k) {
+    const size_t sizes[9] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, aux ? n * 8 * rtw::kAuxCount : 0,
+                             sf ? n * 32 : 0, sf ? 4 * (size_t)obj->count : 0};
+    for (int k = 0; k < 9; ++k) {
         off[k] = total;
         total = align_up(total + sizes[k], 256);
     }
@@ -738,7 +761,9 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     r->st.aux = aux ? (double*)(b + off[6]) : nullptr;
     r->st.sf = sf ? (float4*)(b + off[7]) : nullptr;
     r->st.sl = sf ? (float4*)(b + off[7] + n * 16) : nullptr;
+    r->st.fmax = sf ? (unsigned int*)(b + off[8]) : nullptr;
     RTW_CUDA(cudaMemcpyAsync(r->d_objs, r->objs.data(), sizeof(ObjDev) * objs.size(), cudaMemcpyHostToDevice, s));
+    if (sf) RTW_CUDA(cudaMemsetAsync(r->st.fmax, 0, 4 * (size_t)obj->count, s));
     unsigned int* status = status_word(r->device);
     RTW_CUDA(rtw::launch_trace(r->d_objs, r->nobj, r->st, tp->p_max, aux, status, s, super_shapes));
     return RTW_OK;

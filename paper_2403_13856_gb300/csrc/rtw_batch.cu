@@ -32,12 +32,12 @@ struct Chunk {
 };
 
 // bytes of the ray state of R rays and np orders, and its layout (as rtw_trace)
-size_t state_layout(long long R, int np, char* base, RaysDev* st)
+size_t state_layout(long long R, int np, int nobj, char* base, RaysDev* st)
 {
     const size_t n = (size_t)np * (size_t)R;
-    const size_t sizes[7] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, n * 32};
-    size_t off[7], total = 0;
-    for (int k = 0; k < 7; ++k) {
+    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, n * 32, 4 * (size_t)nobj};
+    size_t off[8], total = 0;
+    for (int k = 0; k < 8; ++k) {
         off[k] = total;
         total = align_up(total + sizes[k], 256);
     }
@@ -53,6 +53,7 @@ size_t state_layout(long long R, int np, char* base, RaysDev* st)
         st->aux = nullptr;
         st->sf = (float4*)(base + off[6]);
         st->sl = (float4*)(base + off[6] + n * 16);
+        st->fmax = (unsigned int*)(base + off[7]);
     }
     return total;
 }
@@ -119,8 +120,9 @@ int enqueue(rtw_batch* b, const rtw_batch_params* bp, const rtw_dirs* dirs, bool
     int e = 0;
     for (const Chunk& c : b->chunks) {
         RaysDev st{};
-        state_layout(c.R, np, (char*)b->state, &st);
+        state_layout(c.R, np, c.count, (char*)b->state, &st);
         st.precision = bp->precision;
+        RTW_CUDA(cudaMemsetAsync(st.fmax, 0, 4 * (size_t)c.count, q));
         if (timing) RTW_CUDA(cudaEventRecord(b->ev[(size_t)e++], q));
         RTW_CUDA(rtw::launch_trace_items(b->d_objs + c.first, c.count, st, bp->p_max, counter, c.nitems, variant,
                                          bp->trace_ctas_per_sm, q));
@@ -210,7 +212,7 @@ int rtw_far_field_batch(const rtw_object* obj, const rtw_batch_params* bp, const
     ws_plan.group = 1;
     for (Chunk& c : chunks) {
         c.plan = rtw::host::plan_grid(objs.data() + c.first, c.count, np, dirs);
-        state_bytes = std::max(state_bytes, state_layout(c.R, np, nullptr, nullptr));
+        state_bytes = std::max(state_bytes, state_layout(c.R, np, c.count, nullptr, nullptr));
         ws_plan.group = std::max(ws_plan.group, c.plan.group);
         ws_plan.max_group_cells = std::max(ws_plan.max_group_cells, c.plan.max_group_cells);
     }

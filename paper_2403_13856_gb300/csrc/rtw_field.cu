@@ -91,11 +91,13 @@ __device__ __forceinline__ void add_contribution(const double* F, double psi, co
 // ---------------------------------------------------------------------------------------------
 // direction tables: cos(theta_i), sin(theta_i), cos(phi_j), sin(phi_j)
 // ---------------------------------------------------------------------------------------------
-// double tables (4 x n) followed by single-precision copies (4 x n floats)
+// double tables (4 x n) followed by single-precision copies (4 x n floats) and the remainders of
+// those copies (4 x n floats: value = copy + remainder to about 2^-48)
 __global__ void dir_tables_kernel(int nt, int nph, double* tab)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float* ftab = reinterpret_cast<float*>(tab + 2 * (nt + nph));
+    float* ltab = ftab + 2 * (nt + nph);
     if (i < nt) {
         double s, c;
         sincos((i + 0.5) * (kPi / nt), &s, &c);
@@ -103,6 +105,8 @@ __global__ void dir_tables_kernel(int nt, int nph, double* tab)
         tab[nt + i] = s;
         ftab[i] = (float)c;
         ftab[nt + i] = (float)s;
+        ltab[i] = (float)(c - (double)(float)c);
+        ltab[nt + i] = (float)(s - (double)(float)s);
     }
     if (i < nph) {
         double s, c;
@@ -111,6 +115,8 @@ __global__ void dir_tables_kernel(int nt, int nph, double* tab)
         tab[2 * nt + nph + i] = s;
         ftab[2 * nt + i] = (float)c;
         ftab[2 * nt + nph + i] = (float)s;
+        ltab[2 * nt + i] = (float)(c - (double)(float)c);
+        ltab[2 * nt + nph + i] = (float)(s - (double)(float)s);
     }
 }
 
@@ -1156,7 +1162,493 @@ __global__ void list_fill_kernel(const int* __restrict__ binid, long long n, con
     bin_dir[first[b] + atomicAdd(cursor + b, 1)] = (int)i;
 }
 
+// ---------------------------------------------------------------------------------------------
+// square grid: summing the hits.  The hits of the classification are sorted by tile of the output
+// (kTileTh x kTileTw grid directions, or kTileDirs consecutive directions of a list, of one object
+// and output slot): a counting pass, an exclusive scan of the counts and a filling pass write the
+// hit indices in tile order.  A CTA then takes a run of sorted hits: each hit is decided and
+// interpolated, and its contribution F e^{i Psi} is added in shared memory as a 64-bit fixed-point
+// number; the tile's words go out once (an integer add per non-zero word, since a long tile may
+// span CTAs), and a last pass turns them into doubles.  Integer sums do not depend on their order,
+// so the field is the same bit for bit from run to run.  On GB300 the double-precision pipe (which
+// also converts between precisions) issues 1.6 operations per clock per SM, against 128 for single
+// precision: the edge planes of a hit are double-float (pairs of floats, error-free products and
+// sums), F is interpolated in single precision from corner values narrowed in the integer pipe
+// (f64_to_f32_int), and double precision is kept for the phase (about ten operations per hit).
+// ---------------------------------------------------------------------------------------------
+constexpr int kTileTh = 8, kTileTw = 16, kTileDirs = kTileTh * kTileTw;
+constexpr int kSumThreads = 256, kSumChunk = 1024;  // hits per CTA of the summing pass
+// fixed point: a value v with |v| < 2^eB (eB the bound of the object's |F|) is stored as
+// round(v 2^(46 - eB)); 2^16 such values add without leaving the 63-bit range
+constexpr int kFixBits = 46;
+
+struct TileGrid {
+    int ntr, ntc;             // tile rows and columns of one slot (a list: one row)
+    int nslots;               // output slots per object (orders, or 1)
+    long long ntiles;         // objects x slots x ntr x ntc of the launch
+    unsigned int* offs;       // ntiles + 1: counts, then their exclusive scan
+    unsigned int* cursor;     // ntiles + 1
+    unsigned int* bsum;       // block sums of the scan
+    unsigned int* perm;       // hit indices in tile order (hit list capacity)
+    const unsigned int* fmax; // per object of the launch: bits of the largest |F|^2
+};
+
+// tile of hit (code, direction dk) and the direction's place in it
+__device__ __forceinline__ long long hit_tile(const FieldArgs& a, const GridBatch& b, const DirSet& d,
+                                              const TileGrid& tg, unsigned long long code, unsigned int dk, int& q)
+{
+    const CellRef c = decode_cell(a, b, (long long)(code >> 1));
+    const int slot = a.per_order ? c.p : 0;
+    int tr, tc;
+    if (d.list) {
+        tr = 0;
+        tc = (int)(dk / (unsigned int)kTileDirs);
+        q = (int)(dk - (unsigned int)tc * kTileDirs);
+    } else {
+        const int it = (int)(dk / (unsigned int)d.nph), jp = (int)(dk - (unsigned int)it * d.nph);
+        tr = it / kTileTh;
+        tc = jp / kTileTw;
+        q = (it - tr * kTileTh) * kTileTw + (jp - tc * kTileTw);
+    }
+    return ((long long)c.orel * tg.nslots + slot) * tg.ntr * tg.ntc + (long long)tr * tg.ntc + tc;
+}
+
+// Counting (fill 0) or filling pass (fill 1) over the hit list, a warp's hits of one tile counted
+// or placed together.  The tile of a hit is integer arithmetic, so both passes agree; the fill
+// still stays inside each tile's range.
+__global__ void __launch_bounds__(256) hit_bin_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h, TileGrid tg,
+                                                      int fill)
+{
+    const unsigned int n = min(*h.n, h.cap);
+    const int lane = threadIdx.x & 31;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int q;
+        const long long tile = hit_tile(a, b, d, tg, h.tri[i], h.dir[i] & ~kHitClose, q);
+        const unsigned int act = __activemask();
+        const unsigned int peers = __match_any_sync(act, (unsigned long long)tile);
+        const int leader = __ffs(peers) - 1;
+        if (!fill) {
+            if (lane == leader) atomicAdd(tg.offs + tile, (unsigned int)__popc(peers));
+        } else {
+            unsigned int base = 0;
+            if (lane == leader) base = atomicAdd(tg.cursor + tile, (unsigned int)__popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            const unsigned int pos = tg.offs[tile] + base + __popc(peers & ((1u << lane) - 1u));
+            if (pos < tg.offs[tile + 1]) tg.perm[pos] = (unsigned int)i;
+        }
+    }
+}
+
+// exclusive scan of n words in place: blocks of kScanTile words, then the block sums, then the
+// offsets added back
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ unsigned int block_exclusive_scan(unsigned int x, unsigned int* warp_sums,
+                                                             unsigned int& total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned int v = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_sums[lane] = v;  // inclusive over warps
+    }
+    __syncthreads();
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    const unsigned int before = w > 0 ? warp_sums[w - 1] : 0u;
+    __syncthreads();
+    return before + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned int* v, long long n, unsigned int* bsum)
+{
+    __shared__ unsigned int ws[32];
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+    unsigned int x[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        x[k] = base + k < n ? v[base + k] : 0u;
+        s += x[k];
+    }
+    unsigned int total;
+    unsigned int run = block_exclusive_scan(s, ws, total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) v[base + k] = run;
+        run += x[k];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(unsigned int* bsum, int nb)
+{
+    __shared__ unsigned int ws[32];
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int i0 = threadIdx.x * per;
+    unsigned int s = 0;
+    for (int k = 0; k < per && i0 + k < nb; ++k) s += bsum[i0 + k];
+    unsigned int total;
+    unsigned int run = block_exclusive_scan(s, ws, total);
+    for (int k = 0; k < per && i0 + k < nb; ++k) {
+        const unsigned int x = bsum[i0 + k];
+        bsum[i0 + k] = run;
+        run += x;
+    }
+}
+
+__global__ void scan_add_kernel(unsigned int* v, long long n, const unsigned int* bsum)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) v[i] += bsum[i / kScanTile];
+}
+
+// ---- double-float pieces ----
+struct F2 {
+    float h, l;
+};
+
+// a b as an unevaluated pair: the rounded product, then its error and the products with the low parts
+__device__ __forceinline__ F2 df_mul(float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    return F2{p, e};
+}
+
+// component k of a x b (a_y b_z - a_z b_y and cyclic), a and b given as hi + lo
+__device__ __forceinline__ F2 df_cross_k(const float* ah, const float* al, const float* bh, const float* bl, int k)
+{
+    const int i = (k + 1) % 3, j = (k + 2) % 3;
+    const F2 p = df_mul(ah[i], al[i], bh[j], bl[j]);
+    const F2 q = df_mul(ah[j], al[j], bh[i], bl[i]);
+    float s, e;
+    df_two_sum(p.h, -q.h, s, e);
+    e = __fadd_rn(e, __fsub_rn(p.l, q.l));
+    df_fast_two_sum(s, e, s, e);
+    return F2{s, e};
+}
+
+// n . x as a normalised pair (n and x given as hi + lo)
+__device__ __forceinline__ F2 df_dot(const float* nh, const float* nl, const float* xh, const float* xl)
+{
+    float s = 0.0f, t = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const F2 p = df_mul(nh[c], nl[c], xh[c], xl[c]);
+        float u, e;
+        df_two_sum(s, p.h, u, e);
+        s = u;
+        t = __fadd_rn(t, __fadd_rn(e, p.l));
+    }
+    df_fast_two_sum(s, t, s, t);
+    return F2{s, t};
+}
+
+// single to double precision in the integer pipe (exact for normal numbers; subnormals give 0)
+__device__ __forceinline__ double f32_to_f64_int(float v)
+{
+    const unsigned int u = __float_as_uint(v);
+    const unsigned int e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// v 2^k rounded to an integer (|v| 2^k < 2^62), in the integer pipe
+__device__ __forceinline__ unsigned long long to_fixed(float v, int k)
+{
+    const unsigned int u = __float_as_uint(v);
+    const int ex = (int)((u >> 23) & 0xffu);
+    if (ex == 0) return 0ull;
+    const unsigned long long m = (unsigned long long)((u & 0x7fffffu) | 0x800000u);
+    const int sh = ex - 127 - 23 + k;
+    long long r;
+    if (sh >= 0) r = (long long)(m << sh);
+    else if (sh > -26) r = (long long)((m + (1ull << (-sh - 1))) >> -sh);
+    else r = 0;
+    return (unsigned long long)((u >> 31) ? -r : r);
+}
+
+// fixed-point exponent of object orel: kFixBits - e with max |F| < 2^e
+__device__ __forceinline__ int fix_exponent(const unsigned int* fmax, int orel)
+{
+    const float b2 = __uint_as_float(fmax[orel]);
+    if (!(b2 > 0.0f)) return 0;
+    int eb;
+    frexpf(sqrtf(b2) * 1.0000005f, &eb);
+    return kFixBits - eb;
+}
+
+// One hit: the exact test of a close call, the weights, F and Psi interpolated, F e^{i Psi} added to
+// the kNc words of acc (the tile's direction q); a singular cell marks the direction instead.
+template <int kNc>
+__device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b, const DirSet& d, const float* lt,
+                                         unsigned long long code, unsigned int dw, int kfix, unsigned long long* acc,
+                                         int q)
+{
+    const bool close = (dw & kHitClose) != 0;
+    const unsigned int dk = dw & ~kHitClose;
+    const CellRef c = decode_cell(a, b, (long long)(code >> 1));
+    TriGeom g;
+    load_triangle(a, c.base, c.nx, c.cx, c.cy, (int)(code & 1ull), g);
+    // the direction (hi + lo) and its e_theta, e_phi
+    float xh[3], xl[3], eth[3], eph[3];
+    if (d.list) {
+        const double* qd = d.ldir + 4 * (long long)dk;
+        const double ct = qd[0], st = qd[1], cp = qd[2], sp = qd[3];
+        const double x[3] = {st * cp, st * sp, ct};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            xh[k] = f64_to_f32_int(x[k]);
+            xl[k] = f64_to_f32_int(x[k] - f32_to_f64_int(xh[k]));
+        }
+        const float ctf = f64_to_f32_int(ct), stf = f64_to_f32_int(st), cpf = f64_to_f32_int(cp),
+                    spf = f64_to_f32_int(sp);
+        eth[0] = ctf * cpf;
+        eth[1] = ctf * spf;
+        eth[2] = -stf;
+        eph[0] = -spf;
+        eph[1] = cpf;
+        eph[2] = 0.0f;
+    } else {
+        const int nt = d.nt, nph = d.nph;
+        const int it = (int)(dk / (unsigned int)nph), jp = (int)(dk - (unsigned int)it * nph);
+        const float* ft = reinterpret_cast<const float*>(d.tab + 2 * (nt + nph));
+        const float cth = ft[it], sth = ft[nt + it], cph = ft[2 * nt + jp], sph = ft[2 * nt + nph + jp];
+        const float ctl = lt[it], stl = lt[nt + it], cpl = lt[2 * nt + jp], spl = lt[2 * nt + nph + jp];
+        const F2 xx = df_mul(sth, stl, cph, cpl), xy = df_mul(sth, stl, sph, spl);
+        xh[0] = xx.h;
+        xl[0] = xx.l;
+        xh[1] = xy.h;
+        xl[1] = xy.l;
+        xh[2] = cth;
+        xl[2] = ctl;
+        eth[0] = cth * cph;
+        eth[1] = cth * sph;
+        eth[2] = -sth;
+        eph[0] = -sph;
+        eph[1] = cph;
+        eph[2] = 0.0f;
+    }
+    // edge planes with their endpoints in index order (both triangles of an edge evaluate the same
+    // plane), double-float values at the direction
+    F2 e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int va = k, vb = (k + 1) % 3;
+        const bool fwd = g.id[va] < g.id[vb];
+        float ah[3], al[3], bh[3], bl[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            ah[r] = fwd ? g.s[va][r] : g.s[vb][r];
+            al[r] = fwd ? g.l[va][r] : g.l[vb][r];
+            bh[r] = fwd ? g.s[vb][r] : g.s[va][r];
+            bl[r] = fwd ? g.l[vb][r] : g.l[va][r];
+        }
+        float nh[3], nl[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const F2 n = df_cross_k(ah, al, bh, bl, r);
+            nh[r] = n.h;
+            nl[r] = n.l;
+        }
+        e[k] = df_dot(nh, nl, xh, xl);
+        if (!fwd) {
+            e[k].h = -e[k].h;
+            e[k].l = -e[k].l;
+        }
+    }
+    if (close) {
+        // orientation s0 . (s1 x s2), then the half-open rule (edge_in) in double-float
+        float nh[3], nl[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const F2 n = df_cross_k(g.s[1], g.l[1], g.s[2], g.l[2], r);
+            nh[r] = n.h;
+            nl[r] = n.l;
+        }
+        const F2 v = df_dot(nh, nl, g.s[0], g.l[0]);
+        const int sigma = v.h > 0.0f ? 1 : (v.h < 0.0f ? -1 : 0);
+        if (sigma == 0) return;
+        auto in = [&](const F2& ev, long long ia, long long ib) {
+            const float se = sigma > 0 ? ev.h : -ev.h;
+            if (se > 0.0f) return true;
+            if (se < 0.0f) return false;
+            return (ia < ib) == (sigma > 0);
+        };
+        if (!in(e[0], g.id[0], g.id[1]) || !in(e[1], g.id[1], g.id[2]) || !in(e[2], g.id[2], g.id[0])) return;
+        const uint32_t* f = g.f;
+        const bool ok = flag_nf(f[0]) == flag_nf(f[1]) && flag_nf(f[1]) == flag_nf(f[2]) &&
+                        ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
+                        ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0 && sigma == ((f[0] & kFlagOrient) ? 1 : -1);
+        if (!ok) {
+            atomicOr(a.mask + (long long)c.orel * b.ndir + dk, kMaskCaustic);
+            return;
+        }
+    }
+    // weights of the central projection: l0 = e12 / S, l1 = e20 / S, l2 = e01 / S, S their sum
+    const df S = df(e[0].h, e[0].l) + df(e[1].h, e[1].l) + df(e[2].h, e[2].l);
+    const df w1 = df(e[2].h, e[2].l) / S, w2 = df(e[0].h, e[0].l) / S;
+    const float l1 = w1.hi, l2 = w2.hi, l0 = 1.0f - l1 - l2;
+    // corner F narrowed in the integer pipe, Psi in double precision
+    float Fi[6];
+    double ps[3];
+    {
+        float F[3][6];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const long long i = c.base + g.id[v];
+            const double2 fx = a.st.Fx[i], fy = a.st.Fy[i], fz = a.st.Fz[i];
+            F[v][0] = f64_to_f32_int(fx.x);
+            F[v][1] = f64_to_f32_int(fx.y);
+            F[v][2] = f64_to_f32_int(fy.x);
+            F[v][3] = f64_to_f32_int(fy.y);
+            F[v][4] = f64_to_f32_int(fz.x);
+            F[v][5] = f64_to_f32_int(fz.y);
+            ps[v] = a.st.s2psi[i].y;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Fi[k] = l0 * F[0][k] + l1 * F[1][k] + l2 * F[2][k];
+    }
+    constexpr double kInv2Pi = 0.15915494309189533577, k2PiHi = 6.28318530717958623200;
+    const double L1 = f32_to_f64_int(w1.hi) + f32_to_f64_int(w1.lo);
+    const double L2 = f32_to_f64_int(w2.hi) + f32_to_f64_int(w2.lo);
+    const double psi = fma(L1, ps[1] - ps[0], fma(L2, ps[2] - ps[0], ps[0]));
+    float sp, cp;
+    sincosf(f64_to_f32_int(fma(-k2PiHi, rint(psi * kInv2Pi), psi)), &sp, &cp);
+    float rr = 0.0f, ri = 0.0f, tr = 0.0f, ti = 0.0f, pr = 0.0f, pi = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float re = Fi[2 * k] * cp - Fi[2 * k + 1] * sp;
+        const float im = Fi[2 * k] * sp + Fi[2 * k + 1] * cp;
+        tr += re * eth[k];
+        ti += im * eth[k];
+        pr += re * eph[k];
+        pi += im * eph[k];
+        if constexpr (kNc == 6) {
+            rr += re * xh[k];
+            ri += im * xh[k];
+        }
+    }
+    unsigned long long* dst = acc + q * kNc;
+    if constexpr (kNc == 6) {
+        atomicAdd(dst + 0, to_fixed(rr, kfix));
+        atomicAdd(dst + 1, to_fixed(ri, kfix));
+        dst += 2;
+    }
+    atomicAdd(dst + 0, to_fixed(tr, kfix));
+    atomicAdd(dst + 1, to_fixed(ti, kfix));
+    atomicAdd(dst + 2, to_fixed(pr, kfix));
+    atomicAdd(dst + 3, to_fixed(pi, kfix));
+}
+
+template <int kNc>
+__global__ void __launch_bounds__(kSumThreads, 2) tile_sum_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h,
+                                                                  TileGrid tg)
+{
+    __shared__ unsigned long long acc[kTileDirs * kNc];
+    const unsigned int n = min(*h.n, h.cap);
+    const unsigned int e_begin = blockIdx.x * (unsigned int)kSumChunk;
+    if (e_begin >= n) return;
+    const unsigned int e_end = min(n, e_begin + (unsigned int)kSumChunk);
+    const float* lt = reinterpret_cast<const float*>(d.tab + 2 * (d.nt + d.nph)) + 2 * (d.nt + d.nph);
+    // tile of the first hit: the last tile whose offset is at most e_begin
+    long long lo = 0, hi = tg.ntiles - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (tg.offs[mid] <= e_begin) lo = mid;
+        else hi = mid - 1;
+    }
+    long long tile = lo;
+    const long long per_obj = (long long)tg.nslots * tg.ntr * tg.ntc;
+    unsigned int e0 = e_begin;
+    while (e0 < e_end) {
+        while (tg.offs[tile + 1] <= e0) ++tile;
+        const unsigned int seg_end = min(e_end, tg.offs[tile + 1]);
+        const int orel = (int)(tile / per_obj);
+        const long long rem = tile - (long long)orel * per_obj;
+        const int slot = (int)(rem / ((long long)tg.ntr * tg.ntc));
+        const int trc = (int)(rem - (long long)slot * tg.ntr * tg.ntc);
+        const int tr = trc / tg.ntc, tc = trc - tr * tg.ntc;
+        const int kfix = fix_exponent(tg.fmax, orel);
+        for (int i = threadIdx.x; i < kTileDirs * kNc; i += kSumThreads) acc[i] = 0ull;
+        __syncthreads();
+        for (unsigned int e = e0 + threadIdx.x; e < seg_end; e += kSumThreads) {
+            const unsigned int hi_ = tg.perm[e];
+            if (hi_ >= n) continue;  // every slot is filled; this only guards the read below
+            const unsigned long long code = h.tri[hi_];
+            const unsigned int dw = h.dir[hi_];
+            const unsigned int dk = dw & ~kHitClose;
+            int q;
+            if (d.list) q = (int)(dk % (unsigned int)kTileDirs);
+            else {
+                const int it = (int)(dk / (unsigned int)d.nph), jp = (int)(dk - (unsigned int)it * d.nph);
+                q = (it - tr * kTileTh) * kTileTw + (jp - tc * kTileTw);
+            }
+            tile_hit<kNc>(a, b, d, lt, code, dw, kfix, acc, q);
+        }
+        __syncthreads();
+        // the tile's words, one integer add each where not zero
+        const long long ndir = b.ndir;
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(a.out);
+        for (int i = threadIdx.x; i < kTileDirs * kNc; i += kSumThreads) {
+            const unsigned long long v = acc[i];
+            if (!v) continue;
+            const int qq = i / kNc, comp = i - qq * kNc;
+            long long dk;
+            if (d.list) dk = (long long)tc * kTileDirs + qq;
+            else dk = (long long)(tr * kTileTh + qq / kTileTw) * d.nph + (tc * kTileTw + qq % kTileTw);
+            atomicAdd(out + ((((long long)orel * ndir + dk) * b.nout + slot) * kNc + comp), v);
+        }
+        __syncthreads();
+        e0 = seg_end;
+    }
+}
+
+// fixed-point words of the launch's objects to doubles, in place
+__global__ void tile_convert_kernel(double* out, long long per_obj, long long n, const unsigned int* fmax)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long v = __double_as_longlong(out[i]);
+    if (!v) return;
+    // 2^-k as a double built from its exponent field (|k| well below 1000)
+    const int k = fix_exponent(fmax, (int)(i / per_obj));
+    out[i] = (double)v * __longlong_as_double((long long)(1023 - k) << 52);
+}
+
 }  // namespace
+
+long long tile_words(long long ntiles) { return 2 * (ntiles + 1) + (ntiles + 1 + kScanTile - 1) / kScanTile; }
+
+long long field_tiles(int nobj, int nslots, bool list, int nt, int nph, long long ndir)
+{
+    const long long ntr = list ? 1 : (nt + kTileTh - 1) / kTileTh;
+    const long long ntc = list ? (ndir + kTileDirs - 1) / kTileDirs : (nph + kTileTw - 1) / kTileTw;
+    return (long long)nobj * nslots * ntr * ntc;
+}
+
+cudaError_t launch_field_convert(double* out, long long per_obj, int nobj, const unsigned int* fmax, cudaStream_t s)
+{
+    const long long n = per_obj * nobj;
+    if (n <= 0) return cudaSuccess;
+    tile_convert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, per_obj, n, fmax);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bin_dirs(const double* list, long long n, int nt, int nph, double* ldir, float4* ldir_f,
                             int* binid, int* count, int* first, int* cursor, int* bin_dir, cudaStream_t s)
@@ -1182,7 +1674,8 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
-                              int newton, cudaStream_t s, int stage)
+                              int newton, cudaStream_t s, int stage, const unsigned int* fmax,
+                              unsigned int* tile_ws, unsigned int* perm)
 {
     if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
@@ -1200,8 +1693,36 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirS
         field_grid_big_kernel<<<(unsigned)(32 * sms), 32 * kBigWarps, 0, s>>>(a, b, d, big, nbig, big_cap, h);
     }
     if (stage != 1) {
-        if (newton) field_grid_hit_kernel<true><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
-        else field_grid_hit_kernel<false><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
+        if (newton) {
+            field_grid_hit_kernel<true><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
+        } else if (!fmax || !tile_ws || !perm) {
+            field_grid_hit_kernel<false><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
+        } else {
+            // hits sorted by tile, each tile summed in fixed point (the words turn into doubles in
+            // launch_field_convert once the launch group is complete)
+            TileGrid tg;
+            tg.ntr = d.list ? 1 : (d.nt + kTileTh - 1) / kTileTh;
+            tg.ntc = d.list ? (int)((d.ndir + kTileDirs - 1) / kTileDirs) : (d.nph + kTileTw - 1) / kTileTw;
+            tg.nslots = b.nout;
+            tg.ntiles = field_tiles(b.nobj, b.nout, d.list != 0, d.nt, d.nph, d.ndir);
+            const long long n1 = tg.ntiles + 1;
+            const long long nb = (n1 + kScanTile - 1) / kScanTile;
+            tg.offs = tile_ws;
+            tg.cursor = tile_ws + n1;
+            tg.bsum = tile_ws + 2 * n1;
+            tg.perm = perm;
+            tg.fmax = fmax;
+            cudaError_t e = cudaMemsetAsync(tile_ws, 0, sizeof(unsigned int) * (size_t)(2 * n1), s);
+            if (e != cudaSuccess) return e;
+            hit_bin_kernel<<<(unsigned)(16 * sms), 256, 0, s>>>(a, b, d, h, tg, 0);
+            scan_blocks_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(tg.offs, n1, tg.bsum);
+            scan_sums_kernel<<<1, kScanThreads, 0, s>>>(tg.bsum, (int)nb);
+            scan_add_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(tg.offs, n1, tg.bsum);
+            hit_bin_kernel<<<(unsigned)(16 * sms), 256, 0, s>>>(a, b, d, h, tg, 1);
+            const unsigned gs = (unsigned)((hit_cap + kSumChunk - 1) / kSumChunk);
+            if (a.st.near_r > 0.0) tile_sum_kernel<6><<<gs, kSumThreads, 0, s>>>(a, b, d, h, tg);
+            else tile_sum_kernel<4><<<gs, kSumThreads, 0, s>>>(a, b, d, h, tg);
+        }
     }
     return cudaGetLastError();
 }

@@ -47,6 +47,11 @@ unsigned long long* newton_counter(int dev);
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void fill_objdev(const ObjHost& o, ObjDev& d);
+// validates one object description and its incident wave and fills o (host arithmetic only, no
+// device call); i numbers the object in error messages
+int make_object_host(const rtw_object_desc& d, const rtw_incident& w, int i, ObjHost& o);
+// the device table entry of o for the ray grid of tp, its rays starting at ray_offset
+int object_device_entry(const ObjHost& o, const rtw_trace_params* tp, long long ray_offset, ObjDev& d);
 // ray grid of one object: spacing, size, fan half-width (host arithmetic only)
 int grid_of(const ObjHost& o, const rtw_trace_params* tp, double* h, long long* nx, long long* ny, double* fan_w);
 
@@ -87,6 +92,8 @@ struct GridWs {
     unsigned long long* hit_tri = nullptr;
     unsigned int* hit_dir = nullptr;
     unsigned int big_cap = 0, hit_cap = 0;
+    unsigned int* tile_ws = nullptr;     // the sort of the hits by output tile
+    unsigned int* perm = nullptr;        //   and their order (hit_cap words)
 };
 // Bytes of the workspace of plan g; carves it from base when base is not null.
 size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, GridWs* w);
@@ -105,7 +112,9 @@ int dirs_prepare(const rtw_dirs* dirs, const GridWs& w, DirSet* d, cudaStream_t 
 // does not fit the hit list is split by its count before any of its hits is summed.  slices
 // (optional, in and out): row slices to start from when they cover the run's rows (else the whole
 // grid); receives the slices that fitted, so that the next run on the same rays and directions
-// takes them directly.
+// takes them directly.  Without Newton refinement, on rays that keep their amplitude bound
+// (RaysDev::fmax), the hits are summed per output tile in 64-bit fixed point (the same field bit
+// for bit from run to run) and turned into doubles once a group is complete.
 int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const RaysDev& st, const GridPlan& g,
                    const rtw_dirs* dirs, const DirSet& d, bool per_order, double* out, unsigned char* mask_out,
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,

@@ -186,7 +186,7 @@ int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned
     };
     const size_t o_obj = take(sizeof(rtw::ObjDev) * od.size());
     const size_t o_feat = take(sizeof(rtw::ObjFeat) * of.size());
-    const size_t o_tab = take(sizeof(double) * 3 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi));
+    const size_t o_tab = take(sizeof(double) * 4 * ((size_t)dirs->n_theta + (size_t)dirs->n_phi));
     const size_t o_x = take(sizeof(__nv_bfloat16) * rtw::kMlpIn * (size_t)rows_max);
     const size_t o_y = take(sizeof(float) * rtw::kMlpOut * (size_t)rows_max);
     const size_t o_mask = take(sizeof(unsigned int) * (size_t)rows_max);

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "rtw.h"
+#include "rtw_host.h"
 #include "rtw_launch.h"
 
 namespace {
@@ -91,64 +92,17 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     if (!(std::fabs(dirs->dalpha) > 0.0) || std::fabs(dirs->dalpha) > 0.5 ||
         std::fabs(dirs->dalpha) * dirs->n_theta > 2.0 * kPi + 1e-9)
         return set_error(RTW_ERR_ARG, "plane grid needs 0 < |dalpha| <= 0.5 and a span <= 2 pi");
-    // object validation and tables (the same rules as rtw_create_object)
-    if (!(d->a > 0.0 && d->b > 0.0 && d->c > 0.0)) return set_error(RTW_ERR_ARG, "semi-axes must be positive");
-    const double qn = std::sqrt(d->quat[0] * d->quat[0] + d->quat[1] * d->quat[1] + d->quat[2] * d->quat[2] +
-                                d->quat[3] * d->quat[3]);
-    if (!(std::fabs(qn - 1.0) <= 1e-9)) return set_error(RTW_ERR_ARG, "|quat| != 1");
-    if (!(d->m_re > 0.0) || d->m_re == 1.0) return set_error(RTW_ERR_ARG, "m must be positive and != 1");
-    if (d->m_im != 0.0) return set_error(RTW_ERR_UNSUPPORTED, "absorbing objects");
-    if (!(w->wavelength_um > 0.0)) return set_error(RTW_ERR_ARG, "wavelength must be positive");
+    // object validation and tables: the same host helpers as rtw_create_object and rtw_trace
     if (w->kind != RTW_INCIDENT_PLANE) return set_error(RTW_ERR_UNSUPPORTED, "plane waves only");
     if (d->shape_e != 0.0 && d->shape_e != 1.0) return set_error(RTW_ERR_UNSUPPORTED, "ellipsoids only");
-    if (w->dir[0] != 0.0 || w->dir[1] != 0.0 || w->dir[2] != 1.0)
-        return set_error(RTW_ERR_UNSUPPORTED, "incident direction must be (0, 0, 1)");
-
-    const double qw = d->quat[0] / qn, qx = d->quat[1] / qn, qy = d->quat[2] / qn, qz = d->quat[3] / qn;
-    const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
-                            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
-                            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-    const double ax[3] = {d->a, d->b, d->c};
-    double W[3][3];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            double s = 0.0;
-            for (int k = 0; k < 3; ++k) s += R[r][k] * R[c][k] / (ax[k] * ax[k]);
-            W[r][c] = s;
-        }
-    const double S00 = W[0][0] - W[0][2] * W[0][2] / W[2][2];
-    const double S01 = W[0][1] - W[0][2] * W[1][2] / W[2][2];
-    const double S11 = W[1][1] - W[1][2] * W[1][2] / W[2][2];
-    const double lmax = std::fmax(d->a, std::fmax(d->b, d->c)), lmin = std::fmin(d->a, std::fmin(d->b, d->c));
+    rtw::host::ObjHost oh;
+    int rc = rtw::host::make_object_host(*d, *w, 0, oh);
+    if (rc != RTW_OK) return rc;
     rtw::ObjDev o;
-    std::memset(&o, 0, sizeof(o));
-    o.W[0] = W[0][0]; o.W[1] = W[0][1]; o.W[2] = W[0][2];
-    o.W[3] = W[1][1]; o.W[4] = W[1][2]; o.W[5] = W[2][2];
-    for (int i = 0; i < 3; ++i) o.c[i] = d->center[i];
-    o.m = d->m_re;
-    o.lambda = w->wavelength_um;
-    o.k0 = 2.0 * kPi / w->wavelength_um;
-    o.jre[0] = w->jones_re[0]; o.jre[1] = w->jones_re[1];
-    o.jim[0] = w->jones_im[0]; o.jim[1] = w->jones_im[1];
-    o.zstart = d->center[2] - 2.0 * lmax - 1.0;
-    o.S[0] = S00; o.S[1] = S01; o.S[2] = S11;
-    o.cap = lmax * lmax * std::cbrt(lmax / w->wavelength_um);
-    o.lmin = lmin;
-    o.lmax = lmax;
-    const double e0 = std::cos(tp->fan_phi), e1 = std::sin(tp->fan_phi);
-    const double fw = 1.0 / std::sqrt(e0 * (S00 * e0 + S01 * e1) + e1 * (S01 * e0 + S11 * e1));
-    o.grid = rtw::kGridFan;
-    o.h = 2.0 * fw / (double)tp->n_rays;
-    o.fan_w = fw;
-    o.fan_ex = e0;
-    o.fan_ey = e1;
-    o.nx = tp->n_rays;
-    o.ny = 1;
-    o.ray_offset = 0;
+    if ((rc = rtw::host::object_device_entry(oh, tp, 0, o)) != RTW_OK) return rc;
 
     unsigned char* base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc != RTW_OK) return rc;
+    if ((rc = scratch_address(&base)) != RTW_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const long long R_ = tp->n_rays, n = R_ * np;
     rtw::RaysDev st{};

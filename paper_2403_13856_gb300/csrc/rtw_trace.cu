@@ -17,6 +17,7 @@ struct StateSink {
     long long j;
     bool aux;
     unsigned int emitted;
+    float f2max;  // largest |F|^2 of the ray's valid records that are not near-caustic
 
     __device__ void emit(int p, const ExitWave& w)
     {
@@ -33,6 +34,15 @@ struct StateSink {
         st.Fy[i] = make_double2(fr.F[2], fr.F[3]);
         st.Fz[i] = make_double2(fr.F[4], fr.F[5]);
         st.flags[i] = fr.flags;
+        if (st.fmax && !(fr.flags & kFlagCaustic)) {
+            float f2 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float v = f64_to_f32_int(fr.F[c]);
+                f2 = fmaf(v, v, f2);
+            }
+            f2max = fmaxf(f2max, f2);
+        }
         if (st.sf) {
             const float hx = (float)fr.s[0], hy = (float)fr.s[1], hz = (float)fr.s[2];
             st.sf[i] = make_float4(hx, hy, hz, 0.0f);
@@ -105,10 +115,21 @@ __device__ __forceinline__ int find_object(const ObjDev* objs, int nobj, long lo
 
 // traces global ray j of object o and clears the flags of the orders it does not reach
 // kSuper: the object set holds superellipsoids; each object takes the path of its own shape.
-template <typename T, bool kNear = false, bool kSuper = false>
-__device__ __forceinline__ void trace_one(const ObjDev* o, const RaysDev& st, long long j, int pmax, int aux)
+// the largest |F|^2 of the warp's rays, per object (oi), into st.fmax
+__device__ __forceinline__ void record_fmax(const RaysDev& st, int oi, float f2max)
 {
-    StateSink<kNear> sink{o, st, j, aux != 0, 0u};
+    if (!st.fmax) return;
+    const unsigned int act = __activemask();
+    const unsigned int peers = __match_any_sync(act, oi);
+    // non-negative floats order as their bit patterns
+    const unsigned int v = __reduce_max_sync(peers, __float_as_uint(f2max < 3.0e38f ? f2max : 0.0f));
+    if ((threadIdx.x & 31) == __ffs(peers) - 1 && v) atomicMax(st.fmax + oi, v);
+}
+
+template <typename T, bool kNear = false, bool kSuper = false>
+__device__ __forceinline__ void trace_one(const ObjDev* o, const RaysDev& st, long long j, int pmax, int aux, int oi)
+{
+    StateSink<kNear> sink{o, st, j, aux != 0, 0u, 0.0f};
     double x, y;
     if (ray_origin(*o, j - o->ray_offset, x, y)) {
         if constexpr (kSuper) {
@@ -120,6 +141,7 @@ __device__ __forceinline__ void trace_one(const ObjDev* o, const RaysDev& st, lo
     }
     for (int p = 0; p < st.np; ++p)
         if (!(sink.emitted & (1u << p))) st.flags[(long long)p * st.R + j] = 0u;
+    record_fmax(st, oi, sink.f2max);
 }
 
 template <typename T, bool kNear = false, bool kSuper = false>
@@ -128,8 +150,8 @@ __device__ __forceinline__ void trace_kernel_body(const ObjDev* __restrict__ obj
 {
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (j >= st.R) return;
-    const ObjDev* o = objs + (nobj > 1 ? find_object(objs, nobj, j) : 0);
-    trace_one<T, kNear, kSuper>(o, st, j, pmax, aux);
+    const int oi = nobj > 1 ? find_object(objs, nobj, j) : 0;
+    trace_one<T, kNear, kSuper>(objs + oi, st, j, pmax, aux, oi);
 }
 
 // object owning work item `it` (largest i with item_first <= it)
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(BS, MINB) trace_items_kernel(const ObjDev* __r
         for (int r = threadIdx.x; r < kRaysPerItem; r += BS) {
             const long long local = first + r;
             if (local >= nr) break;
-            trace_one<T>(o, st, o->ray_offset + local, pmax, 0);
+            trace_one<T>(o, st, o->ray_offset + local, pmax, 0, s_obj);
         }
     }
 }

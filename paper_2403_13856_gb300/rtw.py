@@ -101,6 +101,7 @@ def lib():
             "rtw_mlp_grad_get": ([p, i, p, p], i),
             "rtw_mlp_adam": ([p, i, ctypes.c_float, p, p], i),
             "rtw_field_learned": ([p, p, p, p, i, p, p, p, p], i),
+            "rtw_pipe_peak": ([i, i64, i, p, p, p], i),
             "rtw_sync_status": ([p], i),
             "rtw_newton_failures": ([p, p], i),
             "rtw_status_string": ([i], ctypes.c_char_p),
@@ -409,6 +410,17 @@ def rtw_field_learned(obj: Object, mlp: MLP, params: rtw_learned_params, dirs: r
                       flags=0, stream=None):
     _check(lib().rtw_field_learned(obj.handle, mlp.handle, ctypes.byref(params), ctypes.byref(dirs), flags, _ptr(out),
                                    _ptr(mask), _ptr(roots), _stream_ptr(stream)))
+
+
+RTW_PEAK_FP64, RTW_PEAK_FP32, RTW_PEAK_FP32X2 = 0, 1, 2
+
+
+def rtw_pipe_peak(kind, iters, blocks_per_sm, sink, stream=None) -> float:
+    """Launches the pipe-throughput kernel of `kind` on `stream`; returns the launch's flops."""
+    flops = ctypes.c_double()
+    _check(lib().rtw_pipe_peak(int(kind), int(iters), int(blocks_per_sm), _ptr(sink), ctypes.byref(flops),
+                               _stream_ptr(stream)))
+    return flops.value
 
 
 def rtw_newton_failures(stream=None) -> int:

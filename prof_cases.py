@@ -1,12 +1,12 @@
 """Small, fixed launches of the library's kernels for profilers (ncu) and quick timings.
 
-    python -m paper_2403_13856_gb300.prof_cases mlp_forward [--rows N]
-    python -m paper_2403_13856_gb300.prof_cases batch [--objects N]
-    python -m paper_2403_13856_gb300.prof_cases learned [--objects N]
-    python -m paper_2403_13856_gb300.prof_cases ellipsoid [--rays N]
-    python -m paper_2403_13856_gb300.prof_cases superellipsoid [--rays N] [--shape-e E]
-    python -m paper_2403_13856_gb300.prof_cases po2d [--sphere A] [--spacing H]
-    python -m paper_2403_13856_gb300.prof_cases pattern [--rays N] [--res DEG]
+    python prof_cases.py mlp_forward [--rows N]
+    python prof_cases.py batch [--objects N]
+    python prof_cases.py learned [--objects N]
+    python prof_cases.py ellipsoid [--rays N]
+    python prof_cases.py superellipsoid [--rays N] [--shape-e E]
+    python prof_cases.py po2d [--sphere A] [--spacing H]
+    python prof_cases.py pattern [--rays N] [--res DEG]
 
 Each case builds its inputs (seeded), runs the launch sequence `--reps` times (default 3) after
 one warm-up and prints the CUDA-event time of the last repetition.  Sizes default to cases that
@@ -15,8 +15,13 @@ hold a few GB at most, with inputs larger than L2 where the kernel streams memor
 from __future__ import annotations
 
 import argparse
+import os
+import sys
 
 import numpy as np
+
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def _timed(torch, fn, reps):
@@ -50,8 +55,8 @@ def main():
     a = ap.parse_args()
     import torch
 
-    from . import build, learned, rtw
-    from . import workloads as W
+    from paper_2403_13856_gb300 import build, learned, rtw
+    from paper_2403_13856_gb300 import workloads as W
 
     build.build()
     rtw.lib()

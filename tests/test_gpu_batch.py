@@ -100,8 +100,8 @@ def test_batch_graph_replay_and_chunking_agree(rtw):
 
 
 def test_batch_mixed_precision_vs_oracle(rtw, oracle_mod):
-    """Mixed precision batch against the FP64 oracle: normwise error per object <= 1e-4 and
-    identical masks."""
+    """Mixed precision batch against the FP64 oracle: normwise error per object <= 1e-4, the
+    largest error of any direction <= 1e-3 of the object's largest component, identical masks."""
     from paper_2403_13856_gb300 import workloads as W
 
     specs, rays = W.batch_objects(8, **SMALL)
@@ -109,14 +109,15 @@ def test_batch_mixed_precision_vs_oracle(rtw, oracle_mod):
     p_max, nt, nph = 4, 32, 64
     out, mask, _ = run_batch(rtw, obj, rays, p_max, nt, nph, precision=rtw.RTW_MIXED)
     got, gm = out.cpu().numpy()[:, :, 0], mask.cpu().numpy()
-    worst = 0.0
+    worst = worst_dir = 0.0
     for i, s in enumerate(specs):
         ref, rm = oracle_field(oracle_mod, s, (1.0, 0.0), p_max, nt, nph, rays[i])
         ref = ref.sum(axis=1)
         assert np.array_equal(gm[i], rm)
         worst = max(worst, np.linalg.norm(got[i] - ref) / np.linalg.norm(ref))
-    print(f"mixed batch: worst normwise field error {worst:.2e}")
-    assert worst <= 1e-4
+        worst_dir = max(worst_dir, np.abs(got[i] - ref).max() / np.abs(ref).max())
+    print(f"mixed batch: worst normwise field error {worst:.2e}, worst direction {worst_dir:.2e} of the largest")
+    assert worst <= 1e-4 and worst_dir <= 1e-3
 
 
 def test_batch_newton_vs_oracle_exact(rtw, oracle_mod):
