@@ -444,7 +444,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s, std::vector<std::pair<long long, long long>>* slices)
 {
-    const bool tiled = !newton && st.fmax && w.tile_ws && w.perm;
+    const bool tiled = !newton && st.fmax && st.frec && w.tile_ws && w.perm;
     const int np = st.np;
     const long long ndir = d.ndir;
     const int nout = per_order ? np : 1;
@@ -700,9 +700,9 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     // one allocation carved into 256-byte aligned arrays
     const size_t n = (size_t)np * (size_t)R;
     size_t off[9], total = 0;
-    const bool sf = tp->grid == RTW_GRID_SQUARE;  // single-precision directions for the grid field
+    const bool sf = tp->grid == RTW_GRID_SQUARE;  // single-precision field records for the grid field
     const size_t sizes[9] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, aux ? n * 8 * rtw::kAuxCount : 0,
-                             sf ? n * 32 : 0, sf ? 4 * (size_t)obj->count : 0};
+                             sf ? n * 64 : 0, sf ? 4 * (size_t)obj->count : 0};
     for (int k = 0; k < 9; ++k) {
         off[k] = total;
         total = align_up(total + sizes[k], 256);
@@ -759,8 +759,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     r->st.Fz = (double2*)(b + off[4]);
     r->st.flags = (uint32_t*)(b + off[5]);
     r->st.aux = aux ? (double*)(b + off[6]) : nullptr;
-    r->st.sf = sf ? (float4*)(b + off[7]) : nullptr;
-    r->st.sl = sf ? (float4*)(b + off[7] + n * 16) : nullptr;
+    r->st.frec = sf ? (float4*)(b + off[7]) : nullptr;
     r->st.fmax = sf ? (unsigned int*)(b + off[8]) : nullptr;
     RTW_CUDA(cudaMemcpyAsync(r->d_objs, r->objs.data(), sizeof(ObjDev) * objs.size(), cudaMemcpyHostToDevice, s));
     if (sf) RTW_CUDA(cudaMemsetAsync(r->st.fmax, 0, 4 * (size_t)obj->count, s));

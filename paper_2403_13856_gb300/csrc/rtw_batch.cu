@@ -35,7 +35,7 @@ struct Chunk {
 size_t state_layout(long long R, int np, int nobj, char* base, RaysDev* st)
 {
     const size_t n = (size_t)np * (size_t)R;
-    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, n * 32, 4 * (size_t)nobj};
+    const size_t sizes[8] = {n * 16, n * 16, n * 16, n * 16, n * 16, n * 4, n * 64, 4 * (size_t)nobj};
     size_t off[8], total = 0;
     for (int k = 0; k < 8; ++k) {
         off[k] = total;
@@ -51,8 +51,7 @@ size_t state_layout(long long R, int np, int nobj, char* base, RaysDev* st)
         st->Fz = (double2*)(base + off[4]);
         st->flags = (uint32_t*)(base + off[5]);
         st->aux = nullptr;
-        st->sf = (float4*)(base + off[6]);
-        st->sl = (float4*)(base + off[6] + n * 16);
+        st->frec = (float4*)(base + off[6]);
         st->fmax = (unsigned int*)(base + off[7]);
     }
     return total;

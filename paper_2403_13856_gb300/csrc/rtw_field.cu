@@ -134,6 +134,7 @@ struct TriGeom {
     uint32_t f[3];
     float s[3][3];    // single-precision (hi) exit directions
     float l[3][3];    //   and their lo parts
+    float th[3], ph[3];  // theta and phi of the corners' directions
     float c[3];       // unit vector at the centre of the image triangle (local origin)
     int it0, it1, jp0, jcount;
 };
@@ -353,6 +354,25 @@ __device__ __forceinline__ void cell_triangle(const FieldArgs& a, long long base
     for (int v = 0; v < 3; ++v) g.f[v] = a.st.flags[base + g.id[v]];
 }
 
+// theta, phi and the direction's hi parts of corner v from its field record
+__device__ __forceinline__ void load_corner_hi(const FieldArgs& a, long long i, TriGeom& g, int v)
+{
+    const float4 r0 = a.st.frec[4 * i], r1 = a.st.frec[4 * i + 1];
+    g.th[v] = r0.x;
+    g.ph[v] = r0.y;
+    g.s[v][0] = r1.x;
+    g.s[v][1] = r1.y;
+    g.s[v][2] = r1.z;
+    g.l[v][0] = r1.w;
+}
+
+__device__ __forceinline__ void load_corner_lo(const FieldArgs& a, long long i, TriGeom& g, int v)
+{
+    const float4 r2 = a.st.frec[4 * i + 2];
+    g.l[v][1] = r2.x;
+    g.l[v][2] = r2.y;
+}
+
 // corners of triangle t with their single-precision directions (hi and lo parts)
 __device__ __forceinline__ void load_triangle(const FieldArgs& a, long long base, long long nx, long long cx,
                                               long long cy, int t, TriGeom& g)
@@ -360,14 +380,57 @@ __device__ __forceinline__ void load_triangle(const FieldArgs& a, long long base
     cell_triangle(a, base, nx, cx, cy, t, g);
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-        const float4 hi = a.st.sf[base + g.id[v]], lo = a.st.sl[base + g.id[v]];
-        g.s[v][0] = hi.x;
-        g.s[v][1] = hi.y;
-        g.s[v][2] = hi.z;
-        g.l[v][0] = lo.x;
-        g.l[v][1] = lo.y;
-        g.l[v][2] = lo.z;
+        load_corner_hi(a, base + g.id[v], g, v);
+        load_corner_lo(a, base + g.id[v], g, v);
     }
+}
+
+// Candidate box of a triangle on a (theta, phi) grid from its corners' theta and phi.  A great
+// circle crosses every half-meridian once, so phi along an edge is monotonic and the triangle's phi
+// range is its corners' (less a pole inside); theta along an edge bulges toward the nearer pole by
+// less than L^2 |cot theta| / 8 (L the edge's chord), taken four times over.  Triangles near a pole,
+// wide in phi or long use the cap of tri_setup; so do lists (their bins widen every cap).  Returns
+// the number of candidates (0: none).
+__device__ __forceinline__ long long tri_box(TriGeom& g, const DirSet& d)
+{
+    if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) return 0;
+    if (d.list) return tri_setup(g, d);
+    float l2 = 0.0f, cmax = 0.0f, smin = 1.0f;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const int w = (v + 1) % 3;
+        const float dx = g.s[v][0] - g.s[w][0], dy = g.s[v][1] - g.s[w][1], dz = g.s[v][2] - g.s[w][2];
+        l2 = fmaxf(l2, dx * dx + dy * dy + dz * dz);
+        // sin theta and |cos theta| of a unit direction
+        smin = fminf(smin, sqrtf(g.s[v][0] * g.s[v][0] + g.s[v][1] * g.s[v][1]));
+        cmax = fmaxf(cmax, fabsf(g.s[v][2]));
+    }
+    float p0 = g.ph[0], p1 = g.ph[1], p2 = g.ph[2];
+    if (fmaxf(p0, fmaxf(p1, p2)) - fminf(p0, fminf(p1, p2)) > 3.14159265f) {  // across phi = +-pi
+        p0 += p0 < 0.0f ? 6.28318531f : 0.0f;
+        p1 += p1 < 0.0f ? 6.28318531f : 0.0f;
+        p2 += p2 < 0.0f ? 6.28318531f : 0.0f;
+    }
+    const float pmin = fminf(p0, fminf(p1, p2)), pmax = fmaxf(p0, fmaxf(p1, p2));
+    if (l2 > 0.25f || smin < 0.05f || pmax - pmin > 1.0f) return tri_setup(g, d);
+    const float mt = 0.5f * l2 * (cmax / smin + 1.0f) + 2e-6f, mp = 1e-5f;
+    const float tmin = fminf(g.th[0], fminf(g.th[1], g.th[2])), tmax = fmaxf(g.th[0], fmaxf(g.th[1], g.th[2]));
+    const int nt = d.nt, nph = d.nph;
+    const float dth = 3.14159265358979f / nt, dph = 6.28318530717959f / nph;
+    g.it0 = max((int)ceilf((tmin - mt) / dth - 0.5f), 0);
+    g.it1 = min((int)floorf((tmax + mt) / dth - 0.5f), nt - 1);
+    g.jp0 = (int)ceilf((pmin - mp + 3.14159265358979f) / dph - 0.5f);
+    const int jp1 = (int)floorf((pmax + mp + 3.14159265358979f) / dph - 0.5f);
+    g.jcount = min(max(jp1 - g.jp0 + 1, 0), nph);
+    if (g.it1 < g.it0 || g.jcount <= 0) return 0;
+    // the local origin of the single-precision tests
+    float cx = g.s[0][0] + g.s[1][0] + g.s[2][0], cy = g.s[0][1] + g.s[1][1] + g.s[2][1];
+    float cz = g.s[0][2] + g.s[1][2] + g.s[2][2];
+    const float cn = rsqrtf(cx * cx + cy * cy + cz * cz);
+    g.c[0] = cx * cn;
+    g.c[1] = cy * cn;
+    g.c[2] = cz * cn;
+    return (long long)(g.it1 - g.it0 + 1) * g.jcount;
 }
 
 struct DirTabF {
@@ -415,13 +478,8 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
         cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
         if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) continue;
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const float4 hi = a.st.sf[c.base + g.id[v]];
-            g.s[v][0] = hi.x;
-            g.s[v][1] = hi.y;
-            g.s[v][2] = hi.z;
-        }
-        const long long nc = tri_setup(g, d);
+        for (int v = 0; v < 3; ++v) load_corner_hi(a, c.base + g.id[v], g, v);
+        const long long nc = tri_box(g, d);
         if (nc == 0) continue;
         const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
         if (nc > kInlineCandidates) {
@@ -432,12 +490,7 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
             }
         }
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const float4 lo = a.st.sl[c.base + g.id[v]];
-            g.l[v][0] = lo.x;
-            g.l[v][1] = lo.y;
-            g.l[v][2] = lo.z;
-        }
+        for (int v = 0; v < 3; ++v) load_corner_lo(a, c.base + g.id[v], g, v);
         TriFrame fr;
         tri_frame(g, fr);
         for (int it = g.it0; it <= g.it1; ++it) {
@@ -487,7 +540,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
             const CellRef c = decode_cell(a, b, (long long)(code >> 1));
             TriGeom g;
             load_triangle(a, c.base, c.nx, c.cx, c.cy, (int)(code & 1ull), g);
-            if (tri_setup(g, d) != 0) {
+            if (tri_box(g, d) != 0) {
                 tri_frame(g, mine.fr);
                 mine.c[0] = g.c[0];
                 mine.c[1] = g.c[1];
@@ -1357,16 +1410,6 @@ __device__ __forceinline__ F2 df_dot(const float* nh, const float* nl, const flo
     return F2{s, t};
 }
 
-// single to double precision in the integer pipe (exact for normal numbers; subnormals give 0)
-__device__ __forceinline__ double f32_to_f64_int(float v)
-{
-    const unsigned int u = __float_as_uint(v);
-    const unsigned int e = (u >> 23) & 0xffu;
-    if (e == 0u) return 0.0;
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)b);
-}
 
 // v 2^k rounded to an integer (|v| 2^k < 2^62), in the integer pipe
 __device__ __forceinline__ unsigned long long to_fixed(float v, int k)
@@ -1504,32 +1547,32 @@ __device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b,
     const df S = df(e[0].h, e[0].l) + df(e[1].h, e[1].l) + df(e[2].h, e[2].l);
     const df w1 = df(e[2].h, e[2].l) / S, w2 = df(e[0].h, e[0].l) / S;
     const float l1 = w1.hi, l2 = w2.hi, l0 = 1.0f - l1 - l2;
-    // corner F narrowed in the integer pipe, Psi in double precision
+    // corner F and Psi from the field records
     float Fi[6];
-    double ps[3];
+    df P[3];
     {
         float F[3][6];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const long long i = c.base + g.id[v];
-            const double2 fx = a.st.Fx[i], fy = a.st.Fy[i], fz = a.st.Fz[i];
-            F[v][0] = f64_to_f32_int(fx.x);
-            F[v][1] = f64_to_f32_int(fx.y);
-            F[v][2] = f64_to_f32_int(fy.x);
-            F[v][3] = f64_to_f32_int(fy.y);
-            F[v][4] = f64_to_f32_int(fz.x);
-            F[v][5] = f64_to_f32_int(fz.y);
-            ps[v] = a.st.s2psi[i].y;
+            const float4 r0 = a.st.frec[4 * i], r2 = a.st.frec[4 * i + 2], r3 = a.st.frec[4 * i + 3];
+            F[v][0] = r2.z;
+            F[v][1] = r2.w;
+            F[v][2] = r3.x;
+            F[v][3] = r3.y;
+            F[v][4] = r3.z;
+            F[v][5] = r3.w;
+            P[v] = df(r0.z, r0.w);
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) Fi[k] = l0 * F[0][k] + l1 * F[1][k] + l2 * F[2][k];
     }
-    constexpr double kInv2Pi = 0.15915494309189533577, k2PiHi = 6.28318530717958623200;
-    const double L1 = f32_to_f64_int(w1.hi) + f32_to_f64_int(w1.lo);
-    const double L2 = f32_to_f64_int(w2.hi) + f32_to_f64_int(w2.lo);
-    const double psi = fma(L1, ps[1] - ps[0], fma(L2, ps[2] - ps[0], ps[0]));
+    // Psi_0 + l1 (Psi_1 - Psi_0) + l2 (Psi_2 - Psi_0), reduced modulo 2 pi, in double-float
+    const df psi = P[0] + w1 * (P[1] - P[0]) + w2 * (P[2] - P[0]);
+    const float nturn = rintf(psi.hi * 0.159154943f);
+    const df red = psi - df_mul_f(df(6.28318548f, -1.74845553e-7f), nturn);
     float sp, cp;
-    sincosf(f64_to_f32_int(fma(-k2PiHi, rint(psi * kInv2Pi), psi)), &sp, &cp);
+    sincosf(red.hi + red.lo, &sp, &cp);
     float rr = 0.0f, ri = 0.0f, tr = 0.0f, ti = 0.0f, pr = 0.0f, pi = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

@@ -81,8 +81,11 @@ struct RaysDev {
     double2* Fy;
     double2* Fz;
     uint32_t* flags;
-    float4* sf;       // s split as hi + lo, two floats per component (x, y, z, 0 each), for the
-    float4* sl;       //   field's single-precision candidate tests; null when not kept
+    // single-precision field record of every (ray, order) for the square-grid field, four float4 at
+    // frec[4 i .. 4 i + 3]: (theta, phi, Psi_hi, Psi_lo), (s_x, s_y, s_z hi, s_x lo), (s_y, s_z lo,
+    // F_x), (F_y, F_z) -- direction and phase as hi + lo pairs (about 48 bits), F to single
+    // precision, theta and phi of s to single precision; null when not kept
+    float4* frec;
     double* aux;      // kAuxCount x (np R) or null
     unsigned int* fmax;  // per object: bits of the largest |F|^2 (float) of a valid record that is not
                          //   near-caustic (the scale of the field's fixed-point sums); null when not kept
@@ -104,6 +107,17 @@ __device__ __forceinline__ float f64_to_f32_int(double v)
     const unsigned int m = ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned int r = (lo >> 28) & 1u;
     return __uint_as_float(sign | (((unsigned int)e << 23) + m + r));  // a carry rounds into the exponent
+}
+
+// Single to double precision in the integer pipe (exact for normal numbers; subnormals give 0).
+__device__ __forceinline__ double f32_to_f64_int(float v)
+{
+    const unsigned int u = __float_as_uint(v);
+    const unsigned int e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
 }
 
 // error bits of the device status word

@@ -34,19 +34,31 @@ struct StateSink {
         st.Fy[i] = make_double2(fr.F[2], fr.F[3]);
         st.Fz[i] = make_double2(fr.F[4], fr.F[5]);
         st.flags[i] = fr.flags;
-        if (st.fmax && !(fr.flags & kFlagCaustic)) {
-            float f2 = 0.0f;
+        if (st.frec) {
+            // the field record, narrowed in the integer pipe (one double subtraction per low part)
+            float Ff[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                const float v = f64_to_f32_int(fr.F[c]);
-                f2 = fmaf(v, v, f2);
+            for (int c = 0; c < 6; ++c) Ff[c] = f64_to_f32_int(fr.F[c]);
+            float sh[3], sl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sh[c] = f64_to_f32_int(fr.s[c]);
+                sl[c] = f64_to_f32_int(fr.s[c] - f32_to_f64_int(sh[c]));
             }
-            f2max = fmaxf(f2max, f2);
-        }
-        if (st.sf) {
-            const float hx = (float)fr.s[0], hy = (float)fr.s[1], hz = (float)fr.s[2];
-            st.sf[i] = make_float4(hx, hy, hz, 0.0f);
-            st.sl[i] = make_float4((float)(fr.s[0] - hx), (float)(fr.s[1] - hy), (float)(fr.s[2] - hz), 0.0f);
+            const float ph = f64_to_f32_int(fr.psi);
+            const float pl = f64_to_f32_int(fr.psi - f32_to_f64_int(ph));
+            const float th = atan2f(sqrtf(sh[0] * sh[0] + sh[1] * sh[1]), sh[2]), az = atan2f(sh[1], sh[0]);
+            float4* r = st.frec + 4 * i;
+            r[0] = make_float4(th, az, ph, pl);
+            r[1] = make_float4(sh[0], sh[1], sh[2], sl[0]);
+            r[2] = make_float4(sl[1], sl[2], Ff[0], Ff[1]);
+            r[3] = make_float4(Ff[2], Ff[3], Ff[4], Ff[5]);
+            if (st.fmax && !(fr.flags & kFlagCaustic)) {
+                float f2 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) f2 = fmaf(Ff[c], Ff[c], f2);
+                f2max = fmaxf(f2max, f2);
+            }
         }
         emitted |= 1u << p;
         if (aux) {
