@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="ellipsoid line: leave out the batched (4096 drops) and learned (1024 drops) entries")
     ap.add_argument("--cpu-sample-rows", type=int, default=0)
     ap.add_argument("--workload", default="ellipsoid", choices=["ellipsoid", "batch", "learned"],
                     help="ellipsoid: the single tilted drop (default); batch: 4096 seed-drawn drops; "
@@ -335,6 +337,52 @@ def main():
     return bench_ellipsoid(args, rank, world, local, dist)
 
 
+def timed_on(torch, stream, fn, steps, warmup):
+    """mean seconds of fn over steps calls after warmup calls, CUDA events on stream"""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / steps
+
+
+def system_batch(torch, rtw, precision, steps=2, warmup=1):
+    """The 4096-drop batched form (one graph-replayed call per step, autotuned launch options):
+    rays*interfaces/s, seconds per step and the trace / field split."""
+    from paper_2403_13856_gb300 import autotune
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.BATCH
+    p_max, nt, nph = cfg["p_max"], cfg["n_theta"], cfg["n_phi"]
+    specs, rays = W.batch_objects()
+    n = len(specs)
+    stream = torch.cuda.current_stream()
+    opts = autotune.tune(specs, rays, p_max, precision, nt, nph)
+    obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
+    dirs = rtw.dirs_grid(nt, nph)
+    out = torch.empty((n, nt * nph, 1, 2), dtype=torch.complex128, device="cuda")
+    mask = torch.empty((n, nt * nph), dtype=torch.uint8, device="cuda")
+    units = sum(batch_hits(rtw, torch, specs, rays, stream)) * (p_max + 1)
+    bp = rtw.batch_params(rays, p_max=p_max, precision=precision, use_graph=1, **opts)
+    batch = rtw.rtw_far_field_batch(obj, bp, dirs, out, mask, stream=stream)
+    t = timed_on(torch, stream, lambda: rtw.rtw_far_field_batch(obj, bp, dirs, out, mask, batch=batch, stream=stream),
+                 steps, warmup)
+    rtw.rtw_sync_status(stream)
+    bpt = rtw.batch_params(rays, p_max=p_max, precision=precision, timing=1, **opts)
+    tb = rtw.rtw_far_field_batch(obj, bpt, dirs, out, mask, stream=stream)
+    t_trace, t_field = tb.times()
+    total_rays, nchunks, _ = batch.info()
+    del tb, batch, out, mask
+    return {"value": units / t, "unit": UNIT, "s_per_step": t, "ms_trace": t_trace, "ms_field": t_field,
+            "directions_per_s": n * nt * nph / t, "objects": n, "rays_grid": total_rays, "chunks": nchunks,
+            "launch_options": opts, "steps": steps, "warmup": warmup}
+
+
 def bench_ellipsoid(args, rank, world, local, dist):
     import torch
 
@@ -570,6 +618,14 @@ def bench_ellipsoid(args, rank, world, local, dist):
             "paper_context": "9.4 min for this pattern on an Intel i9-13900KS (CPU, ray count not stated)"}
     del r3, out3, mask3, sph3
 
+    # the system forms on their own workloads: 4096 drops batched (FP64 and mixed), and the learned
+    # proposal on 1024 drops against dense tracing
+    systems = {}
+    if not args.no_systems:
+        systems["batch_4096_drops"] = {"fp64": system_batch(torch, rtw, rtw.RTW_FP64),
+                                       "mixed": system_batch(torch, rtw, rtw.RTW_MIXED)}
+        systems["learned_1024_drops"] = system_learned(torch, rtw, args, local)
+
     # end to end through the public API: host descriptor in, field copied to pinned host memory
     host_out = torch.empty((ndir, 1, 2), dtype=torch.complex128, pin_memory=True)
     host_mask = torch.empty(ndir, dtype=torch.uint8, pin_memory=True)
@@ -649,6 +705,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "paper_fig3_pattern": fig3,
         "sphere_fan": sphere_fan,
     }
+    line.update(systems)
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -836,36 +893,41 @@ def field_errors(torch, got, ref, gmask, rmask):
             "normwise": float((d.abs() ** 2).sum().sqrt() / (r[sel].abs() ** 2).sum().sqrt())}
 
 
-def bench_learned(args, rank, world, local, dist):
-    """Learned proposals + Newton on the exact trace against dense tracing on 1024 drops."""
-    import torch
-
-    from paper_2403_13856_gb300 import autotune
+def learned_networks(torch, rtw, retrain=False):
+    """The per-order networks of the learned proposal: trained once on traced rays of the training
+    drops (stream 2) and kept as a checkpoint; (handle, training seconds or None when loaded)."""
     from paper_2403_13856_gb300 import learned as Lr
-    from paper_2403_13856_gb300 import rtw
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.LEARNED
+    np_ = cfg["p_max"] + 1
+    ck = os.path.join(ROOT, "paper_2403_13856_gb300", "_cache", "learned_p%d" % cfg["p_max"])
+    if os.path.exists(ck + ".json") and not retrain:
+        return Lr.load(ck), None
+    t0 = time.perf_counter()
+    tspecs, _ = W.batch_objects(cfg["train_objects"], stream=W.STREAM_TRAIN)
+    tobj = rtw.Object([rtw.ObjectSpec(**s) for s in tspecs])
+    samples = [Lr.Samples(tobj, cfg["train_rays"], cfg["p_max"])]
+    mlp = rtw.MLP(np_, Lr.init_params(np_))
+    losses = Lr.train(mlp, samples, range(np_), steps=cfg["train_steps"], batch=cfg["batch"], lr=3e-3, lr_end=3e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    Lr.save(mlp, ck, {"losses": losses, "train_s": t_train})
+    return mlp, t_train
+
+
+def system_learned(torch, rtw, args, local, steps=1, warmup=1):
+    """Learned proposals + Newton on the exact trace against dense tracing on 1024 drops: seconds
+    per field of each form, and the errors of the learned and dense fields against the exact
+    branch sum (dense FP64 trace with every hit refined by Newton)."""
+    from paper_2403_13856_gb300 import autotune
     from paper_2403_13856_gb300 import workloads as W
 
     cfg = W.LEARNED
     p_max, nt, nph = cfg["p_max"], cfg["n_theta"], cfg["n_phi"]
     np_ = p_max + 1
     stream = torch.cuda.current_stream()
-    # networks: trained once on traced rays, kept as a checkpoint
-    ck = os.path.join(ROOT, "paper_2403_13856_gb300", "_cache", "learned_p%d" % p_max)
-    t_train = None
-    if os.path.exists(ck + ".json") and not args.retrain:
-        mlp = Lr.load(ck)
-    else:
-        t0 = time.perf_counter()
-        tspecs, _ = W.batch_objects(cfg["train_objects"], stream=W.STREAM_TRAIN)
-        tobj = rtw.Object([rtw.ObjectSpec(**s) for s in tspecs])
-        samples = [Lr.Samples(tobj, cfg["train_rays"], p_max)]
-        mlp = rtw.MLP(np_, Lr.init_params(np_))
-        losses = Lr.train(mlp, samples, range(np_), steps=cfg["train_steps"], batch=cfg["batch"], lr=3e-3,
-                          lr_end=3e-5)
-        torch.cuda.synchronize()
-        t_train = time.perf_counter() - t0
-        Lr.save(mlp, ck, {"losses": losses, "train_s": t_train})
-        del samples, tobj
+    mlp, t_train = learned_networks(torch, rtw, getattr(args, "retrain", False))
     specs, rays = W.batch_objects(cfg["n_objects"], stream=W.STREAM_EVAL)
     n = len(specs)
     obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
@@ -876,62 +938,90 @@ def bench_learned(args, rank, world, local, dist):
     mask_l = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
     roots = torch.empty((n, ndir, np_), dtype=torch.uint8, device="cuda")
     lp = rtw.learned_params(p_max)
-
-    def timed(fn, steps, warmup):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / steps
-
     with ClockSampler(local) as clk:
-        t_learned = timed(lambda: rtw.rtw_field_learned(obj, mlp, lp, dirs, out_l, mask_l, roots, stream=stream),
-                          args.steps, args.warmup)
+        t_learned = timed_on(torch, stream, lambda: rtw.rtw_field_learned(obj, mlp, lp, dirs, out_l, mask_l, roots,
+                                                                           stream=stream), steps, warmup)
     rtw.rtw_sync_status(stream)
+    # the same with a single-precision first approach to each root, and with the dense fallback for
+    # the rows where a confident head did not converge (per-order output, summed afterwards)
+    out_m = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    mask_m = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
+    lpm = rtw.learned_params(p_max, precision=rtw.RTW_MIXED)
+    t_mixed = timed_on(torch, stream, lambda: rtw.rtw_field_learned(obj, mlp, lpm, dirs, out_m, mask_m, stream=stream),
+                       1, 0)
+    out_fp = torch.empty((n, ndir, np_, 2), dtype=torch.complex128, device="cuda")
+    mask_f = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
+    roots_f = torch.empty((n, ndir, np_), dtype=torch.uint8, device="cuda")
+    lpf = rtw.learned_params(p_max, fallback_rays=rays)
+    t_fb = timed_on(torch, stream, lambda: rtw.rtw_field_learned(obj, mlp, lpf, dirs, out_fp, mask_f, roots_f,
+                                                                  flags=rtw.RTW_FIELD_PER_ORDER, stream=stream), 1, 0)
+    rtw.rtw_sync_status(stream)
+    out_f = out_fp.sum(dim=2, keepdim=True)
+    del out_fp
     # dense tracing on the same drops (autotuned batched launch, graph replay)
     opts = autotune.tune(specs, rays, p_max, rtw.RTW_FP64, nt, nph)
-    out_d = torch.empty(shape, dtype=torch.complex128, device="cuda")
-    mask_d = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
     res = {}
     for name, prec, mode in (("dense_fp64", rtw.RTW_FP64, rtw.RTW_DENSE), ("dense_mixed", rtw.RTW_MIXED, rtw.RTW_DENSE),
                              ("exact", rtw.RTW_FP64, rtw.RTW_NEWTON)):
-        o_ = out_d if name != "exact" else torch.empty(shape, dtype=torch.complex128, device="cuda")
-        m_ = mask_d if name != "exact" else torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
+        o_ = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        m_ = torch.empty((n, ndir), dtype=torch.uint8, device="cuda")
         bp = rtw.batch_params(rays, p_max=p_max, precision=prec, use_graph=1, mode=mode, **opts)
         b = rtw.Batch()
-        t = timed(lambda: rtw.rtw_far_field_batch(obj, bp, dirs, o_, m_, batch=b, stream=stream), 1, 1)
+        t = timed_on(torch, stream, lambda: rtw.rtw_far_field_batch(obj, bp, dirs, o_, m_, batch=b, stream=stream),
+                     1, 1)
         rtw.rtw_sync_status(stream)
         res[name] = (t, o_, m_)
     ref, rmask = res["exact"][1], res["exact"][2]
     e_learned = field_errors(torch, out_l, ref, mask_l, rmask)
     e_dense = field_errors(torch, res["dense_fp64"][1], ref, res["dense_fp64"][2], rmask)
+    e_mixed = field_errors(torch, res["dense_mixed"][1], ref, res["dense_mixed"][2], rmask)
+    e_lmixed = field_errors(torch, out_m, ref, mask_m, rmask)
+    e_fb = field_errors(torch, out_f, ref, mask_f, rmask)
+    unc_rows = int(((roots_f & 0x80) != 0).any(dim=-1).sum().item())
     t_dense = res["dense_fp64"][0]
-    rows = n * ndir
-    found = roots.to(torch.int64).sum(dim=(0, 1)).tolist()
+    found = (roots & 0x7F).to(torch.int64).sum(dim=(0, 1)).tolist()
+    uncertain = ((roots & 0x80) != 0).to(torch.int64).sum(dim=(0, 1)).tolist()
+    return {"workload": "1024 drops of the batched recipe (stream 3), 256x512 (theta,phi) directions, p=0..4; "
+                        "networks trained on 2e7 traced rays of 16384 drops (stream 2)",
+            "learned": {"s_per_field": t_learned, "directions_per_s": n * ndir / t_learned,
+                        "roots_per_order": found, "uncertain_rows_per_order": uncertain,
+                        "params": {"p_min": lp.p_min or 0.05, "max_steps": lp.max_steps or 3,
+                                   "max_halvings": lp.max_halvings or 3, "tol": "min(1e-6, 1e-4/(k0 L))"},
+                        "errors_vs_exact": e_learned},
+            "learned_mixed_first_approach": {"s_per_field": t_mixed, "errors_vs_exact": e_lmixed,
+                                             "speedup_vs_dense_fp64": t_dense / t_mixed},
+            "learned_with_dense_fallback": {"s_per_field": t_fb, "errors_vs_exact": e_fb,
+                                            "rows_redone": unc_rows, "rows": n * ndir,
+                                            "speedup_vs_dense_fp64": t_dense / t_fb},
+            "dense_fp64": {"s_per_field": t_dense, "errors_vs_exact": e_dense},
+            "dense_mixed": {"s_per_field": res["dense_mixed"][0], "errors_vs_exact": e_mixed},
+            "exact_reference": {"s_per_field": res["exact"][0],
+                                "what": "dense FP64 trace with every hit refined by Newton on the exact trace"},
+            "speedup_learned_vs_dense_fp64": t_dense / t_learned,
+            "train_s": t_train, "clocks": clk.summary()}
+
+
+def bench_learned(args, rank, world, local, dist):
+    """Learned proposals + Newton on the exact trace against dense tracing on 1024 drops."""
+    import torch
+
+    from paper_2403_13856_gb300 import rtw
+    from paper_2403_13856_gb300 import workloads as W
+
+    cfg = W.LEARNED
+    r = system_learned(torch, rtw, args, local, steps=args.steps, warmup=args.warmup)
+    n = cfg["n_objects"]
+    t_learned = r["learned"]["s_per_field"]
     line = {
-        "metric": METRIC, "value": rows / t_learned, "unit": "directions/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_learned, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
-        "config": {"workload": "1024 drops of the batched recipe (stream 3), 256x512 (theta,phi) directions, "
-                               "p=0..4; networks trained on 2e7 traced rays of 16384 drops (stream 2)",
-                   "learned_params": {"p_min": 0.05, "max_steps": 5, "tol": "min(1e-6, 1e-4/(k0 L))"},
-                   "l2": "inputs larger than L2"},
-        "learned": {"s_per_field": t_learned, "roots_per_order": found, "errors_vs_exact": e_learned},
-        "dense_fp64": {"s_per_field": t_dense, "errors_vs_exact": e_dense},
-        "dense_mixed": {"s_per_field": res["dense_mixed"][0]},
-        "exact_reference": {"s_per_field": res["exact"][0],
-                            "what": "dense FP64 trace with every hit refined by Newton on the exact trace"},
-        "speedup_learned_vs_dense_fp64": t_dense / t_learned,
-        "train_s": t_train,
-        "clocks": clk.summary(),
+        "metric": METRIC, "value": n * cfg["n_theta"] * cfg["n_phi"] / t_learned, "unit": "directions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_learned,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
+        "config": {"workload": r["workload"], "learned_params": r["learned"]["params"], "l2": "inputs larger than L2"},
     }
+    line.update({k: v for k, v in r.items() if k != "workload"})
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline_learned(specs[0], p_max, nt, nph)
+        specs, _ = W.batch_objects(n, stream=W.STREAM_EVAL)
+        line["cpu_baseline"] = cpu_baseline_learned(specs[0], cfg["p_max"], cfg["n_theta"], cfg["n_phi"])
     print(json.dumps(line), flush=True)
 
 

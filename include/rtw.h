@@ -374,11 +374,18 @@ int rtw_mlp_grad_get(const rtw_mlp* m, int order, float* grad, void* stream);
 int rtw_mlp_adam(rtw_mlp* m, int order, float lr, const float* grad, void* stream);
 
 /* Options of rtw_field_learned: orders 0..p_max (networks 0..p_max of the rtw_mlp handle);
- * heads whose softmax weight is below p_min (0: 0.05) are not tried; at most max_steps Newton
- * steps per head (0: 5); convergence at |s - target| < tol (0: per object
+ * heads whose softmax weight is below p_min (0: 0.05) are not tried; at most max_steps
+ * double-precision Newton steps per head (0: 3); convergence at |s - target| < tol (0: per object
  * min(1e-6, 1e-4 / (k0 max(a, b, c))), which keeps the phase error of a converged ray below
  * 1e-4 rad); rows (object, direction) per launch sequence chunk_rows (0: 2^24); a step is halved
- * at most max_halvings times (0: 3, range 1..30) before its head is given up. */
+ * at most max_halvings times (0: 3, range 1..30) before its head is given up.  precision
+ * RTW_MIXED first approaches each root on the single-precision trace (at most 6 steps, to
+ * |s - target| < 3e-6) and then takes the double-precision steps; RTW_FP64 (0) takes only the
+ * latter.  fallback_rays (host, one per object, or NULL): the dense fallback -- every row where a
+ * confident head's steps did not converge (root-count bit 7) is redone by the dense path with a
+ * square ray grid of fallback_rays[i] rays and its per-order values replace the learned ones of the
+ * uncertain orders (needs RTW_FIELD_PER_ORDER; one read-back and a trace per object with such
+ * rows). */
 typedef struct {
     int p_max;
     float p_min;
@@ -386,6 +393,8 @@ typedef struct {
     double tol;
     int64_t chunk_rows;
     int max_halvings;
+    int precision;
+    const int64_t* fallback_rays;
 } rtw_learned_params;
 
 /* The far field of every object of obj on the (theta, phi) grid of dirs from learned proposals:
@@ -396,8 +405,9 @@ typedef struct {
  * an earlier root of the same direction and order is the same ray and is dropped; every other
  * root adds its exact F e^{i Psi}, except a near-caustic root, which marks the direction
  * (RTW_MASK_CAUSTIC) instead.  A branch that no head finds is missing from the sum: roots_out
- * (device, optional, [objects][directions][orders] uint8) reports the roots found, so that a
- * caller can fall back to the dense path where it finds none.  field_out and mask_out as
+ * (device, optional, [objects][directions][orders] uint8) reports the roots found (bits 0..6) and
+ * marks with bit 7 the rows where a head the network is confident about did not converge, the rows
+ * the dense fallback (lp->fallback_rays) redoes.  field_out and mask_out as
  * rtw_field (flags: 0 or RTW_FIELD_PER_ORDER).  Working memory is allocated stream-ordered and
  * freed before the call's work completes.  Asynchronous. */
 int rtw_field_learned(const rtw_object* obj, const rtw_mlp* m, const rtw_learned_params* lp, const rtw_dirs* dirs,

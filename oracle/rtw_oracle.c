@@ -1754,7 +1754,7 @@ static int64_t field_learned(const or_object* o, const double* theta, int pmax, 
                 se += w[k];
             }
             double found[OM_HEADS][2];
-            int nfound = 0;
+            int nfound = 0, uncertain = 0;
             for (int k = 0; k < OM_HEADS; ++k) {
                 if (w[k] / se < p_min) continue;
                 double xy[2];
@@ -1766,7 +1766,10 @@ static int64_t field_learned(const or_object* o, const double* theta, int pmax, 
                     uv[1] *= 0.999 / ru;
                 }
                 om_uv_to_xy(o, uv, &xy[0], &xy[1]);
-                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, max_halvings, rec) < 0) continue;
+                if (or_newton_ex(o, p, s, xy, 0.0, max_steps + 1, tol, max_halvings, rec) < 0) {
+                    uncertain = 1; /* a confident head that did not converge */
+                    continue;
+                }
                 int dup = 0;
                 for (int q = 0; q < nfound; ++q)
                     if (hypot(xy[0] - found[q][0], xy[1] - found[q][1]) <= dedup) dup = 1;
@@ -1780,7 +1783,7 @@ static int64_t field_learned(const or_object* o, const double* theta, int pmax, 
                 }
                 or_project_add(rec + OR_F, rec[OR_PSI], eth, eph, 1.0, out + ((size_t)dk * np + p) * 4);
             }
-            if (roots) roots[(size_t)dk * np + p] = (uint8_t)nfound;
+            if (roots) roots[(size_t)dk * np + p] = (uint8_t)(nfound | (uncertain ? 0x80 : 0));
             total += nfound;
         }
         free(rec);

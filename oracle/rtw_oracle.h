@@ -183,7 +183,8 @@ void or_project_add(const double F[6], double psi, const double eth[3], const do
  * the same direction and order is the same ray and is dropped; every other root adds
  * F e^{i Psi}, except a near-caustic one, which marks the direction instead.
  * out: ndir x (pmax+1) x 4; mask: ndir (axial as or_field_grid); roots (may be NULL):
- * ndir x (pmax+1) counts.  Returns the number of roots. */
+ * ndir x (pmax+1) counts, bit 7 set where a head at or above p_min did not converge.  Returns the
+ * number of roots. */
 int64_t or_field_learned(const or_object* o, const double* theta, int pmax, int ntheta, int nphi, double p_min,
                          int max_steps, double tol, int max_halvings, double* out, uint8_t* mask, uint8_t* roots);
 /* The same on a list of directions: dirs is ndir x (theta, phi); out: ndir x (pmax+1) x 4, mask: ndir,

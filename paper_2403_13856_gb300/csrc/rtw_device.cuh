@@ -76,13 +76,15 @@ struct CaptureSink {
     }
 };
 
-// Residual |t - s_p(x, y)| of the exact double-precision trace; the exit wave of order p in cs.
+// Residual |t - s_p(x, y)| of the trace in precision T (double: the exact trace; float: the
+// mixed-precision trace); the exit wave of order p in cs.
+template <typename T = double>
 __device__ __forceinline__ bool newton_eval(const ObjDev& o, int p, const double t[3], double x, double y,
                                             CaptureSink& cs, FarRecord& r, double& res)
 {
     cs.want = p;
     cs.got = false;
-    trace_ray<double, true>(o, x, y, p, cs);
+    trace_ray<T, true>(o, x, y, p, cs);
     if (!cs.got || !far_record(o, cs.w, r)) return false;
     const double d0 = t[0] - r.s[0], d1 = t[1] - r.s[1], d2 = t[2] - r.s[2];
     res = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
@@ -97,6 +99,8 @@ __device__ __forceinline__ bool newton_eval(const ObjDev& o, int p, const double
 // evaluations (so at most max_checks - 1 steps) and the root lies within rmax of the seed
 // (rmax <= 0: anywhere), so that the ray found is the branch the seed stands for; the root
 // impact point goes to root (when given).
+// T: precision of the traces (float for a cheap first approach to the root).
+template <typename T = double>
 __device__ __forceinline__ bool newton_point(const ObjDev& o, int p, const double t[3], double x, double y,
                                              double rmax, FarRecord& out, int max_checks = 30, double tol = 1e-11,
                                              double* root = nullptr, int max_halvings = 12)
@@ -105,7 +109,7 @@ __device__ __forceinline__ bool newton_point(const ObjDev& o, int p, const doubl
     CaptureSink cs;
     FarRecord r;
     double res;
-    if (!newton_eval(o, p, t, x, y, cs, r, res)) return false;
+    if (!newton_eval<T>(o, p, t, x, y, cs, r, res)) return false;
     for (int it = 0; it < max_checks; ++it) {
         if (res < tol) {
             if (rmax > 0.0 && hypot(x - x0, y - y0) > rmax) return false;
@@ -134,7 +138,7 @@ __device__ __forceinline__ bool newton_point(const ObjDev& o, int p, const doubl
             CaptureSink cc;
             FarRecord rc;
             double resc;
-            if (newton_eval(o, p, t, x + lam * dx, y + lam * dy, cc, rc, resc) && resc < res) {
+            if (newton_eval<T>(o, p, t, x + lam * dx, y + lam * dy, cc, rc, resc) && resc < res) {
                 x += lam * dx;
                 y += lam * dy;
                 cs = cc;

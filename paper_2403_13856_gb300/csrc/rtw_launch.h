@@ -142,8 +142,8 @@ cudaError_t launch_mlp_samples(const ObjDev* objs, const ObjFeat* feat, int nobj
 // network's forward pass and the Newton kernel
 cudaError_t launch_learned(const ObjDev* objs, const ObjFeat* feat, const double* tab, int nt, int nph, long long nrows,
                            const MlpWeights* nets, int np, __nv_bfloat16* X, float* Y, float p_min, int max_steps,
-                           double tol, int max_halvings, int nout, double* out, unsigned int* mask, uint8_t* roots,
-                           unsigned int* status, cudaStream_t s);
+                           double tol, int max_halvings, int mixed, int nout, double* out, unsigned int* mask,
+                           uint8_t* roots, unsigned int* status, cudaStream_t s);
 
 cudaError_t launch_grid_cells(const ObjDev* objs, int n, int np, bool windowed, const int64_t* win, GridCells* cells,
                               cudaStream_t s);

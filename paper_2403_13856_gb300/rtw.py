@@ -396,13 +396,21 @@ def rtw_mlp_adam(mlp: MLP, order, lr, grad=None, stream=None):
 
 class rtw_learned_params(ctypes.Structure):
     _fields_ = [("p_max", ctypes.c_int), ("p_min", ctypes.c_float), ("max_steps", ctypes.c_int),
-                ("tol", ctypes.c_double), ("chunk_rows", ctypes.c_int64), ("max_halvings", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("chunk_rows", ctypes.c_int64), ("max_halvings", ctypes.c_int),
+                ("precision", ctypes.c_int), ("fallback_rays", ctypes.c_void_p)]
 
 
-def learned_params(p_max, p_min=0.0, max_steps=0, tol=0.0, chunk_rows=0, max_halvings=0):
+def learned_params(p_max, p_min=0.0, max_steps=0, tol=0.0, chunk_rows=0, max_halvings=0, precision=0,
+                   fallback_rays=None):
+    """fallback_rays: per-object ray counts of the dense fallback (kept alive in the returned
+    structure), or None."""
     lp = rtw_learned_params()
     lp.p_max, lp.p_min, lp.max_steps, lp.tol, lp.chunk_rows = p_max, p_min, max_steps, tol, int(chunk_rows)
     lp.max_halvings = int(max_halvings)
+    lp.precision = int(precision)
+    if fallback_rays is not None:
+        lp._fallback = (ctypes.c_int64 * len(fallback_rays))(*[int(n) for n in fallback_rays])
+        lp.fallback_rays = ctypes.cast(lp._fallback, ctypes.c_void_p)
     return lp
 
 

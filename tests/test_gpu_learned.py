@@ -35,11 +35,11 @@ def const_theta(n_orders, seeds, logits):
     return th
 
 
-def learned_field(rtw, obj, mlp, p_max, nt, nph, n_obj=1):
+def learned_field(rtw, obj, mlp, p_max, nt, nph, n_obj=1, **params):
     out = torch.zeros((n_obj, nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
     mask = torch.zeros((n_obj, nt * nph), dtype=torch.uint8, device="cuda")
     roots = torch.zeros((n_obj, nt * nph, p_max + 1), dtype=torch.uint8, device="cuda")
-    lp = rtw.learned_params(p_max, max_halvings=3)
+    lp = rtw.learned_params(p_max, **({"max_steps": 5, "max_halvings": 3} | params))
     rtw.rtw_field_learned(obj, mlp, lp, rtw.dirs_grid(nt, nph), out, mask, roots, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_sync_status()
     return out.cpu().numpy(), mask.cpu().numpy(), roots.cpu().numpy()
@@ -61,7 +61,7 @@ def test_learned_pipeline_matches_oracle(rtw, oracle_mod, k):
     got, gm, gr = learned_field(rtw, obj, mlp, p_max, nt, nph)
     o = oracle_mod.Object(spec["a"], spec["b"], spec["c"], quat=spec["quat"], m=spec["m"],
                           wavelength=spec["wavelength"])
-    ref, rm, rr = o.field_learned(th.astype(np.float64), p_max, nt, nph, max_halvings=3)  # 5 steps, object tolerance
+    ref, rm, rr = o.field_learned(th.astype(np.float64), p_max, nt, nph, max_steps=5, max_halvings=3)
     ref = oracle_mod.complex_field(ref)
     print(f"object {k}: roots per order GPU {gr[0].sum(axis=0)}, oracle {rr.sum(axis=0)}")
     assert np.array_equal(gr[0], rr)
@@ -106,3 +106,62 @@ def test_trained_network_gains_over_fixed_seeds(rtw, oracle_mod):
           f"fixed seeds {e_b:.2e}; roots trained {gr[0].sum(axis=0)}, fixed {br[0].sum(axis=0)}; "
           f"directions within 1e-3 per order {np.round(ok, 3)}")
     assert e_t < 0.5 * e_b
+
+
+def test_single_precision_first_approach(rtw):
+    """RTW_MIXED approaches each root on the single-precision trace before at most 3 double-precision
+    steps.  Against the double-precision form given 10 steps and 8 halvings (both to |s - t| <
+    1e-11): where both find the same number of roots per (direction, order) the fields agree within
+    1e-8 of the largest, and that holds on most directions."""
+    spec = SPECS[1]
+    p_max, nt, nph = 2, 24, 48
+    seeds = [[0.0, 0.0], [0.5, 0.25], [-0.375, 0.5], [0.125, -0.625]]
+    th = const_theta(p_max + 1, seeds, [0.0, 0.5, -0.25, -4.0])
+    mlp = rtw.MLP(p_max + 1, th)
+    obj = rtw.Object([rtw.ObjectSpec(**spec)])
+    f64, m64, r64 = learned_field(rtw, obj, mlp, p_max, nt, nph, max_steps=10, max_halvings=8, tol=1e-11)
+    fmx, mmx, rmx = learned_field(rtw, obj, mlp, p_max, nt, nph, max_steps=3, tol=1e-11, precision=rtw.RTW_MIXED)
+    f3, m3, r3 = learned_field(rtw, obj, mlp, p_max, nt, nph, max_steps=3, tol=1e-11)
+    same = ((r64 & 0x7F) == (rmx & 0x7F)).all(axis=-1)[0] & (m64[0] == 0) & (mmx[0] == 0)
+    scale = np.abs(f64).max()
+    err = np.abs(fmx[0][same] - f64[0][same]).max() / scale
+    print(f"mixed first approach: same roots as the 10-step form on {same.mean():.3f} of the directions, "
+          f"max |dF| / max |F| {err:.2e}; roots per order: 10 FP64 steps {(r64 & 0x7F).sum(axis=(0, 1))}, "
+          f"mixed + 3 FP64 steps {(rmx & 0x7F).sum(axis=(0, 1))}, 3 FP64 steps {(r3 & 0x7F).sum(axis=(0, 1))}")
+    n64, nmx, n3 = ((r & 0x7F).sum() for r in (r64, rmx, r3))
+    assert same.mean() > 0.7 and err <= 1e-8
+    # most roots of the 10-step form, and far more than the same 3 steps without the first approach
+    assert nmx >= 0.8 * n64 and nmx >= 2 * n3
+
+
+def test_dense_fallback_replaces_uncertain_rows(rtw):
+    """One confident head (the others below the softmax threshold) seeded at the disk centre with
+    three Newton steps converges on some rows and not on others: those rows are marked (bit 7) and,
+    with fallback_rays, redone by the dense path.  Their orders equal the dense per-order field of
+    the same rays (within 1e-9 of the largest); the other rows keep the learned values."""
+    spec = SPECS[1]
+    p_max, nt, nph = 2, 24, 48
+    seeds = [[0.0, 0.0], [0.5, 0.25], [-0.375, 0.5], [0.125, -0.625]]
+    th = const_theta(p_max + 1, seeds, [0.0, -8.0, -8.0, -8.0])
+    mlp = rtw.MLP(p_max + 1, th)
+    obj = rtw.Object([rtw.ObjectSpec(**spec)])
+    nrays = 40_000
+    plain, pm, pr = learned_field(rtw, obj, mlp, p_max, nt, nph, max_steps=3)
+    fb, fm, fr = learned_field(rtw, obj, mlp, p_max, nt, nph, max_steps=3, fallback_rays=[nrays])
+    assert np.array_equal(pr, fr)
+    unc = (fr[0] & 0x80) != 0
+    assert unc.sum() > 100 and (~unc).sum() > 100
+    # the dense per-order field of the same rays on the whole grid
+    tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=nrays)
+    rays = rtw.rtw_trace(obj, tp)
+    dense = torch.zeros((nt * nph, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    dm = torch.zeros(nt * nph, dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, rtw.dirs_grid(nt, nph), dense, dm, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_sync_status()
+    dense = dense.cpu().numpy()
+    scale = np.abs(dense).max()
+    err_unc = np.abs(fb[0][unc] - dense[unc]).max() / scale
+    err_keep = np.abs(fb[0][~unc] - plain[0][~unc]).max() / scale
+    print(f"uncertain (direction, order) entries {unc.sum()} of {unc.size}: fallback vs dense {err_unc:.2e}, "
+          f"the others vs learned {err_keep:.2e}")
+    assert err_unc <= 1e-9 and err_keep == 0.0

@@ -109,7 +109,7 @@ def test_learned_field_matches_exact_branch_sum(oracle_mod, spec):
         c3 = cnt[:, p].astype(int)
         ok = valid & ((c3 & 0x80) == 0)
         c3 &= 0x7F
-        cl = gr[:, p].astype(int)
+        cl = gr[:, p].astype(int) & 0x7F
         same = ok & (cl == c3) & (c3 > 0)
         scale = np.abs(ref[:, p]).max()
         err = np.abs(got[same, p] - ref[same, p]).max() / scale
@@ -174,7 +174,7 @@ def test_learned_heads_at_closed_form_roots(oracle_mod):
         th = const_theta(O, P_MAX + 1, seeds, [[0.0, 0.0, 0.0, -8.0]] * (P_MAX + 1))
         out, mk, rt = o.field_learned_dirs(th, P_MAX, dirs[k:k + 1], p_min=0.05, **NEWTON)
         got[k] = O.complex_field(out)[0, p]
-        roots[k] = rt[0, p]
+        roots[k] = rt[0, p] & 0x7F
     assert np.array_equal(roots, np.array(counts)), (roots, counts)
     ref, rmask, _, _ = o.field_dirs(P_MAX, dirs, n_target=160_000, flags=O.FIELD_EXACT)
     ref = O.complex_field(ref)[:, p]
