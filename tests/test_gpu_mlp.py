@@ -42,6 +42,15 @@ def seeded_params(n_orders, seed, scale=1.0):
     return th
 
 
+# Bounds of the tensor-core kernels against the oracle, which rounds weights, inputs and hidden
+# activations to bfloat16 as they do.  What remains is the order of the single-precision sums and
+# the GELU's hardware exponential: a hidden activation near a bfloat16 rounding tie may round the
+# other way (one bfloat16 step, 2^-8 of itself), which moves an output by up to about 1e-3 of the
+# largest (measured maxima 6.9e-4 on 1000 rows and 1.6e-3 on 116813 rows, medians about 1e-8), and a
+# gradient block by up to 3.1e-3 (normwise).  Twice the measured maxima:
+FWD_MAX, FWD_MEDIAN, GRAD_REL = 3.5e-3, 1e-6, 6.5e-3
+
+
 def bf16_rows(x):
     t = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16)
     return t, t.to(torch.float64).numpy()
@@ -65,7 +74,7 @@ def test_forward_matches_oracle(rtw, oracle_mod):
         scale = np.abs(ref).max()
         print(f"forward order {order}: max |dy| / max |y| = {err.max() / scale:.2e}, "
               f"median {np.median(err) / scale:.2e}")
-        assert err.max() <= 2e-2 * scale and np.median(err) <= 1e-4 * scale
+        assert err.max() <= FWD_MAX * scale and np.median(err) <= FWD_MEDIAN * scale
 
 
 def test_forward_many_tiles_matches_oracle(rtw, oracle_mod):
@@ -93,7 +102,7 @@ def test_forward_many_tiles_matches_oracle(rtw, oracle_mod):
     err = np.abs(got[sample] - ref)
     scale = np.abs(ref).max()
     print(f"forward {rows} rows: max |dy| / max |y| = {err.max() / scale:.2e}, median {np.median(err) / scale:.2e}")
-    assert err.max() <= 2e-2 * scale and np.median(err) <= 1e-4 * scale
+    assert err.max() <= FWD_MAX * scale and np.median(err) <= FWD_MEDIAN * scale
 
 
 def test_forward_rejects_misaligned_rows(rtw):
@@ -134,7 +143,7 @@ def test_gradient_matches_oracle(rtw, oracle_mod):
         r, gt = ref[k:k + n], got[k:k + n]
         rel = np.linalg.norm(gt - r) / np.linalg.norm(r)
         print(f"grad {name}: relative error {rel:.2e}")
-        assert rel <= 1e-2, name
+        assert rel <= GRAD_REL, name
 
 
 def test_adam_matches_oracle(rtw, oracle_mod):
