@@ -444,7 +444,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s, std::vector<std::pair<long long, long long>>* slices)
 {
-    const bool tiled = !newton && st.fmax && st.frec && w.tile_ws && w.perm;
+    const bool tiled = !newton && st.fmax && st.frec && st.fval && w.tile_ws && w.perm;
     const int np = st.np;
     const long long ndir = d.ndir;
     const int nout = per_order ? np : 1;
@@ -760,6 +760,7 @@ int rtw_trace(rtw_object* obj, const rtw_trace_params* tp, void* stream, rtw_ray
     r->st.flags = (uint32_t*)(b + off[5]);
     r->st.aux = aux ? (double*)(b + off[6]) : nullptr;
     r->st.frec = sf ? (float4*)(b + off[7]) : nullptr;
+    r->st.fval = sf ? (float4*)(b + off[7] + n * 32) : nullptr;
     r->st.fmax = sf ? (unsigned int*)(b + off[8]) : nullptr;
     RTW_CUDA(cudaMemcpyAsync(r->d_objs, r->objs.data(), sizeof(ObjDev) * objs.size(), cudaMemcpyHostToDevice, s));
     if (sf) RTW_CUDA(cudaMemsetAsync(r->st.fmax, 0, 4 * (size_t)obj->count, s));

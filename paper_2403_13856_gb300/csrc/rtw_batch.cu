@@ -52,6 +52,7 @@ size_t state_layout(long long R, int np, int nobj, char* base, RaysDev* st)
         st->flags = (uint32_t*)(base + off[5]);
         st->aux = nullptr;
         st->frec = (float4*)(base + off[6]);
+        st->fval = (float4*)(base + off[6] + n * 32);
         st->fmax = (unsigned int*)(base + off[7]);
     }
     return total;

@@ -357,21 +357,19 @@ __device__ __forceinline__ void cell_triangle(const FieldArgs& a, long long base
 // theta, phi and the direction's hi parts of corner v from its field record
 __device__ __forceinline__ void load_corner_hi(const FieldArgs& a, long long i, TriGeom& g, int v)
 {
-    const float4 r0 = a.st.frec[4 * i], r1 = a.st.frec[4 * i + 1];
+    const float4 r0 = a.st.frec[2 * i], r1 = a.st.frec[2 * i + 1];
     g.th[v] = r0.x;
     g.ph[v] = r0.y;
-    g.s[v][0] = r1.x;
-    g.s[v][1] = r1.y;
-    g.s[v][2] = r1.z;
-    g.l[v][0] = r1.w;
+    g.s[v][0] = r0.z;
+    g.s[v][1] = r0.w;
+    g.s[v][2] = r1.x;
+    g.l[v][0] = r1.y;
+    g.l[v][1] = r1.z;
+    g.l[v][2] = r1.w;
 }
 
-__device__ __forceinline__ void load_corner_lo(const FieldArgs& a, long long i, TriGeom& g, int v)
-{
-    const float4 r2 = a.st.frec[4 * i + 2];
-    g.l[v][1] = r2.x;
-    g.l[v][2] = r2.y;
-}
+// (the low parts come with the geometry record)
+__device__ __forceinline__ void load_corner_lo(const FieldArgs&, long long, TriGeom&, int) {}
 
 // corners of triangle t with their single-precision directions (hi and lo parts)
 __device__ __forceinline__ void load_triangle(const FieldArgs& a, long long base, long long nx, long long cx,
@@ -1555,14 +1553,14 @@ __device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b,
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const long long i = c.base + g.id[v];
-            const float4 r0 = a.st.frec[4 * i], r2 = a.st.frec[4 * i + 2], r3 = a.st.frec[4 * i + 3];
-            F[v][0] = r2.z;
-            F[v][1] = r2.w;
-            F[v][2] = r3.x;
-            F[v][3] = r3.y;
-            F[v][4] = r3.z;
-            F[v][5] = r3.w;
-            P[v] = df(r0.z, r0.w);
+            const float4 r0 = a.st.fval[2 * i], r1 = a.st.fval[2 * i + 1];
+            F[v][0] = r0.z;
+            F[v][1] = r0.w;
+            F[v][2] = r1.x;
+            F[v][3] = r1.y;
+            F[v][4] = r1.z;
+            F[v][5] = r1.w;
+            P[v] = df(r0.x, r0.y);
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) Fi[k] = l0 * F[0][k] + l1 * F[1][k] + l2 * F[2][k];

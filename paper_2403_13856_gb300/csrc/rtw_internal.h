@@ -81,11 +81,13 @@ struct RaysDev {
     double2* Fy;
     double2* Fz;
     uint32_t* flags;
-    // single-precision field record of every (ray, order) for the square-grid field, four float4 at
-    // frec[4 i .. 4 i + 3]: (theta, phi, Psi_hi, Psi_lo), (s_x, s_y, s_z hi, s_x lo), (s_y, s_z lo,
-    // F_x), (F_y, F_z) -- direction and phase as hi + lo pairs (about 48 bits), F to single
-    // precision, theta and phi of s to single precision; null when not kept
+    // single-precision field records of every (ray, order) for the square-grid field, two 32-byte
+    // halves in two arrays: the geometry that the classification reads, frec[2 i], frec[2 i + 1] =
+    // (theta, phi, s_x, s_y hi), (s_z hi, s_x, s_y, s_z lo); the values that a hit reads, fval[2 i],
+    // fval[2 i + 1] = (Psi_hi, Psi_lo, F_x), (F_y, F_z) -- direction and phase as hi + lo pairs (about
+    // 48 bits), F, theta and phi to single precision; null when not kept
     float4* frec;
+    float4* fval;
     double* aux;      // kAuxCount x (np R) or null
     unsigned int* fmax;  // per object: bits of the largest |F|^2 (float) of a valid record that is not
                          //   near-caustic (the scale of the field's fixed-point sums); null when not kept

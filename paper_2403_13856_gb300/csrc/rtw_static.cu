@@ -118,6 +118,7 @@ extern "C" int rtw_fan_field_static(const rtw_object_desc* d, const rtw_incident
     st.flags = reinterpret_cast<uint32_t*>(p + 80 * n);
     st.aux = nullptr;
     st.frec = nullptr;
+    st.fval = nullptr;
     unsigned int* mask_words = reinterpret_cast<unsigned int*>(base + kObjBytes + kStateBytes);
     rtw::ObjDev* d_obj = reinterpret_cast<rtw::ObjDev*>(base);
 

@@ -48,11 +48,10 @@ struct StateSink {
             const float ph = f64_to_f32_int(fr.psi);
             const float pl = f64_to_f32_int(fr.psi - f32_to_f64_int(ph));
             const float th = atan2f(sqrtf(sh[0] * sh[0] + sh[1] * sh[1]), sh[2]), az = atan2f(sh[1], sh[0]);
-            float4* r = st.frec + 4 * i;
-            r[0] = make_float4(th, az, ph, pl);
-            r[1] = make_float4(sh[0], sh[1], sh[2], sl[0]);
-            r[2] = make_float4(sl[1], sl[2], Ff[0], Ff[1]);
-            r[3] = make_float4(Ff[2], Ff[3], Ff[4], Ff[5]);
+            st.frec[2 * i] = make_float4(th, az, sh[0], sh[1]);
+            st.frec[2 * i + 1] = make_float4(sh[2], sl[0], sl[1], sl[2]);
+            st.fval[2 * i] = make_float4(ph, pl, Ff[0], Ff[1]);
+            st.fval[2 * i + 1] = make_float4(Ff[2], Ff[3], Ff[4], Ff[5]);
             if (st.fmax && !(fr.flags & kFlagCaustic)) {
                 float f2 = 0.0f;
 #pragma unroll
