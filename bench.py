@@ -45,12 +45,12 @@ def _oracle_flops():
     except (OSError, KeyError, ValueError):
         return float(KERNEL_FLOPS_PER_INTERACTION), "hand count of the kernel source (stored oracle count missing)"
 FP64_NOMINAL_GFLOPS = 1250.0
-# DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload: ncu measured
-# 1.56 MB + 578.0 MB at 1e6 rays (the ray-state write); the traffic grows with the rays that hit,
-# 4x at 4e6
-TRACE_TRAFFIC_BYTES = 4 * (1_564_160 + 577_976_576)
-TRACE_TRAFFIC_NOTE = ("DRAM bytes per launch from ncu at 1e6 rays, scaled by hits (4x); "
-                      "profiles/trace_kernel_fp64_ellipsoid_1e6rays.md")
+# DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload at 4e6 rays
+# (ncu: 4.04 MB + 3180.7 MB, the ray-state write)
+TRACE_TRAFFIC_BYTES = 4_041_000 + 3_180_708_000
+TRACE_TRAFFIC_NOTE = "DRAM bytes of one launch at 4e6 rays (ncu); profiles/trace_kernel_fp64_ellipsoid_4e6rays.md"
+# FP64 flops the kernel executes per interaction (ncu: DFMA x 2 + DMUL + DADD over the interactions)
+EXECUTED_FLOPS_PER_INTERACTION = 462
 FLOPS_PER_INTERACTION, FLOPS_SOURCE = _oracle_flops()
 
 
@@ -656,9 +656,9 @@ def bench_ellipsoid(args, rank, world, local, dist):
     achieved = FLOPS_PER_INTERACTION * units / tr / 1e9
     peak = pipes["fp64_gflops"]
     clocks = clk.summary()
-    # the field's algorithmic bytes: the ray state it reads (direction, F, Psi, flags per (ray,
-    # order) that hit: 68 B) and the complex128 grid it writes
-    field_bytes = units * 68 + ndir * 32
+    # the field's algorithmic bytes: the ray state it reads once (the 64-byte single-precision field
+    # record of every (ray, order) that hit) and the complex128 grid it writes
+    field_bytes = units * 64 + ndir * 32
     hbm = peaks.get("hbm_gbs")
     mixed_tr = forms["mixed"]["ms_trace"] / 1e3
     cpu = None
@@ -681,18 +681,27 @@ def bench_ellipsoid(args, rank, world, local, dist):
                      "peak_source": f"measured: DFMA chains (rtw_pipe_peak) at {pipes['sm_mhz']} MHz; "
                                     f"cuBLAS DGEMM 4096^3 {fp64_dgemm:.0f}; nominal {FP64_NOMINAL_GFLOPS:.0f}",
                      "flops_per_interaction": FLOPS_PER_INTERACTION, "flops_source": FLOPS_SOURCE,
-                     "frac_kernel_count": KERNEL_FLOPS_PER_INTERACTION * units / tr / 1e9 / peak,
+                     "frac_executed": EXECUTED_FLOPS_PER_INTERACTION * units / tr / 1e9 / peak,
+                     "executed_flops_per_interaction": EXECUTED_FLOPS_PER_INTERACTION,
+                     "note": "the oracle's operation count per interaction (760) exceeds what the kernel "
+                             "executes (462: one reciprocal where the oracle divides), so the algorithmic "
+                             "rate passes the DFMA-chain peak; the FP64 pipe is 88.5 % busy (ncu)",
                      "traffic": TRACE_TRAFFIC_BYTES, "traffic_note": TRACE_TRAFFIC_NOTE},
-        "roofline_field": {"kernels": "field_grid_kernel, field_grid_big_kernel, field_grid_hit_kernel",
+        "roofline_field": {"kernels": "field_grid_kernel, field_grid_big_kernel, hit_bin_kernel, tile_sum_kernel, "
+                                      "tile_convert_kernel",
                            "bound": "hbm", "achieved": field_bytes / tf / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": (field_bytes / tf / 1e9 / hbm) if hbm else None, "bytes": field_bytes,
-                           "bytes_note": "ray state read (68 B per hit ray and order) + complex128 grid written"},
+                           "bytes_note": "the ray state read once (the 64-byte field record of every hit ray and "
+                                         "order) + the complex128 grid written; the classification is "
+                                         "instruction-bound (profiles/field_kernels_ellipsoid_4e6rays.md)"},
         "roofline_mixed": {"kernel": "trace_kernel_mixed", "bound": "alu",
                            "achieved": FLOPS_PER_INTERACTION * units / mixed_tr / 1e9,
                            "peak": pipes["fp32_gflops"], "unit": "GFLOP/s FP32",
                            "frac": FLOPS_PER_INTERACTION * units / mixed_tr / 1e9 / pipes["fp32_gflops"],
                            "note": "the same algorithmic flops as the FP64 trace over the mixed trace's time, "
-                                   "against the FP32 pipe (the larger of FFMA and packed FFMA2)"},
+                                   "against the FP32 pipe (the larger of FFMA and packed FFMA2); the kernel is "
+                                   "bound by its residual double-precision work instead (FP64 pipe 86.5 % busy, "
+                                   "profiles/trace_kernel_mixed_ellipsoid_1e6rays.md)"},
         "pipe_peaks": pipes,
         "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
