@@ -268,6 +268,46 @@ typedef struct {
 int rtw_field_po2d(const rtw_rays* rays, const rtw_po2d_params* pp, const double* dirs, int64_t n_dirs,
                    void* field_out, int64_t* n_used, void* stream);
 
+/* 2-D physical optics at the 3-D caustics of a square-grid far field (the "Diffraction effect
+ * correction based on VCRM" carried to three dimensions, where the paper leaves it "under study").
+ * The field of rtw_field (RTW_DENSE), and for every order p >= p_min: the directions C_p that cell
+ * triangles of order p which are not consistent cover (the directions rtw_field masks for that
+ * order) set the weight s_p(u) = ramp(angle from u to the nearest direction of C_p) -- 1 up to
+ * po_full, cos^2 down to 0 at po_end -- and the field of that order becomes
+ *     (1 - s_p) F_rays + s_p F_PO,
+ * F_PO the Kirchhoff integral of the exit waves over a plane, as rtw_field_po2d: for the directions
+ * of one tile of tile_theta x tile_phi grid directions the plane passes through the object centre
+ * normal to the tile's centre direction a, every ray of order p is weighted by the angle of its exit
+ * direction to a (1 up to rho + cone_full, cos^2 to 0 at rho + cone_end, rho the largest angle from a
+ * to a direction of the tile), and F_PO(u) = k0 / (2 pi i) (u . a) sum w U dA e^{-i k0 u . x}, the
+ * plane's far field (Rayleigh-Sommerfeld).  Widths left 0 take the fan's: with Aw = (lambda / L)^(2/3)
+ * and Fw = 1 / sqrt(k0 L), L the largest semi-axis, po_full = 1.5 Aw, po_end = 3 Aw, cone_full =
+ * 3 Aw + 3 Fw, cone_end = 3 Aw + 6 Fw.  The integral samples the plane at the rays' crossing points:
+ * like rtw_field_po2d it is accurate to about 1e-2 of the field at grid spacings near 0.1 um, and
+ * converges as the spacing shrinks.  tile_theta, tile_phi 0 take 16; p_min 0 takes 1 (order 0 of
+ * an ellipsoid has no fold).
+ * rays: one ellipsoid in a plane wave, square grid, RTW_FP64, traced with RTW_TRACE_APERTURE, far
+ * field.  dirs: RTW_DIRS_GRID, cell_window all -1.  flags: 0 or RTW_FIELD_PER_ORDER.  field_out
+ * (device): as rtw_field.  mask_out (device, optional): as rtw_field, except that the caustic bit is
+ * kept only on the directions of C_p where s_p < 1 (none for po_full > 0) or p < p_min, and every
+ * direction with s_p > 0 for some p has RTW_MASK_PO.  weights_out (device, optional):
+ * [directions][orders] doubles, s_p (0 for p < p_min).  Errors: RTW_ERR_ARG (rays or directions not
+ * as above, tile_theta or tile_phi negative or tile_theta tile_phi above 256, 0 <= po_full < po_end
+ * and 0 <= cone_full < cone_end violated, a tile's radius bound (tile_theta pi / n_theta + tile_phi
+ * pi / n_phi) / 2 plus cone_end reaching pi / 2, p_min beyond the orders), RTW_ERR_NOMEM, RTW_ERR_CUDA.
+ * Asynchronous; scratch (16 bytes per direction, 32 per direction and order without
+ * RTW_FIELD_PER_ORDER, 16 per 256 rays) is allocated and freed in stream order.  Cost: per order, the
+ * plane crossing of every ray whose 16 x 16 block meets a tile's cone, and one FP32 sincos per
+ * (ray in the cone, direction of the tile). */
+typedef struct {
+    int tile_theta, tile_phi;
+    double po_full, po_end;
+    double cone_full, cone_end;
+    int p_min;
+} rtw_caustic_params;
+int rtw_field_caustic(const rtw_rays* rays, const rtw_dirs* dirs, const rtw_caustic_params* cp, int flags,
+                      void* field_out, uint8_t* mask_out, double* weights_out, void* stream);
+
 /* ---- many objects in one launch sequence ---- */
 
 /* Options of rtw_far_field_batch.  n_rays (host, one entry per object, read during the call) is

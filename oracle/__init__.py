@@ -76,6 +76,8 @@ def lib():
         L.or_field_sphere.restype = i64
         L.or_field_po2d.argtypes = [p, i64, d, i, p, d, d, d, d, p, i64, p]
         L.or_field_po2d.restype = i64
+        L.or_field_grid_caustic.argtypes = [p, i64, d, i, i, i, p, p, p, p, p, p, i]
+        L.or_field_grid_caustic.restype = i64
         L.or_newton.argtypes = [p, i, p, p, d, p]
         L.or_newton.restype = i
         L.om_gelu.argtypes = [d]
@@ -181,6 +183,39 @@ class Object:
         if used < 0:
             raise ValueError("invalid aperture window or cone")
         return complex_field(out), int(used)
+
+    def caustic_defaults(self):
+        """Widths of the caustic correction of an object of largest semi-axis L: the Airy width
+        Aw = (lambda / L)^(2/3) and the Fresnel width Fw = 1 / sqrt(k0 L) set po_full = 1.5 Aw,
+        po_end = 3 Aw, cone_full = 3 Aw + 3 Fw and cone_end = 3 Aw + 6 Fw (the fan's constants)."""
+        L = max(self.a, self.b, self.c)
+        aw = (self.wavelength / L) ** (2.0 / 3.0)
+        fw = 1.0 / np.sqrt(self.k0 * L)
+        return dict(po_full=1.5 * aw, po_end=3.0 * aw, cone_full=3.0 * aw + 3.0 * fw, cone_end=3.0 * aw + 6.0 * fw)
+
+    def field_grid_caustic(self, pmax, ntheta, nphi, tile=(16, 16), po_full=None, po_end=None, cone_full=None,
+                           cone_end=None, p_min=1, n_target=0, h=0.0, threads=0):
+        """or_field_grid_caustic: the square-grid field with the 2-D physical optics of the caustics
+        blended in.  Widths left None take caustic_defaults().  Returns (out (ndir, pmax+1, 4), mask,
+        weights (ndir, pmax+1), caustic orders (ndir uint32, bit p), l1 (ndir, pmax+1), hits)."""
+        dflt = self.caustic_defaults()
+        w = [dflt[k] if v is None else v for k, v in (("po_full", po_full), ("po_end", po_end),
+                                                       ("cone_full", cone_full), ("cone_end", cone_end))]
+        cp = np.array([tile[0], tile[1], *w, p_min], dtype=np.float64)
+        nd = ntheta * nphi
+        out = np.zeros((nd, pmax + 1, 4))
+        mask = np.zeros(nd, dtype=np.uint8)
+        weights = np.zeros((nd, pmax + 1))
+        corders = np.zeros(nd, dtype=np.uint32)
+        l1 = np.zeros((nd, pmax + 1))
+        hits = lib().or_field_grid_caustic(self.handle, int(n_target), float(h), int(pmax), int(ntheta), int(nphi),
+                                           _ptr(cp), _ptr(out), _ptr(mask), _ptr(weights), _ptr(corders), _ptr(l1),
+                                           int(threads))
+        if hits == -2:
+            raise ValueError("a tile's cone reaches 90 degrees from its aperture normal")
+        if hits < 0:
+            raise RuntimeError("or_field_grid_caustic failed")
+        return out, mask, weights, corders, l1, int(hits)
 
     def field_grid(self, pmax, ntheta, nphi, n_target=0, h=0.0, window=None, flags=0, threads=0):
         out = np.zeros((ntheta * nphi, pmax + 1, 4))

@@ -1292,9 +1292,12 @@ static int edge_in(double e, int64_t ia, int64_t ib, int sigma)
 /* The square-grid field on either the cell-centred (theta, phi) grid (list == NULL) or the
  * directions of a list (n_list x (theta, phi)); one loop body tests a direction against a cell
  * triangle for both. */
+/* corders (may be NULL): per direction, bit p set where a cell triangle of order p that is not
+ * consistent covers it (the directions the caustic mask bit comes from, by order) */
 static int64_t field_square(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
                             const double* list, int64_t n_list, const int64_t* window, int flags, double* out,
-                            uint8_t* mask, int nthreads, int64_t* newton_fail, double near_R, uint8_t* counts)
+                            uint8_t* mask, int nthreads, int64_t* newton_fail, double near_R, uint8_t* counts,
+                            uint32_t* corders)
 {
     const int np = pmax + 1;
     double h, xc, yc;
@@ -1354,6 +1357,7 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
     memset(out, 0, sizeof(double) * (size_t)ndir * np * nout);
     memset(mask, 0, (size_t)ndir);
     if (counts) memset(counts, 0, (size_t)ndir * np);
+    if (corders) memset(corders, 0, sizeof(uint32_t) * (size_t)ndir);
     const double dth = list ? 1.0 : PI / ntheta, dph = list ? 1.0 : 2.0 * PI / nphi;
     double axial = 2.0 * o->lambda / o->Lmin;
     /* unit vector, e_theta, e_phi of every direction */
@@ -1478,6 +1482,12 @@ static int64_t field_square(const or_object* o, int64_t n_target, double h_in, i
 #pragma omp atomic
 #endif
                             mask[dk] |= OR_MASK_CAUSTIC;
+                            if (corders) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                                corders[dk] |= 1u << p;
+                            }
                             continue;
                         }
                         /* barycentric weights of the central projection onto the corner plane */
@@ -1542,14 +1552,14 @@ int64_t or_field_grid(const or_object* o, int64_t n_target, double h_in, int pma
                       int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, window, flags, out, mask, nthreads,
-                        newton_fail, 0.0, NULL);
+                        newton_fail, 0.0, NULL, NULL);
 }
 
 int64_t or_field_grid_counts(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
                              int flags, double* out, uint8_t* mask, uint8_t* counts, int nthreads, int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, flags, out, mask, nthreads,
-                        newton_fail, 0.0, counts);
+                        newton_fail, 0.0, counts, NULL);
 }
 
 int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi, double R,
@@ -1557,14 +1567,14 @@ int64_t or_field_sphere(const or_object* o, int64_t n_target, double h_in, int p
 {
     double rc = sqrt(dot3(o->center, o->center));
     if (!(R > rc + o->Rbound)) return -1;
-    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, R, NULL);
+    return field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, R, NULL, NULL);
 }
 
 int64_t or_field_dirs(const or_object* o, int64_t n_target, double h_in, int pmax, const double* dirs,
                       int64_t ndir, int flags, double* out, uint8_t* mask, int nthreads, int64_t* newton_fail)
 {
     return field_square(o, n_target, h_in, pmax, 0, 0, dirs, ndir, NULL, flags, out, mask, nthreads,
-                        newton_fail, 0.0, NULL);
+                        newton_fail, 0.0, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------------------- */
@@ -1700,6 +1710,283 @@ int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, 
     free(ok);
     free(wgt);
     return used;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* 2-D physical optics at the caustics of a square-grid field                              */
+/* ------------------------------------------------------------------------------------- */
+
+/* what the aperture integral needs of one (ray, order) record */
+typedef struct {
+    int valid;
+    double s[3], r[3], Q[4], E[4], v1[3], v2[3], dlegs, nflegs, path;
+} aprec;
+
+/* Reading of "Diffraction effect correction based on VCRM" and the "Strategy of Ray Theory of
+ * Waves" for 3-D caustics, which the paper leaves "under study": near the directions a fold covers,
+ * the field of that order is the Kirchhoff integral of the exit waves over a plane (the 2-D form of
+ * the fan's physical optics), blended into the ray sum with the fan's angular taper.
+ *
+ *   C_p    the directions covered by a cell triangle of order p that is not consistent (the
+ *          directions whose caustic mask bit comes from order p);
+ *   d_p(u) the angle from u to the nearest direction of C_p;
+ *   s_p(u) = ramp(d_p(u), po_full, po_end): 1 within po_full, cos^2 down to 0 at po_end;
+ *   F_p(u) = (1 - s_p(u)) F_rays,p(u) + s_p(u) F_PO,p(u).
+ *
+ * F_PO of a direction u of the (theta, phi) grid tile it falls in (tile_theta x tile_phi
+ * directions) is taken over the plane through the object centre whose normal a is the tile's centre
+ * direction: every ray of order p carries its exit wave to the plane (x, U as or_field_po2d), each
+ * weighted by ramp(g, rho + cone_full, rho + cone_end) of the angle g between its exit direction
+ * and a (rho: the largest angle from a to a direction of the tile), the plane's area per grid cell
+ * from central differences of the neighbours' crossing points, and
+ *   F_PO(u) = k0 / (2 pi i) (u . a) sum_j w_j U_j dA_j e^{-i k0 u . x_j}
+ * projected on (e_theta, e_phi), the far field of the plane's field (Rayleigh-Sommerfeld; the factor
+ * u . a makes the result independent of the plane to the order of the ray fields themselves).
+ * Orders p >= p_min are corrected; the caustic bit stays on a direction of C_p only where s_p < 1
+ * (so none, for po_full > 0: s_p = 1 on C_p), and every corrected direction has OR_MASK_PO. */
+int64_t or_field_grid_caustic(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
+                              const double* cp, double* out, uint8_t* mask, double* weights, uint32_t* corders_out,
+                              double* l1, int nthreads)
+{
+    const int np = pmax + 1;
+    const int tt = (int)cp[0], tp = (int)cp[1];
+    const double po_full = cp[2], po_end = cp[3], cone_full = cp[4], cone_end = cp[5];
+    const int p_min = (int)cp[6];
+    if (o->src || o->shape_e != 1.0) return -1; /* plane wave on an ellipsoid */
+    if (ntheta < 1 || nphi < 1 || tt < 1 || tp < 1 || p_min < 0 || p_min > pmax || pmax > 31) return -1;
+    if (!(po_full >= 0.0 && po_end > po_full && cone_full >= 0.0 && cone_end > cone_full)) return -1;
+    const int64_t ndir = (int64_t)ntheta * nphi;
+    const double dth = PI / ntheta, dph = 2.0 * PI / nphi;
+    double h, xc, yc;
+    int64_t nx, ny;
+    or_square_grid(o, n_target, h_in, &h, &nx, &ny, &xc, &yc);
+    const int nc = np - p_min;
+    const int64_t nv = nx * ny;
+    uint32_t* corders = (uint32_t*)calloc((size_t)ndir, sizeof(uint32_t));
+    double* sw = (double*)malloc(sizeof(double) * (size_t)ndir);
+    aprec* ar = (aprec*)calloc((size_t)nv * nc, sizeof(aprec));
+    double* dv = (double*)malloc(sizeof(double) * 9 * (size_t)ndir);
+    double* xq = (double*)malloc(sizeof(double) * 3 * (size_t)nv);
+    double* wq = (double*)malloc(sizeof(double) * (size_t)nv);
+    uint8_t* okq = (uint8_t*)malloc((size_t)nv);
+    cplx* Tq = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)nv);
+    int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)nv);
+    int64_t* cdir = (int64_t*)malloc(sizeof(int64_t) * (size_t)ndir);
+    /* the ray sum of every order, and the orders of the caustic directions */
+    int64_t rc = -1;
+    if (corders && sw && ar && dv && xq && wq && okq && Tq && list && cdir)
+        rc = field_square(o, n_target, h_in, pmax, ntheta, nphi, NULL, 0, NULL, 0, out, mask, nthreads, NULL, 0.0,
+                          NULL, corders);
+    if (rc < 0) {
+        free(corders); free(sw); free(ar); free(dv); free(xq); free(wq); free(okq); free(Tq); free(list); free(cdir);
+        return rc;
+    }
+    if (weights) memset(weights, 0, sizeof(double) * (size_t)ndir * np);
+    if (l1) memset(l1, 0, sizeof(double) * (size_t)ndir * np);
+    /* the exit records of every grid vertex for the corrected orders */
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double* buf = (double*)malloc(sizeof(double) * (size_t)np * OR_NFIELD);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t iy = 0; iy < ny; ++iy)
+            for (int64_t ix = 0; ix < nx; ++ix) {
+                double x = grid_coord(xc, ix, nx, h), y = grid_coord(yc, iy, ny, h);
+                double dx = x - xc, dy = y - yc;
+                double qf = dx * (o->S[0][0] * dx + o->S[0][1] * dy) + dy * (o->S[1][0] * dx + o->S[1][1] * dy);
+                if (!(qf < 1.0)) continue;
+                or_trace_ray(o, x, y, pmax, buf, NULL);
+                for (int p = p_min; p < np; ++p) {
+                    const double* r = buf + (size_t)p * OR_NFIELD;
+                    aprec* a = ar + (size_t)(p - p_min) * nv + iy * nx + ix;
+                    a->valid = r[OR_VALID] != 0.0;
+                    if (!a->valid) continue;
+                    memcpy(a->s, r + OR_S, sizeof(a->s));
+                    memcpy(a->r, r + OR_REXIT, sizeof(a->r));
+                    memcpy(a->Q, r + OR_Q, sizeof(a->Q));
+                    memcpy(a->E, r + OR_E, sizeof(a->E));
+                    memcpy(a->v1, r + OR_V1, sizeof(a->v1));
+                    memcpy(a->v2, r + OR_V2, sizeof(a->v2));
+                    a->dlegs = r[OR_DLEGS];
+                    a->nflegs = r[OR_NFLEGS];
+                    a->path = r[OR_PATH];
+                }
+            }
+        free(buf);
+    }
+    /* unit vector, e_theta, e_phi of every direction */
+    for (int64_t k = 0; k < ndir; ++k) {
+        double th = (k / nphi + 0.5) * dth, ph = -PI + (k % nphi + 0.5) * dph;
+        double* d = dv + 9 * k;
+        d[0] = sin(th) * cos(ph);
+        d[1] = sin(th) * sin(ph);
+        d[2] = cos(th);
+        d[3] = cos(th) * cos(ph);
+        d[4] = cos(th) * sin(ph);
+        d[5] = -sin(th);
+        d[6] = -sin(ph);
+        d[7] = cos(ph);
+        d[8] = 0.0;
+    }
+    const int ntt = (ntheta + tt - 1) / tt, ntp = (nphi + tp - 1) / tp;
+    const cplx pre = -I * o->k0 / (2.0 * PI);
+    /* the caustic orders of each direction that the correction leaves uncovered (s_p < 1) */
+    uint32_t* left = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)ndir);
+    if (!left) rc = -1;
+    else memcpy(left, corders, sizeof(uint32_t) * (size_t)ndir);
+    for (int p = p_min; p < np && rc >= 0; ++p) {
+        const aprec* arp = ar + (size_t)(p - p_min) * nv;
+        /* s_p: the taper of the angle to the nearest caustic direction of order p; the caustic
+         * directions are listed in row order, and only rows within po_end can be that close */
+        int64_t ncd = 0;
+        for (int64_t k = 0; k < ndir; ++k)
+            if (corders[k] & (1u << p)) cdir[ncd++] = k;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+        for (int64_t k = 0; k < ndir; ++k) {
+            const double thk = (k / nphi + 0.5) * dth;
+            double best = -2.0;
+            for (int64_t c = 0; c < ncd; ++c) {
+                const double thc = (cdir[c] / nphi + 0.5) * dth;
+                if (fabs(thc - thk) > po_end) continue;
+                best = fmax(best, dot3(dv + 9 * k, dv + 9 * cdir[c]));
+            }
+            const double d = best < -1.5 ? 2.0 * PI : acos(fmin(1.0, fmax(-1.0, best)));
+            sw[k] = d < po_end ? ramp(d, po_full, po_end) : 0.0;
+        }
+        for (int bt = 0; bt < ntt && rc >= 0; ++bt)
+            for (int bp = 0; bp < ntp && rc >= 0; ++bp) {
+                const int r0 = bt * tt, r1 = r0 + tt < ntheta ? r0 + tt : ntheta;
+                const int c0 = bp * tp, c1 = c0 + tp < nphi ? c0 + tp : nphi;
+                int active = 0;
+                for (int i = r0; i < r1; ++i)
+                    for (int j = c0; j < c1; ++j) active |= sw[(int64_t)i * nphi + j] > 0.0;
+                if (!active) continue;
+                /* the aperture of the tile: the plane through the centre normal to the tile's
+                 * centre direction; rho, the largest angle from there to a direction of the tile */
+                const double tha = 0.5 * (r0 + r1) * dth, pha = -PI + 0.5 * (c0 + c1) * dph;
+                const double a[3] = {sin(tha) * cos(pha), sin(tha) * sin(pha), cos(tha)};
+                double rho = 0.0;
+                for (int i = r0; i < r1; ++i)
+                    for (int j = c0; j < c1; ++j)
+                        rho = fmax(rho, acos(fmin(1.0, fmax(-1.0, dot3(a, dv + 9 * ((int64_t)i * nphi + j))))));
+                const double cf = rho + cone_full, ce = rho + cone_end;
+                if (!(ce < 0.5 * PI)) {
+                    rc = -2; /* the cone reaches the plane */
+                    break;
+                }
+                /* every ray's crossing point; the field and weight of those in the cone */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+                for (int64_t q = 0; q < nv; ++q) {
+                    const aprec* r = arp + q;
+                    okq[q] = 0;
+                    wq[q] = 0.0;
+                    if (!r->valid) continue;
+                    const double sa = dot3(a, r->s);
+                    if (!(fabs(sa) > 1e-6)) continue;
+                    const double dd[3] = {o->center[0] - r->r[0], o->center[1] - r->r[1], o->center[2] - r->r[2]};
+                    const double tau = dot3(a, dd) / sa;
+                    for (int c = 0; c < 3; ++c) xq[3 * q + c] = r->r[c] + tau * r->s[c];
+                    okq[q] = 1;
+                    const double w = ramp(acos(fmin(1.0, fmax(-1.0, sa))), cf, ce);
+                    if (w == 0.0) continue;
+                    double Am[2][2] = {{1.0 + tau * r->Q[0], tau * r->Q[1]}, {tau * r->Q[2], 1.0 + tau * r->Q[3]}};
+                    const double det = det2(Am);
+                    if (det == 0.0) continue;
+                    const int nfl = neg_eigs(Am);
+                    const int nf_ap = (int)r->nflegs + (tau > 0.0 ? nfl : -nfl);
+                    const cplx amp = sqrt(r->dlegs / fabs(det)) * minus_i_pow(nf_ap) * cexp(I * o->k0 * (r->path + tau));
+                    const cplx E0 = r->E[0] + I * r->E[1], E1 = r->E[2] + I * r->E[3];
+                    for (int c = 0; c < 3; ++c) Tq[3 * q + c] = amp * (E0 * r->v1[c] + E1 * r->v2[c]);
+                    wq[q] = w;
+                }
+                /* the plane's area per grid cell (central differences, one-sided next to a
+                 * vertex without a crossing, none where an axis has no neighbour at all) */
+                int64_t nl = 0;
+                for (int64_t q = 0; q < nv; ++q) {
+                    if (wq[q] == 0.0) continue;
+                    const int64_t ix = q % nx, iy = q / nx;
+                    const int64_t qxm = ix > 0 && okq[q - 1] ? q - 1 : q, qxp = ix + 1 < nx && okq[q + 1] ? q + 1 : q;
+                    const int64_t qym = iy > 0 && okq[q - nx] ? q - nx : q, qyp = iy + 1 < ny && okq[q + nx] ? q + nx : q;
+                    if (qxm == qxp || qym == qyp) continue;
+                    double ex[3], ey[3], cr[3];
+                    for (int c = 0; c < 3; ++c) {
+                        ex[c] = (xq[3 * qxp + c] - xq[3 * qxm + c]) / (double)(qxp - qxm);
+                        ey[c] = (xq[3 * qyp + c] - xq[3 * qym + c]) / (double)((qyp - qym) / nx);
+                    }
+                    cross3(ex, ey, cr);
+                    const double f = wq[q] * fabs(dot3(cr, a));
+                    for (int c = 0; c < 3; ++c) Tq[3 * q + c] *= f;
+                    list[nl++] = q;
+                }
+                /* the far field of the plane at the tile's directions in the correction zone */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+                for (int i = r0; i < r1; ++i)
+                    for (int j = c0; j < c1; ++j) {
+                        const int64_t k = (int64_t)i * nphi + j;
+                        if (!(sw[k] > 0.0)) continue;
+                        const double* u = dv + 9 * k;
+                        cplx v[3] = {0.0, 0.0, 0.0};
+                        double norm1 = 0.0;
+                        for (int64_t m = 0; m < nl; ++m) {
+                            const int64_t q = list[m];
+                            const cplx e = cexp(-I * o->k0 * dot3(u, xq + 3 * q));
+                            double t2 = 0.0;
+                            for (int c = 0; c < 3; ++c) {
+                                v[c] += Tq[3 * q + c] * e;
+                                t2 += creal(Tq[3 * q + c]) * creal(Tq[3 * q + c]) + cimag(Tq[3 * q + c]) * cimag(Tq[3 * q + c]);
+                            }
+                            norm1 += sqrt(t2);
+                        }
+                        const double ua = dot3(u, a);
+                        cplx ft = 0.0, fp = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            ft += v[c] * u[3 + c];
+                            fp += v[c] * u[6 + c];
+                        }
+                        ft *= pre * ua;
+                        fp *= pre * ua;
+                        const double s = sw[k];
+                        double* acc = out + ((size_t)k * np + p) * 4;
+                        acc[0] = (1.0 - s) * acc[0] + s * creal(ft);
+                        acc[1] = (1.0 - s) * acc[1] + s * cimag(ft);
+                        acc[2] = (1.0 - s) * acc[2] + s * creal(fp);
+                        acc[3] = (1.0 - s) * acc[3] + s * cimag(fp);
+                        if (l1) l1[(size_t)k * np + p] = s * o->k0 / (2.0 * PI) * fabs(ua) * norm1;
+                        mask[k] |= OR_MASK_PO;
+                    }
+            }
+        for (int64_t k = 0; k < ndir && rc >= 0; ++k) {
+            if (weights) weights[(size_t)k * np + p] = sw[k];
+            if (sw[k] == 1.0) left[k] &= ~(1u << p); /* the order's ray sum is wholly replaced */
+        }
+    }
+    /* the caustic bit stays where an order's caustic direction is not wholly corrected */
+    if (rc >= 0)
+        for (int64_t k = 0; k < ndir; ++k)
+            mask[k] = (uint8_t)((mask[k] & ~OR_MASK_CAUSTIC) | (left[k] ? OR_MASK_CAUSTIC : 0u));
+    if (corders_out) memcpy(corders_out, corders, sizeof(uint32_t) * (size_t)ndir);
+    free(left);
+    free(corders);
+    free(sw);
+    free(ar);
+    free(dv);
+    free(xq);
+    free(wq);
+    free(okq);
+    free(Tq);
+    free(list);
+    free(cdir);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------------------- */

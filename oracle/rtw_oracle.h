@@ -161,6 +161,21 @@ int64_t or_field_po2d(const or_object* o, int64_t n_target, double h_in, int p, 
                       double ap_theta, double ap_phi, double cone_full, double cone_end, const double* dirs,
                       int64_t ndir, double* out);
 
+/* Square-grid field with the 2-D physical optics of the caustics (plane wave on an ellipsoid): the
+ * ray sum of or_field_grid, and for every order p >= p_min the Kirchhoff integral of the exit waves
+ * over a plane blended in around the directions that order's fold cells cover (taper s_p of the
+ * angle to them: 1 up to po_full, cos^2 to 0 at po_end); one plane per tile of tile_theta x tile_phi
+ * directions, normal to the tile's centre direction a, the rays weighted by the angle of their
+ * exit direction to a (1 up to rho + cone_full, 0 from rho + cone_end, rho the tile's radius about a).
+ * cp: {tile_theta, tile_phi, po_full, po_end, cone_full, cone_end, p_min}.  out: ndir x (pmax+1) x 4,
+ * mask: ndir (caustic bit only where an uncorrected order put it, OR_MASK_PO where s_p > 0).
+ * Optional: weights ndir x (pmax+1) (s_p), corders ndir (bit p: covered by an inconsistent cell of
+ * order p), l1 ndir x (pmax+1) (s_p k0 / 2 pi |u . a| sum |w U dA|, the size of the summed terms).
+ * Returns the hits of the ray sum, -1 for invalid arguments, -2 when a cone reaches 90 deg. */
+int64_t or_field_grid_caustic(const or_object* o, int64_t n_target, double h_in, int pmax, int ntheta, int nphi,
+                              const double* cp, double* out, uint8_t* mask, double* weights, uint32_t* corders,
+                              double* l1, int nthreads);
+
 /* Newton on the exact trace: finds the ray of order p whose exit direction is target, from the
  * seed impact point xy (2), with steps halved until the residual decreases; the root must lie
  * within rmax of the seed (rmax <= 0: no bound).  Returns iterations used, or -1 if it did not

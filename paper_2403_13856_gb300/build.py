@@ -17,7 +17,8 @@ LIBDIR = os.path.join(PKG, "lib")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(LIBDIR, "librtw.so")
 SOURCES = ["rtw_api.cu", "rtw_trace.cu", "rtw_field.cu", "rtw_static.cu", "rtw_batch.cu", "rtw_mlp.cu",
-           "rtw_mlp_tc.cu", "rtw_mlp_api.cu", "rtw_learned.cu", "rtw_po2d.cu", "rtw_peaks.cu"]
+           "rtw_mlp_tc.cu", "rtw_mlp_api.cu", "rtw_learned.cu", "rtw_po2d.cu", "rtw_peaks.cu",
+           "rtw_caustic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

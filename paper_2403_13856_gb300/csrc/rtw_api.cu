@@ -589,6 +589,35 @@ int ensure_device(int* dev)
     return RTW_OK;
 }
 
+// The plan, workspace (grown in the rays' block when too small) and prepared directions of a
+// square-grid field of rays on dirs; the row slices kept from an earlier run are dropped when the
+// directions or the window changed.
+int grid_prepare(rtw_rays* rays, const rtw_dirs* dirs, rtw::host::GridPlan* g, rtw::host::GridWs* w,
+                 rtw::DirSet* d, cudaStream_t s)
+{
+    *g = rtw::host::plan_grid(rays->objs.data(), rays->nobj, rays->np, dirs);
+    const size_t total = rtw::host::grid_ws(*g, rays->np, dirs, nullptr, nullptr);
+    if (rays->ws_bytes < total) {
+        if (rays->ws) cudaFree(rays->ws);
+        rays->ws = nullptr;
+        rays->ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&rays->ws, total);
+        if (e != cudaSuccess) return fail(RTW_ERR_NOMEM, "rtw_field: workspace of %zu bytes", total);
+        rays->ws_bytes = total;
+    }
+    rtw::host::grid_ws(*g, rays->np, dirs, (char*)rays->ws, w);
+    int rc = rtw::host::dirs_prepare(dirs, *w, d, s);
+    if (rc != RTW_OK) return rc;
+    const long long ndir = rtw::host::dir_count(dirs);
+    const int64_t* cw = dirs->cell_window;
+    const long long key = (ndir * 64 + rays->np) ^ (cw[0] * 7919 + cw[1] * 104729 + cw[2] * 1299709 + cw[3] * 15485863);
+    if (rays->slice_key != key) {
+        rays->slice_key = key;
+        rays->slices.clear();
+    }
+    return RTW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -902,31 +931,15 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
         return fail(RTW_ERR_ARG, "rtw_field: RTW_FIELD_PO needs a fan traced with RTW_TRACE_APERTURE");
     unsigned int* status = status_word(rays->device);
     if (dirs->kind != RTW_DIRS_PLANE) {
-        const rtw::host::GridPlan g = rtw::host::plan_grid(rays->objs.data(), rays->nobj, rays->np, dirs);
-        const size_t total = rtw::host::grid_ws(g, rays->np, dirs, nullptr, nullptr);
-        if (rays->ws_bytes < total) {
-            if (rays->ws) cudaFree(rays->ws);
-            rays->ws = nullptr;
-            rays->ws_bytes = 0;
-            cudaError_t e = cudaMalloc(&rays->ws, total);
-            if (e != cudaSuccess) return fail(RTW_ERR_NOMEM, "rtw_field: workspace of %zu bytes", total);
-            rays->ws_bytes = total;
-        }
+        rtw::host::GridPlan g;
         rtw::host::GridWs w;
-        rtw::host::grid_ws(g, rays->np, dirs, (char*)rays->ws, &w);
+        rtw::DirSet d;
+        int rc = grid_prepare(rays, dirs, &g, &w, &d, s);
+        if (rc != RTW_OK) return rc;
         const size_t ncomp = rays->st.near_r > 0.0 ? 6 : 4;
         RTW_CUDA(cudaMemsetAsync(field_out, 0,
                                  sizeof(double) * ncomp * (size_t)nout * (size_t)ndir * (size_t)rays->nobj, s));
-        rtw::DirSet d;
-        int rc = rtw::host::dirs_prepare(dirs, w, &d, s);
-        if (rc != RTW_OK) return rc;
         // the slices found for these directions and this window are kept for the next call
-        const int64_t* cw = dirs->cell_window;
-        const long long key = (ndir * 64 + rays->np) ^ (cw[0] * 7919 + cw[1] * 104729 + cw[2] * 1299709 + cw[3] * 15485863);
-        if (rays->slice_key != key) {
-            rays->slice_key = key;
-            rays->slices.clear();
-        }
         return rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, rays->nobj, rays->st, g, dirs, d,
                                          per_order, (double*)field_out, mask_out, w, 0, newton, status,
                                          newton_counter(rays->device), s, &rays->slices);
@@ -976,6 +989,81 @@ int rtw_field(const rtw_rays* rays_c, const rtw_dirs* dirs, int mode, int flags,
                                                ndir, 0, dirs->n_theta, 0, dirs->alpha0, dirs->dalpha, s));
     }
     return RTW_OK;
+}
+
+int rtw_field_caustic(const rtw_rays* rays_c, const rtw_dirs* dirs, const rtw_caustic_params* cp, int flags,
+                      void* field_out, uint8_t* mask_out, double* weights_out, void* stream)
+{
+    rtw_rays* rays = const_cast<rtw_rays*>(rays_c);
+    if (!rays || !dirs || !cp || !field_out) return fail(RTW_ERR_ARG, "rtw_field_caustic: null pointer");
+    if (rays->grid != RTW_GRID_SQUARE || rays->nobj != 1 || !rays->st.aux || rays->st.near_r != 0.0 ||
+        rays->precision != RTW_FP64)
+        return fail(RTW_ERR_ARG, "rtw_field_caustic: one object on a square grid traced in RTW_FP64 with "
+                                 "RTW_TRACE_APERTURE (far field) is required");
+    const ObjDev& o = rays->objs[0];
+    if (o.src_mode != 0 || o.shape_e != 1.0)
+        return fail(RTW_ERR_ARG, "rtw_field_caustic: an ellipsoid in a plane wave is required");
+    if (flags & ~RTW_FIELD_PER_ORDER) return fail(RTW_ERR_ARG, "rtw_field_caustic: flags 0 or RTW_FIELD_PER_ORDER");
+    if (dirs->kind != RTW_DIRS_GRID) return fail(RTW_ERR_ARG, "rtw_field_caustic: a (theta, phi) grid is required");
+    int rc = rtw::host::check_grid_dirs(dirs, false, "rtw_field_caustic");
+    if (rc != RTW_OK) return rc;
+    const int tt = cp->tile_theta ? cp->tile_theta : 16, tp = cp->tile_phi ? cp->tile_phi : 16;
+    if (tt < 1 || tp < 1 || tt * tp > 256)
+        return fail(RTW_ERR_ARG, "rtw_field_caustic: tiles of 1 to 256 directions (%d x %d)", tt, tp);
+    const double aw = std::pow(o.lambda / o.lmax, 2.0 / 3.0), fw = 1.0 / std::sqrt(o.k0 * o.lmax);
+    const bool po_default = cp->po_full == 0.0 && cp->po_end == 0.0;
+    const bool cone_default = cp->cone_full == 0.0 && cp->cone_end == 0.0;
+    const double po_full = po_default ? 1.5 * aw : cp->po_full, po_end = po_default ? 3.0 * aw : cp->po_end;
+    const double cone_full = cone_default ? 3.0 * aw + 3.0 * fw : cp->cone_full;
+    const double cone_end = cone_default ? 3.0 * aw + 6.0 * fw : cp->cone_end;
+    if (!(po_full >= 0.0 && po_end > po_full && cone_full >= 0.0 && cone_end > cone_full))
+        return fail(RTW_ERR_ARG, "rtw_field_caustic: 0 <= po_full < po_end and 0 <= cone_full < cone_end");
+    const int nt = dirs->n_theta, nph = dirs->n_phi;
+    const double rho_bound = 0.5 * (tt * kPi / nt + tp * kPi / nph);
+    if (!(rho_bound + cone_end < 0.5 * kPi))
+        return fail(RTW_ERR_ARG, "rtw_field_caustic: a tile's cone reaches pi/2 (radius bound %g + cone_end %g)",
+                    rho_bound, cone_end);
+    const int np = rays->np;
+    const int p_min = cp->p_min ? cp->p_min : 1;
+    if (p_min < 0 || p_min > np) return fail(RTW_ERR_ARG, "rtw_field_caustic: p_min %d beyond the orders", p_min);
+    const bool per_order = (flags & RTW_FIELD_PER_ORDER) != 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    rtw::host::GridPlan g;
+    rtw::host::GridWs w;
+    rtw::DirSet d;
+    rc = grid_prepare(rays, dirs, &g, &w, &d, s);
+    if (rc != RTW_OK) return rc;
+    const long long ndir = (long long)nt * nph;
+    const long long ntiles = (long long)((nt + tt - 1) / tt) * ((nph + tp - 1) / tp);
+    const long long nblocks = ((o.nx + 15) / 16) * ((o.ny + 15) / 16);
+    const size_t per_bytes = sizeof(double) * 4 * (size_t)np * (size_t)ndir;
+    const size_t sc_bytes = rtw::caustic_scratch_bytes(ndir, ntiles, nblocks);
+    // the per-order field (the caller's output with RTW_FIELD_PER_ORDER) and the correction's scratch
+    char* block = nullptr;
+    const size_t off_sc = per_order ? 0 : align_up(per_bytes, 256);
+    if (cudaMallocAsync((void**)&block, off_sc + sc_bytes, s) != cudaSuccess)
+        return fail(RTW_ERR_NOMEM, "rtw_field_caustic: scratch of %zu bytes", off_sc + sc_bytes);
+    double* per = per_order ? (double*)field_out : (double*)block;
+    void* scratch = block + off_sc;
+    auto run = [&]() -> int {
+        RTW_CUDA(cudaMemsetAsync(per, 0, per_bytes, s));
+        int r = rtw::host::grid_field_run(rays->objs.data(), rays->d_objs, 1, rays->st, g, dirs, d, true, per,
+                                          nullptr, w, 0, 0, status_word(rays->device),
+                                          newton_counter(rays->device), s, &rays->slices);
+        if (r != RTW_OK) return r;
+        if (weights_out) RTW_CUDA(cudaMemsetAsync(weights_out, 0, sizeof(double) * (size_t)np * (size_t)ndir, s));
+        for (int p = p_min; p < np; ++p)
+            RTW_CUDA(rtw::launch_caustic_order(rays->st, o, p, nt, nph, tt, tp, po_full, po_end, cone_full, cone_end,
+                                               w.mask_words, per, weights_out, scratch, s));
+        RTW_CUDA(rtw::launch_caustic_finish(w.mask_words, ndir, per, per_order ? nullptr : (double*)field_out, np, s));
+        if (mask_out)
+            RTW_CUDA(rtw::launch_finalize_mask(w.mask_words, mask_out, rays->d_objs, 1, ndir, 1, nt, nph, 0.0, 0.0, s,
+                                               nullptr));
+        return RTW_OK;
+    };
+    rc = run();
+    cudaFreeAsync(block, s);
+    return rc;
 }
 
 int rtw_newton_failures(void* stream, int64_t* count)

@@ -293,16 +293,20 @@ __device__ __forceinline__ void push_hit(const HitArgs& h, unsigned int* status,
     }
 }
 
+// caustic bits of a direction covered by a triangle of order p that is not consistent: bit 0, and bit
+// 8 + p that tells the orders apart (the caustic correction reads it; the byte mask keeps bit 0)
+__device__ __forceinline__ unsigned int caustic_bits(int p) { return kMaskCaustic | (0x100u << p); }
+
 __device__ __forceinline__ void candidate(const FieldArgs& a, const HitArgs& h, const TriFrame& fr,
-                                          unsigned long long code, unsigned int* mask, unsigned int dk, float dx0,
-                                          float dx1, float dx2)
+                                          unsigned long long code, unsigned int* mask, unsigned int cbit,
+                                          unsigned int dk, float dx0, float dx1, float dx2)
 {
     const int cls = tri_classify(fr, dx0, dx1, dx2);
     if (cls == 0) return;
     if (cls == 2) {
         push_hit(h, a.status, code, dk | kHitClose);
     } else if (!fr.ok) {  // singular or folded cell: mark, add nothing
-        if (!(mask[dk] & kMaskCaustic)) atomicOr(mask + dk, kMaskCaustic);
+        if ((mask[dk] & cbit) != cbit) atomicOr(mask + dk, cbit);
     } else {
         push_hit(h, a.status, code, dk);
     }
@@ -446,11 +450,12 @@ __device__ __forceinline__ DirTabF dir_tab_f(const double* tab, int nt, int nph)
 // every candidate direction of one (bin) grid point (it, jp): the point itself, or a bin's list
 __device__ __forceinline__ void candidates_at(const FieldArgs& a, const HitArgs& h, const DirSet& d,
                                               const DirTabF& T, const TriFrame& fr, const TriGeom& g,
-                                              unsigned long long code, unsigned int* mask, int it, int jp)
+                                              unsigned long long code, unsigned int* mask, unsigned int cbit, int it,
+                                              int jp)
 {
     if (!d.list) {
         const float sth = T.st[it];
-        candidate(a, h, fr, code, mask, (unsigned int)it * (unsigned int)d.nph + (unsigned int)jp,
+        candidate(a, h, fr, code, mask, cbit, (unsigned int)it * (unsigned int)d.nph + (unsigned int)jp,
                   sth * T.cp[jp] - g.c[0], sth * T.sp[jp] - g.c[1], T.ct[it] - g.c[2]);
         return;
     }
@@ -458,7 +463,7 @@ __device__ __forceinline__ void candidates_at(const FieldArgs& a, const HitArgs&
     for (int m = d.bin_first[bn]; m < d.bin_first[bn + 1]; ++m) {
         const unsigned int dk = (unsigned int)d.bin_dir[m];
         const float4 x = d.ldir_f[dk];
-        candidate(a, h, fr, code, mask, dk, x.x - g.c[0], x.y - g.c[1], x.z - g.c[2]);
+        candidate(a, h, fr, code, mask, cbit, dk, x.x - g.c[0], x.y - g.c[1], x.z - g.c[2]);
     }
 }
 
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch 
             for (int jj = 0; jj < g.jcount; ++jj) {
                 int jp = g.jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
+                candidates_at(a, h, d, T, fr, g, code, mask, caustic_bits(c.p), it, jp);
             }
         }
     }
@@ -511,7 +516,7 @@ struct BigRec {
     float c[3];
     int it0, it1, jp0, jcount;
     unsigned long long code;
-    int orel, valid;
+    int orel, valid;  // valid: 1 + the order of the cell, 0 for an empty entry
 };
 constexpr int kBigWarps = 8;  // warps per block of the large-triangle kernel
 
@@ -549,7 +554,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
                 mine.jcount = g.jcount;
                 mine.code = code;
                 mine.orel = c.orel;
-                mine.valid = 1;
+                mine.valid = 1 + c.p;
             }
         }
         __syncwarp();
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
             while (it <= it1) {
                 int jp = jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidates_at(a, h, d, T, fr, g, code, mask, it, jp);
+                candidates_at(a, h, d, T, fr, g, code, mask, caustic_bits(r.valid - 1), it, jp);
                 it += step_r;
                 jj += step_c;
                 if (jj >= jc) {
@@ -654,7 +659,7 @@ __global__ void __launch_bounds__(256) field_grid_hit_kernel(FieldArgs a, GridBa
                             ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
                             ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0 && sigma == ((f[0] & kFlagOrient) ? 1 : -1);
             if (!ok) {
-                atomicOr(a.mask + (long long)c.orel * b.ndir + dk, kMaskCaustic);
+                atomicOr(a.mask + (long long)c.orel * b.ndir + dk, caustic_bits(c.p));
                 continue;
             }
         }
@@ -1537,7 +1542,7 @@ __device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b,
                         ((f[0] ^ f[1]) & kFlagOrient) == 0 && ((f[1] ^ f[2]) & kFlagOrient) == 0 &&
                         ((f[0] | f[1] | f[2]) & kFlagCaustic) == 0 && sigma == ((f[0] & kFlagOrient) ? 1 : -1);
         if (!ok) {
-            atomicOr(a.mask + (long long)c.orel * b.ndir + dk, kMaskCaustic);
+            atomicOr(a.mask + (long long)c.orel * b.ndir + dk, caustic_bits(c.p));
             return;
         }
     }

@@ -152,4 +152,16 @@ cudaError_t launch_finalize_mask(const unsigned int* words, unsigned char* mask_
                                  long long ndir, int kind, int nt, int nph, double alpha0, double dalpha,
                                  cudaStream_t s, const double* list = nullptr);
 
+// 2-D physical optics at the caustics of a square-grid field (rtw_caustic.cu): scratch bytes for
+// ndir directions, ntiles tiles and nblocks 16 x 16 ray blocks; one order's correction of the
+// per-order field ([directions][np][4]) and mask words (the caustic bit of the order cleared where its
+// weight is 1, RTW_MASK_PO set where it is above 0); then bit 0 of the words from the order bits left,
+// and (out not null) the sum over the orders into out ([directions][4])
+size_t caustic_scratch_bytes(long long ndir, long long ntiles, long long nblocks);
+cudaError_t launch_caustic_order(const RaysDev& st, const ObjDev& o, int order, int nt, int nph, int tt, int tp,
+                                 double po_full, double po_end, double cone_full, double cone_end, unsigned int* words,
+                                 double* field, double* weights, void* scratch, cudaStream_t s);
+cudaError_t launch_caustic_finish(unsigned int* words, long long ndir, const double* per_order, double* out, int np,
+                                  cudaStream_t s);
+
 }  // namespace rtw

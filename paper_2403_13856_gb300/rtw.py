@@ -87,6 +87,7 @@ def lib():
             "rtw_trace_points": ([p, i, p, i64, i, p, p, p, p, p], i),
             "rtw_field": ([p, p, i, i, p, p, p], i),
             "rtw_field_po2d": ([p, p, p, i64, p, p, p], i),
+            "rtw_field_caustic": ([p, p, p, i, p, p, p, p], i),
             "rtw_far_field_batch": ([p, p, p, i, p, p, p, p], i),
             "rtw_batch_info": ([p, p, p, p], i),
             "rtw_batch_times": ([p, p, p], i),
@@ -279,6 +280,30 @@ def rtw_field_po2d(rays: Rays, pp: rtw_po2d_params, dirs, out, count=False, stre
     _check(lib().rtw_field_po2d(rays.handle, ctypes.byref(pp), _ptr(dirs), dirs.shape[0], _ptr(out),
                                 ctypes.byref(n) if count else None, _stream_ptr(stream)))
     return n.value if count else None
+
+
+class rtw_caustic_params(ctypes.Structure):
+    _fields_ = [("tile_theta", ctypes.c_int), ("tile_phi", ctypes.c_int), ("po_full", ctypes.c_double),
+                ("po_end", ctypes.c_double), ("cone_full", ctypes.c_double), ("cone_end", ctypes.c_double),
+                ("p_min", ctypes.c_int)]
+
+
+def caustic_params(tile=(0, 0), po=(0.0, 0.0), cone=(0.0, 0.0), p_min=0) -> rtw_caustic_params:
+    """Parameters of rtw_field_caustic; zeros take the library's defaults."""
+    cp = rtw_caustic_params()
+    cp.tile_theta, cp.tile_phi = int(tile[0]), int(tile[1])
+    cp.po_full, cp.po_end = float(po[0]), float(po[1])
+    cp.cone_full, cp.cone_end = float(cone[0]), float(cone[1])
+    cp.p_min = int(p_min)
+    return cp
+
+
+def rtw_field_caustic(rays: Rays, dirs: rtw_dirs, cp: rtw_caustic_params, out, mask=None, weights=None, flags=0,
+                      stream=None):
+    """Square-grid far field with the 2-D physical optics of the caustics blended in (device tensors:
+    out as rtw_field, mask (directions,) uint8, weights (directions, orders) float64)."""
+    _check(lib().rtw_field_caustic(rays.handle, ctypes.byref(dirs), ctypes.byref(cp), flags, _ptr(out), _ptr(mask),
+                                   _ptr(weights), _stream_ptr(stream)))
 
 
 def rtw_field(rays: Rays, dirs: rtw_dirs, out, mask=None, mode=RTW_DENSE, flags=0, stream=None):

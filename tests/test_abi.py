@@ -80,6 +80,7 @@ def test_null_arguments(librtw):
     assert L.rtw_field(None, None, 0, 0, None, None, None) == -1
     assert L.rtw_rays_info(None, None, None, None) == -1
     assert L.rtw_far_field_batch(None, None, None, 0, None, None, None, None) == -1
+    assert L.rtw_field_caustic(None, None, None, 0, None, None, None, None) == -1
     assert L.rtw_batch_info(None, None, None, None) == -1
     assert L.rtw_batch_times(None, None, None) == -1
     L.rtw_destroy_batch(None)
