@@ -383,6 +383,48 @@ def system_batch(torch, rtw, precision, steps=2, warmup=1):
             "launch_options": opts, "steps": steps, "warmup": warmup}
 
 
+def caustic_forms(torch, rtw, W, stream):
+    """The 2-D physical optics at the 3-D caustics (rtw_field_caustic, default widths, 16 x 16 tiles,
+    summed orders) on the drop of the headline workload and on the Fig. 3 spheroid at 0.1 deg: time of
+    the corrected field against the plain one on the same rays (traced with the aperture records), and
+    the directions masked as caustic before and after."""
+    res = {}
+    cases = (("ellipsoid_512x1024", W.ELLIPSOID, W.ELLIPSOID_GRID, 512, 1024, (1.0, 0.0),
+              "ellipsoid (120,100,80) um tilt 20 deg about x, 4e6 rays, p=0..5, 512x1024 directions"),
+             ("spheroid_1800x3600", W.SPHEROID_SIDE, W.SPHEROID_PATTERN, 1800, 3600, (0.0, 1.0),
+              "oblate spheroid a=b=100, c=90 um along its x axis, 4e6 rays, p=0..5, 1800x3600 = 0.1 deg"))
+    for name, spec, cfg, nt, nph, jv, desc in cases:
+        obj = rtw.Object([rtw.ObjectSpec(**spec, jones=jv)])
+        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=cfg["n_rays"],
+                              flags=rtw.RTW_TRACE_APERTURE)
+        rays = rtw.rtw_trace(obj, tp, stream=stream)
+        nd = nt * nph
+        d = rtw.dirs_grid(nt, nph)
+        out = torch.zeros((nd, 1, 2), dtype=torch.complex128, device="cuda")
+        m0 = torch.zeros(nd, dtype=torch.uint8, device="cuda")
+        m1 = torch.zeros(nd, dtype=torch.uint8, device="cuda")
+        cp = rtw.caustic_params()
+        rtw.rtw_field(rays, d, out, m0, stream=stream)
+        rtw.rtw_field_caustic(rays, d, cp, out, m1, stream=stream)  # warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        rtw.rtw_field(rays, d, out, m0, stream=stream)
+        ev[1].record(stream)
+        for _ in range(2):
+            rtw.rtw_field_caustic(rays, d, cp, out, m1, stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        rtw.rtw_sync_status(stream)
+        res[name] = {"workload": desc + ", FP64 trace with aperture records",
+                     "ms_field": ev[0].elapsed_time(ev[1]), "ms_field_caustic": ev[1].elapsed_time(ev[2]) / 2,
+                     "masked_caustic_before": float(((m0 & 1) != 0).float().mean().item()),
+                     "masked_caustic_after": float(((m1 & 1) != 0).float().mean().item()),
+                     "corrected_fraction": float(((m1 & 4) != 0).float().mean().item()),
+                     "note": "orders 1..5 corrected; caustic directions left after are those of order 0"}
+        del rays, out, m0, m1
+    return res
+
+
 def bench_ellipsoid(args, rank, world, local, dist):
     import torch
 
@@ -618,6 +660,8 @@ def bench_ellipsoid(args, rank, world, local, dist):
             "paper_context": "9.4 min for this pattern on an Intel i9-13900KS (CPU, ray count not stated)"}
     del r3, out3, mask3, sph3
 
+    caustics = caustic_forms(torch, rtw, W, stream)
+
     # the system forms on their own workloads: 4096 drops batched (FP64 and mixed), and the learned
     # proposal on 1024 drops against dense tracing
     systems = {}
@@ -712,6 +756,7 @@ def bench_ellipsoid(args, rank, world, local, dist):
         "superellipsoid": superellipsoid,
         "po2d_rainbow": po2d,
         "paper_fig3_pattern": fig3,
+        "caustic_po": caustics,
         "sphere_fan": sphere_fan,
     }
     line.update(systems)

@@ -113,5 +113,7 @@ def test_caustic_arguments(rtw):
     with pytest.raises(rtw.RTWError):  # windows are not taken
         rtw.rtw_field_caustic(ap, rtw.dirs_grid(nt, nph, (0, 10, 0, 10)), rtw.caustic_params(), out,
                               flags=rtw.RTW_FIELD_PER_ORDER)
-    rtw.rtw_field_caustic(ap, d, rtw.caustic_params(), out, flags=rtw.RTW_FIELD_PER_ORDER)
+    with pytest.raises(rtw.RTWError):  # 16 x 16 tiles of this coarse grid: a cone reaches pi/2
+        rtw.rtw_field_caustic(ap, d, rtw.caustic_params(), out, flags=rtw.RTW_FIELD_PER_ORDER)
+    rtw.rtw_field_caustic(ap, d, rtw.caustic_params(tile=(4, 2)), out, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_sync_status()
