@@ -134,9 +134,11 @@ struct TriGeom {
     uint32_t f[3];
     float s[3][3];    // single-precision (hi) exit directions
     float l[3][3];    //   and their lo parts
-    float th[3], ph[3];  // theta and phi of the corners' directions
+    float th[3], ph[3];  // theta and phi of the corners' directions (phi unwrapped by tri_box)
     float c[3];       // unit vector at the centre of the image triangle (local origin)
     int it0, it1, jp0, jcount;
+    float mt;         // tri_box: the theta margin of the edges' bulge; 0 for a cap (tri_setup)
+    float cth, cph, crho;  // tri_setup: the cap's centre (theta, phi) and radius
 };
 
 // the single-precision candidate cap of a triangle whose corners are loaded; returns the number of
@@ -167,6 +169,10 @@ __device__ __forceinline__ long long tri_setup(TriGeom& g, const DirSet& d)
     // a list's bins are candidates when their centre lies within the cap widened by a bin radius
     const float rho = 2.0f * asinf(fminf(1.0f, 0.5f * ch)) + 1e-5f + d.pad;
     const float thc = atan2f(sqrtf(cmx * cmx + cmy * cmy), cmz), phc = atan2f(cmy, cmx);
+    g.mt = 0.0f;
+    g.cth = thc;
+    g.cph = phc;
+    g.crho = rho;
     const float dth = 3.14159265358979f / nt, dph = 6.28318530717959f / nph;
     g.it0 = max((int)ceilf((thc - rho) / dth - 0.5f), 0);
     g.it1 = min((int)floorf((thc + rho) / dth - 0.5f), nt - 1);
@@ -395,18 +401,21 @@ __device__ __forceinline__ void load_triangle(const FieldArgs& a, long long base
 // the number of candidates (0: none).
 __device__ __forceinline__ long long tri_box(TriGeom& g, const DirSet& d)
 {
+    g.mt = 0.0f;
     if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) return 0;
     if (d.list) return tri_setup(g, d);
-    float l2 = 0.0f, cmax = 0.0f, smin = 1.0f;
+    float l2 = 0.0f, cmax = 0.0f, s2min = 1.0f;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
         const int w = (v + 1) % 3;
         const float dx = g.s[v][0] - g.s[w][0], dy = g.s[v][1] - g.s[w][1], dz = g.s[v][2] - g.s[w][2];
         l2 = fmaxf(l2, dx * dx + dy * dy + dz * dz);
-        // sin theta and |cos theta| of a unit direction
-        smin = fminf(smin, sqrtf(g.s[v][0] * g.s[v][0] + g.s[v][1] * g.s[v][1]));
+        // sin^2 theta and |cos theta| of a unit direction
+        s2min = fminf(s2min, g.s[v][0] * g.s[v][0] + g.s[v][1] * g.s[v][1]);
         cmax = fmaxf(cmax, fabsf(g.s[v][2]));
     }
+    // the margins below exceed the rounding of these approximate forms (relative 1e-6) many times
+    const float smin = s2min * rsqrtf(fmaxf(s2min, 1e-30f));
     float p0 = g.ph[0], p1 = g.ph[1], p2 = g.ph[2];
     if (fmaxf(p0, fmaxf(p1, p2)) - fminf(p0, fminf(p1, p2)) > 3.14159265f) {  // across phi = +-pi
         p0 += p0 < 0.0f ? 6.28318531f : 0.0f;
@@ -415,14 +424,20 @@ __device__ __forceinline__ long long tri_box(TriGeom& g, const DirSet& d)
     }
     const float pmin = fminf(p0, fminf(p1, p2)), pmax = fmaxf(p0, fmaxf(p1, p2));
     if (l2 > 0.25f || smin < 0.05f || pmax - pmin > 1.0f) return tri_setup(g, d);
-    const float mt = 0.5f * l2 * (cmax / smin + 1.0f) + 2e-6f, mp = 1e-5f;
+    const float mt = 0.5f * l2 * (__fdividef(cmax, smin) + 1.0f) + 2e-6f, mp = 1e-5f;
+    g.ph[0] = p0;
+    g.ph[1] = p1;
+    g.ph[2] = p2;
+    g.mt = mt;
     const float tmin = fminf(g.th[0], fminf(g.th[1], g.th[2])), tmax = fmaxf(g.th[0], fmaxf(g.th[1], g.th[2]));
     const int nt = d.nt, nph = d.nph;
-    const float dth = 3.14159265358979f / nt, dph = 6.28318530717959f / nph;
-    g.it0 = max((int)ceilf((tmin - mt) / dth - 0.5f), 0);
-    g.it1 = min((int)floorf((tmax + mt) / dth - 0.5f), nt - 1);
-    g.jp0 = (int)ceilf((pmin - mp + 3.14159265358979f) / dph - 0.5f);
-    const int jp1 = (int)floorf((pmax + mp + 3.14159265358979f) / dph - 0.5f);
+    // rows and columns by multiplication with the reciprocal spacing: the rounding, 1.5 ulp of index
+    // values up to 2 nph (0.006 of a column at 36000 columns), stays below a tenth of the margins
+    const float ith = nt * 0.318309886f, iph = nph * 0.159154943f;
+    g.it0 = max((int)ceilf((tmin - mt) * ith - 0.5f), 0);
+    g.it1 = min((int)floorf((tmax + mt) * ith - 0.5f), nt - 1);
+    g.jp0 = (int)ceilf((pmin - mp + 3.14159265358979f) * iph - 0.5f);
+    const int jp1 = (int)floorf((pmax + mp + 3.14159265358979f) * iph - 0.5f);
     g.jcount = min(max(jp1 - g.jp0 + 1, 0), nph);
     if (g.it1 < g.it0 || g.jcount <= 0) return 0;
     // the local origin of the single-precision tests
@@ -515,10 +530,92 @@ struct BigRec {
     TriFrame fr;
     float c[3];
     int it0, it1, jp0, jcount;
+    // the rows' spans: a boxed triangle's corners (theta 3, phi 3 unwrapped) and bulge margin (> 0),
+    // or a cap's centre theta, phi and radius (sp[6] = 0)
+    float sp[7];
     unsigned long long code;
     int orel, valid;  // valid: 1 + the order of the cell, 0 for an empty entry
 };
 constexpr int kBigWarps = 8;  // warps per block of the large-triangle kernel
+constexpr int kSpanMin = 128;  // boxes of more candidates take the rows' spans (big_row_span)
+
+// Candidate columns of row it of a large triangle, inside its box: [*j0, *j0 + count), unwrapped
+// (taken modulo nph).  A boxed triangle's points on the row lie, at the same phi, within its bulge
+// margin in theta of the plane triangle of its corners' (theta, phi) (the margin that widens its box),
+// so their phi lies in the phi extent of that plane triangle clipped to the strip of that half-width
+// about the row.  A cap's points on the row lie within the cap's phi half-width there,
+// cos dphi = (cos rho - cos theta cos theta_c) / (sin theta sin theta_c), taken wider by the
+// rounding of the single-precision terms.  The margins cover the rounding of the box's own bounds.
+__device__ __forceinline__ int big_row_span(const BigRec& r, int it, float dth, float dph, int nph, int* j0)
+{
+    const float tr = (it + 0.5f) * dth;
+    float pmin, pmax;
+    bool all = false;
+    if (r.sp[6] > 0.0f) {
+        const float lo = tr - r.sp[6], hi = tr + r.sp[6];
+        pmin = 1e30f;
+        pmax = -1e30f;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float t0 = r.sp[v], p0 = r.sp[3 + v];
+            if (t0 >= lo && t0 <= hi) {
+                pmin = fminf(pmin, p0);
+                pmax = fmaxf(pmax, p0);
+            }
+            const int w = v == 2 ? 0 : v + 1;
+            const float t1 = r.sp[w], p1 = r.sp[3 + w];
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float y = b ? hi : lo;
+                if ((t0 - y) * (t1 - y) < 0.0f) {
+                    const float pc = p0 + (y - t0) / (t1 - t0) * (p1 - p0);
+                    pmin = fminf(pmin, pc);
+                    pmax = fmaxf(pmax, pc);
+                }
+            }
+        }
+        if (!(pmin <= pmax)) return 0;
+    } else {
+        const float thc = r.sp[0], phc = r.sp[1], rho = r.sp[2];
+        float st, ct, sc, cc;
+        sincosf(tr, &st, &ct);
+        sincosf(thc, &sc, &cc);
+        const float den = st * sc;
+        if (den < 1e-4f) {
+            all = true;
+            pmin = pmax = 0.0f;
+        } else {
+            const float arg = (cosf(rho) - ct * cc) / den - 4e-6f / den - 1e-5f;
+            if (arg <= -1.0f) {
+                all = true;
+                pmin = pmax = 0.0f;
+            } else {
+                const float dphi = acosf(fminf(arg, 1.0f)) + 1e-4f;
+                pmin = phc - dphi;
+                pmax = phc + dphi;
+            }
+        }
+    }
+    const bool full_box = r.jcount >= nph;
+    if (all) {
+        *j0 = r.jp0;
+        return r.jcount;
+    }
+    const float mp = 2e-5f;
+    int jlo = (int)ceilf((pmin - mp + 3.14159265358979f) / dph - 0.5f);
+    int jhi = (int)floorf((pmax + mp + 3.14159265358979f) / dph - 0.5f);
+    if (full_box) {  // a box of every column: the row's span may cross the seam; modulo nph later
+        if (jhi - jlo + 1 >= nph) {
+            *j0 = 0;
+            return nph;
+        }
+    } else {
+        jlo = max(jlo, r.jp0);
+        jhi = min(jhi, r.jp0 + r.jcount - 1);
+    }
+    *j0 = jlo;
+    return jhi >= jlo ? jhi - jlo + 1 : 0;
+}
 
 __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArgs a, GridBatch b, DirSet d,
                                                                       const unsigned long long* big,
@@ -531,6 +628,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
     const long long warps = (long long)gridDim.x * kBigWarps;
     const int nph = d.nph;
     const DirTabF T = dir_tab_f(d.tab, d.nt, nph);
+    const float dth = 3.14159265358979f / d.nt, dph = 6.28318530717959f / nph;
     // lane l of warp w takes list entries w + warps (32 i + l): consecutive entries (neighbouring,
     // alike triangles) are spread over all warps
     const long long w = blockIdx.x * (long long)kBigWarps + wib;
@@ -552,6 +650,19 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
                 mine.it1 = g.it1;
                 mine.jp0 = g.jp0;
                 mine.jcount = g.jcount;
+                if (g.mt > 0.0f) {
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        mine.sp[v] = g.th[v];
+                        mine.sp[3 + v] = g.ph[v];
+                    }
+                    mine.sp[6] = g.mt;
+                } else {
+                    mine.sp[0] = g.cth;
+                    mine.sp[1] = g.cph;
+                    mine.sp[2] = g.crho;
+                    mine.sp[6] = 0.0f;
+                }
                 mine.code = code;
                 mine.orel = c.orel;
                 mine.valid = 1 + c.p;
@@ -568,18 +679,37 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
             g.c[2] = r.c[2];
             const unsigned long long code = r.code;
             unsigned int* mask = a.mask + (long long)r.orel * b.ndir;
-            // candidate q = (it - it0) jcount + jj; each lane steps q by 32 = step_r rows + step_c columns
-            const int jc = r.jcount, it1 = r.it1, jp0 = r.jp0, step_r = 32 / jc, step_c = 32 % jc;
-            int it = r.it0 + lane / jc, jj = lane % jc;
-            while (it <= it1) {
-                int jp = jp0 + jj;
-                jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidates_at(a, h, d, T, fr, g, code, mask, caustic_bits(r.valid - 1), it, jp);
-                it += step_r;
-                jj += step_c;
-                if (jj >= jc) {
-                    jj -= jc;
-                    ++it;
+            const unsigned int cbit = caustic_bits(r.valid - 1);
+            // 32 rows at a time: lane l takes the span of row r0 + l; the warp's inclusive scan of
+            // the spans numbers the candidates, and each lane finds the row of candidate q by a
+            // binary search over the scan (shuffles), the column from the row's first one
+            const bool spans = (long long)(r.it1 - r.it0 + 1) * r.jcount > kSpanMin;
+            for (int r0 = r.it0; r0 <= r.it1; r0 += 32) {
+                int j0 = r.jp0, jn = 0;
+                if (r0 + lane <= r.it1) jn = spans ? big_row_span(r, r0 + lane, dth, dph, nph, &j0) : r.jcount;
+                int incl = jn;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int q0 = 0; q0 < total; q0 += 32) {
+                    const int q = q0 + lane;
+                    int L = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
+                        if (v <= q) L += step;
+                    }
+                    const int before = __shfl_sync(0xffffffffu, incl, L > 0 ? L - 1 : 0);
+                    const int first = __shfl_sync(0xffffffffu, j0, L);
+                    if (q < total) {
+                        int jp = first + (q - (L > 0 ? before : 0));
+                        jp %= nph;
+                        jp = jp < 0 ? jp + nph : jp;
+                        candidates_at(a, h, d, T, fr, g, code, mask, cbit, r0 + L, jp);
+                    }
                 }
             }
         }
