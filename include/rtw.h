@@ -401,10 +401,19 @@ int rtw_mlp_samples(const rtw_object* obj, const double* uv, const int32_t* obj_
  * tensor cores.  X and Y must start on 16-byte boundaries (RTW_ERR_ARG otherwise).  Asynchronous; a
  * bounded wait inside the kernel that gives up is reported as RTW_ERR_TIMEOUT by rtw_sync_status. */
 int rtw_mlp_forward(const rtw_mlp* m, int order, const void* X, int64_t rows, float* Y, void* stream);
+/* The hidden activation of rtw_mlp_forward's kernel on n values (device x, y, float): its GELU (tanh
+ * form, single precision, before the kernel rounds it to bfloat16), for tests of the activation
+ * against its definition.  Errors: RTW_ERR_ARG.  Asynchronous. */
+int rtw_mlp_activation_eval(const float* x, float* y, int64_t n, void* stream);
 /* Gradient of the mean loss over the labelled rows (valid != 0) into the network's gradient
  * buffer: for each row head valid - 1 carries the squared distance to the target uv, and beta
  * times the softmax cross-entropy of the logits towards that head is added.  loss_out (device double, may be NULL)
- * receives the loss.  Deterministic (fixed summation order).  Asynchronous. */
+ * receives the loss.  The forward pass (keeping every hidden layer's pre-activations and bf16
+ * activations), the backward data pass and the weight gradients run on the tensor cores (tcgen05,
+ * bf16 operands, f32 accumulation in tensor memory).  X (rows x 16 bf16) must start on a 16-byte
+ * boundary and rows < 2^31 (RTW_ERR_ARG otherwise).  Deterministic (fixed summation order).
+ * Asynchronous; a bounded wait inside a kernel that gives up is reported as RTW_ERR_TIMEOUT by
+ * rtw_sync_status. */
 int rtw_mlp_grad(rtw_mlp* m, int order, const void* X, const float* T, const uint8_t* valid, int64_t rows, float beta,
                  double* loss_out, void* stream);
 /* Copies the gradient buffer (RTW_MLP_NPARAM floats) to grad (host or device).  Asynchronous. */

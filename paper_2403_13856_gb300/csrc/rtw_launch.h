@@ -123,14 +123,27 @@ cudaError_t launch_field_fan(const FieldArgs& a, long long nrays, double fan_phi
 // learned proposal (rtw_mlp.cu; the inference forward pass is rtw_mlp_tc.cu)
 cudaError_t mlp_prepare_kernels();
 cudaError_t mlp_prepare_tc_kernel();
+// the tensor-core inference kernel's hidden activation (GELU in single precision, before its bfloat16
+// rounding) on n values
+cudaError_t launch_activation_eval(const float* x, float* y, long long n, cudaStream_t s);
 // X (rows x 16 bf16) and Y (rows x 16 f32) 16-byte aligned; a bounded wait that gives up sets the
 // timeout bit of *status
 cudaError_t launch_mlp_forward(const MlpWeights& w, const __nv_bfloat16* X, long long rows, float* Y,
                                unsigned int* status, cudaStream_t s);
-// forward with stored activations, loss, backward and weight gradients of one batch into grad;
-// part holds ceil(rows / 512) x kMlpParams floats
+// the tensor-core training passes (rtw_mlp_tc.cu): forward with the hidden layers' Z and H kept in
+// acts (Y into acts.y); backward data pass from acts.dyb to acts.dz3, dz2, dz1; weight gradients of
+// chunks of rows into part[chunk] (returns the number of chunks, *err the launch status)
+cudaError_t launch_mlp_train_tc(const MlpWeights& w, const __nv_bfloat16* X, long long rows, const MlpActs& acts,
+                                unsigned int* status, cudaStream_t s);
+cudaError_t launch_mlp_backward_tc(const MlpWeights& w, long long rows, const MlpActs& acts, unsigned int* status,
+                                   cudaStream_t s);
+int launch_mlp_wgrad_tc(const __nv_bfloat16* X, long long rows, const MlpActs& acts, float* part, unsigned int* status,
+                        cudaStream_t s, cudaError_t* err);
+// forward with stored activations, loss, backward and weight gradients of one batch into grad, all
+// products on the tensor cores; part holds ceil(rows / 512) x kMlpParams floats; X 16-byte aligned
 cudaError_t launch_mlp_grad(const MlpWeights& w, const __nv_bfloat16* X, const float* T, const uint8_t* valid,
-                            long long rows, float beta, const MlpActs& acts, float* part, float* grad, cudaStream_t s);
+                            long long rows, float beta, const MlpActs& acts, float* part, float* grad,
+                            unsigned int* status, cudaStream_t s);
 cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* grad, int update, float lr, float b1,
                             float b2, float eps, float c1, float c2, __nv_bfloat16* w1, __nv_bfloat16* w2,
                             __nv_bfloat16* w3, __nv_bfloat16* w4, __nv_bfloat16* w2t, __nv_bfloat16* w3t,

@@ -270,18 +270,29 @@ int rtw_mlp_forward(const rtw_mlp* m, int order, const void* X, int64_t rows, fl
     return RTW_OK;
 }
 
+int rtw_mlp_activation_eval(const float* x, float* y, int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(RTW_ERR_ARG, "rtw_mlp_activation_eval: arguments");
+    RTW_CUDA(rtw::launch_activation_eval(x, y, n, (cudaStream_t)stream));
+    return RTW_OK;
+}
+
 int rtw_mlp_grad(rtw_mlp* m, int order, const void* X, const float* T, const uint8_t* valid, int64_t rows, float beta,
                  double* loss_out, void* stream)
 {
     int rc = check_order(m, order);
     if (rc != RTW_OK) return rc;
     if (rows < 1 || !X || !T || !valid) return fail(RTW_ERR_ARG, "rtw_mlp_grad: arguments");
+    if ((uintptr_t)X & 15u) return fail(RTW_ERR_ARG, "rtw_mlp_grad: X must be 16-byte aligned");
+    if (rows >= (1ll << 31)) return fail(RTW_ERR_ARG, "rtw_mlp_grad: rows < 2^31");
     rc = ensure_ws(m, rows);
     if (rc != RTW_OK) return rc;
+    unsigned int* status = rtw::host::status_word(m->device);
+    if (!status) return fail(RTW_ERR_CUDA, "rtw_mlp_grad: status word");
     cudaStream_t s = (cudaStream_t)stream;
     Net& n = m->nets[(size_t)order];
     RTW_CUDA(rtw::launch_mlp_grad(weights_of(n), (const __nv_bfloat16*)X, T, valid, rows, beta, m->acts, m->part, n.grad,
-                                  s));
+                                  status, s));
     if (loss_out) RTW_CUDA(cudaMemcpyAsync(loss_out, m->acts.scal, sizeof(double), cudaMemcpyDeviceToDevice, s));
     return RTW_OK;
 }

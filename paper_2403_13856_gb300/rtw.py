@@ -98,6 +98,7 @@ def lib():
             "rtw_mlp_set": ([p, i, p, p, p, i64], i),
             "rtw_mlp_samples": ([p, p, p, i64, i, p, p, p, p], i),
             "rtw_mlp_forward": ([p, i, p, i64, p, p], i),
+            "rtw_mlp_activation_eval": ([p, p, i64, p], i),
             "rtw_mlp_grad": ([p, i, p, p, p, i64, ctypes.c_float, p, p], i),
             "rtw_mlp_grad_get": ([p, i, p, p], i),
             "rtw_mlp_adam": ([p, i, ctypes.c_float, p, p], i),
@@ -404,6 +405,11 @@ def rtw_mlp_samples(obj: Object, uv, obj_index, p_max, X, T, valid, stream=None)
 
 def rtw_mlp_forward(mlp: MLP, order, X, Y, stream=None):
     _check(lib().rtw_mlp_forward(mlp.handle, order, _ptr(X), X.shape[0], _ptr(Y), _stream_ptr(stream)))
+
+
+def rtw_mlp_activation_eval(x, y, stream=None):
+    """The inference kernel's GELU on a float32 device tensor x into y."""
+    _check(lib().rtw_mlp_activation_eval(_ptr(x), _ptr(y), x.numel(), _stream_ptr(stream)))
 
 
 def rtw_mlp_grad(mlp: MLP, order, X, T, valid, beta=0.1, loss=None, stream=None):

@@ -105,6 +105,27 @@ def test_forward_many_tiles_matches_oracle(rtw, oracle_mod):
     assert err.max() <= FWD_MAX * scale and np.median(err) <= FWD_MEDIAN * scale
 
 
+def test_activation_gelu_matches_definition(rtw):
+    """The inference kernel's GELU (the hardware power of two and reciprocal, single precision) against
+    the tanh form in double precision, within 1e-6 (1 + |a|) relative, a the exponent of 1 + 2^a, which
+    is formed in single precision (its rounding, a few 1e-8 of |a|, becomes ln 2 |a| times as much in
+    2^a), plus 1e-30 (the far negative tail flushes to zero)."""
+    g = np.random.default_rng(7)
+    z = np.concatenate([np.linspace(-20.0, 20.0, 400001), g.standard_normal(100000) * 3.0]).astype(np.float32)
+    zd = torch.tensor(z, device="cuda")
+    out = torch.empty_like(zd)
+    rtw.rtw_mlp_activation_eval(zd, out)
+    gz = out.cpu().numpy().astype(np.float64)
+    zz = z.astype(np.float64)
+    u = np.sqrt(2.0 / np.pi) * (zz + 0.044715 * zz ** 3)
+    with np.errstate(over="ignore"):  # (1 + tanh u) / 2 = 1 / (1 + e^{-2u}), without the cancellation
+        ref = zz / (1.0 + np.exp(-2.0 * u))
+    err = np.abs(gz - ref)
+    a = np.abs(zz * (2.302208198144325 + 0.1029432395800235 * zz * zz))
+    print(f"GELU: max relative error {np.max(err / np.maximum(np.abs(ref), 1e-30)):.2e}")
+    assert np.all(err <= 1e-6 * (1.0 + a) * np.abs(ref) + 1e-30)
+
+
 def test_forward_rejects_misaligned_rows(rtw):
     """The forward pass reads rows as 16-byte vectors: an input or output 8 bytes off is refused."""
     mlp = rtw.MLP(1, seeded_params(1, 15))
