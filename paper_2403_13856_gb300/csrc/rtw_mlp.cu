@@ -31,46 +31,77 @@ __global__ void mlp_count_kernel(const uint8_t* __restrict__ valid, long long ro
 
 // loss of each row and dL/dy: the row's label names the head of its branch (label - 1, from
 // the ray's focal-line count); that head carries the squared distance, the logits a softmax
-// cross-entropy towards it; mean over the labelled rows
-__global__ void mlp_loss_kernel(const float* __restrict__ Y, const float* __restrict__ T,
-                                const uint8_t* __restrict__ valid, long long rows, float beta, MlpActs acts)
+// cross-entropy towards it; mean over the labelled rows (per-block partial sums of the loss into
+// lpart, added in a fixed order by mlp_loss_sum_kernel: the same value on every run)
+__global__ void __launch_bounds__(256) mlp_loss_kernel(const float* __restrict__ Y, const float* __restrict__ T,
+                                                       const uint8_t* __restrict__ valid, long long rows, float beta,
+                                                       MlpActs acts, double* __restrict__ lpart)
 {
+    __shared__ double red[8];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    float dy[kMlpOut];
+    double li = 0.0;  // this row's share of the loss
+    if (i < rows) {
+        float dy[kMlpOut];
 #pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) dy[k] = 0.0f;
-    if (valid[i]) {
-        const double nv = acts.scal[1];
-        const float inv = nv > 0.0 ? (float)(1.0 / nv) : 0.0f;
-        const float* y = Y + i * kMlpOut;
-        const float t0 = T[2 * i], t1 = T[2 * i + 1];
-        const int j = (valid[i] - 1) & (kMlpHeads - 1);
-        const float e0 = y[2 * j] - t0, e1 = y[2 * j + 1] - t1;
-        const float best = e0 * e0 + e1 * e1;
-        float zmax = y[8];
+        for (int k = 0; k < kMlpOut; ++k) dy[k] = 0.0f;
+        if (valid[i]) {
+            const double nv = acts.scal[1];
+            const float inv = nv > 0.0 ? (float)(1.0 / nv) : 0.0f;
+            const float* y = Y + i * kMlpOut;
+            const float t0 = T[2 * i], t1 = T[2 * i + 1];
+            const int j = (valid[i] - 1) & (kMlpHeads - 1);
+            const float e0 = y[2 * j] - t0, e1 = y[2 * j + 1] - t1;
+            const float best = e0 * e0 + e1 * e1;
+            float zmax = y[8];
 #pragma unroll
-        for (int k = 1; k < kMlpHeads; ++k) zmax = fmaxf(zmax, y[8 + k]);
-        float p[kMlpHeads], se = 0.0f;
+            for (int k = 1; k < kMlpHeads; ++k) zmax = fmaxf(zmax, y[8 + k]);
+            float p[kMlpHeads], se = 0.0f;
 #pragma unroll
-        for (int k = 0; k < kMlpHeads; ++k) {
-            p[k] = expf(y[8 + k] - zmax);
-            se += p[k];
+            for (int k = 0; k < kMlpHeads; ++k) {
+                p[k] = expf(y[8 + k] - zmax);
+                se += p[k];
+            }
+            const float ise = 1.0f / se;
+#pragma unroll
+            for (int k = 0; k < kMlpHeads; ++k) p[k] *= ise;
+            li = (double)((best - beta * logf(p[j])) * inv);
+            dy[2 * j] = 2.0f * (y[2 * j] - t0) * inv;
+            dy[2 * j + 1] = 2.0f * (y[2 * j + 1] - t1) * inv;
+#pragma unroll
+            for (int k = 0; k < kMlpHeads; ++k) dy[8 + k] = beta * (p[k] - (k == j ? 1.0f : 0.0f)) * inv;
         }
-        const float ise = 1.0f / se;
 #pragma unroll
-        for (int k = 0; k < kMlpHeads; ++k) p[k] *= ise;
-        atomicAdd(acts.scal, (double)((best - beta * logf(p[j])) * inv));
-        dy[2 * j] = 2.0f * (y[2 * j] - t0) * inv;
-        dy[2 * j + 1] = 2.0f * (y[2 * j + 1] - t1) * inv;
-#pragma unroll
-        for (int k = 0; k < kMlpHeads; ++k) dy[8 + k] = beta * (p[k] - (k == j ? 1.0f : 0.0f)) * inv;
+        for (int k = 0; k < kMlpOut; k += 2) {
+            *reinterpret_cast<float2*>(acts.dy + i * kMlpOut + k) = make_float2(dy[k], dy[k + 1]);
+            *reinterpret_cast<uint32_t*>(acts.dyb + i * kMlpOut + k) = pack_bf16(dy[k], dy[k + 1]);
+        }
     }
+    // the block's loss in a fixed order (warps, then the block), one partial per block
 #pragma unroll
-    for (int k = 0; k < kMlpOut; k += 2) {
-        *reinterpret_cast<float2*>(acts.dy + i * kMlpOut + k) = make_float2(dy[k], dy[k + 1]);
-        *reinterpret_cast<uint32_t*>(acts.dyb + i * kMlpOut + k) = pack_bf16(dy[k], dy[k + 1]);
+    for (int off = 16; off > 0; off >>= 1) li += __shfl_down_sync(0xffffffffu, li, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = li;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < 8; ++w) b += red[w];
+        lpart[blockIdx.x] = b;
     }
+}
+
+// the loss: the blocks' partials added in a fixed order (thread t takes partials t, t + 256, ...,
+// then a fixed tree over the threads): the same value on every run
+__global__ void __launch_bounds__(256) mlp_loss_sum_kernel(const double* __restrict__ lpart, int nblocks, double* scal)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) s += lpart[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[0] = red[0];
 }
 
 // grad[i] = sum over chunks of part[chunk][i], in chunk order
@@ -192,7 +223,10 @@ cudaError_t launch_mlp_grad(const MlpWeights& w, const __nv_bfloat16* X, const f
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((rows + 255) / 256);
     mlp_count_kernel<<<nb, 256, 0, s>>>(valid, rows, acts.scal);
-    mlp_loss_kernel<<<nb, 256, 0, s>>>(acts.y, T, valid, rows, beta, acts);
+    // the loss partials borrow the weight-gradient partial buffer, which is written only later
+    double* lpart = reinterpret_cast<double*>(part);
+    mlp_loss_kernel<<<nb, 256, 0, s>>>(acts.y, T, valid, rows, beta, acts, lpart);
+    mlp_loss_sum_kernel<<<1, 256, 0, s>>>(lpart, (int)nb, acts.scal);
     e = launch_mlp_backward_tc(w, rows, acts, status, s);
     if (e != cudaSuccess) return e;
     const int nchunks = launch_mlp_wgrad_tc(X, rows, acts, part, status, s, &e);

@@ -1,6 +1,7 @@
 """Small, fixed launches of the library's kernels for profilers (ncu) and quick timings.
 
     python prof_cases.py mlp_forward [--rows N]
+    python prof_cases.py mlp_train [--rows N]
     python prof_cases.py batch [--objects N]
     python prof_cases.py learned [--objects N]
     python prof_cases.py ellipsoid [--rays N]
@@ -40,7 +41,7 @@ def _timed(torch, fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["mlp_forward", "batch", "learned", "ellipsoid", "superellipsoid", "po2d",
+    ap.add_argument("case", choices=["mlp_forward", "mlp_train", "batch", "learned", "ellipsoid", "superellipsoid", "po2d",
                                      "pattern"])
     ap.add_argument("--rows", type=int, default=1 << 22)
     ap.add_argument("--objects", type=int, default=64)
@@ -70,6 +71,22 @@ def main():
         ms = _timed(torch, lambda: rtw.rtw_mlp_forward(mlp, 0, X, Y), a.reps)
         flops = 2.0 * a.rows * (16 * 128 + 2 * 128 * 128 + 128 * 16)
         print(f"mlp_forward rows={a.rows}: {ms:.3f} ms, {flops / ms / 1e9:.1f} TFLOP/s")
+    elif a.case == "mlp_train":
+        # one training step of one network: gradient (tensor-core forward, backward and weight
+        # gradients) and Adam on a batch of rows
+        mlp = rtw.MLP(1, learned.init_params(1))
+        g = np.random.default_rng(3)
+        X = torch.tensor(g.uniform(-1, 1, (a.rows, 16)), dtype=torch.float32).to(torch.bfloat16).cuda()
+        T = torch.tensor(g.uniform(-1, 1, (a.rows, 2)), dtype=torch.float32).cuda()
+        V = torch.tensor(g.integers(1, 5, a.rows), dtype=torch.uint8).cuda()
+
+        def tstep():
+            rtw.rtw_mlp_grad(mlp, 0, X, T, V)
+            rtw.rtw_mlp_adam(mlp, 0, 1e-3)
+
+        ms = _timed(torch, tstep, a.reps)
+        flops = 3 * 2.0 * a.rows * (16 * 128 + 2 * 128 * 128 + 128 * 16)
+        print(f"mlp_train rows={a.rows}: {ms:.3f} ms per step, {flops / ms / 1e9:.1f} TFLOP/s")
     elif a.case == "batch":
         specs, rays = W.batch_objects(a.objects)
         obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
