@@ -2,6 +2,7 @@
 
     python prof_cases.py mlp_forward [--rows N]
     python prof_cases.py mlp_train [--rows N]
+    python prof_cases.py caustic [--rays N]
     python prof_cases.py batch [--objects N]
     python prof_cases.py learned [--objects N]
     python prof_cases.py ellipsoid [--rays N]
@@ -41,7 +42,7 @@ def _timed(torch, fn, reps):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["mlp_forward", "mlp_train", "batch", "learned", "ellipsoid", "superellipsoid", "po2d",
+    ap.add_argument("case", choices=["mlp_forward", "mlp_train", "caustic", "batch", "learned", "ellipsoid", "superellipsoid", "po2d",
                                      "pattern"])
     ap.add_argument("--rows", type=int, default=1 << 22)
     ap.add_argument("--objects", type=int, default=64)
@@ -87,6 +88,18 @@ def main():
         ms = _timed(torch, tstep, a.reps)
         flops = 3 * 2.0 * a.rows * (16 * 128 + 2 * 128 * 128 + 128 * 16)
         print(f"mlp_train rows={a.rows}: {ms:.3f} ms per step, {flops / ms / 1e9:.1f} TFLOP/s")
+    elif a.case == "caustic":
+        # the physical optics at the caustics of the ellipsoid's 512 x 1024 field (default widths and tiles)
+        spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
+        obj = rtw.Object([rtw.ObjectSpec(**spec, jones=(1.0, 0.0))])
+        tp = rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=cfg["p_max"], n_rays=a.rays, flags=rtw.RTW_TRACE_APERTURE)
+        rays = rtw.rtw_trace(obj, tp)
+        nd = cfg["n_theta"] * cfg["n_phi"]
+        out = torch.empty((nd, 1, 2), dtype=torch.complex128, device="cuda")
+        d = rtw.dirs_grid(cfg["n_theta"], cfg["n_phi"])
+        cp = rtw.caustic_params()
+        ms = _timed(torch, lambda: rtw.rtw_field_caustic(rays, d, cp, out), a.reps)
+        print(f"caustic rays={a.rays}: field with the caustic correction {ms:.3f} ms")
     elif a.case == "batch":
         specs, rays = W.batch_objects(a.objects)
         obj = rtw.Object([rtw.ObjectSpec(**s) for s in specs])
