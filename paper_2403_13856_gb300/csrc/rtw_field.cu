@@ -669,9 +669,49 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
             }
         }
         __syncwarp();
+        // the batch's boxes of at most kSpanMin candidates as one list: lane l's triangle holds
+        // candidates [before_l, incl_l) of it (a warp scan of the box sizes); each lane finds the
+        // triangle of candidate q by a binary search over the scan (shuffles), and its row and column
+        // from the index inside the box, so that small boxes keep every lane busy
+        {
+            const BigRec& mr = rec[wib][lane];
+            const long long box = (long long)(mr.it1 - mr.it0 + 1) * mr.jcount;
+            const int cnt = (mr.valid && box <= kSpanMin) ? (int)box : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                int L = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, incl, L + step - 1);
+                    if (v <= q) L += step;
+                }
+                const int before = __shfl_sync(0xffffffffu, incl, L > 0 ? L - 1 : 0);
+                if (q < total) {
+                    const BigRec& r = rec[wib][L];
+                    const int e = q - (L > 0 ? before : 0);
+                    const int row = e / r.jcount;
+                    int jp = r.jp0 + (e - row * r.jcount);
+                    jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
+                    TriGeom g;
+                    g.c[0] = r.c[0];
+                    g.c[1] = r.c[1];
+                    g.c[2] = r.c[2];
+                    candidates_at(a, h, d, T, r.fr, g, r.code, a.mask + (long long)r.orel * b.ndir,
+                                  caustic_bits(r.valid - 1), r.it0 + row, jp);
+                }
+            }
+        }
+        // the boxes of more candidates one by one, their rows' spans taken
         for (int k = 0; k < 32; ++k) {
             const BigRec& r = rec[wib][k];
-            if (!r.valid) continue;
+            if (!r.valid || (long long)(r.it1 - r.it0 + 1) * r.jcount <= kSpanMin) continue;
             const TriFrame fr = r.fr;
             TriGeom g;
             g.c[0] = r.c[0];
@@ -683,10 +723,9 @@ __global__ void __launch_bounds__(32 * kBigWarps) field_grid_big_kernel(FieldArg
             // 32 rows at a time: lane l takes the span of row r0 + l; the warp's inclusive scan of
             // the spans numbers the candidates, and each lane finds the row of candidate q by a
             // binary search over the scan (shuffles), the column from the row's first one
-            const bool spans = (long long)(r.it1 - r.it0 + 1) * r.jcount > kSpanMin;
             for (int r0 = r.it0; r0 <= r.it1; r0 += 32) {
                 int j0 = r.jp0, jn = 0;
-                if (r0 + lane <= r.it1) jn = spans ? big_row_span(r, r0 + lane, dth, dph, nph, &j0) : r.jcount;
+                if (r0 + lane <= r.it1) jn = big_row_span(r, r0 + lane, dth, dph, nph, &j0);
                 int incl = jn;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
