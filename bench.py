@@ -383,6 +383,33 @@ def system_batch(torch, rtw, precision, steps=2, warmup=1):
             "launch_options": opts, "steps": steps, "warmup": warmup}
 
 
+def precision_errors(torch, rtw, ref_rays, rays, dirs, ndir, p_max):
+    """Per-order errors of a field summed from rays traced in another precision against the FP64 one
+    on the same directions: over the directions unmasked in both where the FP64 field of that order
+    is at least 1e-3 of its largest, the largest relative amplitude error | |F| - |F_64| | / |F_64|
+    and phase error |arg(F . conj(F_64))| (rad)."""
+    outs = []
+    for r in (ref_rays, rays):
+        o = torch.zeros((ndir, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+        m = torch.zeros(ndir, dtype=torch.uint8, device="cuda")
+        rtw.rtw_field(r, dirs, o, m, flags=rtw.RTW_FIELD_PER_ORDER)
+        outs.append((o, m))
+    torch.cuda.synchronize()
+    (f64, m64), (fx, mx) = outs
+    ok = (m64 == 0) & (mx == 0)
+    res = []
+    for p in range(p_max + 1):
+        a = f64[:, p].abs().pow(2).sum(-1).sqrt()
+        keep = ok & (a >= 1e-3 * a.max())
+        b = fx[:, p].abs().pow(2).sum(-1).sqrt()
+        rel = ((b - a).abs() / a)[keep]
+        ph = torch.angle((fx[:, p] * f64[:, p].conj()).sum(-1))[keep].abs()
+        res.append({"order": p, "directions": int(keep.sum().item()),
+                    "max_rel_amplitude": float(rel.max().item()) if rel.numel() else None,
+                    "max_phase_rad": float(ph.max().item()) if ph.numel() else None})
+    return res
+
+
 def caustic_forms(torch, rtw, W, stream):
     """The 2-D physical optics at the 3-D caustics (rtw_field_caustic, default widths, 16 x 16 tiles,
     summed orders) on the drop of the headline workload and on the Fig. 3 spheroid at 0.1 deg: time of
@@ -505,6 +532,8 @@ def bench_ellipsoid(args, rank, world, local, dist):
         tt = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
         ts = statistics.median([e[0].elapsed_time(e[2]) for e in ev])
         forms[name] = {"value": units / (ts / 1e3), "ms_per_step": ts, "ms_trace": tt}
+        if name == "mixed":
+            forms[name]["errors_per_order"] = precision_errors(torch, rtw, rays, rf, dirs, ndir, p_max)
         del rf
     rtw.rtw_sync_status(stream)
 

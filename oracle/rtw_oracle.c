@@ -603,11 +603,15 @@ static void far_field(const or_object* o, const wave_t* w, const double rexit[3]
                       double dlegs, int nf_legs, double cosprod, int nrefl, double* rec)
 {
     double detQ = det2(w->Q);
-    if (!(fabs(detQ) > 0.0) || !isfinite(detQ)) return;
+    if (!isfinite(detQ)) return;
+    /* an exit wave flat in a principal direction (det Q' = 0, where a stretch of surface has no
+     * curvature) sends its energy into a single direction: a caustic at infinity, kept as a valid
+     * ray with the caustic flag and no amplitude (its cells mask the directions they cover) */
+    const int flat = !(fabs(detQ) > 0.0);
     /* last leg to infinity: kappa_GM / kappa'_G(p+1) -> 1/(r^2 det Q'); r^2 is removed */
     int nf = nf_legs + neg_eigs(w->Q);
-    double D = dlegs / fabs(detQ);
-    cplx ph = minus_i_pow(nf) * sqrt(D);
+    double D = flat ? INFINITY : dlegs / fabs(detQ);
+    cplx ph = flat ? 0.0 : minus_i_pow(nf) * sqrt(D);
     for (int c = 0; c < 3; ++c) {
         cplx Fc = ph * (w->E[0] * w->u[0][c] + w->E[1] * w->u[1][c]);
         rec[OR_F + 2 * c] = creal(Fc);
@@ -648,7 +652,7 @@ static void far_field(const or_object* o, const wave_t* w, const double rexit[3]
     double e2 = creal(w->E[0] * conj(w->E[0]) + w->E[1] * conj(w->E[1]));
     rec[OR_POWER] = e2 * cosprod;
     rec[OR_COSPROD] = cosprod;
-    rec[OR_CAUSTIC] = rec[OR_DGEO] > or_caustic_cap(o) ? 1.0 : 0.0;
+    rec[OR_CAUSTIC] = (flat || rec[OR_DGEO] > or_caustic_cap(o)) ? 1.0 : 0.0;
 }
 
 /* Record of the same ray at the point M where it crosses the sphere |M| = R (Eqs. IntVCRM,

@@ -64,9 +64,13 @@ __device__ __forceinline__ void symv(const double* W, double x, double y, double
 __device__ __forceinline__ bool far_record(const ObjDev& o, const ExitWave& w, FarRecord& fr)
 {
     double detQ = w.q11 * w.q22 - w.q12 * w.q12;
-    if (!(fabs(detQ) > 0.0) || !isfinite(detQ)) return false;
+    if (!isfinite(detQ)) return false;
+    // an exit wave flat in a principal direction (det Q' = 0, where a stretch of surface has no
+    // curvature) sends its energy into a single direction: a caustic at infinity, kept as a valid
+    // ray with the caustic flag and no amplitude
+    const bool flat = !(fabs(detQ) > 0.0);
     int nf = w.nf_legs + neg_eigs_sym(w.q11, w.q12, w.q22);
-    double amp = rsqrt(fabs(detQ) * w.pdet);
+    double amp = flat ? 0.0 : rsqrt(fabs(detQ) * w.pdet);
     double D = amp * amp;
     double pr = 1.0, pi = 0.0;  // (-i)^nf
     switch (nf & 3) {
@@ -94,7 +98,7 @@ __device__ __forceinline__ bool far_record(const ObjDev& o, const ExitWave& w, F
     // v1 x v2 = ep x (ep x s) = -s
     int orient = (detQ > 0.0 ? 1 : -1) * w.sT * -1;
     // caustic when dA/dOmega = D / cosprod exceeds the cap
-    uint32_t f = kFlagValid | (orient > 0 ? kFlagOrient : 0u) | (D > o.cap * w.cosprod ? kFlagCaustic : 0u);
+    uint32_t f = kFlagValid | (orient > 0 ? kFlagOrient : 0u) | ((flat || D > o.cap * w.cosprod) ? kFlagCaustic : 0u);
     f |= (uint32_t)(nf > 255 ? 255 : nf) << 8;
     fr.flags = f;
     return true;
