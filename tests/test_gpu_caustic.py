@@ -117,3 +117,58 @@ def test_caustic_arguments(rtw):
         rtw.rtw_field_caustic(ap, d, rtw.caustic_params(), out, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_field_caustic(ap, d, rtw.caustic_params(tile=(4, 2)), out, flags=rtw.RTW_FIELD_PER_ORDER)
     rtw.rtw_sync_status()
+
+
+def test_caustic_full_size_blend(rtw):
+    """The ellipsoid workload at full size (4e6 rays, orders 0..5, 512 x 1024 directions, default
+    widths and tiles, as the benchmark times it), checked by properties that hold at any size: the
+    field of every order is (1 - s) F_rays + s F_PO with F_rays the plain field (rtw_field) and F_PO
+    the field of a call whose widths give every direction s = 1 (the same tiles and cones), within
+    the single-precision terms' 1e-6 of the largest component; s lies in [0, 1]; the caustic bit is
+    left only where order 0 (not corrected) put it."""
+    import math
+
+    from paper_2403_13856_gb300 import workloads as W
+
+    spec, cfg = W.ELLIPSOID, W.ELLIPSOID_GRID
+    p_max, nt, nph = cfg["p_max"], cfg["n_theta"], cfg["n_phi"]
+    nd = nt * nph
+    g = rtw.Object([rtw.ObjectSpec(**spec, jones=(1.0, 0.0))])
+    rays = rtw.rtw_trace(g, rtw.trace_params(grid=rtw.RTW_GRID_SQUARE, p_max=p_max, n_rays=cfg["n_rays"],
+                                             flags=rtw.RTW_TRACE_APERTURE))
+    d = rtw.dirs_grid(nt, nph)
+    per = rtw.RTW_FIELD_PER_ORDER
+    plain = torch.zeros((nd, p_max + 1, 2), dtype=torch.complex128, device="cuda")
+    pm = torch.zeros(nd, dtype=torch.uint8, device="cuda")
+    rtw.rtw_field(rays, d, plain, pm, flags=per)
+    blend = torch.zeros_like(plain)
+    bm = torch.zeros_like(pm)
+    w = torch.zeros((nd, p_max + 1), dtype=torch.float64, device="cuda")
+    rtw.rtw_field_caustic(rays, d, rtw.caustic_params(), blend, bm, w, flags=per)
+    L = max(spec["a"], spec["b"], spec["c"])
+    aw = (spec["wavelength"] / L) ** (2.0 / 3.0)
+    fw = 1.0 / math.sqrt(2.0 * math.pi / spec["wavelength"] * L)
+    full = rtw.caustic_params(po=(3.5, 3.6), cone=(3 * aw + 3 * fw, 3 * aw + 6 * fw))
+    po = torch.zeros_like(plain)
+    w1 = torch.zeros_like(w)
+    rtw.rtw_field_caustic(rays, d, full, po, None, w1, flags=per)
+    rtw.rtw_sync_status()
+    corrected = (w > 0).any(0)  # the orders with caustic directions
+    assert bool(corrected[1:].any()) and not bool(corrected[0])
+    for p in range(1, p_max + 1):
+        if corrected[p]:
+            assert bool((w1[:, p] == 1.0).all())
+    assert bool((w >= 0).all()) and bool((w <= 1).all())
+    s = w[..., None]
+    want = (1.0 - s) * plain + s * po
+    want[:, ~corrected] = plain[:, ~corrected]
+    scale = plain.abs().max().item()
+    err = (blend - want).abs().max().item()
+    print(f"full size: corrected (direction, order) pairs {int((w > 0).sum().item())}, "
+          f"max |blend - (1 - s) F_rays - s F_PO| / max |F| = {err / scale:.2e}")
+    assert err <= 1e-6 * scale
+    # masks: the PO bit where a weight is positive; the caustic bit only where the plain field had
+    # it and no corrected order removed it (order 0 keeps its own)
+    assert bool(((bm & 4) != 0).eq((w > 0).any(1)).all())
+    assert bool((((bm & 1) != 0) <= ((pm & 1) != 0)).all())
+    assert ((bm & 1) != 0).float().mean().item() < ((pm & 1) != 0).float().mean().item()
