@@ -387,11 +387,7 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
     size_t off_cnt = align_up(off_big + 8 * (size_t)big_cap, 256);
     size_t off_hit_tri = align_up(off_cnt + 256, 256);
     size_t off_hit_dir = align_up(off_hit_tri + 8 * (size_t)hit_cap, 256);
-    // the sort of the hits by output tile: at most np slots per object
-    const long long ntiles = field_tiles(g.group, np, list, nt, nph, ndir);
-    size_t off_tile = align_up(off_hit_dir + 4 * (size_t)hit_cap, 256);
-    size_t off_perm = align_up(off_tile + 4 * (size_t)tile_words(ntiles), 256);
-    size_t total = align_up(off_perm + 4 * (size_t)hit_cap, 256);
+    size_t total = align_up(off_hit_dir + 4 * (size_t)hit_cap, 256);
     if (base && w) {
         w->mask_words = (unsigned int*)(base + off_mask);
         w->tab = (double*)(base + off_tab);
@@ -410,8 +406,6 @@ size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, Grid
         w->hit_dir = (unsigned int*)(base + off_hit_dir);
         w->big_cap = big_cap;
         w->hit_cap = hit_cap;
-        w->tile_ws = (unsigned int*)(base + off_tile);
-        w->perm = (unsigned int*)(base + off_perm);
     }
     return total;
 }
@@ -444,7 +438,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                    const GridWs& w, int classify_block, int newton, unsigned int* status, unsigned long long* nfail,
                    cudaStream_t s, std::vector<std::pair<long long, long long>>* slices)
 {
-    const bool tiled = !newton && st.fmax && st.frec && st.fval && w.tile_ws && w.perm;
+    const bool fixed = !newton && st.fmax && st.frec && st.fval;
     const int np = st.np;
     const long long ndir = d.ndir;
     const int nout = per_order ? np : 1;
@@ -484,13 +478,13 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
             b.nout = nout;
             return RTW_OK;
         };
-        const unsigned int* fmax = tiled ? st.fmax + g0 : nullptr;
+        const unsigned int* fmax = fixed ? st.fmax + g0 : nullptr;
         if (!g.sliced) {
             GridBatch b;
             int rc = batch(g.windowed, win, b);
             if (rc != RTW_OK) return rc;
             RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
-                                       classify_block, newton, s, kFieldAll, fmax, w.tile_ws, w.perm));
+                                       classify_block, newton, s, kFieldAll, fmax));
         } else {
             long long rows = 0, cols = 0;
             for (int oi = g0; oi < g0 + gn; ++oi) {
@@ -534,7 +528,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                     continue;
                 }
                 RTW_CUDA(launch_field_grid(a, b, d, w.big, w.nbig, w.big_cap, w.hit_tri, w.hit_dir, w.nhit, w.hit_cap,
-                                           classify_block, newton, s, kFieldSum, fmax, w.tile_ws, w.perm));
+                                           classify_block, newton, s, kFieldSum, fmax));
                 fitted.push_back(sl);
             }
             if (slices) {
@@ -542,7 +536,7 @@ int grid_field_run(const ObjDev* h_objs, const ObjDev* d_objs, int nobj, const R
                 *slices = fitted;
             }
         }
-        if (tiled) RTW_CUDA(launch_field_convert(a.out, (long long)out_obj, gn, fmax, s));
+        if (fixed) RTW_CUDA(launch_field_convert(a.out, (long long)out_obj, gn, fmax, s));
         if (mask_out)
             RTW_CUDA(launch_finalize_mask(w.mask_words, mask_out + (size_t)g0 * (size_t)ndir, d_objs + g0, gn, ndir,
                                           d.list ? 2 : 1, d.nt, d.nph, 0.0, 0.0, s, d.lsrc));

@@ -121,12 +121,13 @@ __global__ void dir_tables_kernel(int nt, int nph, double* tab)
 }
 
 // ---------------------------------------------------------------------------------------------
-// square grid.  Phase 1: one thread per (order, cell); a triangle whose candidate cap holds few
-// grid directions is finished in place, a larger one (rim rays near grazing incidence map onto
-// wide image triangles) goes to a list.  Phase 2: one warp per listed triangle, the lanes taking
-// its candidate directions in turn, so that no thread serialises thousands of tests.
+// square grid.  Phase 1: one thread per (order, cell) boxes the cell's two triangles; a triangle
+// whose candidate box holds few grid directions is queued in the block and finished there by one
+// thread, a larger one (rim rays near grazing incidence map onto wide image triangles) goes to a
+// list.  Phase 2: the listed triangles a warp at a time, the lanes taking their candidate directions
+// in turn, so that no thread serialises thousands of tests.  Phase 3: the hits summed.
 // ---------------------------------------------------------------------------------------------
-constexpr int kInlineCandidates = 16;  // measured best of 2..64 on the ellipsoid workload (1e6, 4e6 rays)
+constexpr int kInlineCandidates = 32;  // measured best of 4..64 with the block queue (ellipsoid, spheroid)
 constexpr unsigned int kHitClose = 0x80000000u;  // hit entry flag: needs the double-precision test
 
 struct TriGeom {
@@ -460,8 +461,6 @@ __device__ __forceinline__ DirTabF dir_tab_f(const double* tab, int nt, int nph)
     return DirTabF{f, f + nt, f + 2 * nt, f + 2 * nt + nph};
 }
 
-// Phase 1: one thread per (object, order, cell).  Triangles with few candidates are tested here;
-// larger ones go to the big list (one warp each in phase 2).
 // every candidate direction of one (bin) grid point (it, jp): the point itself, or a bin's list
 __device__ __forceinline__ void candidates_at(const FieldArgs& a, const HitArgs& h, const DirSet& d,
                                               const DirTabF& T, const TriFrame& fr, const TriGeom& g,
@@ -482,40 +481,73 @@ __device__ __forceinline__ void candidates_at(const FieldArgs& a, const HitArgs&
     }
 }
 
-__global__ void __launch_bounds__(256) field_grid_kernel(FieldArgs a, GridBatch b, DirSet d, unsigned long long* big,
-                                                         unsigned int* nbig, unsigned int big_cap, HitArgs h)
+// Triangles with at most kInlineCandidates candidates are queued in shared memory by the first pass and taken
+// one per thread by the second, so that the few threads whose triangles hold candidates (about one
+// triangle in ten on dense ray grids) work in full warps instead of a few lanes of every warp.
+constexpr int kClassifyMaxThreads = 256;
+
+__global__ void __launch_bounds__(kClassifyMaxThreads) field_grid_kernel(FieldArgs a, GridBatch b, DirSet d,
+                                                                         unsigned long long* big, unsigned int* nbig,
+                                                                         unsigned int big_cap, HitArgs h)
 {
+    __shared__ unsigned long long queue[2 * kClassifyMaxThreads];
+    __shared__ unsigned int nqueue;
+    if (threadIdx.x == 0) nqueue = 0u;
+    __syncthreads();
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= b.total) return;
-    const CellRef c = decode_cell(a, b, tid);
-    unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
+    const int lane = threadIdx.x & 31;
+    if (tid < b.total) {
+        const CellRef c = decode_cell(a, b, tid);
+        for (int t = 0; t < 2; ++t) {
+            TriGeom g;
+            cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
+            if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) continue;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) load_corner_hi(a, c.base + g.id[v], g, v);
+            const long long nc = tri_box(g, d);
+            if (nc == 0) continue;
+            const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
+            if (nc > kInlineCandidates) {
+                // warp-aggregated append to the list of the large-triangle kernel
+                const unsigned int m = __activemask();
+                const int leader = __ffs(m) - 1;
+                unsigned int slot = 0;
+                if (lane == leader) slot = atomicAdd(nbig, (unsigned int)__popc(m));
+                slot = __shfl_sync(m, slot, leader) + __popc(m & ((1u << lane) - 1u));
+                if (slot < big_cap) {
+                    big[slot] = code;
+                    continue;
+                }
+            }
+            // the block's queue (two entries per thread at most: it cannot overflow)
+            const unsigned int m = __activemask();
+            const int leader = __ffs(m) - 1;
+            unsigned int slot = 0;
+            if (lane == leader) slot = atomicAdd(&nqueue, (unsigned int)__popc(m));
+            slot = __shfl_sync(m, slot, leader) + __popc(m & ((1u << lane) - 1u));
+            queue[slot] = code;
+        }
+    }
+    __syncthreads();
+    const unsigned int nq = nqueue;
     const int nph = d.nph;
     const DirTabF T = dir_tab_f(d.tab, d.nt, nph);
-    for (int t = 0; t < 2; ++t) {
+    for (unsigned int e = threadIdx.x; e < nq; e += blockDim.x) {
+        // the triangle again (its corners are in this SM's cache), its candidate box and edge frame
+        const unsigned long long code = queue[e];
+        const CellRef c = decode_cell(a, b, (long long)(code >> 1));
         TriGeom g;
-        cell_triangle(a, c.base, c.nx, c.cx, c.cy, t, g);
-        if (!(g.f[0] & g.f[1] & g.f[2] & kFlagValid)) continue;
-#pragma unroll
-        for (int v = 0; v < 3; ++v) load_corner_hi(a, c.base + g.id[v], g, v);
-        const long long nc = tri_box(g, d);
-        if (nc == 0) continue;
-        const unsigned long long code = ((unsigned long long)tid << 1) | (unsigned long long)t;
-        if (nc > kInlineCandidates) {
-            const unsigned int slot = atomicAdd(nbig, 1u);
-            if (slot < big_cap) {
-                big[slot] = code;
-                continue;
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < 3; ++v) load_corner_lo(a, c.base + g.id[v], g, v);
+        load_triangle(a, c.base, c.nx, c.cx, c.cy, (int)(code & 1ull), g);
+        tri_box(g, d);
         TriFrame fr;
         tri_frame(g, fr);
+        unsigned int* mask = a.mask + (long long)c.orel * b.ndir;
+        const unsigned int cbit = caustic_bits(c.p);
         for (int it = g.it0; it <= g.it1; ++it) {
             for (int jj = 0; jj < g.jcount; ++jj) {
                 int jp = g.jp0 + jj;
                 jp = jp >= nph ? jp - nph : (jp < 0 ? jp + nph : jp);
-                candidates_at(a, h, d, T, fr, g, code, mask, caustic_bits(c.p), it, jp);
+                candidates_at(a, h, d, T, fr, g, code, mask, cbit, it, jp);
             }
         }
     }
@@ -1388,155 +1420,23 @@ __global__ void list_fill_kernel(const int* __restrict__ binid, long long n, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// square grid: summing the hits.  The hits of the classification are sorted by tile of the output
-// (kTileTh x kTileTw grid directions, or kTileDirs consecutive directions of a list, of one object
-// and output slot): a counting pass, an exclusive scan of the counts and a filling pass write the
-// hit indices in tile order.  A CTA then takes a run of sorted hits: each hit is decided and
-// interpolated, and its contribution F e^{i Psi} is added in shared memory as a 64-bit fixed-point
-// number; the tile's words go out once (an integer add per non-zero word, since a long tile may
-// span CTAs), and a last pass turns them into doubles.  Integer sums do not depend on their order,
-// so the field is the same bit for bit from run to run.  On GB300 the double-precision pipe (which
-// also converts between precisions) issues 1.6 operations per clock per SM, against 128 for single
-// precision: the edge planes of a hit are double-float (pairs of floats, error-free products and
-// sums), F is interpolated in single precision from corner values narrowed in the integer pipe
-// (f64_to_f32_int), and double precision is kept for the phase (about ten operations per hit).
+// square grid: summing the hits.  One thread per hit, in the order of the hit list (the order of the
+// classified cells on the ray grid, so that neighbouring hits share corner records in the caches):
+// the hit is decided and interpolated, and its contribution F e^{i Psi} is added to its direction's
+// words as 64-bit fixed-point numbers by integer atomics; a last pass turns the words into doubles.
+// Integer sums do not depend on their order, so the field is the same bit for bit from run to run.
+// (Sorting the hits by tile of 8 x 16 directions and summing each tile in shared memory gives the
+// same words and took 0.42 ms longer on the 4e6-ray ellipsoid: the sort's passes cost more than the
+// atomics they save, and the tile order scatters the corner reads.)  On GB300 the double-precision
+// pipe (which also converts between precisions) issues 1.6 operations per clock per SM, against 128
+// for single precision: the edge planes of a hit are double-float (pairs of floats, error-free
+// products and sums), F is interpolated in single precision from corner values narrowed in the
+// integer pipe (f64_to_f32_int), and double precision is kept for the phase (about ten operations
+// per hit).
 // ---------------------------------------------------------------------------------------------
-constexpr int kTileTh = 8, kTileTw = 16, kTileDirs = kTileTh * kTileTw;
-constexpr int kSumThreads = 256, kSumChunk = 1024;  // hits per CTA of the summing pass
 // fixed point: a value v with |v| < 2^eB (eB the bound of the object's |F|) is stored as
 // round(v 2^(46 - eB)); 2^16 such values add without leaving the 63-bit range
 constexpr int kFixBits = 46;
-
-struct TileGrid {
-    int ntr, ntc;             // tile rows and columns of one slot (a list: one row)
-    int nslots;               // output slots per object (orders, or 1)
-    long long ntiles;         // objects x slots x ntr x ntc of the launch
-    unsigned int* offs;       // ntiles + 1: counts, then their exclusive scan
-    unsigned int* cursor;     // ntiles + 1
-    unsigned int* bsum;       // block sums of the scan
-    unsigned int* perm;       // hit indices in tile order (hit list capacity)
-    const unsigned int* fmax; // per object of the launch: bits of the largest |F|^2
-};
-
-// tile of hit (code, direction dk) and the direction's place in it
-__device__ __forceinline__ long long hit_tile(const FieldArgs& a, const GridBatch& b, const DirSet& d,
-                                              const TileGrid& tg, unsigned long long code, unsigned int dk, int& q)
-{
-    const CellRef c = decode_cell(a, b, (long long)(code >> 1));
-    const int slot = a.per_order ? c.p : 0;
-    int tr, tc;
-    if (d.list) {
-        tr = 0;
-        tc = (int)(dk / (unsigned int)kTileDirs);
-        q = (int)(dk - (unsigned int)tc * kTileDirs);
-    } else {
-        const int it = (int)(dk / (unsigned int)d.nph), jp = (int)(dk - (unsigned int)it * d.nph);
-        tr = it / kTileTh;
-        tc = jp / kTileTw;
-        q = (it - tr * kTileTh) * kTileTw + (jp - tc * kTileTw);
-    }
-    return ((long long)c.orel * tg.nslots + slot) * tg.ntr * tg.ntc + (long long)tr * tg.ntc + tc;
-}
-
-// Counting (fill 0) or filling pass (fill 1) over the hit list, a warp's hits of one tile counted
-// or placed together.  The tile of a hit is integer arithmetic, so both passes agree; the fill
-// still stays inside each tile's range.
-__global__ void __launch_bounds__(256) hit_bin_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h, TileGrid tg,
-                                                      int fill)
-{
-    const unsigned int n = min(*h.n, h.cap);
-    const int lane = threadIdx.x & 31;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int q;
-        const long long tile = hit_tile(a, b, d, tg, h.tri[i], h.dir[i] & ~kHitClose, q);
-        const unsigned int act = __activemask();
-        const unsigned int peers = __match_any_sync(act, (unsigned long long)tile);
-        const int leader = __ffs(peers) - 1;
-        if (!fill) {
-            if (lane == leader) atomicAdd(tg.offs + tile, (unsigned int)__popc(peers));
-        } else {
-            unsigned int base = 0;
-            if (lane == leader) base = atomicAdd(tg.cursor + tile, (unsigned int)__popc(peers));
-            base = __shfl_sync(peers, base, leader);
-            const unsigned int pos = tg.offs[tile] + base + __popc(peers & ((1u << lane) - 1u));
-            if (pos < tg.offs[tile + 1]) tg.perm[pos] = (unsigned int)i;
-        }
-    }
-}
-
-// exclusive scan of n words in place: blocks of kScanTile words, then the block sums, then the
-// offsets added back
-constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
-
-__device__ __forceinline__ unsigned int block_exclusive_scan(unsigned int x, unsigned int* warp_sums,
-                                                             unsigned int& total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned int incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_sums[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        unsigned int v = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        warp_sums[lane] = v;  // inclusive over warps
-    }
-    __syncthreads();
-    total = warp_sums[(blockDim.x >> 5) - 1];
-    const unsigned int before = w > 0 ? warp_sums[w - 1] : 0u;
-    __syncthreads();
-    return before + incl - x;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(unsigned int* v, long long n, unsigned int* bsum)
-{
-    __shared__ unsigned int ws[32];
-    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
-    unsigned int x[kScanPer], s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        x[k] = base + k < n ? v[base + k] : 0u;
-        s += x[k];
-    }
-    unsigned int total;
-    unsigned int run = block_exclusive_scan(s, ws, total);
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        if (base + k < n) v[base + k] = run;
-        run += x[k];
-    }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(unsigned int* bsum, int nb)
-{
-    __shared__ unsigned int ws[32];
-    const int per = (nb + kScanThreads - 1) / kScanThreads;
-    const int i0 = threadIdx.x * per;
-    unsigned int s = 0;
-    for (int k = 0; k < per && i0 + k < nb; ++k) s += bsum[i0 + k];
-    unsigned int total;
-    unsigned int run = block_exclusive_scan(s, ws, total);
-    for (int k = 0; k < per && i0 + k < nb; ++k) {
-        const unsigned int x = bsum[i0 + k];
-        bsum[i0 + k] = run;
-        run += x;
-    }
-}
-
-__global__ void scan_add_kernel(unsigned int* v, long long n, const unsigned int* bsum)
-{
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) v[i] += bsum[i / kScanTile];
-}
 
 // ---- double-float pieces ----
 struct F2 {
@@ -1609,11 +1509,10 @@ __device__ __forceinline__ int fix_exponent(const unsigned int* fmax, int orel)
 }
 
 // One hit: the exact test of a close call, the weights, F and Psi interpolated, F e^{i Psi} added to
-// the kNc words of acc (the tile's direction q); a singular cell marks the direction instead.
+// the kNc fixed-point words at dst (scale 2^kfix); a singular cell marks the direction instead.
 template <int kNc>
-__device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b, const DirSet& d, const float* lt,
-                                         unsigned long long code, unsigned int dw, int kfix, unsigned long long* acc,
-                                         int q)
+__device__ __forceinline__ void sum_hit(const FieldArgs& a, const GridBatch& b, const DirSet& d, const float* lt,
+                                        unsigned long long code, unsigned int dw, int kfix, unsigned long long* dst)
 {
     const bool close = (dw & kHitClose) != 0;
     const unsigned int dk = dw & ~kHitClose;
@@ -1759,7 +1658,6 @@ __device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b,
             ri += im * xh[k];
         }
     }
-    unsigned long long* dst = acc + q * kNc;
     if constexpr (kNc == 6) {
         atomicAdd(dst + 0, to_fixed(rr, kfix));
         atomicAdd(dst + 1, to_fixed(ri, kfix));
@@ -1771,66 +1669,21 @@ __device__ __forceinline__ void tile_hit(const FieldArgs& a, const GridBatch& b,
     atomicAdd(dst + 3, to_fixed(pi, kfix));
 }
 
+// The hits of the list, a thread each, added to their directions' fixed-point words.
 template <int kNc>
-__global__ void __launch_bounds__(kSumThreads, 2) tile_sum_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h,
-                                                                  TileGrid tg)
+__global__ void __launch_bounds__(256, 3) hit_sum_kernel(FieldArgs a, GridBatch b, DirSet d, HitArgs h,
+                                                         const unsigned int* fmax)
 {
-    __shared__ unsigned long long acc[kTileDirs * kNc];
     const unsigned int n = min(*h.n, h.cap);
-    const unsigned int e_begin = blockIdx.x * (unsigned int)kSumChunk;
-    if (e_begin >= n) return;
-    const unsigned int e_end = min(n, e_begin + (unsigned int)kSumChunk);
     const float* lt = reinterpret_cast<const float*>(d.tab + 2 * (d.nt + d.nph)) + 2 * (d.nt + d.nph);
-    // tile of the first hit: the last tile whose offset is at most e_begin
-    long long lo = 0, hi = tg.ntiles - 1;
-    while (lo < hi) {
-        const long long mid = (lo + hi + 1) >> 1;
-        if (tg.offs[mid] <= e_begin) lo = mid;
-        else hi = mid - 1;
-    }
-    long long tile = lo;
-    const long long per_obj = (long long)tg.nslots * tg.ntr * tg.ntc;
-    unsigned int e0 = e_begin;
-    while (e0 < e_end) {
-        while (tg.offs[tile + 1] <= e0) ++tile;
-        const unsigned int seg_end = min(e_end, tg.offs[tile + 1]);
-        const int orel = (int)(tile / per_obj);
-        const long long rem = tile - (long long)orel * per_obj;
-        const int slot = (int)(rem / ((long long)tg.ntr * tg.ntc));
-        const int trc = (int)(rem - (long long)slot * tg.ntr * tg.ntc);
-        const int tr = trc / tg.ntc, tc = trc - tr * tg.ntc;
-        const int kfix = fix_exponent(tg.fmax, orel);
-        for (int i = threadIdx.x; i < kTileDirs * kNc; i += kSumThreads) acc[i] = 0ull;
-        __syncthreads();
-        for (unsigned int e = e0 + threadIdx.x; e < seg_end; e += kSumThreads) {
-            const unsigned int hi_ = tg.perm[e];
-            if (hi_ >= n) continue;  // every slot is filled; this only guards the read below
-            const unsigned long long code = h.tri[hi_];
-            const unsigned int dw = h.dir[hi_];
-            const unsigned int dk = dw & ~kHitClose;
-            int q;
-            if (d.list) q = (int)(dk % (unsigned int)kTileDirs);
-            else {
-                const int it = (int)(dk / (unsigned int)d.nph), jp = (int)(dk - (unsigned int)it * d.nph);
-                q = (it - tr * kTileTh) * kTileTw + (jp - tc * kTileTw);
-            }
-            tile_hit<kNc>(a, b, d, lt, code, dw, kfix, acc, q);
-        }
-        __syncthreads();
-        // the tile's words, one integer add each where not zero
-        const long long ndir = b.ndir;
-        unsigned long long* out = reinterpret_cast<unsigned long long*>(a.out);
-        for (int i = threadIdx.x; i < kTileDirs * kNc; i += kSumThreads) {
-            const unsigned long long v = acc[i];
-            if (!v) continue;
-            const int qq = i / kNc, comp = i - qq * kNc;
-            long long dk;
-            if (d.list) dk = (long long)tc * kTileDirs + qq;
-            else dk = (long long)(tr * kTileTh + qq / kTileTw) * d.nph + (tc * kTileTw + qq % kTileTw);
-            atomicAdd(out + ((((long long)orel * ndir + dk) * b.nout + slot) * kNc + comp), v);
-        }
-        __syncthreads();
-        e0 = seg_end;
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(a.out);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long code = h.tri[i];
+        const unsigned int dw = h.dir[i];
+        const CellRef c = decode_cell(a, b, (long long)(code >> 1));
+        const long long dk = (long long)(dw & ~kHitClose);
+        unsigned long long* dst = out + (((long long)c.orel * b.ndir + dk) * b.nout + (a.per_order ? c.p : 0)) * kNc;
+        sum_hit<kNc>(a, b, d, lt, code, dw, fix_exponent(fmax, c.orel), dst);
     }
 }
 
@@ -1847,15 +1700,6 @@ __global__ void tile_convert_kernel(double* out, long long per_obj, long long n,
 }
 
 }  // namespace
-
-long long tile_words(long long ntiles) { return 2 * (ntiles + 1) + (ntiles + 1 + kScanTile - 1) / kScanTile; }
-
-long long field_tiles(int nobj, int nslots, bool list, int nt, int nph, long long ndir)
-{
-    const long long ntr = list ? 1 : (nt + kTileTh - 1) / kTileTh;
-    const long long ntc = list ? (ndir + kTileDirs - 1) / kTileDirs : (nph + kTileTw - 1) / kTileTw;
-    return (long long)nobj * nslots * ntr * ntc;
-}
 
 cudaError_t launch_field_convert(double* out, long long per_obj, int nobj, const unsigned int* fmax, cudaStream_t s)
 {
@@ -1889,14 +1733,14 @@ cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s)
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
-                              int newton, cudaStream_t s, int stage, const unsigned int* fmax,
-                              unsigned int* tile_ws, unsigned int* perm)
+                              int newton, cudaStream_t s, int stage, const unsigned int* fmax)
 {
     if (b.total <= 0) return cudaSuccess;
     const int bs = 256;
     const int cb = classify_block > 0 ? classify_block : bs;
     HitArgs h{hit_tri, hit_dir, nhit, hit_cap, stage == kFieldClassify ? 0 : 1};
-    // fixed grids walk the lists: 32 blocks per SM for the large triangles, 16 for the hits
+    // fixed grids walk the lists: 32 blocks per SM for the large triangles, 16 for the hits (8 for the
+    // fixed-point sums, measured best of 8 to 64)
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1910,33 +1754,14 @@ cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirS
     if (stage != 1) {
         if (newton) {
             field_grid_hit_kernel<true><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
-        } else if (!fmax || !tile_ws || !perm) {
+        } else if (!fmax) {
             field_grid_hit_kernel<false><<<(unsigned)(16 * sms), bs, 0, s>>>(a, b, d, h);
+        } else if (a.st.near_r > 0.0) {
+            // fixed-point sums (the words turn into doubles in launch_field_convert once the launch
+            // group is complete)
+            hit_sum_kernel<6><<<(unsigned)(8 * sms), 256, 0, s>>>(a, b, d, h, fmax);
         } else {
-            // hits sorted by tile, each tile summed in fixed point (the words turn into doubles in
-            // launch_field_convert once the launch group is complete)
-            TileGrid tg;
-            tg.ntr = d.list ? 1 : (d.nt + kTileTh - 1) / kTileTh;
-            tg.ntc = d.list ? (int)((d.ndir + kTileDirs - 1) / kTileDirs) : (d.nph + kTileTw - 1) / kTileTw;
-            tg.nslots = b.nout;
-            tg.ntiles = field_tiles(b.nobj, b.nout, d.list != 0, d.nt, d.nph, d.ndir);
-            const long long n1 = tg.ntiles + 1;
-            const long long nb = (n1 + kScanTile - 1) / kScanTile;
-            tg.offs = tile_ws;
-            tg.cursor = tile_ws + n1;
-            tg.bsum = tile_ws + 2 * n1;
-            tg.perm = perm;
-            tg.fmax = fmax;
-            cudaError_t e = cudaMemsetAsync(tile_ws, 0, sizeof(unsigned int) * (size_t)(2 * n1), s);
-            if (e != cudaSuccess) return e;
-            hit_bin_kernel<<<(unsigned)(16 * sms), 256, 0, s>>>(a, b, d, h, tg, 0);
-            scan_blocks_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(tg.offs, n1, tg.bsum);
-            scan_sums_kernel<<<1, kScanThreads, 0, s>>>(tg.bsum, (int)nb);
-            scan_add_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(tg.offs, n1, tg.bsum);
-            hit_bin_kernel<<<(unsigned)(16 * sms), 256, 0, s>>>(a, b, d, h, tg, 1);
-            const unsigned gs = (unsigned)((hit_cap + kSumChunk - 1) / kSumChunk);
-            if (a.st.near_r > 0.0) tile_sum_kernel<6><<<gs, kSumThreads, 0, s>>>(a, b, d, h, tg);
-            else tile_sum_kernel<4><<<gs, kSumThreads, 0, s>>>(a, b, d, h, tg);
+            hit_sum_kernel<4><<<(unsigned)(8 * sms), 256, 0, s>>>(a, b, d, h, fmax);
         }
     }
     return cudaGetLastError();

@@ -92,8 +92,6 @@ struct GridWs {
     unsigned long long* hit_tri = nullptr;
     unsigned int* hit_dir = nullptr;
     unsigned int big_cap = 0, hit_cap = 0;
-    unsigned int* tile_ws = nullptr;     // the sort of the hits by output tile
-    unsigned int* perm = nullptr;        //   and their order (hit_cap words)
 };
 // Bytes of the workspace of plan g; carves it from base when base is not null.
 size_t grid_ws(const GridPlan& g, int np, const rtw_dirs* dirs, char* base, GridWs* w);

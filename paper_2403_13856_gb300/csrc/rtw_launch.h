@@ -86,18 +86,13 @@ cudaError_t launch_export(RaysDev st, int order, long long first, long long coun
 cudaError_t launch_dir_tables(int nt, int nph, double* tab, cudaStream_t s);
 // The square-grid field of one launch: classification of the cell triangles into (triangle,
 // direction) hits, then their sum.  Without Newton refinement and with fmax (RaysDev::fmax of the
-// launch's first object), tile_ws (tile_words(field_tiles(...)) words) and perm (hit_cap
-// words), the hits are sorted by output tile and each tile is summed in 64-bit fixed point: the
-// output words then hold integers until launch_field_convert (once per launch group, after every
-// slice).  Otherwise every hit adds its doubles with atomics.
+// launch's first object), every hit adds its contribution as 64-bit fixed-point integers: the output
+// words then hold integers until launch_field_convert (once per launch group, after every slice).
+// Otherwise every hit adds its doubles with atomics.
 cudaError_t launch_field_grid(const FieldArgs& a, const GridBatch& b, const DirSet& d, unsigned long long* big,
                               unsigned int* nbig, unsigned int big_cap, unsigned long long* hit_tri,
                               unsigned int* hit_dir, unsigned int* nhit, unsigned int hit_cap, int classify_block,
-                              int newton, cudaStream_t s, int stage = 0, const unsigned int* fmax = nullptr,
-                              unsigned int* tile_ws = nullptr, unsigned int* perm = nullptr);
-// output tiles of a launch and the words of its tile sort
-long long field_tiles(int nobj, int nslots, bool list, int nt, int nph, long long ndir);
-long long tile_words(long long ntiles);
+                              int newton, cudaStream_t s, int stage = 0, const unsigned int* fmax = nullptr);
 // fixed-point output words of nobj objects (per_obj words each) to doubles, in place
 cudaError_t launch_field_convert(double* out, long long per_obj, int nobj, const unsigned int* fmax, cudaStream_t s);
 // 2-D physical optics over a window of grid vertices [win0, win1] x [win2, win3] of one square-grid
