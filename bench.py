@@ -395,7 +395,10 @@ def precision_errors(torch, rtw, ref_rays, rays, dirs, nt, nph, p_max):
     whose focal line lies at an interface, where single precision loses the digits of det(I + d Q), or
     that took a different caustic decision in the two precisions); and the largest |F - F_64| /
     max |F_64| of the order over the directions compared and over every direction unmasked in both
-    (normwise; the second includes the edges of the support)."""
+    (normwise; the second includes the edges of the support), with the number of directions unmasked
+    in both where |F - F_64| exceeds 1e-3 max |F_64| (on the ellipsoid workload a handful, where the
+    two precisions' triangles cover a direction differently: the edge of an order's image, or of one
+    branch of it, whose rim triangles map very different directions)."""
     ndir = nt * nph
     outs = []
     for r in (ref_rays, rays):
@@ -429,7 +432,8 @@ def precision_errors(torch, rtw, ref_rays, rays, dirs, nt, nph, p_max):
         amax = float(a.max().item())
         e = {"order": p, "directions": int(keep.sum().item()), "left_out": int((big & ~keep).sum().item()),
              "normwise_max": float(dF[unmasked].max().item()) / amax if amax > 0 and bool(unmasked.any()) else None,
-             "normwise_interior": float(dF[keep].max().item()) / amax if amax > 0 and bool(keep.any()) else None}
+             "normwise_interior": float(dF[keep].max().item()) / amax if amax > 0 and bool(keep.any()) else None,
+             "dF_above_1e-3_max": int((unmasked & big & (dF > 1e-3 * amax)).sum().item())}
         if rel.numel():
             q = torch.tensor([0.5, 0.999], dtype=torch.float64, device=rel.device)
             ra, pa = torch.quantile(rel, q).tolist(), torch.quantile(ph, q).tolist()
