@@ -640,13 +640,15 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         T le1r = T(0), le1i = T(0), le2r = T(0), le2i = T(0), lt21 = T(0), lt22 = T(0);
         // the wave reflected inside at the last interaction is never used
         if (q == 1 || q <= pmax) {
-            lk0 = (tx - kin * nx) * inv_ki;
-            lk1 = (ty - kin * ny) * inv_ki;
-            lk2 = (tz - kin * nz) * inv_ki;
-            const T dn = T(-2) * kin;
-            lq11 = (ki * Qe11 + C11 * dn) * inv_ki;
-            lq12 = (-ki * ci * Qe12 + C12 * dn) * inv_ki * inv_ci;
-            lq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_ki * inv_ci * inv_ci;
+            // k_l = (tau - k_in n) / k_i = k - 2 ci n; in the entries below (the general ones with
+            // k' = k_i and n.(k_l - k_i) = -2 k_in) the factors k_i and ci cancel exactly
+            const T ci2 = T(2) * ci;
+            lk0 = k0v - ci2 * nx;
+            lk1 = k1v - ci2 * ny;
+            lk2 = k2v - ci2 * nz;
+            lq11 = Qe11 - ci2 * C11;
+            lq12 = -Qe12 - T(2) * C12;
+            lq22 = Qe22 - T(2) * C22 * inv_ci;
             le1r = rp_r * Ep_r - rp_i * Ep_i;
             le1i = rp_r * Ep_i + rp_i * Ep_r;
             le2r = rq_r * Eq_r - rq_i * Eq_i;
@@ -667,7 +669,7 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
             const T dn = ktn - kin;
             const T inv_ct = kt * inv_ktn;
             tq11 = (ki * Qe11 + C11 * dn) * inv_kt;
-            tq12 = -(-ki * ci * Qe12 + C12 * dn) * inv_kt * inv_ct;
+            tq12 = (kin * Qe12 - C12 * dn) * inv_ktn;  // inv_kt inv_ct = 1 / k_tn
             tq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
             te1r = tp_r * Ep_r;
             te1i = tp_r * Ep_i;
