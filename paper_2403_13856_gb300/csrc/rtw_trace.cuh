@@ -594,12 +594,20 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
             C12 = (ex * wsx + ey * wsy + ez * wsz) * inv_gn;
             C22 = (s2x * wsx + s2y * wsy + s2z * wsz) * inv_gn;
         }
-        // Eq. (SnellVec): common tangential wave vector
+        // Eq. (SnellVec): the common tangential wave vector tau = k_i k - k_in n has |tau|^2 =
+        // k_i^2 - k_in^2 for a unit k; single precision, whose k is unit only to 6e-8, forms tau
         const T ki = k0 * n_in, kt = k0 * n_out;
         const T kin = ki * ci;
-        const T tx = ki * k0v - kin * nx, ty = ki * k1v - kin * ny, tz = ki * k2v - kin * nz;
-        const T tau2 = tx * tx + ty * ty + tz * tz;
-        const T ktn2 = kt * kt - tau2;
+        constexpr bool kTau = std::is_same<T, float>::value;
+        T tx = T(0), ty = T(0), tz = T(0), ktn2;
+        if constexpr (kTau) {
+            tx = ki * k0v - kin * nx;
+            ty = ki * k1v - kin * ny;
+            tz = ki * k2v - kin * nz;
+            ktn2 = kt * kt - (tx * tx + ty * ty + tz * tz);
+        } else {
+            ktn2 = (kt * kt - ki * ki) + kin * kin;
+        }
         const T mr = (q == 1) ? mo : inv_mo, mr2 = mr * mr;  // n_out / n_in
         // Eq. (Fres)
         const bool tok = ktn2 > T(0);
@@ -662,15 +670,25 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         T te1r = T(0), te1i = T(0), te2r = T(0), te2i = T(0), tt21 = T(0), tt22 = T(0);
         T ct = T(0);
         if (tok) {
-            tk0 = (tx + ktn * nx) * inv_kt;
-            tk1 = (ty + ktn * ny) * inv_kt;
-            tk2 = (tz + ktn * nz) * inv_kt;
-            ct = ktn * inv_kt;  // signed cosine of the transmitted wave
             const T dn = ktn - kin;
             const T inv_ct = kt * inv_ktn;
-            tq11 = (ki * Qe11 + C11 * dn) * inv_kt;
+            ct = ktn * inv_kt;  // signed cosine of the transmitted wave
             tq12 = (kin * Qe12 - C12 * dn) * inv_ktn;  // inv_kt inv_ct = 1 / k_tn
-            tq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
+            if constexpr (kTau) {
+                tk0 = (tx + ktn * nx) * inv_kt;
+                tk1 = (ty + ktn * ny) * inv_kt;
+                tk2 = (tz + ktn * nz) * inv_kt;
+                tq11 = (ki * Qe11 + C11 * dn) * inv_kt;
+                tq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
+            } else {
+                // k_t = (tau + k_tn n) / k_t = rio k + g n, rio = k_i / k_t, g = (k_tn - k_in) / k_t
+                const T rio = ki * inv_kt, g = dn * inv_kt;
+                tk0 = rio * k0v + g * nx;
+                tk1 = rio * k1v + g * ny;
+                tk2 = rio * k2v + g * nz;
+                tq11 = rio * Qe11 + C11 * g;
+                tq22 = (rio * ci * ci * Qe22 + C22 * g) * (inv_ct * inv_ct);
+            }
             te1r = tp_r * Ep_r;
             te1i = tp_r * Ep_i;
             te2r = tq_r * Eq_r;
