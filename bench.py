@@ -47,7 +47,7 @@ def _oracle_flops():
 FP64_NOMINAL_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload at 4e6 rays
 # (ncu: 6.68 MB + 3.18 GB, the ray-state write)
-TRACE_TRAFFIC_BYTES = 6_680_000 + 3_180_000_000
+TRACE_TRAFFIC_BYTES = 3_398_144 + 3_180_410_368
 TRACE_TRAFFIC_NOTE = "DRAM bytes of one launch at 4e6 rays (ncu); profiles/trace_kernel_fp64_ellipsoid_4e6rays.md"
 # FP64 flops the kernel executes per interaction (ncu: DFMA x 2 + DMUL + DADD over the interactions)
 EXECUTED_FLOPS_PER_INTERACTION = 462

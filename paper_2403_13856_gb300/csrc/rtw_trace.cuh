@@ -42,13 +42,18 @@ struct FarRecord {
     uint32_t flags;
 };
 
-__device__ __forceinline__ int neg_eigs_sym(double a11, double a12, double a22)
+// negative eigenvalues of a symmetric 2 x 2 matrix from its trace and determinant
+__device__ __forceinline__ int neg_eigs_td(double tr, double det)
 {
-    double det = a11 * a22 - a12 * a12, tr = a11 + a22;
     if (det < 0.0) return 1;
     if (det > 0.0 && tr < 0.0) return 2;
     if (det == 0.0 && tr < 0.0) return 1;
     return 0;
+}
+
+__device__ __forceinline__ int neg_eigs_sym(double a11, double a12, double a22)
+{
+    return neg_eigs_td(a11 + a22, a11 * a22 - a12 * a12);
 }
 
 __device__ __forceinline__ void symv(const double* W, double x, double y, double z, double& ox, double& oy,
@@ -57,6 +62,17 @@ __device__ __forceinline__ void symv(const double* W, double x, double y, double
     ox = W[0] * x + W[1] * y + W[2] * z;
     oy = W[1] * x + W[3] * y + W[4] * z;
     oz = W[2] * x + W[4] * y + W[5] * z;
+}
+
+// amp (-i)^nf (er + i ei): a quarter turn per focal line, by swaps and signs
+__device__ __forceinline__ void focal_phase(int nf, double amp, double er, double ei, double& ar, double& ai)
+{
+    switch (nf & 3) {
+    case 1: ar = amp * ei; ai = -amp * er; break;
+    case 2: ar = -amp * er; ai = -amp * ei; break;
+    case 3: ar = -amp * ei; ai = amp * er; break;
+    default: ar = amp * er; ai = amp * ei; break;
+    }
 }
 
 // Far-field record of an exit wave: F = E' sqrt(D_legs / |det Q'|) (-i)^{N_f}, Psi = k0 (L - s.r),
@@ -69,18 +85,12 @@ __device__ __forceinline__ bool far_record(const ObjDev& o, const ExitWave& w, F
     // curvature) sends its energy into a single direction: a caustic at infinity, kept as a valid
     // ray with the caustic flag and no amplitude
     const bool flat = !(fabs(detQ) > 0.0);
-    int nf = w.nf_legs + neg_eigs_sym(w.q11, w.q12, w.q22);
+    const int nf = w.nf_legs + neg_eigs_td(w.q11 + w.q22, detQ);
     double amp = flat ? 0.0 : rsqrt(fabs(detQ) * w.pdet);
     double D = amp * amp;
-    double pr = 1.0, pi = 0.0;  // (-i)^nf
-    switch (nf & 3) {
-    case 1: pr = 0.0; pi = -1.0; break;
-    case 2: pr = -1.0; pi = 0.0; break;
-    case 3: pr = 0.0; pi = 1.0; break;
-    default: break;
-    }
-    double a1r = amp * (w.e1r * pr - w.e1i * pi), a1i = amp * (w.e1r * pi + w.e1i * pr);
-    double a2r = amp * (w.e2r * pr - w.e2i * pi), a2i = amp * (w.e2r * pi + w.e2i * pr);
+    double a1r, a1i, a2r, a2i;
+    focal_phase(nf, amp, w.e1r, w.e1i, a1r, a1i);
+    focal_phase(nf, amp, w.e2r, w.e2i, a2r, a2i);
     double v2x = w.ep[1] * w.k[2] - w.ep[2] * w.k[1];
     double v2y = w.ep[2] * w.k[0] - w.ep[0] * w.k[2];
     double v2z = w.ep[0] * w.k[1] - w.ep[1] * w.k[0];
@@ -121,18 +131,12 @@ __device__ __forceinline__ bool near_record(const ObjDev& o, const ExitWave& w, 
     const double a11 = 1.0 + t * w.q11, a12 = t * w.q12, a22 = 1.0 + t * w.q22;
     const double detA = a11 * a22 - a12 * a12;
     if (!(fabs(detA) > 0.0) || !isfinite(detA)) return false;
-    const int nf = w.nf_legs + neg_eigs_sym(a11, a12, a22);
+    const int nf = w.nf_legs + neg_eigs_td(a11 + a22, detA);
     const double amp = rsqrt(fabs(detA) * w.pdet);
     const double D = amp * amp;
-    double pr = 1.0, pi = 0.0;  // (-i)^nf
-    switch (nf & 3) {
-    case 1: pr = 0.0; pi = -1.0; break;
-    case 2: pr = -1.0; pi = 0.0; break;
-    case 3: pr = 0.0; pi = 1.0; break;
-    default: break;
-    }
-    const double a1r = amp * (w.e1r * pr - w.e1i * pi), a1i = amp * (w.e1r * pi + w.e1i * pr);
-    const double a2r = amp * (w.e2r * pr - w.e2i * pi), a2i = amp * (w.e2r * pi + w.e2i * pr);
+    double a1r, a1i, a2r, a2i;
+    focal_phase(nf, amp, w.e1r, w.e1i, a1r, a1i);
+    focal_phase(nf, amp, w.e2r, w.e2i, a2r, a2i);
     const double v2x = w.ep[1] * w.k[2] - w.ep[2] * w.k[1];
     const double v2y = w.ep[2] * w.k[0] - w.ep[0] * w.k[2];
     const double v2z = w.ep[0] * w.k[1] - w.ep[1] * w.k[0];
@@ -229,6 +233,21 @@ __device__ __forceinline__ double chord_to_surface(const ObjDev& o, const T* Wt,
         d -= (double)((float)f / (float)fp);
     }
     return d;
+}
+
+// Chord from the surface point r along the inward direction k (the far root of the quadric) with
+// A = k^T W k and 1/A given (the reciprocal formed with the interaction's others) and wp = W (r - c),
+// the gradient at r; double precision only (single precision takes chord_to_surface and its polish).
+template <typename T>
+__device__ __forceinline__ double chord_inside(const ObjDev& o, const double r[3], const T k[3], T Ak, T iAk,
+                                               const T* wp)
+{
+    const T px = (T)(r[0] - o.c[0]), py = (T)(r[1] - o.c[1]), pz = (T)(r[2] - o.c[2]);
+    const T Bk = k[0] * wp[0] + k[1] * wp[1] + k[2] * wp[2];
+    const T Ck = px * wp[0] + py * wp[1] + pz * wp[2] - T(1);
+    T dk = Bk * Bk - Ak * Ck;
+    if (dk < T(0)) dk = T(0);
+    return (double)((-Bk + sqrt(dk)) * iAk);
 }
 
 // ---- superellipsoid F(x) = sum_i |u_i|^(2e) = 1 (e > 1), u = diag(1/a) Rb^T (x - c) ----
@@ -609,17 +628,48 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
             ktn2 = (kt * kt - ki * ki) + kin * kin;
         }
         const T mr = (q == 1) ? mo : inv_mo, mr2 = mr * mr;  // n_out / n_in
-        // Eq. (Fres)
+        const T inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
         const bool tok = ktn2 > T(0);
         T ktn = T(0);
+        if (tok) ktn = copysign(sqrt(ktn2), kin);
+        // directions of the reflected wave, k_l = (tau - k_in n) / k_i = k - 2 ci n, and of the
+        // transmitted one, k_t = (tau + k_tn n) / k_t (= rio k + g n, rio = k_i / k_t, g = (k_tn - k_in) / k_t)
+        const T ci2 = T(2) * ci;
+        const T lk0 = k0v - ci2 * nx, lk1 = k1v - ci2 * ny, lk2 = k2v - ci2 * nz;
+        T tk0 = T(0), tk1 = T(0), tk2 = T(0), dn = T(0), rio = T(0), g = T(0);
+        if (tok) {
+            dn = ktn - kin;
+            if constexpr (kTau) {
+                tk0 = (tx + ktn * nx) * inv_kt;
+                tk1 = (ty + ktn * ny) * inv_kt;
+                tk2 = (tz + ktn * nz) * inv_kt;
+            } else {
+                rio = ki * inv_kt;
+                g = dn * inv_kt;
+                tk0 = rio * k0v + g * nx;
+                tk1 = rio * k1v + g * ny;
+                tk2 = rio * k2v + g * nz;
+            }
+        }
+        // in double precision, W k and A = k^T W k of the chord that follows (along the transmitted
+        // wave at the entry, the reflected one after it): its 1/A joins the reciprocal below
+        constexpr bool kFoldA = std::is_same<T, double>::value && !kSuper;
+        T cwk[3] = {T(0), T(0), T(0)}, cAk = T(1), iAk = T(1);
+        if (kFoldA && q <= pmax && (q > 1 || tok)) {
+            const T c0 = q == 1 ? tk0 : lk0, c1 = q == 1 ? tk1 : lk1, c2 = q == 1 ? tk2 : lk2;
+            symvT(W, c0, c1, c2, cwk[0], cwk[1], cwk[2]);
+            cAk = c0 * cwk[0] + c1 * cwk[1] + c2 * cwk[2];
+        }
+        // Eq. (Fres)
         T rp_r, rp_i, rq_r, rq_i, tp_r = T(0), tq_r = T(0);
         T inv_ci, inv_ktn = T(0);
         if (tok) {
-            ktn = copysign(sqrt(ktn2), kin);
-            // one reciprocal serves 1/(k_in + k_tn), 1/(m^2 k_in + k_tn), 1/ci and 1/k_tn
+            // one reciprocal serves 1/(k_in + k_tn), 1/(m^2 k_in + k_tn), 1/ci, 1/k_tn (and 1/A)
             const T den1 = kin + ktn, den2 = mr2 * kin + ktn;
-            const T aa = den1 * den2, bb = ci * ktn;
-            const T inv = T(1) / (aa * bb);
+            const T aa = den1 * den2, bb = ci * ktn, P = aa * bb;
+            const T invA = T(1) / (P * cAk);
+            const T inv = cAk * invA;
+            iAk = P * invA;
             const T i1 = den2 * bb * inv, i2 = den1 * bb * inv;
             inv_ci = aa * ktn * inv;
             inv_ktn = aa * ci * inv;
@@ -632,28 +682,35 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         } else {
             // total internal reflection: k_tn = i sign(k_in) kappa
             const T kap = copysign(sqrt(-ktn2), kin);
-            const T d1 = T(1) / (kin * kin + kap * kap);
+            const T u = mr2 * kin;
+            T d1, d2;
+            if constexpr (kFoldA) {
+                // one reciprocal for both denominators, 1/ci and 1/A
+                const T D1 = kin * kin + kap * kap, D2 = u * u + kap * kap, P = D1 * D2 * ci;
+                const T invA = T(1) / (P * cAk);
+                const T inv = cAk * invA;
+                iAk = P * invA;
+                d1 = D2 * ci * inv;
+                d2 = D1 * ci * inv;
+                inv_ci = D1 * D2 * inv;
+            } else {
+                d1 = T(1) / (kin * kin + kap * kap);
+                d2 = T(1) / (u * u + kap * kap);
+                inv_ci = T(1) / ci;
+            }
             rp_r = (kin * kin - kap * kap) * d1;
             rp_i = T(-2) * kin * kap * d1;
-            const T u = mr2 * kin;
-            const T d2 = T(1) / (u * u + kap * kap);
             rq_r = (u * u - kap * kap) * d2;
             rq_i = T(-2) * u * kap * d2;
-            inv_ci = T(1) / ci;
         }
-        const T inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
         // reflected wave: k_l = tau - k_in n, signed cosine -ci; Eq. (WavefrontEqVec) in the
         // diagonal bases with n.(k_l - k_i) = -2 k_in
-        T lk0 = T(0), lk1 = T(0), lk2 = T(0), lq11 = T(0), lq12 = T(0), lq22 = T(0);
+        T lq11 = T(0), lq12 = T(0), lq22 = T(0);
         T le1r = T(0), le1i = T(0), le2r = T(0), le2i = T(0), lt21 = T(0), lt22 = T(0);
         // the wave reflected inside at the last interaction is never used
         if (q == 1 || q <= pmax) {
-            // k_l = (tau - k_in n) / k_i = k - 2 ci n; in the entries below (the general ones with
-            // k' = k_i and n.(k_l - k_i) = -2 k_in) the factors k_i and ci cancel exactly
-            const T ci2 = T(2) * ci;
-            lk0 = k0v - ci2 * nx;
-            lk1 = k1v - ci2 * ny;
-            lk2 = k2v - ci2 * nz;
+            // the entries of the general equation with k' = k_i and n.(k_l - k_i) = -2 k_in, the
+            // factors k_i and ci cancelled exactly
             lq11 = Qe11 - ci2 * C11;
             lq12 = -Qe12 - T(2) * C12;
             lq22 = Qe22 - T(2) * C22 * inv_ci;
@@ -666,26 +723,17 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
                 lt22 = -Te22;
             }
         }
-        T tk0 = T(0), tk1 = T(0), tk2 = T(0), tq11 = T(0), tq12 = T(0), tq22 = T(0);
+        T tq11 = T(0), tq12 = T(0), tq22 = T(0);
         T te1r = T(0), te1i = T(0), te2r = T(0), te2i = T(0), tt21 = T(0), tt22 = T(0);
         T ct = T(0);
         if (tok) {
-            const T dn = ktn - kin;
             const T inv_ct = kt * inv_ktn;
             ct = ktn * inv_kt;  // signed cosine of the transmitted wave
             tq12 = (kin * Qe12 - C12 * dn) * inv_ktn;  // inv_kt inv_ct = 1 / k_tn
             if constexpr (kTau) {
-                tk0 = (tx + ktn * nx) * inv_kt;
-                tk1 = (ty + ktn * ny) * inv_kt;
-                tk2 = (tz + ktn * nz) * inv_kt;
                 tq11 = (ki * Qe11 + C11 * dn) * inv_kt;
                 tq22 = (ki * ci * ci * Qe22 + C22 * dn) * inv_kt * inv_ct * inv_ct;
             } else {
-                // k_t = (tau + k_tn n) / k_t = rio k + g n, rio = k_i / k_t, g = (k_tn - k_in) / k_t
-                const T rio = ki * inv_kt, g = dn * inv_kt;
-                tk0 = rio * k0v + g * nx;
-                tk1 = rio * k1v + g * ny;
-                tk2 = rio * k2v + g * nz;
                 tq11 = rio * Qe11 + C11 * g;
                 tq22 = (rio * ci * ci * Qe22 + C22 * g) * (inv_ct * inv_ct);
             }
@@ -755,6 +803,12 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         double dd;
         if constexpr (kSuper) {
             dd = super_chord(o, r, kk);
+        } else if constexpr (kFoldA) {
+            const T wg[3] = {gx, gy, gz};
+            dd = chord_inside<T>(o, r, kk, cAk, iAk, wg);
+            wk[0] = cwk[0];
+            wk[1] = cwk[1];
+            wk[2] = cwk[2];
         } else {
             bool ok;
             const T wg[3] = {gx, gy, gz};
