@@ -50,7 +50,7 @@ FP64_NOMINAL_GFLOPS = 1250.0
 TRACE_TRAFFIC_BYTES = 3_398_144 + 3_180_410_368
 TRACE_TRAFFIC_NOTE = "DRAM bytes of one launch at 4e6 rays (ncu); profiles/trace_kernel_fp64_ellipsoid_4e6rays.md"
 # FP64 flops the kernel executes per interaction (ncu: DFMA x 2 + DMUL + DADD over the interactions)
-EXECUTED_FLOPS_PER_INTERACTION = 462
+EXECUTED_FLOPS_PER_INTERACTION = 431
 FLOPS_PER_INTERACTION, FLOPS_SOURCE = _oracle_flops()
 
 
