@@ -793,8 +793,9 @@ def bench_ellipsoid(args, rank, world, local, dist):
                      "frac_executed": EXECUTED_FLOPS_PER_INTERACTION * units / tr / 1e9 / peak,
                      "executed_flops_per_interaction": EXECUTED_FLOPS_PER_INTERACTION,
                      "note": "the oracle's operation count per interaction (760) exceeds what the kernel "
-                             "executes (462: one reciprocal where the oracle divides), so the algorithmic "
-                             "rate passes the DFMA-chain peak; the FP64 pipe is 88.5 % busy (ncu)",
+                             "executes (431: two reciprocals where the oracle divides, reduced reflection and "
+                             "transmission forms), so the algorithmic rate passes the DFMA-chain peak; the FP64 "
+                             "pipe is 88.3 % busy (ncu)",
                      "traffic": TRACE_TRAFFIC_BYTES, "traffic_note": TRACE_TRAFFIC_NOTE},
         "roofline_field": {"kernels": "field_grid_kernel, field_grid_big_kernel, hit_sum_kernel, tile_convert_kernel",
                            "bound": "hbm", "achieved": field_bytes / tf / 1e9, "peak": hbm, "unit": "GB/s",
