@@ -831,7 +831,8 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         q12 = q12 * idet;
         q22 = (q22 + d * dq) * idet;
         pdet *= fabs(detA);
-        nf += neg_eigs_sym((double)A11, (double)A12, (double)A22);
+        if constexpr (std::is_same<T, double>::value) nf += neg_eigs_td(A11 + A22, detA);
+        else nf += neg_eigs_sym((double)A11, (double)A12, (double)A22);
         if (detA < T(0)) sT = -sT;
         if (kJ) {
             const T n11 = A11 * T11 + A12 * T21, n12 = A11 * T12 + A12 * T22;
