@@ -799,7 +799,7 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         if (q == pmax + 1) break;
         // chord to the next surface point along the inward direction
         const T kk[3] = {k0v, k1v, k2v};
-        T wk[3];
+        T wk[3] = {T(0), T(0), T(0)};
         double dd;
         if constexpr (kSuper) {
             dd = super_chord(o, r, kk);
@@ -816,7 +816,7 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         }
         if (!(dd > 0.0)) return;
         const T d = (T)dd;
-        if (kCarryGrad) {
+        if constexpr (kCarryGrad) {
             gnext[0] = gx + d * wk[0];
             gnext[1] = gy + d * wk[1];
             gnext[2] = gz + d * wk[2];
