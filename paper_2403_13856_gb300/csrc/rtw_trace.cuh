@@ -566,15 +566,25 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         // e_perp = k x n / |k x n| (normal of the incident plane)
         T ex = k1v * nz - k2v * ny, ey = k2v * nx - k0v * nz, ez = k0v * ny - k1v * nx;
         const T el2 = ex * ex + ey * ey + ez * ez;
+        T il = T(0);
         if (el2 < T(1e-24)) {
             ex = a0; ey = a1; ez = a2;
         } else {
-            const T il = rsqrt(el2);
+            il = rsqrt(el2);
             ex *= il; ey *= il; ez *= il;
         }
-        // rotation of the incident basis (a, b = a x k) onto (e_perp, e_perp x k)
-        const T b0 = a1 * k2v - a2 * k1v, b1 = a2 * k0v - a0 * k2v, b2 = a0 * k1v - a1 * k0v;
-        const T cr = a0 * ex + a1 * ey + a2 * ez, sr = b0 * ex + b1 * ey + b2 * ez;
+        // rotation of the incident basis (a, b = a x k) onto (e_perp, e_perp x k): cr = a.e_perp and
+        // sr = b.e_perp = ((a.k) ci - a.n) / |k x n|, which is -(a.n) / |k x n| since a is normal to k
+        // (0 where e_perp falls back to a); the other precisions, whose a.k is zero only to their
+        // rounding, form b
+        const T cr = a0 * ex + a1 * ey + a2 * ez;
+        T sr;
+        if constexpr (!std::is_same<T, double>::value) {
+            const T b0 = a1 * k2v - a2 * k1v, b1 = a2 * k0v - a0 * k2v, b2 = a0 * k1v - a1 * k0v;
+            sr = b0 * ex + b1 * ey + b2 * ez;
+        } else {
+            sr = -(a0 * nx + a1 * ny + a2 * nz) * il;
+        }
         const T Ep_r = E1r * cr + E2r * sr, Ep_i = E1i * cr + E2i * sr;
         const T Eq_r = -E1r * sr + E2r * cr, Eq_i = -E1i * sr + E2i * cr;
         const T cc = cr * cr, ss = sr * sr, cs = cr * sr;
@@ -714,10 +724,17 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
             lq11 = Qe11 - ci2 * C11;
             lq12 = -Qe12 - T(2) * C12;
             lq22 = Qe22 - T(2) * C22 * inv_ci;
-            le1r = rp_r * Ep_r - rp_i * Ep_i;
-            le1i = rp_r * Ep_i + rp_i * Ep_r;
-            le2r = rq_r * Eq_r - rq_i * Eq_i;
-            le2i = rq_r * Eq_i + rq_i * Eq_r;
+            if (std::is_same<T, double>::value && tok) {  // real coefficients
+                le1r = rp_r * Ep_r;
+                le1i = rp_r * Ep_i;
+                le2r = rq_r * Eq_r;
+                le2i = rq_r * Eq_i;
+            } else {
+                le1r = rp_r * Ep_r - rp_i * Ep_i;
+                le1i = rp_r * Ep_i + rp_i * Ep_r;
+                le2r = rq_r * Eq_r - rq_i * Eq_i;
+                le2i = rq_r * Eq_i + rq_i * Eq_r;
+            }
             if (kJ) {
                 lt21 = -Te21;
                 lt22 = -Te22;
