@@ -77,6 +77,26 @@ def test_batch_small_per_order_vs_oracle(rtw, oracle_mod, variant):
         compare(got[i], ref, gm[i], rm)
 
 
+def test_batch_classification_blocks_give_identical_fields(rtw):
+    """The classification queues its block's small triangles in shared memory and finishes them after
+    a barrier, so the block size changes which thread tests which triangle and the order of the hits,
+    never the result: with the hits summed as fixed-point integers the field of every block size the
+    autotuner may choose (64, 128, 256 threads) is the same bit for bit, summed and per order, masks
+    included."""
+    from paper_2403_13856_gb300 import workloads as W
+
+    specs, rays = W.batch_objects(12, **SMALL)
+    obj = make_batch(rtw, specs)
+    p_max, nt, nph = 4, 48, 96
+    for flags in (0, rtw.RTW_FIELD_PER_ORDER):
+        res = [run_batch(rtw, obj, rays, p_max, nt, nph, flags=flags, classify_block=cb)[:2] for cb in (64, 128, 256)]
+        out0, mask0 = res[0]
+        assert torch.count_nonzero(out0).item() > 1000
+        for out, mask in res[1:]:
+            assert torch.equal(out.view(torch.int64), out0.view(torch.int64))
+            assert torch.equal(mask, mask0)
+
+
 def test_batch_graph_replay_and_chunking_agree(rtw):
     """Graph replay reproduces the eager run; one chunk and many chunks agree (the same sums in
     another order of atomic additions: relative 1e-12)."""
