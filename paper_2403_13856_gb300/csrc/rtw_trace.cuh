@@ -247,7 +247,8 @@ __device__ __forceinline__ double chord_inside(const ObjDev& o, const double r[3
     const T Ck = px * wp[0] + py * wp[1] + pz * wp[2] - T(1);
     T dk = Bk * Bk - Ak * Ck;
     if (dk < T(0)) dk = T(0);
-    return (double)((-Bk + sqrt(dk)) * iAk);
+    const T sq = dk > T(0) ? dk * rsqrt(dk) : T(0);  // rsqrt: 1 ulp, no correctly rounded root needed
+    return (double)((-Bk + sq) * iAk);
 }
 
 // ---- superellipsoid F(x) = sum_i |u_i|^(2e) = 1 (e > 1), u = diag(1/a) Rb^T (x - c) ----
@@ -641,7 +642,17 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
         const T inv_ki = (q == 1) ? ik_host : ik_obj, inv_kt = (q == 1) ? ik_obj : ik_host;
         const bool tok = ktn2 > T(0);
         T ktn = T(0);
-        if (tok) ktn = copysign(sqrt(ktn2), kin);
+        // double precision: |k_tn| and 1 / |k_tn| from one reciprocal square root (1 ulp)
+        constexpr bool kRootRecip = std::is_same<T, double>::value;
+        T rktn = T(0);
+        if (tok) {
+            if constexpr (kRootRecip) {
+                rktn = rsqrt(ktn2);
+                ktn = copysign(ktn2 * rktn, kin);
+            } else {
+                ktn = copysign(sqrt(ktn2), kin);
+            }
+        }
         // directions of the reflected wave, k_l = (tau - k_in n) / k_i = k - 2 ci n, and of the
         // transmitted one, k_t = (tau + k_tn n) / k_t (= rio k + g n, rio = k_i / k_t, g = (k_tn - k_in) / k_t)
         const T ci2 = T(2) * ci;
@@ -682,7 +693,8 @@ __device__ void trace_ray(const ObjDev& o, double x, double y, int pmax, Sink& s
             iAk = P * invA;
             const T i1 = den2 * bb * inv, i2 = den1 * bb * inv;
             inv_ci = aa * ktn * inv;
-            inv_ktn = aa * ci * inv;
+            if constexpr (kRootRecip) inv_ktn = copysign(rktn, kin);
+            else inv_ktn = aa * ci * inv;
             rp_r = (kin - ktn) * i1;
             rq_r = (mr2 * kin - ktn) * i2;
             tp_r = T(2) * kin * i1;
