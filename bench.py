@@ -47,10 +47,10 @@ def _oracle_flops():
 FP64_NOMINAL_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one trace_kernel_fp64 launch on the ellipsoid workload at 4e6 rays
 # (ncu: 6.68 MB + 3.18 GB, the ray-state write)
-TRACE_TRAFFIC_BYTES = 2_673_920 + 3_180_083_968
+TRACE_TRAFFIC_BYTES = 6_674_944 + 3_180_807_168
 TRACE_TRAFFIC_NOTE = "DRAM bytes of one launch at 4e6 rays (ncu); profiles/trace_kernel_fp64_ellipsoid_4e6rays.md"
 # FP64 flops the kernel executes per interaction (ncu: DFMA x 2 + DMUL + DADD over the interactions)
-EXECUTED_FLOPS_PER_INTERACTION = 417
+EXECUTED_FLOPS_PER_INTERACTION = 407
 FLOPS_PER_INTERACTION, FLOPS_SOURCE = _oracle_flops()
 
 
@@ -793,9 +793,9 @@ def bench_ellipsoid(args, rank, world, local, dist):
                      "frac_executed": EXECUTED_FLOPS_PER_INTERACTION * units / tr / 1e9 / peak,
                      "executed_flops_per_interaction": EXECUTED_FLOPS_PER_INTERACTION,
                      "note": "the oracle's operation count per interaction (760) exceeds what the kernel "
-                             "executes (417: two reciprocals where the oracle divides, reduced reflection and "
+                             "executes (407: two reciprocals where the oracle divides, reduced reflection and "
                              "transmission forms), so the algorithmic rate passes the DFMA-chain peak; the FP64 "
-                             "pipe is 87.7 % busy (ncu)",
+                             "pipe is 87.6 % busy (ncu)",
                      "traffic": TRACE_TRAFFIC_BYTES, "traffic_note": TRACE_TRAFFIC_NOTE},
         "roofline_field": {"kernels": "field_grid_kernel, field_grid_big_kernel, hit_sum_kernel, tile_convert_kernel",
                            "bound": "hbm", "achieved": field_bytes / tf / 1e9, "peak": hbm, "unit": "GB/s",
